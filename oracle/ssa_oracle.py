@@ -1,0 +1,372 @@
+"""CPU FP64 oracle for SSA, MSSA, 2D-SSA and Shaped 2D-SSA.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+statement of what the GPU library computes.  Only the test-suite, the smoke
+check and the benchmark's CPU-baseline leg may import it; the library never
+does, and the library fails loudly instead of falling back to it.
+
+It shares no code with the CUDA path: no FFT, no Lanczos, no packed spectra.
+Every quantity is formed from its definition in the paper:
+
+* shapes -- the window set (Sec. 5.1, ordered lexicographically = column-major),
+  the origin set ``K = {kappa : L (+) {kappa} subset N}`` (eq. sh_Ks) by brute
+  force over all origins, and the reconstructable set ``N' = L (+) K``;
+* the trajectory matrix -- built entry by entry from ``X_ij = x_{l_i (+) k_j}``
+  (eq. ssa_embedding for 1D, eq. mssa_embedding for stacked series, eqs.
+  block_hankel_cols / qh_mat for images), using 0-based indices, so the paper's
+  shifted sum ``l (+) k = l + k - 1`` becomes ``l + k``;
+* the SVD step -- exactly as Step 2 of Sec. 2.1 states it: ``S = X X^T``,
+  eigenvalues ``lambda_1 >= ...`` with eigenvectors ``U_j`` and factor vectors
+  ``V_j = X^T U_j / sqrt(lambda_j)`` (eq. mmexp); a one-sided Jacobi SVD of the
+  explicit matrix is kept beside it as an independent second route;
+* reconstruction -- the projection ``Pi^(H)`` of Step 4 written out: every
+  entry ``(i, j)`` of the grouped matrix is added into the data element
+  ``l_i (+) k_j`` and divided by the count ``w_k = |A_k|`` of entries that map
+  there (eq. res_decomp and the averaging formula above it).
+
+A "problem" is a list of channels (one for 1D and 2D, ``s`` for MSSA), each an
+``(Nx, Ny)`` float64 array with NaN marking missing values, sharing one window
+shape.  The MSSA trajectory matrix is the horizontal stack of the channels'
+matrices (eq. mssa_embedding); a 1D series of length N is the ``(N, 1)`` array.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "Problem", "window_set", "origin_set", "trajectory_matrix",
+    "trajectory_columns", "weights", "svd_eigen", "svd_jacobi", "decompose",
+    "reconstruct", "reconstruct_at", "matvec", "rmatvec",
+]
+
+
+# ---------------------------------------------------------------- shapes
+def window_set(lx: int, ly: int = 1, wmask=None) -> np.ndarray:
+    """Window shape as an ``(L, 2)`` int array of 0-based ``(l_x, l_y)``.
+
+    Lexicographic order in the paper's sense (Sec. 5.1: the order in which the
+    elements appear in the column-major vectorisation), i.e. sorted by
+    ``l_y`` then ``l_x``.  ``wmask`` (``lx x ly`` bool) selects a sub-shape.
+    """
+    if wmask is None:
+        wmask = np.ones((lx, ly), dtype=bool)
+    wmask = np.asarray(wmask, dtype=bool)
+    assert wmask.shape == (lx, ly)
+    out = [(a, b) for b in range(ly) for a in range(lx) if wmask[a, b]]
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
+
+
+def observed(x: np.ndarray, mask=None) -> np.ndarray:
+    """The set N: pixels that are inside ``mask`` and not NaN (Sec. 5.2: NA
+    values and the user mask are both excluded)."""
+    ok = ~np.isnan(x)
+    if mask is not None:
+        ok &= np.asarray(mask, dtype=bool)
+    return ok
+
+
+def origin_set(obs: np.ndarray, Lset: np.ndarray) -> np.ndarray:
+    """All origins ``kappa`` with ``L (+) {kappa}`` inside N (eq. sh_Ks).
+
+    Every candidate origin of the grid starts admissible and is struck out as
+    soon as one window element ``l + kappa`` falls on a pixel outside N (one
+    shifted comparison of the whole grid per window element).  Returned as a
+    ``(K, 2)`` array in lexicographic (column-major) order.
+    """
+    nx, ny = obs.shape
+    ex = int(Lset[:, 0].max()) + 1
+    ey = int(Lset[:, 1].max()) + 1
+    cx, cy = nx - ex + 1, ny - ey + 1          # origins keeping the box inside
+    if cx <= 0 or cy <= 0:
+        return np.zeros((0, 2), dtype=np.int64)
+    ok = np.ones((cx, cy), dtype=bool)
+    for (lx, ly) in Lset:
+        ok &= obs[lx:lx + cx, ly:ly + cy]
+    kx, ky = np.nonzero(ok.T)                  # column-major order: ky outer
+    return np.stack([ky, kx], axis=1).astype(np.int64)
+
+
+def trajectory_columns(x: np.ndarray, Lset: np.ndarray, Kset: np.ndarray,
+                       cols=None) -> np.ndarray:
+    """Columns ``cols`` of the trajectory matrix: ``X_ij = x[l_i + k_j]``.
+
+    Eq. qh_mat with 0-based indices; for a full rectangle this is the
+    Hankel-block-Hankel matrix of eq. block_hankel_matrix and for a series the
+    Hankel matrix of eq. ssa_embedding.
+    """
+    if cols is None:
+        cols = np.arange(len(Kset))
+    px = Lset[:, 0][:, None] + Kset[cols, 0][None, :]
+    py = Lset[:, 1][:, None] + Kset[cols, 1][None, :]
+    return np.asarray(x, dtype=np.float64)[px, py]
+
+
+def trajectory_matrix(x: np.ndarray, Lset: np.ndarray, Kset: np.ndarray) -> np.ndarray:
+    """The full ``L x K`` trajectory matrix of one channel."""
+    return trajectory_columns(x, Lset, Kset)
+
+
+def weights(shape, Lset: np.ndarray, Kset: np.ndarray) -> np.ndarray:
+    """``w_k = |A_k|``: how many trajectory entries hold data element k.
+
+    Counted directly: for every window element l, each origin kappa adds one
+    at ``l + kappa``.  Zero outside N' (the elements that never enter the
+    trajectory matrix, Sec. 5.1).
+    """
+    nx, ny = shape
+    w = np.zeros((nx, ny), dtype=np.int64)
+    ind = np.zeros((nx, ny), dtype=np.int64)
+    ind[Kset[:, 0], Kset[:, 1]] = 1
+    for (lx, ly) in Lset:
+        w[lx:, ly:] += ind[:nx - lx, :ny - ly]
+    return w
+
+
+# ---------------------------------------------------------------- problem
+class Problem:
+    """Channels sharing one window shape; see the module docstring."""
+
+    def __init__(self, channels, lx: int, ly: int = 1, wmask=None, masks=None):
+        self.channels = [np.asarray(c, dtype=np.float64).reshape(c.shape[0], -1)
+                         for c in channels]
+        if masks is None:
+            masks = [None] * len(self.channels)
+        self.obs = [observed(c, m) for c, m in zip(self.channels, masks)]
+        self.Lset = window_set(lx, ly, wmask)
+        self.Ksets = [origin_set(o, self.Lset) for o in self.obs]
+        self.L = len(self.Lset)
+        self.Ks = [len(k) for k in self.Ksets]
+        self.K = int(sum(self.Ks))
+        self.offsets = np.concatenate([[0], np.cumsum(self.Ks)]).astype(np.int64)
+
+    @classmethod
+    def series(cls, x, L: int):
+        """Basic SSA of one series (eq. ssa_embedding)."""
+        x = np.asarray(x, dtype=np.float64)
+        return cls([x.reshape(-1, 1)], L, 1)
+
+    @classmethod
+    def multi(cls, xs, L: int):
+        """MSSA of a system of series of possibly unequal lengths
+        (eq. mssa_embedding)."""
+        return cls([np.asarray(x, dtype=np.float64).reshape(-1, 1) for x in xs], L, 1)
+
+    @classmethod
+    def image(cls, x, lx: int, ly: int, wmask=None, mask=None):
+        """2D-SSA (full window and image) or Shaped 2D-SSA (wmask / mask /
+        NaN pixels)."""
+        return cls([np.asarray(x, dtype=np.float64)], lx, ly, wmask=wmask,
+                   masks=[mask])
+
+    def block(self, c: int, cols=None) -> np.ndarray:
+        """Columns of channel c's trajectory matrix."""
+        return trajectory_columns(self.channels[c], self.Lset, self.Ksets[c], cols)
+
+    def matrix(self) -> np.ndarray:
+        """The stacked ``L x K`` trajectory matrix ``[X^(1) : ... : X^(s)]``."""
+        return np.hstack([self.block(c) for c in range(len(self.channels))])
+
+    def weights(self, c: int = 0) -> np.ndarray:
+        return weights(self.channels[c].shape, self.Lset, self.Ksets[c])
+
+    def column_blocks(self, width: int = 4096):
+        """Yield ``(global_col0, X_block)`` over all channels, in column order."""
+        for c in range(len(self.channels)):
+            for j0 in range(0, self.Ks[c], width):
+                cols = np.arange(j0, min(j0 + width, self.Ks[c]))
+                yield int(self.offsets[c] + j0), self.block(c, cols)
+
+
+# ---------------------------------------------------------------- matvec
+def matvec(P: Problem, v: np.ndarray) -> np.ndarray:
+    """``u = X v`` with the explicit trajectory matrix (column blocks)."""
+    u = np.zeros(P.L)
+    for j0, Xb in P.column_blocks():
+        u += Xb @ v[j0:j0 + Xb.shape[1]]
+    return u
+
+
+def rmatvec(P: Problem, u: np.ndarray) -> np.ndarray:
+    """``v = X^T u`` with the explicit trajectory matrix."""
+    v = np.zeros(P.K)
+    for j0, Xb in P.column_blocks():
+        v[j0:j0 + Xb.shape[1]] = Xb.T @ u
+    return v
+
+
+# ---------------------------------------------------------------- SVD step
+def svd_eigen(P: Problem, r: int | None = None):
+    """Step 2 of Sec. 2.1 as written: ``S = X X^T``; its eigenvalues in
+    decreasing order with eigenvectors ``U_j``; ``sqrt(lambda_j)`` are the
+    singular values and ``V_j = X^T U_j / sqrt(lambda_j)`` the factor vectors.
+
+    ``S`` is summed over column blocks of X (a matrix product split by
+    columns).  Returns ``sigma (r,), U (L, r), V (K, r)``.
+    """
+    S = np.zeros((P.L, P.L))
+    for _, Xb in P.column_blocks():
+        S += Xb @ Xb.T
+    lam, U = np.linalg.eigh(S)
+    order = np.argsort(lam)[::-1]
+    lam, U = lam[order], U[:, order]
+    d = int(np.sum(lam > lam[0] * 1e-28)) if lam[0] > 0 else 0
+    if r is None:
+        r = d
+    r = min(r, d)
+    lam, U = lam[:r], U[:, :r]
+    sigma = np.sqrt(lam)
+    V = np.zeros((P.K, r))
+    for j0, Xb in P.column_blocks():
+        V[j0:j0 + Xb.shape[1]] = Xb.T @ U
+    V /= sigma[None, :]
+    return sigma, U, V
+
+
+def _round_robin(n: int):
+    """Pairings of a round-robin tournament on n (even) players: n-1 rounds of
+    n/2 disjoint pairs covering every pair once."""
+    players = list(range(n))
+    rounds = []
+    for _ in range(n - 1):
+        half = n // 2
+        rounds.append((np.array(players[:half]), np.array(players[half:][::-1])))
+        players = [players[0]] + [players[-1]] + players[1:-1]
+    return rounds
+
+
+def svd_jacobi(X: np.ndarray, tol: float = 1e-15, max_sweeps: int = 80):
+    """One-sided (Hestenes) Jacobi SVD of an explicit matrix.
+
+    Columns of the (tall) working matrix are rotated pairwise until every pair
+    is orthogonal to ``|a.b| <= tol |a||b|``; singular values are the final
+    column norms.  Returns ``sigma (n,), U (m, n), V (q, n)`` with
+    ``X = U diag(sigma) V^T`` and sigma decreasing, n = min(m, q).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    transpose = X.shape[1] > X.shape[0]
+    A = (X.T if transpose else X).copy()          # tall: m >= n
+    m, n = A.shape
+    n2 = n + (n % 2)
+    if n2 != n:
+        A = np.hstack([A, np.zeros((m, 1))])
+    R = np.eye(n2)
+    rounds = _round_robin(n2)
+    for _ in range(max_sweeps):
+        rotated = False
+        for p, q in rounds:
+            a, b = A[:, p], A[:, q]
+            alpha = np.einsum("ij,ij->j", a, a)
+            beta = np.einsum("ij,ij->j", b, b)
+            gamma = np.einsum("ij,ij->j", a, b)
+            need = np.abs(gamma) > tol * np.sqrt(alpha * beta)
+            if not np.any(need):
+                continue
+            rotated = True
+            g = np.where(need, gamma, 1.0)
+            zeta = (beta - alpha) / (2.0 * g)
+            t = np.sign(zeta) / (np.abs(zeta) + np.sqrt(1.0 + zeta * zeta))
+            t = np.where(zeta == 0, 1.0, t)
+            t = np.where(need, t, 0.0)
+            c = 1.0 / np.sqrt(1.0 + t * t)
+            s = c * t
+            A[:, p], A[:, q] = c * a - s * b, s * a + c * b
+            rp, rq = R[:, p], R[:, q]
+            R[:, p], R[:, q] = c * rp - s * rq, s * rp + c * rq
+        if not rotated:
+            break
+    A, R = A[:, :n], R[:n, :n]
+    sigma = np.linalg.norm(A, axis=0)
+    order = np.argsort(sigma)[::-1]
+    sigma, A, R = sigma[order], A[:, order], R[:, order]
+    safe = np.where(sigma > 0, sigma, 1.0)
+    W = A / safe[None, :]
+    if transpose:          # X^T = W diag(sigma) R^T  =>  X = R diag(sigma) W^T
+        return sigma, R, W
+    return sigma, W, R
+
+
+def decompose(P: Problem, r: int, method: str = "eigen"):
+    """The r leading eigentriples ``(sigma, U, V)`` of the trajectory matrix,
+    each pair ``(U_i, V_i)`` signed so that the largest-magnitude entry of U_i
+    is positive (singular vectors are defined up to sign, Sec. 3.4)."""
+    if method == "eigen":
+        sigma, U, V = svd_eigen(P, r)
+    elif method == "jacobi":
+        sigma, U, V = svd_jacobi(P.matrix())
+        sigma, U, V = sigma[:r], U[:, :r], V[:, :r]
+    else:
+        raise ValueError(method)
+    for i in range(U.shape[1]):
+        if U[np.argmax(np.abs(U[:, i])), i] < 0:
+            U[:, i] *= -1
+            V[:, i] *= -1
+    return sigma, U, V
+
+
+# ---------------------------------------------------------------- reconstruction
+def reconstruct(P: Problem, sigma, U, V, groups, residual: bool = False):
+    """Step 4 of Sec. 2.1: for each group I, ``X_I = sum_{i in I} sigma_i U_i
+    V_i^T`` is averaged over the sets ``A_k`` (diagonal averaging).
+
+    Returns ``out[g][c]``: an array of channel c's shape with NaN outside N'.
+    With ``residual`` one more group ``x - sum_g x~_g`` (on N') is appended.
+    """
+    sigma = np.asarray(sigma, dtype=np.float64)
+    out = []
+    for g in groups:
+        g = list(g)
+        per_ch = []
+        for c, x in enumerate(P.channels):
+            nx, ny = x.shape
+            Kc = P.Ksets[c]
+            Vc = V[P.offsets[c]:P.offsets[c + 1]]
+            Y = (U[:, g] * sigma[g][None, :]) @ Vc[:, g].T            # L x K_c
+            # data element of entry (i, j): l_i + k_j, flattened column-major
+            flat = ((P.Lset[:, 0][:, None] + Kc[:, 0][None, :])
+                    + nx * (P.Lset[:, 1][:, None] + Kc[:, 1][None, :]))
+            acc = np.bincount(flat.ravel(), weights=Y.ravel(),
+                              minlength=nx * ny).reshape((nx, ny), order="F")
+            cnt = np.bincount(flat.ravel(),
+                              minlength=nx * ny).reshape((nx, ny), order="F")
+            rec = np.full((nx, ny), np.nan)
+            ok = cnt > 0
+            rec[ok] = acc[ok] / cnt[ok]
+            per_ch.append(rec)
+        out.append(per_ch)
+    if residual:
+        res = []
+        for c, x in enumerate(P.channels):
+            r_ = x.copy()
+            for g in range(len(groups)):
+                r_ = r_ - out[g][c]
+            res.append(r_)
+        out.append(res)
+    return out
+
+
+def reconstruct_at(P: Problem, Ug: np.ndarray, points, c: int = 0) -> np.ndarray:
+    """Reconstruction of the group spanned by the orthonormal columns ``Ug`` at
+    selected data elements, one element at a time.
+
+    Uses ``X_I = U_I U_I^T X`` (the group's matrix is the projection of X on
+    its eigenvectors, since ``sigma_i V_i^T = U_i^T X``) and averages the
+    entries of ``A_k`` for each requested ``k = (m, n)`` of channel c.
+    """
+    x = P.channels[c]
+    Kc = P.Ksets[c]
+    kindex = {(int(a), int(b)): j for j, (a, b) in enumerate(Kc)}
+    vals = []
+    for (m, n) in points:
+        rows, cols = [], []
+        for i, (lx, ly) in enumerate(P.Lset):
+            j = kindex.get((m - int(lx), n - int(ly)))
+            if j is not None:
+                rows.append(i)
+                cols.append(j)
+        if not rows:
+            vals.append(np.nan)
+            continue
+        Xc = trajectory_columns(x, P.Lset, Kc, np.array(cols))   # L x |A_k|
+        proj = Ug @ (Ug.T @ Xc)                                   # L x |A_k|
+        vals.append(float(np.mean(proj[np.array(rows), np.arange(len(rows))])))
+    return np.array(vals)
