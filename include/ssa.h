@@ -1,0 +1,214 @@
+/*
+ * ssa.h -- C ABI of the GB300 SSA library (libssa.so).
+ *
+ * Singular Spectrum Analysis of a series (SSA), a system of series (MSSA), an
+ * image (2D-SSA) and a shaped / masked image (Shaped 2D-SSA), following
+ * Golyandina, Korobeynikov, Shlemov and Usevich, "Multivariate and 2D
+ * Extensions of Singular Spectrum Analysis with the Rssa Package":
+ *   embedding (Sec. 2.1 Step 1; eqs. ssa_embedding, mssa_embedding,
+ *   block_hankel_cols, qh_mat), truncated SVD of the trajectory matrix
+ *   (Step 2, eq. mmexp), grouping (Step 3, eq. mmexp_g) and reconstruction by
+ *   averaging over the sets A_k (Step 4, eq. res_decomp).
+ * The trajectory matrix is never formed: its products with vectors and the
+ * rank-one diagonal averaging go through FFTs (Sec. 6.1-6.2).
+ *
+ * Conventions for every entry point
+ *  - Return value: SSA_OK (0) or a negative SSA_E* code; ssa_strerror() names
+ *    it and ssa_last_error() gives a one-line detail for the calling thread.
+ *  - Arrays are column-major.  Images are Nx x Ny with x (rows) running down
+ *    and y (columns) right, the paper's orientation (Sec. 4.1.1).  Vectors
+ *    over the window set L and the origin set K follow the lexicographic
+ *    (column-major) order of Sec. 5.1.  Group and component indices are
+ *    0-based (the paper's are 1-based).
+ *  - Pointers marked "host or device" follow the call's on_device flag; all
+ *    others are host pointers.  The library copies its inputs and never keeps
+ *    a caller pointer; outputs go to caller-allocated buffers.
+ *  - A context owns every byte of device memory it allocates and frees it in
+ *    ssa_destroy().  All work of a context is ordered on its CUDA stream; one
+ *    context must not be used from two threads at once.
+ *  - Errors leave the context usable unless SSA_ECUDA is returned (then the
+ *    CUDA context may be unusable and the caller should destroy it).
+ */
+#ifndef SSA_GB300_H
+#define SSA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SSA_OK = 0,
+  SSA_EINVAL = -1,       /* bad argument (sizes, window, Inf in the data, ...) */
+  SSA_EEMPTY = -2,       /* no admissible window origin: K is empty */
+  SSA_ERANK = -3,        /* rank r outside [1, min(L, K)] */
+  SSA_ENOMEM = -4,       /* device allocation failed */
+  SSA_ENOTCONV = -5,     /* restarts exhausted; results valid, residuals in ssa_info */
+  SSA_ETIMEOUT = -6,     /* a bounded wait expired */
+  SSA_ECUDA = -7,        /* CUDA runtime error */
+  SSA_ESTATE = -8,       /* call out of order (e.g. reconstruct before decompose) */
+  SSA_EUNSUPPORTED = -9  /* size outside what this build supports */
+};
+
+typedef enum { SSA_1D = 0, SSA_MSSA = 1, SSA_2D = 2 } ssa_kind;  /* SSA_2D covers shaped */
+typedef enum { SSA_F32 = 0, SSA_F64 = 1 } ssa_dtype;
+/* Precision forms: FFTs, matvecs and the long-side Lanczos basis in FP32 with
+ * FP64 re-orthogonalisation, small SVD and reconstruction sums; or all FP64. */
+typedef enum { SSA_PREC_FP32FFT_FP64REORTH = 0, SSA_PREC_FP64 = 1 } ssa_prec;
+
+typedef struct ssa_ctx ssa_ctx;
+
+typedef struct {
+  int32_t kind;            /* ssa_kind */
+  int32_t dtype;           /* ssa_dtype of data */
+  int32_t on_device;       /* data and mask are device (1) or host (0) pointers */
+  int32_t n_series;        /* MSSA: number of series s (>= 1); ignored otherwise */
+  const void* data;        /* host or device.  1D: n values.  MSSA: the s series
+                              concatenated.  2D: nx*ny values, column-major.
+                              NaN marks a missing value (Sec. 5.2) */
+  int64_t n;               /* 1D: series length N */
+  const int64_t* lengths;  /* MSSA: s lengths N_p (host) */
+  int64_t nx, ny;          /* 2D: image size */
+  const uint8_t* mask;     /* optional, host or device, same layout as data:
+                              nonzero = observed; NULL = all observed */
+} ssa_input;
+
+typedef struct {
+  int64_t L;               /* 1D / MSSA window length, 1 < L < N (MSSA: < min N_p) */
+  int64_t lx, ly;          /* 2D window bounding box, 1 <= lx <= nx, 1 <= ly <= ny */
+  const uint8_t* wmask;    /* optional 2D window shape, lx*ly column-major (host);
+                              NULL = the full rectangle */
+} ssa_window;
+
+typedef struct {
+  int32_t rank;            /* r >= 1: eigentriples wanted */
+  int32_t krylov_dim;      /* k; 0 = min(2r + 16, 112, min(L, K)) */
+  int32_t max_restarts;    /* 0 = 40 */
+  int32_t prec;            /* ssa_prec */
+  double tol;              /* residual tolerance relative to sigma_1;
+                              0 = 1e-7 (FP32 form) / 1e-12 (FP64 form) */
+  uint64_t seed;           /* start vector seed */
+} ssa_params;
+
+typedef struct {
+  int64_t L, K;            /* trajectory matrix size */
+  int64_t nx, ny;          /* grid of the (first) channel */
+  int32_t n_channels;      /* s for MSSA, else 1 */
+  int32_t rank;            /* r of the last decomposition (0 before) */
+  int32_t krylov_dim;      /* k used */
+  int32_t restarts;        /* restart cycles run */
+  int32_t converged;       /* 1 if every wanted triple met the tolerance */
+  int32_t prec;            /* precision form of the last decomposition */
+  int64_t fft_mx, fft_my;  /* FFT grid */
+  double max_residual;     /* max_i ||X^T u_i - sigma_i v_i|| / sigma_1 (Lanczos estimate) */
+  int64_t device_bytes;    /* device memory held by the context */
+} ssa_info;
+
+/*
+ * ssa_embed -- Step 1 (Sec. 2.1) and the shape calculus (Sec. 5.1, 6.2.4).
+ * Validates the input, copies it to the device and computes, exactly in
+ * integers, the origin set K = {kappa : L (+) {kappa} inside N} (eq. sh_Ks),
+ * the reconstructable set N' = L (+) K and the weights w_k = |A_k|.  The data
+ * spectrum (Sec. 6.1.2: "F(x) can be precomputed") is built on first use.
+ * cuda_stream: a cudaStream_t to order the context's work on, or NULL for a
+ * stream owned by the context.  On success *out receives a new context.
+ * Errors: SSA_EINVAL (sizes, window, +-Inf), SSA_EEMPTY (K empty),
+ * SSA_EUNSUPPORTED (FFT grid above 16384 along x or 4096 along y).
+ */
+int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out);
+
+/*
+ * ssa_decompose -- Step 2 (Sec. 2.1, eq. mmexp): the r leading eigentriples
+ * (sigma_i, U_i, V_i) of the trajectory matrix, by Golub-Kahan-Lanczos
+ * bidiagonalisation on FFT products (Sec. 6.1.2 Alg. hmul_u; Sec. 6.2.2) with
+ * thick restarts; the truncated-SVD role Rssa gives PROPACK / nu-TRLan
+ * (Sec. 2.4).  Signs: each pair (U_i, V_i) is flipped so that the entry of
+ * U_i with the largest magnitude is positive.
+ * Errors: SSA_ERANK, SSA_ENOTCONV (results kept), SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_decompose(ssa_ctx* ctx, const ssa_params* params);
+
+/*
+ * ssa_decompose_batch -- the same for n contexts at once: every kernel of the
+ * Lanczos step is launched once for the whole batch (all problems advance in
+ * lock-step).  params: n entries (one per context).  All contexts must live
+ * on the current device; work is ordered on ctxs[0]'s stream.  status
+ * (host, n entries, may be NULL) receives each context's code; the return
+ * value is the first non-OK code.
+ */
+int ssa_decompose_batch(ssa_ctx* const* ctxs, int32_t n, const ssa_params* params, int32_t* status);
+
+/* ssa_get_info -- sizes and solver statistics (host struct). */
+int ssa_get_info(const ssa_ctx* ctx, ssa_info* info);
+
+/* ssa_get_sigma -- the r singular values sqrt(lambda_i), descending, into
+ * sigma (host, r doubles); r must not exceed the decomposed rank. */
+int ssa_get_sigma(const ssa_ctx* ctx, double* sigma, int32_t r);
+
+/*
+ * ssa_get_vectors -- eigenvectors U (L x r) and factor vectors V (K x r),
+ * column-major FP64, into host or device buffers (on_device).  Either pointer
+ * may be NULL.  MSSA factor vectors stack the series' factor subvectors
+ * (Sec. 3.2); image vectors list the window / origin sets lexicographically.
+ */
+int ssa_get_vectors(const ssa_ctx* ctx, double* U, double* V, int32_t on_device);
+
+/*
+ * ssa_reconstruct -- Steps 3-4 (Sec. 2.1; eq. res_decomp): for each group g the
+ * component x~_g = T^-1 Pi^(H) sum_{i in g} sigma_i U_i V_i^T, computed by
+ * rank-one FFT hankelization summed in frequency space (Sec. 6.1.3 Alg.
+ * hankelization, Sec. 6.2.3 Alg. qhankelization / diagsums).
+ * group_of: r entries (host), component i goes to group group_of[i] in
+ * [0, n_groups), or -1 to leave it out.  residual: if nonzero one more output
+ * x - sum_g x~_g is appended.  out (host or device): (n_groups + residual)
+ * blocks of FP64 values in the input's layout (1D: N; MSSA: sum N_p, series
+ * concatenated; 2D: nx*ny); NaN outside N' (values that never enter the
+ * trajectory matrix, Sec. 5.1).
+ */
+int ssa_reconstruct(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, int32_t residual, double* out,
+                    int32_t on_device);
+
+/*
+ * ssa_reconstruct_batch -- ssa_reconstruct for n decomposed contexts; every
+ * context uses the same grouping (group_of has the first context's r entries,
+ * the others must have the same r).  out_ptrs: n pointers (host array) to
+ * buffers as for ssa_reconstruct.
+ */
+int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_of, int32_t n_groups,
+                          int32_t residual, double* const* out_ptrs, int32_t on_device);
+
+/*
+ * ssa_get_shape -- the shape calculus results (host buffers, any may be NULL):
+ * L, K; origin_mask (uint8, input layout: 1 where an element is a window origin
+ * kappa of K); weights (int32, input layout: w_k = |A_k|, 0 outside N').
+ */
+int ssa_get_shape(const ssa_ctx* ctx, int64_t* L, int64_t* K, uint8_t* origin_mask, int32_t* weights);
+
+/*
+ * ssa_matvec -- one product with the trajectory matrix by FFT: transpose = 0
+ * gives u = X v (in: K values, out: L values), transpose = 1 gives
+ * v = X^T u (in: L, out: K).  Sec. 6.1.2 Alg. hmul_u and Sec. 6.2.2.
+ * prec selects the arithmetic (ssa_prec).  in/out: FP64, host or device.
+ */
+int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, double* out, int32_t on_device);
+
+/* ssa_synchronize -- wait for the context's stream. */
+int ssa_synchronize(ssa_ctx* ctx);
+
+/* ssa_destroy -- free the context and its device memory (NULL is a no-op). */
+void ssa_destroy(ssa_ctx* ctx);
+
+/* ssa_strerror -- static name of a return code. */
+const char* ssa_strerror(int code);
+
+/* ssa_last_error -- detail of the calling thread's last failure (static buffer). */
+const char* ssa_last_error(void);
+
+/* ssa_version -- library version string. */
+const char* ssa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSA_GB300_H */

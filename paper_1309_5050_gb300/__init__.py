@@ -1,0 +1,284 @@
+"""GB300-native Singular Spectrum Analysis (SSA, MSSA, 2D-SSA, Shaped 2D-SSA).
+
+Python face of ``libssa.so``; see ``include/ssa.h`` for the C ABI.  Inputs may
+be numpy arrays (host) or CUDA torch tensors (device, used in place).  All
+computation happens in the library's sm_103a kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import (SSA_1D, SSA_2D, SSA_F32, SSA_F64, SSA_MSSA,  # noqa: F401
+                   SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64, SSAError)
+
+__all__ = ["SSA", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
+           "load", "SSAError", "PREC"]
+
+PREC = {"fp32": SSA_PREC_FP32FFT_FP64REORTH, "fp64": SSA_PREC_FP64}
+
+
+def load():
+    """Load (building if needed) the CUDA library."""
+    return L.load()
+
+
+def window_circle(R: int) -> np.ndarray:
+    """Circular window of radius R (bounding box (2R+1)^2, (i-R)^2+(j-R)^2 <= R^2)."""
+    i = np.arange(2 * R + 1)[:, None]
+    j = np.arange(2 * R + 1)[None, :]
+    return (i - R) ** 2 + (j - R) ** 2 <= R * R
+
+
+def window_triangle(side: int) -> np.ndarray:
+    """Right isosceles triangle, right angle top-left: i + j <= side - 1."""
+    i = np.arange(side)[:, None]
+    j = np.arange(side)[None, :]
+    return i + j <= side - 1
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x, dtype=None):
+    """(pointer, on_device, keepalive, dtype_code) for a numpy array or a torch tensor."""
+    if _is_torch(x):
+        if not x.is_contiguous():
+            x = x.contiguous()
+        code = {"torch.float32": SSA_F32, "torch.float64": SSA_F64}.get(str(x.dtype))
+        return x.data_ptr(), 1 if x.is_cuda else 0, x, code
+    a = np.ascontiguousarray(x) if dtype is None else np.ascontiguousarray(x, dtype=dtype)
+    code = {np.dtype(np.float32): SSA_F32, np.dtype(np.float64): SSA_F64}.get(a.dtype)
+    return a.ctypes.data, 0, a, code
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class SSA:
+    """One SSA problem held on the GPU (a library context)."""
+
+    def __init__(self, inp: L.ssa_input, win: L.ssa_window, keep, stream=None, layout=None):
+        lib = L.load()
+        ctx = C.c_void_p()
+        L.check(lib.ssa_embed(C.byref(inp), C.byref(win), _stream_ptr(stream), C.byref(ctx)), "ssa_embed")
+        self._lib = lib
+        self.ctx = ctx
+        self.layout = layout            # ("1d", n) | ("mssa", lengths) | ("2d", nx, ny)
+        self.rank = 0
+        del keep
+
+    # ----------------------------------------------------------- builders
+    @classmethod
+    def series(cls, x, L_: int, stream=None):
+        if not _is_torch(x):
+            x = np.asarray(x)
+            if x.dtype not in (np.float32, np.float64):
+                x = x.astype(np.float64)
+        ptr, dev, keep, code = _buf(x)
+        n = int(x.shape[0])
+        inp = L.ssa_input(kind=SSA_1D, dtype=code, on_device=dev, n_series=1, data=ptr, n=n)
+        win = L.ssa_window(L=L_)
+        return cls(inp, win, keep, stream, ("1d", n))
+
+    @classmethod
+    def multi(cls, xs, L_: int, stream=None, dtype=np.float32):
+        """MSSA of a list of series (host arrays) or of one concatenated
+        device tensor with ``lengths``."""
+        if isinstance(xs, (list, tuple)):
+            lengths = np.array([len(v) for v in xs], dtype=np.int64)
+            cat = np.concatenate([np.asarray(v, dtype=dtype) for v in xs])
+            ptr, dev, keep, code = _buf(cat)
+        else:
+            raise TypeError("multi() takes a list of series; use multi_concat for a flat buffer")
+        return cls._multi_flat(ptr, dev, keep, code, lengths, L_, stream)
+
+    @classmethod
+    def multi_concat(cls, flat, lengths, L_: int, stream=None):
+        ptr, dev, keep, code = _buf(flat)
+        return cls._multi_flat(ptr, dev, keep, code, np.asarray(lengths, dtype=np.int64), L_, stream)
+
+    @classmethod
+    def _multi_flat(cls, ptr, dev, keep, code, lengths, L_, stream):
+        lens = np.ascontiguousarray(lengths, dtype=np.int64)
+        inp = L.ssa_input(kind=SSA_MSSA, dtype=code, on_device=dev, n_series=len(lens), data=ptr,
+                          lengths=lens.ctypes.data_as(C.POINTER(C.c_int64)))
+        win = L.ssa_window(L=L_)
+        obj = cls(inp, win, (keep, lens), stream, ("mssa", lens.copy()))
+        return obj
+
+    @classmethod
+    def image(cls, x, lx: int, ly: int, wmask=None, mask=None, stream=None):
+        """2D-SSA / Shaped 2D-SSA of an (nx, ny) image (x down, y right).
+        Host arrays are passed column-major; a device tensor must already be
+        laid out column-major (i.e. be the transpose-contiguous view)."""
+        if _is_torch(x):
+            nx, ny = int(x.shape[0]), int(x.shape[1])
+            xt = x.t().contiguous()          # column-major bytes
+            ptr, dev, keep, code = _buf(xt)
+        else:
+            a = np.asarray(x)
+            if a.dtype not in (np.float32, np.float64):
+                a = a.astype(np.float64)
+            nx, ny = a.shape
+            af = np.asfortranarray(a)
+            ptr, dev, keep, code = af.ctypes.data, 0, af, {np.dtype(np.float32): SSA_F32,
+                                                            np.dtype(np.float64): SSA_F64}[af.dtype]
+        mptr, mkeep = None, None
+        if mask is not None:
+            if _is_torch(mask):
+                mkeep = mask.t().contiguous().to(dtype=__import__("torch").uint8)
+                mptr = mkeep.data_ptr()
+            else:
+                if dev:
+                    raise TypeError("a device image needs a device mask")
+                m = np.asfortranarray(np.asarray(mask, dtype=np.uint8))
+                mptr, mkeep = m.ctypes.data, m
+        wptr, wkeep = None, None
+        if wmask is not None:
+            w = np.asfortranarray(np.asarray(wmask, dtype=np.uint8))
+            wptr, wkeep = w.ctypes.data, w
+            lx, ly = w.shape
+        inp = L.ssa_input(kind=SSA_2D, dtype=code, on_device=dev, n_series=1, data=ptr, nx=nx, ny=ny, mask=mptr)
+        win = L.ssa_window(lx=lx, ly=ly, wmask=wptr)
+        return cls(inp, win, (keep, mkeep, wkeep), stream, ("2d", nx, ny))
+
+    # ----------------------------------------------------------- calls
+    def decompose(self, rank: int, prec: str = "fp32", krylov_dim: int = 0, tol: float = 0.0,
+                  seed: int = 0, max_restarts: int = 0, check: bool = True) -> int:
+        p = L.ssa_params(rank=rank, krylov_dim=krylov_dim, max_restarts=max_restarts,
+                         prec=PREC[prec], tol=tol, seed=seed)
+        rc = self._lib.ssa_decompose(self.ctx, C.byref(p))
+        if check:
+            L.check(rc, "ssa_decompose")
+        self.rank = rank
+        return rc
+
+    def info(self) -> dict:
+        i = L.ssa_info()
+        L.check(self._lib.ssa_get_info(self.ctx, C.byref(i)), "ssa_get_info")
+        return {f: getattr(i, f) for f, _ in L.ssa_info._fields_}
+
+    def sigma(self, r: int | None = None) -> np.ndarray:
+        r = self.rank if r is None else r
+        out = np.zeros(r)
+        L.check(self._lib.ssa_get_sigma(self.ctx, out.ctypes.data_as(C.POINTER(C.c_double)), r), "ssa_get_sigma")
+        return out
+
+    def vectors(self):
+        inf = self.info()
+        U = np.zeros((inf["L"], self.rank), order="F")
+        V = np.zeros((inf["K"], self.rank), order="F")
+        L.check(self._lib.ssa_get_vectors(self.ctx, U.ctypes.data, V.ctypes.data, 0), "ssa_get_vectors")
+        return U, V
+
+    def _total(self):
+        if self.layout[0] == "1d":
+            return self.layout[1]
+        if self.layout[0] == "mssa":
+            return int(np.sum(self.layout[1]))
+        return self.layout[1] * self.layout[2]
+
+    def _split(self, flat):
+        kind = self.layout[0]
+        if kind == "1d":
+            return flat
+        if kind == "mssa":
+            offs = np.concatenate([[0], np.cumsum(self.layout[1])])
+            return [flat[offs[i]:offs[i + 1]] for i in range(len(self.layout[1]))]
+        return flat.reshape((self.layout[1], self.layout[2]), order="F")
+
+    def reconstruct(self, groups, residual: bool = False):
+        """groups: list of lists of 0-based component indices.  Returns one
+        array per group (plus the residual) in the input's shape; NaN outside N'."""
+        gof = np.full(self.rank, -1, dtype=np.int32)
+        for g, idx in enumerate(groups):
+            for i in idx:
+                gof[i] = g
+        nout = len(groups) + (1 if residual else 0)
+        total = self._total()
+        out = np.zeros(total * nout)
+        L.check(self._lib.ssa_reconstruct(self.ctx, gof.ctypes.data_as(C.POINTER(C.c_int32)), len(groups),
+                                          1 if residual else 0, out.ctypes.data, 0), "ssa_reconstruct")
+        return [self._split(out[g * total:(g + 1) * total]) for g in range(nout)]
+
+    def shape(self):
+        """(L, K, origin_mask, weights) in the input's layout."""
+        total = self._total()
+        Lc, Kc = C.c_int64(), C.c_int64()
+        om = np.zeros(total, dtype=np.uint8)
+        w = np.zeros(total, dtype=np.int32)
+        L.check(self._lib.ssa_get_shape(self.ctx, C.byref(Lc), C.byref(Kc), om.ctypes.data, w.ctypes.data),
+                "ssa_get_shape")
+        return Lc.value, Kc.value, self._split(om), self._split(w)
+
+    def matvec(self, v, transpose: bool = False, prec: str = "fp32") -> np.ndarray:
+        inf = self.info()
+        nin, nout = (inf["L"], inf["K"]) if transpose else (inf["K"], inf["L"])
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        assert a.shape == (nin,)
+        out = np.zeros(nout)
+        L.check(self._lib.ssa_matvec(self.ctx, 1 if transpose else 0, PREC[prec], a.ctypes.data, out.ctypes.data, 0),
+                "ssa_matvec")
+        return out
+
+    def synchronize(self):
+        L.check(self._lib.ssa_synchronize(self.ctx), "ssa_synchronize")
+
+    def close(self):
+        if self.ctx:
+            self._lib.ssa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decompose_batch(problems, rank, prec: str = "fp32", krylov_dim: int = 0, tol: float = 0.0, seed: int = 0,
+                    max_restarts: int = 0, check: bool = True):
+    """Decompose many SSA objects in one batched run (lock-step Lanczos)."""
+    lib = L.load()
+    n = len(problems)
+    ranks = rank if isinstance(rank, (list, tuple)) else [rank] * n
+    arr = (C.c_void_p * n)(*[p.ctx for p in problems])
+    ps = (L.ssa_params * n)(*[L.ssa_params(rank=r, krylov_dim=krylov_dim, max_restarts=max_restarts,
+                                           prec=PREC[prec], tol=tol, seed=seed) for r in ranks])
+    st = (C.c_int32 * n)()
+    rc = lib.ssa_decompose_batch(arr, n, ps, st)
+    for p, r in zip(problems, ranks):
+        p.rank = r
+    if check:
+        L.check(rc, "ssa_decompose_batch")
+    return rc, list(st)
+
+
+def reconstruct_batch(problems, groups, residual: bool = False):
+    lib = L.load()
+    n = len(problems)
+    r = problems[0].rank
+    gof = np.full(r, -1, dtype=np.int32)
+    for g, idx in enumerate(groups):
+        for i in idx:
+            gof[i] = g
+    nout = len(groups) + (1 if residual else 0)
+    outs = [np.zeros(p._total() * nout) for p in problems]
+    ptrs = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+    arr = (C.c_void_p * n)(*[p.ctx for p in problems])
+    L.check(lib.ssa_reconstruct_batch(arr, n, gof.ctypes.data_as(C.POINTER(C.c_int32)), len(groups),
+                                      1 if residual else 0, ptrs, 0), "ssa_reconstruct_batch")
+    res = []
+    for p, o in zip(problems, outs):
+        t = p._total()
+        res.append([p._split(o[g * t:(g + 1) * t]) for g in range(nout)])
+    return res

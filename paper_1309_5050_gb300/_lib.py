@@ -1,0 +1,109 @@
+"""ctypes binding of libssa.so: the C ABI of include/ssa.h, same names.
+
+Argument marshalling only -- every computation runs in the library's CUDA
+kernels.  Loading fails loudly when the library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+SSA_OK, SSA_EINVAL, SSA_EEMPTY, SSA_ERANK, SSA_ENOMEM = 0, -1, -2, -3, -4
+SSA_ENOTCONV, SSA_ETIMEOUT, SSA_ECUDA, SSA_ESTATE, SSA_EUNSUPPORTED = -5, -6, -7, -8, -9
+SSA_1D, SSA_MSSA, SSA_2D = 0, 1, 2
+SSA_F32, SSA_F64 = 0, 1
+SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64 = 0, 1
+
+EXPORTS = [
+    "ssa_embed", "ssa_decompose", "ssa_decompose_batch", "ssa_get_info", "ssa_get_sigma",
+    "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_get_shape", "ssa_matvec",
+    "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
+]
+
+
+class ssa_input(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("dtype", C.c_int32), ("on_device", C.c_int32),
+                ("n_series", C.c_int32), ("data", C.c_void_p), ("n", C.c_int64),
+                ("lengths", C.POINTER(C.c_int64)), ("nx", C.c_int64), ("ny", C.c_int64),
+                ("mask", C.c_void_p)]
+
+
+class ssa_window(C.Structure):
+    _fields_ = [("L", C.c_int64), ("lx", C.c_int64), ("ly", C.c_int64), ("wmask", C.c_void_p)]
+
+
+class ssa_params(C.Structure):
+    _fields_ = [("rank", C.c_int32), ("krylov_dim", C.c_int32), ("max_restarts", C.c_int32),
+                ("prec", C.c_int32), ("tol", C.c_double), ("seed", C.c_uint64)]
+
+
+class ssa_info(C.Structure):
+    _fields_ = [("L", C.c_int64), ("K", C.c_int64), ("nx", C.c_int64), ("ny", C.c_int64),
+                ("n_channels", C.c_int32), ("rank", C.c_int32), ("krylov_dim", C.c_int32),
+                ("restarts", C.c_int32), ("converged", C.c_int32), ("prec", C.c_int32),
+                ("fft_mx", C.c_int64), ("fft_my", C.c_int64), ("max_residual", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libssa.so (building it first when asked); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libssa.so not found at {path}; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.ssa_embed.argtypes = [C.POINTER(ssa_input), C.POINTER(ssa_window), P, C.POINTER(P)]
+    lib.ssa_decompose.argtypes = [P, C.POINTER(ssa_params)]
+    lib.ssa_decompose_batch.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(ssa_params), C.POINTER(C.c_int32)]
+    lib.ssa_get_info.argtypes = [P, C.POINTER(ssa_info)]
+    lib.ssa_get_sigma.argtypes = [P, C.POINTER(C.c_double), C.c_int32]
+    lib.ssa_get_vectors.argtypes = [P, P, P, C.c_int32]
+    lib.ssa_reconstruct.argtypes = [P, C.POINTER(C.c_int32), C.c_int32, C.c_int32, P, C.c_int32]
+    lib.ssa_reconstruct_batch.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                          C.c_int32, C.POINTER(P), C.c_int32]
+    lib.ssa_get_shape.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), P, P]
+    lib.ssa_matvec.argtypes = [P, C.c_int32, C.c_int32, P, P, C.c_int32]
+    lib.ssa_synchronize.argtypes = [P]
+    lib.ssa_destroy.argtypes = [P]
+    lib.ssa_destroy.restype = None
+    lib.ssa_strerror.argtypes = [C.c_int]
+    lib.ssa_strerror.restype = C.c_char_p
+    lib.ssa_last_error.argtypes = []
+    lib.ssa_last_error.restype = C.c_char_p
+    lib.ssa_version.restype = C.c_char_p
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if f.restype is C.c_int:
+            pass
+    _lib = lib
+    return lib
+
+
+class SSAError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load(False)
+        msg = lib.ssa_strerror(code).decode()
+        detail = lib.ssa_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}): {detail}")
+        self.code = code
+
+
+def check(rc: int, where: str) -> int:
+    if rc != SSA_OK:
+        raise SSAError(rc, where)
+    return rc

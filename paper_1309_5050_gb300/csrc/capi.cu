@@ -1,0 +1,1167 @@
+// C ABI and host orchestration of the SSA library: contexts, shapes, spectra,
+// the batched Lanczos driver, reconstruction.  Every arithmetic step runs in
+// the kernels of k_*.cu; this file sizes buffers, builds work items and
+// sequences launches on the context stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/ssa.h"
+#include "kernels.cuh"
+#include "lanczos.h"
+#include "launch.h"
+#include "recon.h"
+#include "shape.h"
+
+using namespace ssa;
+
+// ============================================================== errors
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != SSA_OK) return rc_; \
+  } while (0)
+
+// ============================================================== per-device setup
+namespace ssa {
+
+static std::mutex g_mu;
+
+void set_max_smem(const void* fn) {
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (done.count({fn, dev})) return;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, device_max_smem());
+  done.insert({fn, dev});
+}
+
+int device_max_smem() {
+  static std::map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cache[dev] = v;
+  return v;
+}
+
+__global__ void k_twiddles(Cx<float>* t32, Cx<double>* t64) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < TW_N; j += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)j / (double)TW_N, &s, &c);
+    t64[j] = cx(c, s);
+    t32[j] = cx((float)c, (float)s);
+  }
+}
+
+struct DevTables { Cx<float>* t32 = nullptr; Cx<double>* t64 = nullptr; };
+static std::map<int, DevTables> g_tables;
+
+static int ensure_tables(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_tables.count(dev)) return SSA_OK;
+  DevTables t;
+  CU(cudaMalloc(&t.t32, sizeof(Cx<float>) * TW_N));
+  CU(cudaMalloc(&t.t64, sizeof(Cx<double>) * TW_N));
+  k_twiddles<<<64, 256>>>(t.t32, t.t64);
+  CU(cudaGetLastError());
+  CU(cudaDeviceSynchronize());
+  g_tables[dev] = t;
+  return SSA_OK;
+}
+
+template <> const Cx<float>* twiddles<float>(int dev) { return g_tables[dev].t32; }
+template <> const Cx<double>* twiddles<double>(int dev) { return g_tables[dev].t64; }
+
+// small helper kernels of the driver
+__global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int max_restarts, int full) {
+  st->full = full; st->pad_ = 0;
+  st->j0 = 0; st->k = k; st->r = r; st->kk = kk; st->active = 1; st->converged = 0;
+  st->nconv = 0; st->breakdown = 0; st->restarts = 0; st->max_restarts = max_restarts;
+  st->beta_k = 0.0; st->anorm = 0.0; st->tol = tol; st->sigma1 = 0.0; st->maxres = 0.0;
+}
+
+template <typename T>
+__global__ void k_sum_parts_to_double(const T* parts, int nparts, int64_t ld, int64_t n, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int p = 0; p < nparts; ++p) a += (double)parts[p * ld + i];
+    out[i] = a;
+  }
+}
+
+template <typename TO, typename TI>
+__global__ void k_convert(const TI* in, TO* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+__global__ void k_kmask(const uint32_t* kbits, int kwords, int cx, int cy, int nx, int ny, uint8_t* out) {
+  const int y = blockIdx.y;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+    uint8_t v = 0;
+    if (x < cx && y < cy) v = (kbits[(int64_t)y * kwords + (x >> 5)] >> (x & 31)) & 1u;
+    out[x + (int64_t)nx * y] = v;
+  }
+}
+
+}  // namespace ssa
+
+static unsigned grid1(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 8192));
+}
+
+static int ilog2_ceil(int64_t n) {
+  int l = 0;
+  while ((int64_t(1) << l) < n) ++l;
+  return l;
+}
+
+// ============================================================== context
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct ShapeSet {          // a set of grid points as per-column bit rows
+  bool dense = true;       // rectangle [0,bx) x [0,by)
+  int bx = 0, by = 0, words = 0;
+  uint32_t* bits = nullptr;     // device
+  int32_t* colbase = nullptr;   // device, by + 1
+  int32_t* cnt = nullptr;       // device scratch, by + 1
+  int64_t count = 0;
+  MapDev dev() const {
+    MapDev m;
+    m.dense = dense ? 1 : 0; m.bx = bx; m.by = by; m.words = words;
+    m.bits = bits; m.colbase = colbase;
+    return m;
+  }
+};
+
+struct Channel {
+  int64_t nx = 0, ny = 0;
+  int64_t data_off = 0;        // element offset of the channel's data
+  ShapeSet K;                  // origins (bounding grid cx x cy)
+  int cx = 0, cy = 0;
+  int64_t koff = 0;            // offset of the channel's slice in K-vectors
+  int32_t* w = nullptr;        // nx*ny weights
+  uint32_t* obs = nullptr;     // observed bits, ny x nwords
+  int nwords = 0;
+  void* xh32 = nullptr;        // spectra
+  void* xh64 = nullptr;
+};
+
+struct Workspace {             // Lanczos + results, per precision
+  int prec = -1, r = 0, k = 0, kk = 0;
+  bool swapped = false;
+  int64_t Ls = 0, Kl = 0;
+  int nblk_s = 0, nblk_l = 0;
+  LzState* st = nullptr;
+  double* U = nullptr; void* V = nullptr;
+  double* p = nullptr; void* q = nullptr;
+  void* parts_s = nullptr; void* parts_l = nullptr;
+  int n_part_s = 1, n_part_l = 1;
+  double* B = nullptr; double* P = nullptr; double* Q = nullptr; double* sig = nullptr;
+  double* cpa = nullptr; double* cpb = nullptr; double* np_s = nullptr; double* np_l = nullptr;
+  void* g1 = nullptr; void* g2 = nullptr;
+  void* Uo = nullptr; void* Vo = nullptr;
+  double* sigma = nullptr; double* sgn = nullptr;
+  bool done = false;
+  LzState host_st;
+};
+
+struct ssa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int kind = 0, dtype = 0;
+  std::vector<Channel> ch;
+  int64_t total = 0;           // data elements
+  void* data = nullptr;        // device copy of the input (dtype)
+  int log2Mx = 0, log2My = 0;
+  ShapeSet Lset;               // window set (bounding box ex x ey)
+  int ex = 0, ey = 0;
+  uint32_t* wrows = nullptr;   // window rows (bits), ey x wwords
+  uint32_t* rrows = nullptr;   // reversed window rows
+  int wwords = 0;
+  int64_t L = 0, K = 0;
+  Workspace ws;
+  std::vector<std::pair<void*, size_t>> allocs;   // everything owned
+  int64_t bytes = 0;
+
+  int alloc(void** p, size_t n) {
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMallocAsync(p, n, stream);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA,
+                                      "device allocation of %zu bytes: %s", n, cudaGetErrorString(e));
+    allocs.push_back({*p, n});
+    bytes += (int64_t)n;
+    return SSA_OK;
+  }
+  template <typename X> int allocT(X** p, size_t count) { return alloc((void**)p, count * sizeof(X)); }
+  void release(void* p) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i].first == p) {
+        cudaFreeAsync(p, stream);
+        bytes -= (int64_t)allocs[i].second;
+        allocs.erase(allocs.begin() + i);
+        return;
+      }
+  }
+};
+
+// upload a small host array into ctx-owned device memory
+template <typename X>
+static int upload(ssa_ctx* c, const std::vector<X>& h, X** d) {
+  TRY(c->allocT(d, std::max<size_t>(h.size(), 1)));
+  if (!h.empty()) CU(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice, c->stream));
+  return SSA_OK;
+}
+
+// ============================================================== shapes
+static int build_set_counts(ssa_ctx* c, ShapeSet& s) {
+  // colbase of a bit-row set (device) and its total count (synchronous read)
+  TRY(c->allocT(&s.cnt, (size_t)s.by + 1));
+  TRY(c->allocT(&s.colbase, (size_t)s.by + 1));
+  launch_col_counts(s.bits, s.words, s.by, s.cnt, s.colbase, c->stream);
+  CU(cudaGetLastError());
+  int32_t tot = 0;
+  CU(cudaMemcpyAsync(&tot, s.colbase + s.by, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  s.count = tot;
+  return SSA_OK;
+}
+
+static int embed_shapes(ssa_ctx* c, const ssa_window* win) {
+  // window rows
+  int ex, ey;
+  std::vector<uint8_t> wm;
+  if (c->kind == SSA_2D) {
+    ex = (int)win->lx; ey = (int)win->ly;
+    wm.assign((size_t)ex * ey, 1);
+    if (win->wmask) std::memcpy(wm.data(), win->wmask, wm.size());
+  } else {
+    ex = (int)win->L; ey = 1;
+    wm.assign((size_t)ex, 1);
+  }
+  // trim empty border rows / columns of the window mask (its bounding box)
+  int x0 = ex, x1 = -1, y0 = ey, y1 = -1;
+  for (int y = 0; y < ey; ++y)
+    for (int x = 0; x < ex; ++x)
+      if (wm[x + (size_t)ex * y]) { x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y); }
+  if (x1 < 0) return fail(SSA_EINVAL, "window mask is empty");
+  if (x0 != 0 || y0 != 0) return fail(SSA_EINVAL, "window mask must touch its first row and column");
+  ex = x1 + 1; ey = y1 + 1;
+  bool full = true;
+  for (int y = 0; y < ey; ++y)
+    for (int x = 0; x < ex; ++x) full &= wm[x + (size_t)(c->kind == SSA_2D ? win->lx : ex) * y] != 0;
+  const int ldm = (c->kind == SSA_2D) ? (int)win->lx : ex;
+  c->ex = ex; c->ey = ey;
+  c->wwords = (ex + 31) / 32;
+  std::vector<uint32_t> rows((size_t)ey * c->wwords, 0u), rrows((size_t)ey * c->wwords, 0u);
+  for (int y = 0; y < ey; ++y)
+    for (int x = 0; x < ex; ++x)
+      if (wm[x + (size_t)ldm * y]) {
+        rows[(size_t)y * c->wwords + (x >> 5)] |= 1u << (x & 31);
+        const int xr = ex - 1 - x;
+        rrows[(size_t)y * c->wwords + (xr >> 5)] |= 1u << (xr & 31);
+      }
+  TRY(upload(c, rows, &c->wrows));
+  TRY(upload(c, rrows, &c->rrows));
+  ShapeSet& Ls = c->Lset;
+  Ls.bx = ex; Ls.by = ey; Ls.words = c->wwords;
+  Ls.dense = full;
+  Ls.bits = c->wrows;
+  TRY(build_set_counts(c, Ls));
+  c->L = Ls.count;
+
+  int* derr = nullptr;
+  TRY(c->allocT(&derr, 1));
+  CU(cudaMemsetAsync(derr, 0, sizeof(int), c->stream));
+  c->K = 0;
+  for (size_t q = 0; q < c->ch.size(); ++q) {
+    Channel& h = c->ch[q];
+    h.nwords = (int)((h.nx + 31) / 32);
+    TRY(c->allocT(&h.obs, (size_t)h.ny * h.nwords));
+    const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
+    const void* dptr = (const char*)c->data + h.data_off * esz;
+    launch_obs_bits(dptr, c->dtype == SSA_F64, nullptr, (int)h.nx, (int)h.ny, h.nwords, h.obs, derr, c->stream);
+    CU(cudaGetLastError());
+    h.cx = (int)(h.nx - ex + 1);
+    h.cy = (int)(h.ny - ey + 1);
+    ShapeSet& ks = h.K;
+    if (h.cx <= 0 || h.cy <= 0) {
+      ks.bx = 0; ks.by = 0; ks.words = 0; ks.count = 0; ks.dense = true;
+    } else {
+      ks.bx = h.cx; ks.by = h.cy; ks.words = (h.cx + 31) / 32;
+      TRY(c->allocT(&ks.bits, (size_t)ks.by * ks.words));
+      launch_origins(h.obs, h.nwords, c->wrows, c->wwords, ey, h.cx, h.cy, ks.words, ks.bits, c->stream);
+      CU(cudaGetLastError());
+      TRY(build_set_counts(c, ks));
+      ks.dense = (ks.count == (int64_t)h.cx * h.cy);
+    }
+    h.koff = c->K;
+    c->K += ks.count;
+    TRY(c->allocT(&h.w, (size_t)(h.nx * h.ny)));
+    uint32_t* nb = nullptr;
+    TRY(c->allocT(&nb, (size_t)h.ny * h.nwords));
+    if (ks.count > 0) {
+      launch_weights(ks.bits, ks.words, ks.by, c->rrows, c->wwords, ex, ey, (int)h.nx, (int)h.ny, h.w, nb,
+                     h.nwords, c->stream);
+      CU(cudaGetLastError());
+    } else {
+      CU(cudaMemsetAsync(h.w, 0, sizeof(int32_t) * h.nx * h.ny, c->stream));
+    }
+    c->release(nb);
+  }
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->release(derr);
+  if (herr) return fail(SSA_EINVAL, "input holds +-Inf at an observed position");
+  if (c->K <= 0) return fail(SSA_EEMPTY, "no window origin keeps the whole window inside the observed set");
+  return SSA_OK;
+}
+
+// ============================================================== spectrum
+template <typename T>
+static int ensure_spectrum(ssa_ctx* c) {
+  const bool f32 = std::is_same<T, float>::value;
+  bool have = true;
+  for (auto& h : c->ch) have &= (f32 ? h.xh32 : h.xh64) != nullptr;
+  if (have) return SSA_OK;
+  const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
+  std::vector<SpecItem<T>> items;
+  std::vector<YItem<T>> yitems;
+  void* g1 = nullptr;
+  if (c->log2My > 0) TRY(c->alloc(&g1, sizeof(Cx<T>) * (size_t)(H + 1) * My * c->ch.size()));
+  const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
+  int max_ny = 0;
+  for (size_t q = 0; q < c->ch.size(); ++q) {
+    Channel& h = c->ch[q];
+    void* xh = nullptr;
+    TRY(c->alloc(&xh, sizeof(Cx<T>) * (size_t)(H + 1) * My));
+    (f32 ? h.xh32 : h.xh64) = xh;
+    SpecItem<T> s;
+    s.data = (const char*)c->data + h.data_off * esz;
+    s.obs = h.obs; s.obs_words = h.nwords;
+    s.data_double = c->dtype == SSA_F64;
+    s.nx = (int)h.nx; s.ny = (int)h.ny;
+    s.log2Mx = c->log2Mx; s.log2My = c->log2My;
+    s.g1 = g1 ? (Cx<T>*)g1 + q * (size_t)(H + 1) * My : nullptr;
+    s.xh = (Cx<T>*)xh;
+    s.scale = (T)(1.0 / ((double)(2 * H) * (double)My));
+    items.push_back(s);
+    YItem<T> y;
+    y.src = s.g1; y.dst = s.xh; y.mul = nullptr; y.st = nullptr;
+    y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = (int)h.ny; y.out_hi = My; y.scale = T(0);
+    yitems.push_back(y);
+    max_ny = std::max(max_ny, (int)h.ny);
+  }
+  SpecItem<T>* di = nullptr;
+  YItem<T>* dy = nullptr;
+  TRY(upload(c, items, &di));
+  TRY(upload(c, yitems, &dy));
+  launch_spec<T>(di, dy, (int)items.size(), c->log2Mx, c->log2My, max_ny, twiddles<T>(c->device), c->stream);
+  CU(cudaGetLastError());
+  c->release(di);
+  c->release(dy);
+  if (g1) c->release(g1);
+  return SSA_OK;
+}
+
+// ============================================================== matvec items
+// Direction "X" maps K -> L (sum over channels); "XT" maps L -> K (slices).
+template <typename T>
+struct MvSet {
+  std::vector<MvItem<T>> items;
+  std::vector<YItem<T>> yitems;
+  MvItem<T>* d_items = nullptr;
+  YItem<T>* d_y = nullptr;
+  int max_y_in = 0, max_y_out = 0;
+};
+
+template <typename T>
+static MvItem<T> make_mv(ssa_ctx* c, const Channel& h, bool XT, VecRef in, int in_type, VecRef out,
+                         Cx<T>* g1, Cx<T>* g2, const LzState* st) {
+  MvItem<T> m;
+  m.xh = (const Cx<T>*)(std::is_same<T, float>::value ? h.xh32 : h.xh64);
+  m.in = in; m.out = out;
+  m.min = XT ? c->Lset.dev() : h.K.dev();
+  m.mout = XT ? h.K.dev() : c->Lset.dev();
+  m.g1 = g1; m.g2 = g2; m.st = st;
+  m.log2Mx = c->log2Mx; m.log2My = c->log2My;
+  m.in_type = in_type;
+  m.y_in_hi = XT ? c->ey : h.cy;
+  m.y_out_hi = XT ? h.cy : c->ey;
+  m.pad_ = 0;
+  return m;
+}
+
+template <typename T>
+static YItem<T> ymv(const MvItem<T>& m) {
+  YItem<T> y;
+  y.src = m.g1; y.dst = m.g2; y.mul = m.xh; y.st = m.st;
+  y.log2Mx = m.log2Mx; y.log2My = m.log2My;
+  y.in_hi = m.y_in_hi; y.out_hi = m.y_out_hi; y.scale = T(0);
+  return y;
+}
+
+template <typename T>
+static int finish_set(ssa_ctx* c, MvSet<T>& s) {
+  for (auto& m : s.items) {
+    s.yitems.push_back(ymv(m));
+    s.max_y_in = std::max(s.max_y_in, m.y_in_hi);
+    s.max_y_out = std::max(s.max_y_out, m.y_out_hi);
+  }
+  TRY(upload(c, s.items, &s.d_items));
+  TRY(upload(c, s.yitems, &s.d_y));
+  return SSA_OK;
+}
+
+template <typename T>
+static void run_mv(ssa_ctx* c, const MvSet<T>& s, int max_log2Mx, int max_log2My, int step) {
+  const int n = (int)s.items.size();
+  if (max_log2My == 0)
+    launch_mv1d<T>(s.d_items, n, max_log2Mx, step, twiddles<T>(c->device), c->stream);
+  else
+    launch_mv2d<T>(s.d_items, s.d_y, n, max_log2Mx, max_log2My, s.max_y_in, s.max_y_out, step,
+                   twiddles<T>(c->device), c->stream);
+}
+
+// ============================================================== decompose (batched)
+static int default_k(int r, int64_t L, int64_t K, int req) {
+  int64_t mn = std::min(L, K);
+  int64_t k = req > 0 ? req : 2 * r + 16;
+  k = std::min<int64_t>(k, KMAX);
+  k = std::min<int64_t>(k, mn);
+  k = std::max<int64_t>(k, r);
+  return (int)k;
+}
+
+template <typename T>
+static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
+  // release a previous workspace
+  void* olds[] = {w.st, w.U, w.V, w.p, w.q, w.parts_s, w.parts_l, w.B, w.P, w.Q, w.sig, w.cpa, w.cpb,
+                  w.np_s, w.np_l, w.g1, w.g2, w.Uo, w.Vo, w.sigma, w.sgn};
+  for (void* o : olds)
+    if (o) c->release(o);
+  w = Workspace();
+  w.prec = p.prec;
+  w.r = p.rank;
+  w.k = default_k(p.rank, c->L, c->K, p.krylov_dim);
+  w.kk = std::max(w.r, std::min(w.k - 2, w.r + std::max(8, w.r / 2)));
+  w.swapped = c->L > c->K;
+  w.Ls = w.swapped ? c->K : c->L;
+  w.Kl = w.swapped ? c->L : c->K;
+  w.nblk_s = (int)((w.Ls + SHORT_RB - 1) / SHORT_RB);
+  w.nblk_l = (int)((w.Kl + LONG_RB - 1) / LONG_RB);
+  const int nch = (int)c->ch.size();
+  w.n_part_s = w.swapped ? 1 : nch;
+  w.n_part_l = w.swapped ? nch : 1;
+  const size_t k1 = (size_t)w.k + 1;
+  TRY(c->allocT(&w.st, 1));
+  TRY(c->allocT(&w.U, (size_t)w.Ls * k1));
+  TRY(c->alloc(&w.V, sizeof(T) * (size_t)w.Kl * k1));
+  TRY(c->allocT(&w.p, (size_t)w.Ls));
+  TRY(c->alloc(&w.q, sizeof(T) * (size_t)w.Kl));
+  TRY(c->alloc(&w.parts_s, sizeof(T) * (size_t)w.Ls * w.n_part_s));
+  TRY(c->alloc(&w.parts_l, sizeof(T) * (size_t)w.Kl * w.n_part_l));
+  TRY(c->allocT(&w.B, (size_t)w.k * w.k));
+  TRY(c->allocT(&w.P, (size_t)w.k * w.k));
+  TRY(c->allocT(&w.Q, (size_t)w.k * w.k));
+  TRY(c->allocT(&w.sig, (size_t)w.k));
+  TRY(c->allocT(&w.cpa, (size_t)w.nblk_s * (KMAX + 1)));
+  TRY(c->allocT(&w.cpb, (size_t)w.nblk_s * (KMAX + 1)));
+  TRY(c->allocT(&w.np_s, (size_t)w.nblk_s));
+  TRY(c->allocT(&w.np_l, (size_t)w.nblk_l));
+  if (c->log2My > 0) {
+    const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
+    TRY(c->alloc(&w.g1, sizeof(Cx<T>) * hs * nch));
+    TRY(c->alloc(&w.g2, sizeof(Cx<T>) * hs * nch));
+  }
+  TRY(c->alloc(&w.Uo, sizeof(T) * (size_t)c->L * w.r));
+  TRY(c->alloc(&w.Vo, sizeof(T) * (size_t)c->K * w.r));
+  TRY(c->allocT(&w.sigma, (size_t)w.r));
+  TRY(c->allocT(&w.sgn, (size_t)w.r));
+  CU(cudaMemsetAsync(w.B, 0, sizeof(double) * w.k * w.k, c->stream));
+  CU(cudaMemsetAsync(w.parts_s, 0, sizeof(T) * (size_t)w.Ls * w.n_part_s, c->stream));
+  CU(cudaMemsetAsync(w.parts_l, 0, sizeof(T) * (size_t)w.Kl * w.n_part_l, c->stream));
+  double tol = p.tol > 0 ? p.tol : (std::is_same<T, float>::value ? 1e-7 : 1e-12);
+  int maxr = p.max_restarts > 0 ? p.max_restarts : 40;
+  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0);
+  CU(cudaGetLastError());
+  return SSA_OK;
+}
+
+template <typename T>
+static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, int32_t* status) {
+  ssa_ctx* c0 = cs[0];
+  cudaStream_t st = c0->stream;
+  // make every context's prior work visible on the batch stream
+  std::vector<cudaEvent_t> evs;
+  for (int i = 1; i < n; ++i)
+    if (cs[i]->stream != st) {
+      cudaEvent_t e;
+      CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      CU(cudaEventRecord(e, cs[i]->stream));
+      CU(cudaStreamWaitEvent(st, e, 0));
+      evs.push_back(e);
+    }
+  std::vector<int> ok(n, 1);
+  for (int i = 0; i < n; ++i) {
+    ssa_ctx* c = cs[i];
+    const ssa_params& p = ps[i];
+    int rc = SSA_OK;
+    if (p.rank < 1 || p.rank > std::min(c->L, c->K))
+      rc = fail(SSA_ERANK, "rank %d outside [1, min(L, K) = %lld]", p.rank, (long long)std::min(c->L, c->K));
+    if (rc == SSA_OK) {
+      cudaStream_t keep = c->stream;
+      c->stream = st;
+      rc = ensure_spectrum<T>(c);
+      if (rc == SSA_OK) rc = alloc_ws<T>(c, p, c->ws);
+      c->stream = keep;
+    }
+    if (status) status[i] = rc;
+    if (rc != SSA_OK) { ok[i] = 0; c->ws.done = false; }
+  }
+  // items
+  std::vector<ShortItem> sh;
+  std::vector<LongItem<T>> lg;
+  std::vector<SvdItem> sv;
+  std::vector<RitzItem<T>> rz;
+  std::vector<FinalItem<T>> fi;
+  MvSet<T> mvA, mvAT;    // A v (long -> short) and A^T u (short -> long)
+  int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1, max_steps = 0;
+  int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
+  int max_log2Mx = 1, max_log2My = 0;
+  std::vector<ssa_ctx*> live;
+  for (int i = 0; i < n; ++i) {
+    if (!ok[i]) continue;
+    ssa_ctx* c = cs[i];
+    Workspace& w = c->ws;
+    live.push_back(c);
+    ShortItem s;
+    s.st = w.st; s.U = w.U; s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
+    s.parts_double = std::is_same<T, double>::value; s.p = w.p; s.B = w.B; s.ldb = w.k; s.nblk = w.nblk_s;
+    s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
+    sh.push_back(s);
+    LongItem<T> l;
+    l.st = w.st; l.V = (T*)w.V; l.ldv = w.Kl; l.parts = (const T*)w.parts_l; l.part_ld = w.Kl;
+    l.n_part = w.n_part_l; l.nblk = w.nblk_l; l.q = (T*)w.q; l.npart = w.np_l; l.B = w.B; l.ldb = w.k;
+    l.pad_ = 0; l.Kl = w.Kl; l.seed = ps[i].seed;
+    lg.push_back(l);
+    SvdItem v;
+    v.st = w.st; v.B = w.B; v.ldb = w.k; v.pad_ = 0; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
+    sv.push_back(v);
+    RitzItem<T> z;
+    z.st = w.st; z.U = w.U; z.ldu = w.Ls; z.Ls = w.Ls; z.V = (T*)w.V; z.ldv = w.Kl; z.Kl = w.Kl;
+    z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.pad_ = 0;
+    rz.push_back(z);
+    FinalItem<T> f;
+    f.st = w.st; f.U = w.U; f.ldu = w.Ls; f.Ls = w.Ls; f.V = (const T*)w.V; f.ldv = w.Kl; f.Kl = w.Kl;
+    f.sig = w.sig; f.swapped = w.swapped; f.r = w.r; f.Uo = (T*)w.Uo; f.Vo = (T*)w.Vo; f.sigma_out = w.sigma;
+    f.sgn = w.sgn;
+    fi.push_back(f);
+    // matvec items per channel
+    const size_t hs = c->log2My > 0 ? ((size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My) : 0;
+    for (size_t q = 0; q < c->ch.size(); ++q) {
+      const Channel& h = c->ch[q];
+      Cx<T>* g1 = hs ? (Cx<T>*)w.g1 + q * hs : nullptr;
+      Cx<T>* g2 = hs ? (Cx<T>*)w.g2 + q * hs : nullptr;
+      VecRef vin{}, vout{};
+      if (!w.swapped) {
+        // A v = X v : K -> L partial per channel
+        vin.base = w.V; vin.off = h.koff; vin.ld = w.Kl; vin.st = w.st; vin.jdelta = 0;
+        vout.base = w.parts_s; vout.off = (int64_t)q * w.Ls; vout.ld = 0; vout.st = nullptr;
+        mvA.items.push_back(make_mv<T>(c, h, false, vin, 0, vout, g1, g2, w.st));
+        // A^T u = X^T u : L -> K slice
+        vin.base = w.U; vin.off = 0; vin.ld = w.Ls; vin.st = w.st;
+        vout.base = w.parts_l; vout.off = h.koff; vout.st = nullptr;
+        mvAT.items.push_back(make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st));
+      } else {
+        // A v = X^T v : L -> K slice
+        vin.base = w.V; vin.off = 0; vin.ld = w.Kl; vin.st = w.st;
+        vout.base = w.parts_s; vout.off = h.koff; vout.st = nullptr;
+        mvA.items.push_back(make_mv<T>(c, h, true, vin, 0, vout, g1, g2, w.st));
+        // A^T u = X u : K -> L partial
+        vin.base = w.U; vin.off = h.koff; vin.ld = w.Ls; vin.st = w.st;
+        vout.base = w.parts_l; vout.off = (int64_t)q * w.Kl; vout.st = nullptr;
+        mvAT.items.push_back(make_mv<T>(c, h, false, vin, 1, vout, g1, g2, w.st));
+      }
+    }
+    max_blk_s = std::max(max_blk_s, w.nblk_s);
+    max_blk_l = std::max(max_blk_l, w.nblk_l);
+    max_k = std::max(max_k, w.k);
+    max_r = std::max(max_r, w.r);
+    max_steps = std::max(max_steps, w.k);
+    max_Ls = std::max(max_Ls, w.Ls);
+    max_Kl = std::max(max_Kl, w.Kl);
+    max_rows = std::max(max_rows, std::max(c->L, c->K));
+    max_log2Mx = std::max(max_log2Mx, c->log2Mx);
+    max_log2My = std::max(max_log2My, c->log2My);
+  }
+  if (live.empty()) return status ? status[0] : SSA_EINVAL;
+  // all live problems must share the grid kind (series vs image) for one launch shape
+  ShortItem* d_sh = nullptr; LongItem<T>* d_lg = nullptr; SvdItem* d_sv = nullptr;
+  RitzItem<T>* d_rz = nullptr; FinalItem<T>* d_fi = nullptr;
+  // temporarily route allocations of items through ctx 0 on the batch stream
+  TRY(upload(c0, sh, &d_sh));
+  TRY(upload(c0, lg, &d_lg));
+  TRY(upload(c0, sv, &d_sv));
+  TRY(upload(c0, rz, &d_rz));
+  TRY(upload(c0, fi, &d_fi));
+  TRY(finish_set(c0, mvA));
+  TRY(finish_set(c0, mvAT));
+  const int nl = (int)live.size();
+  // start vectors
+  launch_long_init<T>(d_lg, nl, max_blk_l, st);
+  CU(cudaGetLastError());
+  std::vector<LzState> hst(nl);
+  int rc_all = SSA_OK;
+  for (int cycle = 0;; ++cycle) {
+    // steps of this cycle (j0 = 0 in the first cycle, kk afterwards)
+    int steps = 0;
+    for (int i = 0; i < nl; ++i) {
+      Workspace& w = live[i]->ws;
+      const int j0 = cycle == 0 ? 0 : w.kk;
+      if (cycle == 0 || hst[i].active) steps = std::max(steps, w.k - j0);
+    }
+    for (int s = 0; s < steps; ++s) {
+      run_mv<T>(c0, mvA, max_log2Mx, max_log2My, s);
+      launch_short_steps(d_sh, nl, max_blk_s, s, st);
+      run_mv<T>(c0, mvAT, max_log2Mx, max_log2My, s);
+      launch_long_step<T>(d_lg, nl, max_blk_l, s, st);
+    }
+    launch_bsvd(d_sv, nl, max_k, st);
+    CU(cudaGetLastError());
+    for (int i = 0; i < nl; ++i)
+      CU(cudaMemcpyAsync(&hst[i], live[i]->ws.st, sizeof(LzState), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int i = 0; i < nl; ++i) any |= hst[i].active != 0;
+    if (!any) break;
+    launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 0, st);
+    launch_restart(d_sv, nl, st);
+    CU(cudaGetLastError());
+  }
+  launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 1, st);
+  launch_finalize<T>(d_fi, nl, max_r, max_rows, st);
+  CU(cudaGetLastError());
+  CU(cudaStreamSynchronize(st));
+  for (int i = 0; i < nl; ++i) {
+    Workspace& w = live[i]->ws;
+    w.host_st = hst[i];
+    w.done = true;
+    if (!hst[i].converged && !hst[i].breakdown) {
+      int idx = (int)(std::find(cs, cs + n, live[i]) - cs);
+      if (status) status[idx] = SSA_ENOTCONV;
+      if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", hst[i].maxres);
+    }
+  }
+  c0->release(d_sh); c0->release(d_lg); c0->release(d_sv); c0->release(d_rz); c0->release(d_fi);
+  c0->release(mvA.d_items); c0->release(mvA.d_y); c0->release(mvAT.d_items); c0->release(mvAT.d_y);
+  for (auto e : evs) cudaEventDestroy(e);
+  for (int i = 0; i < n; ++i)
+    if (!ok[i] && rc_all == SSA_OK) rc_all = status ? status[i] : SSA_EINVAL;
+  return rc_all;
+}
+
+// ============================================================== reconstruction
+template <typename T>
+static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int ng, int residual,
+                         double* const* outs, int on_device) {
+  ssa_ctx* c0 = cs[0];
+  cudaStream_t st = c0->stream;
+  const int r = c0->ws.r;
+  std::vector<std::vector<int32_t>> comps(ng);
+  for (int i = 0; i < r; ++i) {
+    if (group_of[i] < -1 || group_of[i] >= ng) return fail(SSA_EINVAL, "group_of[%d] = %d out of range", i, group_of[i]);
+    if (group_of[i] >= 0) comps[group_of[i]].push_back(i);
+  }
+  std::vector<int32_t> flat, start(ng + 1, 0);
+  for (int g = 0; g < ng; ++g) { start[g] = (int32_t)flat.size(); flat.insert(flat.end(), comps[g].begin(), comps[g].end()); }
+  start[ng] = (int32_t)flat.size();
+  int32_t* d_flat = nullptr;
+  TRY(upload(c0, flat, &d_flat));
+  std::vector<void*> tmp;
+  const int nout = ng + (residual ? 1 : 0);
+  std::vector<double*> dout(n, nullptr);
+  const Cx<T>* tw = twiddles<T>(c0->device);
+  if (c0->log2My == 0) {
+    // ---- series: F(U_i) once per problem, then one CTA per (problem, group, channel)
+    std::vector<RecColItem<T>> ui;
+    std::vector<Rec1Item<T>> ri;
+    int max_log2Mx = 1;
+    for (int p = 0; p < n; ++p) {
+      ssa_ctx* c = cs[p];
+      Workspace& w = c->ws;
+      const int H = 1 << (c->log2Mx - 1);
+      Cx<T>* gu = nullptr;
+      TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * (size_t)(H + 1) * r));
+      tmp.push_back(gu);
+      double* o = nullptr;
+      if (on_device) o = outs[p];
+      else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
+      dout[p] = o;
+      for (int i = 0; i < r; ++i) {
+        RecColItem<T> u;
+        u.vec = (const T*)w.Uo + (size_t)c->L * i; u.map = c->Lset.dev(); u.dst = gu + (size_t)(H + 1) * i;
+        u.log2Mx = c->log2Mx; u.ncols = 1;
+        ui.push_back(u);
+      }
+      for (int g = 0; g < ng; ++g)
+        for (size_t q = 0; q < c->ch.size(); ++q) {
+          const Channel& h = c->ch[q];
+          Rec1Item<T> it;
+          it.V = (const T*)w.Vo + h.koff; it.ldv = c->K; it.map = h.K.dev();
+          it.gu = gu; it.ldgu = H + 1; it.sigma = w.sigma;
+          it.comps = d_flat + start[g]; it.ncomp = start[g + 1] - start[g];
+          it.log2Mx = c->log2Mx; it.w = h.w; it.n = (int32_t)h.nx;
+          it.out = o + (size_t)g * c->total + h.data_off;
+          it.inv_norm = 1.0 / (double)(2 * H);
+          ri.push_back(it);
+        }
+      max_log2Mx = std::max(max_log2Mx, c->log2Mx);
+    }
+    RecColItem<T>* d_ui = nullptr; Rec1Item<T>* d_ri = nullptr;
+    TRY(upload(c0, ui, &d_ui));
+    TRY(upload(c0, ri, &d_ri));
+    launch_rec_col_fft<T>(d_ui, (int)ui.size(), max_log2Mx, 1, tw, st);
+    launch_rec1d<T>(d_ri, (int)ri.size(), max_log2Mx, tw, st);
+    CU(cudaGetLastError());
+    tmp.push_back(d_ui); tmp.push_back(d_ri);
+  } else {
+    // ---- images: per problem, per component 2D transforms, accumulated per group
+    for (int p = 0; p < n; ++p) {
+      ssa_ctx* c = cs[p];
+      Workspace& w = c->ws;
+      const Channel& h = c->ch[0];
+      const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
+      const size_t hs = (size_t)(H + 1) * My;
+      double* o = nullptr;
+      if (on_device) o = outs[p];
+      else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
+      dout[p] = o;
+      Cx<T> *gx = nullptr, *gu = nullptr, *acc = nullptr, *g2 = nullptr;
+      TRY(c0->alloc((void**)&gx, sizeof(Cx<T>) * hs));
+      TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * hs));
+      TRY(c0->alloc((void**)&acc, sizeof(Cx<T>) * hs * std::max(ng, 1)));
+      TRY(c0->alloc((void**)&g2, sizeof(Cx<T>) * hs));
+      tmp.push_back(gx); tmp.push_back(gu); tmp.push_back(acc); tmp.push_back(g2);
+      CU(cudaMemsetAsync(acc, 0, sizeof(Cx<T>) * hs * std::max(ng, 1), st));
+      std::vector<double> sig(r);
+      CU(cudaMemcpyAsync(sig.data(), w.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      std::vector<RecColItem<T>> cu(2);
+      std::vector<YItem<T>> yu(2);
+      RecColItem<T>* d_cu = nullptr; YItem<T>* d_yu = nullptr;
+      TRY(c0->allocT(&d_cu, 2 * (size_t)r));
+      TRY(c0->allocT(&d_yu, 2 * (size_t)r));
+      tmp.push_back(d_cu); tmp.push_back(d_yu);
+      std::vector<RecColItem<T>> allc;
+      std::vector<YItem<T>> ally;
+      for (int i = 0; i < r; ++i) {
+        const int g = group_of[i];
+        RecColItem<T> a;
+        a.vec = (const T*)w.Uo + (size_t)c->L * i; a.map = c->Lset.dev(); a.dst = gx; a.log2Mx = c->log2Mx;
+        a.ncols = c->ey;
+        RecColItem<T> b;
+        b.vec = (const T*)w.Vo + (size_t)c->K * i; b.map = h.K.dev(); b.dst = gx; b.log2Mx = c->log2Mx;
+        b.ncols = h.cy;
+        YItem<T> ya;
+        ya.src = gx; ya.dst = gu; ya.mul = nullptr; ya.st = nullptr; ya.log2Mx = c->log2Mx; ya.log2My = c->log2My;
+        ya.in_hi = c->ey; ya.out_hi = My; ya.scale = T(0);
+        YItem<T> yb = ya;
+        yb.dst = acc + (size_t)std::max(g, 0) * hs; yb.mul = gu; yb.in_hi = h.cy;
+        yb.scale = (T)(sig[i] / ((double)(2 * H) * (double)My));
+        allc.push_back(a); allc.push_back(b);
+        ally.push_back(ya); ally.push_back(yb);
+      }
+      CU(cudaMemcpyAsync(d_cu, allc.data(), sizeof(RecColItem<T>) * allc.size(), cudaMemcpyHostToDevice, st));
+      CU(cudaMemcpyAsync(d_yu, ally.data(), sizeof(YItem<T>) * ally.size(), cudaMemcpyHostToDevice, st));
+      for (int i = 0; i < r; ++i) {
+        if (group_of[i] < 0) continue;
+        launch_rec_col_fft<T>(d_cu + 2 * i, 1, c->log2Mx, c->ey, tw, st);
+        launch_ypass<T>(d_yu + 2 * i, 1, Y_FWD, c->log2Mx, c->log2My, -1, tw, st);
+        launch_rec_col_fft<T>(d_cu + 2 * i + 1, 1, c->log2Mx, h.cy, tw, st);
+        launch_ypass<T>(d_yu + 2 * i + 1, 1, Y_CONVACC, c->log2Mx, c->log2My, -1, tw, st);
+      }
+      std::vector<YItem<T>> yi;
+      std::vector<Rec2Item<T>> xi;
+      for (int g = 0; g < ng; ++g) {
+        YItem<T> y;
+        y.src = acc + (size_t)g * hs; y.dst = g2; y.mul = nullptr; y.st = nullptr;
+        y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = My; y.out_hi = (int)h.ny; y.scale = T(0);
+        yi.push_back(y);
+        Rec2Item<T> x;
+        x.g2 = g2; x.w = h.w; x.out = o + (size_t)g * c->total; x.log2Mx = c->log2Mx; x.nx = (int)h.nx;
+        x.ny = (int)h.ny; x.pad_ = 0; x.inv_norm = 1.0;
+        xi.push_back(x);
+      }
+      YItem<T>* d_yi = nullptr; Rec2Item<T>* d_xi = nullptr;
+      TRY(upload(c0, yi, &d_yi));
+      TRY(upload(c0, xi, &d_xi));
+      tmp.push_back(d_yi); tmp.push_back(d_xi);
+      for (int g = 0; g < ng; ++g) {
+        launch_ypass<T>(d_yi + g, 1, Y_INV, c->log2Mx, c->log2My, -1, tw, st);
+        launch_rec_xinv<T>(d_xi + g, 1, c->log2Mx, (int)h.ny, tw, st);
+      }
+      CU(cudaGetLastError());
+    }
+  }
+  // residual and copy-out
+  for (int p = 0; p < n; ++p) {
+    ssa_ctx* c = cs[p];
+    if (residual) {
+      for (size_t q = 0; q < c->ch.size(); ++q) {
+        const Channel& h = c->ch[q];
+        const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
+        launch_residual((const char*)c->data + h.data_off * esz, c->dtype == SSA_F64, h.w, h.nx * h.ny,
+                        dout[p] + h.data_off, c->total, ng, dout[p] + (size_t)ng * c->total + h.data_off, st);
+      }
+      CU(cudaGetLastError());
+    }
+    if (!on_device)
+      CU(cudaMemcpyAsync(outs[p], dout[p], sizeof(double) * (size_t)c->total * nout, cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  for (void* t : tmp) c0->release(t);
+  c0->release(d_flat);
+  return SSA_OK;
+}
+
+template <typename T>
+static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, int on_device) {
+  TRY(ensure_spectrum<T>(c));
+  const int64_t nin = transpose ? c->L : c->K, nout = transpose ? c->K : c->L;
+  const int nch = (int)c->ch.size();
+  T *din = nullptr, *dparts = nullptr;
+  double *dd = nullptr, *dres = nullptr;
+  TRY(c->alloc((void**)&din, sizeof(T) * nin));
+  const int nparts = transpose ? 1 : nch;
+  TRY(c->alloc((void**)&dparts, sizeof(T) * (size_t)nout * nparts));
+  if (on_device) { dd = const_cast<double*>(in); dres = out; }
+  else {
+    TRY(c->allocT(&dd, (size_t)nin));
+    TRY(c->allocT(&dres, (size_t)nout));
+    CU(cudaMemcpyAsync(dd, in, sizeof(double) * nin, cudaMemcpyHostToDevice, c->stream));
+  }
+  k_convert<T, double><<<grid1(nin), 256, 0, c->stream>>>(dd, din, nin);
+  CU(cudaGetLastError());
+  void *g1 = nullptr, *g2 = nullptr;
+  const size_t hs = c->log2My > 0 ? ((size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My) : 0;
+  if (hs) { TRY(c->alloc(&g1, sizeof(Cx<T>) * hs * nch)); TRY(c->alloc(&g2, sizeof(Cx<T>) * hs * nch)); }
+  MvSet<T> s;
+  for (int q = 0; q < nch; ++q) {
+    const Channel& h = c->ch[q];
+    VecRef vi{}, vo{};
+    vi.base = din; vi.off = transpose ? 0 : h.koff; vi.ld = 0; vi.st = nullptr;
+    vo.base = dparts; vo.off = transpose ? h.koff : (int64_t)q * nout; vo.ld = 0; vo.st = nullptr;
+    s.items.push_back(make_mv<T>(c, h, transpose != 0, vi, 0, vo, hs ? (Cx<T>*)g1 + q * hs : nullptr,
+                                 hs ? (Cx<T>*)g2 + q * hs : nullptr, nullptr));
+  }
+  TRY(finish_set(c, s));
+  run_mv<T>(c, s, c->log2Mx, c->log2My, 0);
+  k_sum_parts_to_double<T><<<grid1(nout), 256, 0, c->stream>>>(dparts, nparts, nout, nout, dres);
+  CU(cudaGetLastError());
+  if (!on_device) CU(cudaMemcpyAsync(out, dres, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->release(din); c->release(dparts);
+  if (!on_device) { c->release(dd); c->release(dres); }
+  if (g1) { c->release(g1); c->release(g2); }
+  c->release(s.d_items); c->release(s.d_y);
+  return SSA_OK;
+}
+
+// ============================================================== C ABI
+extern "C" {
+
+const char* ssa_version(void) { return "ssa-gb300 0.1 (sm_103a)"; }
+
+const char* ssa_strerror(int code) {
+  switch (code) {
+    case SSA_OK: return "ok";
+    case SSA_EINVAL: return "invalid argument";
+    case SSA_EEMPTY: return "empty origin set";
+    case SSA_ERANK: return "rank out of range";
+    case SSA_ENOMEM: return "out of device memory";
+    case SSA_ENOTCONV: return "not converged";
+    case SSA_ETIMEOUT: return "timeout";
+    case SSA_ECUDA: return "CUDA error";
+    case SSA_ESTATE: return "call out of order";
+    case SSA_EUNSUPPORTED: return "unsupported size";
+  }
+  return "unknown error";
+}
+
+const char* ssa_last_error(void) { return g_err; }
+
+int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out) {
+  if (!in || !win || !out || !in->data) return fail(SSA_EINVAL, "null argument");
+  *out = nullptr;
+  if (in->dtype != SSA_F32 && in->dtype != SSA_F64) return fail(SSA_EINVAL, "dtype must be SSA_F32 or SSA_F64");
+  ssa_ctx* c = new ssa_ctx();
+  auto bail = [&](int rc) { ssa_destroy(c); return rc; };
+  CU(cudaGetDevice(&c->device));
+  if (ensure_tables(c->device) != SSA_OK) return bail(SSA_ECUDA);
+  c->kind = in->kind;
+  c->dtype = in->dtype;
+  if (cuda_stream) c->stream = (cudaStream_t)cuda_stream;
+  else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(SSA_ECUDA, "stream creation failed"));
+    c->own_stream = true;
+  }
+  // channel geometry
+  if (in->kind == SSA_1D) {
+    if (in->n < 2) return bail(fail(SSA_EINVAL, "series length %lld < 2", (long long)in->n));
+    if (win->L < 2 || win->L >= in->n) return bail(fail(SSA_EINVAL, "window L=%lld must satisfy 1 < L < N=%lld", (long long)win->L, (long long)in->n));
+    Channel h; h.nx = in->n; h.ny = 1; h.data_off = 0;
+    c->ch.push_back(h);
+    c->total = in->n;
+  } else if (in->kind == SSA_MSSA) {
+    if (in->n_series < 1 || !in->lengths) return bail(fail(SSA_EINVAL, "MSSA needs n_series >= 1 and lengths"));
+    int64_t off = 0, mn = INT64_MAX;
+    for (int q = 0; q < in->n_series; ++q) {
+      Channel h; h.nx = in->lengths[q]; h.ny = 1; h.data_off = off;
+      if (h.nx < 2) return bail(fail(SSA_EINVAL, "series %d has length %lld", q, (long long)h.nx));
+      off += h.nx; mn = std::min(mn, h.nx);
+      c->ch.push_back(h);
+    }
+    if (win->L < 2 || win->L >= mn) return bail(fail(SSA_EINVAL, "window L=%lld must satisfy 1 < L < min N_p=%lld", (long long)win->L, (long long)mn));
+    c->total = off;
+  } else if (in->kind == SSA_2D) {
+    if (in->nx < 1 || in->ny < 1) return bail(fail(SSA_EINVAL, "image size"));
+    if (win->lx < 1 || win->ly < 1 || win->lx > in->nx || win->ly > in->ny || win->lx * win->ly <= 1 ||
+        win->lx * win->ly >= in->nx * in->ny)
+      return bail(fail(SSA_EINVAL, "window %lldx%lld must satisfy 1<=lx<=nx, 1<=ly<=ny, 1<lx*ly<nx*ny",
+                       (long long)win->lx, (long long)win->ly));
+    Channel h; h.nx = in->nx; h.ny = in->ny; h.data_off = 0;
+    c->ch.push_back(h);
+    c->total = in->nx * in->ny;
+  } else {
+    return bail(fail(SSA_EINVAL, "unknown kind %d", in->kind));
+  }
+  int64_t mx = 0, my = 0;
+  for (auto& h : c->ch) { mx = std::max(mx, h.nx); my = std::max(my, h.ny); }
+  c->log2Mx = std::max(ilog2_ceil(mx), 4);
+  c->log2My = (in->kind == SSA_2D) ? ilog2_ceil(my) : 0;
+  if (c->log2Mx > 14) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along x exceeds 16384", (long long)(1ll << c->log2Mx)));
+  if (c->log2My > 12) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along y exceeds 4096", (long long)(1ll << c->log2My)));
+  // data (and mask) to the device; masked samples become NaN in the device copy
+  const size_t esz = in->dtype == SSA_F64 ? 8 : 4;
+  int rc = c->alloc(&c->data, esz * (size_t)c->total);
+  if (rc) return bail(rc);
+  if (cudaMemcpyAsync(c->data, in->data, esz * c->total, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess)
+    return bail(fail(SSA_ECUDA, "input copy failed"));
+  if (in->mask) {
+    uint8_t* dm = nullptr;
+    rc = c->allocT(&dm, (size_t)c->total);
+    if (rc) return bail(rc);
+    if (cudaMemcpyAsync(dm, in->mask, (size_t)c->total, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+      return bail(fail(SSA_ECUDA, "mask copy failed"));
+    // fold the mask into the data as NaN so the observed set is one test
+    extern void launch_apply_mask(void*, int, const uint8_t*, int64_t, cudaStream_t);
+    launch_apply_mask(c->data, in->dtype == SSA_F64, dm, c->total, c->stream);
+    c->release(dm);
+  }
+  rc = embed_shapes(c, win);
+  if (rc) return bail(rc);
+  CU(cudaStreamSynchronize(c->stream));
+  *out = c;
+  return SSA_OK;
+}
+
+int ssa_decompose_batch(ssa_ctx* const* ctxs, int32_t n, const ssa_params* params, int32_t* status) {
+  if (!ctxs || n < 1 || !params) return fail(SSA_EINVAL, "null argument");
+  const int prec = params[0].prec;
+  const bool img = ctxs[0]->log2My > 0;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(SSA_EINVAL, "null context %d", i);
+    if (params[i].prec != prec) return fail(SSA_EINVAL, "one precision form per batch");
+    if ((ctxs[i]->log2My > 0) != img) return fail(SSA_EINVAL, "a batch holds only series or only images");
+    if (params[i].prec == SSA_PREC_FP64 && ctxs[i]->log2Mx > 13)
+      return fail(SSA_EUNSUPPORTED, "FP64 form supports FFT length <= 8192 along x");
+  }
+  if (prec == SSA_PREC_FP64) return decompose_batch_T<double>(ctxs, n, params, status);
+  if (prec == SSA_PREC_FP32FFT_FP64REORTH) return decompose_batch_T<float>(ctxs, n, params, status);
+  return fail(SSA_EINVAL, "unknown precision %d", prec);
+}
+
+int ssa_decompose(ssa_ctx* ctx, const ssa_params* params) {
+  int32_t st = 0;
+  return ssa_decompose_batch(&ctx, 1, params, &st);
+}
+
+int ssa_get_info(const ssa_ctx* c, ssa_info* info) {
+  if (!c || !info) return fail(SSA_EINVAL, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  info->L = c->L; info->K = c->K;
+  info->nx = c->ch[0].nx; info->ny = c->ch[0].ny;
+  info->n_channels = (int32_t)c->ch.size();
+  info->fft_mx = 1ll << c->log2Mx; info->fft_my = 1ll << c->log2My;
+  info->device_bytes = c->bytes;
+  if (c->ws.done) {
+    info->rank = c->ws.r; info->krylov_dim = c->ws.k; info->restarts = c->ws.host_st.restarts;
+    info->converged = c->ws.host_st.converged || c->ws.host_st.breakdown; info->prec = c->ws.prec;
+    info->max_residual = c->ws.host_st.maxres;
+  }
+  return SSA_OK;
+}
+
+int ssa_get_sigma(const ssa_ctx* c, double* sigma, int32_t r) {
+  if (!c || !sigma) return fail(SSA_EINVAL, "null argument");
+  if (!c->ws.done) return fail(SSA_ESTATE, "no decomposition yet");
+  if (r < 0 || r > c->ws.r) return fail(SSA_EINVAL, "r=%d exceeds the decomposed rank %d", r, c->ws.r);
+  CU(cudaMemcpyAsync(sigma, c->ws.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return SSA_OK;
+}
+
+int ssa_get_vectors(const ssa_ctx* cc, double* U, double* V, int32_t on_device) {
+  ssa_ctx* c = const_cast<ssa_ctx*>(cc);
+  if (!c) return fail(SSA_EINVAL, "null argument");
+  if (!c->ws.done) return fail(SSA_ESTATE, "no decomposition yet");
+  const Workspace& w = c->ws;
+  struct { double* dst; const void* src; int64_t n; } jobs[2] = {{U, w.Uo, c->L * w.r}, {V, w.Vo, c->K * w.r}};
+  for (auto& j : jobs) {
+    if (!j.dst) continue;
+    double* d = j.dst;
+    if (!on_device) TRY(c->allocT(&d, (size_t)j.n));
+    if (w.prec == SSA_PREC_FP64)
+      CU(cudaMemcpyAsync(d, j.src, sizeof(double) * j.n, cudaMemcpyDeviceToDevice, c->stream));
+    else
+      k_convert<double, float><<<grid1(j.n), 256, 0, c->stream>>>((const float*)j.src, d, j.n);
+    CU(cudaGetLastError());
+    if (!on_device) {
+      CU(cudaMemcpyAsync(j.dst, d, sizeof(double) * j.n, cudaMemcpyDeviceToHost, c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      c->release(d);
+    }
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  return SSA_OK;
+}
+
+int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_of, int32_t n_groups,
+                          int32_t residual, double* const* outs, int32_t on_device) {
+  if (!ctxs || n < 1 || !group_of || !outs || n_groups < 0) return fail(SSA_EINVAL, "null argument");
+  const int prec = ctxs[0]->ws.prec;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || !ctxs[i]->ws.done) return fail(SSA_ESTATE, "context %d has no decomposition", i);
+    if (ctxs[i]->ws.prec != prec || ctxs[i]->ws.r != ctxs[0]->ws.r) return fail(SSA_EINVAL, "batch mixes precision or rank");
+    if ((ctxs[i]->log2My > 0) != (ctxs[0]->log2My > 0)) return fail(SSA_EINVAL, "batch mixes series and images");
+    if (!outs[i]) return fail(SSA_EINVAL, "null output %d", i);
+  }
+  if (n_groups + (residual ? 1 : 0) == 0) return SSA_OK;
+  if (prec == SSA_PREC_FP64) return reconstruct_T<double>(ctxs, n, group_of, n_groups, residual, outs, on_device);
+  return reconstruct_T<float>(ctxs, n, group_of, n_groups, residual, outs, on_device);
+}
+
+int ssa_reconstruct(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, int32_t residual, double* out,
+                    int32_t on_device) {
+  return ssa_reconstruct_batch(&ctx, 1, group_of, n_groups, residual, &out, on_device);
+}
+
+int ssa_get_shape(const ssa_ctx* cc, int64_t* L, int64_t* K, uint8_t* origin_mask, int32_t* weights) {
+  ssa_ctx* c = const_cast<ssa_ctx*>(cc);
+  if (!c) return fail(SSA_EINVAL, "null argument");
+  if (L) *L = c->L;
+  if (K) *K = c->K;
+  if (origin_mask) {
+    uint8_t* d = nullptr;
+    TRY(c->allocT(&d, (size_t)c->total));
+    for (auto& h : c->ch) {
+      dim3 g(grid1(h.nx), (unsigned)h.ny);
+      if (h.K.count > 0 || h.K.bits)
+        k_kmask<<<g, 256, 0, c->stream>>>(h.K.bits, h.K.words, h.cx, h.cy, (int)h.nx, (int)h.ny, d + h.data_off);
+      else
+        CU(cudaMemsetAsync(d + h.data_off, 0, (size_t)(h.nx * h.ny), c->stream));
+    }
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(origin_mask, d, (size_t)c->total, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->release(d);
+  }
+  if (weights) {
+    for (auto& h : c->ch)
+      CU(cudaMemcpyAsync(weights + h.data_off, h.w, sizeof(int32_t) * h.nx * h.ny, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  return SSA_OK;
+}
+
+int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, double* out, int32_t on_device) {
+  if (!ctx || !in || !out) return fail(SSA_EINVAL, "null argument");
+  if (prec == SSA_PREC_FP64) {
+    if (ctx->log2Mx > 13) return fail(SSA_EUNSUPPORTED, "FP64 form supports FFT length <= 8192 along x");
+    return matvec_T<double>(ctx, transpose, in, out, on_device);
+  }
+  return matvec_T<float>(ctx, transpose, in, out, on_device);
+}
+
+int ssa_synchronize(ssa_ctx* c) {
+  if (!c) return fail(SSA_EINVAL, "null argument");
+  CU(cudaStreamSynchronize(c->stream));
+  return SSA_OK;
+}
+
+void ssa_destroy(ssa_ctx* c) {
+  if (!c) return;
+  if (c->stream) {
+    for (auto& a : c->allocs) cudaFreeAsync(a.first, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+}
+
+}  // extern "C"
+
+// NaN at masked-out samples (the observed set is then "not NaN")
+__global__ void k_apply_mask(void* data, int dbl, const uint8_t* m, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!m[i]) {
+      if (dbl) ((double*)data)[i] = __longlong_as_double(0x7ff8000000000000ll);
+      else ((float*)data)[i] = __int_as_float(0x7fc00000);
+    }
+}
+
+void launch_apply_mask(void* data, int dbl, const uint8_t* m, int64_t n, cudaStream_t st) {
+  k_apply_mask<<<grid1(n), 256, 0, st>>>(data, dbl, m, n);
+}

@@ -1,0 +1,166 @@
+// Block-cooperative FFTs in shared memory, and the packed real-to-half-spectrum
+// conversions used by every pass.
+//
+// Complex DFT convention (Sec. 6.1.1, eq. fft_def): Y_k = sum_n x_n W^{nk},
+// W = exp(-2 pi i / n); the inverse uses W^{-1} and is left unnormalised here
+// (all scale factors are folded into the precomputed data spectrum).
+//
+// block_fft runs the Stockham autosort algorithm (published by Stockham, in
+// the GPU form of Govindaraju et al., SC'08): log2(n) is split into radix-8
+// stages plus one radix-4 or radix-2 stage; each stage reads R values with
+// stride n/R, multiplies by W_{Ns R}^{k r}, does an R-point DFT and writes
+// them with stride Ns, ping-ponging between two shared buffers.
+#pragma once
+#include "common.cuh"
+
+namespace ssa {
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft2(Cx<T>& a, Cx<T>& b) {
+  Cx<T> t = a - b;
+  a = a + b;
+  b = t;
+}
+
+// multiply by the 4th root W_4 = -i (forward) or +i (inverse)
+template <typename T, bool INV>
+__device__ __forceinline__ Cx<T> rot4(Cx<T> a) { return INV ? mul_pi(a) : mul_mi(a); }
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(Cx<T>& v0, Cx<T>& v1, Cx<T>& v2, Cx<T>& v3) {
+  Cx<T> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = rot4<T, INV>(v1 - v3);
+  v0 = t0 + t2;
+  v2 = t0 - t2;
+  v1 = t1 + t3;
+  v3 = t1 - t3;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(Cx<T>* v) {
+  // split into even / odd 4-point DFTs, then combine with W_8^k
+  dft4<T, INV>(v[0], v[2], v[4], v[6]);
+  dft4<T, INV>(v[1], v[3], v[5], v[7]);
+  const T h = T(0.70710678118654752440084436210485);
+  Cx<T> o1 = v[3], o2 = v[5], o3 = v[7];
+  // W_8^1 = (1 - i)/sqrt2, W_8^2 = -i, W_8^3 = (-1 - i)/sqrt2 (conjugates for INV)
+  if (!INV) {
+    o1 = cx(h * (o1.re + o1.im), h * (o1.im - o1.re));
+    o2 = mul_mi(o2);
+    o3 = cx(h * (o3.im - o3.re), -h * (o3.re + o3.im));
+  } else {
+    o1 = cx(h * (o1.re - o1.im), h * (o1.re + o1.im));
+    o2 = mul_pi(o2);
+    o3 = cx(-h * (o3.re + o3.im), h * (o3.re - o3.im));
+  }
+  Cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  v[0] = e0 + o0; v[4] = e0 - o0;
+  v[1] = e1 + o1; v[5] = e1 - o1;
+  v[2] = e2 + o2; v[6] = e2 - o2;
+  v[3] = e3 + o3; v[7] = e3 - o3;
+}
+
+template <typename T, bool INV, int LR>
+__device__ __forceinline__ void stockham_stage(const Cx<T>* __restrict__ src, Cx<T>* __restrict__ dst,
+                                               int log2n, int nb, int log2Ns, const Cx<T>* tw) {
+  constexpr int R = 1 << LR;
+  const int n = 1 << log2n;
+  const int nq = n >> LR;            // butterflies per transform
+  const int Ns = 1 << log2Ns;
+  const int total = nq * nb;
+  for (int jj = threadIdx.x; jj < total; jj += blockDim.x) {
+    const int b = jj >> (log2n - LR);
+    const int j = jj & (nq - 1);
+    const Cx<T>* s = src + ((int64_t)b << log2n);
+    Cx<T>* d = dst + ((int64_t)b << log2n);
+    const int k = j & (Ns - 1);
+    Cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[j + r * nq];
+    if (log2Ns > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        Cx<T> w = twid(tw, log2Ns + LR, (int64_t)k * r);
+        if (INV) w = conj(w);
+        v[r] = v[r] * w;
+      }
+    }
+    if (LR == 3) dft8<T, INV>(v);
+    else if (LR == 2) dft4<T, INV>(v[0], v[1], v[2], v[3]);
+    else dft2<T, INV>(v[0], v[1]);
+    const int base = ((j - k) << LR) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[base + r * Ns] = v[r];
+  }
+}
+
+// nb independent transforms of length 2^log2n stored back to back in a.
+// Returns the buffer (a or b) holding the result.  Caller syncs before.
+template <typename T, bool INV>
+__device__ Cx<T>* block_fft(Cx<T>* a, Cx<T>* b, int log2n, int nb, const Cx<T>* tw) {
+  int done = 0;
+  while (done < log2n) {
+    int rem = log2n - done;
+    if (rem >= 3) stockham_stage<T, INV, 3>(a, b, log2n, nb, done, tw), done += 3;
+    else if (rem == 2) stockham_stage<T, INV, 2>(a, b, log2n, nb, done, tw), done += 2;
+    else stockham_stage<T, INV, 1>(a, b, log2n, nb, done, tw), done += 1;
+    __syncthreads();
+    Cx<T>* t = a; a = b; b = t;
+  }
+  return a;
+}
+
+// Packed real transform, forward: z[n] = g[2n] + i g[2n+1] (length H) has
+// been transformed to Z; produce the half spectrum G[k], k = 0..H, of the real
+// length-2H signal g:  G[k] = E + W^k O,  E = (Z[k] + conj Z[H-k]) / 2,
+// O = -i (Z[k] - conj Z[H-k]) / 2,  W = exp(-2 pi i / 2H).
+template <typename T>
+__device__ __forceinline__ Cx<T> untwist_fwd(const Cx<T>* Z, int k, int log2H, const Cx<T>* tw) {
+  const int H = 1 << log2H;
+  Cx<T> a = Z[k & (H - 1)];
+  Cx<T> b = conj(Z[(H - k) & (H - 1)]);
+  Cx<T> E = T(0.5) * (a + b);
+  Cx<T> O = T(0.5) * mul_mi(a - b);
+  return E + twid(tw, log2H + 1, k) * O;
+}
+
+// Packed real transform, inverse: from a half spectrum P[0..H] of a real
+// signal r of length 2H, form Q[k] (k < H) whose unnormalised inverse
+// length-H transform is r[2n] + i r[2n+1] times 2H:
+// Q[k] = (P[k] + conj P[H-k]) + i W^{-k} (P[k] - conj P[H-k]).
+template <typename T>
+__device__ __forceinline__ Cx<T> twist_inv(const Cx<T>* P, int k, int log2H, const Cx<T>* tw) {
+  const int H = 1 << log2H;
+  Cx<T> a = P[k];
+  Cx<T> b = conj(P[H - k]);
+  Cx<T> w = conj(twid(tw, log2H + 1, k));
+  return (a + b) + mul_pi(w * (a - b));
+}
+
+// Exclusive prefix of popcounts of n words (n <= 32 * blockDim.x), result in
+// out[0..n).  Uses out as scratch; ends with __syncthreads.
+__device__ __forceinline__ void block_popc_scan(const uint32_t* words, int n, int32_t* out,
+                                                int32_t* warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = (i < n) ? __popc(words[i]) : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int carry = (base == 0) ? 0 : out[base - 1] + __popc(words[base - 1]);
+      for (int w = 0; w < nw; ++w) { int t = warp_tot[w]; warp_tot[w] = carry; carry += t; }
+    }
+    __syncthreads();
+    if (i < n) out[i] = x - v + warp_tot[warp];
+    __syncthreads();
+  }
+}
+
+}  // namespace ssa

@@ -1,0 +1,540 @@
+// Golub-Kahan-Lanczos bidiagonalisation with one-sided full
+// re-orthogonalisation and thick restart; Ritz extraction by a one-sided
+// Jacobi SVD of the small B in FP64.  See lanczos.h for the recurrences.
+//
+// The paper delegates this step to PROPACK / nu-TRLan (Sec. 2.4, 4.2); the
+// method computes the same r leading eigentriples (Sec. 2.1, Step 2).
+#include <algorithm>
+#include <type_traits>
+#include "lanczos.h"
+#include "launch.h"
+
+namespace ssa {
+
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; result valid in every thread (uses red[32]).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];   // fixed order: deterministic
+  return t;
+}
+
+__device__ __forceinline__ bool lz_skip(const LzState* st, int j) {
+  return !st->active || j >= st->k || j < -1;
+}
+
+// partial dots out[i] = sum over this block's rows of U[row, i] * pv[row - r0]
+__device__ void block_dots(const double* __restrict__ U, int64_t ldu, int64_t r0, int nrows,
+                           const double* pv, int j, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < j; i += nw) {
+    const double* col = U + ldu * i + r0;
+    double acc = 0.0;
+    for (int t = lane; t < nrows; t += 32) acc += col[t] * pv[t];
+    acc = warp_sum(acc);
+    if (lane == 0) out[i] = acc;
+  }
+}
+
+// ------------------------------------------------------------ short side
+// step 1: p = sum(partials) - sum_i B[i,j] u_i ; partial dots U^T p
+__global__ void __launch_bounds__(SHORT_RB) k_short1(const ShortItem* __restrict__ items, int s) {
+  const ShortItem it = items[blockIdx.y];
+  const int j = it.st->j0 + s;
+  if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
+  __shared__ double bcol[KMAX + 1];
+  __shared__ double pv[SHORT_RB];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) bcol[i] = it.B[i + (int64_t)it.ldb * j];
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * SHORT_RB;
+  const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
+  const int64_t row = r0 + threadIdx.x;
+  double val = 0.0;
+  if ((int)threadIdx.x < nrows) {
+    if (it.parts_double) {
+      const double* pp = (const double*)it.parts;
+      for (int q = 0; q < it.n_part; ++q) val += pp[q * it.part_ld + row];
+    } else {
+      const float* pp = (const float*)it.parts;
+      for (int q = 0; q < it.n_part; ++q) val += (double)pp[q * it.part_ld + row];
+    }
+    for (int i = 0; i < j; ++i) {
+      const double b = bcol[i];
+      if (b != 0.0) val -= b * it.U[row + it.ldu * i];
+    }
+    it.p[row] = val;
+  }
+  pv[threadIdx.x] = val;
+  __syncthreads();
+  block_dots(it.U, it.ldu, r0, nrows, pv, j, it.cpa + (int64_t)blockIdx.x * (KMAX + 1));
+}
+
+// steps 2 and 3: p -= U c (c summed from the partials in fixed order); step 2
+// also forms the partial dots of the second Gram-Schmidt pass, step 3 the
+// partial squared norm.
+template <int PASS>
+__global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restrict__ items, int s) {
+  const ShortItem it = items[blockIdx.y];
+  const int j = it.st->j0 + s;
+  if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
+  __shared__ double c[KMAX + 1];
+  __shared__ double pv[SHORT_RB];
+  __shared__ double red[32];
+  const double* src = (PASS == 2) ? it.cpa : it.cpb;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    double a = 0.0;
+    for (int b = 0; b < it.nblk; ++b) a += src[(int64_t)b * (KMAX + 1) + i];
+    c[i] = a;
+  }
+  __syncthreads();
+  const int64_t r0 = (int64_t)blockIdx.x * SHORT_RB;
+  const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
+  const int64_t row = r0 + threadIdx.x;
+  double val = 0.0;
+  if ((int)threadIdx.x < nrows) {
+    val = it.p[row];
+    for (int i = 0; i < j; ++i) val -= it.U[row + it.ldu * i] * c[i];
+    it.p[row] = val;
+  }
+  if (PASS == 2) {
+    pv[threadIdx.x] = val;
+    __syncthreads();
+    block_dots(it.U, it.ldu, r0, nrows, pv, j, it.cpb + (int64_t)blockIdx.x * (KMAX + 1));
+  } else {
+    const double tot = block_sum(val * val, red);
+    if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
+  }
+}
+
+// step 4: alpha_j = ||p||, u_j = p / alpha_j, B[j,j] = alpha_j
+__global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict__ items, int s) {
+  const ShortItem it = items[blockIdx.y];
+  LzState* st = it.st;
+  const int j = st->j0 + s;
+  if (j < 0 || lz_skip(st, j) || (int)blockIdx.x >= it.nblk) return;
+  __shared__ double alpha_s;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int b = 0; b < it.nblk; ++b) a += it.npart[b];
+    alpha_s = sqrt(a);
+  }
+  __syncthreads();
+  const double alpha = alpha_s;
+  const bool ok = alpha > 1e-200;
+  const int64_t row = (int64_t)blockIdx.x * SHORT_RB + threadIdx.x;
+  if (row < it.Ls) it.U[row + it.ldu * j] = ok ? it.p[row] / alpha : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    it.B[j + (int64_t)it.ldb * j] = ok ? alpha : 0.0;
+    if (ok) { if (alpha > st->anorm) st->anorm = alpha; }
+    else { st->k = j + 1; st->beta_k = 0.0; st->breakdown = 1; }
+  }
+}
+
+// ------------------------------------------------------------ long side
+__device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i) {
+  // SplitMix64 output function (Steele, Lea, Flood 2014) -> [-1, 1)
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// q = sum(partials) - alpha_j v_j ; partial squared norms
+template <typename T>
+__global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ items, int s) {
+  const LongItem<T> it = items[blockIdx.y];
+  const int j = it.st->j0 + s;
+  if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
+  __shared__ double red[32];
+  const double alpha = it.B[j + (int64_t)it.ldb * j];
+  const T* vj = it.V + it.ldv * j;
+  const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
+    const int64_t row = r0 + t;
+    if (row >= it.Kl) break;
+    T v = T(0);
+    for (int q = 0; q < it.n_part; ++q) v += it.parts[q * it.part_ld + row];
+    v = v - (T)alpha * vj[row];
+    it.q[row] = v;
+    acc += (double)v * (double)v;
+  }
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict__ items) {
+  const LongItem<T> it = items[blockIdx.y];
+  if (!it.st->active || (int)blockIdx.x >= it.nblk) return;
+  __shared__ double red[32];
+  const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
+    const int64_t row = r0 + t;
+    if (row >= it.Kl) break;
+    const T v = (T)hash_uniform(it.seed, (uint64_t)row);
+    it.q[row] = v;
+    acc += (double)v * (double)v;
+  }
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
+}
+
+// beta_j = ||q||, v_{j+1} = q / beta_j, B[j, j+1] = beta_j (or beta_k at the end)
+template <typename T>
+__global__ void __launch_bounds__(256) k_long2(const LongItem<T>* __restrict__ items, int s) {
+  const LongItem<T> it = items[blockIdx.y];
+  LzState* st = it.st;
+  const int j = st->j0 + s;
+  if (lz_skip(st, j) || (int)blockIdx.x >= it.nblk) return;
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < it.nblk; b += blockDim.x) a += it.npart[b];
+  const double beta = sqrt(block_sum(a, red));
+  const bool ok = beta > 1e-200;
+  const T inv = ok ? (T)(1.0 / beta) : T(0);
+  T* dst = it.V + it.ldv * (j + 1);
+  const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
+  for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
+    const int64_t row = r0 + t;
+    if (row >= it.Kl) break;
+    dst[row] = it.q[row] * inv;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && j >= 0) {
+    if (ok) {
+      if (j + 1 < st->k) it.B[j + (int64_t)it.ldb * (j + 1)] = beta;
+      else st->beta_k = beta;
+      if (beta > st->anorm) st->anorm = beta;
+    } else {
+      st->k = j + 1;
+      st->beta_k = 0.0;
+      st->breakdown = 1;
+    }
+  }
+}
+
+// ------------------------------------------------------------ small SVD
+// One-sided Jacobi on the columns of B (k x k): B Qm = W with orthogonal
+// columns; sigma_i = ||W_i||, P_i = W_i / sigma_i.  Round-robin pair order,
+// one warp per pair.  Then residuals beta_k |P[k-1, i]| decide convergence.
+__global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items) {
+  const SvdItem it = items[blockIdx.x];
+  LzState* st = it.st;
+  if (!st->active) return;
+  const int k = st->k, ld = it.ldb;
+  extern __shared__ __align__(16) double sm[];
+  double* W = sm;              // column c at W + c*k
+  double* Qm = W + k * k;
+  __shared__ int rotated;
+  __shared__ double nrm[KMAX];
+  __shared__ int order[KMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    W[e] = it.B[i + (int64_t)ld * c];
+    Qm[e] = (i == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int n2 = k + (k & 1);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int rd = 0; rd < n2 - 1; ++rd) {
+      for (int t = warp; t < n2 / 2; t += nw) {
+        const int sa = t, sb = n2 - 1 - t;
+        const int a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
+        const int b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
+        if (a >= k || b >= k) continue;
+        double* wa = W + a * k;
+        double* wb = W + b * k;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < k; i += 32) {
+          const double x = wa[i], y = wb[i];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+          double* qa = Qm + a * k;
+          double* qb = Qm + b * k;
+          for (int i = lane; i < k; i += 32) {
+            const double x = wa[i], y = wb[i];
+            wa[i] = cs * x - sn * y;
+            wb[i] = sn * x + cs * y;
+            const double u = qa[i], v = qb[i];
+            qa[i] = cs * u - sn * v;
+            qb[i] = sn * u + cs * v;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  for (int c = warp; c < k; c += nw) {
+    double a = 0.0;
+    for (int i = lane; i < k; i += 32) a += W[c * k + i] * W[c * k + i];
+    a = warp_sum(a);
+    if (lane == 0) nrm[c] = sqrt(a);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < k; ++c) order[c] = c;
+    for (int a = 0; a < k; ++a) {          // selection sort, descending, stable
+      int best = a;
+      for (int b = a + 1; b < k; ++b)
+        if (nrm[order[b]] > nrm[order[best]]) best = b;
+      const int t = order[a]; order[a] = order[best]; order[best] = t;
+    }
+  }
+  __syncthreads();
+  const int kd = ld;  // allocated dimension: clear what lies beyond k
+  for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
+    const int c = e / kd, i = e - c * kd;
+    double pv = 0.0, qv = 0.0;
+    if (c < k && i < k) {
+      const int o = order[c];
+      const double sg = nrm[o];
+      pv = sg > 0.0 ? W[o * k + i] / sg : 0.0;
+      qv = Qm[o * k + i];
+    }
+    it.P[i + (int64_t)kd * c] = pv;
+    it.Q[i + (int64_t)kd * c] = qv;
+  }
+  for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int r = min(st->r, k);
+    const double s1 = nrm[order[0]];
+    double mres = 0.0;
+    int nconv = 0;
+    bool conv = true;
+    for (int i = 0; i < r; ++i) {
+      const int o = order[i];
+      const double sg = nrm[o];
+      const double pk = sg > 0.0 ? W[o * k + (k - 1)] / sg : 0.0;
+      const double res = fabs(st->beta_k * pk);
+      const double rel = s1 > 0.0 ? res / s1 : 0.0;
+      if (rel > mres) mres = rel;
+      if (rel <= st->tol) { if (nconv == i) ++nconv; }
+      else conv = false;
+    }
+    if (st->full) { conv = true; nconv = r; }
+    st->sigma1 = s1;
+    st->maxres = mres;
+    st->nconv = nconv;
+    st->converged = conv ? 1 : 0;
+    st->restarts += 1;
+    if (conv || st->breakdown || st->restarts > st->max_restarts) st->active = 0;
+  }
+}
+
+// B <- [diag(sigma_1..kk) | rho] with rho_i = beta_k P[k-1, i]; j0 <- kk
+__global__ void k_restart(const SvdItem* __restrict__ items) {
+  const SvdItem it = items[blockIdx.x];
+  LzState* st = it.st;
+  if (!st->active) return;
+  const int k = st->k, kk = st->kk, ld = it.ldb;
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    const int c = e / ld, i = e - c * ld;
+    double v = 0.0;
+    if (c == i && c < kk) v = it.sig[c];
+    else if (c == kk && i < kk) v = st->beta_k * it.P[(k - 1) + (int64_t)ld * i];
+    it.B[e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st->j0 = kk;
+}
+
+// ------------------------------------------------------------ Ritz vectors
+// In place, by row blocks: basis[:, 0:kk] <- basis[:, 0:k] C[0:k, 0:kk];
+// on a restart the long basis also moves column k to column kk.
+template <typename T, bool SHORT>
+__global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, int final_pass, int rows_per) {
+  const RitzItem<T> it = items[blockIdx.y];
+  const LzState* st = it.st;
+  if (!final_pass && !st->active) return;
+  typedef typename std::conditional<SHORT, double, T>::type E;
+  const int k = st->k;
+  const int kk = final_pass ? min(st->r, k) : st->kk;
+  const bool move = !SHORT && !final_pass;
+  E* basis = SHORT ? (E*)it.U : (E*)it.V;
+  const int64_t ldb = SHORT ? it.ldu : it.ldv;
+  const int64_t nrow = SHORT ? it.Ls : it.Kl;
+  const double* C = SHORT ? it.P : it.Q;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+  if (r0 >= nrow) return;
+  const int nr = (int)imin64(rows_per, nrow - r0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  E* blk = reinterpret_cast<E*>(smraw);               // rows_per x (k+1), column-major
+  E* cf = blk + (int64_t)rows_per * (k + 1);           // k x kk
+  const int ncol = move ? k + 1 : k;
+  for (int e = threadIdx.x; e < ncol * rows_per; e += blockDim.x) {
+    const int c = e / rows_per, t = e - c * rows_per;
+    if (t < nr) blk[e] = basis[r0 + t + ldb * c];
+  }
+  for (int e = threadIdx.x; e < k * kk; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    cf[e] = (E)C[i + (int64_t)it.ldc * c];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * kk; e += blockDim.x) {
+    const int c = e / nr, t = e - c * nr;
+    E acc = E(0);
+    for (int i = 0; i < k; ++i) acc += blk[t + (int64_t)rows_per * i] * cf[i + k * c];
+    basis[r0 + t + ldb * c] = acc;
+  }
+  if (move)
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) basis[r0 + t + ldb * kk] = blk[t + (int64_t)rows_per * k];
+}
+
+// ------------------------------------------------------------ outputs
+// Sign convention: each pair (U_i, V_i) is flipped so that the entry of U_i
+// (the window-side vector) with the largest magnitude is positive (first such
+// entry on ties).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sign(const FinalItem<T>* __restrict__ items) {
+  const FinalItem<T> it = items[blockIdx.y];
+  const int i = blockIdx.x;
+  const int r = it.r;
+  if (i >= r) return;
+  const int keff = min(it.st->k, r);
+  __shared__ double bv[256];
+  __shared__ int64_t bi[256];
+  double best = -1.0;
+  int64_t bidx = 0;
+  double bval = 0.0;
+  const int64_t n = it.swapped ? it.Kl : it.Ls;
+  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+    const double v = it.swapped ? (double)it.V[t + it.ldv * i] : it.U[t + it.ldu * i];
+    if (fabs(v) > best) { best = fabs(v); bidx = t; bval = v; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __shared__ double sval[256];
+  sval[threadIdx.x] = bval;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const int u = threadIdx.x + o;
+      if (bv[u] > bv[threadIdx.x] || (bv[u] == bv[threadIdx.x] && bi[u] < bi[threadIdx.x])) {
+        bv[threadIdx.x] = bv[u]; bi[threadIdx.x] = bi[u]; sval[threadIdx.x] = sval[u];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    it.sgn[i] = (sval[0] < 0.0) ? -1.0 : 1.0;
+    it.sigma_out[i] = (i < keff) ? it.sig[i] : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_final_copy(const FinalItem<T>* __restrict__ items) {
+  const FinalItem<T> it = items[blockIdx.z];
+  const int i = blockIdx.y;
+  if (i >= it.r) return;
+  const bool zero = i >= it.st->k;
+  const double sg = it.sgn[i];
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // window side (L) and origin side (K)
+  const int64_t L = it.swapped ? it.Kl : it.Ls;
+  const int64_t K = it.swapped ? it.Ls : it.Kl;
+  for (int64_t t = t0; t < L; t += stride) {
+    double v = it.swapped ? (double)it.V[t + it.ldv * i] : it.U[t + it.ldu * i];
+    it.Uo[t + L * i] = zero ? T(0) : (T)(sg * v);
+  }
+  for (int64_t t = t0; t < K; t += stride) {
+    double v = it.swapped ? it.U[t + it.ldu * i] : (double)it.V[t + it.ldv * i];
+    it.Vo[t + K * i] = zero ? T(0) : (T)(sg * v);
+  }
+}
+
+// ------------------------------------------------------------ launchers
+void launch_short_steps(const ShortItem* items, int n, int max_blk, int s, cudaStream_t st) {
+  if (n <= 0) return;
+  dim3 g(max_blk, n);
+  k_short1<<<g, SHORT_RB, 0, st>>>(items, s);
+  k_short23<2><<<g, SHORT_RB, 0, st>>>(items, s);
+  k_short23<3><<<g, SHORT_RB, 0, st>>>(items, s);
+  k_short4<<<g, SHORT_RB, 0, st>>>(items, s);
+}
+
+template <typename T>
+void launch_long_step(const LongItem<T>* items, int n, int max_blk, int s, cudaStream_t st) {
+  if (n <= 0) return;
+  dim3 g(max_blk, n);
+  k_long1<T><<<g, 256, 0, st>>>(items, s);
+  k_long2<T><<<g, 256, 0, st>>>(items, s);
+}
+
+template <typename T>
+void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t st) {
+  if (n <= 0) return;
+  dim3 g(max_blk, n);
+  k_long_init<T><<<g, 256, 0, st>>>(items);
+  k_long2<T><<<g, 256, 0, st>>>(items, -1);
+}
+
+void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
+  if (n <= 0) return;
+  const size_t sm = 2 * (size_t)kmax * kmax * sizeof(double);
+  set_max_smem((const void*)k_bsvd);
+  k_bsvd<<<n, 256, sm, st>>>(items);
+}
+
+void launch_restart(const SvdItem* items, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_restart<<<n, 256, 0, st>>>(items);
+}
+
+template <typename T>
+void launch_ritz(const RitzItem<T>* items, int n, int kmax, int64_t max_short, int64_t max_long, int final_pass,
+                 cudaStream_t st) {
+  if (n <= 0) return;
+  const int rs = 64, rl = 128;
+  size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)kmax * kmax * sizeof(double);
+  size_t sml = (size_t)rl * (kmax + 1) * sizeof(T) + (size_t)kmax * kmax * sizeof(T);
+  set_max_smem((const void*)k_ritz<T, true>);
+  set_max_smem((const void*)k_ritz<T, false>);
+  k_ritz<T, true><<<dim3((unsigned)((max_short + rs - 1) / rs), n), 256, sms, st>>>(items, final_pass, rs);
+  k_ritz<T, false><<<dim3((unsigned)((max_long + rl - 1) / rl), n), 256, sml, st>>>(items, final_pass, rl);
+}
+
+template <typename T>
+void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st) {
+  if (n <= 0) return;
+  k_sign<T><<<dim3(max_r, n), 256, 0, st>>>(items);
+  unsigned gx = (unsigned)std::min<int64_t>((max_rows + 255) / 256, 1024);
+  k_final_copy<T><<<dim3(gx, max_r, n), 256, 0, st>>>(items);
+}
+
+#define INST(T)                                                                                        \
+  template void launch_long_step<T>(const LongItem<T>*, int, int, int, cudaStream_t);                  \
+  template void launch_long_init<T>(const LongItem<T>*, int, int, cudaStream_t);                       \
+  template void launch_ritz<T>(const RitzItem<T>*, int, int, int64_t, int64_t, int, cudaStream_t);     \
+  template void launch_finalize<T>(const FinalItem<T>*, int, int, int64_t, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace ssa

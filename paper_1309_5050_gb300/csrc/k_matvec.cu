@@ -1,0 +1,319 @@
+// Trajectory-matrix products by FFT (Sec. 6.1.2 Alg. hmul_u; Sec. 6.2.2, the
+// quasi-Hankel product) and the data spectrum they share.
+//
+//   u = X v :  scatter v onto the grid at the origins K, transform, multiply by
+//              the data spectrum times the conjugate, transform back, gather the
+//              window positions L.  (X^T u swaps the roles of L and K.)
+//
+// Series (My == 1) run fused in one CTA per (problem, channel): load with
+// scatter, length-H complex FFT of the packed real signal, half-spectrum
+// product, inverse, gather -- all in shared memory.  Images run as three
+// passes: x-pass (packed real FFT down every grid column, scatter fused),
+// y-pass (complex FFT across columns, spectrum product, inverse, pruned to the
+// output's columns), x-pass inverse (gather fused).
+#include "fft_block.cuh"
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace ssa {
+
+// ---------------------------------------------------------------- helpers
+// Fill rb[0..Mx) with grid column y of a compact vector (zeros elsewhere).
+template <typename T, typename TI>
+__device__ void load_col(T* rb, int Mx, const TI* __restrict__ in, const MapDev& m, int y,
+                         int32_t* s_pre, int32_t* s_wt) {
+  if (m.dense || y >= m.by) {
+    const bool ok = (y < m.by);
+    const TI* src = in + (int64_t)y * m.bx;
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x)
+      rb[x] = (ok && x < m.bx) ? (T)src[x] : T(0);
+  } else {
+    const uint32_t* wb = m.bits + (int64_t)y * m.words;
+    block_popc_scan(wb, m.words, s_pre, s_wt);
+    const TI* src = in + m.colbase[y];
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
+      T v = T(0);
+      if (x < m.bx) {
+        const uint32_t w = wb[x >> 5];
+        const int b = x & 31;
+        if ((w >> b) & 1u) v = (T)src[s_pre[x >> 5] + __popc(w & ((1u << b) - 1u))];
+      }
+      rb[x] = v;
+    }
+  }
+}
+
+// Write the map's positions of grid column y from rb into a compact vector.
+template <typename T, typename TO>
+__device__ void store_col(const T* rb, TO* __restrict__ out, const MapDev& m, int y,
+                          int32_t* s_pre, int32_t* s_wt) {
+  if (y >= m.by) return;
+  if (m.dense) {
+    TO* dst = out + (int64_t)y * m.bx;
+    for (int x = threadIdx.x; x < m.bx; x += blockDim.x) dst[x] = (TO)rb[x];
+  } else {
+    const uint32_t* wb = m.bits + (int64_t)y * m.words;
+    block_popc_scan(wb, m.words, s_pre, s_wt);
+    TO* dst = out + m.colbase[y];
+    for (int x = threadIdx.x; x < m.bx; x += blockDim.x) {
+      const uint32_t w = wb[x >> 5];
+      const int b = x & 31;
+      if ((w >> b) & 1u) dst[s_pre[x >> 5] + __popc(w & ((1u << b) - 1u))] = (TO)rb[x];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool item_skip(const LzState* st, int s) {
+  return st && (!st->active || st->j0 + s >= st->k || st->j0 + s < 0);
+}
+
+// x-pass shared layout: two (H+1) complex buffers, then scan scratch.
+template <typename T>
+struct XSmem {
+  Cx<T>* A; Cx<T>* B; int32_t* pre; int32_t* wt;
+  __device__ XSmem(unsigned char* p, int H) {
+    A = reinterpret_cast<Cx<T>*>(p);
+    B = A + (H + 1);
+    pre = reinterpret_cast<int32_t*>(B + (H + 1));
+    wt = pre + ((2 * H) / 32 + 1);
+  }
+};
+
+// Forward half of an x-pass: packed FFT of rb (viewed in A) and untwist into
+// the other buffer.  Returns the half spectrum (H+1 values).
+template <typename T>
+__device__ Cx<T>* xpass_forward(XSmem<T>& sm, int log2H, const Cx<T>* tw) {
+  const int H = 1 << log2H;
+  __syncthreads();
+  Cx<T>* Z = block_fft<T, false>(sm.A, sm.B, log2H, 1, tw);
+  Cx<T>* G = (Z == sm.A) ? sm.B : sm.A;
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd(Z, k, log2H, tw);
+  __syncthreads();
+  return G;
+}
+
+// Inverse half of an x-pass: P (H+1 values, in one buffer) -> real signal
+// (2H values) viewed in the returned buffer.
+template <typename T>
+__device__ T* xpass_inverse(XSmem<T>& sm, Cx<T>* P, int log2H, const Cx<T>* tw) {
+  const int H = 1 << log2H;
+  Cx<T>* Q = (P == sm.A) ? sm.B : sm.A;
+  for (int k = threadIdx.x; k < H; k += blockDim.x) Q[k] = twist_inv(P, k, log2H, tw);
+  __syncthreads();
+  Cx<T>* R = block_fft<T, true>(Q, P, log2H, 1, tw);
+  return reinterpret_cast<T*>(R);
+}
+
+// ---------------------------------------------------------------- kernels
+template <typename T>
+__global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ items, int s,
+                                              const Cx<T>* __restrict__ tw) {
+  const MvItem<T> it = items[blockIdx.x];
+  if (item_skip<T>(it.st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H;
+  XSmem<T> sm(smem, H);
+  const int64_t ioff = vec_elem_off(it.in, s);
+  if (it.in_type == 1)
+    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt);
+  else
+    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt);
+  Cx<T>* G = xpass_forward(sm, log2H, tw);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = it.xh[k] * conj(G[k]);
+  __syncthreads();
+  T* r = xpass_inverse(sm, G, log2H, tw);
+  __syncthreads();
+  store_col<T, T>(r, (T*)it.out.base + vec_elem_off(it.out, s), it.mout, 0, sm.pre, sm.wt);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_mv_xfwd(const MvItem<T>* __restrict__ items, int s,
+                                                 const Cx<T>* __restrict__ tw) {
+  const MvItem<T> it = items[blockIdx.y];
+  const int y = blockIdx.x;
+  if (y >= it.y_in_hi || item_skip<T>(it.st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H;
+  XSmem<T> sm(smem, H);
+  const int64_t ioff = vec_elem_off(it.in, s);
+  if (it.in_type == 1)
+    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, y, sm.pre, sm.wt);
+  else
+    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, y, sm.pre, sm.wt);
+  Cx<T>* G = xpass_forward(sm, log2H, tw);
+  Cx<T>* dst = it.g1 + (int64_t)y * (H + 1);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) dst[k] = G[k];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_mv_xinv(const MvItem<T>* __restrict__ items, int s,
+                                                 const Cx<T>* __restrict__ tw) {
+  const MvItem<T> it = items[blockIdx.y];
+  const int y = blockIdx.x;
+  if (y >= it.y_out_hi || item_skip<T>(it.st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H;
+  XSmem<T> sm(smem, H);
+  const Cx<T>* src = it.g2 + (int64_t)y * (H + 1);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.A[k] = src[k];
+  __syncthreads();
+  T* r = xpass_inverse(sm, sm.A, log2H, tw);
+  __syncthreads();
+  store_col<T, T>(r, (T*)it.out.base + vec_elem_off(it.out, s), it.mout, y, sm.pre, sm.wt);
+}
+
+// y-pass over a tile of TK consecutive x-frequencies (all My rows).
+template <typename T>
+__global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ items, int mode, int s,
+                                               int buf_elems, const Cx<T>* __restrict__ tw) {
+  const YItem<T> it = items[blockIdx.y];
+  if (item_skip<T>(it.st, s)) return;
+  const int log2My = it.log2My, My = 1 << log2My;
+  const int H = 1 << (it.log2Mx - 1), ld = H + 1;
+  int TK = buf_elems >> log2My;
+  if (TK > 16) TK = 16;
+  const int k0 = blockIdx.x * TK;
+  if (k0 > H) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
+  Cx<T>* B = A + (TK << log2My);
+  const int n = TK << log2My;
+  const Cx<T> zero = cx(T(0), T(0));
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int m = t / TK, b = t - m * TK, k = k0 + b;
+    Cx<T> v = zero;
+    if (m < it.in_hi && k <= H) v = it.src[k + (int64_t)ld * m];
+    A[(b << log2My) + m] = v;
+  }
+  __syncthreads();
+  Cx<T>* F = A;
+  if (mode != Y_INV) F = block_fft<T, false>(A, B, log2My, TK, tw);
+  Cx<T>* O = (F == A) ? B : A;
+  if (mode == Y_FWD) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int m = t / TK, b = t - m * TK, k = k0 + b;
+      if (m < it.out_hi && k <= H) it.dst[k + (int64_t)ld * m] = F[(b << log2My) + m];
+    }
+    return;
+  }
+  if (mode == Y_CONVACC) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int m = t / TK, b = t - m * TK, k = k0 + b;
+      if (k <= H) {
+        const int64_t g = k + (int64_t)ld * m;
+        it.dst[g] = it.dst[g] + it.scale * (it.mul[g] * F[(b << log2My) + m]);
+      }
+    }
+    return;
+  }
+  if (mode == Y_MULCONJ_INV) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int m = t / TK, b = t - m * TK, k = k0 + b;
+      const int i = (b << log2My) + m;
+      F[i] = (k <= H) ? it.mul[k + (int64_t)ld * m] * conj(F[i]) : zero;
+    }
+    __syncthreads();
+  }
+  Cx<T>* R = block_fft<T, true>(F, O, log2My, TK, tw);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int m = t / TK, b = t - m * TK, k = k0 + b;
+    if (m < it.out_hi && k <= H) it.dst[k + (int64_t)ld * m] = R[(b << log2My) + m];
+  }
+}
+
+// Data to half spectrum, x-pass: masked / missing samples enter as zero
+// (they never reach the trajectory matrix); scaled by 1/(Mx My).
+template <typename T>
+__global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ items,
+                                                const Cx<T>* __restrict__ tw) {
+  const SpecItem<T> it = items[blockIdx.y];
+  const int y = blockIdx.x;
+  if (y >= it.ny) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H, Mx = 2 * H;
+  XSmem<T> sm(smem, H);
+  T* rb = reinterpret_cast<T*>(sm.A);
+  for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
+    T v = T(0);
+    if (x < it.nx) {
+      bool ok = true;
+      if (it.obs) ok = (it.obs[(int64_t)y * it.obs_words + (x >> 5)] >> (x & 31)) & 1u;
+      if (ok) {
+        const int64_t g = x + (int64_t)it.nx * y;
+        double d = it.data_double ? ((const double*)it.data)[g] : (double)((const float*)it.data)[g];
+        v = (T)d * it.scale;
+      }
+    }
+    rb[x] = v;
+  }
+  Cx<T>* G = xpass_forward(sm, log2H, tw);
+  Cx<T>* dst = ((it.log2My == 0) ? it.xh : it.g1) + (int64_t)y * (H + 1);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) dst[k] = G[k];
+}
+
+// ---------------------------------------------------------------- launchers
+static inline size_t xsmem_bytes(int log2Mx, size_t csz) {
+  const size_t H = size_t(1) << (log2Mx - 1);
+  return 2 * (H + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
+}
+
+template <typename T>
+int ypass_buf_elems() { return (64 * 1024) / (int)sizeof(Cx<T>); }
+
+template <typename T>
+void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st) {
+  if (n <= 0) return;
+  size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  set_max_smem((const void*)k_mv1d<T>);
+  k_mv1d<T><<<n, 512, sm, st>>>(items, s, tw);
+}
+
+template <typename T>
+void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
+                 int max_y_in, int max_y_out, int s, const Cx<T>* tw, cudaStream_t st) {
+  if (n <= 0) return;
+  size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  set_max_smem((const void*)k_mv_xfwd<T>);
+  set_max_smem((const void*)k_mv_xinv<T>);
+  k_mv_xfwd<T><<<dim3(max_y_in, n), 512, sm, st>>>(items, s, tw);
+  launch_ypass<T>(yitems, n, Y_MULCONJ_INV, max_log2Mx, max_log2My, s, tw, st);
+  k_mv_xinv<T><<<dim3(max_y_out, n), 512, sm, st>>>(items, s, tw);
+}
+
+template <typename T>
+void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int max_log2My, int s,
+                  const Cx<T>* tw, cudaStream_t st) {
+  if (n <= 0) return;
+  const int buf = ypass_buf_elems<T>();
+  int TK = buf >> max_log2My;            // smallest tile width among the items
+  if (TK > 16) TK = 16;
+  if (TK < 1) TK = 1;
+  const int H = 1 << (max_log2Mx - 1);
+  const int tiles = (H + 1 + TK - 1) / TK;
+  const size_t sm = 2 * (size_t)buf * sizeof(Cx<T>);
+  set_max_smem((const void*)k_ypass<T>);
+  k_ypass<T><<<dim3(tiles, n), 512, sm, st>>>(items, mode, s, buf, tw);
+}
+
+template <typename T>
+void launch_spec(const SpecItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
+                 int max_ny, const Cx<T>* tw, cudaStream_t st) {
+  if (n <= 0) return;
+  size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  set_max_smem((const void*)k_spec_x<T>);
+  k_spec_x<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw);
+  if (max_log2My > 0) launch_ypass<T>(yitems, n, Y_FWD, max_log2Mx, max_log2My, -1, tw, st);
+}
+
+#define INST(T)                                                                                       \
+  template void launch_mv1d<T>(const MvItem<T>*, int, int, int, const Cx<T>*, cudaStream_t);          \
+  template void launch_mv2d<T>(const MvItem<T>*, const YItem<T>*, int, int, int, int, int, int,        \
+                               const Cx<T>*, cudaStream_t);                                           \
+  template void launch_ypass<T>(const YItem<T>*, int, int, int, int, int, const Cx<T>*, cudaStream_t); \
+  template void launch_spec<T>(const SpecItem<T>*, const YItem<T>*, int, int, int, int, const Cx<T>*,  \
+                               cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace ssa

@@ -1,0 +1,191 @@
+// Grouped reconstruction: rank-one (quasi-)hankelization by FFT (Sec. 6.1.3,
+// Alg. hankelization; Sec. 6.2.3, Alg. qhankelization and Alg. diagsums).
+//
+// For a group I the reconstruction is  sum_{i in I} sigma_i diagsums(U_i, V_i)
+// divided by the weights w.  diagsums(U, V) is the linear convolution of U
+// scattered on the window set with V scattered on the origin set, i.e.
+// F^-1(F(U') . F(V')) (Lemma hbh_tbt_elmat).  Linearity lets the group be
+// summed in frequency space, so each (group, channel) needs one inverse
+// transform; F(U'_i) is shared by all channels and groups.
+#include "fft_block.cuh"
+#include "kernels.cuh"
+#include "launch.h"
+#include <algorithm>
+#include "recon.h"
+
+namespace ssa {
+
+// (same scatter as the matvec x-pass; duplicated here to keep the translation
+// units independent)
+template <typename T, typename TI>
+__device__ void rec_load_col(T* rb, int Mx, const TI* __restrict__ in, const MapDev& m, int y,
+                             int32_t* s_pre, int32_t* s_wt) {
+  if (m.dense || y >= m.by) {
+    const bool ok = (y < m.by);
+    const TI* src = in + (int64_t)y * m.bx;
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x) rb[x] = (ok && x < m.bx) ? (T)src[x] : T(0);
+  } else {
+    const uint32_t* wb = m.bits + (int64_t)y * m.words;
+    block_popc_scan(wb, m.words, s_pre, s_wt);
+    const TI* src = in + m.colbase[y];
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
+      T v = T(0);
+      if (x < m.bx) {
+        const uint32_t w = wb[x >> 5];
+        const int b = x & 31;
+        if ((w >> b) & 1u) v = (T)src[s_pre[x >> 5] + __popc(w & ((1u << b) - 1u))];
+      }
+      rb[x] = v;
+    }
+  }
+}
+
+template <typename T>
+struct RSmem {
+  Cx<T>* A; Cx<T>* B; Cx<T>* C; int32_t* pre; int32_t* wt;
+  __device__ RSmem(unsigned char* p, int H) {
+    A = reinterpret_cast<Cx<T>*>(p);
+    B = A + (H + 1);
+    C = B + (H + 1);
+    pre = reinterpret_cast<int32_t*>(C + (H + 1));
+    wt = pre + ((2 * H) / 32 + 1);
+  }
+};
+
+template <typename T>
+__device__ Cx<T>* rec_forward(Cx<T>* A, Cx<T>* B, int log2H, const Cx<T>* tw) {
+  const int H = 1 << log2H;
+  __syncthreads();
+  Cx<T>* Z = block_fft<T, false>(A, B, log2H, 1, tw);
+  Cx<T>* G = (Z == A) ? B : A;
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd(Z, k, log2H, tw);
+  __syncthreads();
+  return G;
+}
+
+// Half spectrum of one column of a compact vector (U_i or V_i): x-pass.
+template <typename T>
+__global__ void __launch_bounds__(512) k_rec_col_fft(const RecColItem<T>* __restrict__ items,
+                                                     const Cx<T>* __restrict__ tw) {
+  const RecColItem<T> it = items[blockIdx.y];
+  const int y = blockIdx.x;
+  if (y >= it.ncols) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H;
+  RSmem<T> sm(smem, H);
+  rec_load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, it.vec, it.map, y, sm.pre, sm.wt);
+  Cx<T>* G = rec_forward(sm.A, sm.B, log2H, tw);
+  Cx<T>* dst = it.dst + (int64_t)y * (H + 1);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) dst[k] = G[k];
+}
+
+// Series: one CTA per (group, channel).  acc = sum_i (sigma_i / Mx) F(U'_i) F(V'_i)
+// then inverse, divide by w, NaN where w = 0.
+template <typename T>
+__global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T>* __restrict__ items, const Cx<T>* __restrict__ tw) {
+  const Rec1Item<T> it = items[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H;
+  RSmem<T> sm(smem, H);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = cx(T(0), T(0));
+  for (int c = 0; c < it.ncomp; ++c) {
+    const int i = it.comps[c];
+    rec_load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, it.V + it.ldv * i, it.map, 0, sm.pre, sm.wt);
+    Cx<T>* G = rec_forward(sm.A, sm.B, log2H, tw);
+    const Cx<T>* gu = it.gu + it.ldgu * i;
+    const T sc = (T)(it.sigma[i] * it.inv_norm);
+    for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = sm.C[k] + sc * (gu[k] * G[k]);
+    __syncthreads();
+  }
+  // inverse of the accumulated half spectrum (C), into A/C ping-pong
+  for (int k = threadIdx.x; k < H; k += blockDim.x) sm.A[k] = twist_inv(sm.C, k, log2H, tw);
+  __syncthreads();
+  Cx<T>* R = block_fft<T, true>(sm.A, sm.B, log2H, 1, tw);
+  const T* r = reinterpret_cast<const T*>(R);
+  for (int n = threadIdx.x; n < it.n; n += blockDim.x) {
+    const int w = it.w[n];
+    it.out[n] = (w > 0) ? (double)r[n] / (double)w : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+// Images: inverse x-pass of the accumulated spectrum, divide by w.
+template <typename T>
+__global__ void __launch_bounds__(512) k_rec_xinv(const Rec2Item<T>* __restrict__ items, const Cx<T>* __restrict__ tw) {
+  const Rec2Item<T> it = items[blockIdx.y];
+  const int y = blockIdx.x;
+  if (y >= it.ny) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2Mx - 1, H = 1 << log2H;
+  RSmem<T> sm(smem, H);
+  const Cx<T>* src = it.g2 + (int64_t)y * (H + 1);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = src[k];
+  __syncthreads();
+  for (int k = threadIdx.x; k < H; k += blockDim.x) sm.A[k] = twist_inv(sm.C, k, log2H, tw);
+  __syncthreads();
+  Cx<T>* R = block_fft<T, true>(sm.A, sm.B, log2H, 1, tw);
+  const T* r = reinterpret_cast<const T*>(R);
+  for (int x = threadIdx.x; x < it.nx; x += blockDim.x) {
+    const int64_t g = x + (int64_t)it.nx * y;
+    const int w = it.w[g];
+    it.out[g] = (w > 0) ? (double)r[x] * it.inv_norm / (double)w : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+// residual = x - sum of the groups, on N' (NaN elsewhere), in FP64
+__global__ void k_residual(const void* data, int data_double, const int32_t* w, int64_t n, const double* groups,
+                           int64_t gstride, int ngroups, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (w[i] <= 0) { out[i] = __longlong_as_double(0x7ff8000000000000ll); continue; }
+    double v = data_double ? ((const double*)data)[i] : (double)((const float*)data)[i];
+    for (int g = 0; g < ngroups; ++g) v -= groups[g * gstride + i];
+    out[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+static inline size_t rsmem_bytes(int log2Mx, size_t csz) {
+  const size_t H = size_t(1) << (log2Mx - 1);
+  return 3 * (H + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
+}
+
+template <typename T>
+void launch_rec_col_fft(const RecColItem<T>* items, int n, int max_log2Mx, int max_cols, const Cx<T>* tw,
+                        cudaStream_t st) {
+  if (n <= 0) return;
+  size_t sm = rsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  set_max_smem((const void*)k_rec_col_fft<T>);
+  k_rec_col_fft<T><<<dim3(max_cols, n), 512, sm, st>>>(items, tw);
+}
+
+template <typename T>
+void launch_rec1d(const Rec1Item<T>* items, int n, int max_log2Mx, const Cx<T>* tw, cudaStream_t st) {
+  if (n <= 0) return;
+  size_t sm = rsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  set_max_smem((const void*)k_rec1d<T>);
+  k_rec1d<T><<<n, 512, sm, st>>>(items, tw);
+}
+
+template <typename T>
+void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny, const Cx<T>* tw,
+                     cudaStream_t st) {
+  if (n <= 0) return;
+  size_t sm = rsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  set_max_smem((const void*)k_rec_xinv<T>);
+  k_rec_xinv<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw);
+}
+
+void launch_residual(const void* data, int data_double, const int32_t* w, int64_t n, const double* groups,
+                     int64_t gstride, int ngroups, double* out, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (blocks < 1) blocks = 1;
+  k_residual<<<blocks, 256, 0, st>>>(data, data_double, w, n, groups, gstride, ngroups, out);
+}
+
+#define INST(T)                                                                                        \
+  template void launch_rec_col_fft<T>(const RecColItem<T>*, int, int, int, const Cx<T>*, cudaStream_t); \
+  template void launch_rec1d<T>(const Rec1Item<T>*, int, int, const Cx<T>*, cudaStream_t);              \
+  template void launch_rec_xinv<T>(const Rec2Item<T>*, int, int, int, const Cx<T>*, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace ssa

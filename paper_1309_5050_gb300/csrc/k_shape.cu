@@ -1,0 +1,169 @@
+// Shapes and weights (Sec. 5.1 and 6.2.3-6.2.4), computed exactly in integers.
+//
+//  * N  -- observed samples: inside the user mask and not NaN (Sec. 5.2);
+//  * K  -- window origins kappa with L (+) {kappa} inside N (eq. sh_Ks).  The
+//          paper finds K from one FFT product (Alg. find_ks) and keeps the
+//          entries equal to L; here each origin tests the window's bit rows
+//          against the observed bit rows directly, so no rounding is involved;
+//  * w  -- w_k = #{(i, j) : l_i (+) k_j = k}, the diagonal-averaging weights
+//          (Alg. qhankelization step 1); N' = {w > 0}.
+// All sets are stored as per-column bit masks (bit x of column y).
+#include "common.cuh"
+#include "shape.h"
+
+namespace ssa {
+
+// 32 bits of a column bit-row starting at (possibly negative) bit position p;
+// bits outside [0, 32*nw) read as zero.
+__device__ __forceinline__ uint32_t extract32(const uint32_t* col, int nw, int p) {
+  int w = p >> 5;                       // floor division for negative p
+  int b = p & 31;
+  uint32_t lo = (w >= 0 && w < nw) ? col[w] : 0u;
+  uint32_t hi = (w + 1 >= 0 && w + 1 < nw) ? col[w + 1] : 0u;
+  return __funnelshift_r(lo, hi, b);
+}
+
+// Observed bits; flags +-Inf inside the mask as bad input.
+__global__ void k_obs_bits(const void* data, int data_double, const uint8_t* mask, int nx, int ny,
+                           int words, uint32_t* bits, int* err) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = false;
+  if (x < nx) {
+    const int64_t g = x + (int64_t)nx * y;
+    double v = data_double ? ((const double*)data)[g] : (double)((const float*)data)[g];
+    bool m = mask ? (mask[g] != 0) : true;
+    ok = m && !isnan(v);
+    if (ok && isinf(v)) { atomicExch(err, 1); ok = false; }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, ok);
+  const int w = x >> 5;
+  if ((threadIdx.x & 31) == 0 && w < words) bits[(int64_t)y * words + w] = bal;
+}
+
+// Origins: thread per candidate (kx, ky); a warp covers 32 consecutive kx.
+// wrows: window bit rows, ey columns x wwords words (bit lx of column ly).
+__global__ void k_origins(const uint32_t* obs, int nwords_obs, const uint32_t* wrows, int wwords, int ey,
+                          int cx, int cy, int kwords, uint32_t* kbits) {
+  const int ky = blockIdx.y;
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  bool in = kx < cx && ky < cy;
+  if (in) {
+    for (int ly = 0; ly < ey && in; ++ly) {
+      const uint32_t* col = obs + (int64_t)(ky + ly) * nwords_obs;
+      const uint32_t* wr = wrows + (int64_t)ly * wwords;
+      for (int t = 0; t < wwords; ++t) {
+        const uint32_t wb = wr[t];
+        if (wb == 0u) continue;
+        const uint32_t o = extract32(col, nwords_obs, kx + 32 * t);
+        if (wb & ~o) { in = false; break; }
+      }
+    }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, in);
+  const int w = kx >> 5;
+  if ((threadIdx.x & 31) == 0 && w < kwords) kbits[(int64_t)ky * kwords + w] = bal;
+}
+
+__device__ __forceinline__ int block_sum_int(int v, int* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int t = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+__global__ void k_col_popc(const uint32_t* bits, int words, int ncols, int32_t* cnt) {
+  const int y = blockIdx.x;
+  __shared__ int red[32];
+  int c = 0;
+  for (int w = threadIdx.x; w < words; w += blockDim.x) c += __popc(bits[(int64_t)y * words + w]);
+  int tot = block_sum_int(c, red);
+  if (threadIdx.x == 0) cnt[y] = tot;
+}
+
+// Exclusive prefix sum of n counts into base[0..n] (base[n] = total), one CTA.
+__global__ void k_scan_counts(const int32_t* cnt, int n, int32_t* base) {
+  __shared__ int wt[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c = carry;
+      for (int w = 0; w < nw; ++w) { int t = wt[w]; wt[w] = c; c += t; }
+      carry = c;
+    }
+    __syncthreads();
+    if (i < n) base[i] = x - v + wt[warp];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) base[n] = carry;
+}
+
+// Weights: w(x, y) = sum over window columns ly of the number of origins in
+// column y-ly at x-lx for lx in the window column (reversed rows make it an
+// aligned AND + popcount).  rrows: reversed window rows, bit (ex-1-lx).
+__global__ void k_weights(const uint32_t* kbits, int kwords, int kcols, const uint32_t* rrows, int rwords,
+                          int ex, int ey, int nx, int ny, int32_t* w, uint32_t* nbits, int nwords) {
+  const int y = blockIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = 0;
+  if (x < nx) {
+    for (int ly = 0; ly < ey; ++ly) {
+      const int ky = y - ly;
+      if (ky < 0 || ky >= kcols) continue;
+      const uint32_t* col = kbits + (int64_t)ky * kwords;
+      const uint32_t* rr = rrows + (int64_t)ly * rwords;
+      const int p0 = x - ex + 1;
+      for (int t = 0; t < rwords; ++t) {
+        const uint32_t rb = rr[t];
+        if (rb == 0u) continue;
+        cnt += __popc(rb & extract32(col, kwords, p0 + 32 * t));
+      }
+    }
+    w[x + (int64_t)nx * y] = cnt;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
+  const int wd = x >> 5;
+  if ((threadIdx.x & 31) == 0 && wd < nwords) nbits[(int64_t)y * nwords + wd] = bal;
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_obs_bits(const void* data, int data_double, const uint8_t* mask, int nx, int ny, int words,
+                     uint32_t* bits, int* err, cudaStream_t st) {
+  dim3 g((nx + 255) / 256, ny);
+  k_obs_bits<<<g, 256, 0, st>>>(data, data_double, mask, nx, ny, words, bits, err);
+}
+
+void launch_origins(const uint32_t* obs, int nwords_obs, const uint32_t* wrows, int wwords, int ey, int cx,
+                    int cy, int kwords, uint32_t* kbits, cudaStream_t st) {
+  dim3 g((cx + 255) / 256, cy);
+  k_origins<<<g, 256, 0, st>>>(obs, nwords_obs, wrows, wwords, ey, cx, cy, kwords, kbits);
+}
+
+void launch_col_counts(const uint32_t* bits, int words, int ncols, int32_t* cnt, int32_t* colbase,
+                       cudaStream_t st) {
+  k_col_popc<<<ncols, 256, 0, st>>>(bits, words, ncols, cnt);
+  k_scan_counts<<<1, 1024, 0, st>>>(cnt, ncols, colbase);
+}
+
+void launch_weights(const uint32_t* kbits, int kwords, int kcols, const uint32_t* rrows, int rwords, int ex,
+                    int ey, int nx, int ny, int32_t* w, uint32_t* nbits, int nwords, cudaStream_t st) {
+  dim3 g((nx + 255) / 256, ny);
+  k_weights<<<g, 256, 0, st>>>(kbits, kwords, kcols, rrows, rwords, ex, ey, nx, ny, w, nbits, nwords);
+}
+
+}  // namespace ssa

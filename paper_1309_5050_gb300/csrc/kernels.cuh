@@ -1,0 +1,92 @@
+// Work-item descriptors shared by the kernels and the host orchestration.
+#pragma once
+#include "common.cuh"
+
+namespace ssa {
+
+// Per-problem Lanczos state kept in device memory.
+struct LzState {
+  int32_t j0;         // first step of the current cycle (0, or kk after a restart)
+  int32_t k;          // Krylov dimension
+  int32_t r;          // wanted rank
+  int32_t kk;         // vectors kept on restart
+  int32_t active;     // 1 while the problem still iterates
+  int32_t converged;  // set by the small-SVD kernel
+  int32_t nconv;      // leading triples that pass the residual test
+  int32_t breakdown;  // a Lanczos norm vanished
+  int32_t restarts;   // restart cycles done
+  int32_t max_restarts;
+  int32_t full;       // k equals min(L, K): one cycle spans the whole space
+  int32_t pad_;
+  double beta_k;      // coupling to the (k+1)-th long vector after k steps
+  double anorm;       // largest Lanczos coefficient seen (scale for breakdown)
+  double tol;         // residual tolerance relative to sigma_1
+  double sigma1;      // current leading Ritz value
+  double maxres;      // largest relative residual among the r wanted
+};
+
+// A compact vector, possibly column (j0 + s + jdelta) of a basis.
+struct VecRef {
+  void* base;
+  int64_t off;              // element offset (channel slice or partial row)
+  int64_t ld;               // column stride in elements
+  const LzState* st;        // non-null: column chosen from the Lanczos step
+  int32_t jdelta;
+  int32_t pad_;
+};
+
+__device__ __forceinline__ int64_t vec_elem_off(const VecRef& v, int s) {
+  int64_t o = v.off;
+  if (v.st) o += (int64_t)(v.st->j0 + s + v.jdelta) * v.ld;
+  return o;
+}
+
+// One matvec job: a channel of one problem in one direction.
+template <typename T>
+struct MvItem {
+  const Cx<T>* xh;          // channel spectrum, (H+1) x My, pre-scaled by 1/(Mx My)
+  VecRef in, out;           // compact input / output
+  MapDev min, mout;         // their grid positions
+  Cx<T>* g1;                // 2D scratch: after x-pass, (H+1) x My
+  Cx<T>* g2;                // 2D scratch: after y-pass
+  const LzState* st;        // non-null: skip when inactive or past k
+  int32_t log2Mx, log2My;
+  int32_t in_type;          // 0: T, 1: double
+  int32_t y_in_hi;          // grid columns [0, y_in_hi) may hold input
+  int32_t y_out_hi;         // grid columns [0, y_out_hi) hold output positions
+  int32_t pad_;
+};
+
+// Raw data to half spectrum (step 1 of the matvec algorithms, precomputed).
+template <typename T>
+struct SpecItem {
+  const void* data;         // Nx x Ny column-major (float or double)
+  const uint32_t* obs;      // observed bits, Ny columns x words (null = all)
+  int32_t obs_words;
+  int32_t data_double;
+  int32_t nx, ny;
+  int32_t log2Mx, log2My;
+  Cx<T>* g1;                // x-pass result (2D)
+  Cx<T>* xh;                // output spectrum (H+1) x My
+  T scale;                  // 1/(Mx My)
+};
+
+enum YMode : int { Y_FWD = 0, Y_MULCONJ_INV = 1, Y_CONVACC = 2, Y_INV = 3 };
+
+// One y-pass job (2D grids): a complex FFT along y of every x-frequency.
+//  Y_FWD         dst = F_y(src)                     (rows m < in_hi nonzero)
+//  Y_MULCONJ_INV dst = F_y^-1(mul . conj F_y(src))  (rows m < out_hi written)
+//  Y_CONVACC     dst += scale * mul . F_y(src)      (all rows)
+//  Y_INV         dst = F_y^-1(src)                  (rows m < out_hi written)
+template <typename T>
+struct YItem {
+  const Cx<T>* src;
+  Cx<T>* dst;
+  const Cx<T>* mul;
+  const LzState* st;
+  int32_t log2Mx, log2My;
+  int32_t in_hi, out_hi;
+  T scale;
+};
+
+}  // namespace ssa

@@ -1,0 +1,90 @@
+// Lanczos bidiagonalisation work items and launchers (internal).
+//
+// The operator A is the trajectory matrix or its transpose, oriented so that
+// its rows are the shorter side ("short", length Ls) and its columns the longer
+// ("long", length Kl).  Golub-Kahan-Lanczos steps build
+//   A V_k = U_k B_k,   A^T U_k = V_k B_k^T + beta_k v_{k+1} e_k^T,
+// with U (short side, FP64) fully re-orthogonalised by classical Gram-Schmidt
+// applied twice, and V (long side, storage type T) left as the three-term
+// recurrence makes it (one-sided re-orthogonalisation, as in Simon and Zha's
+// and Baglama and Reichel's bidiagonalisation methods).  After k steps the
+// small B is decomposed; if the r leading triples have not converged, the
+// method restarts from the kk best Ritz vectors (thick / augmented restart).
+#pragma once
+#include <cuda_runtime.h>
+#include "kernels.cuh"
+
+namespace ssa {
+
+constexpr int SHORT_RB = 256;   // rows per CTA on the short side
+constexpr int LONG_RB = 2048;   // rows per CTA on the long side
+constexpr int KMAX = 112;       // largest Krylov dimension (small SVD in shared memory)
+
+struct ShortItem {
+  LzState* st;
+  double* U; int64_t ldu;                 // Ls x (k+1), FP64
+  const void* parts; int64_t part_ld;     // n_part partial products (type of the matvec)
+  int32_t n_part; int32_t parts_double;
+  double* p;                              // work vector, Ls
+  double* B; int32_t ldb; int32_t nblk;   // B column-major, ldb = k
+  double* cpa; double* cpb;               // nblk x (KMAX+1) partial dots
+  double* npart;                          // nblk partial squared norms
+  int64_t Ls;
+};
+
+template <typename T>
+struct LongItem {
+  LzState* st;
+  T* V; int64_t ldv;                      // Kl x (k+1)
+  const T* parts; int64_t part_ld; int32_t n_part; int32_t nblk;
+  T* q;                                   // work vector, Kl
+  double* npart;                          // nblk partial squared norms
+  double* B; int32_t ldb; int32_t pad_;
+  int64_t Kl;
+  uint64_t seed;
+};
+
+struct SvdItem {
+  LzState* st;
+  double* B; int32_t ldb; int32_t pad_;
+  double* sig;                            // k singular values (descending)
+  double* P;                              // k x k left vectors of B (ld k)
+  double* Q;                              // k x k right vectors of B (ld k)
+};
+
+template <typename T>
+struct RitzItem {
+  LzState* st;
+  double* U; int64_t ldu; int64_t Ls;     // short basis
+  T* V; int64_t ldv; int64_t Kl;          // long basis
+  const double* P; const double* Q;       // from the small SVD
+  int32_t ldc; int32_t pad_;              // their leading dimension (allocated k)
+};
+
+template <typename T>
+struct FinalItem {
+  LzState* st;
+  const double* U; int64_t ldu; int64_t Ls;   // short basis (Ritz vectors in the first r columns)
+  const T* V; int64_t ldv; int64_t Kl;
+  const double* sig;
+  int32_t swapped;                            // 1: the short side is the K side
+  int32_t r;
+  T* Uo; T* Vo;                               // canonical outputs: L x r, K x r
+  double* sigma_out;                          // r
+  double* sgn;                                // r signs (scratch)
+};
+
+void launch_short_steps(const ShortItem* items, int n, int max_blk, int s, cudaStream_t st);
+template <typename T>
+void launch_long_step(const LongItem<T>* items, int n, int max_blk, int s, cudaStream_t st);
+template <typename T>
+void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t st);
+void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st);
+void launch_restart(const SvdItem* items, int n, cudaStream_t st);
+template <typename T>
+void launch_ritz(const RitzItem<T>* items, int n, int kmax, int64_t max_short, int64_t max_long, int final_pass,
+                 cudaStream_t st);
+template <typename T>
+void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st);
+
+}  // namespace ssa

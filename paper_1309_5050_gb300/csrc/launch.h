@@ -1,0 +1,29 @@
+// Host-side entry points of the kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include "kernels.cuh"
+
+namespace ssa {
+
+// Lift the dynamic shared-memory limit of a kernel to the device maximum
+// (once per kernel and device).
+void set_max_smem(const void* fn);
+int device_max_smem();
+
+// twiddle table (per device, built once)
+template <typename T> const Cx<T>* twiddles(int device);
+
+// matvec / spectrum
+template <typename T>
+void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
+                 int max_y_in, int max_y_out, int s, const Cx<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int max_log2My, int s,
+                  const Cx<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_spec(const SpecItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
+                 int max_ny, const Cx<T>* tw, cudaStream_t st);
+
+}  // namespace ssa

@@ -1,0 +1,52 @@
+// Reconstruction work items and launchers (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include "kernels.cuh"
+
+namespace ssa {
+
+// x-pass transform of columns of one compact vector (U_i or V_i slice).
+template <typename T>
+struct RecColItem {
+  const T* vec;          // compact vector
+  MapDev map;            // its grid positions
+  Cx<T>* dst;            // (H+1) x ncols half spectra
+  int32_t log2Mx, ncols; // grid columns to transform
+};
+
+// Series reconstruction of one (group, channel).
+template <typename T>
+struct Rec1Item {
+  const T* V; int64_t ldv;     // channel slice of the factor vectors (column i at V + ldv*i)
+  MapDev map;                  // the channel's origin set
+  const Cx<T>* gu; int64_t ldgu;  // F(U'_i) at gu + ldgu*i
+  const double* sigma;         // device
+  const int32_t* comps; int32_t ncomp;
+  int32_t log2Mx;
+  const int32_t* w; int32_t n; // weights of the channel grid, n = N_c
+  double* out;                 // n values
+  double inv_norm;             // 1 / Mx
+};
+
+// Image reconstruction, final inverse x-pass of one group.
+template <typename T>
+struct Rec2Item {
+  const Cx<T>* g2;             // y-inverse of the accumulated spectrum
+  const int32_t* w;            // Nx x Ny weights
+  double* out;                 // Nx x Ny
+  int32_t log2Mx, nx, ny, pad_;
+  double inv_norm;             // 1 / (Mx My)
+};
+
+template <typename T>
+void launch_rec_col_fft(const RecColItem<T>* items, int n, int max_log2Mx, int max_cols, const Cx<T>* tw,
+                        cudaStream_t st);
+template <typename T>
+void launch_rec1d(const Rec1Item<T>* items, int n, int max_log2Mx, const Cx<T>* tw, cudaStream_t st);
+template <typename T>
+void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny, const Cx<T>* tw,
+                     cudaStream_t st);
+void launch_residual(const void* data, int data_double, const int32_t* w, int64_t n, const double* groups,
+                     int64_t gstride, int ngroups, double* out, cudaStream_t st);
+
+}  // namespace ssa

@@ -1,0 +1,320 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU FP64 oracle.
+
+Tolerances (FP32-FFT form / FP64 form):
+  * singular values: |s - s*| <= 1e-5 s* / 1e-10 s* (per value);
+  * reconstructions: max |x~ - x~*| <= 1e-4 max|x| / 1e-9 max|x| over N',
+    for groups whose boundaries sit in spectral gaps (a group that splits a
+    cluster of near-equal singular values has no unique answer);
+  * one FFT product: |u - u*|_inf <= 5e-6 ||x||_2 ||v||_2 / 1e-13 ||x||_2 ||v||_2
+    (FP32 FFT convolution error grows like eps log2(M) ||x|| ||v||, M <= 2^14);
+  * shapes and weights: bit-exact (integers).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1309_5050_gb300 as pkg  # noqa: E402
+import workloads as W  # noqa: E402
+from oracle import ssa_oracle as O  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TOL_SIG = {"fp32": 1e-5, "fp64": 1e-10}
+TOL_REC = {"fp32": 1e-4, "fp64": 1e-9}
+TOL_MV = {"fp32": 5e-6, "fp64": 1e-13}
+
+
+def gap_groups(sig, min_gap=1.03):
+    """Split 0..len-1 at the boundaries where sigma drops by >= min_gap."""
+    groups, cur = [], [0]
+    for i in range(1, len(sig)):
+        if sig[i - 1] / sig[i] >= min_gap:
+            groups.append(cur)
+            cur = []
+        cur.append(i)
+    return groups  # the last (open) cluster is left out: its end is not a gap
+
+
+def noisy_series(n, seed):
+    rng = np.random.default_rng(seed)
+    t = np.arange(n, dtype=float)
+    return (0.02 * t + 3 * np.sin(2 * np.pi * t / 11.3) + 1.5 * np.cos(2 * np.pi * t / 4.7 + 0.3)
+            + rng.normal(0, 0.3, n))
+
+
+def noisy_image(nx, ny, seed):
+    return W.harmonic_image(nx, ny, n_harm=2, seed=seed, noise=0.2, trend=True, dtype=np.float64)
+
+
+# ------------------------------------------------------------------ cases
+def case_1d(n, L, seed):
+    x = noisy_series(n, seed)
+    return pkg.SSA.series(x, L), O.Problem.series(x, L), x
+
+
+def case_mssa(lengths, L, seed):
+    xs = [noisy_series(n, seed + i) for i, n in enumerate(lengths)]
+    xs32 = [np.asarray(v, np.float32).astype(np.float64) for v in xs]
+    return pkg.SSA.multi(xs, L), O.Problem.multi(xs32, L), xs32
+
+
+def case_2d(nx, ny, lx, ly, seed, wmask=None, holes=False):
+    x = noisy_image(nx, ny, seed)
+    mask = None
+    if holes:
+        rng = np.random.default_rng(seed)
+        mask = np.ones((nx, ny), bool)
+        for _ in range(3):
+            cx, cy = rng.integers(0, nx), rng.integers(0, ny)
+            mask[max(0, cx - 2):cx + 2, max(0, cy - 3):cy + 2] = False
+        x = x.copy()
+        x[rng.integers(0, nx), rng.integers(0, ny)] = np.nan
+    return (pkg.SSA.image(x, lx, ly, wmask=wmask, mask=mask),
+            O.Problem.image(x, lx, ly, wmask=wmask, mask=mask), x)
+
+
+SMALL = [
+    ("1d_37_11", lambda: case_1d(37, 11, 1)),
+    ("1d_1000_500", lambda: case_1d(1000, 500, 2)),
+    ("1d_1000_700_swapped", lambda: case_1d(1000, 700, 3)),
+    ("1d_4097_1500", lambda: case_1d(4097, 1500, 4)),
+    ("mssa_3x_ragged", lambda: case_mssa([50, 73, 61], 20, 5)),
+    ("mssa_5x_300_700", lambda: case_mssa([300, 701, 455, 512, 333], 100, 6)),
+    ("2d_30x27_w7x5", lambda: case_2d(30, 27, 7, 5, 7)),
+    ("2d_100x130_w20x30", lambda: case_2d(100, 130, 20, 30, 8)),
+    ("shaped_40x35_circle4_holes", lambda: case_2d(40, 35, 9, 9, 9, wmask=pkg.window_circle(4), holes=True)),
+    ("shaped_64x50_triangle6", lambda: case_2d(64, 50, 6, 6, 10, wmask=pkg.window_triangle(6), holes=True)),
+]
+
+
+def flat(P, arrs):
+    """oracle per-channel arrays -> the library's flat layout"""
+    return np.concatenate([np.asarray(a).ravel(order="F") for a in arrs])
+
+
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_shapes_exact(name, make):
+    s, P, _ = make()
+    L, K, om, w = s.shape()
+    assert L == P.L and K == P.K
+    om_ref, w_ref = [], []
+    for c in range(len(P.channels)):
+        shp = P.channels[c].shape
+        m = np.zeros(shp, np.uint8)
+        if len(P.Ksets[c]):
+            m[P.Ksets[c][:, 0], P.Ksets[c][:, 1]] = 1
+        om_ref.append(m)
+        w_ref.append(P.weights(c))
+    np.testing.assert_array_equal(np.ravel(om, order="F") if not isinstance(om, list) else np.concatenate(om),
+                                  flat(P, om_ref))
+    np.testing.assert_array_equal(np.ravel(w, order="F") if not isinstance(w, list) else np.concatenate(w),
+                                  flat(P, w_ref))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_matvec(name, make, prec):
+    s, P, _ = make()
+    rng = np.random.default_rng(0)
+    xnorm = math.sqrt(sum(np.nansum(np.where(o, c, 0.0) ** 2) for c, o in zip(P.channels, P.obs)))
+    v = rng.normal(size=P.K)
+    u = rng.normal(size=P.L)
+    got = s.matvec(v, False, prec)
+    ref = O.matvec(P, v)
+    assert np.max(np.abs(got - ref)) <= TOL_MV[prec] * xnorm * np.linalg.norm(v)
+    got = s.matvec(u, True, prec)
+    ref = O.rmatvec(P, u)
+    assert np.max(np.abs(got - ref)) <= TOL_MV[prec] * xnorm * np.linalg.norm(u)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("name,make", SMALL, ids=[s[0] for s in SMALL])
+def test_decompose_and_reconstruct(name, make, prec):
+    s, P, x = make()
+    r = min(8, min(P.L, P.K) - 1)
+    so, Uo, Vo = O.decompose(P, r + 1)
+    s.decompose(r, prec)
+    sig = s.sigma()
+    rel = np.abs(sig - so[:r]) / so[:r]
+    assert rel.max() <= TOL_SIG[prec], (rel, sig, so)
+    groups = gap_groups(so[:r + 1])
+    groups = [g for g in groups if max(g) < r]
+    if not groups:
+        return
+    rec = s.reconstruct(groups, residual=True)
+    ref = O.reconstruct(P, so, Uo, Vo, groups, residual=True)
+    xmax = max(np.nanmax(np.abs(np.where(o, c, np.nan))) for c, o in zip(P.channels, P.obs))
+    for g in range(len(groups) + 1):
+        got = rec[g]
+        got = [got] if not isinstance(got, list) else got
+        for c in range(len(P.channels)):
+            a = np.asarray(got[c]).reshape(P.channels[c].shape, order="F")
+            b = ref[g][c]
+            np.testing.assert_array_equal(np.isnan(a), np.isnan(b))
+            err = np.nanmax(np.abs(a - b)) / xmax
+            assert err <= TOL_REC[prec], (g, err)
+
+
+def test_vectors_satisfy_svd_relations():
+    """U, V returned by the C ABI: orthonormal and X V_i = sigma_i U_i."""
+    s, P, _ = case_2d(48, 40, 9, 7, 11)
+    s.decompose(6, "fp64")
+    sig = s.sigma()
+    U, V = s.vectors()
+    np.testing.assert_allclose(U.T @ U, np.eye(6), atol=1e-9)
+    np.testing.assert_allclose(V.T @ V, np.eye(6), atol=1e-9)
+    for i in range(6):
+        np.testing.assert_allclose(O.matvec(P, V[:, i]), sig[i] * U[:, i], atol=1e-8 * sig[0])
+        k = np.argmax(np.abs(U[:, i]))
+        assert U[k, i] > 0
+
+
+def test_batch_equals_single():
+    """ssa_decompose_batch gives each problem the result it gets alone."""
+    cases = [case_mssa([300, 400, 350], 80, 20 + i)[0] for i in range(3)]
+    singles = []
+    for s in cases:
+        s.decompose(6, "fp32")
+        singles.append(s.sigma())
+    pkg.decompose_batch(cases, 6, "fp32")
+    for s, ref in zip(cases, singles):
+        np.testing.assert_allclose(s.sigma(), ref, rtol=1e-6)
+
+
+# ------------------------------------------------------------------ errors
+def test_error_codes():
+    lib = pkg.load()
+    x = noisy_series(50, 1)
+    with pytest.raises(pkg.SSAError) as e:
+        pkg.SSA.series(x, 50)
+    assert e.value.code == -1
+    y = x.copy()
+    y[3] = np.inf
+    with pytest.raises(pkg.SSAError) as e:
+        pkg.SSA.series(y, 10)
+    assert e.value.code == -1
+    img = np.full((20, 20), np.nan)
+    img[:5, :5] = 1.0
+    with pytest.raises(pkg.SSAError) as e:
+        pkg.SSA.image(img, 8, 8)
+    assert e.value.code == -2
+    s = pkg.SSA.series(x, 10)
+    with pytest.raises(pkg.SSAError) as e:
+        s.decompose(11)
+    assert e.value.code == -3
+    with pytest.raises(pkg.SSAError) as e:
+        s.reconstruct([[0]])
+    assert e.value.code == -8
+    del lib
+
+
+def test_rank_edge_cases():
+    """r = 1, r = min(L, K) and L = 2."""
+    x = noisy_series(60, 3)
+    for L, r in [(2, 1), (2, 2), (30, 30), (12, 1)]:
+        s = pkg.SSA.series(x, L)
+        P = O.Problem.series(x, L)
+        s.decompose(r, "fp64")
+        so = O.decompose(P, r)[0]
+        np.testing.assert_allclose(s.sigma(), so, rtol=1e-9)
+
+
+def test_empty_groups_and_skipped_components():
+    x = noisy_series(200, 4)
+    s = pkg.SSA.series(x, 60)
+    s.decompose(6)
+    rec = s.reconstruct([[], [0]], residual=False)
+    ok = ~np.isnan(rec[0])
+    assert np.all(rec[0][ok] == 0.0)
+
+
+# ------------------------------------------------------------------ full-size workloads
+def golden(name):
+    d = np.load(os.path.join(GOLDEN, name + ".npz"))
+    return d["sigma"], d["U"], int(d["L"]), int(d["K"])
+
+
+def check_sigma(sig, ref, prec="fp32"):
+    rel = np.abs(sig - ref) / ref
+    assert rel.max() <= TOL_SIG[prec], rel
+
+
+def test_workload_series_1d_n1000():
+    cfg = W.CONFIGS["series_1d_n1000"]
+    x = W.series_1d(cfg["n"], seed=cfg["seed"])
+    ref, Ug, L, K = golden("series_1d_n1000")
+    s = pkg.SSA.series(x, cfg["L"])
+    s.decompose(cfg["rank"])
+    check_sigma(s.sigma(), ref)
+    P = O.Problem.series(x, cfg["L"])
+    so, Uo, Vo = O.decompose(P, cfg["rank"])
+    xmax = np.abs(x).max()
+    # gap-bounded groups, then the groups of the workload ({1,2},{3,4},rest)
+    for groups in ([[0], [1, 2], [3], [4, 5]], cfg["groups"]):
+        rec = s.reconstruct(groups, residual=True)
+        refr = O.reconstruct(P, so, Uo, Vo, groups, residual=True)
+        for g in range(len(groups) + 1):
+            err = np.nanmax(np.abs(rec[g] - refr[g][0][:, 0])) / xmax
+            assert err <= TOL_REC["fp32"], (groups, g, err)
+
+
+def sampled_points(nx, ny, n, seed):
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0), (nx - 1, ny - 1), (nx // 2, ny // 2), (0, ny - 1), (nx - 1, 0)]
+    pts += [(int(a), int(b)) for a, b in zip(rng.integers(0, nx, n), rng.integers(0, ny, n))]
+    return pts
+
+
+def test_workload_mssa_16_series():
+    cfg = W.CONFIGS["mssa_16x2000-8000_L1000"]
+    xs = W.mssa_series(cfg["s"], seed=cfg["seed"])
+    ref, Ug, L, K = golden("mssa_16x2000-8000_L1000")
+    s = pkg.SSA.multi(xs, cfg["L"])
+    assert s.info()["K"] == K
+    s.decompose(cfg["rank"])
+    check_sigma(s.sigma(), ref)
+    groups = [[0], [1, 2], [3, 4]]
+    rec = s.reconstruct(groups)
+    P = O.Problem.multi([np.asarray(v, np.float64) for v in xs], cfg["L"])
+    xmax = max(np.abs(v).max() for v in xs)
+    for gi, g in enumerate(groups):
+        for c in (0, 7, 15):
+            n = len(xs[c])
+            pts = [(m, 0) for m in sampled_points(n, 1, 10, c)[:0]] + \
+                  [(0, 0), (n - 1, 0), (n // 2, 0), (999, 0), (n - 1000, 0), (17, 0)]
+            want = O.reconstruct_at(P, Ug[:, g], pts, c)
+            got = np.array([rec[gi][c][m] for m, _ in pts])
+            assert np.max(np.abs(got - want)) / xmax <= TOL_REC["fp32"], (g, c)
+
+
+@pytest.mark.parametrize("name", ["image_1024x1024_w64", "shaped_2048x2048_disc40holes_w32"])
+def test_workload_images(name):
+    cfg = W.CONFIGS[name]
+    mask = None
+    if cfg["kind"] == "2d":
+        x = W.harmonic_image(cfg["nx"], cfg["ny"], seed=cfg["seed"])
+    else:
+        x, mask, _ = W.shaped_image(cfg["nx"], cfg["ny"], seed=cfg["seed"])
+    ref, Ug, L, K = golden(name)
+    s = pkg.SSA.image(x, cfg["lx"], cfg["ly"])
+    assert s.info()["L"] == L and s.info()["K"] == K
+    s.decompose(cfg["rank"])
+    check_sigma(s.sigma(), ref)
+    groups = gap_groups(ref)
+    rec = s.reconstruct(groups)
+    P = O.Problem.image(x, cfg["lx"], cfg["ly"])
+    xmax = np.nanmax(np.abs(x))
+    pts = sampled_points(cfg["nx"], cfg["ny"], 12, 1)
+    for gi, g in enumerate(groups):
+        want = O.reconstruct_at(P, Ug[:, g], pts)
+        got = np.array([rec[gi][m, n] for m, n in pts])
+        np.testing.assert_array_equal(np.isnan(got), np.isnan(want))
+        err = np.nanmax(np.abs(got - want)) / xmax if np.any(~np.isnan(want)) else 0.0
+        assert err <= TOL_REC["fp32"], (g, err)
