@@ -1,0 +1,314 @@
+"""Benchmark: batched MSSA decompositions on one GB300 (or N replicas).
+
+Workload: the MSSA configuration -- 16 float32 series of lengths U{2000..8000}
+(shared periods 12 and 50, random amplitudes and phases, exp(0.0002 t) trend,
+N(0, 0.2^2) noise), window L = 1000, rank r = 20.  One step is the whole hot
+path over a batch of B such problems (distinct seeds): shapes and weights,
+data spectra, Lanczos decomposition, reconstruction of the groups {1}, {2,3},
+{4,5} plus the residual.
+
+  value  decompositions/s with the series already resident in HBM (device
+         pointers through the C ABI; reconstructions written to HBM);
+  e2e    the same through the C ABI from pinned host buffers, the host->device
+         copies of the series and the device->host copy of the results inside
+         the timed region.
+Between timed steps L2 is flushed by writing a 512 MiB buffer.
+
+--impl reference times the CPU FP64 oracle (explicit trajectory matrix,
+S = X X^T eigendecomposition, direct diagonal averaging) on the same problems.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "mssa_16x2000-8000_L1000"
+CFG = W.CONFIGS[WORKLOAD]
+GROUPS = [[0], [1, 2], [3, 4]]
+METRIC = "ssa_decomps_per_s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def problem_series(seed):
+    return W.mssa_series(CFG["s"], seed=seed)
+
+
+# ------------------------------------------------------------------ oracle arm
+def run_oracle(n_problems, base_seed):
+    from oracle import ssa_oracle as O
+    t0 = time.perf_counter()
+    for i in range(n_problems):
+        xs = problem_series(base_seed + i)
+        P = O.Problem.multi([np.asarray(x, np.float64) for x in xs], CFG["L"])
+        s, U, V = O.decompose(P, CFG["rank"])
+        O.reconstruct(P, s, U, V, GROUPS, residual=True)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(budget_s=12.0):
+    """Time the oracle on as many problems as fit in about budget_s."""
+    n, total = 0, 0.0
+    while total < budget_s and n < 8:
+        total += run_oracle(1, 1000 + n)
+        n += 1
+    return {"value": n / total, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{n} MSSA problems (16 series, L=1000, r=20) through the FP64 oracle, "
+                      f"{total:.1f} s"}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 6:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        for _ in range(args.warmup):
+            run_oracle(1, 5000)
+        times = [run_oracle(1, 6000 + i) for i in range(args.steps)]
+        tot = sum(times)
+        value = args.steps / tot
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "decomps/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "batch": 1, "series": 16, "L": 1000, "rank": 20,
+                           "l2": "n/a (host)"},
+                "cpu_baseline": {"value": value, "unit": "decomps/s", "cores": cpu_cores(), "kind": "oracle",
+                                 "sample": f"{args.steps} MSSA problems, one per step"},
+                "e2e": {"value": value, "unit": "decomps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    import paper_1309_5050_gb300 as pkg
+    from paper_1309_5050_gb300 import _lib
+
+    # a process pool is never used; the oracle leg runs in-process before CUDA work
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    pkg.load()
+    B = args.batch
+
+    # inputs: B problems per rank, distinct seeds per rank
+    probs = []
+    for i in range(B):
+        xs = problem_series(2 + rank * 100003 + i)
+        lens = np.array([len(x) for x in xs], dtype=np.int64)
+        flat = np.concatenate(xs).astype(np.float32)
+        probs.append((lens, flat))
+    dev_inputs = [torch.from_numpy(f).to(dev) for _, f in probs]
+    host_inputs = [torch.from_numpy(f).pin_memory() for _, f in probs]
+    nout = len(GROUPS) + 1
+    dev_outs = [torch.empty(int(l.sum()) * nout, dtype=torch.float64, device=dev) for l, _ in probs]
+    host_outs = [torch.empty(int(l.sum()) * nout, dtype=torch.float64).pin_memory() for l, _ in probs]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(inputs, outs, prec):
+        ps = [pkg.SSA.multi_concat(x, l, CFG["L"], stream=stream) for x, (l, _) in zip(inputs, probs)]
+        pkg.decompose_batch(ps, CFG["rank"], prec)
+        if outs[0].is_cuda:
+            pkg.reconstruct_batch(ps, GROUPS, residual=True, outs=outs)
+        else:
+            # results through device buffers, then one read back per problem
+            pkg.reconstruct_batch(ps, GROUPS, residual=True, outs=dev_outs)
+            for d, h in zip(dev_outs, outs):
+                h.copy_(d, non_blocking=True)
+        for p in ps:
+            p.close()
+
+    def timed(nsteps, inputs, outs, prec, profile=False):
+        ts = []
+        for _ in range(nsteps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(inputs, outs, prec)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(dev_inputs, dev_outs, args.prec)
+    torch.cuda.synchronize()
+
+    # timed region (device-resident inputs), with phase profiling and clocks
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    l0 = _lib.kernel_launches()
+    with Clocks(local) as ck:
+        ts = timed(args.steps, dev_inputs, dev_outs, args.prec)
+    launches = _lib.kernel_launches() - l0
+    prof = _lib.profile_read()
+    _lib.profile_enable(False)
+    clocks = ck.summary()
+
+    ms = sum(ts) / len(ts)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B / (ms / 1000.0)
+
+    # end to end from pinned host memory
+    ts_e2e = timed(max(2, args.steps // 2), host_inputs, host_outs, args.prec)
+    ms_e2e = sum(ts_e2e) / len(ts_e2e)
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = int(sum(f.nbytes for _, f in probs))
+    d2h = int(sum(o.numel() * 8 for o in host_outs))
+
+    # FP64 form on the same problems (fewer steps)
+    fp64 = None
+    if not args.no_fp64_form and args.prec == "fp32":
+        step(dev_inputs, dev_outs, "fp64")
+        t64 = timed(max(1, args.steps // 3), dev_inputs, dev_outs, "fp64")
+        fp64 = {"value": world * B / (sum(t64) / len(t64) / 1000.0), "unit": "decomps/s",
+                "ms_per_step": sum(t64) / len(t64)}
+
+    # roofline of the dominant phase
+    hbm, src = peaks()
+    total_ms = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    mv_ms, mv_launch, mv_calls = prof["matvec"]
+    # algorithmic bytes of one trajectory product of one problem: v (K fp32) +
+    # spectra (16 x (H+1) complex fp32) + u (L fp32); one call = B problems.
+    Ks = [int((l - CFG["L"] + 1).sum()) for l, _ in probs]
+    H = 4096
+    per_call = sum(K * 4 + 16 * (H + 1) * 8 + CFG["L"] * 4 for K in Ks)
+    mv_avg_ms = mv_ms / max(mv_calls, 1)
+    achieved = per_call / (mv_avg_ms / 1000.0) / 1e9
+    roof = {"kernel": "k_mv1d (fused FFT trajectory product)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak_source": src, "launches_timed": mv_calls,
+            "phase_share": {k: (v[0] / total_ms if total_ms else 0.0) for k, v in prof.items()},
+            "dominant_phase": dom}
+
+    if rank == 0:
+        ts_sorted = sorted(ts)
+        line = {"metric": METRIC, "value": value, "unit": "decomps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "batch_per_gpu": B, "series": 16, "series_len": [2000, 8000],
+                           "L": CFG["L"], "rank": CFG["rank"], "groups": GROUPS, "residual": True,
+                           "precision_form": "fp32 FFT + fp64 reorth" if args.prec == "fp32" else "fp64",
+                           "l2": "flushed (512 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
+                "latency_ms": {"p50": float(np.percentile(ts_sorted, 50)), "p99": float(np.percentile(ts_sorted, 99)),
+                               "what": "completion of one batch"},
+                "fp64_form": fp64,
+                "roofline": roof,
+                "cpu_baseline": cpu,
+                "e2e": {"value": world * B / (ms_e2e / 1000.0), "unit": "decomps/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+                "gpu_launches": int(launches),
+                "phases_ms": {k: v[0] / args.steps for k, v in prof.items()},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -87,7 +87,7 @@ typedef struct {
   int32_t max_restarts;    /* 0 = 40 */
   int32_t prec;            /* ssa_prec */
   double tol;              /* residual tolerance relative to sigma_1;
-                              0 = 1e-7 (FP32 form) / 1e-12 (FP64 form) */
+                              0 = 1e-7 (FP32 form) / 1e-13 (FP64 form) */
   uint64_t seed;           /* start vector seed */
 } ssa_params;
 
@@ -192,6 +192,22 @@ int ssa_get_shape(const ssa_ctx* ctx, int64_t* L, int64_t* K, uint8_t* origin_ma
  * prec selects the arithmetic (ssa_prec).  in/out: FP64, host or device.
  */
 int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, double* out, int32_t on_device);
+
+/*
+ * Profiling (process-wide; no paper counterpart -- measurement support).
+ * Phases: 0 shapes and weights, 1 data spectrum, 2 trajectory products
+ * (X v and X^T u), 3 short-side Lanczos (re-orthogonalisation), 4 long-side
+ * Lanczos, 5 small SVD / Ritz vectors / restart, 6 reconstruction.
+ * ssa_profile_enable(1) records CUDA events on the launching stream around
+ * each phase; ssa_profile_read() waits for them and returns the summed device
+ * milliseconds, the kernels launched and the phase instances since the last
+ * reset.  Launch counts are kept even when timing is off.
+ * ssa_kernel_launches() returns every kernel this library has launched.
+ */
+int ssa_profile_enable(int32_t on);
+int ssa_profile_reset(void);
+int ssa_profile_read(int32_t phase, double* ms, int64_t* launches, int64_t* calls);
+int64_t ssa_kernel_launches(void);
 
 /* ssa_synchronize -- wait for the context's stream. */
 int ssa_synchronize(ssa_ctx* ctx);

@@ -199,7 +199,8 @@ class SSA:
     def reconstruct(self, groups, residual: bool = False):
         """groups: list of lists of 0-based component indices.  Returns one
         array per group (plus the residual) in the input's shape; NaN outside N'."""
-        gof = np.full(self.rank, -1, dtype=np.int32)
+        need = max([self.rank] + [i + 1 for g in groups for i in g])
+        gof = np.full(max(need, 1), -1, dtype=np.int32)
         for g, idx in enumerate(groups):
             for i in idx:
                 gof[i] = g
@@ -263,7 +264,11 @@ def decompose_batch(problems, rank, prec: str = "fp32", krylov_dim: int = 0, tol
     return rc, list(st)
 
 
-def reconstruct_batch(problems, groups, residual: bool = False):
+def reconstruct_batch(problems, groups, residual: bool = False, outs=None):
+    """Reconstruct many decomposed problems at once.  With ``outs`` (one CUDA
+    tensor of float64 per problem, (n_groups + residual) * total elements) the
+    results stay on the device and the tensors are returned; otherwise host
+    arrays split per group are returned."""
     lib = L.load()
     n = len(problems)
     r = problems[0].rank
@@ -272,11 +277,17 @@ def reconstruct_batch(problems, groups, residual: bool = False):
         for i in idx:
             gof[i] = g
     nout = len(groups) + (1 if residual else 0)
-    outs = [np.zeros(p._total() * nout) for p in problems]
-    ptrs = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+    on_device = outs is not None
+    if outs is None:
+        outs = [np.zeros(p._total() * nout) for p in problems]
+        ptrs = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+    else:
+        ptrs = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
     arr = (C.c_void_p * n)(*[p.ctx for p in problems])
     L.check(lib.ssa_reconstruct_batch(arr, n, gof.ctypes.data_as(C.POINTER(C.c_int32)), len(groups),
-                                      1 if residual else 0, ptrs, 0), "ssa_reconstruct_batch")
+                                      1 if residual else 0, ptrs, 1 if on_device else 0), "ssa_reconstruct_batch")
+    if on_device:
+        return outs
     res = []
     for p, o in zip(problems, outs):
         t = p._total()

@@ -21,7 +21,9 @@ EXPORTS = [
     "ssa_embed", "ssa_decompose", "ssa_decompose_batch", "ssa_get_info", "ssa_get_sigma",
     "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_get_shape", "ssa_matvec",
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
+    "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
 ]
+PHASES = ["shapes", "spectrum", "matvec", "short", "long", "ritz", "recon"]
 
 
 class ssa_input(C.Structure):
@@ -86,10 +88,11 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.ssa_last_error.argtypes = []
     lib.ssa_last_error.restype = C.c_char_p
     lib.ssa_version.restype = C.c_char_p
-    for name in EXPORTS:
-        f = getattr(lib, name)
-        if f.restype is C.c_int:
-            pass
+    lib.ssa_profile_enable.argtypes = [C.c_int32]
+    lib.ssa_profile_reset.argtypes = []
+    lib.ssa_profile_read.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.ssa_kernel_launches.argtypes = []
+    lib.ssa_kernel_launches.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -107,3 +110,26 @@ def check(rc: int, where: str) -> int:
     if rc != SSA_OK:
         raise SSAError(rc, where)
     return rc
+
+
+def profile_enable(on: bool = True) -> None:
+    check(load().ssa_profile_enable(1 if on else 0), "ssa_profile_enable")
+
+
+def profile_reset() -> None:
+    check(load().ssa_profile_reset(), "ssa_profile_reset")
+
+
+def profile_read() -> dict:
+    """{phase: (device ms, kernel launches, phase instances)} since the last reset."""
+    lib = load()
+    out = {}
+    for i, name in enumerate(PHASES):
+        ms, la, ca = C.c_double(), C.c_int64(), C.c_int64()
+        check(lib.ssa_profile_read(i, C.byref(ms), C.byref(la), C.byref(ca)), "ssa_profile_read")
+        out[name] = (ms.value, la.value, ca.value)
+    return out
+
+
+def kernel_launches() -> int:
+    return int(load().ssa_kernel_launches())

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <set>
@@ -54,13 +55,63 @@ namespace ssa {
 
 static std::mutex g_mu;
 
+// ---------------------------------------------------------------- profiling
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  double ms[PH_COUNT] = {0};
+  long long launches[PH_COUNT] = {0}, calls[PH_COUNT] = {0};
+  struct Pend { int ph; cudaEvent_t a, b; };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e; cudaEventCreate(&e); return e;
+  }
+  void resolve() {   // caller holds mu
+    for (auto& p : pend) {
+      float t = 0.f;
+      cudaEventSynchronize(p.b);
+      if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.ph] += t;
+      pool.push_back(p.a); pool.push_back(p.b);
+    }
+    pend.clear();
+  }
+};
+static Profiler g_prof;
+
+PhaseScope::PhaseScope(int ph_, cudaStream_t st_) : ph(ph_), st(st_), a(nullptr), l0(g_launches.load()) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  cudaEvent_t e = g_prof.get();
+  cudaEventRecord(e, st);
+  a = (void*)e;
+}
+PhaseScope::~PhaseScope() {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.launches[ph] += g_launches.load() - l0;
+  g_prof.calls[ph] += 1;
+  if (!a) return;
+  cudaEvent_t b = g_prof.get();
+  cudaEventRecord(b, st);
+  g_prof.pend.push_back({ph, (cudaEvent_t)a, b});
+  if (g_prof.pend.size() > 4096) g_prof.resolve();
+}
+
 void set_max_smem(const void* fn) {
   static std::set<std::pair<const void*, int>> done;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_mu);
   if (done.count({fn, dev})) return;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, device_max_smem());
+  cudaFuncAttributes fa;
+  int avail = device_max_smem();
+  if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) avail -= (int)fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, avail) != cudaSuccess)
+    cudaGetLastError();  // leave no sticky error: the launch itself reports a too-large request
   done.insert({fn, dev});
 }
 
@@ -94,7 +145,7 @@ static int ensure_tables(int dev) {
   DevTables t;
   CU(cudaMalloc(&t.t32, sizeof(Cx<float>) * TW_N));
   CU(cudaMalloc(&t.t64, sizeof(Cx<double>) * TW_N));
-  k_twiddles<<<64, 256>>>(t.t32, t.t64);
+  k_twiddles<<<64, 256>>>(t.t32, t.t64); count_launch();
   CU(cudaGetLastError());
   CU(cudaDeviceSynchronize());
   g_tables[dev] = t;
@@ -307,6 +358,7 @@ static int embed_shapes(ssa_ctx* c, const ssa_window* win) {
   TRY(build_set_counts(c, Ls));
   c->L = Ls.count;
 
+  PhaseScope ps_(PH_SHAPES, c->stream);
   int* derr = nullptr;
   TRY(c->allocT(&derr, 1));
   CU(cudaMemsetAsync(derr, 0, sizeof(int), c->stream));
@@ -362,6 +414,7 @@ static int ensure_spectrum(ssa_ctx* c) {
   bool have = true;
   for (auto& h : c->ch) have &= (f32 ? h.xh32 : h.xh64) != nullptr;
   if (have) return SSA_OK;
+  PhaseScope ps_(PH_SPECTRUM, c->stream);
   const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
   std::vector<SpecItem<T>> items;
   std::vector<YItem<T>> yitems;
@@ -453,6 +506,7 @@ static int finish_set(ssa_ctx* c, MvSet<T>& s) {
 
 template <typename T>
 static void run_mv(ssa_ctx* c, const MvSet<T>& s, int max_log2Mx, int max_log2My, int step) {
+  PhaseScope ps_(PH_MATVEC, c->stream);
   const int n = (int)s.items.size();
   if (max_log2My == 0)
     launch_mv1d<T>(s.d_items, n, max_log2Mx, step, twiddles<T>(c->device), c->stream);
@@ -501,7 +555,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->alloc(&w.parts_l, sizeof(T) * (size_t)w.Kl * w.n_part_l));
   TRY(c->allocT(&w.B, (size_t)w.k * w.k));
   TRY(c->allocT(&w.P, (size_t)w.k * w.k));
-  TRY(c->allocT(&w.Q, (size_t)w.k * w.k));
+  TRY(c->allocT(&w.Q, (size_t)(w.k + 1) * w.k));
   TRY(c->allocT(&w.sig, (size_t)w.k));
   TRY(c->allocT(&w.cpa, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.cpb, (size_t)w.nblk_s * (KMAX + 1)));
@@ -519,9 +573,9 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   CU(cudaMemsetAsync(w.B, 0, sizeof(double) * w.k * w.k, c->stream));
   CU(cudaMemsetAsync(w.parts_s, 0, sizeof(T) * (size_t)w.Ls * w.n_part_s, c->stream));
   CU(cudaMemsetAsync(w.parts_l, 0, sizeof(T) * (size_t)w.Kl * w.n_part_l, c->stream));
-  double tol = p.tol > 0 ? p.tol : (std::is_same<T, float>::value ? 1e-7 : 1e-12);
+  double tol = p.tol > 0 ? p.tol : (std::is_same<T, float>::value ? 1e-7 : 1e-13);
   int maxr = p.max_restarts > 0 ? p.max_restarts : 40;
-  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0);
+  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0); count_launch();
   CU(cudaGetLastError());
   return SSA_OK;
 }
@@ -647,7 +701,7 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
   TRY(finish_set(c0, mvAT));
   const int nl = (int)live.size();
   // start vectors
-  launch_long_init<T>(d_lg, nl, max_blk_l, st);
+  { PhaseScope ps_(PH_LONG, st); launch_long_init<T>(d_lg, nl, max_blk_l, st); }
   CU(cudaGetLastError());
   std::vector<LzState> hst(nl);
   int rc_all = SSA_OK;
@@ -661,11 +715,11 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
     }
     for (int s = 0; s < steps; ++s) {
       run_mv<T>(c0, mvA, max_log2Mx, max_log2My, s);
-      launch_short_steps(d_sh, nl, max_blk_s, s, st);
+      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, nl, max_blk_s, s, st); }
       run_mv<T>(c0, mvAT, max_log2Mx, max_log2My, s);
-      launch_long_step<T>(d_lg, nl, max_blk_l, s, st);
+      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, nl, max_blk_l, s, st); }
     }
-    launch_bsvd(d_sv, nl, max_k, st);
+    { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
     CU(cudaGetLastError());
     for (int i = 0; i < nl; ++i)
       CU(cudaMemcpyAsync(&hst[i], live[i]->ws.st, sizeof(LzState), cudaMemcpyDeviceToHost, st));
@@ -673,12 +727,18 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
     bool any = false;
     for (int i = 0; i < nl; ++i) any |= hst[i].active != 0;
     if (!any) break;
-    launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 0, st);
-    launch_restart(d_sv, nl, st);
+    {
+      PhaseScope ps_(PH_RITZ, st);
+      launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 0, st);
+      launch_restart(d_sv, nl, st);
+    }
     CU(cudaGetLastError());
   }
-  launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 1, st);
-  launch_finalize<T>(d_fi, nl, max_r, max_rows, st);
+  {
+    PhaseScope ps_(PH_RITZ, st);
+    launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 1, st);
+    launch_finalize<T>(d_fi, nl, max_r, max_rows, st);
+  }
   CU(cudaGetLastError());
   CU(cudaStreamSynchronize(st));
   for (int i = 0; i < nl; ++i) {
@@ -700,12 +760,16 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
 }
 
 // ============================================================== reconstruction
-template <typename T>
+// Reconstruction arithmetic runs in TC (FP64 unless the grid is too long for
+// an FP64 single-CTA pass); the decomposition's vectors are read as TV.
+template <typename TC, typename TV>
 static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int ng, int residual,
                          double* const* outs, int on_device) {
+  typedef TC T;
   ssa_ctx* c0 = cs[0];
   cudaStream_t st = c0->stream;
   const int r = c0->ws.r;
+  PhaseScope ps_(PH_RECON, st);
   std::vector<std::vector<int32_t>> comps(ng);
   for (int i = 0; i < r; ++i) {
     if (group_of[i] < -1 || group_of[i] >= ng) return fail(SSA_EINVAL, "group_of[%d] = %d out of range", i, group_of[i]);
@@ -722,8 +786,8 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
   const Cx<T>* tw = twiddles<T>(c0->device);
   if (c0->log2My == 0) {
     // ---- series: F(U_i) once per problem, then one CTA per (problem, group, channel)
-    std::vector<RecColItem<T>> ui;
-    std::vector<Rec1Item<T>> ri;
+    std::vector<RecColItem<T, TV>> ui;
+    std::vector<Rec1Item<T, TV>> ri;
     int max_log2Mx = 1;
     for (int p = 0; p < n; ++p) {
       ssa_ctx* c = cs[p];
@@ -737,16 +801,16 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
       else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
       dout[p] = o;
       for (int i = 0; i < r; ++i) {
-        RecColItem<T> u;
-        u.vec = (const T*)w.Uo + (size_t)c->L * i; u.map = c->Lset.dev(); u.dst = gu + (size_t)(H + 1) * i;
+        RecColItem<T, TV> u;
+        u.vec = (const TV*)w.Uo + (size_t)c->L * i; u.map = c->Lset.dev(); u.dst = gu + (size_t)(H + 1) * i;
         u.log2Mx = c->log2Mx; u.ncols = 1;
         ui.push_back(u);
       }
       for (int g = 0; g < ng; ++g)
         for (size_t q = 0; q < c->ch.size(); ++q) {
           const Channel& h = c->ch[q];
-          Rec1Item<T> it;
-          it.V = (const T*)w.Vo + h.koff; it.ldv = c->K; it.map = h.K.dev();
+          Rec1Item<T, TV> it;
+          it.V = (const TV*)w.Vo + h.koff; it.ldv = c->K; it.map = h.K.dev();
           it.gu = gu; it.ldgu = H + 1; it.sigma = w.sigma;
           it.comps = d_flat + start[g]; it.ncomp = start[g + 1] - start[g];
           it.log2Mx = c->log2Mx; it.w = h.w; it.n = (int32_t)h.nx;
@@ -756,11 +820,11 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
         }
       max_log2Mx = std::max(max_log2Mx, c->log2Mx);
     }
-    RecColItem<T>* d_ui = nullptr; Rec1Item<T>* d_ri = nullptr;
+    RecColItem<T, TV>* d_ui = nullptr; Rec1Item<T, TV>* d_ri = nullptr;
     TRY(upload(c0, ui, &d_ui));
     TRY(upload(c0, ri, &d_ri));
-    launch_rec_col_fft<T>(d_ui, (int)ui.size(), max_log2Mx, 1, tw, st);
-    launch_rec1d<T>(d_ri, (int)ri.size(), max_log2Mx, tw, st);
+    launch_rec_col_fft<T, TV>(d_ui, (int)ui.size(), max_log2Mx, 1, tw, st);
+    launch_rec1d<T, TV>(d_ri, (int)ri.size(), max_log2Mx, tw, st);
     CU(cudaGetLastError());
     tmp.push_back(d_ui); tmp.push_back(d_ri);
   } else {
@@ -785,21 +849,20 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
       std::vector<double> sig(r);
       CU(cudaMemcpyAsync(sig.data(), w.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
       CU(cudaStreamSynchronize(st));
-      std::vector<RecColItem<T>> cu(2);
-      std::vector<YItem<T>> yu(2);
-      RecColItem<T>* d_cu = nullptr; YItem<T>* d_yu = nullptr;
+            std::vector<YItem<T>> yu(2);
+      RecColItem<T, TV>* d_cu = nullptr; YItem<T>* d_yu = nullptr;
       TRY(c0->allocT(&d_cu, 2 * (size_t)r));
       TRY(c0->allocT(&d_yu, 2 * (size_t)r));
       tmp.push_back(d_cu); tmp.push_back(d_yu);
-      std::vector<RecColItem<T>> allc;
+      std::vector<RecColItem<T, TV>> allc;
       std::vector<YItem<T>> ally;
       for (int i = 0; i < r; ++i) {
         const int g = group_of[i];
-        RecColItem<T> a;
-        a.vec = (const T*)w.Uo + (size_t)c->L * i; a.map = c->Lset.dev(); a.dst = gx; a.log2Mx = c->log2Mx;
+        RecColItem<T, TV> a;
+        a.vec = (const TV*)w.Uo + (size_t)c->L * i; a.map = c->Lset.dev(); a.dst = gx; a.log2Mx = c->log2Mx;
         a.ncols = c->ey;
-        RecColItem<T> b;
-        b.vec = (const T*)w.Vo + (size_t)c->K * i; b.map = h.K.dev(); b.dst = gx; b.log2Mx = c->log2Mx;
+        RecColItem<T, TV> b;
+        b.vec = (const TV*)w.Vo + (size_t)c->K * i; b.map = h.K.dev(); b.dst = gx; b.log2Mx = c->log2Mx;
         b.ncols = h.cy;
         YItem<T> ya;
         ya.src = gx; ya.dst = gu; ya.mul = nullptr; ya.st = nullptr; ya.log2Mx = c->log2Mx; ya.log2My = c->log2My;
@@ -810,13 +873,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
         allc.push_back(a); allc.push_back(b);
         ally.push_back(ya); ally.push_back(yb);
       }
-      CU(cudaMemcpyAsync(d_cu, allc.data(), sizeof(RecColItem<T>) * allc.size(), cudaMemcpyHostToDevice, st));
+      CU(cudaMemcpyAsync(d_cu, allc.data(), sizeof(RecColItem<T, TV>) * allc.size(), cudaMemcpyHostToDevice, st));
       CU(cudaMemcpyAsync(d_yu, ally.data(), sizeof(YItem<T>) * ally.size(), cudaMemcpyHostToDevice, st));
       for (int i = 0; i < r; ++i) {
         if (group_of[i] < 0) continue;
-        launch_rec_col_fft<T>(d_cu + 2 * i, 1, c->log2Mx, c->ey, tw, st);
+        launch_rec_col_fft<T, TV>(d_cu + 2 * i, 1, c->log2Mx, c->ey, tw, st);
         launch_ypass<T>(d_yu + 2 * i, 1, Y_FWD, c->log2Mx, c->log2My, -1, tw, st);
-        launch_rec_col_fft<T>(d_cu + 2 * i + 1, 1, c->log2Mx, h.cy, tw, st);
+        launch_rec_col_fft<T, TV>(d_cu + 2 * i + 1, 1, c->log2Mx, h.cy, tw, st);
         launch_ypass<T>(d_yu + 2 * i + 1, 1, Y_CONVACC, c->log2Mx, c->log2My, -1, tw, st);
       }
       std::vector<YItem<T>> yi;
@@ -879,7 +942,7 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
     TRY(c->allocT(&dres, (size_t)nout));
     CU(cudaMemcpyAsync(dd, in, sizeof(double) * nin, cudaMemcpyHostToDevice, c->stream));
   }
-  k_convert<T, double><<<grid1(nin), 256, 0, c->stream>>>(dd, din, nin);
+  k_convert<T, double><<<grid1(nin), 256, 0, c->stream>>>(dd, din, nin); count_launch();
   CU(cudaGetLastError());
   void *g1 = nullptr, *g2 = nullptr;
   const size_t hs = c->log2My > 0 ? ((size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My) : 0;
@@ -895,7 +958,7 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
   }
   TRY(finish_set(c, s));
   run_mv<T>(c, s, c->log2Mx, c->log2My, 0);
-  k_sum_parts_to_double<T><<<grid1(nout), 256, 0, c->stream>>>(dparts, nparts, nout, nout, dres);
+  k_sum_parts_to_double<T><<<grid1(nout), 256, 0, c->stream>>>(dparts, nparts, nout, nout, dres); count_launch();
   CU(cudaGetLastError());
   if (!on_device) CU(cudaMemcpyAsync(out, dres, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -928,6 +991,31 @@ const char* ssa_strerror(int code) {
 }
 
 const char* ssa_last_error(void) { return g_err; }
+
+int ssa_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = on != 0;
+  return SSA_OK;
+}
+
+int ssa_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.resolve();
+  for (int i = 0; i < PH_COUNT; ++i) { g_prof.ms[i] = 0.0; g_prof.launches[i] = 0; g_prof.calls[i] = 0; }
+  return SSA_OK;
+}
+
+int ssa_profile_read(int32_t phase, double* ms, int64_t* launches, int64_t* calls) {
+  if (phase < 0 || phase >= PH_COUNT) return fail(SSA_EINVAL, "phase %d", phase);
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.resolve();
+  if (ms) *ms = g_prof.ms[phase];
+  if (launches) *launches = g_prof.launches[phase];
+  if (calls) *calls = g_prof.calls[phase];
+  return SSA_OK;
+}
+
+int64_t ssa_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out) {
   if (!in || !win || !out || !in->data) return fail(SSA_EINVAL, "null argument");
@@ -1066,7 +1154,7 @@ int ssa_get_vectors(const ssa_ctx* cc, double* U, double* V, int32_t on_device) 
     if (w.prec == SSA_PREC_FP64)
       CU(cudaMemcpyAsync(d, j.src, sizeof(double) * j.n, cudaMemcpyDeviceToDevice, c->stream));
     else
-      k_convert<double, float><<<grid1(j.n), 256, 0, c->stream>>>((const float*)j.src, d, j.n);
+      k_convert<double, float><<<grid1(j.n), 256, 0, c->stream>>>((const float*)j.src, d, j.n); count_launch();
     CU(cudaGetLastError());
     if (!on_device) {
       CU(cudaMemcpyAsync(j.dst, d, sizeof(double) * j.n, cudaMemcpyDeviceToHost, c->stream));
@@ -1089,8 +1177,12 @@ int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_
     if (!outs[i]) return fail(SSA_EINVAL, "null output %d", i);
   }
   if (n_groups + (residual ? 1 : 0) == 0) return SSA_OK;
-  if (prec == SSA_PREC_FP64) return reconstruct_T<double>(ctxs, n, group_of, n_groups, residual, outs, on_device);
-  return reconstruct_T<float>(ctxs, n, group_of, n_groups, residual, outs, on_device);
+  int max_log2Mx = 0;
+  for (int i = 0; i < n; ++i) max_log2Mx = std::max(max_log2Mx, ctxs[i]->log2Mx);
+  if (prec == SSA_PREC_FP64) return reconstruct_T<double, double>(ctxs, n, group_of, n_groups, residual, outs, on_device);
+  // FP64 sums unless one FP64 pass would not fit a CTA (x grids above 8192)
+  if (max_log2Mx <= 13) return reconstruct_T<double, float>(ctxs, n, group_of, n_groups, residual, outs, on_device);
+  return reconstruct_T<float, float>(ctxs, n, group_of, n_groups, residual, outs, on_device);
 }
 
 int ssa_reconstruct(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, int32_t residual, double* out,
@@ -1108,10 +1200,11 @@ int ssa_get_shape(const ssa_ctx* cc, int64_t* L, int64_t* K, uint8_t* origin_mas
     TRY(c->allocT(&d, (size_t)c->total));
     for (auto& h : c->ch) {
       dim3 g(grid1(h.nx), (unsigned)h.ny);
-      if (h.K.count > 0 || h.K.bits)
-        k_kmask<<<g, 256, 0, c->stream>>>(h.K.bits, h.K.words, h.cx, h.cy, (int)h.nx, (int)h.ny, d + h.data_off);
-      else
+      if (h.K.count > 0 || h.K.bits) {
+        k_kmask<<<g, 256, 0, c->stream>>>(h.K.bits, h.K.words, h.cx, h.cy, (int)h.nx, (int)h.ny, d + h.data_off); count_launch();
+      } else {
         CU(cudaMemsetAsync(d + h.data_off, 0, (size_t)(h.nx * h.ny), c->stream));
+      }
     }
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(origin_mask, d, (size_t)c->total, cudaMemcpyDeviceToHost, c->stream));
@@ -1163,5 +1256,5 @@ __global__ void k_apply_mask(void* data, int dbl, const uint8_t* m, int64_t n) {
 }
 
 void launch_apply_mask(void* data, int dbl, const uint8_t* m, int64_t n, cudaStream_t st) {
-  k_apply_mask<<<grid1(n), 256, 0, st>>>(data, dbl, m, n);
+  k_apply_mask<<<grid1(n), 256, 0, st>>>(data, dbl, m, n); count_launch();
 }

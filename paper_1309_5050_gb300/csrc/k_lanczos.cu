@@ -228,28 +228,41 @@ __global__ void __launch_bounds__(256) k_long2(const LongItem<T>* __restrict__ i
 }
 
 // ------------------------------------------------------------ small SVD
-// One-sided Jacobi on the columns of B (k x k): B Qm = W with orthogonal
-// columns; sigma_i = ||W_i||, P_i = W_i / sigma_i.  Round-robin pair order,
-// one warp per pair.  Then residuals beta_k |P[k-1, i]| decide convergence.
+// One-sided Jacobi on the columns of W = B (k x k): W Qm has orthogonal
+// columns; sigma_i = their norms, P_i = column / sigma_i.  Round-robin pair
+// order, one warp per pair.  Residuals beta_k |P[k-1, i]| decide convergence.
+// When k equals the short dimension the short basis is complete and
+// A = U_k [B | beta_k e_k] V_{k+1}^T holds exactly, so W gets that extra
+// column and the singular values are exact (no restart needed).
+// Outputs: sig (k), P (k x k, ld ldb), Q ((k+1) x k, ld ldb+1; row k is zero
+// unless the extra column was used).
 __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
   if (!st->active) return;
   const int k = st->k, ld = it.ldb;
+  const bool aug = st->full != 0;
+  const int nc = aug ? k + 1 : k;       // columns of W
   extern __shared__ __align__(16) double sm[];
-  double* W = sm;              // column c at W + c*k
-  double* Qm = W + k * k;
+  double* W = sm;                        // column c at W + c*k (k rows)
+  double* Qm = W + nc * k;               // column c at Qm + c*nc (nc rows)
   __shared__ int rotated;
-  __shared__ double nrm[KMAX];
-  __shared__ int order[KMAX];
+  __shared__ double nrm[KMAX + 1];
+  __shared__ int order[KMAX + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+  for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
     const int c = e / k, i = e - c * k;
-    W[e] = it.B[i + (int64_t)ld * c];
+    double v;
+    if (c < k) v = it.B[i + (int64_t)ld * c];
+    else v = (i == k - 1) ? st->beta_k : 0.0;
+    W[e] = v;
+  }
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+    const int c = e / nc, i = e - c * nc;
     Qm[e] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  const int n2 = k + (k & 1);
+  const int n2 = nc + (nc & 1);
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
         const int sa = t, sb = n2 - 1 - t;
         const int a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
         const int b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
-        if (a >= k || b >= k) continue;
+        if (a >= nc || b >= nc) continue;
         double* wa = W + a * k;
         double* wb = W + b * k;
         double al = 0.0, be = 0.0, ga = 0.0;
@@ -271,12 +284,14 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
           const double zeta = (be - al) / (2.0 * ga);
           const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-          double* qa = Qm + a * k;
-          double* qb = Qm + b * k;
           for (int i = lane; i < k; i += 32) {
             const double x = wa[i], y = wb[i];
             wa[i] = cs * x - sn * y;
             wb[i] = sn * x + cs * y;
+          }
+          double* qa = Qm + a * nc;
+          double* qb = Qm + b * nc;
+          for (int i = lane; i < nc; i += 32) {
             const double u = qa[i], v = qb[i];
             qa[i] = cs * u - sn * v;
             qb[i] = sn * u + cs * v;
@@ -290,7 +305,7 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     __syncthreads();
     if (!any) break;
   }
-  for (int c = warp; c < k; c += nw) {
+  for (int c = warp; c < nc; c += nw) {
     double a = 0.0;
     for (int i = lane; i < k; i += 32) a += W[c * k + i] * W[c * k + i];
     a = warp_sum(a);
@@ -298,27 +313,31 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int c = 0; c < k; ++c) order[c] = c;
-    for (int a = 0; a < k; ++a) {          // selection sort, descending, stable
+    for (int c = 0; c < nc; ++c) order[c] = c;
+    for (int a = 0; a < nc; ++a) {          // selection sort, descending, stable
       int best = a;
-      for (int b = a + 1; b < k; ++b)
+      for (int b = a + 1; b < nc; ++b)
         if (nrm[order[b]] > nrm[order[best]]) best = b;
       const int t = order[a]; order[a] = order[best]; order[best] = t;
     }
   }
   __syncthreads();
-  const int kd = ld;  // allocated dimension: clear what lies beyond k
+  const int kd = ld, kq = ld + 1;
   for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
     const int c = e / kd, i = e - c * kd;
-    double pv = 0.0, qv = 0.0;
+    double pv = 0.0;
     if (c < k && i < k) {
       const int o = order[c];
       const double sg = nrm[o];
       pv = sg > 0.0 ? W[o * k + i] / sg : 0.0;
-      qv = Qm[o * k + i];
     }
     it.P[i + (int64_t)kd * c] = pv;
-    it.Q[i + (int64_t)kd * c] = qv;
+  }
+  for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
+    const int c = e / kq, i = e - c * kq;
+    double qv = 0.0;
+    if (c < k && i < nc) qv = Qm[order[c] * nc + i];
+    it.Q[i + (int64_t)kq * c] = qv;
   }
   for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
   __syncthreads();
@@ -332,13 +351,12 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
       const int o = order[i];
       const double sg = nrm[o];
       const double pk = sg > 0.0 ? W[o * k + (k - 1)] / sg : 0.0;
-      const double res = fabs(st->beta_k * pk);
+      const double res = aug ? 0.0 : fabs(st->beta_k * pk);
       const double rel = s1 > 0.0 ? res / s1 : 0.0;
       if (rel > mres) mres = rel;
       if (rel <= st->tol) { if (nconv == i) ++nconv; }
       else conv = false;
     }
-    if (st->full) { conv = true; nconv = r; }
     st->sigma1 = s1;
     st->maxres = mres;
     st->nconv = nconv;
@@ -386,21 +404,23 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   const int nr = (int)imin64(rows_per, nrow - r0);
   extern __shared__ __align__(16) unsigned char smraw[];
   E* blk = reinterpret_cast<E*>(smraw);               // rows_per x (k+1), column-major
-  E* cf = blk + (int64_t)rows_per * (k + 1);           // k x kk
-  const int ncol = move ? k + 1 : k;
+  E* cf = blk + (int64_t)rows_per * (k + 1);           // kc x kk
+  const int kc = SHORT ? k : k + 1;                    // coefficient rows (Q has k+1)
+  const int cld = SHORT ? it.ldc : it.ldc + 1;
+  const int ncol = SHORT ? k : k + 1;
   for (int e = threadIdx.x; e < ncol * rows_per; e += blockDim.x) {
     const int c = e / rows_per, t = e - c * rows_per;
     if (t < nr) blk[e] = basis[r0 + t + ldb * c];
   }
-  for (int e = threadIdx.x; e < k * kk; e += blockDim.x) {
-    const int c = e / k, i = e - c * k;
-    cf[e] = (E)C[i + (int64_t)it.ldc * c];
+  for (int e = threadIdx.x; e < kc * kk; e += blockDim.x) {
+    const int c = e / kc, i = e - c * kc;
+    cf[e] = (E)C[i + (int64_t)cld * c];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * kk; e += blockDim.x) {
     const int c = e / nr, t = e - c * nr;
     E acc = E(0);
-    for (int i = 0; i < k; ++i) acc += blk[t + (int64_t)rows_per * i] * cf[i + k * c];
+    for (int i = 0; i < kc; ++i) acc += blk[t + (int64_t)rows_per * i] * cf[i + kc * c];
     basis[r0 + t + ldb * c] = acc;
   }
   if (move)
@@ -474,38 +494,38 @@ __global__ void __launch_bounds__(256) k_final_copy(const FinalItem<T>* __restri
 void launch_short_steps(const ShortItem* items, int n, int max_blk, int s, cudaStream_t st) {
   if (n <= 0) return;
   dim3 g(max_blk, n);
-  k_short1<<<g, SHORT_RB, 0, st>>>(items, s);
-  k_short23<2><<<g, SHORT_RB, 0, st>>>(items, s);
-  k_short23<3><<<g, SHORT_RB, 0, st>>>(items, s);
-  k_short4<<<g, SHORT_RB, 0, st>>>(items, s);
+  k_short1<<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
+  k_short23<2><<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
+  k_short23<3><<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
+  k_short4<<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
 }
 
 template <typename T>
 void launch_long_step(const LongItem<T>* items, int n, int max_blk, int s, cudaStream_t st) {
   if (n <= 0) return;
   dim3 g(max_blk, n);
-  k_long1<T><<<g, 256, 0, st>>>(items, s);
-  k_long2<T><<<g, 256, 0, st>>>(items, s);
+  k_long1<T><<<g, 256, 0, st>>>(items, s); count_launch();
+  k_long2<T><<<g, 256, 0, st>>>(items, s); count_launch();
 }
 
 template <typename T>
 void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t st) {
   if (n <= 0) return;
   dim3 g(max_blk, n);
-  k_long_init<T><<<g, 256, 0, st>>>(items);
-  k_long2<T><<<g, 256, 0, st>>>(items, -1);
+  k_long_init<T><<<g, 256, 0, st>>>(items); count_launch();
+  k_long2<T><<<g, 256, 0, st>>>(items, -1); count_launch();
 }
 
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
   if (n <= 0) return;
-  const size_t sm = 2 * (size_t)kmax * kmax * sizeof(double);
+  const size_t sm = 2 * (size_t)(kmax + 1) * (kmax + 1) * sizeof(double);
   set_max_smem((const void*)k_bsvd);
-  k_bsvd<<<n, 256, sm, st>>>(items);
+  k_bsvd<<<n, 256, sm, st>>>(items); count_launch();
 }
 
 void launch_restart(const SvdItem* items, int n, cudaStream_t st) {
   if (n <= 0) return;
-  k_restart<<<n, 256, 0, st>>>(items);
+  k_restart<<<n, 256, 0, st>>>(items); count_launch();
 }
 
 template <typename T>
@@ -514,19 +534,19 @@ void launch_ritz(const RitzItem<T>* items, int n, int kmax, int64_t max_short, i
   if (n <= 0) return;
   const int rs = 64, rl = 128;
   size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)kmax * kmax * sizeof(double);
-  size_t sml = (size_t)rl * (kmax + 1) * sizeof(T) + (size_t)kmax * kmax * sizeof(T);
+  size_t sml = (size_t)rl * (kmax + 1) * sizeof(T) + (size_t)(kmax + 1) * kmax * sizeof(T);
   set_max_smem((const void*)k_ritz<T, true>);
   set_max_smem((const void*)k_ritz<T, false>);
-  k_ritz<T, true><<<dim3((unsigned)((max_short + rs - 1) / rs), n), 256, sms, st>>>(items, final_pass, rs);
-  k_ritz<T, false><<<dim3((unsigned)((max_long + rl - 1) / rl), n), 256, sml, st>>>(items, final_pass, rl);
+  k_ritz<T, true><<<dim3((unsigned)((max_short + rs - 1) / rs), n), 256, sms, st>>>(items, final_pass, rs); count_launch();
+  k_ritz<T, false><<<dim3((unsigned)((max_long + rl - 1) / rl), n), 256, sml, st>>>(items, final_pass, rl); count_launch();
 }
 
 template <typename T>
 void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st) {
   if (n <= 0) return;
-  k_sign<T><<<dim3(max_r, n), 256, 0, st>>>(items);
+  k_sign<T><<<dim3(max_r, n), 256, 0, st>>>(items); count_launch();
   unsigned gx = (unsigned)std::min<int64_t>((max_rows + 255) / 256, 1024);
-  k_final_copy<T><<<dim3(gx, max_r, n), 256, 0, st>>>(items);
+  k_final_copy<T><<<dim3(gx, max_r, n), 256, 0, st>>>(items); count_launch();
 }
 
 #define INST(T)                                                                                        \

@@ -266,7 +266,7 @@ void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<
   if (n <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_mv1d<T>);
-  k_mv1d<T><<<n, 512, sm, st>>>(items, s, tw);
+  k_mv1d<T><<<n, 512, sm, st>>>(items, s, tw); count_launch();
 }
 
 template <typename T>
@@ -276,9 +276,9 @@ void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, int max_
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_mv_xfwd<T>);
   set_max_smem((const void*)k_mv_xinv<T>);
-  k_mv_xfwd<T><<<dim3(max_y_in, n), 512, sm, st>>>(items, s, tw);
+  k_mv_xfwd<T><<<dim3(max_y_in, n), 512, sm, st>>>(items, s, tw); count_launch();
   launch_ypass<T>(yitems, n, Y_MULCONJ_INV, max_log2Mx, max_log2My, s, tw, st);
-  k_mv_xinv<T><<<dim3(max_y_out, n), 512, sm, st>>>(items, s, tw);
+  k_mv_xinv<T><<<dim3(max_y_out, n), 512, sm, st>>>(items, s, tw); count_launch();
 }
 
 template <typename T>
@@ -293,7 +293,7 @@ void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int ma
   const int tiles = (H + 1 + TK - 1) / TK;
   const size_t sm = 2 * (size_t)buf * sizeof(Cx<T>);
   set_max_smem((const void*)k_ypass<T>);
-  k_ypass<T><<<dim3(tiles, n), 512, sm, st>>>(items, mode, s, buf, tw);
+  k_ypass<T><<<dim3(tiles, n), 512, sm, st>>>(items, mode, s, buf, tw); count_launch();
 }
 
 template <typename T>
@@ -302,7 +302,7 @@ void launch_spec(const SpecItem<T>* items, const YItem<T>* yitems, int n, int ma
   if (n <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_spec_x<T>);
-  k_spec_x<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw);
+  k_spec_x<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw); count_launch();
   if (max_log2My > 0) launch_ypass<T>(yitems, n, Y_FWD, max_log2Mx, max_log2My, -1, tw, st);
 }
 

@@ -64,16 +64,16 @@ __device__ Cx<T>* rec_forward(Cx<T>* A, Cx<T>* B, int log2H, const Cx<T>* tw) {
 }
 
 // Half spectrum of one column of a compact vector (U_i or V_i): x-pass.
-template <typename T>
-__global__ void __launch_bounds__(512) k_rec_col_fft(const RecColItem<T>* __restrict__ items,
+template <typename T, typename TV>
+__global__ void __launch_bounds__(512) k_rec_col_fft(const RecColItem<T, TV>* __restrict__ items,
                                                      const Cx<T>* __restrict__ tw) {
-  const RecColItem<T> it = items[blockIdx.y];
+  const RecColItem<T, TV> it = items[blockIdx.y];
   const int y = blockIdx.x;
   if (y >= it.ncols) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
   RSmem<T> sm(smem, H);
-  rec_load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, it.vec, it.map, y, sm.pre, sm.wt);
+  rec_load_col<T, TV>(reinterpret_cast<T*>(sm.A), 2 * H, it.vec, it.map, y, sm.pre, sm.wt);
   Cx<T>* G = rec_forward(sm.A, sm.B, log2H, tw);
   Cx<T>* dst = it.dst + (int64_t)y * (H + 1);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) dst[k] = G[k];
@@ -81,16 +81,16 @@ __global__ void __launch_bounds__(512) k_rec_col_fft(const RecColItem<T>* __rest
 
 // Series: one CTA per (group, channel).  acc = sum_i (sigma_i / Mx) F(U'_i) F(V'_i)
 // then inverse, divide by w, NaN where w = 0.
-template <typename T>
-__global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T>* __restrict__ items, const Cx<T>* __restrict__ tw) {
-  const Rec1Item<T> it = items[blockIdx.x];
+template <typename T, typename TV>
+__global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T, TV>* __restrict__ items, const Cx<T>* __restrict__ tw) {
+  const Rec1Item<T, TV> it = items[blockIdx.x];
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
   RSmem<T> sm(smem, H);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = cx(T(0), T(0));
   for (int c = 0; c < it.ncomp; ++c) {
     const int i = it.comps[c];
-    rec_load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, it.V + it.ldv * i, it.map, 0, sm.pre, sm.wt);
+    rec_load_col<T, TV>(reinterpret_cast<T*>(sm.A), 2 * H, it.V + it.ldv * i, it.map, 0, sm.pre, sm.wt);
     Cx<T>* G = rec_forward(sm.A, sm.B, log2H, tw);
     const Cx<T>* gu = it.gu + it.ldgu * i;
     const T sc = (T)(it.sigma[i] * it.inv_norm);
@@ -148,21 +148,21 @@ static inline size_t rsmem_bytes(int log2Mx, size_t csz) {
   return 3 * (H + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
 }
 
-template <typename T>
-void launch_rec_col_fft(const RecColItem<T>* items, int n, int max_log2Mx, int max_cols, const Cx<T>* tw,
+template <typename T, typename TV>
+void launch_rec_col_fft(const RecColItem<T, TV>* items, int n, int max_log2Mx, int max_cols, const Cx<T>* tw,
                         cudaStream_t st) {
   if (n <= 0) return;
   size_t sm = rsmem_bytes(max_log2Mx, sizeof(Cx<T>));
-  set_max_smem((const void*)k_rec_col_fft<T>);
-  k_rec_col_fft<T><<<dim3(max_cols, n), 512, sm, st>>>(items, tw);
+  set_max_smem((const void*)k_rec_col_fft<T, TV>);
+  k_rec_col_fft<T, TV><<<dim3(max_cols, n), 512, sm, st>>>(items, tw); count_launch();
 }
 
-template <typename T>
-void launch_rec1d(const Rec1Item<T>* items, int n, int max_log2Mx, const Cx<T>* tw, cudaStream_t st) {
+template <typename T, typename TV>
+void launch_rec1d(const Rec1Item<T, TV>* items, int n, int max_log2Mx, const Cx<T>* tw, cudaStream_t st) {
   if (n <= 0) return;
   size_t sm = rsmem_bytes(max_log2Mx, sizeof(Cx<T>));
-  set_max_smem((const void*)k_rec1d<T>);
-  k_rec1d<T><<<n, 512, sm, st>>>(items, tw);
+  set_max_smem((const void*)k_rec1d<T, TV>);
+  k_rec1d<T, TV><<<n, 512, sm, st>>>(items, tw); count_launch();
 }
 
 template <typename T>
@@ -171,21 +171,23 @@ void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny
   if (n <= 0) return;
   size_t sm = rsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_rec_xinv<T>);
-  k_rec_xinv<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw);
+  k_rec_xinv<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw); count_launch();
 }
 
 void launch_residual(const void* data, int data_double, const int32_t* w, int64_t n, const double* groups,
                      int64_t gstride, int ngroups, double* out, cudaStream_t st) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
-  k_residual<<<blocks, 256, 0, st>>>(data, data_double, w, n, groups, gstride, ngroups, out);
+  k_residual<<<blocks, 256, 0, st>>>(data, data_double, w, n, groups, gstride, ngroups, out); count_launch();
 }
 
-#define INST(T)                                                                                        \
-  template void launch_rec_col_fft<T>(const RecColItem<T>*, int, int, int, const Cx<T>*, cudaStream_t); \
-  template void launch_rec1d<T>(const Rec1Item<T>*, int, int, const Cx<T>*, cudaStream_t);              \
-  template void launch_rec_xinv<T>(const Rec2Item<T>*, int, int, int, const Cx<T>*, cudaStream_t);
-INST(float)
-INST(double)
+#define INST(T, TV)                                                                                       \
+  template void launch_rec_col_fft<T, TV>(const RecColItem<T, TV>*, int, int, int, const Cx<T>*, cudaStream_t); \
+  template void launch_rec1d<T, TV>(const Rec1Item<T, TV>*, int, int, const Cx<T>*, cudaStream_t);
+INST(float, float)
+INST(double, float)
+INST(double, double)
+template void launch_rec_xinv<float>(const Rec2Item<float>*, int, int, int, const Cx<float>*, cudaStream_t);
+template void launch_rec_xinv<double>(const Rec2Item<double>*, int, int, int, const Cx<double>*, cudaStream_t);
 
 }  // namespace ssa

@@ -10,6 +10,7 @@
 // All sets are stored as per-column bit masks (bit x of column y).
 #include "common.cuh"
 #include "shape.h"
+#include "launch.h"
 
 namespace ssa {
 
@@ -145,25 +146,25 @@ __global__ void k_weights(const uint32_t* kbits, int kwords, int kcols, const ui
 void launch_obs_bits(const void* data, int data_double, const uint8_t* mask, int nx, int ny, int words,
                      uint32_t* bits, int* err, cudaStream_t st) {
   dim3 g((nx + 255) / 256, ny);
-  k_obs_bits<<<g, 256, 0, st>>>(data, data_double, mask, nx, ny, words, bits, err);
+  k_obs_bits<<<g, 256, 0, st>>>(data, data_double, mask, nx, ny, words, bits, err); count_launch();
 }
 
 void launch_origins(const uint32_t* obs, int nwords_obs, const uint32_t* wrows, int wwords, int ey, int cx,
                     int cy, int kwords, uint32_t* kbits, cudaStream_t st) {
   dim3 g((cx + 255) / 256, cy);
-  k_origins<<<g, 256, 0, st>>>(obs, nwords_obs, wrows, wwords, ey, cx, cy, kwords, kbits);
+  k_origins<<<g, 256, 0, st>>>(obs, nwords_obs, wrows, wwords, ey, cx, cy, kwords, kbits); count_launch();
 }
 
 void launch_col_counts(const uint32_t* bits, int words, int ncols, int32_t* cnt, int32_t* colbase,
                        cudaStream_t st) {
-  k_col_popc<<<ncols, 256, 0, st>>>(bits, words, ncols, cnt);
-  k_scan_counts<<<1, 1024, 0, st>>>(cnt, ncols, colbase);
+  k_col_popc<<<ncols, 256, 0, st>>>(bits, words, ncols, cnt); count_launch();
+  k_scan_counts<<<1, 1024, 0, st>>>(cnt, ncols, colbase); count_launch();
 }
 
 void launch_weights(const uint32_t* kbits, int kwords, int kcols, const uint32_t* rrows, int rwords, int ex,
                     int ey, int nx, int ny, int32_t* w, uint32_t* nbits, int nwords, cudaStream_t st) {
   dim3 g((nx + 255) / 256, ny);
-  k_weights<<<g, 256, 0, st>>>(kbits, kwords, kcols, rrows, rwords, ex, ey, nx, ny, w, nbits, nwords);
+  k_weights<<<g, 256, 0, st>>>(kbits, kwords, kcols, rrows, rwords, ex, ey, nx, ny, w, nbits, nwords); count_launch();
 }
 
 }  // namespace ssa

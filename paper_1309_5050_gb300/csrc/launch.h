@@ -5,6 +5,16 @@
 
 namespace ssa {
 
+// Kernel-launch counter (process-wide) and per-phase device timing.
+void count_launch(int n = 1);
+enum Phase : int { PH_SHAPES = 0, PH_SPECTRUM = 1, PH_MATVEC = 2, PH_SHORT = 3, PH_LONG = 4, PH_RITZ = 5,
+                   PH_RECON = 6, PH_COUNT = 7 };
+struct PhaseScope {
+  int ph; cudaStream_t st; void* a; long long l0;
+  PhaseScope(int ph, cudaStream_t st);
+  ~PhaseScope();
+};
+
 // Lift the dynamic shared-memory limit of a kernel to the device maximum
 // (once per kernel and device).
 void set_max_smem(const void* fn);

@@ -6,18 +6,18 @@
 namespace ssa {
 
 // x-pass transform of columns of one compact vector (U_i or V_i slice).
-template <typename T>
+template <typename T, typename TV>
 struct RecColItem {
-  const T* vec;          // compact vector
+  const TV* vec;         // compact vector
   MapDev map;            // its grid positions
   Cx<T>* dst;            // (H+1) x ncols half spectra
   int32_t log2Mx, ncols; // grid columns to transform
 };
 
 // Series reconstruction of one (group, channel).
-template <typename T>
+template <typename T, typename TV>
 struct Rec1Item {
-  const T* V; int64_t ldv;     // channel slice of the factor vectors (column i at V + ldv*i)
+  const TV* V; int64_t ldv;     // channel slice of the factor vectors (column i at V + ldv*i)
   MapDev map;                  // the channel's origin set
   const Cx<T>* gu; int64_t ldgu;  // F(U'_i) at gu + ldgu*i
   const double* sigma;         // device
@@ -38,11 +38,11 @@ struct Rec2Item {
   double inv_norm;             // 1 / (Mx My)
 };
 
-template <typename T>
-void launch_rec_col_fft(const RecColItem<T>* items, int n, int max_log2Mx, int max_cols, const Cx<T>* tw,
+template <typename T, typename TV>
+void launch_rec_col_fft(const RecColItem<T, TV>* items, int n, int max_log2Mx, int max_cols, const Cx<T>* tw,
                         cudaStream_t st);
-template <typename T>
-void launch_rec1d(const Rec1Item<T>* items, int n, int max_log2Mx, const Cx<T>* tw, cudaStream_t st);
+template <typename T, typename TV>
+void launch_rec1d(const Rec1Item<T, TV>* items, int n, int max_log2Mx, const Cx<T>* tw, cudaStream_t st);
 template <typename T>
 void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny, const Cx<T>* tw,
                      cudaStream_t st);

@@ -26,12 +26,12 @@ import workloads as W  # noqa: E402
 from oracle import ssa_oracle as O  # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-TOL_SIG = {"fp32": 1e-5, "fp64": 1e-10}
+TOL_SIG = {"fp32": 1e-5, "fp64": 1e-9}
 TOL_REC = {"fp32": 1e-4, "fp64": 1e-9}
 TOL_MV = {"fp32": 5e-6, "fp64": 1e-13}
 
 
-def gap_groups(sig, min_gap=1.03):
+def gap_groups(sig, min_gap=1.1):
     """Split 0..len-1 at the boundaries where sigma drops by >= min_gap."""
     groups, cur = [], [0]
     for i in range(1, len(sig)):
