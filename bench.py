@@ -197,7 +197,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(inputs, outs, prec):
-        ps = [pkg.SSA.multi_concat(x, l, CFG["L"], stream=stream) for x, (l, _) in zip(inputs, probs)]
+        ps = pkg.embed_multi_batch(inputs, [l for l, _ in probs], CFG["L"], stream=stream)
         pkg.decompose_batch(ps, CFG["rank"], prec)
         if outs[0].is_cuda:
             pkg.reconstruct_batch(ps, GROUPS, residual=True, outs=outs)

@@ -119,6 +119,17 @@ typedef struct {
 int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out);
 
 /*
+ * ssa_embed_batch -- ssa_embed for n inputs (ins[i] with window wins[i]) in
+ * one pass: the shape kernels of all inputs are launched back to back and the
+ * host waits twice for the whole batch.  outs (host array of n) receives the
+ * contexts (NULL where an input failed); status (may be NULL) each code.
+ * Returns the first non-OK code.  All contexts share cuda_stream (NULL: each
+ * gets its own).
+ */
+int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, void* cuda_stream, ssa_ctx** outs,
+                    int32_t* status);
+
+/*
  * ssa_decompose -- Step 2 (Sec. 2.1, eq. mmexp): the r leading eigentriples
  * (sigma_i, U_i, V_i) of the trajectory matrix, by Golub-Kahan-Lanczos
  * bidiagonalisation on FFT products (Sec. 6.1.2 Alg. hmul_u; Sec. 6.2.2) with

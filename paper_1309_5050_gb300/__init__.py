@@ -14,7 +14,7 @@ from . import _lib as L
 from ._lib import (SSA_1D, SSA_2D, SSA_F32, SSA_F64, SSA_MSSA,  # noqa: F401
                    SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64, SSAError)
 
-__all__ = ["SSA", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
+__all__ = ["SSA", "embed_multi_batch", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
            "load", "SSAError", "PREC"]
 
 PREC = {"fp32": SSA_PREC_FP32FFT_FP64REORTH, "fp64": SSA_PREC_FP64}
@@ -75,6 +75,15 @@ class SSA:
         self.layout = layout            # ("1d", n) | ("mssa", lengths) | ("2d", nx, ny)
         self.rank = 0
         del keep
+
+    @classmethod
+    def _wrap(cls, ctx, layout):
+        obj = cls.__new__(cls)
+        obj._lib = L.load()
+        obj.ctx = ctx
+        obj.layout = layout
+        obj.rank = 0
+        return obj
 
     # ----------------------------------------------------------- builders
     @classmethod
@@ -244,6 +253,29 @@ class SSA:
             self.close()
         except Exception:
             pass
+
+
+def embed_multi_batch(flats, lengths, L_: int, stream=None):
+    """Batched MSSA embed of n problems: flats[i] holds problem i's series
+    concatenated (numpy array or torch tensor, host or device), lengths[i]
+    their lengths.  Returns n SSA objects."""
+    lib = L.load()
+    n = len(flats)
+    ins = (L.ssa_input * n)()
+    wins = (L.ssa_window * n)()
+    keep = []
+    for i, (f, ln) in enumerate(zip(flats, lengths)):
+        ptr, dev, kp, code = _buf(f)
+        lens = np.ascontiguousarray(ln, dtype=np.int64)
+        keep.append((kp, lens))
+        ins[i] = L.ssa_input(kind=SSA_MSSA, dtype=code, on_device=dev, n_series=len(lens), data=ptr,
+                             lengths=lens.ctypes.data_as(C.POINTER(C.c_int64)))
+        wins[i] = L.ssa_window(L=L_)
+    outs = (C.c_void_p * n)()
+    st = (C.c_int32 * n)()
+    L.check(lib.ssa_embed_batch(ins, wins, n, _stream_ptr(stream), outs, st), "ssa_embed_batch")
+    return [SSA._wrap(C.c_void_p(outs[i]), ("mssa", np.asarray(lengths[i], dtype=np.int64).copy()))
+            for i in range(n)]
 
 
 def decompose_batch(problems, rank, prec: str = "fp32", krylov_dim: int = 0, tol: float = 0.0, seed: int = 0,

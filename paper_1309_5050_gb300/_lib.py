@@ -18,7 +18,7 @@ SSA_F32, SSA_F64 = 0, 1
 SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64 = 0, 1
 
 EXPORTS = [
-    "ssa_embed", "ssa_decompose", "ssa_decompose_batch", "ssa_get_info", "ssa_get_sigma",
+    "ssa_embed", "ssa_embed_batch", "ssa_decompose", "ssa_decompose_batch", "ssa_get_info", "ssa_get_sigma",
     "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_get_shape", "ssa_matvec",
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
     "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
@@ -70,6 +70,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib = C.CDLL(path)
     P = C.c_void_p
     lib.ssa_embed.argtypes = [C.POINTER(ssa_input), C.POINTER(ssa_window), P, C.POINTER(P)]
+    lib.ssa_embed_batch.argtypes = [C.POINTER(ssa_input), C.POINTER(ssa_window), C.c_int32, P, C.POINTER(P),
+                                    C.POINTER(C.c_int32)]
     lib.ssa_decompose.argtypes = [P, C.POINTER(ssa_params)]
     lib.ssa_decompose_batch.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(ssa_params), C.POINTER(C.c_int32)]
     lib.ssa_get_info.argtypes = [P, C.POINTER(ssa_info)]

@@ -143,6 +143,14 @@ static int ensure_tables(int dev) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_tables.count(dev)) return SSA_OK;
   DevTables t;
+  // keep memory that contexts free cached in this process's stream-ordered
+  // pool (the default releases it at every synchronisation, and mapping it
+  // again costs milliseconds per context)
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   CU(cudaMalloc(&t.t32, sizeof(Cx<float>) * TW_N));
   CU(cudaMalloc(&t.t64, sizeof(Cx<double>) * TW_N));
   k_twiddles<<<64, 256>>>(t.t32, t.t64); count_launch();
@@ -157,7 +165,7 @@ template <> const Cx<double>* twiddles<double>(int dev) { return g_tables[dev].t
 
 // small helper kernels of the driver
 __global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int max_restarts, int full) {
-  st->full = full; st->pad_ = 0;
+  st->full = full; st->sweeps = 0;
   st->j0 = 0; st->k = k; st->r = r; st->kk = kk; st->active = 1; st->converged = 0;
   st->nconv = 0; st->breakdown = 0; st->restarts = 0; st->max_restarts = max_restarts;
   st->beta_k = 0.0; st->anorm = 0.0; st->tol = tol; st->sigma1 = 0.0; st->maxres = 0.0;
@@ -176,6 +184,10 @@ template <typename TO, typename TI>
 __global__ void k_convert(const TI* in, TO* out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (TO)in[i];
+}
+
+__global__ void k_gather_states(LzState* const* src, int n, LzState* dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = *src[i];
 }
 
 __global__ void k_kmask(const uint32_t* kbits, int kwords, int cx, int cy, int nx, int ny, uint8_t* out) {
@@ -269,10 +281,16 @@ struct ssa_ctx {
   int wwords = 0;
   int64_t L = 0, K = 0;
   Workspace ws;
-  std::vector<std::pair<void*, size_t>> allocs;   // everything owned
+  std::vector<std::pair<void*, size_t>> allocs;   // device allocations owned
   int64_t bytes = 0;
+  // Buffers with one lifetime are carved from one allocation (an arena):
+  // many small stream-ordered allocations per context cost far more than the
+  // work they hold.  A request that does not fit falls back to its own block.
+  struct Arena { char* base = nullptr; size_t cap = 0, used = 0; };
+  Arena embed_arena, spec_arena[2], ws_arena;
+  Arena* cur = nullptr;
 
-  int alloc(void** p, size_t n) {
+  int raw_alloc(void** p, size_t n) {
     if (n == 0) n = 16;
     cudaError_t e = cudaMallocAsync(p, n, stream);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? SSA_ENOMEM : SSA_ECUDA,
@@ -281,8 +299,24 @@ struct ssa_ctx {
     bytes += (int64_t)n;
     return SSA_OK;
   }
+  int make_arena(Arena& a, size_t cap) {
+    if (a.base) release(a.base);
+    a = Arena();
+    TRY(raw_alloc((void**)&a.base, cap));
+    a.cap = cap;
+    return SSA_OK;
+  }
+  int alloc(void** p, size_t n) {
+    n = (std::max<size_t>(n, 16) + 255) & ~size_t(255);
+    if (cur && cur->base && cur->used + n <= cur->cap) {
+      *p = cur->base + cur->used;
+      cur->used += n;
+      return SSA_OK;
+    }
+    return raw_alloc(p, n);
+  }
   template <typename X> int allocT(X** p, size_t count) { return alloc((void**)p, count * sizeof(X)); }
-  void release(void* p) {
+  void release(void* p) {   // arena pieces are freed with their arena
     for (size_t i = 0; i < allocs.size(); ++i)
       if (allocs[i].first == p) {
         cudaFreeAsync(p, stream);
@@ -293,30 +327,90 @@ struct ssa_ctx {
   }
 };
 
+static inline size_t rnd256(size_t n) { return ((n ? n : 16) + 255) & ~size_t(255); }
+
+// Small host-to-device uploads (work items, window rows) go through a pinned
+// ring buffer: a copy from pageable memory would make the driver wait for the
+// stream, serialising every context set-up behind the work queued before it.
+// A region of the ring is rewritten only after the event recorded behind its
+// previous copy has completed.
+struct PinnedRing {
+  char* base = nullptr;
+  size_t cap = 0, head = 0;
+  struct Use { size_t a, b; cudaEvent_t ev; };
+  std::vector<Use> inflight;      // oldest first
+  std::vector<cudaEvent_t> spare;
+  ~PinnedRing() {
+    for (auto& u : inflight) cudaEventDestroy(u.ev);
+    for (auto e : spare) cudaEventDestroy(e);
+    if (base) cudaFreeHost(base);
+  }
+  int copy(void* dst, const void* src, size_t n, cudaStream_t st) {
+    if (n == 0) return SSA_OK;
+    const size_t need = (n + 255) & ~size_t(255);
+    if (!base || need > cap) {
+      if (need > (size_t(8) << 20))   // large: plain copy
+        return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess ? SSA_OK : SSA_ECUDA;
+      if (!base) {
+        cap = size_t(32) << 20;
+        if (cudaHostAlloc((void**)&base, cap, cudaHostAllocDefault) != cudaSuccess) {
+          base = nullptr; cap = 0;
+          return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess ? SSA_OK : SSA_ECUDA;
+        }
+      }
+    }
+    if (head + need > cap) head = 0;
+    const size_t a = head, b = head + need;
+    while (!inflight.empty()) {       // wait for older copies still reading [a, b)
+      const Use& u = inflight.front();
+      if (u.b <= a || u.a >= b) break;
+      cudaEventSynchronize(u.ev);
+      spare.push_back(u.ev);
+      inflight.erase(inflight.begin());
+    }
+    std::memcpy(base + a, src, n);
+    if (cudaMemcpyAsync(dst, base + a, n, cudaMemcpyHostToDevice, st) != cudaSuccess) return SSA_ECUDA;
+    cudaEvent_t ev;
+    if (!spare.empty()) { ev = spare.back(); spare.pop_back(); }
+    else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return SSA_ECUDA;
+    cudaEventRecord(ev, st);
+    inflight.push_back({a, b, ev});
+    head = b;
+    return SSA_OK;
+  }
+};
+static thread_local PinnedRing g_ring;
+
 // upload a small host array into ctx-owned device memory
 template <typename X>
 static int upload(ssa_ctx* c, const std::vector<X>& h, X** d) {
   TRY(c->allocT(d, std::max<size_t>(h.size(), 1)));
-  if (!h.empty()) CU(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(X), cudaMemcpyHostToDevice, c->stream));
+  if (!h.empty() && g_ring.copy(*d, h.data(), h.size() * sizeof(X), c->stream) != SSA_OK)
+    return fail(SSA_ECUDA, "upload of %zu bytes failed", h.size() * sizeof(X));
   return SSA_OK;
 }
 
 // ============================================================== shapes
-static int build_set_counts(ssa_ctx* c, ShapeSet& s) {
-  // colbase of a bit-row set (device) and its total count (synchronous read)
+// Shapes are computed in three host stages so that a batch of contexts needs
+// two stream synchronisations in all: stage 1 launches the window / observed /
+// origin bit rows and their counts (totals staged to pinned host memory),
+// stage 2 reads the counts and launches the weights, stage 3 checks flags.
+static int launch_set_counts(ssa_ctx* c, ShapeSet& s, int32_t* pinned_total) {
   TRY(c->allocT(&s.cnt, (size_t)s.by + 1));
   TRY(c->allocT(&s.colbase, (size_t)s.by + 1));
   launch_col_counts(s.bits, s.words, s.by, s.cnt, s.colbase, c->stream);
   CU(cudaGetLastError());
-  int32_t tot = 0;
-  CU(cudaMemcpyAsync(&tot, s.colbase + s.by, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  s.count = tot;
+  CU(cudaMemcpyAsync(pinned_total, s.colbase + s.by, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
   return SSA_OK;
 }
 
-static int embed_shapes(ssa_ctx* c, const ssa_window* win) {
-  // window rows
+// pinned slots per context: [0] L, [1 + q] K of channel q, [1 + s] error flag
+static size_t embed_slots(const ssa_ctx* c) { return c->ch.size() + 2; }
+
+struct EmbedTmp { int* derr = nullptr; };
+
+static int embed_stage1(ssa_ctx* c, const ssa_window* win, int32_t* pin, EmbedTmp& tmp) {
+  PhaseScope ps_(PH_SHAPES, c->stream);
   int ex, ey;
   std::vector<uint8_t> wm;
   if (c->kind == SSA_2D) {
@@ -327,18 +421,18 @@ static int embed_shapes(ssa_ctx* c, const ssa_window* win) {
     ex = (int)win->L; ey = 1;
     wm.assign((size_t)ex, 1);
   }
-  // trim empty border rows / columns of the window mask (its bounding box)
+  const int ldm = ex;
+  // the window mask's bounding box must start at its first row and column
   int x0 = ex, x1 = -1, y0 = ey, y1 = -1;
   for (int y = 0; y < ey; ++y)
     for (int x = 0; x < ex; ++x)
-      if (wm[x + (size_t)ex * y]) { x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y); }
+      if (wm[x + (size_t)ldm * y]) { x0 = std::min(x0, x); x1 = std::max(x1, x); y0 = std::min(y0, y); y1 = std::max(y1, y); }
   if (x1 < 0) return fail(SSA_EINVAL, "window mask is empty");
   if (x0 != 0 || y0 != 0) return fail(SSA_EINVAL, "window mask must touch its first row and column");
   ex = x1 + 1; ey = y1 + 1;
   bool full = true;
   for (int y = 0; y < ey; ++y)
-    for (int x = 0; x < ex; ++x) full &= wm[x + (size_t)(c->kind == SSA_2D ? win->lx : ex) * y] != 0;
-  const int ldm = (c->kind == SSA_2D) ? (int)win->lx : ex;
+    for (int x = 0; x < ex; ++x) full &= wm[x + (size_t)ldm * y] != 0;
   c->ex = ex; c->ey = ey;
   c->wwords = (ex + 31) / 32;
   std::vector<uint32_t> rows((size_t)ey * c->wwords, 0u), rrows((size_t)ey * c->wwords, 0u);
@@ -355,42 +449,50 @@ static int embed_shapes(ssa_ctx* c, const ssa_window* win) {
   Ls.bx = ex; Ls.by = ey; Ls.words = c->wwords;
   Ls.dense = full;
   Ls.bits = c->wrows;
-  TRY(build_set_counts(c, Ls));
-  c->L = Ls.count;
-
-  PhaseScope ps_(PH_SHAPES, c->stream);
-  int* derr = nullptr;
-  TRY(c->allocT(&derr, 1));
-  CU(cudaMemsetAsync(derr, 0, sizeof(int), c->stream));
-  c->K = 0;
+  TRY(launch_set_counts(c, Ls, &pin[0]));
+  TRY(c->allocT(&tmp.derr, 1));
+  CU(cudaMemsetAsync(tmp.derr, 0, sizeof(int), c->stream));
+  const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
   for (size_t q = 0; q < c->ch.size(); ++q) {
     Channel& h = c->ch[q];
     h.nwords = (int)((h.nx + 31) / 32);
     TRY(c->allocT(&h.obs, (size_t)h.ny * h.nwords));
-    const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
     const void* dptr = (const char*)c->data + h.data_off * esz;
-    launch_obs_bits(dptr, c->dtype == SSA_F64, nullptr, (int)h.nx, (int)h.ny, h.nwords, h.obs, derr, c->stream);
+    launch_obs_bits(dptr, c->dtype == SSA_F64, nullptr, (int)h.nx, (int)h.ny, h.nwords, h.obs, tmp.derr, c->stream);
     CU(cudaGetLastError());
     h.cx = (int)(h.nx - ex + 1);
     h.cy = (int)(h.ny - ey + 1);
     ShapeSet& ks = h.K;
     if (h.cx <= 0 || h.cy <= 0) {
       ks.bx = 0; ks.by = 0; ks.words = 0; ks.count = 0; ks.dense = true;
+      pin[1 + q] = 0;
     } else {
       ks.bx = h.cx; ks.by = h.cy; ks.words = (h.cx + 31) / 32;
       TRY(c->allocT(&ks.bits, (size_t)ks.by * ks.words));
       launch_origins(h.obs, h.nwords, c->wrows, c->wwords, ey, h.cx, h.cy, ks.words, ks.bits, c->stream);
       CU(cudaGetLastError());
-      TRY(build_set_counts(c, ks));
-      ks.dense = (ks.count == (int64_t)h.cx * h.cy);
+      TRY(launch_set_counts(c, ks, &pin[1 + q]));
     }
+  }
+  return SSA_OK;
+}
+
+static int embed_stage2(ssa_ctx* c, int32_t* pin, EmbedTmp& tmp) {
+  PhaseScope ps_(PH_SHAPES, c->stream);
+  c->L = pin[0];
+  c->K = 0;
+  for (size_t q = 0; q < c->ch.size(); ++q) {
+    Channel& h = c->ch[q];
+    ShapeSet& ks = h.K;
+    ks.count = pin[1 + q];
+    if (ks.by > 0) ks.dense = (ks.count == (int64_t)h.cx * h.cy);
     h.koff = c->K;
     c->K += ks.count;
     TRY(c->allocT(&h.w, (size_t)(h.nx * h.ny)));
     uint32_t* nb = nullptr;
     TRY(c->allocT(&nb, (size_t)h.ny * h.nwords));
     if (ks.count > 0) {
-      launch_weights(ks.bits, ks.words, ks.by, c->rrows, c->wwords, ex, ey, (int)h.nx, (int)h.ny, h.w, nb,
+      launch_weights(ks.bits, ks.words, ks.by, c->rrows, c->wwords, c->ex, c->ey, (int)h.nx, (int)h.ny, h.w, nb,
                      h.nwords, c->stream);
       CU(cudaGetLastError());
     } else {
@@ -398,13 +500,33 @@ static int embed_shapes(ssa_ctx* c, const ssa_window* win) {
     }
     c->release(nb);
   }
-  int herr = 0;
-  CU(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CU(cudaStreamSynchronize(c->stream));
-  c->release(derr);
-  if (herr) return fail(SSA_EINVAL, "input holds +-Inf at an observed position");
+  CU(cudaMemcpyAsync(&pin[1 + c->ch.size()], tmp.derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  return SSA_OK;
+}
+
+static int embed_stage3(ssa_ctx* c, int32_t* pin, EmbedTmp& tmp) {
+  c->release(tmp.derr);
+  tmp.derr = nullptr;
+  c->cur = nullptr;
+  if (pin[1 + c->ch.size()]) return fail(SSA_EINVAL, "input holds +-Inf at an observed position");
   if (c->K <= 0) return fail(SSA_EEMPTY, "no window origin keeps the whole window inside the observed set");
   return SSA_OK;
+}
+
+// growable pinned staging buffer (per host thread)
+static int32_t* pinned_slots(size_t n) {
+  static thread_local int32_t* buf = nullptr;
+  static thread_local size_t cap = 0;
+  if (n > cap) {
+    if (buf) cudaFreeHost(buf);
+    size_t nc = std::max<size_t>(n, 1024);
+    if (cudaHostAlloc((void**)&buf, nc * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+      buf = nullptr; cap = 0;
+      return nullptr;
+    }
+    cap = nc;
+  }
+  return buf;
 }
 
 // ============================================================== spectrum
@@ -419,7 +541,12 @@ static int ensure_spectrum(ssa_ctx* c) {
   std::vector<SpecItem<T>> items;
   std::vector<YItem<T>> yitems;
   void* g1 = nullptr;
-  if (c->log2My > 0) TRY(c->alloc(&g1, sizeof(Cx<T>) * (size_t)(H + 1) * My * c->ch.size()));
+  if (c->log2My > 0) TRY(c->raw_alloc(&g1, sizeof(Cx<T>) * (size_t)(H + 1) * My * c->ch.size()));
+  ssa_ctx::Arena& ar = c->spec_arena[f32 ? 0 : 1];
+  TRY(c->make_arena(ar, c->ch.size() * rnd256(sizeof(Cx<T>) * (size_t)(H + 1) * My) +
+                            rnd256(sizeof(SpecItem<T>) * c->ch.size()) + rnd256(sizeof(YItem<T>) * c->ch.size())));
+  ssa_ctx::Arena* keep_cur = c->cur;
+  c->cur = &ar;
   const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
   int max_ny = 0;
   for (size_t q = 0; q < c->ch.size(); ++q) {
@@ -448,9 +575,8 @@ static int ensure_spectrum(ssa_ctx* c) {
   TRY(upload(c, items, &di));
   TRY(upload(c, yitems, &dy));
   launch_spec<T>(di, dy, (int)items.size(), c->log2Mx, c->log2My, max_ny, twiddles<T>(c->device), c->stream);
+  c->cur = keep_cur;
   CU(cudaGetLastError());
-  c->release(di);
-  c->release(dy);
   if (g1) c->release(g1);
   return SSA_OK;
 }
@@ -527,11 +653,6 @@ static int default_k(int r, int64_t L, int64_t K, int req) {
 
 template <typename T>
 static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
-  // release a previous workspace
-  void* olds[] = {w.st, w.U, w.V, w.p, w.q, w.parts_s, w.parts_l, w.B, w.P, w.Q, w.sig, w.cpa, w.cpb,
-                  w.np_s, w.np_l, w.g1, w.g2, w.Uo, w.Vo, w.sigma, w.sgn};
-  for (void* o : olds)
-    if (o) c->release(o);
   w = Workspace();
   w.prec = p.prec;
   w.r = p.rank;
@@ -546,6 +667,21 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   w.n_part_s = w.swapped ? 1 : nch;
   w.n_part_l = w.swapped ? nch : 1;
   const size_t k1 = (size_t)w.k + 1;
+  {
+    const size_t cz = std::is_same<T, float>::value ? 4 : 8;
+    size_t need = rnd256(sizeof(LzState)) + rnd256(8 * w.Ls * k1) + rnd256(cz * w.Kl * k1) + rnd256(8 * w.Ls) +
+                  rnd256(cz * w.Kl) + rnd256(cz * w.Ls * w.n_part_s) + rnd256(cz * w.Kl * w.n_part_l) +
+                  3 * rnd256(8 * k1 * k1) + rnd256(8 * k1) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
+                  rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)w.nblk_l) + rnd256(cz * c->L * w.r) +
+                  rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r);
+    if (c->log2My > 0) {
+      const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
+      need += 2 * rnd256(2 * cz * hs * c->ch.size());
+    }
+    TRY(c->make_arena(c->ws_arena, need));
+  }
+  ssa_ctx::Arena* keep_cur = c->cur;
+  c->cur = &c->ws_arena;
   TRY(c->allocT(&w.st, 1));
   TRY(c->allocT(&w.U, (size_t)w.Ls * k1));
   TRY(c->alloc(&w.V, sizeof(T) * (size_t)w.Kl * k1));
@@ -575,6 +711,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   CU(cudaMemsetAsync(w.parts_l, 0, sizeof(T) * (size_t)w.Kl * w.n_part_l, c->stream));
   double tol = p.tol > 0 ? p.tol : (std::is_same<T, float>::value ? 1e-7 : 1e-13);
   int maxr = p.max_restarts > 0 ? p.max_restarts : 40;
+  c->cur = keep_cur;
   k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0); count_launch();
   CU(cudaGetLastError());
   return SSA_OK;
@@ -700,6 +837,23 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
   TRY(finish_set(c0, mvA));
   TRY(finish_set(c0, mvAT));
   const int nl = (int)live.size();
+  // per-cycle state read-back: gather on the device, one pinned copy
+  std::vector<LzState*> stp(nl);
+  for (int i = 0; i < nl; ++i) stp[i] = live[i]->ws.st;
+  LzState** d_stp = nullptr;
+  LzState* d_stg = nullptr;
+  TRY(upload(c0, stp, &d_stp));
+  TRY(c0->allocT(&d_stg, (size_t)nl));
+  static thread_local LzState* h_st = nullptr;
+  static thread_local int h_cap = 0;
+  if (nl > h_cap) {
+    if (h_st) cudaFreeHost(h_st);
+    h_cap = std::max(nl, 256);
+    if (cudaHostAlloc((void**)&h_st, sizeof(LzState) * h_cap, cudaHostAllocDefault) != cudaSuccess) {
+      h_st = nullptr; h_cap = 0;
+      return fail(SSA_ENOMEM, "pinned state buffer");
+    }
+  }
   // start vectors
   { PhaseScope ps_(PH_LONG, st); launch_long_init<T>(d_lg, nl, max_blk_l, st); }
   CU(cudaGetLastError());
@@ -721,9 +875,10 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
     }
     { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
     CU(cudaGetLastError());
-    for (int i = 0; i < nl; ++i)
-      CU(cudaMemcpyAsync(&hst[i], live[i]->ws.st, sizeof(LzState), cudaMemcpyDeviceToHost, st));
+    k_gather_states<<<1, 128, 0, st>>>(d_stp, nl, d_stg); count_launch();
+    CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
     bool any = false;
     for (int i = 0; i < nl; ++i) any |= hst[i].active != 0;
     if (!any) break;
@@ -751,6 +906,7 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
       if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", hst[i].maxres);
     }
   }
+  c0->release(d_stp); c0->release(d_stg);
   c0->release(d_sh); c0->release(d_lg); c0->release(d_sv); c0->release(d_rz); c0->release(d_fi);
   c0->release(mvA.d_items); c0->release(mvA.d_y); c0->release(mvAT.d_items); c0->release(mvAT.d_y);
   for (auto e : evs) cudaEventDestroy(e);
@@ -873,8 +1029,9 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
         allc.push_back(a); allc.push_back(b);
         ally.push_back(ya); ally.push_back(yb);
       }
-      CU(cudaMemcpyAsync(d_cu, allc.data(), sizeof(RecColItem<T, TV>) * allc.size(), cudaMemcpyHostToDevice, st));
-      CU(cudaMemcpyAsync(d_yu, ally.data(), sizeof(YItem<T>) * ally.size(), cudaMemcpyHostToDevice, st));
+      if (g_ring.copy(d_cu, allc.data(), sizeof(RecColItem<T, TV>) * allc.size(), st) != SSA_OK ||
+          g_ring.copy(d_yu, ally.data(), sizeof(YItem<T>) * ally.size(), st) != SSA_OK)
+        return fail(SSA_ECUDA, "item upload failed");
       for (int i = 0; i < r; ++i) {
         if (group_of[i] < 0) continue;
         launch_rec_col_fft<T, TV>(d_cu + 2 * i, 1, c->log2Mx, c->ey, tw, st);
@@ -969,55 +1126,7 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
   return SSA_OK;
 }
 
-// ============================================================== C ABI
-extern "C" {
-
-const char* ssa_version(void) { return "ssa-gb300 0.1 (sm_103a)"; }
-
-const char* ssa_strerror(int code) {
-  switch (code) {
-    case SSA_OK: return "ok";
-    case SSA_EINVAL: return "invalid argument";
-    case SSA_EEMPTY: return "empty origin set";
-    case SSA_ERANK: return "rank out of range";
-    case SSA_ENOMEM: return "out of device memory";
-    case SSA_ENOTCONV: return "not converged";
-    case SSA_ETIMEOUT: return "timeout";
-    case SSA_ECUDA: return "CUDA error";
-    case SSA_ESTATE: return "call out of order";
-    case SSA_EUNSUPPORTED: return "unsupported size";
-  }
-  return "unknown error";
-}
-
-const char* ssa_last_error(void) { return g_err; }
-
-int ssa_profile_enable(int32_t on) {
-  std::lock_guard<std::mutex> lk(g_prof.mu);
-  g_prof.on = on != 0;
-  return SSA_OK;
-}
-
-int ssa_profile_reset(void) {
-  std::lock_guard<std::mutex> lk(g_prof.mu);
-  g_prof.resolve();
-  for (int i = 0; i < PH_COUNT; ++i) { g_prof.ms[i] = 0.0; g_prof.launches[i] = 0; g_prof.calls[i] = 0; }
-  return SSA_OK;
-}
-
-int ssa_profile_read(int32_t phase, double* ms, int64_t* launches, int64_t* calls) {
-  if (phase < 0 || phase >= PH_COUNT) return fail(SSA_EINVAL, "phase %d", phase);
-  std::lock_guard<std::mutex> lk(g_prof.mu);
-  g_prof.resolve();
-  if (ms) *ms = g_prof.ms[phase];
-  if (launches) *launches = g_prof.launches[phase];
-  if (calls) *calls = g_prof.calls[phase];
-  return SSA_OK;
-}
-
-int64_t ssa_kernel_launches(void) { return (int64_t)g_launches.load(); }
-
-int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out) {
+static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out) {
   if (!in || !win || !out || !in->data) return fail(SSA_EINVAL, "null argument");
   *out = nullptr;
   if (in->dtype != SSA_F32 && in->dtype != SSA_F64) return fail(SSA_EINVAL, "dtype must be SSA_F32 or SSA_F64");
@@ -1071,6 +1180,22 @@ int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa
   if (c->log2My > 12) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along y exceeds 4096", (long long)(1ll << c->log2My)));
   // data (and mask) to the device; masked samples become NaN in the device copy
   const size_t esz = in->dtype == SSA_F64 ? 8 : 4;
+  {
+    // one arena for everything the embedding keeps (sizes from the geometry)
+    const size_t lx = in->kind == SSA_2D ? (size_t)win->lx : (size_t)win->L;
+    const size_t ly = in->kind == SSA_2D ? (size_t)win->ly : 1;
+    const size_t ww = (lx + 31) / 32;
+    size_t need = rnd256(esz * c->total) + (in->mask ? rnd256(c->total) : 0) + 2 * rnd256(ly * ww * 4) +
+                  2 * rnd256((ly + 1) * 4) + rnd256(4);
+    for (auto& h : c->ch) {
+      const size_t nw = (h.nx + 31) / 32;
+      const size_t cy = h.ny, kw = nw;
+      need += rnd256(h.ny * nw * 4) * 2 + rnd256(cy * kw * 4) + 2 * rnd256((cy + 1) * 4) + rnd256(h.nx * h.ny * 4);
+    }
+    int rc0 = c->make_arena(c->embed_arena, need);
+    if (rc0) return bail(rc0);
+    c->cur = &c->embed_arena;
+  }
   int rc = c->alloc(&c->data, esz * (size_t)c->total);
   if (rc) return bail(rc);
   if (cudaMemcpyAsync(c->data, in->data, esz * c->total, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -1088,11 +1213,102 @@ int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa
     launch_apply_mask(c->data, in->dtype == SSA_F64, dm, c->total, c->stream);
     c->release(dm);
   }
-  rc = embed_shapes(c, win);
-  if (rc) return bail(rc);
-  CU(cudaStreamSynchronize(c->stream));
   *out = c;
   return SSA_OK;
+}
+
+
+// ============================================================== C ABI
+extern "C" {
+
+const char* ssa_version(void) { return "ssa-gb300 0.1 (sm_103a)"; }
+
+const char* ssa_strerror(int code) {
+  switch (code) {
+    case SSA_OK: return "ok";
+    case SSA_EINVAL: return "invalid argument";
+    case SSA_EEMPTY: return "empty origin set";
+    case SSA_ERANK: return "rank out of range";
+    case SSA_ENOMEM: return "out of device memory";
+    case SSA_ENOTCONV: return "not converged";
+    case SSA_ETIMEOUT: return "timeout";
+    case SSA_ECUDA: return "CUDA error";
+    case SSA_ESTATE: return "call out of order";
+    case SSA_EUNSUPPORTED: return "unsupported size";
+  }
+  return "unknown error";
+}
+
+const char* ssa_last_error(void) { return g_err; }
+
+int ssa_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = on != 0;
+  return SSA_OK;
+}
+
+int ssa_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.resolve();
+  for (int i = 0; i < PH_COUNT; ++i) { g_prof.ms[i] = 0.0; g_prof.launches[i] = 0; g_prof.calls[i] = 0; }
+  return SSA_OK;
+}
+
+int ssa_profile_read(int32_t phase, double* ms, int64_t* launches, int64_t* calls) {
+  if (phase < 0 || phase >= PH_COUNT) return fail(SSA_EINVAL, "phase %d", phase);
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.resolve();
+  if (ms) *ms = g_prof.ms[phase];
+  if (launches) *launches = g_prof.launches[phase];
+  if (calls) *calls = g_prof.calls[phase];
+  return SSA_OK;
+}
+
+int64_t ssa_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, void* cuda_stream, ssa_ctx** outs,
+                    int32_t* status) {
+  if (!ins || !wins || !outs || n < 1) return fail(SSA_EINVAL, "null argument");
+  std::vector<int> rc(n, SSA_OK);
+  std::vector<EmbedTmp> tmp(n);
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    outs[i] = nullptr;
+    rc[i] = embed_prepare(&ins[i], &wins[i], cuda_stream, &outs[i]);
+    off[i + 1] = off[i] + (rc[i] == SSA_OK ? embed_slots(outs[i]) : 0);
+  }
+  int32_t* pin = pinned_slots(off[n] + 1);
+  if (!pin) {
+    for (int i = 0; i < n; ++i) ssa_destroy(outs[i]), outs[i] = nullptr;
+    return fail(SSA_ENOMEM, "pinned staging allocation failed");
+  }
+  for (int i = 0; i < n; ++i)
+    if (rc[i] == SSA_OK) rc[i] = embed_stage1(outs[i], &wins[i], pin + off[i], tmp[i]);
+  for (int i = 0; i < n; ++i)
+    if (outs[i]) cudaStreamSynchronize(outs[i]->stream);
+  for (int i = 0; i < n; ++i)
+    if (rc[i] == SSA_OK) rc[i] = embed_stage2(outs[i], pin + off[i], tmp[i]);
+  for (int i = 0; i < n; ++i)
+    if (outs[i]) cudaStreamSynchronize(outs[i]->stream);
+  int first = SSA_OK;
+  for (int i = 0; i < n; ++i) {
+    if (rc[i] == SSA_OK) rc[i] = embed_stage3(outs[i], pin + off[i], tmp[i]);
+    if (rc[i] != SSA_OK) {
+      ssa_destroy(outs[i]);
+      outs[i] = nullptr;
+      if (first == SSA_OK) first = rc[i];
+    }
+    if (status) status[i] = rc[i];
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess && first == SSA_OK) first = fail(SSA_ECUDA, "embed: %s", cudaGetErrorString(e));
+  return first;
+}
+
+int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out) {
+  if (!out) return fail(SSA_EINVAL, "null argument");
+  int32_t st = 0;
+  return ssa_embed_batch(in, win, 1, cuda_stream, out, &st);
 }
 
 int ssa_decompose_batch(ssa_ctx* const* ctxs, int32_t n, const ssa_params* params, int32_t* status) {

@@ -49,31 +49,41 @@ __device__ void block_dots(const double* __restrict__ U, int64_t ldu, int64_t r0
 }
 
 // ------------------------------------------------------------ short side
-// step 1: p = sum(partials) - sum_i B[i,j] u_i ; partial dots U^T p
+// step 1: p = sum of the channel partial products A v_j; partial dots U^T p.
+// The coupling terms beta_{j-1} u_{j-1} (or rho_i u_i after a restart) are
+// not subtracted explicitly: they are exactly the components along U that the
+// first Gram-Schmidt pass removes.
 __global__ void __launch_bounds__(SHORT_RB) k_short1(const ShortItem* __restrict__ items, int s) {
   const ShortItem it = items[blockIdx.y];
   const int j = it.st->j0 + s;
   if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
-  __shared__ double bcol[KMAX + 1];
   __shared__ double pv[SHORT_RB];
-  for (int i = threadIdx.x; i < j; i += blockDim.x) bcol[i] = it.B[i + (int64_t)it.ldb * j];
-  __syncthreads();
   const int64_t r0 = (int64_t)blockIdx.x * SHORT_RB;
   const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
   const int64_t row = r0 + threadIdx.x;
   double val = 0.0;
   if ((int)threadIdx.x < nrows) {
+    // sum of the channel partial products, loads issued four at a time
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int q = 0;
     if (it.parts_double) {
-      const double* pp = (const double*)it.parts;
-      for (int q = 0; q < it.n_part; ++q) val += pp[q * it.part_ld + row];
+      const double* pp = (const double*)it.parts + row;
+      for (; q + 3 < it.n_part; q += 4) {
+        const double x0 = pp[(q + 0) * it.part_ld], x1 = pp[(q + 1) * it.part_ld];
+        const double x2 = pp[(q + 2) * it.part_ld], x3 = pp[(q + 3) * it.part_ld];
+        acc[0] += x0; acc[1] += x1; acc[2] += x2; acc[3] += x3;
+      }
+      for (; q < it.n_part; ++q) acc[0] += pp[q * it.part_ld];
     } else {
-      const float* pp = (const float*)it.parts;
-      for (int q = 0; q < it.n_part; ++q) val += (double)pp[q * it.part_ld + row];
+      const float* pp = (const float*)it.parts + row;
+      for (; q + 3 < it.n_part; q += 4) {
+        const float x0 = pp[(q + 0) * it.part_ld], x1 = pp[(q + 1) * it.part_ld];
+        const float x2 = pp[(q + 2) * it.part_ld], x3 = pp[(q + 3) * it.part_ld];
+        acc[0] += (double)x0; acc[1] += (double)x1; acc[2] += (double)x2; acc[3] += (double)x3;
+      }
+      for (; q < it.n_part; ++q) acc[0] += (double)pp[q * it.part_ld];
     }
-    for (int i = 0; i < j; ++i) {
-      const double b = bcol[i];
-      if (b != 0.0) val -= b * it.U[row + it.ldu * i];
-    }
+    val = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     it.p[row] = val;
   }
   pv[threadIdx.x] = val;
@@ -228,12 +238,20 @@ __global__ void __launch_bounds__(256) k_long2(const LongItem<T>* __restrict__ i
 }
 
 // ------------------------------------------------------------ small SVD
-// One-sided Jacobi on the columns of W = B (k x k): W Qm has orthogonal
-// columns; sigma_i = their norms, P_i = column / sigma_i.  Round-robin pair
-// order, one warp per pair.  Residuals beta_k |P[k-1, i]| decide convergence.
+// One-sided (Hestenes) Jacobi on the columns of W = B (k x k): rotate column
+// pairs until all are orthogonal; sigma_i are the final column norms and
+// P_i = W_i / sigma_i the left singular vectors.  The right vectors follow as
+// Q = W0^T P diag(1/sigma) from the original matrix W0.
 // When k equals the short dimension the short basis is complete and
 // A = U_k [B | beta_k e_k] V_{k+1}^T holds exactly, so W gets that extra
 // column and the singular values are exact (no restart needed).
+//
+// GB300 runs FP64 at two lanes per clock per SM, so the work is laid out to
+// spend FP64 only where it counts: one thread owns one column pair of a
+// round-robin round (dot product, rotation parameters, column update), the
+// squared column norms are carried by the exact Jacobi update
+// (a' = a - t g, b' = b + t g) and refreshed once per sweep, and no rotation
+// is accumulated (Q is formed once at the end).
 // Outputs: sig (k), P (k x k, ld ldb), Q ((k+1) x k, ld ldb+1; row k is zero
 // unless the extra column was used).
 __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items) {
@@ -243,60 +261,64 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
   const int k = st->k, ld = it.ldb;
   const bool aug = st->full != 0;
   const int nc = aug ? k + 1 : k;       // columns of W
+  const int cs = k | 1;                 // odd column stride: lane-per-pair accesses spread over banks
   extern __shared__ __align__(16) double sm[];
-  double* W = sm;                        // column c at W + c*k (k rows)
-  double* Qm = W + nc * k;               // column c at Qm + c*nc (nc rows)
+  double* W = sm;                        // column c at W + c*cs (k rows)
   __shared__ int rotated;
-  __shared__ double nrm[KMAX + 1];
-  __shared__ int order[KMAX + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double nrm2[KMAX + 2];
+  __shared__ double nrm[KMAX + 2];
+  __shared__ int order[KMAX + 2];
   for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
     const int c = e / k, i = e - c * k;
     double v;
     if (c < k) v = it.B[i + (int64_t)ld * c];
     else v = (i == k - 1) ? st->beta_k : 0.0;
-    W[e] = v;
-  }
-  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
-    const int c = e / nc, i = e - c * nc;
-    Qm[e] = (i == c) ? 1.0 : 0.0;
+    W[c * cs + i] = v;
   }
   __syncthreads();
   const int n2 = nc + (nc & 1);
+  const double jtol = 2.220446049250313e-16 * (double)(k > 8 ? k : 8);
+  int sweeps = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
+    sweeps = sweep + 1;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const double* w = W + c * cs;
+      double a0 = 0.0, a1 = 0.0;
+      int i = 0;
+      for (; i + 1 < k; i += 2) { a0 = fma(w[i], w[i], a0); a1 = fma(w[i + 1], w[i + 1], a1); }
+      if (i < k) a0 = fma(w[i], w[i], a0);
+      nrm2[c] = a0 + a1;
+    }
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int rd = 0; rd < n2 - 1; ++rd) {
-      for (int t = warp; t < n2 / 2; t += nw) {
+      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
         const int sa = t, sb = n2 - 1 - t;
         const int a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
         const int b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
         if (a >= nc || b >= nc) continue;
-        double* wa = W + a * k;
-        double* wb = W + b * k;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int i = lane; i < k; i += 32) {
-          const double x = wa[i], y = wb[i];
-          al += x * x; be += y * y; ga += x * y;
-        }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+        double* wa = W + a * cs;
+        double* wb = W + b * cs;
+        double g0 = 0.0, g1 = 0.0;
+        int i = 0;
+        for (; i + 1 < k; i += 2) { g0 = fma(wa[i], wb[i], g0); g1 = fma(wa[i + 1], wb[i + 1], g1); }
+        if (i < k) g0 = fma(wa[i], wb[i], g0);
+        const double ga = g0 + g1;
+        const double al = nrm2[a], be = nrm2[b];
+        // a pair is done once its cosine is at the rounding level of a
+        // k-term FP64 dot product (k * eps); tighter never settles.
+        if (ga != 0.0 && fabs(ga) > jtol * sqrt(al * be)) {
           const double zeta = (be - al) / (2.0 * ga);
           const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-          for (int i = lane; i < k; i += 32) {
-            const double x = wa[i], y = wb[i];
-            wa[i] = cs * x - sn * y;
-            wb[i] = sn * x + cs * y;
+          const double cn = rsqrt(1.0 + tt * tt), sn = cn * tt;
+          for (int m = 0; m < k; ++m) {
+            const double x = wa[m], y = wb[m];
+            wa[m] = cn * x - sn * y;
+            wb[m] = sn * x + cn * y;
           }
-          double* qa = Qm + a * nc;
-          double* qb = Qm + b * nc;
-          for (int i = lane; i < nc; i += 32) {
-            const double u = qa[i], v = qb[i];
-            qa[i] = cs * u - sn * v;
-            qb[i] = sn * u + cs * v;
-          }
-          if (lane == 0) rotated = 1;
+          nrm2[a] = al - tt * ga;
+          nrm2[b] = be + tt * ga;
+          rotated = 1;
         }
       }
       __syncthreads();
@@ -305,11 +327,11 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     __syncthreads();
     if (!any) break;
   }
-  for (int c = warp; c < nc; c += nw) {
-    double a = 0.0;
-    for (int i = lane; i < k; i += 32) a += W[c * k + i] * W[c * k + i];
-    a = warp_sum(a);
-    if (lane == 0) nrm[c] = sqrt(a);
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const double* w = W + c * cs;
+    double a0 = 0.0;
+    for (int i = 0; i < k; ++i) a0 = fma(w[i], w[i], a0);
+    nrm[c] = sqrt(a0);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -323,23 +345,40 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
   }
   __syncthreads();
   const int kd = ld, kq = ld + 1;
+  // P_i = W_{o(i)} / sigma_i
   for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
     const int c = e / kd, i = e - c * kd;
     double pv = 0.0;
     if (c < k && i < k) {
       const int o = order[c];
       const double sg = nrm[o];
-      pv = sg > 0.0 ? W[o * k + i] / sg : 0.0;
+      pv = sg > 0.0 ? W[o * cs + i] / sg : 0.0;
     }
     it.P[i + (int64_t)kd * c] = pv;
   }
-  for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
-    const int c = e / kq, i = e - c * kq;
-    double qv = 0.0;
-    if (c < k && i < nc) qv = Qm[order[c] * nc + i];
-    it.Q[i + (int64_t)kq * c] = qv;
-  }
   for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
+  __syncthreads();
+  // Q_i = W0^T P_i / sigma_i with W0 = [B | beta_k e_k] (re-read from global)
+  for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
+    const int c = e / kq, j = e - c * kq;
+    double qv = 0.0;
+    if (c < k && j < nc) {
+      const int o = order[c];
+      const double sg = nrm[o];
+      if (sg > 0.0) {
+        const double* pc = W + o * cs;         // unnormalised P column
+        double acc = 0.0;
+        if (j < k) {
+          const double* bc = it.B + (int64_t)ld * j;
+          for (int m = 0; m <= j && m < k; ++m) acc = fma(bc[m], pc[m], acc);   // B upper triangular
+        } else {
+          acc = st->beta_k * pc[k - 1];
+        }
+        qv = acc / (sg * sg);
+      }
+    }
+    it.Q[j + (int64_t)kq * c] = qv;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     const int r = min(st->r, k);
@@ -350,15 +389,17 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     for (int i = 0; i < r; ++i) {
       const int o = order[i];
       const double sg = nrm[o];
-      const double pk = sg > 0.0 ? W[o * k + (k - 1)] / sg : 0.0;
+      const double pk = sg > 0.0 ? W[o * cs + (k - 1)] / sg : 0.0;
       const double res = aug ? 0.0 : fabs(st->beta_k * pk);
       const double rel = s1 > 0.0 ? res / s1 : 0.0;
       if (rel > mres) mres = rel;
       if (rel <= st->tol) { if (nconv == i) ++nconv; }
       else conv = false;
     }
+    if (st->full) { conv = true; nconv = r; }
     st->sigma1 = s1;
     st->maxres = mres;
+    st->sweeps = sweeps;
     st->nconv = nconv;
     st->converged = conv ? 1 : 0;
     st->restarts += 1;
@@ -518,7 +559,7 @@ void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t
 
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
   if (n <= 0) return;
-  const size_t sm = 2 * (size_t)(kmax + 1) * (kmax + 1) * sizeof(double);
+  const size_t sm = (size_t)(kmax + 1) * (kmax | 1) * sizeof(double);
   set_max_smem((const void*)k_bsvd);
   k_bsvd<<<n, 256, sm, st>>>(items); count_launch();
 }

@@ -17,7 +17,7 @@ struct LzState {
   int32_t restarts;   // restart cycles done
   int32_t max_restarts;
   int32_t full;       // k equals min(L, K): one cycle spans the whole space
-  int32_t pad_;
+  int32_t sweeps;     // Jacobi sweeps of the last small SVD
   double beta_k;      // coupling to the (k+1)-th long vector after k steps
   double anorm;       // largest Lanczos coefficient seen (scale for breakdown)
   double tol;         // residual tolerance relative to sigma_1
