@@ -14,6 +14,7 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ssa.h"
@@ -391,26 +392,22 @@ static int upload(ssa_ctx* c, const std::vector<X>& h, X** d) {
 }
 
 // ============================================================== shapes
-// Shapes are computed in three host stages so that a batch of contexts needs
-// two stream synchronisations in all: stage 1 launches the window / observed /
-// origin bit rows and their counts (totals staged to pinned host memory),
-// stage 2 reads the counts and launches the weights, stage 3 checks flags.
-static int launch_set_counts(ssa_ctx* c, ShapeSet& s, int32_t* pinned_total) {
-  TRY(c->allocT(&s.cnt, (size_t)s.by + 1));
-  TRY(c->allocT(&s.colbase, (size_t)s.by + 1));
-  launch_col_counts(s.bits, s.words, s.by, s.cnt, s.colbase, c->stream);
-  CU(cudaGetLastError());
-  CU(cudaMemcpyAsync(pinned_total, s.colbase + s.by, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
-  return SSA_OK;
-}
+// Shapes for a batch of contexts: stage 1 launches the observed bits, origin
+// bits and their per-column counts for every channel of every context (one
+// launch per kernel kind), stage 2 reads the totals and launches the weights,
+// stage 3 checks the error flags -- two host waits for the whole batch.
+struct EmbedBatch {
+  std::vector<ObsItem> obs;
+  std::vector<OriginItem> org;
+  std::vector<CountItem> cnt;
+  std::vector<WeightItem> wts;
+  int max_nx = 1, max_ny = 1, max_cx = 0, max_cy = 0, max_cols = 1;
+  std::vector<int> cnt_slot_L;                    // per context: count slot of its window set
+  std::vector<std::vector<int>> cnt_slot_K;       // per context and channel (-1: empty)
+};
 
-// pinned slots per context: [0] L, [1 + q] K of channel q, [1 + s] error flag
-static size_t embed_slots(const ssa_ctx* c) { return c->ch.size() + 2; }
-
-struct EmbedTmp { int* derr = nullptr; };
-
-static int embed_stage1(ssa_ctx* c, const ssa_window* win, int32_t* pin, EmbedTmp& tmp) {
-  PhaseScope ps_(PH_SHAPES, c->stream);
+static int embed_stage1(ssa_ctx* c, const ssa_window* win, EmbedBatch& eb, int ci, int32_t* d_totals,
+                        int* d_err) {
   int ex, ey;
   std::vector<uint8_t> wm;
   if (c->kind == SSA_2D) {
@@ -449,66 +446,69 @@ static int embed_stage1(ssa_ctx* c, const ssa_window* win, int32_t* pin, EmbedTm
   Ls.bx = ex; Ls.by = ey; Ls.words = c->wwords;
   Ls.dense = full;
   Ls.bits = c->wrows;
-  TRY(launch_set_counts(c, Ls, &pin[0]));
-  TRY(c->allocT(&tmp.derr, 1));
-  CU(cudaMemsetAsync(tmp.derr, 0, sizeof(int), c->stream));
+  TRY(c->allocT(&Ls.cnt, (size_t)Ls.by + 1));
+  TRY(c->allocT(&Ls.colbase, (size_t)Ls.by + 1));
+  eb.cnt_slot_L[ci] = (int)eb.cnt.size();
+  eb.cnt.push_back({Ls.bits, Ls.words, Ls.by, Ls.cnt, Ls.colbase, d_totals + eb.cnt.size()});
+  eb.max_cols = std::max(eb.max_cols, Ls.by);
   const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
+  eb.cnt_slot_K[ci].assign(c->ch.size(), -1);
   for (size_t q = 0; q < c->ch.size(); ++q) {
     Channel& h = c->ch[q];
     h.nwords = (int)((h.nx + 31) / 32);
     TRY(c->allocT(&h.obs, (size_t)h.ny * h.nwords));
     const void* dptr = (const char*)c->data + h.data_off * esz;
-    launch_obs_bits(dptr, c->dtype == SSA_F64, nullptr, (int)h.nx, (int)h.ny, h.nwords, h.obs, tmp.derr, c->stream);
-    CU(cudaGetLastError());
+    eb.obs.push_back({dptr, c->dtype == SSA_F64, (int)h.nx, (int)h.ny, h.nwords, h.obs, d_err + ci});
+    eb.max_nx = std::max(eb.max_nx, (int)h.nx);
+    eb.max_ny = std::max(eb.max_ny, (int)h.ny);
     h.cx = (int)(h.nx - ex + 1);
     h.cy = (int)(h.ny - ey + 1);
     ShapeSet& ks = h.K;
     if (h.cx <= 0 || h.cy <= 0) {
       ks.bx = 0; ks.by = 0; ks.words = 0; ks.count = 0; ks.dense = true;
-      pin[1 + q] = 0;
     } else {
       ks.bx = h.cx; ks.by = h.cy; ks.words = (h.cx + 31) / 32;
       TRY(c->allocT(&ks.bits, (size_t)ks.by * ks.words));
-      launch_origins(h.obs, h.nwords, c->wrows, c->wwords, ey, h.cx, h.cy, ks.words, ks.bits, c->stream);
-      CU(cudaGetLastError());
-      TRY(launch_set_counts(c, ks, &pin[1 + q]));
+      TRY(c->allocT(&ks.cnt, (size_t)ks.by + 1));
+      TRY(c->allocT(&ks.colbase, (size_t)ks.by + 1));
+      eb.org.push_back({h.obs, h.nwords, c->wwords, c->wrows, ey, h.cx, h.cy, ks.words, ks.bits});
+      eb.max_cx = std::max(eb.max_cx, h.cx);
+      eb.max_cy = std::max(eb.max_cy, h.cy);
+      eb.cnt_slot_K[ci][q] = (int)eb.cnt.size();
+      eb.cnt.push_back({ks.bits, ks.words, ks.by, ks.cnt, ks.colbase, d_totals + eb.cnt.size()});
+      eb.max_cols = std::max(eb.max_cols, ks.by);
     }
+    TRY(c->allocT(&h.w, (size_t)(h.nx * h.ny)));
   }
   return SSA_OK;
 }
 
-static int embed_stage2(ssa_ctx* c, int32_t* pin, EmbedTmp& tmp) {
-  PhaseScope ps_(PH_SHAPES, c->stream);
-  c->L = pin[0];
+static int embed_stage2(ssa_ctx* c, EmbedBatch& eb, int ci, const int32_t* totals) {
+  c->L = totals[eb.cnt_slot_L[ci]];
   c->K = 0;
   for (size_t q = 0; q < c->ch.size(); ++q) {
     Channel& h = c->ch[q];
     ShapeSet& ks = h.K;
-    ks.count = pin[1 + q];
+    const int slot = eb.cnt_slot_K[ci][q];
+    ks.count = slot >= 0 ? totals[slot] : 0;
     if (ks.by > 0) ks.dense = (ks.count == (int64_t)h.cx * h.cy);
     h.koff = c->K;
     c->K += ks.count;
-    TRY(c->allocT(&h.w, (size_t)(h.nx * h.ny)));
     uint32_t* nb = nullptr;
     TRY(c->allocT(&nb, (size_t)h.ny * h.nwords));
     if (ks.count > 0) {
-      launch_weights(ks.bits, ks.words, ks.by, c->rrows, c->wwords, c->ex, c->ey, (int)h.nx, (int)h.ny, h.w, nb,
-                     h.nwords, c->stream);
-      CU(cudaGetLastError());
+      eb.wts.push_back({ks.bits, ks.words, ks.by, c->rrows, c->wwords, c->ex, c->ey, (int)h.nx, (int)h.ny,
+                        h.nwords, h.w, nb});
     } else {
       CU(cudaMemsetAsync(h.w, 0, sizeof(int32_t) * h.nx * h.ny, c->stream));
     }
-    c->release(nb);
   }
-  CU(cudaMemcpyAsync(&pin[1 + c->ch.size()], tmp.derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return SSA_OK;
 }
 
-static int embed_stage3(ssa_ctx* c, int32_t* pin, EmbedTmp& tmp) {
-  c->release(tmp.derr);
-  tmp.derr = nullptr;
+static int embed_stage3(ssa_ctx* c, int err) {
   c->cur = nullptr;
-  if (pin[1 + c->ch.size()]) return fail(SSA_EINVAL, "input holds +-Inf at an observed position");
+  if (err) return fail(SSA_EINVAL, "input holds +-Inf at an observed position");
   if (c->K <= 0) return fail(SSA_EEMPTY, "no window origin keeps the whole window inside the observed set");
   return SSA_OK;
 }
@@ -530,56 +530,84 @@ static int32_t* pinned_slots(size_t n) {
 }
 
 // ============================================================== spectrum
+// Data spectra (Sec. 6.1.2: F(x) is computed once and reused by every
+// product) for every channel of every context that lacks them, in one launch.
 template <typename T>
-static int ensure_spectrum(ssa_ctx* c) {
+static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
   const bool f32 = std::is_same<T, float>::value;
-  bool have = true;
-  for (auto& h : c->ch) have &= (f32 ? h.xh32 : h.xh64) != nullptr;
-  if (have) return SSA_OK;
-  PhaseScope ps_(PH_SPECTRUM, c->stream);
-  const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
   std::vector<SpecItem<T>> items;
   std::vector<YItem<T>> yitems;
-  void* g1 = nullptr;
-  if (c->log2My > 0) TRY(c->raw_alloc(&g1, sizeof(Cx<T>) * (size_t)(H + 1) * My * c->ch.size()));
-  ssa_ctx::Arena& ar = c->spec_arena[f32 ? 0 : 1];
-  TRY(c->make_arena(ar, c->ch.size() * rnd256(sizeof(Cx<T>) * (size_t)(H + 1) * My) +
-                            rnd256(sizeof(SpecItem<T>) * c->ch.size()) + rnd256(sizeof(YItem<T>) * c->ch.size())));
-  ssa_ctx::Arena* keep_cur = c->cur;
-  c->cur = &ar;
-  const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
-  int max_ny = 0;
-  for (size_t q = 0; q < c->ch.size(); ++q) {
-    Channel& h = c->ch[q];
-    void* xh = nullptr;
-    TRY(c->alloc(&xh, sizeof(Cx<T>) * (size_t)(H + 1) * My));
-    (f32 ? h.xh32 : h.xh64) = xh;
-    SpecItem<T> s;
-    s.data = (const char*)c->data + h.data_off * esz;
-    s.obs = h.obs; s.obs_words = h.nwords;
-    s.data_double = c->dtype == SSA_F64;
-    s.nx = (int)h.nx; s.ny = (int)h.ny;
-    s.log2Mx = c->log2Mx; s.log2My = c->log2My;
-    s.g1 = g1 ? (Cx<T>*)g1 + q * (size_t)(H + 1) * My : nullptr;
-    s.xh = (Cx<T>*)xh;
-    s.scale = (T)(1.0 / ((double)(2 * H) * (double)My));
-    items.push_back(s);
-    YItem<T> y;
-    y.src = s.g1; y.dst = s.xh; y.mul = nullptr; y.st = nullptr;
-    y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = (int)h.ny; y.out_hi = My; y.scale = T(0);
-    yitems.push_back(y);
-    max_ny = std::max(max_ny, (int)h.ny);
+  std::vector<std::pair<ssa_ctx*, void*>> scratch;
+  int max_ny = 1, max_log2Mx = 1, max_log2My = 0;
+  for (int i = 0; i < n; ++i) {
+    ssa_ctx* c = cs[i];
+    bool have = true;
+    for (auto& h : c->ch) have &= (f32 ? h.xh32 : h.xh64) != nullptr;
+    if (have) continue;
+    cudaStream_t keep = c->stream;
+    c->stream = st;
+    const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
+    void* g1 = nullptr;
+    if (c->log2My > 0) {
+      TRY(c->raw_alloc(&g1, sizeof(Cx<T>) * (size_t)(H + 1) * My * c->ch.size()));
+      scratch.push_back({c, g1});
+    }
+    ssa_ctx::Arena& ar = c->spec_arena[f32 ? 0 : 1];
+    TRY(c->make_arena(ar, c->ch.size() * rnd256(sizeof(Cx<T>) * (size_t)(H + 1) * My)));
+    ssa_ctx::Arena* keep_cur = c->cur;
+    c->cur = &ar;
+    const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
+    for (size_t q = 0; q < c->ch.size(); ++q) {
+      Channel& h = c->ch[q];
+      void* xh = nullptr;
+      TRY(c->alloc(&xh, sizeof(Cx<T>) * (size_t)(H + 1) * My));
+      (f32 ? h.xh32 : h.xh64) = xh;
+      SpecItem<T> sp;
+      sp.data = (const char*)c->data + h.data_off * esz;
+      sp.obs = h.obs; sp.obs_words = h.nwords;
+      sp.data_double = c->dtype == SSA_F64;
+      sp.nx = (int)h.nx; sp.ny = (int)h.ny;
+      sp.log2Mx = c->log2Mx; sp.log2My = c->log2My;
+      sp.g1 = g1 ? (Cx<T>*)g1 + q * (size_t)(H + 1) * My : nullptr;
+      sp.xh = (Cx<T>*)xh;
+      sp.scale = (T)(1.0 / ((double)(2 * H) * (double)My));
+      items.push_back(sp);
+      YItem<T> y;
+      y.src = sp.g1; y.dst = sp.xh; y.mul = nullptr; y.st = nullptr;
+      y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = (int)h.ny; y.out_hi = My; y.scale = T(0);
+      yitems.push_back(y);
+      max_ny = std::max(max_ny, (int)h.ny);
+    }
+    max_log2Mx = std::max(max_log2Mx, c->log2Mx);
+    max_log2My = std::max(max_log2My, c->log2My);
+    c->cur = keep_cur;
+    c->stream = keep;
   }
+  if (items.empty()) return SSA_OK;
+  PhaseScope ps_(PH_SPECTRUM, st);
   SpecItem<T>* di = nullptr;
   YItem<T>* dy = nullptr;
-  TRY(upload(c, items, &di));
-  TRY(upload(c, yitems, &dy));
-  launch_spec<T>(di, dy, (int)items.size(), c->log2Mx, c->log2My, max_ny, twiddles<T>(c->device), c->stream);
-  c->cur = keep_cur;
+  if (cudaMallocAsync((void**)&di, sizeof(SpecItem<T>) * items.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&dy, sizeof(YItem<T>) * yitems.size(), st) != cudaSuccess)
+    return fail(SSA_ENOMEM, "spectrum items");
+  if (g_ring.copy(di, items.data(), sizeof(SpecItem<T>) * items.size(), st) != SSA_OK ||
+      g_ring.copy(dy, yitems.data(), sizeof(YItem<T>) * yitems.size(), st) != SSA_OK)
+    return fail(SSA_ECUDA, "spectrum item upload");
+  launch_spec<T>(di, dy, (int)items.size(), max_log2Mx, max_log2My, max_ny, twiddles<T>(cs[0]->device), st);
   CU(cudaGetLastError());
-  if (g1) c->release(g1);
+  cudaFreeAsync(di, st);
+  cudaFreeAsync(dy, st);
+  for (auto& sc : scratch) {
+    cudaStream_t keep = sc.first->stream;
+    sc.first->stream = st;
+    sc.first->release(sc.second);
+    sc.first->stream = keep;
+  }
   return SSA_OK;
 }
+
+template <typename T>
+static int ensure_spectrum(ssa_ctx* c) { return ensure_spectra<T>(&c, 1, c->stream); }
 
 // ============================================================== matvec items
 // Direction "X" maps K -> L (sum over channels); "XT" maps L -> K (slices).
@@ -732,6 +760,12 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
       evs.push_back(e);
     }
   std::vector<int> ok(n, 1);
+  {
+    std::vector<ssa_ctx*> need;
+    for (int i = 0; i < n; ++i)
+      if (ps[i].rank >= 1 && ps[i].rank <= std::min(cs[i]->L, cs[i]->K)) need.push_back(cs[i]);
+    if (!need.empty()) TRY(ensure_spectra<T>(need.data(), (int)need.size(), st));
+  }
   for (int i = 0; i < n; ++i) {
     ssa_ctx* c = cs[i];
     const ssa_params& p = ps[i];
@@ -741,8 +775,7 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
     if (rc == SSA_OK) {
       cudaStream_t keep = c->stream;
       c->stream = st;
-      rc = ensure_spectrum<T>(c);
-      if (rc == SSA_OK) rc = alloc_ws<T>(c, p, c->ws);
+      rc = alloc_ws<T>(c, p, c->ws);
       c->stream = keep;
     }
     if (status) status[i] = rc;
@@ -1062,18 +1095,28 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
       CU(cudaGetLastError());
     }
   }
-  // residual and copy-out
-  for (int p = 0; p < n; ++p) {
-    ssa_ctx* c = cs[p];
-    if (residual) {
+  // residual (one launch for every channel of every problem) and copy-out
+  if (residual) {
+    std::vector<ResItem> ri;
+    int64_t max_n = 1;
+    for (int p = 0; p < n; ++p) {
+      ssa_ctx* c = cs[p];
+      const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
       for (size_t q = 0; q < c->ch.size(); ++q) {
         const Channel& h = c->ch[q];
-        const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
-        launch_residual((const char*)c->data + h.data_off * esz, c->dtype == SSA_F64, h.w, h.nx * h.ny,
-                        dout[p] + h.data_off, c->total, ng, dout[p] + (size_t)ng * c->total + h.data_off, st);
+        ri.push_back({(const char*)c->data + h.data_off * esz, c->dtype == SSA_F64, ng, h.w,
+                      dout[p] + h.data_off, c->total, h.nx * h.ny, dout[p] + (size_t)ng * c->total + h.data_off});
+        max_n = std::max<int64_t>(max_n, h.nx * h.ny);
       }
-      CU(cudaGetLastError());
     }
+    ResItem* d_ri = nullptr;
+    TRY(upload(c0, ri, &d_ri));
+    tmp.push_back(d_ri);
+    launch_residual_batch(d_ri, (int)ri.size(), max_n, st);
+    CU(cudaGetLastError());
+  }
+  for (int p = 0; p < n; ++p) {
+    ssa_ctx* c = cs[p];
     if (!on_device)
       CU(cudaMemcpyAsync(outs[p], dout[p], sizeof(double) * (size_t)c->total * nout, cudaMemcpyDeviceToHost, st));
   }
@@ -1269,40 +1312,88 @@ int64_t ssa_kernel_launches(void) { return (int64_t)g_launches.load(); }
 int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, void* cuda_stream, ssa_ctx** outs,
                     int32_t* status) {
   if (!ins || !wins || !outs || n < 1) return fail(SSA_EINVAL, "null argument");
+  // one stream for the whole batch: the caller's, or one shared per host thread
+  static thread_local cudaStream_t own = nullptr;
+  void* bs = cuda_stream;
+  if (!bs && n > 1) {
+    if (!own && cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(SSA_ECUDA, "stream creation failed");
+    bs = (void*)own;
+  }
   std::vector<int> rc(n, SSA_OK);
-  std::vector<EmbedTmp> tmp(n);
-  std::vector<size_t> off(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     outs[i] = nullptr;
-    rc[i] = embed_prepare(&ins[i], &wins[i], cuda_stream, &outs[i]);
-    off[i + 1] = off[i] + (rc[i] == SSA_OK ? embed_slots(outs[i]) : 0);
+    rc[i] = embed_prepare(&ins[i], &wins[i], bs, &outs[i]);
   }
-  int32_t* pin = pinned_slots(off[n] + 1);
-  if (!pin) {
-    for (int i = 0; i < n; ++i) ssa_destroy(outs[i]), outs[i] = nullptr;
-    return fail(SSA_ENOMEM, "pinned staging allocation failed");
-  }
+  cudaStream_t st = nullptr;
   for (int i = 0; i < n; ++i)
-    if (rc[i] == SSA_OK) rc[i] = embed_stage1(outs[i], &wins[i], pin + off[i], tmp[i]);
-  for (int i = 0; i < n; ++i)
-    if (outs[i]) cudaStreamSynchronize(outs[i]->stream);
-  for (int i = 0; i < n; ++i)
-    if (rc[i] == SSA_OK) rc[i] = embed_stage2(outs[i], pin + off[i], tmp[i]);
-  for (int i = 0; i < n; ++i)
-    if (outs[i]) cudaStreamSynchronize(outs[i]->stream);
+    if (outs[i]) { st = outs[i]->stream; break; }
   int first = SSA_OK;
-  for (int i = 0; i < n; ++i) {
-    if (rc[i] == SSA_OK) rc[i] = embed_stage3(outs[i], pin + off[i], tmp[i]);
-    if (rc[i] != SSA_OK) {
-      ssa_destroy(outs[i]);
-      outs[i] = nullptr;
-      if (first == SSA_OK) first = rc[i];
+  auto finish = [&]() {
+    for (int i = 0; i < n; ++i) {
+      if (rc[i] != SSA_OK) {
+        if (outs[i]) ssa_destroy(outs[i]);
+        outs[i] = nullptr;
+        if (first == SSA_OK) first = rc[i];
+      }
+      if (status) status[i] = rc[i];
     }
-    if (status) status[i] = rc[i];
-  }
+    return first;
+  };
+  if (!st) return finish();
+  // batch scratch: totals and error flags (device) + pinned mirrors
+  size_t ncount = 0;
+  for (int i = 0; i < n; ++i)
+    if (outs[i]) ncount += outs[i]->ch.size() + 1;
+  int32_t* d_tot = nullptr;
+  int* d_err = nullptr;
+  if (cudaMallocAsync((void**)&d_tot, sizeof(int32_t) * (ncount + 1), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&d_err, sizeof(int) * n, st) != cudaSuccess)
+    return fail(SSA_ENOMEM, "embed scratch");
+  cudaMemsetAsync(d_err, 0, sizeof(int) * n, st);
+  int32_t* pin = pinned_slots(ncount + n + 1);
+  if (!pin) return fail(SSA_ENOMEM, "pinned staging allocation failed");
+  EmbedBatch eb;
+  eb.cnt_slot_L.assign(n, -1);
+  eb.cnt_slot_K.resize(n);
+  PhaseScope ps_(PH_SHAPES, st);
+  for (int i = 0; i < n; ++i)
+    if (rc[i] == SSA_OK) rc[i] = embed_stage1(outs[i], &wins[i], eb, i, d_tot, d_err);
+  ObsItem* d_obs = nullptr; OriginItem* d_org = nullptr; CountItem* d_cnt = nullptr; WeightItem* d_wts = nullptr;
+  auto upload_raw = [&](auto& vec, auto** dptr) -> int {
+    typedef typename std::remove_reference<decltype(vec[0])>::type X;
+    if (cudaMallocAsync((void**)dptr, sizeof(X) * std::max<size_t>(vec.size(), 1), st) != cudaSuccess) return SSA_ENOMEM;
+    if (!vec.empty() && g_ring.copy(*dptr, vec.data(), sizeof(X) * vec.size(), st) != SSA_OK) return SSA_ECUDA;
+    return SSA_OK;
+  };
+  int urc = upload_raw(eb.obs, &d_obs);
+  if (urc == SSA_OK) urc = upload_raw(eb.org, &d_org);
+  if (urc == SSA_OK) urc = upload_raw(eb.cnt, &d_cnt);
+  if (urc != SSA_OK) return fail(urc, "embed item upload");
+  launch_obs_batch(d_obs, (int)eb.obs.size(), eb.max_nx, eb.max_ny, st);
+  launch_origins_batch(d_org, (int)eb.org.size(), eb.max_cx, eb.max_cy, st);
+  launch_counts_batch(d_cnt, (int)eb.cnt.size(), eb.max_cols, st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(pin, d_tot, sizeof(int32_t) * std::max<size_t>(ncount, 1), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  std::vector<int32_t> totals(pin, pin + ncount);
+  for (int i = 0; i < n; ++i)
+    if (rc[i] == SSA_OK) rc[i] = embed_stage2(outs[i], eb, i, totals.data());
+  urc = upload_raw(eb.wts, &d_wts);
+  if (urc != SSA_OK) return fail(urc, "embed item upload");
+  int wnx = 1, wny = 1;
+  for (auto& w : eb.wts) { wnx = std::max(wnx, w.nx); wny = std::max(wny, w.ny); }
+  launch_weights_batch(d_wts, (int)eb.wts.size(), wnx, wny, st);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(pin, d_err, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i)
+    if (rc[i] == SSA_OK) rc[i] = embed_stage3(outs[i], pin[i]);
+  cudaFreeAsync(d_tot, st); cudaFreeAsync(d_err, st);
+  cudaFreeAsync(d_obs, st); cudaFreeAsync(d_org, st); cudaFreeAsync(d_cnt, st); cudaFreeAsync(d_wts, st);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess && first == SSA_OK) first = fail(SSA_ECUDA, "embed: %s", cudaGetErrorString(e));
-  return first;
+  if (e != cudaSuccess) return fail(SSA_ECUDA, "embed: %s", cudaGetErrorString(e));
+  return finish();
 }
 
 int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out) {

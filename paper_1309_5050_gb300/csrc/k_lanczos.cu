@@ -291,31 +291,61 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     }
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
+    // A team of 4 lanes owns one column pair (rows interleaved over the team);
+    // teams fill whole warps (pair t -> warp t / 8, team t % 8), so a round's
+    // FP64 instructions run with full warps on every scheduler of the SM.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int team = lane >> 2, q = lane & 3;
+    const int nteams = (blockDim.x >> 5) * 8;
     for (int rd = 0; rd < n2 - 1; ++rd) {
-      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
-        const int sa = t, sb = n2 - 1 - t;
-        const int a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
-        const int b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
-        if (a >= nc || b >= nc) continue;
-        double* wa = W + a * cs;
-        double* wb = W + b * cs;
+      for (int t0 = warp * 8; t0 < n2 / 2; t0 += nteams) {
+        const int t = t0 + team;
+        int a = -1, b = -1;
+        if (t < n2 / 2) {
+          const int sa = t, sb = n2 - 1 - t;
+          a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
+          b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
+          if (a >= nc || b >= nc) a = b = -1;
+        }
+        double* __restrict__ wa = W + (a < 0 ? 0 : a) * cs;
+        double* __restrict__ wb = W + (b < 0 ? 0 : b) * cs;
         double g0 = 0.0, g1 = 0.0;
-        int i = 0;
-        for (; i + 1 < k; i += 2) { g0 = fma(wa[i], wb[i], g0); g1 = fma(wa[i + 1], wb[i + 1], g1); }
-        if (i < k) g0 = fma(wa[i], wb[i], g0);
-        const double ga = g0 + g1;
-        const double al = nrm2[a], be = nrm2[b];
-        // a pair is done once its cosine is at the rounding level of a
-        // k-term FP64 dot product (k * eps); tighter never settles.
-        if (ga != 0.0 && fabs(ga) > jtol * sqrt(al * be)) {
+        if (a >= 0) {
+          int i = q;
+          for (; i + 4 < k; i += 8) { g0 = fma(wa[i], wb[i], g0); g1 = fma(wa[i + 4], wb[i + 4], g1); }
+          for (; i < k; i += 4) g0 = fma(wa[i], wb[i], g0);
+        }
+        double ga = g0 + g1;
+        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+        bool rot = false;
+        double tt = 0.0, al = 0.0, be = 0.0;
+        if (a >= 0) {
+          al = nrm2[a];
+          be = nrm2[b];
+          // a pair is done once its cosine is at the rounding level of a
+          // k-term FP64 dot product (k * eps); tighter never settles.
+          rot = ga != 0.0 && fabs(ga) > jtol * sqrt(al * be);
+        }
+        if (rot) {
           const double zeta = (be - al) / (2.0 * ga);
-          const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double cn = rsqrt(1.0 + tt * tt), sn = cn * tt;
-          for (int m = 0; m < k; ++m) {
+          int m = q;
+          for (; m + 4 < k; m += 8) {
+            const double x0 = wa[m], x1 = wa[m + 4];
+            const double y0 = wb[m], y1 = wb[m + 4];
+            wa[m] = cn * x0 - sn * y0; wa[m + 4] = cn * x1 - sn * y1;
+            wb[m] = sn * x0 + cn * y0; wb[m + 4] = sn * x1 + cn * y1;
+          }
+          for (; m < k; m += 4) {
             const double x = wa[m], y = wb[m];
             wa[m] = cn * x - sn * y;
             wb[m] = sn * x + cn * y;
           }
+        }
+        __syncwarp();   // every lane of the team has read the old norms
+        if (rot && q == 0) {
           nrm2[a] = al - tt * ga;
           nrm2[b] = be + tt * ga;
           rotated = 1;
@@ -425,14 +455,21 @@ __global__ void k_restart(const SvdItem* __restrict__ items) {
 }
 
 // ------------------------------------------------------------ Ritz vectors
-// In place, by row blocks: basis[:, 0:kk] <- basis[:, 0:k] C[0:k, 0:kk];
-// on a restart the long basis also moves column k to column kk.
+// In place, by row blocks: basis[:, 0:kk] <- basis[:, 0:kc] C[0:kc, 0:kk]
+// (kc = k on the short side, k + 1 on the long side, whose coefficients carry
+// the extra row of the complete-basis case); on a restart the long basis also
+// moves column k to column kk.  A CTA stages its RB rows and the coefficients
+// in shared memory; thread (tx, ty) of 8 x 32 accumulates rows ty + 32a and
+// columns tx + 8m (a < RB/32, m < 8) in registers, so every shared load feeds
+// several FMAs and each warp writes 32 consecutive rows of a column.
 template <typename T, bool SHORT>
-__global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, int final_pass, int rows_per) {
+__global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, int final_pass) {
+  typedef typename std::conditional<SHORT, double, T>::type E;
+  constexpr int RB = (sizeof(E) == 8) ? 64 : 128;
+  constexpr int RA = RB / 32;
   const RitzItem<T> it = items[blockIdx.y];
   const LzState* st = it.st;
   if (!final_pass && !st->active) return;
-  typedef typename std::conditional<SHORT, double, T>::type E;
   const int k = st->k;
   const int kk = final_pass ? min(st->r, k) : st->kk;
   const bool move = !SHORT && !final_pass;
@@ -440,32 +477,59 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   const int64_t ldb = SHORT ? it.ldu : it.ldv;
   const int64_t nrow = SHORT ? it.Ls : it.Kl;
   const double* C = SHORT ? it.P : it.Q;
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per;
-  if (r0 >= nrow) return;
-  const int nr = (int)imin64(rows_per, nrow - r0);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  E* blk = reinterpret_cast<E*>(smraw);               // rows_per x (k+1), column-major
-  E* cf = blk + (int64_t)rows_per * (k + 1);           // kc x kk
-  const int kc = SHORT ? k : k + 1;                    // coefficient rows (Q has k+1)
+  const int kc = SHORT ? k : k + 1;
   const int cld = SHORT ? it.ldc : it.ldc + 1;
+  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  if (r0 >= nrow) return;
+  const int nr = (int)imin64(RB, nrow - r0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  E* blk = reinterpret_cast<E*>(smraw);               // RB x (k+1), column-major
+  const int kkp = ((kk + 7) / 8) * 8;
+  E* cf = blk + (int64_t)RB * (k + 1);                 // kc x kkp, row-major in i
   const int ncol = SHORT ? k : k + 1;
-  for (int e = threadIdx.x; e < ncol * rows_per; e += blockDim.x) {
-    const int c = e / rows_per, t = e - c * rows_per;
-    if (t < nr) blk[e] = basis[r0 + t + ldb * c];
+  for (int e = threadIdx.x; e < ncol * RB; e += blockDim.x) {
+    const int c = e / RB, t = e - c * RB;
+    blk[e] = (t < nr) ? basis[r0 + t + ldb * c] : E(0);
   }
-  for (int e = threadIdx.x; e < kc * kk; e += blockDim.x) {
-    const int c = e / kc, i = e - c * kc;
-    cf[e] = (E)C[i + (int64_t)cld * c];
+  for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
+    const int i = e / kkp, c = e - i * kkp;
+    cf[e] = (c < kk) ? (E)C[i + (int64_t)cld * c] : E(0);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nr * kk; e += blockDim.x) {
-    const int c = e / nr, t = e - c * nr;
-    E acc = E(0);
-    for (int i = 0; i < kc; ++i) acc += blk[t + (int64_t)rows_per * i] * cf[i + kc * c];
-    basis[r0 + t + ldb * c] = acc;
+  const int tx = threadIdx.x >> 5, ty = threadIdx.x & 31;
+  for (int c0 = 0; c0 < kk; c0 += 64) {
+    E acc[RA][8];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+      for (int m = 0; m < 8; ++m) acc[a][m] = E(0);
+    for (int i = 0; i < kc; ++i) {
+      E av[RA], bv[8];
+#pragma unroll
+      for (int a = 0; a < RA; ++a) av[a] = blk[i * RB + ty + 32 * a];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int c = c0 + tx + 8 * m;
+        bv[m] = (c < kkp) ? cf[i * kkp + c] : E(0);
+      }
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int m = 0; m < 8; ++m) acc[a][m] = fma(av[a], bv[m], acc[a][m]);
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int c = c0 + tx + 8 * m;
+      if (c >= kk) continue;
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const int t = ty + 32 * a;
+        if (t < nr) basis[r0 + t + ldb * c] = acc[a][m];
+      }
+    }
   }
   if (move)
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) basis[r0 + t + ldb * kk] = blk[t + (int64_t)rows_per * k];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) basis[r0 + t + ldb * kk] = blk[t + (int64_t)RB * k];
 }
 
 // ------------------------------------------------------------ outputs
@@ -573,13 +637,14 @@ template <typename T>
 void launch_ritz(const RitzItem<T>* items, int n, int kmax, int64_t max_short, int64_t max_long, int final_pass,
                  cudaStream_t st) {
   if (n <= 0) return;
-  const int rs = 64, rl = 128;
-  size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)kmax * kmax * sizeof(double);
-  size_t sml = (size_t)rl * (kmax + 1) * sizeof(T) + (size_t)(kmax + 1) * kmax * sizeof(T);
+  const int rs = 64, rl = (sizeof(T) == 8) ? 64 : 128;
+  const int kp = ((kmax + 7) / 8) * 8;
+  const size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)(kmax + 1) * kp * sizeof(double);
+  const size_t sml = (size_t)rl * (kmax + 2) * sizeof(T) + (size_t)(kmax + 1) * kp * sizeof(T);
   set_max_smem((const void*)k_ritz<T, true>);
   set_max_smem((const void*)k_ritz<T, false>);
-  k_ritz<T, true><<<dim3((unsigned)((max_short + rs - 1) / rs), n), 256, sms, st>>>(items, final_pass, rs); count_launch();
-  k_ritz<T, false><<<dim3((unsigned)((max_long + rl - 1) / rl), n), 256, sml, st>>>(items, final_pass, rl); count_launch();
+  k_ritz<T, true><<<dim3((unsigned)((max_short + rs - 1) / rs), n), 256, sms, st>>>(items, final_pass); count_launch();
+  k_ritz<T, false><<<dim3((unsigned)((max_long + rl - 1) / rl), n), 256, sml, st>>>(items, final_pass); count_launch();
 }
 
 template <typename T>

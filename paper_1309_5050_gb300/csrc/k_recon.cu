@@ -142,6 +142,22 @@ __global__ void k_residual(const void* data, int data_double, const int32_t* w, 
   }
 }
 
+__global__ void k_residual_batch(const ResItem* __restrict__ items) {
+  const ResItem it = items[blockIdx.y];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < it.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (it.w[i] <= 0) { it.out[i] = __longlong_as_double(0x7ff8000000000000ll); continue; }
+    double v = it.data_double ? ((const double*)it.data)[i] : (double)((const float*)it.data)[i];
+    for (int g = 0; g < it.ngroups; ++g) v -= it.groups[g * it.gstride + i];
+    it.out[i] = v;
+  }
+}
+
+void launch_residual_batch(const ResItem* items, int n, int64_t max_n, cudaStream_t st) {
+  if (n <= 0) return;
+  const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, 1024));
+  k_residual_batch<<<dim3(bx, n), 256, 0, st>>>(items); count_launch();
+}
+
 // ---------------------------------------------------------------- launchers
 static inline size_t rsmem_bytes(int log2Mx, size_t csz) {
   const size_t H = size_t(1) << (log2Mx - 1);

@@ -8,6 +8,7 @@
 //  * w  -- w_k = #{(i, j) : l_i (+) k_j = k}, the diagonal-averaging weights
 //          (Alg. qhankelization step 1); N' = {w > 0}.
 // All sets are stored as per-column bit masks (bit x of column y).
+#include <algorithm>
 #include "common.cuh"
 #include "shape.h"
 #include "launch.h"
@@ -140,6 +141,130 @@ __global__ void k_weights(const uint32_t* kbits, int kwords, int kcols, const ui
   const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
   const int wd = x >> 5;
   if ((threadIdx.x & 31) == 0 && wd < nwords) nbits[(int64_t)y * nwords + wd] = bal;
+}
+
+// ---------------------------------------------------------------- batched forms
+__global__ void k_obs_batch(const ObsItem* __restrict__ items) {
+  const ObsItem it = items[blockIdx.z];
+  const int y = blockIdx.y;
+  if (y >= it.ny || (int)blockIdx.x * (int)blockDim.x >= ((it.nx + 31) & ~31)) return;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = false;
+  if (x < it.nx) {
+    const int64_t g = x + (int64_t)it.nx * y;
+    const double v = it.data_double ? ((const double*)it.data)[g] : (double)((const float*)it.data)[g];
+    ok = !isnan(v);
+    if (ok && isinf(v)) { atomicExch(it.err, 1); ok = false; }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, ok);
+  const int w = x >> 5;
+  if ((threadIdx.x & 31) == 0 && w < it.words) it.bits[(int64_t)y * it.words + w] = bal;
+}
+
+__global__ void k_origins_batch(const OriginItem* __restrict__ items) {
+  const OriginItem it = items[blockIdx.z];
+  const int ky = blockIdx.y;
+  if (ky >= it.cy || (int)blockIdx.x * (int)blockDim.x >= ((it.cx + 31) & ~31)) return;
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+  bool in = kx < it.cx;
+  if (in) {
+    for (int ly = 0; ly < it.ey && in; ++ly) {
+      const uint32_t* col = it.obs + (int64_t)(ky + ly) * it.nwords_obs;
+      const uint32_t* wr = it.wrows + (int64_t)ly * it.wwords;
+      for (int t = 0; t < it.wwords; ++t) {
+        const uint32_t wb = wr[t];
+        if (wb == 0u) continue;
+        if (wb & ~extract32(col, it.nwords_obs, kx + 32 * t)) { in = false; break; }
+      }
+    }
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, in);
+  const int w = kx >> 5;
+  if ((threadIdx.x & 31) == 0 && w < it.kwords) it.kbits[(int64_t)ky * it.kwords + w] = bal;
+}
+
+__global__ void k_popc_batch(const CountItem* __restrict__ items) {
+  const CountItem it = items[blockIdx.z];
+  const int y = blockIdx.x;
+  if (y >= it.ncols) return;
+  __shared__ int red[32];
+  int c = 0;
+  for (int w = threadIdx.x; w < it.words; w += blockDim.x) c += __popc(it.bits[(int64_t)y * it.words + w]);
+  const int tot = block_sum_int(c, red);
+  if (threadIdx.x == 0) it.cnt[y] = tot;
+}
+
+__global__ void k_scan_batch(const CountItem* __restrict__ items) {
+  const CountItem it = items[blockIdx.x];
+  __shared__ int wt[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < it.ncols; b0 += blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const int v = i < it.ncols ? it.cnt[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c = carry;
+      for (int w = 0; w < nw; ++w) { const int t = wt[w]; wt[w] = c; c += t; }
+      carry = c;
+    }
+    __syncthreads();
+    if (i < it.ncols) it.colbase[i] = x - v + wt[warp];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { it.colbase[it.ncols] = carry; *it.total = carry; }
+}
+
+__global__ void k_weights_batch(const WeightItem* __restrict__ items) {
+  const WeightItem it = items[blockIdx.z];
+  const int y = blockIdx.y;
+  if (y >= it.ny || (int)blockIdx.x * (int)blockDim.x >= ((it.nx + 31) & ~31)) return;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = 0;
+  if (x < it.nx) {
+    for (int ly = 0; ly < it.ey; ++ly) {
+      const int ky = y - ly;
+      if (ky < 0 || ky >= it.kcols) continue;
+      const uint32_t* col = it.kbits + (int64_t)ky * it.kwords;
+      const uint32_t* rr = it.rrows + (int64_t)ly * it.rwords;
+      const int p0 = x - it.ex + 1;
+      for (int t = 0; t < it.rwords; ++t) {
+        const uint32_t rb = rr[t];
+        if (rb == 0u) continue;
+        cnt += __popc(rb & extract32(col, it.kwords, p0 + 32 * t));
+      }
+    }
+    it.w[x + (int64_t)it.nx * y] = cnt;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, cnt > 0);
+  const int wd = x >> 5;
+  if ((threadIdx.x & 31) == 0 && wd < it.nwords) it.nbits[(int64_t)y * it.nwords + wd] = bal;
+}
+
+void launch_obs_batch(const ObsItem* it, int n, int max_nx, int max_ny, cudaStream_t st) {
+  if (n <= 0) return;
+  k_obs_batch<<<dim3((max_nx + 255) / 256, max_ny, n), 256, 0, st>>>(it); count_launch();
+}
+void launch_origins_batch(const OriginItem* it, int n, int max_cx, int max_cy, cudaStream_t st) {
+  if (n <= 0 || max_cx <= 0 || max_cy <= 0) return;
+  k_origins_batch<<<dim3((max_cx + 255) / 256, max_cy, n), 256, 0, st>>>(it); count_launch();
+}
+void launch_counts_batch(const CountItem* it, int n, int max_cols, cudaStream_t st) {
+  if (n <= 0) return;
+  k_popc_batch<<<dim3(std::max(max_cols, 1), 1, n), 256, 0, st>>>(it); count_launch();
+  k_scan_batch<<<n, 1024, 0, st>>>(it); count_launch();
+}
+void launch_weights_batch(const WeightItem* it, int n, int max_nx, int max_ny, cudaStream_t st) {
+  if (n <= 0) return;
+  k_weights_batch<<<dim3((max_nx + 255) / 256, max_ny, n), 256, 0, st>>>(it); count_launch();
 }
 
 // ---------------------------------------------------------------- launchers

@@ -46,6 +46,12 @@ void launch_rec1d(const Rec1Item<T, TV>* items, int n, int max_log2Mx, const Cx<
 template <typename T>
 void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny, const Cx<T>* tw,
                      cudaStream_t st);
+struct ResItem {                // residual x - sum of groups for one channel
+  const void* data; int32_t data_double, ngroups;
+  const int32_t* w; const double* groups; int64_t gstride, n;
+  double* out;
+};
+void launch_residual_batch(const ResItem* items, int n, int64_t max_n, cudaStream_t st);
 void launch_residual(const void* data, int data_double, const int32_t* w, int64_t n, const double* groups,
                      int64_t gstride, int ngroups, double* out, cudaStream_t st);
 

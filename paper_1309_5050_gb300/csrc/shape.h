@@ -4,6 +4,31 @@
 #include <cuda_runtime.h>
 
 namespace ssa {
+
+// Batched forms: one launch for many grids (blockIdx.z = item).
+struct ObsItem {
+  const void* data; int32_t data_double, nx, ny, words;
+  uint32_t* bits; int* err;
+};
+struct OriginItem {
+  const uint32_t* obs; int32_t nwords_obs; int32_t wwords;
+  const uint32_t* wrows; int32_t ey, cx, cy, kwords;
+  uint32_t* kbits;
+};
+struct CountItem {            // per-column popcounts and their exclusive scan
+  const uint32_t* bits; int32_t words, ncols;
+  int32_t* cnt; int32_t* colbase; int32_t* total;
+};
+struct WeightItem {
+  const uint32_t* kbits; int32_t kwords, kcols;
+  const uint32_t* rrows; int32_t rwords, ex, ey, nx, ny, nwords;
+  int32_t* w; uint32_t* nbits;
+};
+void launch_obs_batch(const ObsItem* it, int n, int max_nx, int max_ny, cudaStream_t st);
+void launch_origins_batch(const OriginItem* it, int n, int max_cx, int max_cy, cudaStream_t st);
+void launch_counts_batch(const CountItem* it, int n, int max_cols, cudaStream_t st);
+void launch_weights_batch(const WeightItem* it, int n, int max_nx, int max_ny, cudaStream_t st);
+
 void launch_obs_bits(const void* data, int data_double, const uint8_t* mask, int nx, int ny, int words,
                      uint32_t* bits, int* err, cudaStream_t st);
 void launch_origins(const uint32_t* obs, int nwords_obs, const uint32_t* wrows, int wwords, int ey, int cx,
