@@ -220,6 +220,31 @@ int ssa_profile_reset(void);
 int ssa_profile_read(int32_t phase, double* ms, int64_t* launches, int64_t* calls);
 int64_t ssa_kernel_launches(void);
 
+/*
+ * ssa_matvec_series_noalloc -- one Hankel trajectory-matrix product of a
+ * single FP32 series, for callers that cannot allocate device memory at call
+ * time (inside a captured CUDA graph region, hosts with a fixed memory budget,
+ * plug-in hosts that keep the allocator to themselves).  The paper has no
+ * counterpart: this is a deployment variant of the FFT product of ssa_matvec.
+ *   x    device, n floats (the series, no missing values)
+ *   L    window length, 1 < L < n; K = n - L + 1
+ *   transpose 0: out = X in  (in: K floats, out: L floats, device)
+ *   transpose 1: out = X^T in (in: L floats, out: K floats, device)
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL = default stream)
+ * The only intermediate data (twiddle table and the series' half spectrum)
+ * live in one fixed device array of about 320 KB that every GPU loading the
+ * library holds until the process exits; n is limited to 16384 samples
+ * (larger returns SSA_EUNSUPPORTED).  The first call on a device looks the
+ * array up and fills its twiddle table (and waits for that): make it before
+ * any stream capture.  Calls share the array, so calls whose work overlaps on
+ * the GPU race; order them on one stream.  Nothing is allocated or freed.
+ * Errors: SSA_EINVAL, SSA_EUNSUPPORTED, SSA_ECUDA; ssa_noalloc_last_error()
+ * gives the detail (static buffer of the calling thread).
+ */
+int ssa_matvec_series_noalloc(const float* x, int64_t n, int64_t L, int32_t transpose, const float* in,
+                              float* out, void* cuda_stream);
+const char* ssa_noalloc_last_error(void);
+
 /* ssa_synchronize -- wait for the context's stream. */
 int ssa_synchronize(ssa_ctx* ctx);
 

@@ -22,6 +22,7 @@ EXPORTS = [
     "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_get_shape", "ssa_matvec",
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
     "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
+    "ssa_matvec_series_noalloc", "ssa_noalloc_last_error",
 ]
 PHASES = ["shapes", "spectrum", "matvec", "short", "long", "ritz", "recon"]
 
@@ -95,6 +96,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.ssa_profile_read.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     lib.ssa_kernel_launches.argtypes = []
     lib.ssa_kernel_launches.restype = C.c_int64
+    lib.ssa_matvec_series_noalloc.argtypes = [P, C.c_int64, C.c_int64, C.c_int32, P, P, P]
+    lib.ssa_noalloc_last_error.argtypes = []
+    lib.ssa_noalloc_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -135,3 +139,16 @@ def profile_read() -> dict:
 
 def kernel_launches() -> int:
     return int(load().ssa_kernel_launches())
+
+
+def matvec_series_noalloc(x, L: int, v, out, transpose: bool = False, stream=None) -> None:
+    """Hankel trajectory-matrix product of one FP32 series without any device
+    allocation (see ssa_matvec_series_noalloc in include/ssa.h).  x, v, out are
+    CUDA float32 tensors owned by the caller."""
+    lib = load()
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib.ssa_matvec_series_noalloc(x.data_ptr(), int(x.numel()), int(L), 1 if transpose else 0,
+                                       v.data_ptr(), out.data_ptr(), sp)
+    if rc != SSA_OK:
+        raise RuntimeError(f"ssa_matvec_series_noalloc: {lib.ssa_strerror(rc).decode()} ({rc}): "
+                           f"{lib.ssa_noalloc_last_error().decode()}")
