@@ -236,6 +236,7 @@ struct ShapeSet {          // a set of grid points as per-column bit rows
 
 struct Channel {
   int64_t nx = 0, ny = 0;
+  int log2M = 0;               // FFT length along x of this channel's products
   int64_t data_off = 0;        // element offset of the channel's data
   ShapeSet K;                  // origins (bounding grid cx x cy)
   int cx = 0, cy = 0;
@@ -258,6 +259,7 @@ struct Workspace {             // Lanczos + results, per precision
   void* parts_s = nullptr; void* parts_l = nullptr;
   int n_part_s = 1, n_part_l = 1;
   double* B = nullptr; double* P = nullptr; double* Q = nullptr; double* sig = nullptr;
+  double* colscale = nullptr;
   double* cpa = nullptr; double* cpb = nullptr; double* np_s = nullptr; double* np_l = nullptr;
   void* g1 = nullptr; void* g2 = nullptr;
   void* Uo = nullptr; void* Vo = nullptr;
@@ -553,24 +555,27 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
       scratch.push_back({c, g1});
     }
     ssa_ctx::Arena& ar = c->spec_arena[f32 ? 0 : 1];
-    TRY(c->make_arena(ar, c->ch.size() * rnd256(sizeof(Cx<T>) * (size_t)(H + 1) * My)));
+    size_t need = 0;
+    for (auto& h : c->ch) need += rnd256(sizeof(Cx<T>) * (size_t)((1 << (h.log2M - 1)) + 1) * My);
+    TRY(c->make_arena(ar, need));
     ssa_ctx::Arena* keep_cur = c->cur;
     c->cur = &ar;
     const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
     for (size_t q = 0; q < c->ch.size(); ++q) {
       Channel& h = c->ch[q];
+      const int Hc = 1 << (h.log2M - 1);
       void* xh = nullptr;
-      TRY(c->alloc(&xh, sizeof(Cx<T>) * (size_t)(H + 1) * My));
+      TRY(c->alloc(&xh, sizeof(Cx<T>) * (size_t)(Hc + 1) * My));
       (f32 ? h.xh32 : h.xh64) = xh;
       SpecItem<T> sp;
       sp.data = (const char*)c->data + h.data_off * esz;
       sp.obs = h.obs; sp.obs_words = h.nwords;
       sp.data_double = c->dtype == SSA_F64;
       sp.nx = (int)h.nx; sp.ny = (int)h.ny;
-      sp.log2Mx = c->log2Mx; sp.log2My = c->log2My;
+      sp.log2Mx = h.log2M; sp.log2My = c->log2My;
       sp.g1 = g1 ? (Cx<T>*)g1 + q * (size_t)(H + 1) * My : nullptr;
       sp.xh = (Cx<T>*)xh;
-      sp.scale = (T)(1.0 / ((double)(2 * H) * (double)My));
+      sp.scale = (T)(1.0 / ((double)(2 * Hc) * (double)My));
       items.push_back(sp);
       YItem<T> y;
       y.src = sp.g1; y.dst = sp.xh; y.mul = nullptr; y.st = nullptr;
@@ -626,10 +631,11 @@ static MvItem<T> make_mv(ssa_ctx* c, const Channel& h, bool XT, VecRef in, int i
   MvItem<T> m;
   m.xh = (const Cx<T>*)(std::is_same<T, float>::value ? h.xh32 : h.xh64);
   m.in = in; m.out = out;
+  m.in_scale = nullptr;
   m.min = XT ? c->Lset.dev() : h.K.dev();
   m.mout = XT ? h.K.dev() : c->Lset.dev();
   m.g1 = g1; m.g2 = g2; m.st = st;
-  m.log2Mx = c->log2Mx; m.log2My = c->log2My;
+  m.log2Mx = h.log2M; m.log2My = c->log2My;
   m.in_type = in_type;
   m.y_in_hi = XT ? c->ey : h.cy;
   m.y_out_hi = XT ? h.cy : c->ey;
@@ -699,7 +705,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
     const size_t cz = std::is_same<T, float>::value ? 4 : 8;
     size_t need = rnd256(sizeof(LzState)) + rnd256(8 * w.Ls * k1) + rnd256(cz * w.Kl * k1) + rnd256(8 * w.Ls) +
                   rnd256(cz * w.Kl) + rnd256(cz * w.Ls * w.n_part_s) + rnd256(cz * w.Kl * w.n_part_l) +
-                  3 * rnd256(8 * k1 * k1) + rnd256(8 * k1) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
+                  3 * rnd256(8 * k1 * k1) + 2 * rnd256(8 * (k1 + 1)) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
                   rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)w.nblk_l) + rnd256(cz * c->L * w.r) +
                   rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r);
     if (c->log2My > 0) {
@@ -721,6 +727,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->allocT(&w.P, (size_t)w.k * w.k));
   TRY(c->allocT(&w.Q, (size_t)(w.k + 1) * w.k));
   TRY(c->allocT(&w.sig, (size_t)w.k));
+  TRY(c->allocT(&w.colscale, (size_t)w.k + 2));
   TRY(c->allocT(&w.cpa, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.cpb, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.np_s, (size_t)w.nblk_s));
@@ -803,15 +810,16 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
     s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
     sh.push_back(s);
     LongItem<T> l;
-    l.st = w.st; l.V = (T*)w.V; l.ldv = w.Kl; l.parts = (const T*)w.parts_l; l.part_ld = w.Kl;
+    l.st = w.st; l.V = (T*)w.V; l.ldv = w.Kl; l.colscale = w.colscale; l.parts = (const T*)w.parts_l; l.part_ld = w.Kl;
     l.n_part = w.n_part_l; l.nblk = w.nblk_l; l.q = (T*)w.q; l.npart = w.np_l; l.B = w.B; l.ldb = w.k;
     l.pad_ = 0; l.Kl = w.Kl; l.seed = ps[i].seed;
     lg.push_back(l);
     SvdItem v;
-    v.st = w.st; v.B = w.B; v.ldb = w.k; v.pad_ = 0; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
+    v.st = w.st; v.B = w.B; v.ldb = w.k; v.pad_ = 0; v.colscale = w.colscale; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
     sv.push_back(v);
     RitzItem<T> z;
     z.st = w.st; z.U = w.U; z.ldu = w.Ls; z.Ls = w.Ls; z.V = (T*)w.V; z.ldv = w.Kl; z.Kl = w.Kl;
+    z.colscale = w.colscale;
     z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.pad_ = 0;
     rz.push_back(z);
     FinalItem<T> f;
@@ -831,6 +839,7 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
         vin.base = w.V; vin.off = h.koff; vin.ld = w.Kl; vin.st = w.st; vin.jdelta = 0;
         vout.base = w.parts_s; vout.off = (int64_t)q * w.Ls; vout.ld = 0; vout.st = nullptr;
         mvA.items.push_back(make_mv<T>(c, h, false, vin, 0, vout, g1, g2, w.st));
+        mvA.items.back().in_scale = w.colscale;
         // A^T u = X^T u : L -> K slice
         vin.base = w.U; vin.off = 0; vin.ld = w.Ls; vin.st = w.st;
         vout.base = w.parts_l; vout.off = h.koff; vout.st = nullptr;
@@ -840,6 +849,7 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
         vin.base = w.V; vin.off = 0; vin.ld = w.Kl; vin.st = w.st;
         vout.base = w.parts_s; vout.off = h.koff; vout.st = nullptr;
         mvA.items.push_back(make_mv<T>(c, h, true, vin, 0, vout, g1, g2, w.st));
+        mvA.items.back().in_scale = w.colscale;
         // A^T u = X u : K -> L partial
         vin.base = w.U; vin.off = h.koff; vin.ld = w.Ls; vin.st = w.st;
         vout.base = w.parts_l; vout.off = (int64_t)q * w.Kl; vout.st = nullptr;
@@ -1220,6 +1230,9 @@ static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_
   c->log2Mx = std::max(ilog2_ceil(mx), 4);
   c->log2My = (in->kind == SSA_2D) ? ilog2_ceil(my) : 0;
   if (c->log2Mx > 14) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along x exceeds 16384", (long long)(1ll << c->log2Mx)));
+  // series of a system each get the shortest grid that holds them (any
+  // M >= N_p gives the same product); images keep the common grid
+  for (auto& h : c->ch) h.log2M = (in->kind == SSA_2D) ? c->log2Mx : std::max(ilog2_ceil(h.nx), 4);
   if (c->log2My > 12) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along y exceeds 4096", (long long)(1ll << c->log2My)));
   // data (and mask) to the device; masked samples become NaN in the device copy
   const size_t esz = in->dtype == SSA_F64 ? 8 : 4;

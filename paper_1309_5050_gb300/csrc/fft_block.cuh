@@ -109,6 +109,145 @@ __device__ Cx<T>* block_fft(Cx<T>* a, Cx<T>* b, int log2n, int nb, const Cx<T>* 
   return a;
 }
 
+// ---------------------------------------------------------------- shared tables
+// Octant twiddle table in shared memory: tab[m] = W_N^m for m in [0, N/8],
+// N = 2^log2N >= 8, copied from the global table (correctly rounded values).
+// Any W_N^j follows exactly: W_N^{qN/4 + m} = (-i)^q W_N^m, and for
+// N/8 < m < N/4, W_N^m = -i conj(W_N^{N/4 - m}) -- sign changes and swaps only.
+template <typename T>
+__device__ __forceinline__ void load_octant(Cx<T>* tab, int log2N, const Cx<T>* __restrict__ tw) {
+  const int n8 = (1 << log2N) >> 3;
+  for (int m = threadIdx.x; m <= n8; m += blockDim.x) tab[m] = tw[(int64_t)m << (TW_LOG - log2N)];
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> tw_oct(const Cx<T>* tab, int log2N, int64_t j) {
+  const int N = 1 << log2N;
+  const int jj = (int)(j & (N - 1));
+  const int q = jj >> (log2N - 2);
+  const int m = jj & ((N >> 2) - 1);
+  Cx<T> w;
+  if (m <= (N >> 3)) {
+    w = tab[m];
+  } else {
+    const Cx<T> t = tab[(N >> 2) - m];
+    w = cx(-t.im, -t.re);
+  }
+  if (q == 1) w = cx(w.im, -w.re);
+  else if (q == 2) w = cx(-w.re, -w.im);
+  else if (q == 3) w = cx(-w.im, w.re);
+  return w;
+}
+
+// Padded shared layout of the intermediate Stockham buffers: one spare slot
+// per 16 elements, so the scattered stores of the early radix-8 stages hit
+// distinct banks.  First-stage loads and last-stage stores stay unpadded
+// (both are already contiguous across a warp).
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
+
+template <typename T, bool INV, int LR, bool PIN, bool POUT>
+__device__ __forceinline__ void stockham_stage_s(const Cx<T>* __restrict__ src, Cx<T>* __restrict__ dst,
+                                                 int log2n, int nb, int sin, int sout, int log2Ns,
+                                                 const Cx<T>* tab, int log2N) {
+  constexpr int R = 1 << LR;
+  const int n = 1 << log2n;
+  const int nq = n >> LR;
+  const int Ns = 1 << log2Ns;
+  const int total = nq * nb;
+  const int tshift = log2N - (log2Ns + LR);    // W_{Ns R}^a = W_N^{a << tshift}
+  for (int jj = threadIdx.x; jj < total; jj += blockDim.x) {
+    const int b = jj >> (log2n - LR);
+    const int j = jj & (nq - 1);
+    const Cx<T>* s = src + b * sin;
+    Cx<T>* d = dst + b * sout;
+    const int k = j & (Ns - 1);
+    Cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = j + r * nq;
+      v[r] = s[PIN ? padi(i) : i];
+    }
+    if (log2Ns > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        Cx<T> w = tw_oct(tab, log2N, ((int64_t)k * r) << tshift);
+        if (INV) w = conj(w);
+        v[r] = v[r] * w;
+      }
+    }
+    if (LR == 3) dft8<T, INV>(v);
+    else if (LR == 2) dft4<T, INV>(v[0], v[1], v[2], v[3]);
+    else dft2<T, INV>(v[0], v[1]);
+    const int base = ((j - k) << LR) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = base + r * Ns;
+      d[POUT ? padi(i) : i] = v[r];
+    }
+  }
+}
+
+// nb transforms of length 2^log2n.  Input: unpadded, transform b at a + b*n.
+// Output (returned buffer): unpadded, transform b at out + b*n.  Both buffers
+// must hold nb * padded_len(n) elements.  Twiddles from the octant table of
+// W_N (N >= n, N >= 8).  Caller syncs before.
+template <typename T, bool INV>
+__device__ Cx<T>* block_fft_s(Cx<T>* a, Cx<T>* b, int log2n, int nb, const Cx<T>* tab, int log2N) {
+  const int n = 1 << log2n;
+  const int sp = padded_len(n);
+  int done = 0;
+  bool first = true;
+  while (done < log2n) {
+    const int rem = log2n - done;
+    const int lr = rem >= 3 ? 3 : rem;
+    const bool last = (done + lr == log2n);
+    const int sin = first ? n : sp, sout = last ? n : sp;
+#define SSA_STAGE(LRV, PI, PO) stockham_stage_s<T, INV, LRV, PI, PO>(a, b, log2n, nb, sin, sout, done, tab, log2N)
+    if (lr == 3) {
+      if (first && last) SSA_STAGE(3, false, false);
+      else if (first) SSA_STAGE(3, false, true);
+      else if (last) SSA_STAGE(3, true, false);
+      else SSA_STAGE(3, true, true);
+    } else if (lr == 2) {
+      if (first && last) SSA_STAGE(2, false, false);
+      else if (first) SSA_STAGE(2, false, true);
+      else if (last) SSA_STAGE(2, true, false);
+      else SSA_STAGE(2, true, true);
+    } else {
+      if (first && last) SSA_STAGE(1, false, false);
+      else if (first) SSA_STAGE(1, false, true);
+      else if (last) SSA_STAGE(1, true, false);
+      else SSA_STAGE(1, true, true);
+    }
+#undef SSA_STAGE
+    done += lr;
+    first = false;
+    __syncthreads();
+    Cx<T>* t = a; a = b; b = t;
+  }
+  return a;
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> untwist_fwd_s(const Cx<T>* Z, int k, int log2H, const Cx<T>* tab) {
+  const int H = 1 << log2H;
+  Cx<T> a = Z[k & (H - 1)];
+  Cx<T> b = conj(Z[(H - k) & (H - 1)]);
+  Cx<T> E = T(0.5) * (a + b);
+  Cx<T> O = T(0.5) * mul_mi(a - b);
+  return E + tw_oct(tab, log2H + 1, k) * O;
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> twist_inv_s(const Cx<T>* P, int k, int log2H, const Cx<T>* tab) {
+  const int H = 1 << log2H;
+  Cx<T> a = P[k];
+  Cx<T> b = conj(P[H - k]);
+  Cx<T> w = conj(tw_oct(tab, log2H + 1, k));
+  return (a + b) + mul_pi(w * (a - b));
+}
+
 // Packed real transform, forward: z[n] = g[2n] + i g[2n+1] (length H) has
 // been transformed to Z; produce the half spectrum G[k], k = 0..H, of the real
 // length-2H signal g:  G[k] = E + W^k O,  E = (Z[k] + conj Z[H-k]) / 2,

@@ -169,8 +169,10 @@ __global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ i
   const int j = it.st->j0 + s;
   if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
   __shared__ double red[32];
-  const double alpha = it.B[j + (int64_t)it.ldb * j];
+  // alpha_j v_j with v_j = colscale[j] * V[:, j] (stored unnormalised)
+  const T coef = (T)(it.B[j + (int64_t)it.ldb * j] * it.colscale[j]);
   const T* vj = it.V + it.ldv * j;
+  T* qn = it.V + it.ldv * (j + 1);
   const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
   double acc = 0.0;
   for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
@@ -178,8 +180,8 @@ __global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ i
     if (row >= it.Kl) break;
     T v = T(0);
     for (int q = 0; q < it.n_part; ++q) v += it.parts[q * it.part_ld + row];
-    v = v - (T)alpha * vj[row];
-    it.q[row] = v;
+    v = v - coef * vj[row];
+    qn[row] = v;
     acc += (double)v * (double)v;
   }
   const double tot = block_sum(acc, red);
@@ -197,43 +199,37 @@ __global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict
     const int64_t row = r0 + t;
     if (row >= it.Kl) break;
     const T v = (T)hash_uniform(it.seed, (uint64_t)row);
-    it.q[row] = v;
+    it.V[row] = v;
     acc += (double)v * (double)v;
   }
   const double tot = block_sum(acc, red);
   if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
 }
 
-// beta_j = ||q||, v_{j+1} = q / beta_j, B[j, j+1] = beta_j (or beta_k at the end)
+// beta_j = ||q|| from the partial norms (fixed order); column j+1 of V keeps q
+// and its scale 1/beta_j is recorded; B[j, j+1] = beta_j (beta_k at the end).
 template <typename T>
-__global__ void __launch_bounds__(256) k_long2(const LongItem<T>* __restrict__ items, int s) {
-  const LongItem<T> it = items[blockIdx.y];
+__global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict__ items, int s) {
+  const LongItem<T> it = items[blockIdx.x];
   LzState* st = it.st;
   const int j = st->j0 + s;
-  if (lz_skip(st, j) || (int)blockIdx.x >= it.nblk) return;
+  if (lz_skip(st, j)) return;
   __shared__ double red[32];
   double a = 0.0;
   for (int b = threadIdx.x; b < it.nblk; b += blockDim.x) a += it.npart[b];
   const double beta = sqrt(block_sum(a, red));
+  if (threadIdx.x != 0) return;
   const bool ok = beta > 1e-200;
-  const T inv = ok ? (T)(1.0 / beta) : T(0);
-  T* dst = it.V + it.ldv * (j + 1);
-  const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
-  for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
-    const int64_t row = r0 + t;
-    if (row >= it.Kl) break;
-    dst[row] = it.q[row] * inv;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && j >= 0) {
-    if (ok) {
-      if (j + 1 < st->k) it.B[j + (int64_t)it.ldb * (j + 1)] = beta;
-      else st->beta_k = beta;
-      if (beta > st->anorm) st->anorm = beta;
-    } else {
-      st->k = j + 1;
-      st->beta_k = 0.0;
-      st->breakdown = 1;
-    }
+  it.colscale[j + 1] = ok ? 1.0 / beta : 0.0;
+  if (j < 0) return;
+  if (ok) {
+    if (j + 1 < st->k) it.B[j + (int64_t)it.ldb * (j + 1)] = beta;
+    else st->beta_k = beta;
+    if (beta > st->anorm) st->anorm = beta;
+  } else {
+    st->k = j + 1;
+    st->beta_k = 0.0;
+    st->breakdown = 1;
   }
 }
 
@@ -450,8 +446,14 @@ __global__ void k_restart(const SvdItem* __restrict__ items) {
     else if (c == kk && i < kk) v = st->beta_k * it.P[(k - 1) + (int64_t)ld * i];
     it.B[e] = v;
   }
+  // Ritz columns 0..kk-1 are unit vectors; column kk holds the old column k
+  for (int c = threadIdx.x; c <= ld; c += blockDim.x)
+    if (c < kk) it.colscale[c] = 1.0;
   __syncthreads();
-  if (threadIdx.x == 0) st->j0 = kk;
+  if (threadIdx.x == 0) {
+    it.colscale[kk] = it.colscale[k];
+    st->j0 = kk;
+  }
 }
 
 // ------------------------------------------------------------ Ritz vectors
@@ -493,7 +495,8 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   }
   for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
     const int i = e / kkp, c = e - i * kkp;
-    cf[e] = (c < kk) ? (E)C[i + (int64_t)cld * c] : E(0);
+    const double sc = SHORT ? 1.0 : it.colscale[i];
+    cf[e] = (c < kk) ? (E)(C[i + (int64_t)cld * c] * sc) : E(0);
   }
   __syncthreads();
   const int tx = threadIdx.x >> 5, ty = threadIdx.x & 31;
@@ -608,17 +611,15 @@ void launch_short_steps(const ShortItem* items, int n, int max_blk, int s, cudaS
 template <typename T>
 void launch_long_step(const LongItem<T>* items, int n, int max_blk, int s, cudaStream_t st) {
   if (n <= 0) return;
-  dim3 g(max_blk, n);
-  k_long1<T><<<g, 256, 0, st>>>(items, s); count_launch();
-  k_long2<T><<<g, 256, 0, st>>>(items, s); count_launch();
+  k_long1<T><<<dim3(max_blk, n), 256, 0, st>>>(items, s); count_launch();
+  k_long_norm<T><<<n, 256, 0, st>>>(items, s); count_launch();
 }
 
 template <typename T>
 void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t st) {
   if (n <= 0) return;
-  dim3 g(max_blk, n);
-  k_long_init<T><<<g, 256, 0, st>>>(items); count_launch();
-  k_long2<T><<<g, 256, 0, st>>>(items, -1); count_launch();
+  k_long_init<T><<<dim3(max_blk, n), 256, 0, st>>>(items); count_launch();
+  k_long_norm<T><<<n, 256, 0, st>>>(items, -1); count_launch();
 }
 
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {

@@ -21,12 +21,12 @@ namespace ssa {
 // Fill rb[0..Mx) with grid column y of a compact vector (zeros elsewhere).
 template <typename T, typename TI>
 __device__ void load_col(T* rb, int Mx, const TI* __restrict__ in, const MapDev& m, int y,
-                         int32_t* s_pre, int32_t* s_wt) {
+                         int32_t* s_pre, int32_t* s_wt, T scale = T(1)) {
   if (m.dense || y >= m.by) {
     const bool ok = (y < m.by);
     const TI* src = in + (int64_t)y * m.bx;
     for (int x = threadIdx.x; x < Mx; x += blockDim.x)
-      rb[x] = (ok && x < m.bx) ? (T)src[x] : T(0);
+      rb[x] = (ok && x < m.bx) ? (T)src[x] * scale : T(0);
   } else {
     const uint32_t* wb = m.bits + (int64_t)y * m.words;
     block_popc_scan(wb, m.words, s_pre, s_wt);
@@ -36,11 +36,19 @@ __device__ void load_col(T* rb, int Mx, const TI* __restrict__ in, const MapDev&
       if (x < m.bx) {
         const uint32_t w = wb[x >> 5];
         const int b = x & 31;
-        if ((w >> b) & 1u) v = (T)src[s_pre[x >> 5] + __popc(w & ((1u << b) - 1u))];
+        if ((w >> b) & 1u) v = (T)src[s_pre[x >> 5] + __popc(w & ((1u << b) - 1u))] * scale;
       }
       rb[x] = v;
     }
   }
+}
+
+// scale of the input column of a matvec item (deferred normalisation of the
+// long Lanczos vectors), 1 when none
+template <typename T>
+__device__ __forceinline__ T in_scale_of(const MvItem<T>& it, int s) {
+  if (!it.in_scale || !it.in.st) return T(1);
+  return (T)it.in_scale[it.in.st->j0 + s + it.in.jdelta];
 }
 
 // Write the map's positions of grid column y from rb into a compact vector.
@@ -68,27 +76,34 @@ __device__ __forceinline__ bool item_skip(const LzState* st, int s) {
   return st && (!st->active || st->j0 + s >= st->k || st->j0 + s < 0);
 }
 
-// x-pass shared layout: two (H+1) complex buffers, then scan scratch.
+// x-pass shared layout: two padded complex buffers (padded_len(H) >= H+1),
+// the octant twiddle table of W_H (the FFT's), then scan scratch.  The
+// untwist / twist factors W_{2H}^k are read once per element from the global
+// table, which keeps the footprint at three CTAs per SM for H = 4096.
 template <typename T>
 struct XSmem {
-  Cx<T>* A; Cx<T>* B; int32_t* pre; int32_t* wt;
-  __device__ XSmem(unsigned char* p, int H) {
+  Cx<T>* A; Cx<T>* B; Cx<T>* tab; int32_t* pre; int32_t* wt;
+  int log2H;
+  const Cx<T>* tw;
+  __device__ XSmem(unsigned char* p, int H, int log2M_, const Cx<T>* tw_) : log2H(log2M_ - 1), tw(tw_) {
     A = reinterpret_cast<Cx<T>*>(p);
-    B = A + (H + 1);
-    pre = reinterpret_cast<int32_t*>(B + (H + 1));
+    B = A + padded_len(H);
+    tab = B + padded_len(H);
+    pre = reinterpret_cast<int32_t*>(tab + (H >> 3) + 1);
     wt = pre + ((2 * H) / 32 + 1);
+    load_octant(tab, log2H, tw);
   }
 };
 
 // Forward half of an x-pass: packed FFT of rb (viewed in A) and untwist into
 // the other buffer.  Returns the half spectrum (H+1 values).
 template <typename T>
-__device__ Cx<T>* xpass_forward(XSmem<T>& sm, int log2H, const Cx<T>* tw) {
+__device__ Cx<T>* xpass_forward(XSmem<T>& sm, int log2H) {
   const int H = 1 << log2H;
   __syncthreads();
-  Cx<T>* Z = block_fft<T, false>(sm.A, sm.B, log2H, 1, tw);
+  Cx<T>* Z = block_fft_s<T, false>(sm.A, sm.B, log2H, 1, sm.tab, sm.log2H);
   Cx<T>* G = (Z == sm.A) ? sm.B : sm.A;
-  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd(Z, k, log2H, tw);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd(Z, k, log2H, sm.tw);
   __syncthreads();
   return G;
 }
@@ -96,12 +111,12 @@ __device__ Cx<T>* xpass_forward(XSmem<T>& sm, int log2H, const Cx<T>* tw) {
 // Inverse half of an x-pass: P (H+1 values, in one buffer) -> real signal
 // (2H values) viewed in the returned buffer.
 template <typename T>
-__device__ T* xpass_inverse(XSmem<T>& sm, Cx<T>* P, int log2H, const Cx<T>* tw) {
+__device__ T* xpass_inverse(XSmem<T>& sm, Cx<T>* P, int log2H) {
   const int H = 1 << log2H;
   Cx<T>* Q = (P == sm.A) ? sm.B : sm.A;
-  for (int k = threadIdx.x; k < H; k += blockDim.x) Q[k] = twist_inv(P, k, log2H, tw);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) Q[k] = twist_inv(P, k, log2H, sm.tw);
   __syncthreads();
-  Cx<T>* R = block_fft<T, true>(Q, P, log2H, 1, tw);
+  Cx<T>* R = block_fft_s<T, true>(Q, P, log2H, 1, sm.tab, sm.log2H);
   return reinterpret_cast<T*>(R);
 }
 
@@ -113,16 +128,17 @@ __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ item
   if (item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
-  XSmem<T> sm(smem, H);
+  XSmem<T> sm(smem, H, it.log2Mx, tw);
   const int64_t ioff = vec_elem_off(it.in, s);
+  const T isc = in_scale_of(it, s);
   if (it.in_type == 1)
-    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt);
+    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
   else
-    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt);
-  Cx<T>* G = xpass_forward(sm, log2H, tw);
+    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
+  Cx<T>* G = xpass_forward(sm, log2H);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = it.xh[k] * conj(G[k]);
   __syncthreads();
-  T* r = xpass_inverse(sm, G, log2H, tw);
+  T* r = xpass_inverse(sm, G, log2H);
   __syncthreads();
   store_col<T, T>(r, (T*)it.out.base + vec_elem_off(it.out, s), it.mout, 0, sm.pre, sm.wt);
 }
@@ -135,13 +151,14 @@ __global__ void __launch_bounds__(512) k_mv_xfwd(const MvItem<T>* __restrict__ i
   if (y >= it.y_in_hi || item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
-  XSmem<T> sm(smem, H);
+  XSmem<T> sm(smem, H, it.log2Mx, tw);
   const int64_t ioff = vec_elem_off(it.in, s);
+  const T isc = in_scale_of(it, s);
   if (it.in_type == 1)
-    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, y, sm.pre, sm.wt);
+    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, y, sm.pre, sm.wt, isc);
   else
-    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, y, sm.pre, sm.wt);
-  Cx<T>* G = xpass_forward(sm, log2H, tw);
+    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, y, sm.pre, sm.wt, isc);
+  Cx<T>* G = xpass_forward(sm, log2H);
   Cx<T>* dst = it.g1 + (int64_t)y * (H + 1);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) dst[k] = G[k];
 }
@@ -154,11 +171,11 @@ __global__ void __launch_bounds__(512) k_mv_xinv(const MvItem<T>* __restrict__ i
   if (y >= it.y_out_hi || item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
-  XSmem<T> sm(smem, H);
+  XSmem<T> sm(smem, H, it.log2Mx, tw);
   const Cx<T>* src = it.g2 + (int64_t)y * (H + 1);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.A[k] = src[k];
   __syncthreads();
-  T* r = xpass_inverse(sm, sm.A, log2H, tw);
+  T* r = xpass_inverse(sm, sm.A, log2H);
   __syncthreads();
   store_col<T, T>(r, (T*)it.out.base + vec_elem_off(it.out, s), it.mout, y, sm.pre, sm.wt);
 }
@@ -171,13 +188,16 @@ __global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ item
   if (item_skip<T>(it.st, s)) return;
   const int log2My = it.log2My, My = 1 << log2My;
   const int H = 1 << (it.log2Mx - 1), ld = H + 1;
-  int TK = buf_elems >> log2My;
+  int TK = buf_elems / padded_len(My);
   if (TK > 16) TK = 16;
   const int k0 = blockIdx.x * TK;
   if (k0 > H) return;
   extern __shared__ __align__(16) unsigned char smem[];
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
-  Cx<T>* B = A + (TK << log2My);
+  Cx<T>* B = A + buf_elems;
+  Cx<T>* tab = B + buf_elems;
+  const int log2N = log2My < 3 ? 3 : log2My;
+  load_octant(tab, log2N, tw);
   const int n = TK << log2My;
   const Cx<T> zero = cx(T(0), T(0));
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ item
   }
   __syncthreads();
   Cx<T>* F = A;
-  if (mode != Y_INV) F = block_fft<T, false>(A, B, log2My, TK, tw);
+  if (mode != Y_INV) F = block_fft_s<T, false>(A, B, log2My, TK, tab, log2N);
   Cx<T>* O = (F == A) ? B : A;
   if (mode == Y_FWD) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -215,7 +235,7 @@ __global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ item
     }
     __syncthreads();
   }
-  Cx<T>* R = block_fft<T, true>(F, O, log2My, TK, tw);
+  Cx<T>* R = block_fft_s<T, true>(F, O, log2My, TK, tab, log2N);
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const int m = t / TK, b = t - m * TK, k = k0 + b;
     if (m < it.out_hi && k <= H) it.dst[k + (int64_t)ld * m] = R[(b << log2My) + m];
@@ -232,7 +252,7 @@ __global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ 
   if (y >= it.ny) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H, Mx = 2 * H;
-  XSmem<T> sm(smem, H);
+  XSmem<T> sm(smem, H, it.log2Mx, tw);
   T* rb = reinterpret_cast<T*>(sm.A);
   for (int x = threadIdx.x; x < Mx; x += blockDim.x) {
     T v = T(0);
@@ -247,7 +267,7 @@ __global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ 
     }
     rb[x] = v;
   }
-  Cx<T>* G = xpass_forward(sm, log2H, tw);
+  Cx<T>* G = xpass_forward(sm, log2H);
   Cx<T>* dst = ((it.log2My == 0) ? it.xh : it.g1) + (int64_t)y * (H + 1);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) dst[k] = G[k];
 }
@@ -255,7 +275,7 @@ __global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ 
 // ---------------------------------------------------------------- launchers
 static inline size_t xsmem_bytes(int log2Mx, size_t csz) {
   const size_t H = size_t(1) << (log2Mx - 1);
-  return 2 * (H + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
+  return (2 * (size_t)padded_len((int)H) + H / 8 + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
 }
 
 template <typename T>
@@ -286,12 +306,13 @@ void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int ma
                   const Cx<T>* tw, cudaStream_t st) {
   if (n <= 0) return;
   const int buf = ypass_buf_elems<T>();
-  int TK = buf >> max_log2My;            // smallest tile width among the items
+  int TK = buf / padded_len(1 << max_log2My);   // smallest tile width among the items
   if (TK > 16) TK = 16;
   if (TK < 1) TK = 1;
   const int H = 1 << (max_log2Mx - 1);
   const int tiles = (H + 1 + TK - 1) / TK;
-  const size_t sm = 2 * (size_t)buf * sizeof(Cx<T>);
+  const int N = 1 << (max_log2My < 3 ? 3 : max_log2My);
+  const size_t sm = (2 * (size_t)buf + N / 8 + 1) * sizeof(Cx<T>);
   set_max_smem((const void*)k_ypass<T>);
   k_ypass<T><<<dim3(tiles, n), 512, sm, st>>>(items, mode, s, buf, tw); count_launch();
 }

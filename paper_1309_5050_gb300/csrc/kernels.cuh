@@ -46,6 +46,7 @@ template <typename T>
 struct MvItem {
   const Cx<T>* xh;          // channel spectrum, (H+1) x My, pre-scaled by 1/(Mx My)
   VecRef in, out;           // compact input / output
+  const double* in_scale;   // non-null: input column c is scaled by in_scale[c]
   MapDev min, mout;         // their grid positions
   Cx<T>* g1;                // 2D scratch: after x-pass, (H+1) x My
   Cx<T>* g2;                // 2D scratch: after y-pass

@@ -35,7 +35,8 @@ struct ShortItem {
 template <typename T>
 struct LongItem {
   LzState* st;
-  T* V; int64_t ldv;                      // Kl x (k+1)
+  T* V; int64_t ldv;                      // Kl x (k+1), columns stored unnormalised
+  double* colscale;                       // k+1: column c of V times colscale[c] is v_c
   const T* parts; int64_t part_ld; int32_t n_part; int32_t nblk;
   T* q;                                   // work vector, Kl
   double* npart;                          // nblk partial squared norms
@@ -47,6 +48,7 @@ struct LongItem {
 struct SvdItem {
   LzState* st;
   double* B; int32_t ldb; int32_t pad_;
+  double* colscale;                       // long-basis column scales (reset on restart)
   double* sig;                            // k singular values (descending)
   double* P;                              // k x k left vectors of B (ld k)
   double* Q;                              // k x k right vectors of B (ld k)
@@ -56,7 +58,8 @@ template <typename T>
 struct RitzItem {
   LzState* st;
   double* U; int64_t ldu; int64_t Ls;     // short basis
-  T* V; int64_t ldv; int64_t Kl;          // long basis
+  T* V; int64_t ldv; int64_t Kl;          // long basis (column scales below)
+  double* colscale;
   const double* P; const double* Q;       // from the small SVD
   int32_t ldc; int32_t pad_;              // their leading dimension (allocated k)
 };
