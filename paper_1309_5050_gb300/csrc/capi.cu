@@ -752,6 +752,274 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   return SSA_OK;
 }
 
+// Lanczos engine: a set of problems (contexts with a workspace) that advance in
+// lock-step, one launch per kernel kind for all of them.  Members may be in
+// different restart cycles (each has its own j0), and members can be added
+// and retired between cycles -- the batched decomposition and the server use
+// the same engine.
+template <typename T>
+struct LzEngine {
+  cudaStream_t st = nullptr;
+  int device = 0;
+  std::vector<ssa_ctx*> live;
+  std::vector<uint64_t> seed;
+  std::vector<bool> fresh;        // not started yet (no start vector)
+  std::vector<LzState> hst;       // host copy after the last cycle
+  // device item arrays for the current membership
+  ShortItem* d_sh = nullptr; LongItem<T>* d_lg = nullptr; SvdItem* d_sv = nullptr;
+  RitzItem<T>* d_rz = nullptr; LzState** d_stp = nullptr; LzState* d_stg = nullptr;
+  MvSet<T> mvA, mvAT;
+  int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1;
+  int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
+  int max_log2Mx = 1, max_log2My = 0;
+  std::vector<void*> dev_tmp;
+  LzState* h_st = nullptr;
+  int h_cap = 0;
+
+  ~LzEngine() { release_items(); if (h_st) cudaFreeHost(h_st); }
+
+  void release_items() {
+    for (void* p : dev_tmp) cudaFreeAsync(p, st);
+    dev_tmp.clear();
+    mvA = MvSet<T>(); mvAT = MvSet<T>();
+  }
+
+  template <typename X>
+  int up(const std::vector<X>& h, X** d) {
+    if (cudaMallocAsync((void**)d, sizeof(X) * std::max<size_t>(h.size(), 1), st) != cudaSuccess)
+      return fail(SSA_ENOMEM, "engine items");
+    dev_tmp.push_back(*d);
+    if (!h.empty() && g_ring.copy(*d, h.data(), sizeof(X) * h.size(), st) != SSA_OK)
+      return fail(SSA_ECUDA, "engine item upload");
+    return SSA_OK;
+  }
+
+  ShortItem short_item(ssa_ctx* c) {
+    Workspace& w = c->ws;
+    ShortItem s;
+    s.st = w.st; s.U = w.U; s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
+    s.parts_double = std::is_same<T, double>::value; s.p = w.p; s.B = w.B; s.ldb = w.k; s.nblk = w.nblk_s;
+    s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
+    return s;
+  }
+  LongItem<T> long_item(ssa_ctx* c, uint64_t sd) {
+    Workspace& w = c->ws;
+    LongItem<T> l;
+    l.st = w.st; l.V = (T*)w.V; l.ldv = w.Kl; l.colscale = w.colscale; l.parts = (const T*)w.parts_l;
+    l.part_ld = w.Kl; l.n_part = w.n_part_l; l.nblk = w.nblk_l; l.q = (T*)w.q; l.npart = w.np_l; l.B = w.B;
+    l.ldb = w.k; l.pad_ = 0; l.Kl = w.Kl; l.seed = sd;
+    return l;
+  }
+  SvdItem svd_item(ssa_ctx* c) {
+    Workspace& w = c->ws;
+    SvdItem v;
+    v.st = w.st; v.B = w.B; v.ldb = w.k; v.pad_ = 0; v.colscale = w.colscale; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
+    return v;
+  }
+  RitzItem<T> ritz_item(ssa_ctx* c) {
+    Workspace& w = c->ws;
+    RitzItem<T> z;
+    z.st = w.st; z.U = w.U; z.ldu = w.Ls; z.Ls = w.Ls; z.V = (T*)w.V; z.ldv = w.Kl; z.Kl = w.Kl;
+    z.colscale = w.colscale; z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.pad_ = 0;
+    return z;
+  }
+  FinalItem<T> final_item(ssa_ctx* c) {
+    Workspace& w = c->ws;
+    FinalItem<T> f;
+    f.st = w.st; f.U = w.U; f.ldu = w.Ls; f.Ls = w.Ls; f.V = (const T*)w.V; f.ldv = w.Kl; f.Kl = w.Kl;
+    f.sig = w.sig; f.swapped = w.swapped; f.r = w.r; f.Uo = (T*)w.Uo; f.Vo = (T*)w.Vo; f.sigma_out = w.sigma;
+    f.sgn = w.sgn;
+    return f;
+  }
+
+  void add(ssa_ctx* c, uint64_t sd) {
+    live.push_back(c); seed.push_back(sd); fresh.push_back(true);
+    LzState z{};
+    hst.push_back(z);
+  }
+
+  // rebuild the device item arrays for the current members
+  int build() {
+    release_items();
+    std::vector<ShortItem> sh; std::vector<LongItem<T>> lg; std::vector<SvdItem> sv;
+    std::vector<RitzItem<T>> rz; std::vector<LzState*> stp;
+    max_blk_s = max_blk_l = max_k = max_r = 1;
+    max_Ls = max_Kl = max_rows = 1;
+    max_log2Mx = 1; max_log2My = 0;
+    for (size_t i = 0; i < live.size(); ++i) {
+      ssa_ctx* c = live[i];
+      Workspace& w = c->ws;
+      sh.push_back(short_item(c)); lg.push_back(long_item(c, seed[i])); sv.push_back(svd_item(c));
+      rz.push_back(ritz_item(c)); stp.push_back(w.st);
+      const size_t hs = c->log2My > 0 ? ((size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My) : 0;
+      for (size_t q = 0; q < c->ch.size(); ++q) {
+        const Channel& h = c->ch[q];
+        Cx<T>* g1 = hs ? (Cx<T>*)w.g1 + q * hs : nullptr;
+        Cx<T>* g2 = hs ? (Cx<T>*)w.g2 + q * hs : nullptr;
+        VecRef vin{}, vout{};
+        if (!w.swapped) {
+          // A v = X v : K -> L partial per channel
+          vin.base = w.V; vin.off = h.koff; vin.ld = w.Kl; vin.st = w.st; vin.jdelta = 0;
+          vout.base = w.parts_s; vout.off = (int64_t)q * w.Ls; vout.ld = 0; vout.st = nullptr;
+          mvA.items.push_back(make_mv<T>(c, h, false, vin, 0, vout, g1, g2, w.st));
+          mvA.items.back().in_scale = w.colscale;
+          // A^T u = X^T u : L -> K slice
+          vin.base = w.U; vin.off = 0; vin.ld = w.Ls; vin.st = w.st;
+          vout.base = w.parts_l; vout.off = h.koff; vout.st = nullptr;
+          mvAT.items.push_back(make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st));
+        } else {
+          // A v = X^T v : L -> K slice
+          vin.base = w.V; vin.off = 0; vin.ld = w.Kl; vin.st = w.st;
+          vout.base = w.parts_s; vout.off = h.koff; vout.st = nullptr;
+          mvA.items.push_back(make_mv<T>(c, h, true, vin, 0, vout, g1, g2, w.st));
+          mvA.items.back().in_scale = w.colscale;
+          // A^T u = X u : K -> L partial
+          vin.base = w.U; vin.off = h.koff; vin.ld = w.Ls; vin.st = w.st;
+          vout.base = w.parts_l; vout.off = (int64_t)q * w.Kl; vout.st = nullptr;
+          mvAT.items.push_back(make_mv<T>(c, h, false, vin, 1, vout, g1, g2, w.st));
+        }
+      }
+      max_blk_s = std::max(max_blk_s, w.nblk_s);
+      max_blk_l = std::max(max_blk_l, w.nblk_l);
+      max_k = std::max(max_k, w.k);
+      max_r = std::max(max_r, w.r);
+      max_Ls = std::max(max_Ls, w.Ls);
+      max_Kl = std::max(max_Kl, w.Kl);
+      max_rows = std::max(max_rows, std::max(c->L, c->K));
+      max_log2Mx = std::max(max_log2Mx, c->log2Mx);
+      max_log2My = std::max(max_log2My, c->log2My);
+    }
+    if (live.empty()) return SSA_OK;
+    TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
+    for (auto& m : mvA.items) { mvA.yitems.push_back(ymv(m)); mvA.max_y_in = std::max(mvA.max_y_in, m.y_in_hi); mvA.max_y_out = std::max(mvA.max_y_out, m.y_out_hi); }
+    for (auto& m : mvAT.items) { mvAT.yitems.push_back(ymv(m)); mvAT.max_y_in = std::max(mvAT.max_y_in, m.y_in_hi); mvAT.max_y_out = std::max(mvAT.max_y_out, m.y_out_hi); }
+    TRY(up(mvA.items, &mvA.d_items)); TRY(up(mvA.yitems, &mvA.d_y));
+    TRY(up(mvAT.items, &mvAT.d_items)); TRY(up(mvAT.yitems, &mvAT.d_y));
+    if (cudaMallocAsync((void**)&d_stg, sizeof(LzState) * live.size(), st) != cudaSuccess)
+      return fail(SSA_ENOMEM, "engine state buffer");
+    dev_tmp.push_back(d_stg);
+    if ((int)live.size() > h_cap) {
+      if (h_st) cudaFreeHost(h_st);
+      h_cap = std::max((int)live.size(), 256);
+      if (cudaHostAlloc((void**)&h_st, sizeof(LzState) * h_cap, cudaHostAllocDefault) != cudaSuccess) {
+        h_st = nullptr; h_cap = 0;
+        return fail(SSA_ENOMEM, "pinned state buffer");
+      }
+    }
+    return SSA_OK;
+  }
+
+  // start vectors of the members not started yet
+  int start_fresh() {
+    std::vector<LongItem<T>> lg;
+    int mb = 1;
+    for (size_t i = 0; i < live.size(); ++i)
+      if (fresh[i]) { lg.push_back(long_item(live[i], seed[i])); mb = std::max(mb, live[i]->ws.nblk_l); fresh[i] = false; }
+    if (lg.empty()) return SSA_OK;
+    LongItem<T>* d = nullptr;
+    TRY(up(lg, &d));
+    PhaseScope ps_(PH_LONG, st);
+    launch_long_init<T>(d, (int)lg.size(), mb, st);
+    CU(cudaGetLastError());
+    return SSA_OK;
+  }
+
+  // one restart cycle for every member (members that are done skip it), then
+  // the small SVDs and a read-back of every member's state
+  int run_cycle() {
+    const int nl = (int)live.size();
+    if (!nl) return SSA_OK;
+    int steps = 0;
+    for (int i = 0; i < nl; ++i) {
+      const Workspace& w = live[i]->ws;
+      const int j0 = (hst[i].restarts == 0) ? 0 : w.kk;
+      steps = std::max(steps, w.k - j0);
+    }
+    for (int s = 0; s < steps; ++s) {
+      run_mv<T>(live[0], mvA, max_log2Mx, max_log2My, s);
+      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, nl, max_blk_s, s, st); }
+      run_mv<T>(live[0], mvAT, max_log2Mx, max_log2My, s);
+      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, nl, max_blk_l, s, st); }
+    }
+    { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
+    CU(cudaGetLastError());
+    k_gather_states<<<1, 128, 0, st>>>(d_stp, nl, d_stg); count_launch();
+    CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
+    return SSA_OK;
+  }
+
+  // restart every member still active
+  int restart_active() {
+    PhaseScope ps_(PH_RITZ, st);
+    launch_ritz<T>(d_rz, (int)live.size(), max_k, max_Ls, max_Kl, 0, st);
+    launch_restart(d_sv, (int)live.size(), st);
+    CU(cudaGetLastError());
+    return SSA_OK;
+  }
+
+  // final Ritz vectors and outputs of the given members
+  int retire(const std::vector<int>& idx) {
+    if (idx.empty()) return SSA_OK;
+    std::vector<RitzItem<T>> rz; std::vector<FinalItem<T>> fi;
+    int mk = 1, mr = 1;
+    int64_t mls = 1, mkl = 1, mrows = 1;
+    for (int i : idx) {
+      ssa_ctx* c = live[i];
+      rz.push_back(ritz_item(c)); fi.push_back(final_item(c));
+      mk = std::max(mk, c->ws.k); mr = std::max(mr, c->ws.r);
+      mls = std::max(mls, c->ws.Ls); mkl = std::max(mkl, c->ws.Kl);
+      mrows = std::max(mrows, std::max(c->L, c->K));
+    }
+    RitzItem<T>* d_r = nullptr; FinalItem<T>* d_f = nullptr;
+    TRY(up(rz, &d_r)); TRY(up(fi, &d_f));
+    PhaseScope ps_(PH_RITZ, st);
+    launch_ritz<T>(d_r, (int)idx.size(), mk, mls, mkl, 1, st);
+    launch_finalize<T>(d_f, (int)idx.size(), mr, mrows, st);
+    CU(cudaGetLastError());
+    for (int i : idx) {
+      Workspace& w = live[i]->ws;
+      w.host_st = hst[i];
+      w.done = true;
+    }
+    return SSA_OK;
+  }
+
+  // drop members (after retire)
+  void remove(const std::vector<int>& idx) {
+    std::vector<bool> drop(live.size(), false);
+    for (int i : idx) drop[i] = true;
+    std::vector<ssa_ctx*> l2; std::vector<uint64_t> s2; std::vector<bool> f2; std::vector<LzState> h2;
+    for (size_t i = 0; i < live.size(); ++i)
+      if (!drop[i]) { l2.push_back(live[i]); s2.push_back(seed[i]); f2.push_back(fresh[i]); h2.push_back(hst[i]); }
+    live.swap(l2); seed.swap(s2); fresh.swap(f2); hst.swap(h2);
+  }
+};
+
+// Admission of problems into an engine: spectra and workspaces.
+template <typename T>
+static int prepare_members(ssa_ctx* const* cs, int n, const ssa_params* ps, cudaStream_t st, std::vector<int>& rc) {
+  rc.assign(n, SSA_OK);
+  std::vector<ssa_ctx*> need;
+  for (int i = 0; i < n; ++i) {
+    if (ps[i].rank < 1 || ps[i].rank > std::min(cs[i]->L, cs[i]->K))
+      rc[i] = fail(SSA_ERANK, "rank %d outside [1, min(L, K) = %lld]", ps[i].rank,
+                   (long long)std::min(cs[i]->L, cs[i]->K));
+    else need.push_back(cs[i]);
+  }
+  if (!need.empty()) TRY(ensure_spectra<T>(need.data(), (int)need.size(), st));
+  for (int i = 0; i < n; ++i) {
+    if (rc[i] != SSA_OK) continue;
+    ssa_ctx* c = cs[i];
+    cudaStream_t keep = c->stream;
+    c->stream = st;
+    rc[i] = alloc_ws<T>(c, ps[i], c->ws);
+    c->stream = keep;
+  }
+  return SSA_OK;
+}
+
 template <typename T>
 static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, int32_t* status) {
   ssa_ctx* c0 = cs[0];
@@ -766,221 +1034,84 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
       CU(cudaStreamWaitEvent(st, e, 0));
       evs.push_back(e);
     }
-  std::vector<int> ok(n, 1);
-  {
-    std::vector<ssa_ctx*> need;
-    for (int i = 0; i < n; ++i)
-      if (ps[i].rank >= 1 && ps[i].rank <= std::min(cs[i]->L, cs[i]->K)) need.push_back(cs[i]);
-    if (!need.empty()) TRY(ensure_spectra<T>(need.data(), (int)need.size(), st));
-  }
+  std::vector<int> rc;
+  TRY(prepare_members<T>(cs, n, ps, st, rc));
+  LzEngine<T> eng;
+  eng.st = st;
+  eng.device = c0->device;
   for (int i = 0; i < n; ++i) {
-    ssa_ctx* c = cs[i];
-    const ssa_params& p = ps[i];
-    int rc = SSA_OK;
-    if (p.rank < 1 || p.rank > std::min(c->L, c->K))
-      rc = fail(SSA_ERANK, "rank %d outside [1, min(L, K) = %lld]", p.rank, (long long)std::min(c->L, c->K));
-    if (rc == SSA_OK) {
-      cudaStream_t keep = c->stream;
-      c->stream = st;
-      rc = alloc_ws<T>(c, p, c->ws);
-      c->stream = keep;
+    if (status) status[i] = rc[i];
+    if (rc[i] == SSA_OK) eng.add(cs[i], ps[i].seed);
+    else cs[i]->ws.done = false;
+  }
+  int rc_all = SSA_OK;
+  if (!eng.live.empty()) {
+    TRY(eng.build());
+    TRY(eng.start_fresh());
+    for (;;) {
+      TRY(eng.run_cycle());
+      bool any = false;
+      for (auto& h : eng.hst) any |= h.active != 0;
+      if (!any) break;
+      TRY(eng.restart_active());
     }
-    if (status) status[i] = rc;
-    if (rc != SSA_OK) { ok[i] = 0; c->ws.done = false; }
-  }
-  // items
-  std::vector<ShortItem> sh;
-  std::vector<LongItem<T>> lg;
-  std::vector<SvdItem> sv;
-  std::vector<RitzItem<T>> rz;
-  std::vector<FinalItem<T>> fi;
-  MvSet<T> mvA, mvAT;    // A v (long -> short) and A^T u (short -> long)
-  int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1, max_steps = 0;
-  int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
-  int max_log2Mx = 1, max_log2My = 0;
-  std::vector<ssa_ctx*> live;
-  for (int i = 0; i < n; ++i) {
-    if (!ok[i]) continue;
-    ssa_ctx* c = cs[i];
-    Workspace& w = c->ws;
-    live.push_back(c);
-    ShortItem s;
-    s.st = w.st; s.U = w.U; s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
-    s.parts_double = std::is_same<T, double>::value; s.p = w.p; s.B = w.B; s.ldb = w.k; s.nblk = w.nblk_s;
-    s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
-    sh.push_back(s);
-    LongItem<T> l;
-    l.st = w.st; l.V = (T*)w.V; l.ldv = w.Kl; l.colscale = w.colscale; l.parts = (const T*)w.parts_l; l.part_ld = w.Kl;
-    l.n_part = w.n_part_l; l.nblk = w.nblk_l; l.q = (T*)w.q; l.npart = w.np_l; l.B = w.B; l.ldb = w.k;
-    l.pad_ = 0; l.Kl = w.Kl; l.seed = ps[i].seed;
-    lg.push_back(l);
-    SvdItem v;
-    v.st = w.st; v.B = w.B; v.ldb = w.k; v.pad_ = 0; v.colscale = w.colscale; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
-    sv.push_back(v);
-    RitzItem<T> z;
-    z.st = w.st; z.U = w.U; z.ldu = w.Ls; z.Ls = w.Ls; z.V = (T*)w.V; z.ldv = w.Kl; z.Kl = w.Kl;
-    z.colscale = w.colscale;
-    z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.pad_ = 0;
-    rz.push_back(z);
-    FinalItem<T> f;
-    f.st = w.st; f.U = w.U; f.ldu = w.Ls; f.Ls = w.Ls; f.V = (const T*)w.V; f.ldv = w.Kl; f.Kl = w.Kl;
-    f.sig = w.sig; f.swapped = w.swapped; f.r = w.r; f.Uo = (T*)w.Uo; f.Vo = (T*)w.Vo; f.sigma_out = w.sigma;
-    f.sgn = w.sgn;
-    fi.push_back(f);
-    // matvec items per channel
-    const size_t hs = c->log2My > 0 ? ((size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My) : 0;
-    for (size_t q = 0; q < c->ch.size(); ++q) {
-      const Channel& h = c->ch[q];
-      Cx<T>* g1 = hs ? (Cx<T>*)w.g1 + q * hs : nullptr;
-      Cx<T>* g2 = hs ? (Cx<T>*)w.g2 + q * hs : nullptr;
-      VecRef vin{}, vout{};
-      if (!w.swapped) {
-        // A v = X v : K -> L partial per channel
-        vin.base = w.V; vin.off = h.koff; vin.ld = w.Kl; vin.st = w.st; vin.jdelta = 0;
-        vout.base = w.parts_s; vout.off = (int64_t)q * w.Ls; vout.ld = 0; vout.st = nullptr;
-        mvA.items.push_back(make_mv<T>(c, h, false, vin, 0, vout, g1, g2, w.st));
-        mvA.items.back().in_scale = w.colscale;
-        // A^T u = X^T u : L -> K slice
-        vin.base = w.U; vin.off = 0; vin.ld = w.Ls; vin.st = w.st;
-        vout.base = w.parts_l; vout.off = h.koff; vout.st = nullptr;
-        mvAT.items.push_back(make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st));
-      } else {
-        // A v = X^T v : L -> K slice
-        vin.base = w.V; vin.off = 0; vin.ld = w.Kl; vin.st = w.st;
-        vout.base = w.parts_s; vout.off = h.koff; vout.st = nullptr;
-        mvA.items.push_back(make_mv<T>(c, h, true, vin, 0, vout, g1, g2, w.st));
-        mvA.items.back().in_scale = w.colscale;
-        // A^T u = X u : K -> L partial
-        vin.base = w.U; vin.off = h.koff; vin.ld = w.Ls; vin.st = w.st;
-        vout.base = w.parts_l; vout.off = (int64_t)q * w.Kl; vout.st = nullptr;
-        mvAT.items.push_back(make_mv<T>(c, h, false, vin, 1, vout, g1, g2, w.st));
+    std::vector<int> all(eng.live.size());
+    for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
+    TRY(eng.retire(all));
+    CU(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < eng.live.size(); ++i) {
+      const LzState& h = eng.hst[i];
+      if (!h.converged && !h.breakdown) {
+        const int idx = (int)(std::find(cs, cs + n, eng.live[i]) - cs);
+        if (status) status[idx] = SSA_ENOTCONV;
+        if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
       }
     }
-    max_blk_s = std::max(max_blk_s, w.nblk_s);
-    max_blk_l = std::max(max_blk_l, w.nblk_l);
-    max_k = std::max(max_k, w.k);
-    max_r = std::max(max_r, w.r);
-    max_steps = std::max(max_steps, w.k);
-    max_Ls = std::max(max_Ls, w.Ls);
-    max_Kl = std::max(max_Kl, w.Kl);
-    max_rows = std::max(max_rows, std::max(c->L, c->K));
-    max_log2Mx = std::max(max_log2Mx, c->log2Mx);
-    max_log2My = std::max(max_log2My, c->log2My);
   }
-  if (live.empty()) return status ? status[0] : SSA_EINVAL;
-  // all live problems must share the grid kind (series vs image) for one launch shape
-  ShortItem* d_sh = nullptr; LongItem<T>* d_lg = nullptr; SvdItem* d_sv = nullptr;
-  RitzItem<T>* d_rz = nullptr; FinalItem<T>* d_fi = nullptr;
-  // temporarily route allocations of items through ctx 0 on the batch stream
-  TRY(upload(c0, sh, &d_sh));
-  TRY(upload(c0, lg, &d_lg));
-  TRY(upload(c0, sv, &d_sv));
-  TRY(upload(c0, rz, &d_rz));
-  TRY(upload(c0, fi, &d_fi));
-  TRY(finish_set(c0, mvA));
-  TRY(finish_set(c0, mvAT));
-  const int nl = (int)live.size();
-  // per-cycle state read-back: gather on the device, one pinned copy
-  std::vector<LzState*> stp(nl);
-  for (int i = 0; i < nl; ++i) stp[i] = live[i]->ws.st;
-  LzState** d_stp = nullptr;
-  LzState* d_stg = nullptr;
-  TRY(upload(c0, stp, &d_stp));
-  TRY(c0->allocT(&d_stg, (size_t)nl));
-  static thread_local LzState* h_st = nullptr;
-  static thread_local int h_cap = 0;
-  if (nl > h_cap) {
-    if (h_st) cudaFreeHost(h_st);
-    h_cap = std::max(nl, 256);
-    if (cudaHostAlloc((void**)&h_st, sizeof(LzState) * h_cap, cudaHostAllocDefault) != cudaSuccess) {
-      h_st = nullptr; h_cap = 0;
-      return fail(SSA_ENOMEM, "pinned state buffer");
-    }
-  }
-  // start vectors
-  { PhaseScope ps_(PH_LONG, st); launch_long_init<T>(d_lg, nl, max_blk_l, st); }
-  CU(cudaGetLastError());
-  std::vector<LzState> hst(nl);
-  int rc_all = SSA_OK;
-  for (int cycle = 0;; ++cycle) {
-    // steps of this cycle (j0 = 0 in the first cycle, kk afterwards)
-    int steps = 0;
-    for (int i = 0; i < nl; ++i) {
-      Workspace& w = live[i]->ws;
-      const int j0 = cycle == 0 ? 0 : w.kk;
-      if (cycle == 0 || hst[i].active) steps = std::max(steps, w.k - j0);
-    }
-    for (int s = 0; s < steps; ++s) {
-      run_mv<T>(c0, mvA, max_log2Mx, max_log2My, s);
-      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, nl, max_blk_s, s, st); }
-      run_mv<T>(c0, mvAT, max_log2Mx, max_log2My, s);
-      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, nl, max_blk_l, s, st); }
-    }
-    { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
-    CU(cudaGetLastError());
-    k_gather_states<<<1, 128, 0, st>>>(d_stp, nl, d_stg); count_launch();
-    CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
-    bool any = false;
-    for (int i = 0; i < nl; ++i) any |= hst[i].active != 0;
-    if (!any) break;
-    {
-      PhaseScope ps_(PH_RITZ, st);
-      launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 0, st);
-      launch_restart(d_sv, nl, st);
-    }
-    CU(cudaGetLastError());
-  }
-  {
-    PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_rz, nl, max_k, max_Ls, max_Kl, 1, st);
-    launch_finalize<T>(d_fi, nl, max_r, max_rows, st);
-  }
-  CU(cudaGetLastError());
-  CU(cudaStreamSynchronize(st));
-  for (int i = 0; i < nl; ++i) {
-    Workspace& w = live[i]->ws;
-    w.host_st = hst[i];
-    w.done = true;
-    if (!hst[i].converged && !hst[i].breakdown) {
-      int idx = (int)(std::find(cs, cs + n, live[i]) - cs);
-      if (status) status[idx] = SSA_ENOTCONV;
-      if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", hst[i].maxres);
-    }
-  }
-  c0->release(d_stp); c0->release(d_stg);
-  c0->release(d_sh); c0->release(d_lg); c0->release(d_sv); c0->release(d_rz); c0->release(d_fi);
-  c0->release(mvA.d_items); c0->release(mvA.d_y); c0->release(mvAT.d_items); c0->release(mvAT.d_y);
   for (auto e : evs) cudaEventDestroy(e);
   for (int i = 0; i < n; ++i)
-    if (!ok[i] && rc_all == SSA_OK) rc_all = status ? status[i] : SSA_EINVAL;
+    if (rc[i] != SSA_OK && rc_all == SSA_OK) rc_all = rc[i];
   return rc_all;
 }
 
 // ============================================================== reconstruction
 // Reconstruction arithmetic runs in TC (FP64 unless the grid is too long for
 // an FP64 single-CTA pass); the decomposition's vectors are read as TV.
+// One problem's reconstruction request: its grouping and output buffer.
+struct RecReq {
+  const int32_t* group_of;   // r entries (host)
+  int ng;
+  int residual;
+  double* out;               // (ng + residual) x total, host or device
+};
+
 template <typename TC, typename TV>
-static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int ng, int residual,
-                         double* const* outs, int on_device) {
+static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_device) {
   typedef TC T;
   ssa_ctx* c0 = cs[0];
   cudaStream_t st = c0->stream;
-  const int r = c0->ws.r;
   PhaseScope ps_(PH_RECON, st);
-  std::vector<std::vector<int32_t>> comps(ng);
-  for (int i = 0; i < r; ++i) {
-    if (group_of[i] < -1 || group_of[i] >= ng) return fail(SSA_EINVAL, "group_of[%d] = %d out of range", i, group_of[i]);
-    if (group_of[i] >= 0) comps[group_of[i]].push_back(i);
+  // component lists of every (problem, group), flattened for one upload
+  std::vector<int32_t> flat;
+  std::vector<std::vector<int32_t>> start(n);
+  for (int p = 0; p < n; ++p) {
+    const int r = cs[p]->ws.r, ng = req[p].ng;
+    std::vector<std::vector<int32_t>> comps(ng);
+    for (int i = 0; i < r; ++i) {
+      const int g = req[p].group_of[i];
+      if (g < -1 || g >= ng) return fail(SSA_EINVAL, "group_of[%d] = %d out of range", i, g);
+      if (g >= 0) comps[g].push_back(i);
+    }
+    start[p].assign(ng + 1, 0);
+    for (int g = 0; g < ng; ++g) {
+      start[p][g] = (int32_t)flat.size();
+      flat.insert(flat.end(), comps[g].begin(), comps[g].end());
+    }
+    start[p][ng] = (int32_t)flat.size();
   }
-  std::vector<int32_t> flat, start(ng + 1, 0);
-  for (int g = 0; g < ng; ++g) { start[g] = (int32_t)flat.size(); flat.insert(flat.end(), comps[g].begin(), comps[g].end()); }
-  start[ng] = (int32_t)flat.size();
   int32_t* d_flat = nullptr;
   TRY(upload(c0, flat, &d_flat));
   std::vector<void*> tmp;
-  const int nout = ng + (residual ? 1 : 0);
   std::vector<double*> dout(n, nullptr);
   const Cx<T>* tw = twiddles<T>(c0->device);
   if (c0->log2My == 0) {
@@ -991,12 +1122,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
     for (int p = 0; p < n; ++p) {
       ssa_ctx* c = cs[p];
       Workspace& w = c->ws;
+      const int r = w.r, ng = req[p].ng, nout = ng + (req[p].residual ? 1 : 0);
       const int H = 1 << (c->log2Mx - 1);
       Cx<T>* gu = nullptr;
       TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * (size_t)(H + 1) * r));
       tmp.push_back(gu);
       double* o = nullptr;
-      if (on_device) o = outs[p];
+      if (on_device) o = req[p].out;
       else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
       dout[p] = o;
       for (int i = 0; i < r; ++i) {
@@ -1011,7 +1143,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
           Rec1Item<T, TV> it;
           it.V = (const TV*)w.Vo + h.koff; it.ldv = c->K; it.map = h.K.dev();
           it.gu = gu; it.ldgu = H + 1; it.sigma = w.sigma;
-          it.comps = d_flat + start[g]; it.ncomp = start[g + 1] - start[g];
+          it.comps = d_flat + start[p][g]; it.ncomp = start[p][g + 1] - start[p][g];
           it.log2Mx = c->log2Mx; it.w = h.w; it.n = (int32_t)h.nx;
           it.out = o + (size_t)g * c->total + h.data_off;
           it.inv_norm = 1.0 / (double)(2 * H);
@@ -1031,11 +1163,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
     for (int p = 0; p < n; ++p) {
       ssa_ctx* c = cs[p];
       Workspace& w = c->ws;
+      const int r = w.r, ng = req[p].ng, nout = ng + (req[p].residual ? 1 : 0);
+      const int32_t* group_of = req[p].group_of;
       const Channel& h = c->ch[0];
       const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
       const size_t hs = (size_t)(H + 1) * My;
       double* o = nullptr;
-      if (on_device) o = outs[p];
+      if (on_device) o = req[p].out;
       else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
       dout[p] = o;
       Cx<T> *gx = nullptr, *gu = nullptr, *acc = nullptr, *g2 = nullptr;
@@ -1106,11 +1240,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
     }
   }
   // residual (one launch for every channel of every problem) and copy-out
-  if (residual) {
+  {
     std::vector<ResItem> ri;
     int64_t max_n = 1;
     for (int p = 0; p < n; ++p) {
       ssa_ctx* c = cs[p];
+      if (!req[p].residual) continue;
+      const int ng = req[p].ng;
       const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
       for (size_t q = 0; q < c->ch.size(); ++q) {
         const Channel& h = c->ch[q];
@@ -1119,16 +1255,19 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const int32_t* group_of, int
         max_n = std::max<int64_t>(max_n, h.nx * h.ny);
       }
     }
-    ResItem* d_ri = nullptr;
-    TRY(upload(c0, ri, &d_ri));
-    tmp.push_back(d_ri);
-    launch_residual_batch(d_ri, (int)ri.size(), max_n, st);
-    CU(cudaGetLastError());
+    if (!ri.empty()) {
+      ResItem* d_ri = nullptr;
+      TRY(upload(c0, ri, &d_ri));
+      tmp.push_back(d_ri);
+      launch_residual_batch(d_ri, (int)ri.size(), max_n, st);
+      CU(cudaGetLastError());
+    }
   }
   for (int p = 0; p < n; ++p) {
     ssa_ctx* c = cs[p];
+    const int nout = req[p].ng + (req[p].residual ? 1 : 0);
     if (!on_device)
-      CU(cudaMemcpyAsync(outs[p], dout[p], sizeof(double) * (size_t)c->total * nout, cudaMemcpyDeviceToHost, st));
+      CU(cudaMemcpyAsync(req[p].out, dout[p], sizeof(double) * (size_t)c->total * nout, cudaMemcpyDeviceToHost, st));
   }
   CU(cudaStreamSynchronize(st));
   for (void* t : tmp) c0->release(t);
@@ -1273,6 +1412,17 @@ static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_
   return SSA_OK;
 }
 
+
+// precision of the reconstruction sums: FP64 unless one FP64 pass would not
+// fit a CTA (x grids above 8192)
+static int reconstruct_dispatch(ssa_ctx* const* ctxs, int n, const RecReq* req, int on_device) {
+  const int prec = ctxs[0]->ws.prec;
+  int max_log2Mx = 0;
+  for (int i = 0; i < n; ++i) max_log2Mx = std::max(max_log2Mx, ctxs[i]->log2Mx);
+  if (prec == SSA_PREC_FP64) return reconstruct_T<double, double>(ctxs, n, req, on_device);
+  if (max_log2Mx <= 13) return reconstruct_T<double, float>(ctxs, n, req, on_device);
+  return reconstruct_T<float, float>(ctxs, n, req, on_device);
+}
 
 // ============================================================== C ABI
 extern "C" {
@@ -1497,12 +1647,9 @@ int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_
     if (!outs[i]) return fail(SSA_EINVAL, "null output %d", i);
   }
   if (n_groups + (residual ? 1 : 0) == 0) return SSA_OK;
-  int max_log2Mx = 0;
-  for (int i = 0; i < n; ++i) max_log2Mx = std::max(max_log2Mx, ctxs[i]->log2Mx);
-  if (prec == SSA_PREC_FP64) return reconstruct_T<double, double>(ctxs, n, group_of, n_groups, residual, outs, on_device);
-  // FP64 sums unless one FP64 pass would not fit a CTA (x grids above 8192)
-  if (max_log2Mx <= 13) return reconstruct_T<double, float>(ctxs, n, group_of, n_groups, residual, outs, on_device);
-  return reconstruct_T<float, float>(ctxs, n, group_of, n_groups, residual, outs, on_device);
+  std::vector<RecReq> req(n);
+  for (int i = 0; i < n; ++i) req[i] = {group_of, n_groups, residual, outs[i]};
+  return reconstruct_dispatch(ctxs, n, req.data(), on_device);
 }
 
 int ssa_reconstruct(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, int32_t residual, double* out,
