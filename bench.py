@@ -127,6 +127,73 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ serving
+SERVE_N_MAX = 16384   # longest series the single-CTA FFT grid takes (2^14 samples)
+
+
+def serve_submit(srv, q, seed):
+    g = [[0], [1, 2]]
+    if q.kind == "1d":
+        return srv.submit_series(q.data, q.L, q.rank, groups=g, residual=True, seed=seed)
+    if q.kind == "mssa":
+        return srv.submit_multi(q.data, q.L, q.rank, groups=g, residual=True, seed=seed)
+    return srv.submit_image(q.data, q.window[0], q.window[1], q.rank, mask=q.mask, groups=g, residual=True,
+                            seed=seed)
+
+
+def run_serving(pkg, reqs, prec, budget, rate_hz):
+    """Open-loop serving: each request is submitted when its Poisson arrival
+    time comes up on the server's clock; latency runs from that arrival time
+    to the request's completion (results in host memory)."""
+    srv = pkg.Server(memory_budget=budget, prec=prec)
+    for q in reqs[:8]:                      # warm-up requests (not counted)
+        serve_submit(srv, q, 1)
+    srv.drain()
+    for t in srv.finished():
+        srv.take(t)
+    n = len(reqs)
+    arrival = {}
+    lat, status, restarts = [], {}, []
+    max_live = max_q = 0
+    i = 0
+    t0 = srv.clock()
+    t_last = t0
+    steps = 0
+    while len(lat) < n:
+        now = srv.clock() - t0
+        while i < n and reqs[i].arrival_s <= now:
+            arrival[serve_submit(srv, reqs[i], 1000 + i)] = reqs[i].arrival_s
+            i += 1
+        st = srv.stats()
+        max_live = max(max_live, st["live"])
+        max_q = max(max_q, st["queued"])
+        if st["queued"] == 0 and st["live"] == 0:
+            if i < n:
+                dt = reqs[i].arrival_s - (srv.clock() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            continue
+        srv.step()
+        steps += 1
+        for t in srv.finished():
+            r = srv.take(t)
+            lat.append(r["t_done"] - t0 - arrival.pop(t))
+            status[r["status"]] = status.get(r["status"], 0) + 1
+            restarts.append(r["restarts"])
+            t_last = max(t_last, r["t_done"])
+    srv.close()
+    wall = t_last - t0
+    kinds = {}
+    for q in reqs:
+        kinds[q.kind] = kinds.get(q.kind, 0) + 1
+    return {"requests": n, "rate_hz": rate_hz, "kinds": kinds, "throughput_rps": n / wall, "wall_s": wall,
+            "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
+            "mean_ms": 1000 * float(np.mean(lat)), "max_live": max_live, "max_queued": max_q,
+            "server_steps": steps, "mean_restarts": float(np.mean(restarts)),
+            "statuses": {str(k): v for k, v in status.items()}, "budget_bytes": budget,
+            "series_n_max": SERVE_N_MAX, "prec": prec}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -137,6 +204,9 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--serve-rate", type=float, default=1000.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -266,6 +336,13 @@ def main():
         fp64 = {"value": world * B / (sum(t64) / len(t64) / 1000.0), "unit": "decomps/s",
                 "ms_per_step": sum(t64) / len(t64)}
 
+    # serving: a Poisson stream of mixed requests through ssa_server_*
+    serving = None
+    if args.serve_requests > 0:
+        reqs = W.serving_requests(n=args.serve_requests, rate_hz=args.serve_rate, seed=5 + rank,
+                                  n_max=SERVE_N_MAX)
+        serving = run_serving(pkg, reqs, args.prec, int(args.serve_budget_gb * (1 << 30)), args.serve_rate)
+
     # roofline of the dominant phase
     hbm, src = peaks()
     total_ms = sum(v[0] for v in prof.values())
@@ -296,6 +373,7 @@ def main():
                 "latency_ms": {"p50": float(np.percentile(ts_sorted, 50)), "p99": float(np.percentile(ts_sorted, 99)),
                                "what": "completion of one batch"},
                 "fp64_form": fp64,
+                "serving": serving,
                 "roofline": roof,
                 "cpu_baseline": cpu,
                 "e2e": {"value": world * B / (ms_e2e / 1000.0), "unit": "decomps/s", "h2d_bytes_per_step": h2d,

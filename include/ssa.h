@@ -113,8 +113,15 @@ typedef struct {
  * spectrum (Sec. 6.1.2: "F(x) can be precomputed") is built on first use.
  * cuda_stream: a cudaStream_t to order the context's work on, or NULL for a
  * stream owned by the context.  On success *out receives a new context.
+ * Series (1D and every series of an MSSA system) longer than 16384 samples
+ * run in segment form: with B = 4096 the L x K Hankel matrix equals the
+ * Hankel-block-Hankel matrix of the image S[i, c] = x[cB + i] (i < 2B - 1)
+ * with window B x ceil(L/B) and origins B x ceil(K/B), rows and columns past
+ * L and K absent (Sec. 6.2 applied to a 1D series), so the products and the
+ * reconstruction use a 2B x My grid; such series must have no missing values.
  * Errors: SSA_EINVAL (sizes, window, +-Inf), SSA_EEMPTY (K empty),
- * SSA_EUNSUPPORTED (FFT grid above 16384 along x or 4096 along y).
+ * SSA_EUNSUPPORTED (image grid above 16384 along x or 4096 along y; a
+ * segment-form series with missing values or more than 4096 segments).
  */
 int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa_ctx** out);
 
@@ -244,6 +251,96 @@ int64_t ssa_kernel_launches(void);
 int ssa_matvec_series_noalloc(const float* x, int64_t n, int64_t L, int32_t transpose, const float* in,
                               float* out, void* cuda_stream);
 const char* ssa_noalloc_last_error(void);
+
+/*
+ * Serving: many independent decompositions in flight on one GPU.
+ * The arithmetic of each request is that of ssa_embed + ssa_decompose +
+ * ssa_reconstruct (Sec. 2.1, steps 1-4 of the basic algorithm, with the
+ * products of Sec. 6.1 and the truncated SVD of Sec. 6.2); how requests
+ * share the GPU has no paper counterpart.
+ *
+ * A server owns one stream.  ssa_server_submit copies a request (host data
+ * only) into a FIFO queue and returns a ticket.  Each ssa_server_step
+ *   1. admits queued requests in arrival order while the sum of the device
+ *      bytes estimated for the live requests stays within memory_budget and
+ *      fewer than max_live are live (a request larger than the whole budget
+ *      finishes at once with SSA_ENOMEM);
+ *   2. embeds the admitted ones together, builds their spectra and Lanczos
+ *      workspaces and adds them to the live set;
+ *   3. runs ONE thick-restart Lanczos cycle for every live request in shared
+ *      launches (each request at its own cycle: continuous batching at
+ *      restart granularity), then
+ *   4. retires the converged ones -- final Ritz vectors, the requested
+ *      grouped reconstruction, sigma and outputs copied to host memory owned
+ *      by the server, device memory freed -- and restarts the others.
+ * Series requests (1D, MSSA) and images (2D / shaped) iterate in two
+ * separate sets on the same stream.  A request's result does not depend on
+ * what else is in flight: every product, reduction and small SVD of a
+ * request reads only that request's data, and its start vector comes from
+ * its own seed.
+ */
+typedef struct ssa_server ssa_server;
+
+typedef struct {
+  int64_t memory_budget;   /* device bytes for live requests; <= 0: 40 GiB */
+  int32_t max_live;        /* live requests at most; <= 0: 512 */
+  int32_t prec;            /* SSA_PREC_*: precision of every request of this server */
+} ssa_server_config;
+
+typedef struct {
+  int64_t ticket;
+  int32_t status;          /* SSA_OK, or the error that ended the request */
+  int32_t rank;
+  int64_t out_len;         /* doubles in the reconstruction output: (n_groups + residual) x total */
+  int32_t restarts;        /* restart cycles the request took */
+  int32_t pad_;
+  double max_residual;     /* largest relative residual among the wanted triples */
+  double t_submit, t_admit, t_done;   /* seconds on the server's clock */
+  int64_t device_bytes;    /* device bytes the request held */
+  int64_t estimated_bytes; /* the estimate admission charged against the budget */
+} ssa_server_result;
+
+/* ssa_server_create -- cuda_stream: cudaStream_t to run on (NULL: the server
+ * creates its own).  Errors: SSA_EINVAL (precision), SSA_ECUDA. */
+int ssa_server_create(const ssa_server_config* cfg, void* cuda_stream, ssa_server** out);
+
+/* ssa_server_submit -- queue one request.  in/win/p as for ssa_embed and
+ * ssa_decompose (host data only; the server copies it, so the caller's
+ * buffers may be reused at once; p->prec is replaced by the server's);
+ * group_of / n_groups / residual as for ssa_reconstruct (n_groups = 0 and
+ * residual = 0: no reconstruction).  *ticket names the request.
+ * Errors: SSA_EINVAL (null or empty input, MSSA without lengths). */
+int ssa_server_submit(ssa_server* s, const ssa_input* in, const ssa_window* win, const ssa_params* p,
+                      const int32_t* group_of, int32_t n_groups, int32_t residual, int64_t* ticket);
+
+/* ssa_server_step -- one admission + one restart cycle + retirement (above);
+ * waits for the GPU.  *n_done (may be NULL): requests finished in this step.
+ * A request-level failure ends only that request (its status says why); a
+ * return other than SSA_OK is a failure of the server's stream itself. */
+int ssa_server_step(ssa_server* s, int32_t* n_done);
+
+/* ssa_server_stats -- queued, live and finished-but-not-taken requests, and
+ * the device bytes charged to live requests.  Any pointer may be NULL. */
+int ssa_server_stats(const ssa_server* s, int64_t* queued, int64_t* live, int64_t* finished, int64_t* bytes_live);
+
+/* ssa_server_finished -- up to cap tickets of finished requests not taken
+ * yet, in ticket order, into tickets[]; *n = how many were written. */
+int ssa_server_finished(const ssa_server* s, int64_t* tickets, int32_t cap, int32_t* n);
+
+/* ssa_server_take -- copy a finished request's result out and forget it.
+ *   res    (may be NULL) summary above
+ *   sigma  (may be NULL) host, rank doubles
+ *   out    (may be NULL) host, out_len doubles, row-major (n_groups + residual) x total
+ *          as ssa_reconstruct writes it (NaN outside the observed set)
+ * Errors: SSA_ESTATE (unknown ticket or not finished yet). */
+int ssa_server_take(ssa_server* s, int64_t ticket, ssa_server_result* res, double* sigma, double* out);
+
+/* ssa_server_clock -- seconds since the server was created (its time base). */
+double ssa_server_clock(const ssa_server* s);
+
+/* ssa_server_destroy -- wait for the stream, free every request (queued,
+ * live or finished) and the server (NULL is a no-op). */
+void ssa_server_destroy(ssa_server* s);
 
 /* ssa_synchronize -- wait for the context's stream. */
 int ssa_synchronize(ssa_ctx* ctx);

@@ -35,8 +35,9 @@ import numpy as np
 
 __all__ = [
     "Problem", "window_set", "origin_set", "trajectory_matrix",
-    "trajectory_columns", "weights", "svd_eigen", "svd_jacobi", "decompose",
+    "trajectory_columns", "weights", "svd_eigen", "svd_eigen_t", "svd_jacobi", "decompose",
     "reconstruct", "reconstruct_at", "matvec", "rmatvec",
+    "series_rows", "series_cols", "series_hankelize_at",
 ]
 
 
@@ -222,6 +223,26 @@ def svd_eigen(P: Problem, r: int | None = None):
     return sigma, U, V
 
 
+def svd_eigen_t(P: Problem, r: int | None = None):
+    """Step 2 of Sec. 2.1 applied to ``X^T`` (for ``K < L``): the singular
+    triples of ``X^T`` are those of ``X`` with U and V exchanged, so
+    ``S' = X^T X`` (K x K) gives ``V_j`` and ``sigma_j``, and
+    ``U_j = X V_j / sigma_j``.  Forms the explicit matrix; meant for small K.
+    """
+    X = P.matrix()
+    lam, V = np.linalg.eigh(X.T @ X)
+    order = np.argsort(lam)[::-1]
+    lam, V = lam[order], V[:, order]
+    d = int(np.sum(lam > lam[0] * 1e-28)) if lam[0] > 0 else 0
+    if r is None:
+        r = d
+    r = min(r, d)
+    sigma = np.sqrt(lam[:r])
+    V = V[:, :r]
+    U = (X @ V) / sigma[None, :]
+    return sigma, U, V
+
+
 def _round_robin(n: int):
     """Pairings of a round-robin tournament on n (even) players: n-1 rounds of
     n/2 disjoint pairs covering every pair once."""
@@ -291,6 +312,8 @@ def decompose(P: Problem, r: int, method: str = "eigen"):
     is positive (singular vectors are defined up to sign, Sec. 3.4)."""
     if method == "eigen":
         sigma, U, V = svd_eigen(P, r)
+    elif method == "eigen_t":
+        sigma, U, V = svd_eigen_t(P, r)
     elif method == "jacobi":
         sigma, U, V = svd_jacobi(P.matrix())
         sigma, U, V = sigma[:r], U[:, :r], V[:, :r]
@@ -370,3 +393,38 @@ def reconstruct_at(P: Problem, Ug: np.ndarray, points, c: int = 0) -> np.ndarray
         proj = Ug @ (Ug.T @ Xc)                                   # L x |A_k|
         vals.append(float(np.mean(proj[np.array(rows), np.arange(len(rows))])))
     return np.array(vals)
+
+
+# ---------------------------------------------------------------- long series, one entry at a time
+# For series too long for an explicit trajectory matrix: single rows and
+# columns of X, and single reconstructed elements, straight from the
+# embedding X_ij = x_{i+j} (eq. ssa_embedding, 0-based) and the averaging of
+# Step 4 (Sec. 2.1) over the anti-diagonal i + j = p.
+def series_rows(x, L: int, rows, v) -> np.ndarray:
+    """``(X v)_i`` for the listed rows i: ``sum_j x[i + j] v[j]``."""
+    x = np.asarray(x, dtype=np.float64)
+    K = len(x) - L + 1
+    v = np.asarray(v, dtype=np.float64)
+    return np.array([float(x[i:i + K] @ v) for i in rows])
+
+
+def series_cols(x, L: int, cols, u) -> np.ndarray:
+    """``(X^T u)_j`` for the listed columns j: ``sum_i x[i + j] u[i]``."""
+    x = np.asarray(x, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    return np.array([float(x[j:j + L] @ u) for j in cols])
+
+
+def series_hankelize_at(sigma, U, V, group, points) -> np.ndarray:
+    """Element p of the reconstruction of ``group`` from the triples
+    ``(sigma_i, U_i, V_i)``: the mean over the anti-diagonal ``i + j = p`` of
+    ``sum_{c in group} sigma_c U[i, c] V[j, c]``."""
+    L, K = U.shape[0], V.shape[0]
+    g = list(group)
+    s = np.asarray(sigma, dtype=np.float64)[g]
+    out = []
+    for p in points:
+        i = np.arange(max(0, p - K + 1), min(p, L - 1) + 1)
+        vals = (U[i][:, g] * s[None, :] * V[p - i][:, g]).sum(axis=1)
+        out.append(float(vals.mean()))
+    return np.array(out)

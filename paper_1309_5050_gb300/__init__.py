@@ -14,7 +14,7 @@ from . import _lib as L
 from ._lib import (SSA_1D, SSA_2D, SSA_F32, SSA_F64, SSA_MSSA,  # noqa: F401
                    SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64, SSAError)
 
-__all__ = ["SSA", "embed_multi_batch", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
+__all__ = ["SSA", "Server", "embed_multi_batch", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
            "load", "SSAError", "PREC"]
 
 PREC = {"fp32": SSA_PREC_FP32FFT_FP64REORTH, "fp64": SSA_PREC_FP64}
@@ -197,22 +197,12 @@ class SSA:
         return self.layout[1] * self.layout[2]
 
     def _split(self, flat):
-        kind = self.layout[0]
-        if kind == "1d":
-            return flat
-        if kind == "mssa":
-            offs = np.concatenate([[0], np.cumsum(self.layout[1])])
-            return [flat[offs[i]:offs[i + 1]] for i in range(len(self.layout[1]))]
-        return flat.reshape((self.layout[1], self.layout[2]), order="F")
+        return _split_layout(self.layout, flat)
 
     def reconstruct(self, groups, residual: bool = False):
         """groups: list of lists of 0-based component indices.  Returns one
         array per group (plus the residual) in the input's shape; NaN outside N'."""
-        need = max([self.rank] + [i + 1 for g in groups for i in g])
-        gof = np.full(max(need, 1), -1, dtype=np.int32)
-        for g, idx in enumerate(groups):
-            for i in idx:
-                gof[i] = g
+        gof = _group_of(groups, self.rank)
         nout = len(groups) + (1 if residual else 0)
         total = self._total()
         out = np.zeros(total * nout)
@@ -247,6 +237,159 @@ class SSA:
         if self.ctx:
             self._lib.ssa_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _split_layout(layout, flat):
+    """One flat output (the library's element order) in the input's shape."""
+    kind = layout[0]
+    if kind == "1d":
+        return flat
+    if kind == "mssa":
+        offs = np.concatenate([[0], np.cumsum(layout[1])])
+        return [flat[offs[i]:offs[i + 1]] for i in range(len(layout[1]))]
+    return flat.reshape((layout[1], layout[2]), order="F")
+
+
+def _group_of(groups, rank):
+    need = max([rank] + [i + 1 for g in groups for i in g])
+    gof = np.full(max(need, 1), -1, dtype=np.int32)
+    for g, idx in enumerate(groups):
+        for i in idx:
+            gof[i] = g
+    return gof
+
+
+class Server:
+    """Many SSA requests in flight on one GPU (continuous batching at
+    restart-cycle granularity, admission by a device-memory budget); the C
+    side is ssa_server_* in include/ssa.h.  Requests take host data."""
+
+    def __init__(self, memory_budget: int = 40 << 30, max_live: int = 512, prec: str = "fp32", stream=None):
+        self._lib = L.load()
+        cfg = L.ssa_server_config(memory_budget=int(memory_budget), max_live=int(max_live), prec=PREC[prec])
+        h = C.c_void_p()
+        L.check(self._lib.ssa_server_create(C.byref(cfg), _stream_ptr(stream), C.byref(h)), "ssa_server_create")
+        self.h = h
+        self._meta = {}
+
+    def _submit(self, inp, win, layout, total, rank, groups, residual, seed, tol, krylov_dim, max_restarts):
+        groups = [] if groups is None else groups
+        p = L.ssa_params(rank=rank, krylov_dim=krylov_dim, max_restarts=max_restarts, prec=0, tol=tol, seed=seed)
+        gof = _group_of(groups, rank)
+        t = C.c_int64()
+        L.check(self._lib.ssa_server_submit(self.h, C.byref(inp), C.byref(win), C.byref(p),
+                                            gof.ctypes.data if groups else None, len(groups),
+                                            1 if residual else 0, C.byref(t)), "ssa_server_submit")
+        self._meta[t.value] = (layout, total, rank, len(groups) + (1 if residual else 0))
+        return t.value
+
+    def submit_series(self, x, L_: int, rank: int, groups=None, residual: bool = False, seed: int = 0,
+                      tol: float = 0.0, krylov_dim: int = 0, max_restarts: int = 0) -> int:
+        a = np.ascontiguousarray(x)
+        if a.dtype not in (np.float32, np.float64):
+            a = a.astype(np.float64)
+        code = SSA_F32 if a.dtype == np.float32 else SSA_F64
+        n = int(a.shape[0])
+        inp = L.ssa_input(kind=SSA_1D, dtype=code, on_device=0, n_series=1, data=a.ctypes.data, n=n)
+        return self._submit(inp, L.ssa_window(L=L_), ("1d", n), n, rank, groups, residual, seed, tol,
+                            krylov_dim, max_restarts)
+
+    def submit_multi(self, xs, L_: int, rank: int, groups=None, residual: bool = False, seed: int = 0,
+                     tol: float = 0.0, krylov_dim: int = 0, max_restarts: int = 0, dtype=np.float32) -> int:
+        lens = np.array([len(v) for v in xs], dtype=np.int64)
+        cat = np.ascontiguousarray(np.concatenate([np.asarray(v, dtype=dtype) for v in xs]))
+        code = SSA_F32 if cat.dtype == np.float32 else SSA_F64
+        inp = L.ssa_input(kind=SSA_MSSA, dtype=code, on_device=0, n_series=len(lens), data=cat.ctypes.data,
+                          lengths=lens.ctypes.data_as(C.POINTER(C.c_int64)))
+        return self._submit(inp, L.ssa_window(L=L_), ("mssa", lens.copy()), int(lens.sum()), rank, groups,
+                            residual, seed, tol, krylov_dim, max_restarts)
+
+    def submit_image(self, x, lx: int, ly: int, rank: int, wmask=None, mask=None, groups=None,
+                     residual: bool = False, seed: int = 0, tol: float = 0.0, krylov_dim: int = 0,
+                     max_restarts: int = 0) -> int:
+        a = np.asarray(x)
+        if a.dtype not in (np.float32, np.float64):
+            a = a.astype(np.float64)
+        nx, ny = a.shape
+        af = np.asfortranarray(a)
+        code = SSA_F32 if af.dtype == np.float32 else SSA_F64
+        mptr = None
+        if mask is not None:
+            m = np.asfortranarray(np.asarray(mask, dtype=np.uint8))
+            mptr = m.ctypes.data
+        wptr = None
+        if wmask is not None:
+            w = np.asfortranarray(np.asarray(wmask, dtype=np.uint8))
+            wptr = w.ctypes.data
+            lx, ly = w.shape
+        inp = L.ssa_input(kind=SSA_2D, dtype=code, on_device=0, n_series=1, data=af.ctypes.data, nx=nx, ny=ny,
+                          mask=mptr)
+        win = L.ssa_window(lx=lx, ly=ly, wmask=wptr)
+        return self._submit(inp, win, ("2d", nx, ny), nx * ny, rank, groups, residual, seed, tol, krylov_dim,
+                            max_restarts)
+
+    def step(self) -> int:
+        """Admit, run one restart cycle for every live request, retire the
+        converged ones; returns how many finished."""
+        n = C.c_int32()
+        L.check(self._lib.ssa_server_step(self.h, C.byref(n)), "ssa_server_step")
+        return n.value
+
+    def stats(self) -> dict:
+        q, lv, f, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        L.check(self._lib.ssa_server_stats(self.h, C.byref(q), C.byref(lv), C.byref(f), C.byref(b)),
+                "ssa_server_stats")
+        return {"queued": q.value, "live": lv.value, "finished": f.value, "bytes_live": b.value}
+
+    def finished(self, cap: int = 4096) -> list:
+        """Tickets of finished requests not taken yet."""
+        buf = (C.c_int64 * cap)()
+        n = C.c_int32()
+        L.check(self._lib.ssa_server_finished(self.h, buf, cap, C.byref(n)), "ssa_server_finished")
+        return [buf[i] for i in range(n.value)]
+
+    def take(self, ticket: int) -> dict:
+        """Result of a finished request: status, sigma, outputs (one per group,
+        plus the residual, in the input's shape) and its timestamps."""
+        if ticket not in self._meta:        # unknown or already taken: the library says which
+            L.check(self._lib.ssa_server_take(self.h, ticket, None, None, None), "ssa_server_take")
+        layout, total, rank, nout = self._meta[ticket]
+        res = L.ssa_server_result()
+        sig = np.zeros(max(rank, 1))
+        out = np.zeros(max(total * nout, 1))
+        L.check(self._lib.ssa_server_take(self.h, ticket, C.byref(res), sig.ctypes.data, out.ctypes.data),
+                "ssa_server_take")
+        del self._meta[ticket]
+        d = {f: getattr(res, f) for f, _ in L.ssa_server_result._fields_ if f != "pad_"}
+        d["sigma"] = sig[:rank]
+        d["outputs"] = [_split_layout(layout, out[g * total:(g + 1) * total]) for g in range(nout)] \
+            if res.out_len else []
+        return d
+
+    def clock(self) -> float:
+        return float(self._lib.ssa_server_clock(self.h))
+
+    def drain(self, max_steps: int = 1_000_000) -> int:
+        """Step until nothing is queued or live; returns the steps taken."""
+        steps = 0
+        while steps < max_steps:
+            s = self.stats()
+            if s["queued"] == 0 and s["live"] == 0:
+                break
+            self.step()
+            steps += 1
+        return steps
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.ssa_server_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

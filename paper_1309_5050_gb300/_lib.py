@@ -23,6 +23,8 @@ EXPORTS = [
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
     "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
     "ssa_matvec_series_noalloc", "ssa_noalloc_last_error",
+    "ssa_server_create", "ssa_server_submit", "ssa_server_step", "ssa_server_stats", "ssa_server_finished", "ssa_server_take",
+    "ssa_server_clock", "ssa_server_destroy",
 ]
 PHASES = ["shapes", "spectrum", "matvec", "short", "long", "ritz", "recon"]
 
@@ -49,6 +51,17 @@ class ssa_info(C.Structure):
                 ("restarts", C.c_int32), ("converged", C.c_int32), ("prec", C.c_int32),
                 ("fft_mx", C.c_int64), ("fft_my", C.c_int64), ("max_residual", C.c_double),
                 ("device_bytes", C.c_int64)]
+
+
+class ssa_server_config(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("max_live", C.c_int32), ("prec", C.c_int32)]
+
+
+class ssa_server_result(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("status", C.c_int32), ("rank", C.c_int32), ("out_len", C.c_int64),
+                ("restarts", C.c_int32), ("pad_", C.c_int32), ("max_residual", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("device_bytes", C.c_int64), ("estimated_bytes", C.c_int64)]
 
 
 _lib = None
@@ -99,6 +112,18 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.ssa_matvec_series_noalloc.argtypes = [P, C.c_int64, C.c_int64, C.c_int32, P, P, P]
     lib.ssa_noalloc_last_error.argtypes = []
     lib.ssa_noalloc_last_error.restype = C.c_char_p
+    lib.ssa_server_create.argtypes = [C.POINTER(ssa_server_config), P, C.POINTER(P)]
+    lib.ssa_server_submit.argtypes = [P, C.POINTER(ssa_input), C.POINTER(ssa_window), C.POINTER(ssa_params),
+                                      P, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
+    lib.ssa_server_step.argtypes = [P, C.POINTER(C.c_int32)]
+    lib.ssa_server_stats.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]
+    lib.ssa_server_finished.argtypes = [P, C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_int32)]
+    lib.ssa_server_take.argtypes = [P, C.c_int64, C.POINTER(ssa_server_result), P, P]
+    lib.ssa_server_clock.argtypes = [P]
+    lib.ssa_server_clock.restype = C.c_double
+    lib.ssa_server_destroy.argtypes = [P]
+    lib.ssa_server_destroy.restype = None
     _lib = lib
     return lib
 

@@ -6,10 +6,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <chrono>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <set>
@@ -230,9 +233,46 @@ struct ShapeSet {          // a set of grid points as per-column bit rows
     MapDev m;
     m.dense = dense ? 1 : 0; m.bx = bx; m.by = by; m.words = words;
     m.bits = bits; m.colbase = colbase;
+    m.limit = INT64_MAX;
     return m;
   }
 };
+
+// Long series (FFT grid above the single-CTA limit) are handled in segment
+// form: with block length B, the L x K Hankel matrix is the Hankel-block-
+// Hankel matrix of the "segment image" S[i, c] = x[cB + i] (0 <= i < 2B-1):
+// window B x ceil(L/B), origins B x ceil(K/B), window element (i, a) <-> row
+// aB + i, origin (j, b) <-> column bB + j, so X_{aB+i, bB+j} = x[(a+b)B + i + j]
+// = S[i + j, a + b].  Rows and columns past L and K are absent (zero input,
+// output dropped), which is what MapDev::limit expresses.
+constexpr int FOLD_B = 4096;           // segment length: grid 2B = 8192 along x
+constexpr int FOLD_MIN_LOG2 = 15;      // series needing a 2^15 grid or longer are folded
+
+static MapDev fold_map(int B, int nb, int64_t count) {
+  MapDev m;
+  m.dense = 1; m.bx = B; m.by = nb; m.words = 0; m.bits = nullptr; m.colbase = nullptr; m.limit = count;
+  return m;
+}
+
+// Segment-form geometry of complete series of lengths n[] with window L.
+struct FoldGeom {
+  int B = FOLD_B, lb = 0, log2My = 0;
+  std::vector<int> kb, fy;
+};
+static FoldGeom fold_geometry(const std::vector<int64_t>& n, int64_t L) {
+  FoldGeom g;
+  g.lb = (int)((L + g.B - 1) / g.B);
+  int fmax = 1;
+  for (int64_t np : n) {
+    const int64_t K = std::max<int64_t>(np - L + 1, 1);
+    const int kb = (int)((K + g.B - 1) / g.B);
+    g.kb.push_back(kb);
+    g.fy.push_back(g.lb + kb - 1);
+    fmax = std::max(fmax, g.lb + kb - 1);
+  }
+  g.log2My = std::max(ilog2_ceil(fmax), 1);
+  return g;
+}
 
 struct Channel {
   int64_t nx = 0, ny = 0;
@@ -246,6 +286,7 @@ struct Channel {
   int nwords = 0;
   void* xh32 = nullptr;        // spectra
   void* xh64 = nullptr;
+  int kb = 0, fy = 0;          // segment form: origin blocks ceil(K_p/B), segments lb + kb - 1
 };
 
 struct Workspace {             // Lanczos + results, per precision
@@ -277,6 +318,7 @@ struct ssa_ctx {
   int64_t total = 0;           // data elements
   void* data = nullptr;        // device copy of the input (dtype)
   int log2Mx = 0, log2My = 0;
+  int fold_B = 0, lb = 0;      // segment form of long series (0: off), window blocks ceil(L/B)
   ShapeSet Lset;               // window set (bounding box ex x ey)
   int ex = 0, ey = 0;
   uint32_t* wrows = nullptr;   // window rows (bits), ey x wwords
@@ -512,6 +554,10 @@ static int embed_stage3(ssa_ctx* c, int err) {
   c->cur = nullptr;
   if (err) return fail(SSA_EINVAL, "input holds +-Inf at an observed position");
   if (c->K <= 0) return fail(SSA_EEMPTY, "no window origin keeps the whole window inside the observed set");
+  if (c->fold_B)
+    for (auto& h : c->ch)
+      if (!h.K.dense || h.K.count != h.nx - c->L + 1)
+        return fail(SSA_EUNSUPPORTED, "series longer than %d samples must have no missing values", 1 << (FOLD_MIN_LOG2 - 1));
   return SSA_OK;
 }
 
@@ -572,16 +618,25 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
       sp.obs = h.obs; sp.obs_words = h.nwords;
       sp.data_double = c->dtype == SSA_F64;
       sp.nx = (int)h.nx; sp.ny = (int)h.ny;
+      sp.ld = h.nx; sp.n_lin = h.nx * h.ny;
+      if (c->fold_B) {
+        // segment image: column s is x[sB .. sB + 2B - 2] (complete series)
+        sp.obs = nullptr; sp.obs_words = 0;
+        sp.nx = 2 * c->fold_B - 1; sp.ny = h.fy;
+        sp.ld = c->fold_B; sp.n_lin = h.nx;
+      }
       sp.log2Mx = h.log2M; sp.log2My = c->log2My;
       sp.g1 = g1 ? (Cx<T>*)g1 + q * (size_t)(H + 1) * My : nullptr;
       sp.xh = (Cx<T>*)xh;
       sp.scale = (T)(1.0 / ((double)(2 * Hc) * (double)My));
       items.push_back(sp);
-      YItem<T> y;
-      y.src = sp.g1; y.dst = sp.xh; y.mul = nullptr; y.st = nullptr;
-      y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = (int)h.ny; y.out_hi = My; y.scale = T(0);
-      yitems.push_back(y);
-      max_ny = std::max(max_ny, (int)h.ny);
+      if (c->log2My > 0) {
+        YItem<T> y;
+        y.src = sp.g1; y.dst = sp.xh; y.mul = nullptr; y.st = nullptr;
+        y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = sp.ny; y.out_hi = My; y.scale = T(0);
+        yitems.push_back(y);
+      }
+      max_ny = std::max(max_ny, sp.ny);
     }
     max_log2Mx = std::max(max_log2Mx, c->log2Mx);
     max_log2My = std::max(max_log2My, c->log2My);
@@ -593,12 +648,13 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
   SpecItem<T>* di = nullptr;
   YItem<T>* dy = nullptr;
   if (cudaMallocAsync((void**)&di, sizeof(SpecItem<T>) * items.size(), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&dy, sizeof(YItem<T>) * yitems.size(), st) != cudaSuccess)
+      cudaMallocAsync((void**)&dy, sizeof(YItem<T>) * std::max<size_t>(yitems.size(), 1), st) != cudaSuccess)
     return fail(SSA_ENOMEM, "spectrum items");
   if (g_ring.copy(di, items.data(), sizeof(SpecItem<T>) * items.size(), st) != SSA_OK ||
-      g_ring.copy(dy, yitems.data(), sizeof(YItem<T>) * yitems.size(), st) != SSA_OK)
+      (!yitems.empty() && g_ring.copy(dy, yitems.data(), sizeof(YItem<T>) * yitems.size(), st) != SSA_OK))
     return fail(SSA_ECUDA, "spectrum item upload");
-  launch_spec<T>(di, dy, (int)items.size(), max_log2Mx, max_log2My, max_ny, twiddles<T>(cs[0]->device), st);
+  launch_spec<T>(di, (int)items.size(), dy, (int)yitems.size(), max_log2Mx, max_log2My, max_ny,
+                 twiddles<T>(cs[0]->device), st);
   CU(cudaGetLastError());
   cudaFreeAsync(di, st);
   cudaFreeAsync(dy, st);
@@ -618,11 +674,28 @@ static int ensure_spectrum(ssa_ctx* c) { return ensure_spectra<T>(&c, 1, c->stre
 // Direction "X" maps K -> L (sum over channels); "XT" maps L -> K (slices).
 template <typename T>
 struct MvSet {
-  std::vector<MvItem<T>> items;
-  std::vector<YItem<T>> yitems;
-  MvItem<T>* d_items = nullptr;
-  YItem<T>* d_y = nullptr;
+  // series on one FFT grid (fused single-CTA products) and grids with a y
+  // extent (images, segment-form series: x-pass, y-pass, x-pass)
+  std::vector<MvItem<T>> items1, items2;
+  std::vector<YItem<T>> yitems2;
+  MvItem<T>* d1 = nullptr;
+  MvItem<T>* d2 = nullptr;
+  YItem<T>* dy2 = nullptr;
   int max_y_in = 0, max_y_out = 0;
+  int lx1 = 1, lx2 = 1, ly2 = 0;   // largest log2 grid sizes of each list
+  void add(const MvItem<T>& m) {
+    if (m.log2My == 0) {
+      items1.push_back(m);
+      lx1 = std::max(lx1, (int)m.log2Mx);
+    } else {
+      items2.push_back(m);
+      lx2 = std::max(lx2, (int)m.log2Mx);
+      ly2 = std::max(ly2, (int)m.log2My);
+      max_y_in = std::max(max_y_in, (int)m.y_in_hi);
+      max_y_out = std::max(max_y_out, (int)m.y_out_hi);
+    }
+  }
+  size_t size() const { return items1.size() + items2.size(); }
 };
 
 template <typename T>
@@ -639,6 +712,13 @@ static MvItem<T> make_mv(ssa_ctx* c, const Channel& h, bool XT, VecRef in, int i
   m.in_type = in_type;
   m.y_in_hi = XT ? c->ey : h.cy;
   m.y_out_hi = XT ? h.cy : c->ey;
+  if (c->fold_B) {
+    const MapDev wl = fold_map(c->fold_B, c->lb, c->L), ko = fold_map(c->fold_B, h.kb, h.K.count);
+    m.min = XT ? wl : ko;
+    m.mout = XT ? ko : wl;
+    m.y_in_hi = XT ? c->lb : h.kb;
+    m.y_out_hi = XT ? h.kb : c->lb;
+  }
   m.pad_ = 0;
   return m;
 }
@@ -652,26 +732,27 @@ static YItem<T> ymv(const MvItem<T>& m) {
   return y;
 }
 
-template <typename T>
-static int finish_set(ssa_ctx* c, MvSet<T>& s) {
-  for (auto& m : s.items) {
-    s.yitems.push_back(ymv(m));
-    s.max_y_in = std::max(s.max_y_in, m.y_in_hi);
-    s.max_y_out = std::max(s.max_y_out, m.y_out_hi);
+// y-pass items of the set's grids, then both lists to the device (uploader
+// up(vector, device pointer) of the caller's choosing)
+template <typename T, typename Up>
+static int finish_set(MvSet<T>& s, Up&& up) {
+  s.yitems2.clear();
+  for (auto& m : s.items2) s.yitems2.push_back(ymv(m));
+  if (!s.items1.empty()) TRY(up(s.items1, &s.d1));
+  if (!s.items2.empty()) {
+    TRY(up(s.items2, &s.d2));
+    TRY(up(s.yitems2, &s.dy2));
   }
-  TRY(upload(c, s.items, &s.d_items));
-  TRY(upload(c, s.yitems, &s.d_y));
   return SSA_OK;
 }
 
 template <typename T>
-static void run_mv(ssa_ctx* c, const MvSet<T>& s, int max_log2Mx, int max_log2My, int step) {
+static void run_mv(ssa_ctx* c, const MvSet<T>& s, int step) {
   PhaseScope ps_(PH_MATVEC, c->stream);
-  const int n = (int)s.items.size();
-  if (max_log2My == 0)
-    launch_mv1d<T>(s.d_items, n, max_log2Mx, step, twiddles<T>(c->device), c->stream);
-  else
-    launch_mv2d<T>(s.d_items, s.d_y, n, max_log2Mx, max_log2My, s.max_y_in, s.max_y_out, step,
+  if (!s.items1.empty())
+    launch_mv1d<T>(s.d1, (int)s.items1.size(), s.lx1, step, twiddles<T>(c->device), c->stream);
+  if (!s.items2.empty())
+    launch_mv2d<T>(s.d2, s.dy2, (int)s.items2.size(), s.lx2, s.ly2, s.max_y_in, s.max_y_out, step,
                    twiddles<T>(c->device), c->stream);
 }
 
@@ -861,22 +942,24 @@ struct LzEngine {
           // A v = X v : K -> L partial per channel
           vin.base = w.V; vin.off = h.koff; vin.ld = w.Kl; vin.st = w.st; vin.jdelta = 0;
           vout.base = w.parts_s; vout.off = (int64_t)q * w.Ls; vout.ld = 0; vout.st = nullptr;
-          mvA.items.push_back(make_mv<T>(c, h, false, vin, 0, vout, g1, g2, w.st));
-          mvA.items.back().in_scale = w.colscale;
+          MvItem<T> m = make_mv<T>(c, h, false, vin, 0, vout, g1, g2, w.st);
+          m.in_scale = w.colscale;
+          mvA.add(m);
           // A^T u = X^T u : L -> K slice
           vin.base = w.U; vin.off = 0; vin.ld = w.Ls; vin.st = w.st;
           vout.base = w.parts_l; vout.off = h.koff; vout.st = nullptr;
-          mvAT.items.push_back(make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st));
+          mvAT.add(make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st));
         } else {
           // A v = X^T v : L -> K slice
           vin.base = w.V; vin.off = 0; vin.ld = w.Kl; vin.st = w.st;
           vout.base = w.parts_s; vout.off = h.koff; vout.st = nullptr;
-          mvA.items.push_back(make_mv<T>(c, h, true, vin, 0, vout, g1, g2, w.st));
-          mvA.items.back().in_scale = w.colscale;
+          MvItem<T> m = make_mv<T>(c, h, true, vin, 0, vout, g1, g2, w.st);
+          m.in_scale = w.colscale;
+          mvA.add(m);
           // A^T u = X u : K -> L partial
           vin.base = w.U; vin.off = h.koff; vin.ld = w.Ls; vin.st = w.st;
           vout.base = w.parts_l; vout.off = (int64_t)q * w.Kl; vout.st = nullptr;
-          mvAT.items.push_back(make_mv<T>(c, h, false, vin, 1, vout, g1, g2, w.st));
+          mvAT.add(make_mv<T>(c, h, false, vin, 1, vout, g1, g2, w.st));
         }
       }
       max_blk_s = std::max(max_blk_s, w.nblk_s);
@@ -891,10 +974,9 @@ struct LzEngine {
     }
     if (live.empty()) return SSA_OK;
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
-    for (auto& m : mvA.items) { mvA.yitems.push_back(ymv(m)); mvA.max_y_in = std::max(mvA.max_y_in, m.y_in_hi); mvA.max_y_out = std::max(mvA.max_y_out, m.y_out_hi); }
-    for (auto& m : mvAT.items) { mvAT.yitems.push_back(ymv(m)); mvAT.max_y_in = std::max(mvAT.max_y_in, m.y_in_hi); mvAT.max_y_out = std::max(mvAT.max_y_out, m.y_out_hi); }
-    TRY(up(mvA.items, &mvA.d_items)); TRY(up(mvA.yitems, &mvA.d_y));
-    TRY(up(mvAT.items, &mvAT.d_items)); TRY(up(mvAT.yitems, &mvAT.d_y));
+    auto upl = [&](auto& v, auto** d) { return up(v, d); };
+    TRY(finish_set(mvA, upl));
+    TRY(finish_set(mvAT, upl));
     if (cudaMallocAsync((void**)&d_stg, sizeof(LzState) * live.size(), st) != cudaSuccess)
       return fail(SSA_ENOMEM, "engine state buffer");
     dev_tmp.push_back(d_stg);
@@ -936,9 +1018,9 @@ struct LzEngine {
       steps = std::max(steps, w.k - j0);
     }
     for (int s = 0; s < steps; ++s) {
-      run_mv<T>(live[0], mvA, max_log2Mx, max_log2My, s);
+      run_mv<T>(live[0], mvA, s);
       { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, nl, max_blk_s, s, st); }
-      run_mv<T>(live[0], mvAT, max_log2Mx, max_log2My, s);
+      run_mv<T>(live[0], mvAT, s);
       { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, nl, max_blk_l, s, st); }
     }
     { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
@@ -1114,23 +1196,29 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
   std::vector<void*> tmp;
   std::vector<double*> dout(n, nullptr);
   const Cx<T>* tw = twiddles<T>(c0->device);
-  if (c0->log2My == 0) {
-    // ---- series: F(U_i) once per problem, then one CTA per (problem, group, channel)
+  for (int p = 0; p < n; ++p) {
+    const int nout = req[p].ng + (req[p].residual ? 1 : 0);
+    if (on_device) dout[p] = req[p].out;
+    else {
+      TRY(c0->alloc((void**)&dout[p], sizeof(double) * (size_t)cs[p]->total * nout));
+      tmp.push_back(dout[p]);
+    }
+  }
+  // ---- series on one grid: F(U_i) once per problem, then one CTA per (problem, group, channel)
+  {
     std::vector<RecColItem<T, TV>> ui;
     std::vector<Rec1Item<T, TV>> ri;
     int max_log2Mx = 1;
     for (int p = 0; p < n; ++p) {
       ssa_ctx* c = cs[p];
+      if (c->log2My != 0) continue;
       Workspace& w = c->ws;
-      const int r = w.r, ng = req[p].ng, nout = ng + (req[p].residual ? 1 : 0);
+      const int r = w.r, ng = req[p].ng;
       const int H = 1 << (c->log2Mx - 1);
       Cx<T>* gu = nullptr;
       TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * (size_t)(H + 1) * r));
       tmp.push_back(gu);
-      double* o = nullptr;
-      if (on_device) o = req[p].out;
-      else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
-      dout[p] = o;
+      double* o = dout[p];
       for (int i = 0; i < r; ++i) {
         RecColItem<T, TV> u;
         u.vec = (const TV*)w.Uo + (size_t)c->L * i; u.map = c->Lset.dev(); u.dst = gu + (size_t)(H + 1) * i;
@@ -1151,90 +1239,118 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         }
       max_log2Mx = std::max(max_log2Mx, c->log2Mx);
     }
-    RecColItem<T, TV>* d_ui = nullptr; Rec1Item<T, TV>* d_ri = nullptr;
-    TRY(upload(c0, ui, &d_ui));
-    TRY(upload(c0, ri, &d_ri));
-    launch_rec_col_fft<T, TV>(d_ui, (int)ui.size(), max_log2Mx, 1, tw, st);
-    launch_rec1d<T, TV>(d_ri, (int)ri.size(), max_log2Mx, tw, st);
-    CU(cudaGetLastError());
-    tmp.push_back(d_ui); tmp.push_back(d_ri);
-  } else {
-    // ---- images: per problem, per component 2D transforms, accumulated per group
-    for (int p = 0; p < n; ++p) {
-      ssa_ctx* c = cs[p];
-      Workspace& w = c->ws;
-      const int r = w.r, ng = req[p].ng, nout = ng + (req[p].residual ? 1 : 0);
-      const int32_t* group_of = req[p].group_of;
-      const Channel& h = c->ch[0];
-      const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
-      const size_t hs = (size_t)(H + 1) * My;
-      double* o = nullptr;
-      if (on_device) o = req[p].out;
-      else { TRY(c0->alloc((void**)&o, sizeof(double) * (size_t)c->total * nout)); tmp.push_back(o); }
-      dout[p] = o;
-      Cx<T> *gx = nullptr, *gu = nullptr, *acc = nullptr, *g2 = nullptr;
-      TRY(c0->alloc((void**)&gx, sizeof(Cx<T>) * hs));
-      TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * hs));
-      TRY(c0->alloc((void**)&acc, sizeof(Cx<T>) * hs * std::max(ng, 1)));
-      TRY(c0->alloc((void**)&g2, sizeof(Cx<T>) * hs));
-      tmp.push_back(gx); tmp.push_back(gu); tmp.push_back(acc); tmp.push_back(g2);
-      CU(cudaMemsetAsync(acc, 0, sizeof(Cx<T>) * hs * std::max(ng, 1), st));
-      std::vector<double> sig(r);
-      CU(cudaMemcpyAsync(sig.data(), w.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-            std::vector<YItem<T>> yu(2);
-      RecColItem<T, TV>* d_cu = nullptr; YItem<T>* d_yu = nullptr;
-      TRY(c0->allocT(&d_cu, 2 * (size_t)r));
-      TRY(c0->allocT(&d_yu, 2 * (size_t)r));
-      tmp.push_back(d_cu); tmp.push_back(d_yu);
-      std::vector<RecColItem<T, TV>> allc;
-      std::vector<YItem<T>> ally;
+    if (!ui.empty()) {
+      RecColItem<T, TV>* d_ui = nullptr; Rec1Item<T, TV>* d_ri = nullptr;
+      TRY(upload(c0, ui, &d_ui));
+      tmp.push_back(d_ui);
+      launch_rec_col_fft<T, TV>(d_ui, (int)ui.size(), max_log2Mx, 1, tw, st);
+      if (!ri.empty()) {
+        TRY(upload(c0, ri, &d_ri));
+        tmp.push_back(d_ri);
+        launch_rec1d<T, TV>(d_ri, (int)ri.size(), max_log2Mx, tw, st);
+      }
+      CU(cudaGetLastError());
+    }
+  }
+  // ---- grids with a y extent, one problem at a time: per component 2D
+  // transforms accumulated per group in frequency space (Lemma hbh_tbt_elmat)
+  for (int p = 0; p < n; ++p) {
+    ssa_ctx* c = cs[p];
+    if (c->log2My == 0) continue;
+    Workspace& w = c->ws;
+    const int r = w.r, ng = req[p].ng;
+    if (ng == 0) continue;
+    const int32_t* group_of = req[p].group_of;
+    const int H = 1 << (c->log2Mx - 1), My = 1 << c->log2My;
+    const size_t hs = (size_t)(H + 1) * My;
+    double* o = dout[p];
+    const bool fold = c->fold_B != 0;
+    int fymax = 1;
+    for (auto& h : c->ch) fymax = std::max(fymax, h.fy);
+    Cx<T> *gx = nullptr, *gu = nullptr, *acc = nullptr, *g2 = nullptr;
+    double* S = nullptr;
+    TRY(c0->alloc((void**)&gx, sizeof(Cx<T>) * hs));
+    TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * hs));
+    TRY(c0->alloc((void**)&acc, sizeof(Cx<T>) * hs * ng));
+    TRY(c0->alloc((void**)&g2, sizeof(Cx<T>) * hs));
+    tmp.push_back(gx); tmp.push_back(gu); tmp.push_back(acc); tmp.push_back(g2);
+    if (fold) {
+      TRY(c0->alloc((void**)&S, sizeof(double) * (size_t)(2 * H) * fymax));
+      tmp.push_back(S);
+    }
+    std::vector<double> sig(r);
+    CU(cudaMemcpyAsync(sig.data(), w.sigma, sizeof(double) * r, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    // items: per (channel, component) two column transforms and two y-passes;
+    // per (channel, group) the inverse y-pass, inverse x-pass and (segment
+    // form) the overlap-add
+    std::vector<RecColItem<T, TV>> allc;
+    std::vector<YItem<T>> ally, yi;
+    std::vector<Rec2Item<T>> xi;
+    std::vector<RecFoldItem> fi;
+    for (size_t q = 0; q < c->ch.size(); ++q) {
+      const Channel& h = c->ch[q];
+      const MapDev wl = fold ? fold_map(c->fold_B, c->lb, c->L) : c->Lset.dev();
+      const MapDev ko = fold ? fold_map(c->fold_B, h.kb, h.K.count) : h.K.dev();
+      const int wcols = fold ? c->lb : c->ey, kcols = fold ? h.kb : h.cy;
       for (int i = 0; i < r; ++i) {
         const int g = group_of[i];
         RecColItem<T, TV> a;
-        a.vec = (const TV*)w.Uo + (size_t)c->L * i; a.map = c->Lset.dev(); a.dst = gx; a.log2Mx = c->log2Mx;
-        a.ncols = c->ey;
+        a.vec = (const TV*)w.Uo + (size_t)c->L * i; a.map = wl; a.dst = gx; a.log2Mx = c->log2Mx;
+        a.ncols = wcols;
         RecColItem<T, TV> b;
-        b.vec = (const TV*)w.Vo + (size_t)c->K * i; b.map = h.K.dev(); b.dst = gx; b.log2Mx = c->log2Mx;
-        b.ncols = h.cy;
+        b.vec = (const TV*)w.Vo + (size_t)c->K * i + h.koff; b.map = ko; b.dst = gx; b.log2Mx = c->log2Mx;
+        b.ncols = kcols;
         YItem<T> ya;
         ya.src = gx; ya.dst = gu; ya.mul = nullptr; ya.st = nullptr; ya.log2Mx = c->log2Mx; ya.log2My = c->log2My;
-        ya.in_hi = c->ey; ya.out_hi = My; ya.scale = T(0);
+        ya.in_hi = wcols; ya.out_hi = My; ya.scale = T(0);
         YItem<T> yb = ya;
-        yb.dst = acc + (size_t)std::max(g, 0) * hs; yb.mul = gu; yb.in_hi = h.cy;
+        yb.dst = acc + (size_t)std::max(g, 0) * hs; yb.mul = gu; yb.in_hi = kcols;
         yb.scale = (T)(sig[i] / ((double)(2 * H) * (double)My));
         allc.push_back(a); allc.push_back(b);
         ally.push_back(ya); ally.push_back(yb);
       }
-      if (g_ring.copy(d_cu, allc.data(), sizeof(RecColItem<T, TV>) * allc.size(), st) != SSA_OK ||
-          g_ring.copy(d_yu, ally.data(), sizeof(YItem<T>) * ally.size(), st) != SSA_OK)
-        return fail(SSA_ECUDA, "item upload failed");
-      for (int i = 0; i < r; ++i) {
-        if (group_of[i] < 0) continue;
-        launch_rec_col_fft<T, TV>(d_cu + 2 * i, 1, c->log2Mx, c->ey, tw, st);
-        launch_ypass<T>(d_yu + 2 * i, 1, Y_FWD, c->log2Mx, c->log2My, -1, tw, st);
-        launch_rec_col_fft<T, TV>(d_cu + 2 * i + 1, 1, c->log2Mx, h.cy, tw, st);
-        launch_ypass<T>(d_yu + 2 * i + 1, 1, Y_CONVACC, c->log2Mx, c->log2My, -1, tw, st);
-      }
-      std::vector<YItem<T>> yi;
-      std::vector<Rec2Item<T>> xi;
+      const int oy = fold ? h.fy : (int)h.ny;
       for (int g = 0; g < ng; ++g) {
         YItem<T> y;
         y.src = acc + (size_t)g * hs; y.dst = g2; y.mul = nullptr; y.st = nullptr;
-        y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = My; y.out_hi = (int)h.ny; y.scale = T(0);
+        y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = My; y.out_hi = oy; y.scale = T(0);
         yi.push_back(y);
         Rec2Item<T> x;
-        x.g2 = g2; x.w = h.w; x.out = o + (size_t)g * c->total; x.log2Mx = c->log2Mx; x.nx = (int)h.nx;
-        x.ny = (int)h.ny; x.pad_ = 0; x.inv_norm = 1.0;
+        x.g2 = g2; x.log2Mx = c->log2Mx; x.pad_ = 0; x.inv_norm = 1.0;
+        if (fold) {
+          x.w = nullptr; x.out = S; x.nx = 2 * H; x.ny = h.fy;
+          fi.push_back({S, h.w, o + (size_t)g * c->total + h.data_off, (int64_t)c->fold_B, h.nx, (int64_t)h.fy});
+        } else {
+          x.w = h.w; x.out = o + (size_t)g * c->total + h.data_off; x.nx = (int)h.nx; x.ny = (int)h.ny;
+        }
         xi.push_back(x);
       }
-      YItem<T>* d_yi = nullptr; Rec2Item<T>* d_xi = nullptr;
-      TRY(upload(c0, yi, &d_yi));
-      TRY(upload(c0, xi, &d_xi));
-      tmp.push_back(d_yi); tmp.push_back(d_xi);
+    }
+    RecColItem<T, TV>* d_cu = nullptr; YItem<T>* d_yu = nullptr; YItem<T>* d_yi = nullptr;
+    Rec2Item<T>* d_xi = nullptr; RecFoldItem* d_fi = nullptr;
+    TRY(upload(c0, allc, &d_cu)); tmp.push_back(d_cu);
+    TRY(upload(c0, ally, &d_yu)); tmp.push_back(d_yu);
+    TRY(upload(c0, yi, &d_yi)); tmp.push_back(d_yi);
+    TRY(upload(c0, xi, &d_xi)); tmp.push_back(d_xi);
+    if (fold) { TRY(upload(c0, fi, &d_fi)); tmp.push_back(d_fi); }
+    for (size_t q = 0; q < c->ch.size(); ++q) {
+      const Channel& h = c->ch[q];
+      const int wcols = fold ? c->lb : c->ey, kcols = fold ? h.kb : h.cy;
+      CU(cudaMemsetAsync(acc, 0, sizeof(Cx<T>) * hs * ng, st));
+      for (int i = 0; i < r; ++i) {
+        if (group_of[i] < 0) continue;
+        const size_t e = 2 * ((size_t)q * r + i);
+        launch_rec_col_fft<T, TV>(d_cu + e, 1, c->log2Mx, wcols, tw, st);
+        launch_ypass<T>(d_yu + e, 1, Y_FWD, c->log2Mx, c->log2My, -1, tw, st);
+        launch_rec_col_fft<T, TV>(d_cu + e + 1, 1, c->log2Mx, kcols, tw, st);
+        launch_ypass<T>(d_yu + e + 1, 1, Y_CONVACC, c->log2Mx, c->log2My, -1, tw, st);
+      }
       for (int g = 0; g < ng; ++g) {
-        launch_ypass<T>(d_yi + g, 1, Y_INV, c->log2Mx, c->log2My, -1, tw, st);
-        launch_rec_xinv<T>(d_xi + g, 1, c->log2Mx, (int)h.ny, tw, st);
+        const size_t e = (size_t)q * ng + g;
+        launch_ypass<T>(d_yi + e, 1, Y_INV, c->log2Mx, c->log2My, -1, tw, st);
+        launch_rec_xinv<T>(d_xi + e, 1, c->log2Mx, xi[e].ny, tw, st);
+        if (fold) launch_rec_fold(d_fi + e, 1, h.nx, st);
       }
       CU(cudaGetLastError());
     }
@@ -1302,11 +1418,11 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
     VecRef vi{}, vo{};
     vi.base = din; vi.off = transpose ? 0 : h.koff; vi.ld = 0; vi.st = nullptr;
     vo.base = dparts; vo.off = transpose ? h.koff : (int64_t)q * nout; vo.ld = 0; vo.st = nullptr;
-    s.items.push_back(make_mv<T>(c, h, transpose != 0, vi, 0, vo, hs ? (Cx<T>*)g1 + q * hs : nullptr,
-                                 hs ? (Cx<T>*)g2 + q * hs : nullptr, nullptr));
+    s.add(make_mv<T>(c, h, transpose != 0, vi, 0, vo, hs ? (Cx<T>*)g1 + q * hs : nullptr,
+                     hs ? (Cx<T>*)g2 + q * hs : nullptr, nullptr));
   }
-  TRY(finish_set(c, s));
-  run_mv<T>(c, s, c->log2Mx, c->log2My, 0);
+  TRY(finish_set(s, [&](auto& v, auto** d) { return upload(c, v, d); }));
+  run_mv<T>(c, s, 0);
   k_sum_parts_to_double<T><<<grid1(nout), 256, 0, c->stream>>>(dparts, nparts, nout, nout, dres); count_launch();
   CU(cudaGetLastError());
   if (!on_device) CU(cudaMemcpyAsync(out, dres, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
@@ -1314,7 +1430,8 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
   c->release(din); c->release(dparts);
   if (!on_device) { c->release(dd); c->release(dres); }
   if (g1) { c->release(g1); c->release(g2); }
-  c->release(s.d_items); c->release(s.d_y);
+  if (s.d1) c->release(s.d1);
+  if (s.d2) { c->release(s.d2); c->release(s.dy2); }
   return SSA_OK;
 }
 
@@ -1368,10 +1485,26 @@ static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_
   for (auto& h : c->ch) { mx = std::max(mx, h.nx); my = std::max(my, h.ny); }
   c->log2Mx = std::max(ilog2_ceil(mx), 4);
   c->log2My = (in->kind == SSA_2D) ? ilog2_ceil(my) : 0;
-  if (c->log2Mx > 14) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along x exceeds 16384", (long long)(1ll << c->log2Mx)));
-  // series of a system each get the shortest grid that holds them (any
-  // M >= N_p gives the same product); images keep the common grid
-  for (auto& h : c->ch) h.log2M = (in->kind == SSA_2D) ? c->log2Mx : std::max(ilog2_ceil(h.nx), 4);
+  if (in->kind != SSA_2D && c->log2Mx >= FOLD_MIN_LOG2) {
+    // long series: segment form on a 2B x My grid (every channel of the system)
+    std::vector<int64_t> ns;
+    for (auto& h : c->ch) ns.push_back(h.nx);
+    const FoldGeom g = fold_geometry(ns, win->L);
+    c->fold_B = g.B;
+    c->lb = g.lb;
+    c->log2Mx = ilog2_ceil(2 * (int64_t)g.B);
+    c->log2My = g.log2My;
+    for (size_t q = 0; q < c->ch.size(); ++q) {
+      c->ch[q].kb = g.kb[q];
+      c->ch[q].fy = g.fy[q];
+      c->ch[q].log2M = c->log2Mx;
+    }
+  } else {
+    if (c->log2Mx > 14) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along x exceeds 16384", (long long)(1ll << c->log2Mx)));
+    // series of a system each get the shortest grid that holds them (any
+    // M >= N_p gives the same product); images keep the common grid
+    for (auto& h : c->ch) h.log2M = (in->kind == SSA_2D) ? c->log2Mx : std::max(ilog2_ceil(h.nx), 4);
+  }
   if (c->log2My > 12) return bail(fail(SSA_EUNSUPPORTED, "FFT length %lld along y exceeds 4096", (long long)(1ll << c->log2My)));
   // data (and mask) to the device; masked samples become NaN in the device copy
   const size_t esz = in->dtype == SSA_F64 ? 8 : 4;
@@ -1568,11 +1701,9 @@ int ssa_embed(const ssa_input* in, const ssa_window* win, void* cuda_stream, ssa
 int ssa_decompose_batch(ssa_ctx* const* ctxs, int32_t n, const ssa_params* params, int32_t* status) {
   if (!ctxs || n < 1 || !params) return fail(SSA_EINVAL, "null argument");
   const int prec = params[0].prec;
-  const bool img = ctxs[0]->log2My > 0;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i]) return fail(SSA_EINVAL, "null context %d", i);
     if (params[i].prec != prec) return fail(SSA_EINVAL, "one precision form per batch");
-    if ((ctxs[i]->log2My > 0) != img) return fail(SSA_EINVAL, "a batch holds only series or only images");
     if (params[i].prec == SSA_PREC_FP64 && ctxs[i]->log2Mx > 13)
       return fail(SSA_EUNSUPPORTED, "FP64 form supports FFT length <= 8192 along x");
   }
@@ -1643,7 +1774,6 @@ int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || !ctxs[i]->ws.done) return fail(SSA_ESTATE, "context %d has no decomposition", i);
     if (ctxs[i]->ws.prec != prec || ctxs[i]->ws.r != ctxs[0]->ws.r) return fail(SSA_EINVAL, "batch mixes precision or rank");
-    if ((ctxs[i]->log2My > 0) != (ctxs[0]->log2My > 0)) return fail(SSA_EINVAL, "batch mixes series and images");
     if (!outs[i]) return fail(SSA_EINVAL, "null output %d", i);
   }
   if (n_groups + (residual ? 1 : 0) == 0) return SSA_OK;
@@ -1725,3 +1855,375 @@ __global__ void k_apply_mask(void* data, int dbl, const uint8_t* m, int64_t n) {
 void launch_apply_mask(void* data, int dbl, const uint8_t* m, int64_t n, cudaStream_t st) {
   k_apply_mask<<<grid1(n), 256, 0, st>>>(data, dbl, m, n); count_launch();
 }
+
+// ============================================================== serving
+// Continuous batching: requests are admitted (in arrival order) while the
+// device-memory budget allows, join the Lanczos engine at a restart-cycle
+// boundary, advance in the same launches as every other live request (each at
+// its own cycle), and retire -- final Ritz vectors, reconstruction, results
+// copied out, memory freed -- as soon as they converge.  Series (1D / MSSA)
+// and images run in two engines on the same stream.
+namespace {
+
+struct SrvReq {
+  int64_t ticket = 0;
+  ssa_input in{};
+  std::vector<char> data;
+  std::vector<int64_t> lengths;
+  std::vector<uint8_t> mask, wmask;
+  ssa_window win{};
+  ssa_params p{};
+  std::vector<int32_t> group_of;
+  int ng = 0, residual = 0;
+  int64_t total = 0, est = 0, bytes = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  ssa_ctx* ctx = nullptr;
+  int status = SSA_OK;
+  std::vector<double> sigma, out;
+  int32_t restarts = 0;
+  double maxres = 0;
+};
+
+double now_s(const std::chrono::steady_clock::time_point& t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Device bytes a request will hold at most (embedding, spectra, Lanczos
+// workspace, reconstruction scratch), from its sizes alone.
+int64_t estimate_bytes(const SrvReq& q, int prec) {
+  const size_t cz = prec == SSA_PREC_FP64 ? 8 : 4;
+  const size_t esz = q.in.dtype == SSA_F64 ? 8 : 4;
+  std::vector<int64_t> ns;
+  int64_t L = 0, Kmax = 0;
+  if (q.in.kind == SSA_1D) ns.push_back(q.in.n);
+  else if (q.in.kind == SSA_MSSA) ns = q.lengths;
+  if (q.in.kind == SSA_2D) {
+    L = q.win.lx * q.win.ly;
+    Kmax = (q.in.nx - q.win.lx + 1) * (q.in.ny - q.win.ly + 1);
+  } else {
+    L = q.win.L;
+    for (auto n : ns) Kmax += std::max<int64_t>(0, n - L + 1);
+  }
+  const int64_t nch = q.in.kind == SSA_MSSA ? (int64_t)ns.size() : 1;
+  // FFT grid, as ssa_embed chooses it
+  int64_t Mx = 16, My = 1, fymax = 1;
+  bool fold = false;
+  if (q.in.kind == SSA_2D) {
+    while (Mx < q.in.nx) Mx *= 2;
+    while (My < q.in.ny) My *= 2;
+  } else {
+    int64_t mx = 1;
+    for (auto n : ns) mx = std::max(mx, n);
+    while (Mx < mx) Mx *= 2;
+    if (ilog2_ceil(mx) >= FOLD_MIN_LOG2) {
+      const FoldGeom g = fold_geometry(ns, L);
+      fold = true;
+      Mx = 2 * (int64_t)g.B;
+      My = int64_t(1) << g.log2My;
+      for (int f : g.fy) fymax = std::max<int64_t>(fymax, f);
+    }
+  }
+  const int64_t H = Mx / 2, hs = (H + 1) * My;
+  int64_t b = 0;
+  // embedding: data, mask, observed bits, origins, weights
+  b += (int64_t)(esz + 1 + 4) * q.total + q.total / 4 + 4096 * (nch + 2);
+  b += nch * hs * 2 * (int64_t)cz;                                   // spectra
+  if (My > 1) b += nch * hs * 2 * (int64_t)cz;                       // spectrum scratch
+  const int64_t r = q.p.rank, k = std::min<int64_t>(std::min<int64_t>(2 * r + 16, KMAX), std::min(L, Kmax));
+  const int64_t Ls = std::min(L, Kmax), Kl = std::max(L, Kmax);
+  b += 8 * Ls * (k + 1) + (int64_t)cz * Kl * (k + 1) + 8 * Ls + (int64_t)cz * Kl;   // bases, work vectors
+  b += (int64_t)cz * (Ls + Kl) * nch + 4 * 8 * (k + 2) * (k + 2);                    // partials, small matrices
+  b += (int64_t)cz * (L + Kmax) * r;                                 // outputs U, V
+  if (My > 1) b += 2 * nch * hs * 2 * (int64_t)cz;                   // matvec x / y scratch
+  const int64_t nout = q.ng + (q.residual ? 1 : 0);
+  b += 8 * q.total * nout;                                           // reconstruction output
+  if (My > 1) b += (3 + q.ng) * 16 * hs + (fold ? 8 * Mx * fymax : 0);
+  else b += 16 * (H + 1) * r;
+  return b + (1 << 20);
+}
+
+}  // namespace
+
+struct ssa_server {
+  ssa_server_config cfg{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0;
+  int64_t next_ticket = 1;
+  int64_t bytes_live = 0;
+  std::deque<SrvReq*> queue;
+  std::vector<SrvReq*> live_series, live_images;
+  std::map<int64_t, SrvReq*> finished;
+  LzEngine<float> e32s, e32i;
+  LzEngine<double> e64s, e64i;
+  ~ssa_server() {
+    for (auto* q : queue) delete q;
+    for (auto* q : live_series) { ssa_destroy(q->ctx); delete q; }
+    for (auto* q : live_images) { ssa_destroy(q->ctx); delete q; }
+    for (auto& f : finished) delete f.second;
+  }
+};
+
+namespace {
+
+template <typename T>
+int server_round(ssa_server* s, LzEngine<T>& eng, std::vector<SrvReq*>& live, std::vector<SrvReq*>& admitted,
+                 int32_t* n_done) {
+  // admit: spectra and workspaces, join the engine
+  if (!admitted.empty()) {
+    std::vector<ssa_ctx*> cs;
+    std::vector<ssa_params> ps;
+    for (auto* q : admitted) { cs.push_back(q->ctx); ps.push_back(q->p); }
+    std::vector<int> rc;
+    TRY(prepare_members<T>(cs.data(), (int)cs.size(), ps.data(), s->st, rc));
+    for (size_t i = 0; i < admitted.size(); ++i) {
+      SrvReq* q = admitted[i];
+      if (rc[i] != SSA_OK) {
+        q->status = rc[i];
+        q->t_done = now_s(s->t0);
+        s->bytes_live -= q->est;
+        ssa_destroy(q->ctx);
+        q->ctx = nullptr;
+        s->finished[q->ticket] = q;
+        if (n_done) ++*n_done;
+        continue;
+      }
+      eng.add(q->ctx, q->p.seed);
+      live.push_back(q);
+    }
+  }
+  if (live.empty()) return SSA_OK;
+  TRY(eng.build());
+  TRY(eng.start_fresh());
+  TRY(eng.run_cycle());
+  // retire what is done; restart the rest
+  std::vector<int> done;
+  for (size_t i = 0; i < eng.live.size(); ++i)
+    if (!eng.hst[i].active) done.push_back((int)i);
+  TRY(eng.retire(done));
+  TRY(eng.restart_active());
+  if (!done.empty()) {
+    std::vector<ssa_ctx*> cs;
+    std::vector<RecReq> req;
+    std::vector<SrvReq*> reqs;
+    for (int i : done) {
+      ssa_ctx* c = eng.live[i];
+      SrvReq* q = nullptr;
+      for (auto* x : live) if (x->ctx == c) { q = x; break; }
+      reqs.push_back(q);
+      const int nout = q->ng + (q->residual ? 1 : 0);
+      q->out.assign((size_t)q->total * std::max(nout, 0), 0.0);
+      q->restarts = eng.hst[i].restarts;
+      q->maxres = eng.hst[i].maxres;
+      if (!eng.hst[i].converged && !eng.hst[i].breakdown) q->status = SSA_ENOTCONV;
+      if (nout > 0) {
+        cs.push_back(c);
+        req.push_back({q->group_of.data(), q->ng, q->residual, q->out.data()});
+      }
+    }
+    if (!cs.empty()) TRY(reconstruct_dispatch(cs.data(), (int)cs.size(), req.data(), 0));
+    CU(cudaStreamSynchronize(s->st));
+    const double t = now_s(s->t0);
+    for (auto* q : reqs) {
+      q->sigma.assign(q->p.rank, 0.0);
+      CU(cudaMemcpy(q->sigma.data(), q->ctx->ws.sigma, sizeof(double) * q->p.rank, cudaMemcpyDeviceToHost));
+      q->bytes = q->ctx->bytes;
+      q->t_done = t;
+      s->bytes_live -= q->est;
+      ssa_destroy(q->ctx);
+      q->ctx = nullptr;
+      s->finished[q->ticket] = q;
+      live.erase(std::find(live.begin(), live.end(), q));
+      if (n_done) ++*n_done;
+    }
+    eng.remove(done);
+  }
+  return SSA_OK;
+}
+
+template <typename T>
+int server_step_T(ssa_server* s, std::vector<SrvReq*>& adm_s, std::vector<SrvReq*>& adm_i, int32_t* n_done,
+                  LzEngine<T>& es, LzEngine<T>& ei) {
+  TRY(server_round<T>(s, es, s->live_series, adm_s, n_done));
+  TRY(server_round<T>(s, ei, s->live_images, adm_i, n_done));
+  return SSA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ssa_server_create(const ssa_server_config* cfg, void* cuda_stream, ssa_server** out) {
+  if (!cfg || !out) return fail(SSA_EINVAL, "null argument");
+  if (cfg->prec != SSA_PREC_FP32FFT_FP64REORTH && cfg->prec != SSA_PREC_FP64) return fail(SSA_EINVAL, "precision");
+  ssa_server* s = new ssa_server();
+  s->cfg = *cfg;
+  if (s->cfg.memory_budget <= 0) s->cfg.memory_budget = int64_t(40) << 30;
+  if (s->cfg.max_live <= 0) s->cfg.max_live = 512;
+  s->t0 = std::chrono::steady_clock::now();
+  if (cudaGetDevice(&s->device) != cudaSuccess || ensure_tables(s->device) != SSA_OK) {
+    delete s;
+    return fail(SSA_ECUDA, "device set-up failed");
+  }
+  if (cuda_stream) s->st = (cudaStream_t)cuda_stream;
+  else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) { delete s; return fail(SSA_ECUDA, "stream"); }
+    s->own_stream = true;
+  }
+  for (auto* e : {&s->e32s, &s->e32i}) { e->st = s->st; e->device = s->device; }
+  for (auto* e : {&s->e64s, &s->e64i}) { e->st = s->st; e->device = s->device; }
+  *out = s;
+  return SSA_OK;
+}
+
+int ssa_server_submit(ssa_server* s, const ssa_input* in, const ssa_window* win, const ssa_params* p,
+                      const int32_t* group_of, int32_t n_groups, int32_t residual, int64_t* ticket) {
+  if (!s || !in || !win || !p || !ticket || !in->data || n_groups < 0 || (n_groups > 0 && !group_of))
+    return fail(SSA_EINVAL, "null argument");
+  if (in->on_device) return fail(SSA_EINVAL, "server requests take host data");
+  SrvReq* q = new SrvReq();
+  q->in = *in;
+  int64_t total = 0;
+  if (in->kind == SSA_1D) total = in->n;
+  else if (in->kind == SSA_MSSA) {
+    if (!in->lengths || in->n_series < 1) { delete q; return fail(SSA_EINVAL, "MSSA lengths"); }
+    q->lengths.assign(in->lengths, in->lengths + in->n_series);
+    for (auto n : q->lengths) total += n;
+    q->in.lengths = q->lengths.data();
+  } else total = in->nx * in->ny;
+  if (total <= 0) { delete q; return fail(SSA_EINVAL, "empty input"); }
+  q->total = total;
+  const size_t esz = in->dtype == SSA_F64 ? 8 : 4;
+  q->data.assign((const char*)in->data, (const char*)in->data + esz * total);
+  q->in.data = q->data.data();
+  if (in->mask) { q->mask.assign(in->mask, in->mask + total); q->in.mask = q->mask.data(); }
+  q->win = *win;
+  if (win->wmask && in->kind == SSA_2D) {
+    q->wmask.assign(win->wmask, win->wmask + win->lx * win->ly);
+    q->win.wmask = q->wmask.data();
+  }
+  q->p = *p;
+  q->p.prec = s->cfg.prec;
+  q->ng = n_groups;
+  q->residual = residual ? 1 : 0;
+  q->group_of.assign(p->rank > 0 ? p->rank : 0, -1);
+  for (int i = 0; i < p->rank && group_of; ++i) q->group_of[i] = group_of[i];
+  q->ticket = s->next_ticket++;
+  q->t_submit = now_s(s->t0);
+  q->est = estimate_bytes(*q, s->cfg.prec);
+  s->queue.push_back(q);
+  *ticket = q->ticket;
+  return SSA_OK;
+}
+
+int ssa_server_step(ssa_server* s, int32_t* n_done) {
+  if (!s) return fail(SSA_EINVAL, "null argument");
+  if (n_done) *n_done = 0;
+  // admission in arrival order while the budget and the live count allow
+  std::vector<SrvReq*> adm;
+  const int64_t nlive = (int64_t)(s->live_series.size() + s->live_images.size());
+  while (!s->queue.empty() && nlive + (int64_t)adm.size() < s->cfg.max_live) {
+    SrvReq* q = s->queue.front();
+    if (q->est > s->cfg.memory_budget) {
+      s->queue.pop_front();
+      q->status = fail(SSA_ENOMEM, "request needs %lld bytes, budget %lld", (long long)q->est,
+                       (long long)s->cfg.memory_budget);
+      q->t_done = now_s(s->t0);
+      s->finished[q->ticket] = q;
+      if (n_done) ++*n_done;
+      continue;
+    }
+    if (s->bytes_live + q->est > s->cfg.memory_budget) break;
+    s->queue.pop_front();
+    s->bytes_live += q->est;
+    q->t_admit = now_s(s->t0);
+    adm.push_back(q);
+  }
+  std::vector<SrvReq*> adm_s, adm_i;
+  if (!adm.empty()) {
+    std::vector<ssa_input> ins;
+    std::vector<ssa_window> wins;
+    for (auto* q : adm) { ins.push_back(q->in); wins.push_back(q->win); }
+    std::vector<ssa_ctx*> cs(adm.size(), nullptr);
+    const int32_t unset = INT32_MIN;   // status left unwritten: the batch failed as a whole
+    std::vector<int32_t> st(adm.size(), unset);
+    const int brc = ssa_embed_batch(ins.data(), wins.data(), (int32_t)adm.size(), (void*)s->st, cs.data(), st.data());
+    for (size_t i = 0; i < adm.size(); ++i) {
+      SrvReq* q = adm[i];
+      if (st[i] == unset && cs[i]) { ssa_destroy(cs[i]); cs[i] = nullptr; }
+      if (st[i] != SSA_OK || !cs[i]) {
+        q->status = st[i] == unset ? (brc != SSA_OK ? brc : SSA_ECUDA) : (st[i] != SSA_OK ? st[i] : SSA_ECUDA);
+        q->t_done = now_s(s->t0);
+        s->bytes_live -= q->est;
+        s->finished[q->ticket] = q;
+        if (n_done) ++*n_done;
+        continue;
+      }
+      q->ctx = cs[i];
+      (q->in.kind == SSA_2D ? adm_i : adm_s).push_back(q);
+    }
+  }
+  if (s->cfg.prec == SSA_PREC_FP64) TRY(server_step_T<double>(s, adm_s, adm_i, n_done, s->e64s, s->e64i));
+  else TRY(server_step_T<float>(s, adm_s, adm_i, n_done, s->e32s, s->e32i));
+  return SSA_OK;
+}
+
+int ssa_server_stats(const ssa_server* s, int64_t* queued, int64_t* live, int64_t* finished, int64_t* bytes_live) {
+  if (!s) return fail(SSA_EINVAL, "null argument");
+  if (queued) *queued = (int64_t)s->queue.size();
+  if (live) *live = (int64_t)(s->live_series.size() + s->live_images.size());
+  if (finished) *finished = (int64_t)s->finished.size();
+  if (bytes_live) *bytes_live = s->bytes_live;
+  return SSA_OK;
+}
+
+int ssa_server_finished(const ssa_server* s, int64_t* tickets, int32_t cap, int32_t* n) {
+  if (!s || !n || (cap > 0 && !tickets)) return fail(SSA_EINVAL, "null argument");
+  int32_t m = 0;
+  for (auto& f : s->finished) {
+    if (m >= cap) break;
+    tickets[m++] = f.first;
+  }
+  *n = m;
+  return SSA_OK;
+}
+
+int ssa_server_take(ssa_server* s, int64_t ticket, ssa_server_result* res, double* sigma, double* out) {
+  if (!s) return fail(SSA_EINVAL, "null argument");
+  auto it = s->finished.find(ticket);
+  if (it == s->finished.end()) return fail(SSA_ESTATE, "request %lld not finished", (long long)ticket);
+  SrvReq* q = it->second;
+  if (res) {
+    std::memset(res, 0, sizeof(*res));
+    res->ticket = q->ticket;
+    res->status = q->status;
+    res->rank = q->p.rank;
+    res->out_len = (int64_t)q->out.size();
+    res->restarts = q->restarts;
+    res->max_residual = q->maxres;
+    res->t_submit = q->t_submit;
+    res->t_admit = q->t_admit;
+    res->t_done = q->t_done;
+    res->device_bytes = q->bytes;
+    res->estimated_bytes = q->est;
+  }
+  if (sigma && !q->sigma.empty()) std::memcpy(sigma, q->sigma.data(), sizeof(double) * q->sigma.size());
+  if (out && !q->out.empty()) std::memcpy(out, q->out.data(), sizeof(double) * q->out.size());
+  s->finished.erase(it);
+  delete q;
+  return SSA_OK;
+}
+
+double ssa_server_clock(const ssa_server* s) { return s ? now_s(s->t0) : 0.0; }
+
+void ssa_server_destroy(ssa_server* s) {
+  if (!s) return;
+  cudaStream_t st = s->st;
+  bool own = s->own_stream;
+  if (st) cudaStreamSynchronize(st);
+  delete s;
+  if (own && st) cudaStreamDestroy(st);
+}
+
+}  // extern "C"

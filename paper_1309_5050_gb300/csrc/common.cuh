@@ -56,6 +56,7 @@ struct MapDev {
   int32_t words;           // 32-bit words per column (bit mode)
   const uint32_t* bits;    // by * words, bit x of column y at word x>>5, bit x&31
   const int32_t* colbase;  // by: number of set elements in columns < y
+  int64_t limit;           // dense mode: only indices x + bx*y < limit belong to the set
 };
 
 // Error word written by kernels that detect bad input or a stalled wait.

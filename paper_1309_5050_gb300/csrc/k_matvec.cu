@@ -24,9 +24,11 @@ __device__ void load_col(T* rb, int Mx, const TI* __restrict__ in, const MapDev&
                          int32_t* s_pre, int32_t* s_wt, T scale = T(1)) {
   if (m.dense || y >= m.by) {
     const bool ok = (y < m.by);
-    const TI* src = in + (int64_t)y * m.bx;
+    const int64_t base = (int64_t)y * m.bx;
+    const int xe = ok ? (int)min((int64_t)m.bx, m.limit - base) : 0;   // entries of this column
+    const TI* src = in + base;
     for (int x = threadIdx.x; x < Mx; x += blockDim.x)
-      rb[x] = (ok && x < m.bx) ? (T)src[x] * scale : T(0);
+      rb[x] = (x < xe) ? (T)src[x] * scale : T(0);
   } else {
     const uint32_t* wb = m.bits + (int64_t)y * m.words;
     block_popc_scan(wb, m.words, s_pre, s_wt);
@@ -57,8 +59,10 @@ __device__ void store_col(const T* rb, TO* __restrict__ out, const MapDev& m, in
                           int32_t* s_pre, int32_t* s_wt) {
   if (y >= m.by) return;
   if (m.dense) {
-    TO* dst = out + (int64_t)y * m.bx;
-    for (int x = threadIdx.x; x < m.bx; x += blockDim.x) dst[x] = (TO)rb[x];
+    const int64_t base = (int64_t)y * m.bx;
+    const int xe = (int)min((int64_t)m.bx, m.limit - base);
+    TO* dst = out + base;
+    for (int x = threadIdx.x; x < xe; x += blockDim.x) dst[x] = (TO)rb[x];
   } else {
     const uint32_t* wb = m.bits + (int64_t)y * m.words;
     block_popc_scan(wb, m.words, s_pre, s_wt);
@@ -259,8 +263,8 @@ __global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ 
     if (x < it.nx) {
       bool ok = true;
       if (it.obs) ok = (it.obs[(int64_t)y * it.obs_words + (x >> 5)] >> (x & 31)) & 1u;
-      if (ok) {
-        const int64_t g = x + (int64_t)it.nx * y;
+      const int64_t g = x + it.ld * y;
+      if (ok && g < it.n_lin) {
         double d = it.data_double ? ((const double*)it.data)[g] : (double)((const float*)it.data)[g];
         v = (T)d * it.scale;
       }
@@ -318,13 +322,13 @@ void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int ma
 }
 
 template <typename T>
-void launch_spec(const SpecItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
+void launch_spec(const SpecItem<T>* items, int n, const YItem<T>* yitems, int ny, int max_log2Mx, int max_log2My,
                  int max_ny, const Cx<T>* tw, cudaStream_t st) {
   if (n <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_spec_x<T>);
   k_spec_x<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw); count_launch();
-  if (max_log2My > 0) launch_ypass<T>(yitems, n, Y_FWD, max_log2Mx, max_log2My, -1, tw, st);
+  if (ny > 0 && max_log2My > 0) launch_ypass<T>(yitems, ny, Y_FWD, max_log2Mx, max_log2My, -1, tw, st);
 }
 
 #define INST(T)                                                                                       \
@@ -332,8 +336,8 @@ void launch_spec(const SpecItem<T>* items, const YItem<T>* yitems, int n, int ma
   template void launch_mv2d<T>(const MvItem<T>*, const YItem<T>*, int, int, int, int, int, int,        \
                                const Cx<T>*, cudaStream_t);                                           \
   template void launch_ypass<T>(const YItem<T>*, int, int, int, int, int, const Cx<T>*, cudaStream_t); \
-  template void launch_spec<T>(const SpecItem<T>*, const YItem<T>*, int, int, int, int, const Cx<T>*,  \
-                               cudaStream_t);
+  template void launch_spec<T>(const SpecItem<T>*, int, const YItem<T>*, int, int, int, int,          \
+                               const Cx<T>*, cudaStream_t);
 INST(float)
 INST(double)
 

@@ -22,8 +22,10 @@ __device__ void rec_load_col(T* rb, int Mx, const TI* __restrict__ in, const Map
                              int32_t* s_pre, int32_t* s_wt) {
   if (m.dense || y >= m.by) {
     const bool ok = (y < m.by);
-    const TI* src = in + (int64_t)y * m.bx;
-    for (int x = threadIdx.x; x < Mx; x += blockDim.x) rb[x] = (ok && x < m.bx) ? (T)src[x] : T(0);
+    const int64_t base = (int64_t)y * m.bx;
+    const int xe = ok ? (int)min((int64_t)m.bx, m.limit - base) : 0;
+    const TI* src = in + base;
+    for (int x = threadIdx.x; x < Mx; x += blockDim.x) rb[x] = (x < xe) ? (T)src[x] : T(0);
   } else {
     const uint32_t* wb = m.bits + (int64_t)y * m.words;
     block_popc_scan(wb, m.words, s_pre, s_wt);
@@ -130,9 +132,34 @@ __global__ void __launch_bounds__(512) k_rec_xinv(const Rec2Item<T>* __restrict_
   const T* r = reinterpret_cast<const T*>(R);
   for (int x = threadIdx.x; x < it.nx; x += blockDim.x) {
     const int64_t g = x + (int64_t)it.nx * y;
+    if (!it.w) { it.out[g] = (double)r[x] * it.inv_norm; continue; }   // raw sums (long series)
     const int w = it.w[g];
     it.out[g] = (w > 0) ? (double)r[x] * it.inv_norm / (double)w : __longlong_as_double(0x7ff8000000000000ll);
   }
+}
+
+// Long series: the diagonal sums of a group arrive as a segment image S
+// (2B rows, one column per segment) whose column c holds the sums of the
+// data elements cB .. cB + 2B - 2.  Element p gathers row p mod B of column
+// p div B and row B + p mod B of the column before (overlap-add), then is
+// divided by w.
+__global__ void k_rec_fold(const RecFoldItem* __restrict__ items) {
+  const RecFoldItem it = items[blockIdx.y];
+  const int64_t B = it.B;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < it.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int w = it.w[p];
+    if (w <= 0) { it.out[p] = __longlong_as_double(0x7ff8000000000000ll); continue; }
+    const int64_t c = p / B, i = p - c * B;
+    double v = (c < it.ncols) ? it.S[i + 2 * B * c] : 0.0;
+    if (c > 0 && i + B < 2 * B - 1) v += it.S[i + B + 2 * B * (c - 1)];
+    it.out[p] = v / (double)w;
+  }
+}
+
+void launch_rec_fold(const RecFoldItem* items, int n, int64_t max_n, cudaStream_t st) {
+  if (n <= 0) return;
+  const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, 1024));
+  k_rec_fold<<<dim3(bx, n), 256, 0, st>>>(items); count_launch();
 }
 
 // residual = x - sum of the groups, on N' (NaN elsewhere), in FP64

@@ -61,7 +61,9 @@ struct MvItem {
 // Raw data to half spectrum (step 1 of the matvec algorithms, precomputed).
 template <typename T>
 struct SpecItem {
-  const void* data;         // Nx x Ny column-major (float or double)
+  const void* data;         // column y of the grid starts at data + ld*y (float or double)
+  int64_t ld;               // column stride: nx for an image, the segment step for a long series
+  int64_t n_lin;            // elements data[0, n_lin) exist; later ones read as zero
   const uint32_t* obs;      // observed bits, Ny columns x words (null = all)
   int32_t obs_words;
   int32_t data_double;

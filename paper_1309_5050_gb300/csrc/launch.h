@@ -33,7 +33,7 @@ template <typename T>
 void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int max_log2My, int s,
                   const Cx<T>* tw, cudaStream_t st);
 template <typename T>
-void launch_spec(const SpecItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
+void launch_spec(const SpecItem<T>* items, int n, const YItem<T>* yitems, int ny, int max_log2Mx, int max_log2My,
                  int max_ny, const Cx<T>* tw, cudaStream_t st);
 
 }  // namespace ssa

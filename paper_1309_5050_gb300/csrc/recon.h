@@ -32,7 +32,7 @@ struct Rec1Item {
 template <typename T>
 struct Rec2Item {
   const Cx<T>* g2;             // y-inverse of the accumulated spectrum
-  const int32_t* w;            // Nx x Ny weights
+  const int32_t* w;            // Nx x Ny weights (null: write the raw sums, no division)
   double* out;                 // Nx x Ny
   int32_t log2Mx, nx, ny, pad_;
   double inv_norm;             // 1 / (Mx My)
@@ -46,6 +46,14 @@ void launch_rec1d(const Rec1Item<T, TV>* items, int n, int max_log2Mx, const Cx<
 template <typename T>
 void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny, const Cx<T>* tw,
                      cudaStream_t st);
+struct RecFoldItem {            // long series: segment-image sums -> one group's output
+  const double* S;              // 2B x (segments), column-major
+  const int32_t* w;             // n weights
+  double* out;                  // n values
+  int64_t B, n;
+  int64_t ncols;                // columns of S (segments of the grid)
+};
+void launch_rec_fold(const RecFoldItem* items, int n, int64_t max_n, cudaStream_t st);
 struct ResItem {                // residual x - sum of groups for one channel
   const void* data; int32_t data_double, ngroups;
   const int32_t* w; const double* groups; int64_t gstride, n;

@@ -200,6 +200,20 @@ def test_eigen_route_matches_jacobi_route():
     np.testing.assert_allclose(V1[:, :3], V2[:, :3], atol=1e-8)
 
 
+def test_transposed_eigen_route_matches_jacobi_route():
+    """Step 2 on X^T (S' = X^T X, for K < L) gives the triples of the Jacobi
+    SVD of X: the SVD of X^T has the same singular values with U and V
+    exchanged."""
+    rng = np.random.default_rng(6)
+    x = np.cumsum(rng.normal(size=240))
+    P = O.Problem.series(x, 200)          # L = 200 > K = 41
+    s1, U1, V1 = O.decompose(P, 12, "eigen_t")
+    s2, U2, V2 = O.decompose(P, 12, "jacobi")
+    np.testing.assert_allclose(s1, s2, rtol=1e-10)
+    np.testing.assert_allclose(U1[:, :3], U2[:, :3], atol=1e-8)
+    np.testing.assert_allclose(V1[:, :3], V2[:, :3], atol=1e-8)
+
+
 def test_factor_vectors_definition():
     """Eq. mmexp: X = sum sqrt(lambda_j) U_j V_j^T with orthonormal U, V."""
     rng = np.random.default_rng(5)
@@ -404,3 +418,48 @@ def test_reconstruct_at_matches_full_reconstruction():
             assert np.isnan(g)
         else:
             assert abs(g - full[m, n]) < 1e-10
+
+
+# ------------------------------------------------------------ long-series entry routes
+def test_series_rows_cols_geometric_closed_form():
+    """x_t = q^t gives X_ij = q^i q^j (eq. ssa_embedding): every row of X v is
+    q^i times the same sum, every column of X^T u q^j times another."""
+    q = 0.999
+    n, L = 300, 120
+    K = n - L + 1
+    x = q ** np.arange(n)
+    rng = np.random.default_rng(3)
+    v, u = rng.normal(size=K), rng.normal(size=L)
+    rows, cols = [0, 7, 119], [0, 50, 180]
+    sv = float(np.sum(q ** np.arange(K) * v))
+    su = float(np.sum(q ** np.arange(L) * u))
+    np.testing.assert_allclose(O.series_rows(x, L, rows, v), [q ** i * sv for i in rows], rtol=1e-12)
+    np.testing.assert_allclose(O.series_cols(x, L, cols, u), [q ** j * su for j in cols], rtol=1e-12)
+
+
+def test_series_rows_cols_match_trajectory_products():
+    """Single rows / columns agree with the full products of the explicit
+    trajectory matrix (pinned to the printed Hankel form above)."""
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=97)
+    L = 40
+    P = O.Problem.series(x, L)
+    v, u = rng.normal(size=P.K), rng.normal(size=P.L)
+    np.testing.assert_allclose(O.series_rows(x, L, range(P.L), v), O.matvec(P, v), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(O.series_cols(x, L, range(P.K), u), O.rmatvec(P, u), rtol=1e-12, atol=1e-12)
+
+
+def test_series_hankelize_at_full_sum_is_input_and_matches_groups():
+    """All elementary components of a full decomposition sum to the series
+    (Sec. 2.1, Step 4), element by element; a single group agrees with the
+    full diagonal averaging."""
+    rng = np.random.default_rng(5)
+    n, L = 60, 25
+    t = np.arange(n)
+    x = np.sin(2 * np.pi * t / 9) + 0.3 * rng.normal(size=n)
+    P = O.Problem.series(x, L)
+    s, U, V = O.decompose(P, L, "jacobi")
+    pts = list(range(n))
+    np.testing.assert_allclose(O.series_hankelize_at(s, U, V, range(len(s)), pts), x, atol=1e-10)
+    full = O.reconstruct(P, s, U, V, [[0, 1]])[0][0][:, 0]
+    np.testing.assert_allclose(O.series_hankelize_at(s, U, V, [0, 1], pts), full, atol=1e-12)
