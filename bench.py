@@ -128,7 +128,7 @@ class Clocks:
 
 # ------------------------------------------------------------------ GPU arm
 # ------------------------------------------------------------------ serving
-SERVE_N_MAX = 16384   # longest series the single-CTA FFT grid takes (2^14 samples)
+SERVE_N_MAX = 200000  # longest series of the serving mix
 
 
 def serve_submit(srv, q, seed):
@@ -145,12 +145,16 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
     """Open-loop serving: each request is submitted when its Poisson arrival
     time comes up on the server's clock; latency runs from that arrival time
     to the request's completion (results in host memory)."""
+    from paper_1309_5050_gb300 import _lib
     srv = pkg.Server(memory_budget=budget, prec=prec)
     for q in reqs[:8]:                      # warm-up requests (not counted)
         serve_submit(srv, q, 1)
     srv.drain()
     for t in srv.finished():
         srv.take(t)
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    l0 = _lib.kernel_launches()
     n = len(reqs)
     arrival = {}
     lat, status, restarts = [], {}, []
@@ -159,6 +163,7 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
     t0 = srv.clock()
     t_last = t0
     steps = 0
+    step_s = []
     while len(lat) < n:
         now = srv.clock() - t0
         while i < n and reqs[i].arrival_s <= now:
@@ -173,7 +178,9 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
                 if dt > 0:
                     time.sleep(dt)
             continue
+        ts0 = time.perf_counter()
         srv.step()
+        step_s.append(time.perf_counter() - ts0)
         steps += 1
         for t in srv.finished():
             r = srv.take(t)
@@ -182,6 +189,9 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
             restarts.append(r["restarts"])
             t_last = max(t_last, r["t_done"])
     srv.close()
+    launches = _lib.kernel_launches() - l0
+    prof = _lib.profile_read()
+    _lib.profile_enable(False)
     wall = t_last - t0
     kinds = {}
     for q in reqs:
@@ -189,9 +199,11 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
     return {"requests": n, "rate_hz": rate_hz, "kinds": kinds, "throughput_rps": n / wall, "wall_s": wall,
             "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
             "mean_ms": 1000 * float(np.mean(lat)), "max_live": max_live, "max_queued": max_q,
-            "server_steps": steps, "mean_restarts": float(np.mean(restarts)),
+            "server_steps": steps, "step_ms_mean": 1000 * float(np.mean(step_s)),
+            "step_ms_max": 1000 * float(np.max(step_s)), "mean_restarts": float(np.mean(restarts)),
             "statuses": {str(k): v for k, v in status.items()}, "budget_bytes": budget,
-            "series_n_max": SERVE_N_MAX, "prec": prec}
+            "series_n_max": SERVE_N_MAX, "prec": prec, "gpu_launches": int(launches),
+            "phases_ms": {k: v[0] for k, v in prof.items()}}
 
 
 def main():

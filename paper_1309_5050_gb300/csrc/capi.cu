@@ -283,6 +283,7 @@ struct Channel {
   int64_t koff = 0;            // offset of the channel's slice in K-vectors
   int32_t* w = nullptr;        // nx*ny weights
   uint32_t* obs = nullptr;     // observed bits, ny x nwords
+  int32_t* kpre = nullptr;     // origin bits: word prefix counts per column (run-shaped windows)
   int nwords = 0;
   void* xh32 = nullptr;        // spectra
   void* xh64 = nullptr;
@@ -321,6 +322,7 @@ struct ssa_ctx {
   int fold_B = 0, lb = 0;      // segment form of long series (0: off), window blocks ceil(L/B)
   ShapeSet Lset;               // window set (bounding box ex x ey)
   int ex = 0, ey = 0;
+  int32_t* wint = nullptr;     // window columns as runs a, b (null: some column is not a run)
   uint32_t* wrows = nullptr;   // window rows (bits), ey x wwords
   uint32_t* rrows = nullptr;   // reversed window rows
   int wwords = 0;
@@ -442,6 +444,8 @@ static int upload(ssa_ctx* c, const std::vector<X>& h, X** d) {
 // stage 3 checks the error flags -- two host waits for the whole batch.
 struct EmbedBatch {
   std::vector<ObsItem> obs;
+  std::vector<PrefixItem> opre, kpre;
+  int max_opre_cols = 1, max_kpre_cols = 1;
   std::vector<OriginItem> org;
   std::vector<CountItem> cnt;
   std::vector<WeightItem> wts;
@@ -486,6 +490,19 @@ static int embed_stage1(ssa_ctx* c, const ssa_window* win, EmbedBatch& eb, int c
       }
   TRY(upload(c, rows, &c->wrows));
   TRY(upload(c, rrows, &c->rrows));
+  // window columns as runs [a, b] where they are (rectangles, discs, triangles)
+  std::vector<int32_t> wint((size_t)2 * ey, -1);
+  bool runs = true;
+  for (int y = 0; y < ey; ++y) {
+    int a = -1, b = -1, n = 0;
+    for (int x = 0; x < ex; ++x)
+      if (wm[x + (size_t)ldm * y]) { if (a < 0) a = x; b = x; ++n; }
+    if (a >= 0 && n != b - a + 1) runs = false;
+    wint[2 * y] = a; wint[2 * y + 1] = b;
+  }
+  int32_t* d_wint = nullptr;
+  if (runs) TRY(upload(c, wint, &d_wint));
+  c->wint = d_wint;
   ShapeSet& Ls = c->Lset;
   Ls.bx = ex; Ls.by = ey; Ls.words = c->wwords;
   Ls.dense = full;
@@ -503,6 +520,12 @@ static int embed_stage1(ssa_ctx* c, const ssa_window* win, EmbedBatch& eb, int c
     TRY(c->allocT(&h.obs, (size_t)h.ny * h.nwords));
     const void* dptr = (const char*)c->data + h.data_off * esz;
     eb.obs.push_back({dptr, c->dtype == SSA_F64, (int)h.nx, (int)h.ny, h.nwords, h.obs, d_err + ci});
+    int32_t* opre = nullptr;
+    if (runs) {
+      TRY(c->allocT(&opre, (size_t)h.ny * (h.nwords + 1)));
+      eb.opre.push_back({h.obs, h.nwords, (int)h.ny, opre});
+      eb.max_opre_cols = std::max(eb.max_opre_cols, (int)h.ny);
+    }
     eb.max_nx = std::max(eb.max_nx, (int)h.nx);
     eb.max_ny = std::max(eb.max_ny, (int)h.ny);
     h.cx = (int)(h.nx - ex + 1);
@@ -515,7 +538,13 @@ static int embed_stage1(ssa_ctx* c, const ssa_window* win, EmbedBatch& eb, int c
       TRY(c->allocT(&ks.bits, (size_t)ks.by * ks.words));
       TRY(c->allocT(&ks.cnt, (size_t)ks.by + 1));
       TRY(c->allocT(&ks.colbase, (size_t)ks.by + 1));
-      eb.org.push_back({h.obs, h.nwords, c->wwords, c->wrows, ey, h.cx, h.cy, ks.words, ks.bits});
+      eb.org.push_back({h.obs, h.nwords, c->wwords, c->wrows, ey, h.cx, h.cy, ks.words, ks.bits, opre, d_wint,
+                        runs ? 1 : 0, 0});
+      if (runs) {
+        TRY(c->allocT(&h.kpre, (size_t)ks.by * (ks.words + 1)));
+        eb.kpre.push_back({ks.bits, ks.words, ks.by, h.kpre});
+        eb.max_kpre_cols = std::max(eb.max_kpre_cols, ks.by);
+      }
       eb.max_cx = std::max(eb.max_cx, h.cx);
       eb.max_cy = std::max(eb.max_cy, h.cy);
       eb.cnt_slot_K[ci][q] = (int)eb.cnt.size();
@@ -542,7 +571,7 @@ static int embed_stage2(ssa_ctx* c, EmbedBatch& eb, int ci, const int32_t* total
     TRY(c->allocT(&nb, (size_t)h.ny * h.nwords));
     if (ks.count > 0) {
       eb.wts.push_back({ks.bits, ks.words, ks.by, c->rrows, c->wwords, c->ex, c->ey, (int)h.nx, (int)h.ny,
-                        h.nwords, h.w, nb});
+                        h.nwords, h.w, nb, h.kpre, c->wint, c->wint ? 1 : 0, 0});
     } else {
       CU(cudaMemsetAsync(h.w, 0, sizeof(int32_t) * h.nx * h.ny, c->stream));
     }
@@ -585,6 +614,7 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
   const bool f32 = std::is_same<T, float>::value;
   std::vector<SpecItem<T>> items;
   std::vector<YItem<T>> yitems;
+  std::vector<int32_t> sx_pre{0}, sy_pre{0};
   std::vector<std::pair<ssa_ctx*, void*>> scratch;
   int max_ny = 1, max_log2Mx = 1, max_log2My = 0;
   for (int i = 0; i < n; ++i) {
@@ -630,11 +660,14 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
       sp.xh = (Cx<T>*)xh;
       sp.scale = (T)(1.0 / ((double)(2 * Hc) * (double)My));
       items.push_back(sp);
+      sx_pre.push_back(sx_pre.back() + sp.ny);
       if (c->log2My > 0) {
         YItem<T> y;
         y.src = sp.g1; y.dst = sp.xh; y.mul = nullptr; y.st = nullptr;
         y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = sp.ny; y.out_hi = My; y.scale = T(0);
+        y.tk = ypass_tk<T>(c->log2My);
         yitems.push_back(y);
+        sy_pre.push_back(sy_pre.back() + ypass_blocks(c->log2Mx, y.tk));
       }
       max_ny = std::max(max_ny, sp.ny);
     }
@@ -653,11 +686,21 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
   if (g_ring.copy(di, items.data(), sizeof(SpecItem<T>) * items.size(), st) != SSA_OK ||
       (!yitems.empty() && g_ring.copy(dy, yitems.data(), sizeof(YItem<T>) * yitems.size(), st) != SSA_OK))
     return fail(SSA_ECUDA, "spectrum item upload");
-  launch_spec<T>(di, (int)items.size(), dy, (int)yitems.size(), max_log2Mx, max_log2My, max_ny,
-                 twiddles<T>(cs[0]->device), st);
+  int32_t *dpx = nullptr, *dpy = nullptr;
+  if (cudaMallocAsync((void**)&dpx, sizeof(int32_t) * sx_pre.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&dpy, sizeof(int32_t) * sy_pre.size(), st) != cudaSuccess)
+    return fail(SSA_ENOMEM, "spectrum tiles");
+  if (g_ring.copy(dpx, sx_pre.data(), sizeof(int32_t) * sx_pre.size(), st) != SSA_OK ||
+      g_ring.copy(dpy, sy_pre.data(), sizeof(int32_t) * sy_pre.size(), st) != SSA_OK)
+    return fail(SSA_ECUDA, "spectrum tile upload");
+  (void)max_ny;
+  launch_spec<T>(di, Tiles{dpx, (int)items.size(), sx_pre.back()}, dy,
+                 Tiles{dpy, (int)yitems.size(), sy_pre.back()}, max_log2Mx, max_log2My, twiddles<T>(cs[0]->device), st);
   CU(cudaGetLastError());
   cudaFreeAsync(di, st);
   cudaFreeAsync(dy, st);
+  cudaFreeAsync(dpx, st);
+  cudaFreeAsync(dpy, st);
   for (auto& sc : scratch) {
     cudaStream_t keep = sc.first->stream;
     sc.first->stream = st;
@@ -681,6 +724,8 @@ struct MvSet {
   MvItem<T>* d1 = nullptr;
   MvItem<T>* d2 = nullptr;
   YItem<T>* dy2 = nullptr;
+  int32_t *t_xf = nullptr, *t_yp = nullptr, *t_xi = nullptr;   // block ranges of the 2D launches
+  int n_xf = 0, n_yp = 0, n_xi = 0;
   int max_y_in = 0, max_y_out = 0;
   int lx1 = 1, lx2 = 1, ly2 = 0;   // largest log2 grid sizes of each list
   void add(const MvItem<T>& m) {
@@ -729,6 +774,7 @@ static YItem<T> ymv(const MvItem<T>& m) {
   y.src = m.g1; y.dst = m.g2; y.mul = m.xh; y.st = m.st;
   y.log2Mx = m.log2Mx; y.log2My = m.log2My;
   y.in_hi = m.y_in_hi; y.out_hi = m.y_out_hi; y.scale = T(0);
+  y.tk = ypass_tk<T>(m.log2My);
   return y;
 }
 
@@ -737,11 +783,19 @@ static YItem<T> ymv(const MvItem<T>& m) {
 template <typename T, typename Up>
 static int finish_set(MvSet<T>& s, Up&& up) {
   s.yitems2.clear();
-  for (auto& m : s.items2) s.yitems2.push_back(ymv(m));
+  std::vector<int32_t> xf{0}, yp{0}, xi{0};
+  for (auto& m : s.items2) {
+    s.yitems2.push_back(ymv(m));
+    xf.push_back(xf.back() + m.y_in_hi);
+    yp.push_back(yp.back() + ypass_blocks(m.log2Mx, s.yitems2.back().tk));
+    xi.push_back(xi.back() + m.y_out_hi);
+  }
   if (!s.items1.empty()) TRY(up(s.items1, &s.d1));
   if (!s.items2.empty()) {
     TRY(up(s.items2, &s.d2));
     TRY(up(s.yitems2, &s.dy2));
+    TRY(up(xf, &s.t_xf)); TRY(up(yp, &s.t_yp)); TRY(up(xi, &s.t_xi));
+    s.n_xf = xf.back(); s.n_yp = yp.back(); s.n_xi = xi.back();
   }
   return SSA_OK;
 }
@@ -751,9 +805,11 @@ static void run_mv(ssa_ctx* c, const MvSet<T>& s, int step) {
   PhaseScope ps_(PH_MATVEC, c->stream);
   if (!s.items1.empty())
     launch_mv1d<T>(s.d1, (int)s.items1.size(), s.lx1, step, twiddles<T>(c->device), c->stream);
-  if (!s.items2.empty())
-    launch_mv2d<T>(s.d2, s.dy2, (int)s.items2.size(), s.lx2, s.ly2, s.max_y_in, s.max_y_out, step,
-                   twiddles<T>(c->device), c->stream);
+  if (!s.items2.empty()) {
+    const int n2 = (int)s.items2.size();
+    launch_mv2d<T>(s.d2, s.dy2, n2, Tiles{s.t_xf, n2, s.n_xf}, Tiles{s.t_yp, n2, s.n_yp},
+                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(c->device), c->stream);
+  }
 }
 
 // ============================================================== decompose (batched)
@@ -849,6 +905,9 @@ struct LzEngine {
   // device item arrays for the current membership
   ShortItem* d_sh = nullptr; LongItem<T>* d_lg = nullptr; SvdItem* d_sv = nullptr;
   RitzItem<T>* d_rz = nullptr; LzState** d_stp = nullptr; LzState* d_stg = nullptr;
+  // block ranges of the members in the row-block launches
+  int32_t *t_sh = nullptr, *t_lg = nullptr, *t_rs = nullptr, *t_rl = nullptr;
+  int n_sh = 0, n_lg = 0, n_rs = 0, n_rl = 0;
   MvSet<T> mvA, mvAT;
   int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1;
   int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
@@ -872,6 +931,21 @@ struct LzEngine {
     dev_tmp.push_back(*d);
     if (!h.empty() && g_ring.copy(*d, h.data(), sizeof(X) * h.size(), st) != SSA_OK)
       return fail(SSA_ECUDA, "engine item upload");
+    return SSA_OK;
+  }
+
+  // prefix of per-member block counts, uploaded; *total = grid size
+  template <typename F>
+  int tiles(const std::vector<ssa_ctx*>& cs, F&& per, int32_t** d, int* total) {
+    std::vector<int32_t> p{0};
+    for (ssa_ctx* c : cs) p.push_back(p.back() + (int32_t)per(c));
+    *total = p.back();
+    return up(p, d);
+  }
+  static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+  int ritz_tiles(const std::vector<ssa_ctx*>& cs, int32_t** ds, int* ns, int32_t** dl, int* nl) {
+    TRY(tiles(cs, [](ssa_ctx* c) { return cdiv(c->ws.Ls, RITZ_RB_SHORT); }, ds, ns));
+    TRY(tiles(cs, [](ssa_ctx* c) { return cdiv(c->ws.Kl, ritz_rb_long<T>()); }, dl, nl));
     return SSA_OK;
   }
 
@@ -974,6 +1048,9 @@ struct LzEngine {
     }
     if (live.empty()) return SSA_OK;
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
+    TRY(tiles(live, [](ssa_ctx* c) { return c->ws.nblk_s; }, &t_sh, &n_sh));
+    TRY(tiles(live, [](ssa_ctx* c) { return c->ws.nblk_l; }, &t_lg, &n_lg));
+    TRY(ritz_tiles(live, &t_rs, &n_rs, &t_rl, &n_rl));
     auto upl = [&](auto& v, auto** d) { return up(v, d); };
     TRY(finish_set(mvA, upl));
     TRY(finish_set(mvAT, upl));
@@ -994,14 +1071,17 @@ struct LzEngine {
   // start vectors of the members not started yet
   int start_fresh() {
     std::vector<LongItem<T>> lg;
-    int mb = 1;
+    std::vector<ssa_ctx*> cs;
     for (size_t i = 0; i < live.size(); ++i)
-      if (fresh[i]) { lg.push_back(long_item(live[i], seed[i])); mb = std::max(mb, live[i]->ws.nblk_l); fresh[i] = false; }
+      if (fresh[i]) { lg.push_back(long_item(live[i], seed[i])); cs.push_back(live[i]); fresh[i] = false; }
     if (lg.empty()) return SSA_OK;
     LongItem<T>* d = nullptr;
+    int32_t* tp = nullptr;
+    int nt = 0;
     TRY(up(lg, &d));
+    TRY(tiles(cs, [](ssa_ctx* c) { return c->ws.nblk_l; }, &tp, &nt));
     PhaseScope ps_(PH_LONG, st);
-    launch_long_init<T>(d, (int)lg.size(), mb, st);
+    launch_long_init<T>(d, tp, (int)lg.size(), nt, st);
     CU(cudaGetLastError());
     return SSA_OK;
   }
@@ -1019,9 +1099,9 @@ struct LzEngine {
     }
     for (int s = 0; s < steps; ++s) {
       run_mv<T>(live[0], mvA, s);
-      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, nl, max_blk_s, s, st); }
+      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, t_sh, nl, n_sh, s, st); }
       run_mv<T>(live[0], mvAT, s);
-      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, nl, max_blk_l, s, st); }
+      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, s, st); }
     }
     { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
     CU(cudaGetLastError());
@@ -1035,7 +1115,7 @@ struct LzEngine {
   // restart every member still active
   int restart_active() {
     PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_rz, (int)live.size(), max_k, max_Ls, max_Kl, 0, st);
+    launch_ritz<T>(d_rz, (int)live.size(), max_k, t_rs, n_rs, t_rl, n_rl, 0, st);
     launch_restart(d_sv, (int)live.size(), st);
     CU(cudaGetLastError());
     return SSA_OK;
@@ -1045,19 +1125,24 @@ struct LzEngine {
   int retire(const std::vector<int>& idx) {
     if (idx.empty()) return SSA_OK;
     std::vector<RitzItem<T>> rz; std::vector<FinalItem<T>> fi;
+    std::vector<ssa_ctx*> cs;
     int mk = 1, mr = 1;
     int64_t mls = 1, mkl = 1, mrows = 1;
     for (int i : idx) {
       ssa_ctx* c = live[i];
+      cs.push_back(c);
       rz.push_back(ritz_item(c)); fi.push_back(final_item(c));
       mk = std::max(mk, c->ws.k); mr = std::max(mr, c->ws.r);
       mls = std::max(mls, c->ws.Ls); mkl = std::max(mkl, c->ws.Kl);
       mrows = std::max(mrows, std::max(c->L, c->K));
     }
     RitzItem<T>* d_r = nullptr; FinalItem<T>* d_f = nullptr;
+    int32_t *ts = nullptr, *tl = nullptr;
+    int ns = 0, nl = 0;
     TRY(up(rz, &d_r)); TRY(up(fi, &d_f));
+    TRY(ritz_tiles(cs, &ts, &ns, &tl, &nl));
     PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_r, (int)idx.size(), mk, mls, mkl, 1, st);
+    launch_ritz<T>(d_r, (int)idx.size(), mk, ts, ns, tl, nl, 1, st);
     launch_finalize<T>(d_f, (int)idx.size(), mr, mrows, st);
     CU(cudaGetLastError());
     for (int i : idx) {
@@ -1304,6 +1389,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         YItem<T> ya;
         ya.src = gx; ya.dst = gu; ya.mul = nullptr; ya.st = nullptr; ya.log2Mx = c->log2Mx; ya.log2My = c->log2My;
         ya.in_hi = wcols; ya.out_hi = My; ya.scale = T(0);
+        ya.tk = ypass_tk<T>(c->log2My);
         YItem<T> yb = ya;
         yb.dst = acc + (size_t)std::max(g, 0) * hs; yb.mul = gu; yb.in_hi = kcols;
         yb.scale = (T)(sig[i] / ((double)(2 * H) * (double)My));
@@ -1315,6 +1401,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         YItem<T> y;
         y.src = acc + (size_t)g * hs; y.dst = g2; y.mul = nullptr; y.st = nullptr;
         y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = My; y.out_hi = oy; y.scale = T(0);
+        y.tk = ypass_tk<T>(c->log2My);
         yi.push_back(y);
         Rec2Item<T> x;
         x.g2 = g2; x.log2Mx = c->log2Mx; x.pad_ = 0; x.inv_norm = 1.0;
@@ -1334,6 +1421,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
     TRY(upload(c0, yi, &d_yi)); tmp.push_back(d_yi);
     TRY(upload(c0, xi, &d_xi)); tmp.push_back(d_xi);
     if (fold) { TRY(upload(c0, fi, &d_fi)); tmp.push_back(d_fi); }
+    const Tiles y1{nullptr, 1, ypass_blocks(c->log2Mx, ypass_tk<T>(c->log2My))};
     for (size_t q = 0; q < c->ch.size(); ++q) {
       const Channel& h = c->ch[q];
       const int wcols = fold ? c->lb : c->ey, kcols = fold ? h.kb : h.cy;
@@ -1342,13 +1430,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         if (group_of[i] < 0) continue;
         const size_t e = 2 * ((size_t)q * r + i);
         launch_rec_col_fft<T, TV>(d_cu + e, 1, c->log2Mx, wcols, tw, st);
-        launch_ypass<T>(d_yu + e, 1, Y_FWD, c->log2Mx, c->log2My, -1, tw, st);
+        launch_ypass<T>(d_yu + e, y1, Y_FWD, c->log2My, -1, tw, st);
         launch_rec_col_fft<T, TV>(d_cu + e + 1, 1, c->log2Mx, kcols, tw, st);
-        launch_ypass<T>(d_yu + e + 1, 1, Y_CONVACC, c->log2Mx, c->log2My, -1, tw, st);
+        launch_ypass<T>(d_yu + e + 1, y1, Y_CONVACC, c->log2My, -1, tw, st);
       }
       for (int g = 0; g < ng; ++g) {
         const size_t e = (size_t)q * ng + g;
-        launch_ypass<T>(d_yi + e, 1, Y_INV, c->log2Mx, c->log2My, -1, tw, st);
+        launch_ypass<T>(d_yi + e, y1, Y_INV, c->log2My, -1, tw, st);
         launch_rec_xinv<T>(d_xi + e, 1, c->log2Mx, xi[e].ny, tw, st);
         if (fold) launch_rec_fold(d_fi + e, 1, h.nx, st);
       }
@@ -1431,7 +1519,10 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
   if (!on_device) { c->release(dd); c->release(dres); }
   if (g1) { c->release(g1); c->release(g2); }
   if (s.d1) c->release(s.d1);
-  if (s.d2) { c->release(s.d2); c->release(s.dy2); }
+  if (s.d2) {
+    c->release(s.d2); c->release(s.dy2);
+    c->release(s.t_xf); c->release(s.t_yp); c->release(s.t_xi);
+  }
   return SSA_OK;
 }
 
@@ -1514,11 +1605,12 @@ static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_
     const size_t ly = in->kind == SSA_2D ? (size_t)win->ly : 1;
     const size_t ww = (lx + 31) / 32;
     size_t need = rnd256(esz * c->total) + (in->mask ? rnd256(c->total) : 0) + 2 * rnd256(ly * ww * 4) +
-                  2 * rnd256((ly + 1) * 4) + rnd256(4);
+                  2 * rnd256((ly + 1) * 4) + rnd256(4) + rnd256(2 * ly * 4);
     for (auto& h : c->ch) {
       const size_t nw = (h.nx + 31) / 32;
       const size_t cy = h.ny, kw = nw;
-      need += rnd256(h.ny * nw * 4) * 2 + rnd256(cy * kw * 4) + 2 * rnd256((cy + 1) * 4) + rnd256(h.nx * h.ny * 4);
+      need += rnd256(h.ny * nw * 4) * 2 + rnd256(cy * kw * 4) + 2 * rnd256((cy + 1) * 4) + rnd256(h.nx * h.ny * 4) +
+              rnd256(h.ny * (nw + 1) * 4) + rnd256(cy * (kw + 1) * 4);
     }
     int rc0 = c->make_arena(c->embed_arena, need);
     if (rc0) return bail(rc0);
@@ -1662,24 +1754,42 @@ int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, voi
     if (!vec.empty() && g_ring.copy(*dptr, vec.data(), sizeof(X) * vec.size(), st) != SSA_OK) return SSA_ECUDA;
     return SSA_OK;
   };
+  PrefixItem *d_opre = nullptr, *d_kpre = nullptr;
+  // block ranges of every item in each batched launch
+  std::vector<int32_t> t_obs{0}, t_org{0}, t_cnt{0}, t_opre{0}, t_kpre{0}, t_wts{0};
+  for (auto& o : eb.obs) t_obs.push_back(t_obs.back() + ((o.nx + 255) >> 8) * o.ny);
+  for (auto& o : eb.org) t_org.push_back(t_org.back() + ((o.cx + 255) >> 8) * o.cy);
+  for (auto& o : eb.cnt) t_cnt.push_back(t_cnt.back() + o.ncols);
+  for (auto& o : eb.opre) t_opre.push_back(t_opre.back() + o.ncols);
+  for (auto& o : eb.kpre) t_kpre.push_back(t_kpre.back() + o.ncols);
+  int32_t *p_obs = nullptr, *p_org = nullptr, *p_cnt = nullptr, *p_opre = nullptr, *p_kpre = nullptr, *p_wts = nullptr;
   int urc = upload_raw(eb.obs, &d_obs);
   if (urc == SSA_OK) urc = upload_raw(eb.org, &d_org);
   if (urc == SSA_OK) urc = upload_raw(eb.cnt, &d_cnt);
+  if (urc == SSA_OK) urc = upload_raw(eb.opre, &d_opre);
+  if (urc == SSA_OK) urc = upload_raw(eb.kpre, &d_kpre);
+  if (urc == SSA_OK) urc = upload_raw(t_obs, &p_obs);
+  if (urc == SSA_OK) urc = upload_raw(t_org, &p_org);
+  if (urc == SSA_OK) urc = upload_raw(t_cnt, &p_cnt);
+  if (urc == SSA_OK) urc = upload_raw(t_opre, &p_opre);
+  if (urc == SSA_OK) urc = upload_raw(t_kpre, &p_kpre);
   if (urc != SSA_OK) return fail(urc, "embed item upload");
-  launch_obs_batch(d_obs, (int)eb.obs.size(), eb.max_nx, eb.max_ny, st);
-  launch_origins_batch(d_org, (int)eb.org.size(), eb.max_cx, eb.max_cy, st);
-  launch_counts_batch(d_cnt, (int)eb.cnt.size(), eb.max_cols, st);
+  launch_obs_batch(d_obs, p_obs, (int)eb.obs.size(), t_obs.back(), st);
+  launch_prefix_batch(d_opre, p_opre, (int)eb.opre.size(), t_opre.back(), st);
+  launch_origins_batch(d_org, p_org, (int)eb.org.size(), t_org.back(), st);
+  launch_prefix_batch(d_kpre, p_kpre, (int)eb.kpre.size(), t_kpre.back(), st);
+  launch_counts_batch(d_cnt, p_cnt, (int)eb.cnt.size(), t_cnt.back(), st);
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(pin, d_tot, sizeof(int32_t) * std::max<size_t>(ncount, 1), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   std::vector<int32_t> totals(pin, pin + ncount);
   for (int i = 0; i < n; ++i)
     if (rc[i] == SSA_OK) rc[i] = embed_stage2(outs[i], eb, i, totals.data());
+  for (auto& o : eb.wts) t_wts.push_back(t_wts.back() + ((o.nx + 255) >> 8) * o.ny);
   urc = upload_raw(eb.wts, &d_wts);
+  if (urc == SSA_OK) urc = upload_raw(t_wts, &p_wts);
   if (urc != SSA_OK) return fail(urc, "embed item upload");
-  int wnx = 1, wny = 1;
-  for (auto& w : eb.wts) { wnx = std::max(wnx, w.nx); wny = std::max(wny, w.ny); }
-  launch_weights_batch(d_wts, (int)eb.wts.size(), wnx, wny, st);
+  launch_weights_batch(d_wts, p_wts, (int)eb.wts.size(), t_wts.back(), st);
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(pin, d_err, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
@@ -1687,6 +1797,8 @@ int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, voi
     if (rc[i] == SSA_OK) rc[i] = embed_stage3(outs[i], pin[i]);
   cudaFreeAsync(d_tot, st); cudaFreeAsync(d_err, st);
   cudaFreeAsync(d_obs, st); cudaFreeAsync(d_org, st); cudaFreeAsync(d_cnt, st); cudaFreeAsync(d_wts, st);
+  cudaFreeAsync(d_opre, st); cudaFreeAsync(d_kpre, st);
+  for (int32_t* q : {p_obs, p_org, p_cnt, p_opre, p_kpre, p_wts}) cudaFreeAsync(q, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SSA_ECUDA, "embed: %s", cudaGetErrorString(e));
   return finish();

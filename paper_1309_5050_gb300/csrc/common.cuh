@@ -59,6 +59,20 @@ struct MapDev {
   int64_t limit;           // dense mode: only indices x + bx*y < limit belong to the set
 };
 
+// Batched launches over items of different sizes: item i owns the blocks
+// [pre[i], pre[i+1]) of a one-dimensional grid (pre[n] = grid size).  Returns
+// the item of block b and sets the block's index within it.
+__device__ __forceinline__ int tile_item(const int32_t* __restrict__ pre, int n, int b, int& local) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pre + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  local = b - __ldg(pre + lo);
+  return lo;
+}
+
 // Error word written by kernels that detect bad input or a stalled wait.
 enum : int { DEV_OK = 0, DEV_BAD_INPUT = 1 };
 

@@ -53,12 +53,14 @@ __device__ void block_dots(const double* __restrict__ U, int64_t ldu, int64_t r0
 // The coupling terms beta_{j-1} u_{j-1} (or rho_i u_i after a restart) are
 // not subtracted explicitly: they are exactly the components along U that the
 // first Gram-Schmidt pass removes.
-__global__ void __launch_bounds__(SHORT_RB) k_short1(const ShortItem* __restrict__ items, int s) {
-  const ShortItem it = items[blockIdx.y];
+__global__ void __launch_bounds__(SHORT_RB) k_short1(const ShortItem* __restrict__ items, const int32_t* __restrict__ tpre,
+                                                     int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
   const int j = it.st->j0 + s;
-  if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
+  if (j < 0 || lz_skip(it.st, j)) return;
   __shared__ double pv[SHORT_RB];
-  const int64_t r0 = (int64_t)blockIdx.x * SHORT_RB;
+  const int64_t r0 = (int64_t)blk * SHORT_RB;
   const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
   const int64_t row = r0 + threadIdx.x;
   double val = 0.0;
@@ -88,17 +90,19 @@ __global__ void __launch_bounds__(SHORT_RB) k_short1(const ShortItem* __restrict
   }
   pv[threadIdx.x] = val;
   __syncthreads();
-  block_dots(it.U, it.ldu, r0, nrows, pv, j, it.cpa + (int64_t)blockIdx.x * (KMAX + 1));
+  block_dots(it.U, it.ldu, r0, nrows, pv, j, it.cpa + (int64_t)blk * (KMAX + 1));
 }
 
 // steps 2 and 3: p -= U c (c summed from the partials in fixed order); step 2
 // also forms the partial dots of the second Gram-Schmidt pass, step 3 the
 // partial squared norm.
 template <int PASS>
-__global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restrict__ items, int s) {
-  const ShortItem it = items[blockIdx.y];
+__global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restrict__ items, const int32_t* __restrict__ tpre,
+                                                      int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
   const int j = it.st->j0 + s;
-  if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
+  if (j < 0 || lz_skip(it.st, j)) return;
   __shared__ double c[KMAX + 1];
   __shared__ double pv[SHORT_RB];
   __shared__ double red[32];
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restric
     c[i] = a;
   }
   __syncthreads();
-  const int64_t r0 = (int64_t)blockIdx.x * SHORT_RB;
+  const int64_t r0 = (int64_t)blk * SHORT_RB;
   const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
   const int64_t row = r0 + threadIdx.x;
   double val = 0.0;
@@ -121,19 +125,21 @@ __global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restric
   if (PASS == 2) {
     pv[threadIdx.x] = val;
     __syncthreads();
-    block_dots(it.U, it.ldu, r0, nrows, pv, j, it.cpb + (int64_t)blockIdx.x * (KMAX + 1));
+    block_dots(it.U, it.ldu, r0, nrows, pv, j, it.cpb + (int64_t)blk * (KMAX + 1));
   } else {
     const double tot = block_sum(val * val, red);
-    if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
+    if (threadIdx.x == 0) it.npart[blk] = tot;
   }
 }
 
 // step 4: alpha_j = ||p||, u_j = p / alpha_j, B[j,j] = alpha_j
-__global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict__ items, int s) {
-  const ShortItem it = items[blockIdx.y];
+__global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict__ items, const int32_t* __restrict__ tpre,
+                                                     int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
   LzState* st = it.st;
   const int j = st->j0 + s;
-  if (j < 0 || lz_skip(st, j) || (int)blockIdx.x >= it.nblk) return;
+  if (j < 0 || lz_skip(st, j)) return;
   __shared__ double alpha_s;
   if (threadIdx.x == 0) {
     double a = 0.0;
@@ -143,9 +149,9 @@ __global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict
   __syncthreads();
   const double alpha = alpha_s;
   const bool ok = alpha > 1e-200;
-  const int64_t row = (int64_t)blockIdx.x * SHORT_RB + threadIdx.x;
+  const int64_t row = (int64_t)blk * SHORT_RB + threadIdx.x;
   if (row < it.Ls) it.U[row + it.ldu * j] = ok ? it.p[row] / alpha : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blk == 0 && threadIdx.x == 0) {
     it.B[j + (int64_t)it.ldb * j] = ok ? alpha : 0.0;
     if (ok) { if (alpha > st->anorm) st->anorm = alpha; }
     else { st->k = j + 1; st->beta_k = 0.0; st->breakdown = 1; }
@@ -164,16 +170,18 @@ __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i) {
 
 // q = sum(partials) - alpha_j v_j ; partial squared norms
 template <typename T>
-__global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ items, int s) {
-  const LongItem<T> it = items[blockIdx.y];
+__global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ items, const int32_t* __restrict__ tpre,
+                                               int n, int s) {
+  int blk;
+  const LongItem<T> it = items[tile_item(tpre, n, blockIdx.x, blk)];
   const int j = it.st->j0 + s;
-  if (j < 0 || lz_skip(it.st, j) || (int)blockIdx.x >= it.nblk) return;
+  if (j < 0 || lz_skip(it.st, j)) return;
   __shared__ double red[32];
   // alpha_j v_j with v_j = colscale[j] * V[:, j] (stored unnormalised)
   const T coef = (T)(it.B[j + (int64_t)it.ldb * j] * it.colscale[j]);
   const T* vj = it.V + it.ldv * j;
   T* qn = it.V + it.ldv * (j + 1);
-  const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
+  const int64_t r0 = (int64_t)blk * LONG_RB;
   double acc = 0.0;
   for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
     const int64_t row = r0 + t;
@@ -185,15 +193,17 @@ __global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ i
     acc += (double)v * (double)v;
   }
   const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
+  if (threadIdx.x == 0) it.npart[blk] = tot;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict__ items) {
-  const LongItem<T> it = items[blockIdx.y];
-  if (!it.st->active || (int)blockIdx.x >= it.nblk) return;
+__global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict__ items, const int32_t* __restrict__ tpre,
+                                                   int n) {
+  int blk;
+  const LongItem<T> it = items[tile_item(tpre, n, blockIdx.x, blk)];
+  if (!it.st->active) return;
   __shared__ double red[32];
-  const int64_t r0 = (int64_t)blockIdx.x * LONG_RB;
+  const int64_t r0 = (int64_t)blk * LONG_RB;
   double acc = 0.0;
   for (int t = threadIdx.x; t < LONG_RB; t += blockDim.x) {
     const int64_t row = r0 + t;
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict
     acc += (double)v * (double)v;
   }
   const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) it.npart[blockIdx.x] = tot;
+  if (threadIdx.x == 0) it.npart[blk] = tot;
 }
 
 // beta_j = ||q|| from the partial norms (fixed order); column j+1 of V keeps q
@@ -465,11 +475,13 @@ __global__ void k_restart(const SvdItem* __restrict__ items) {
 // columns tx + 8m (a < RB/32, m < 8) in registers, so every shared load feeds
 // several FMAs and each warp writes 32 consecutive rows of a column.
 template <typename T, bool SHORT>
-__global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, int final_pass) {
+__global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, const int32_t* __restrict__ tpre,
+                                              int n, int final_pass) {
   typedef typename std::conditional<SHORT, double, T>::type E;
   constexpr int RB = (sizeof(E) == 8) ? 64 : 128;
   constexpr int RA = RB / 32;
-  const RitzItem<T> it = items[blockIdx.y];
+  int rblk;
+  const RitzItem<T> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
   const LzState* st = it.st;
   if (!final_pass && !st->active) return;
   const int k = st->k;
@@ -481,7 +493,7 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   const double* C = SHORT ? it.P : it.Q;
   const int kc = SHORT ? k : k + 1;
   const int cld = SHORT ? it.ldc : it.ldc + 1;
-  const int64_t r0 = (int64_t)blockIdx.x * RB;
+  const int64_t r0 = (int64_t)rblk * RB;
   if (r0 >= nrow) return;
   const int nr = (int)imin64(RB, nrow - r0);
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -599,26 +611,25 @@ __global__ void __launch_bounds__(256) k_final_copy(const FinalItem<T>* __restri
 }
 
 // ------------------------------------------------------------ launchers
-void launch_short_steps(const ShortItem* items, int n, int max_blk, int s, cudaStream_t st) {
-  if (n <= 0) return;
-  dim3 g(max_blk, n);
-  k_short1<<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
-  k_short23<2><<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
-  k_short23<3><<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
-  k_short4<<<g, SHORT_RB, 0, st>>>(items, s); count_launch();
+void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_short1<<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+  k_short23<2><<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+  k_short23<3><<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+  k_short4<<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
 }
 
 template <typename T>
-void launch_long_step(const LongItem<T>* items, int n, int max_blk, int s, cudaStream_t st) {
-  if (n <= 0) return;
-  k_long1<T><<<dim3(max_blk, n), 256, 0, st>>>(items, s); count_launch();
+void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_long1<T><<<tiles, 256, 0, st>>>(items, tpre, n, s); count_launch();
   k_long_norm<T><<<n, 256, 0, st>>>(items, s); count_launch();
 }
 
 template <typename T>
-void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t st) {
-  if (n <= 0) return;
-  k_long_init<T><<<dim3(max_blk, n), 256, 0, st>>>(items); count_launch();
+void launch_long_init(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_long_init<T><<<tiles, 256, 0, st>>>(items, tpre, n); count_launch();
   k_long_norm<T><<<n, 256, 0, st>>>(items, -1); count_launch();
 }
 
@@ -635,17 +646,17 @@ void launch_restart(const SvdItem* items, int n, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_ritz(const RitzItem<T>* items, int n, int kmax, int64_t max_short, int64_t max_long, int final_pass,
-                 cudaStream_t st) {
+void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s, int tiles_s, const int32_t* pre_l,
+                 int tiles_l, int final_pass, cudaStream_t st) {
   if (n <= 0) return;
-  const int rs = 64, rl = (sizeof(T) == 8) ? 64 : 128;
+  const int rs = RITZ_RB_SHORT, rl = ritz_rb_long<T>();
   const int kp = ((kmax + 7) / 8) * 8;
   const size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)(kmax + 1) * kp * sizeof(double);
   const size_t sml = (size_t)rl * (kmax + 2) * sizeof(T) + (size_t)(kmax + 1) * kp * sizeof(T);
   set_max_smem((const void*)k_ritz<T, true>);
   set_max_smem((const void*)k_ritz<T, false>);
-  k_ritz<T, true><<<dim3((unsigned)((max_short + rs - 1) / rs), n), 256, sms, st>>>(items, final_pass); count_launch();
-  k_ritz<T, false><<<dim3((unsigned)((max_long + rl - 1) / rl), n), 256, sml, st>>>(items, final_pass); count_launch();
+  if (tiles_s > 0) { k_ritz<T, true><<<tiles_s, 256, sms, st>>>(items, pre_s, n, final_pass); count_launch(); }
+  if (tiles_l > 0) { k_ritz<T, false><<<tiles_l, 256, sml, st>>>(items, pre_l, n, final_pass); count_launch(); }
 }
 
 template <typename T>
@@ -657,9 +668,10 @@ void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_ro
 }
 
 #define INST(T)                                                                                        \
-  template void launch_long_step<T>(const LongItem<T>*, int, int, int, cudaStream_t);                  \
-  template void launch_long_init<T>(const LongItem<T>*, int, int, cudaStream_t);                       \
-  template void launch_ritz<T>(const RitzItem<T>*, int, int, int64_t, int64_t, int, cudaStream_t);     \
+  template void launch_long_step<T>(const LongItem<T>*, const int32_t*, int, int, int, cudaStream_t);  \
+  template void launch_long_init<T>(const LongItem<T>*, const int32_t*, int, int, cudaStream_t);       \
+  template void launch_ritz<T>(const RitzItem<T>*, int, int, const int32_t*, int, const int32_t*, int,  \
+                               int, cudaStream_t);                                                      \
   template void launch_finalize<T>(const FinalItem<T>*, int, int, int64_t, cudaStream_t);
 INST(float)
 INST(double)

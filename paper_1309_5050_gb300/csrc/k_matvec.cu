@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ item
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_mv_xfwd(const MvItem<T>* __restrict__ items, int s,
+__global__ void __launch_bounds__(512) k_mv_xfwd(const MvItem<T>* __restrict__ items, Tiles tl, int s,
                                                  const Cx<T>* __restrict__ tw) {
-  const MvItem<T> it = items[blockIdx.y];
-  const int y = blockIdx.x;
+  int y;
+  const MvItem<T> it = items[tile_of(tl, blockIdx.x, y)];
   if (y >= it.y_in_hi || item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
@@ -168,10 +168,10 @@ __global__ void __launch_bounds__(512) k_mv_xfwd(const MvItem<T>* __restrict__ i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_mv_xinv(const MvItem<T>* __restrict__ items, int s,
+__global__ void __launch_bounds__(512) k_mv_xinv(const MvItem<T>* __restrict__ items, Tiles tl, int s,
                                                  const Cx<T>* __restrict__ tw) {
-  const MvItem<T> it = items[blockIdx.y];
-  const int y = blockIdx.x;
+  int y;
+  const MvItem<T> it = items[tile_of(tl, blockIdx.x, y)];
   if (y >= it.y_out_hi || item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
@@ -186,15 +186,15 @@ __global__ void __launch_bounds__(512) k_mv_xinv(const MvItem<T>* __restrict__ i
 
 // y-pass over a tile of TK consecutive x-frequencies (all My rows).
 template <typename T>
-__global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ items, int mode, int s,
+__global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ items, Tiles tl, int mode, int s,
                                                int buf_elems, const Cx<T>* __restrict__ tw) {
-  const YItem<T> it = items[blockIdx.y];
+  int b0;
+  const YItem<T> it = items[tile_of(tl, blockIdx.x, b0)];
   if (item_skip<T>(it.st, s)) return;
-  const int log2My = it.log2My, My = 1 << log2My;
+  const int log2My = it.log2My;
   const int H = 1 << (it.log2Mx - 1), ld = H + 1;
-  int TK = buf_elems / padded_len(My);
-  if (TK > 16) TK = 16;
-  const int k0 = blockIdx.x * TK;
+  const int TK = it.tk;             // TK * padded_len(My) <= buf_elems (ypass_tk)
+  const int k0 = b0 * TK;
   if (k0 > H) return;
   extern __shared__ __align__(16) unsigned char smem[];
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ item
 // Data to half spectrum, x-pass: masked / missing samples enter as zero
 // (they never reach the trajectory matrix); scaled by 1/(Mx My).
 template <typename T>
-__global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ items,
+__global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ items, Tiles tl,
                                                 const Cx<T>* __restrict__ tw) {
-  const SpecItem<T> it = items[blockIdx.y];
-  const int y = blockIdx.x;
+  int y;
+  const SpecItem<T> it = items[tile_of(tl, blockIdx.x, y)];
   if (y >= it.ny) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H, Mx = 2 * H;
@@ -294,49 +294,44 @@ void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<
 }
 
 template <typename T>
-void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
-                 int max_y_in, int max_y_out, int s, const Cx<T>* tw, cudaStream_t st) {
+void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, Tiles xf, Tiles yp, Tiles xi,
+                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st) {
   if (n <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_mv_xfwd<T>);
   set_max_smem((const void*)k_mv_xinv<T>);
-  k_mv_xfwd<T><<<dim3(max_y_in, n), 512, sm, st>>>(items, s, tw); count_launch();
-  launch_ypass<T>(yitems, n, Y_MULCONJ_INV, max_log2Mx, max_log2My, s, tw, st);
-  k_mv_xinv<T><<<dim3(max_y_out, n), 512, sm, st>>>(items, s, tw); count_launch();
+  if (xf.total > 0) { k_mv_xfwd<T><<<xf.total, 512, sm, st>>>(items, xf, s, tw); count_launch(); }
+  launch_ypass<T>(yitems, yp, Y_MULCONJ_INV, max_log2My, s, tw, st);
+  if (xi.total > 0) { k_mv_xinv<T><<<xi.total, 512, sm, st>>>(items, xi, s, tw); count_launch(); }
 }
 
 template <typename T>
-void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int max_log2My, int s,
-                  const Cx<T>* tw, cudaStream_t st) {
-  if (n <= 0) return;
+void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int s, const Cx<T>* tw,
+                  cudaStream_t st) {
+  if (tl.total <= 0) return;
   const int buf = ypass_buf_elems<T>();
-  int TK = buf / padded_len(1 << max_log2My);   // smallest tile width among the items
-  if (TK > 16) TK = 16;
-  if (TK < 1) TK = 1;
-  const int H = 1 << (max_log2Mx - 1);
-  const int tiles = (H + 1 + TK - 1) / TK;
   const int N = 1 << (max_log2My < 3 ? 3 : max_log2My);
   const size_t sm = (2 * (size_t)buf + N / 8 + 1) * sizeof(Cx<T>);
   set_max_smem((const void*)k_ypass<T>);
-  k_ypass<T><<<dim3(tiles, n), 512, sm, st>>>(items, mode, s, buf, tw); count_launch();
+  k_ypass<T><<<tl.total, 512, sm, st>>>(items, tl, mode, s, buf, tw); count_launch();
 }
 
 template <typename T>
-void launch_spec(const SpecItem<T>* items, int n, const YItem<T>* yitems, int ny, int max_log2Mx, int max_log2My,
-                 int max_ny, const Cx<T>* tw, cudaStream_t st) {
-  if (n <= 0) return;
+void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Tiles sy, int max_log2Mx,
+                 int max_log2My, const Cx<T>* tw, cudaStream_t st) {
+  if (sx.total <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_spec_x<T>);
-  k_spec_x<T><<<dim3(max_ny, n), 512, sm, st>>>(items, tw); count_launch();
-  if (ny > 0 && max_log2My > 0) launch_ypass<T>(yitems, ny, Y_FWD, max_log2Mx, max_log2My, -1, tw, st);
+  k_spec_x<T><<<sx.total, 512, sm, st>>>(items, sx, tw); count_launch();
+  if (max_log2My > 0) launch_ypass<T>(yitems, sy, Y_FWD, max_log2My, -1, tw, st);
 }
 
 #define INST(T)                                                                                       \
   template void launch_mv1d<T>(const MvItem<T>*, int, int, int, const Cx<T>*, cudaStream_t);          \
-  template void launch_mv2d<T>(const MvItem<T>*, const YItem<T>*, int, int, int, int, int, int,        \
-                               const Cx<T>*, cudaStream_t);                                           \
-  template void launch_ypass<T>(const YItem<T>*, int, int, int, int, int, const Cx<T>*, cudaStream_t); \
-  template void launch_spec<T>(const SpecItem<T>*, int, const YItem<T>*, int, int, int, int,          \
+  template void launch_mv2d<T>(const MvItem<T>*, const YItem<T>*, int, Tiles, Tiles, Tiles, int, int,  \
+                               int, const Cx<T>*, cudaStream_t);                                      \
+  template void launch_ypass<T>(const YItem<T>*, Tiles, int, int, int, const Cx<T>*, cudaStream_t);    \
+  template void launch_spec<T>(const SpecItem<T>*, Tiles, const YItem<T>*, Tiles, int, int,           \
                                const Cx<T>*, cudaStream_t);
 INST(float)
 INST(double)

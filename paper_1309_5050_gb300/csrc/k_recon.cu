@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T, TV>* __restrict
   RSmem<T> sm(smem, H);
   load_octant(sm.tab, it.log2Mx - 1, tw);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = cx(T(0), T(0));
+  __syncthreads();   // an empty group reads C right away below
   for (int c = 0; c < it.ncomp; ++c) {
     const int i = it.comps[c];
     rec_load_col<T, TV>(reinterpret_cast<T*>(sm.A), 2 * H, it.V + it.ldv * i, it.map, 0, sm.pre, sm.wt);

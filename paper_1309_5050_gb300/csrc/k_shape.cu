@@ -144,11 +144,14 @@ __global__ void k_weights(const uint32_t* kbits, int kwords, int kcols, const ui
 }
 
 // ---------------------------------------------------------------- batched forms
-__global__ void k_obs_batch(const ObsItem* __restrict__ items) {
-  const ObsItem it = items[blockIdx.z];
-  const int y = blockIdx.y;
-  if (y >= it.ny || (int)blockIdx.x * (int)blockDim.x >= ((it.nx + 31) & ~31)) return;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+// Batched kernels: one block per 256 grid rows of one column of one item
+// (tiles laid out by tile_item).
+__global__ void k_obs_batch(const ObsItem* __restrict__ items, const int32_t* __restrict__ pre, int n) {
+  int t;
+  const ObsItem it = items[tile_item(pre, n, blockIdx.x, t)];
+  const int tx = (it.nx + 255) >> 8;
+  const int y = t / tx;
+  const int x = (t - y * tx) * 256 + threadIdx.x;
   bool ok = false;
   if (x < it.nx) {
     const int64_t g = x + (int64_t)it.nx * y;
@@ -161,13 +164,72 @@ __global__ void k_obs_batch(const ObsItem* __restrict__ items) {
   if ((threadIdx.x & 31) == 0 && w < it.words) it.bits[(int64_t)y * it.words + w] = bal;
 }
 
-__global__ void k_origins_batch(const OriginItem* __restrict__ items) {
-  const OriginItem it = items[blockIdx.z];
-  const int ky = blockIdx.y;
-  if (ky >= it.cy || (int)blockIdx.x * (int)blockDim.x >= ((it.cx + 31) & ~31)) return;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
+// Set bits of a column bit row at positions < x, from the word prefix counts
+// (x clamped to [0, 32 nw]).
+__device__ __forceinline__ int bits_below(const uint32_t* col, const int32_t* pre, int nw, int x) {
+  if (x <= 0) return 0;
+  const int w = x >> 5;
+  if (w >= nw) return pre[nw];
+  const int b = x & 31;
+  return pre[w] + (b ? __popc(col[w] & ((1u << b) - 1u)) : 0);
+}
+
+__global__ void k_prefix_batch(const PrefixItem* __restrict__ items, const int32_t* __restrict__ tpre, int n) {
+  int y;
+  const PrefixItem it = items[tile_item(tpre, n, blockIdx.x, y)];
+  __shared__ int wt[32];
+  __shared__ int carry;
+  const uint32_t* col = it.bits + (int64_t)y * it.words;
+  int32_t* pre = it.pre + (int64_t)y * (it.words + 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < it.words; b0 += blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const int v = i < it.words ? __popc(col[i]) : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) wt[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c = carry;
+      for (int w = 0; w < nwp; ++w) { const int t = wt[w]; wt[w] = c; c += t; }
+      carry = c;
+    }
+    __syncthreads();
+    if (i < it.words) pre[i] = x - v + wt[warp];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) pre[it.words] = carry;
+}
+
+void launch_prefix_batch(const PrefixItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_prefix_batch<<<tiles, 256, 0, st>>>(it, pre, n); count_launch();
+}
+
+__global__ void k_origins_batch(const OriginItem* __restrict__ items, const int32_t* __restrict__ pre, int n) {
+  int t;
+  const OriginItem it = items[tile_item(pre, n, blockIdx.x, t)];
+  const int tx = (it.cx + 255) >> 8;
+  const int ky = t / tx;
+  const int kx = (t - ky * tx) * 256 + threadIdx.x;
   bool in = kx < it.cx;
-  if (in) {
+  if (in && it.interval) {
+    // window column ly occupies rows [a, b]: all of kx + a .. kx + b observed
+    for (int ly = 0; ly < it.ey && in; ++ly) {
+      const int a = it.wint[2 * ly], b = it.wint[2 * ly + 1];
+      if (a < 0) continue;
+      const int64_t c = (int64_t)(ky + ly);
+      const uint32_t* col = it.obs + c * it.nwords_obs;
+      const int32_t* pre = it.opre + c * (it.nwords_obs + 1);
+      const int s = kx + a, e = kx + b + 1;
+      in = bits_below(col, pre, it.nwords_obs, e) - bits_below(col, pre, it.nwords_obs, s) == e - s;
+    }
+  } else if (in) {
     for (int ly = 0; ly < it.ey && in; ++ly) {
       const uint32_t* col = it.obs + (int64_t)(ky + ly) * it.nwords_obs;
       const uint32_t* wr = it.wrows + (int64_t)ly * it.wwords;
@@ -183,10 +245,9 @@ __global__ void k_origins_batch(const OriginItem* __restrict__ items) {
   if ((threadIdx.x & 31) == 0 && w < it.kwords) it.kbits[(int64_t)ky * it.kwords + w] = bal;
 }
 
-__global__ void k_popc_batch(const CountItem* __restrict__ items) {
-  const CountItem it = items[blockIdx.z];
-  const int y = blockIdx.x;
-  if (y >= it.ncols) return;
+__global__ void k_popc_batch(const CountItem* __restrict__ items, const int32_t* __restrict__ pre, int n) {
+  int y;
+  const CountItem it = items[tile_item(pre, n, blockIdx.x, y)];
   __shared__ int red[32];
   int c = 0;
   for (int w = threadIdx.x; w < it.words; w += blockDim.x) c += __popc(it.bits[(int64_t)y * it.words + w]);
@@ -223,13 +284,27 @@ __global__ void k_scan_batch(const CountItem* __restrict__ items) {
   if (threadIdx.x == 0) { it.colbase[it.ncols] = carry; *it.total = carry; }
 }
 
-__global__ void k_weights_batch(const WeightItem* __restrict__ items) {
-  const WeightItem it = items[blockIdx.z];
-  const int y = blockIdx.y;
-  if (y >= it.ny || (int)blockIdx.x * (int)blockDim.x >= ((it.nx + 31) & ~31)) return;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_weights_batch(const WeightItem* __restrict__ items, const int32_t* __restrict__ pre, int n) {
+  int t;
+  const WeightItem it = items[tile_item(pre, n, blockIdx.x, t)];
+  const int tx = (it.nx + 255) >> 8;
+  const int y = t / tx;
+  const int x = (t - y * tx) * 256 + threadIdx.x;
   int cnt = 0;
-  if (x < it.nx) {
+  if (x < it.nx && it.interval) {
+    // origins kx with kx + l = x for l in [a, b]: kx in [x - b, x - a]
+    for (int ly = 0; ly < it.ey; ++ly) {
+      const int ky = y - ly;
+      if (ky < 0 || ky >= it.kcols) continue;
+      const int a = it.wint[2 * ly], b = it.wint[2 * ly + 1];
+      if (a < 0) continue;
+      const uint32_t* col = it.kbits + (int64_t)ky * it.kwords;
+      const int32_t* pre = it.kpre + (int64_t)ky * (it.kwords + 1);
+      const int s = x - b, e = x - a + 1;
+      if (e > s) cnt += bits_below(col, pre, it.kwords, e) - bits_below(col, pre, it.kwords, s);
+    }
+    it.w[x + (int64_t)it.nx * y] = cnt;
+  } else if (x < it.nx) {
     for (int ly = 0; ly < it.ey; ++ly) {
       const int ky = y - ly;
       if (ky < 0 || ky >= it.kcols) continue;
@@ -249,22 +324,22 @@ __global__ void k_weights_batch(const WeightItem* __restrict__ items) {
   if ((threadIdx.x & 31) == 0 && wd < it.nwords) it.nbits[(int64_t)y * it.nwords + wd] = bal;
 }
 
-void launch_obs_batch(const ObsItem* it, int n, int max_nx, int max_ny, cudaStream_t st) {
-  if (n <= 0) return;
-  k_obs_batch<<<dim3((max_nx + 255) / 256, max_ny, n), 256, 0, st>>>(it); count_launch();
+void launch_obs_batch(const ObsItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_obs_batch<<<tiles, 256, 0, st>>>(it, pre, n); count_launch();
 }
-void launch_origins_batch(const OriginItem* it, int n, int max_cx, int max_cy, cudaStream_t st) {
-  if (n <= 0 || max_cx <= 0 || max_cy <= 0) return;
-  k_origins_batch<<<dim3((max_cx + 255) / 256, max_cy, n), 256, 0, st>>>(it); count_launch();
+void launch_origins_batch(const OriginItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_origins_batch<<<tiles, 256, 0, st>>>(it, pre, n); count_launch();
 }
-void launch_counts_batch(const CountItem* it, int n, int max_cols, cudaStream_t st) {
+void launch_counts_batch(const CountItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
   if (n <= 0) return;
-  k_popc_batch<<<dim3(std::max(max_cols, 1), 1, n), 256, 0, st>>>(it); count_launch();
+  if (tiles > 0) { k_popc_batch<<<tiles, 256, 0, st>>>(it, pre, n); count_launch(); }
   k_scan_batch<<<n, 1024, 0, st>>>(it); count_launch();
 }
-void launch_weights_batch(const WeightItem* it, int n, int max_nx, int max_ny, cudaStream_t st) {
-  if (n <= 0) return;
-  k_weights_batch<<<dim3((max_nx + 255) / 256, max_ny, n), 256, 0, st>>>(it); count_launch();
+void launch_weights_batch(const WeightItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_weights_batch<<<tiles, 256, 0, st>>>(it, pre, n); count_launch();
 }
 
 // ---------------------------------------------------------------- launchers

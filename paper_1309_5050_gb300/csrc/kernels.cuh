@@ -90,6 +90,18 @@ struct YItem {
   int32_t log2Mx, log2My;
   int32_t in_hi, out_hi;
   T scale;
+  int32_t tk;               // x-frequencies per block (ypass_tk), set by the host
 };
+
+// Block ranges of a batched launch: item i owns blocks [pre[i], pre[i+1]);
+// pre == nullptr means one item owning every block.
+struct Tiles {
+  const int32_t* pre;
+  int32_t n, total;
+};
+__device__ __forceinline__ int tile_of(const Tiles& t, int b, int& local) {
+  if (!t.pre) { local = b; return 0; }
+  return tile_item(t.pre, t.n, b, local);
+}
 
 }  // namespace ssa

@@ -77,16 +77,22 @@ struct FinalItem {
   double* sgn;                                // r signs (scratch)
 };
 
-void launch_short_steps(const ShortItem* items, int n, int max_blk, int s, cudaStream_t st);
+// Row-block launches are tile-mapped: item i owns blocks [tpre[i], tpre[i+1])
+// (short side ceil(Ls / SHORT_RB), long side ceil(Kl / LONG_RB), Ritz
+// ceil(rows / RITZ_RB_*)), tiles = tpre[n].
+constexpr int RITZ_RB_SHORT = 64;
 template <typename T>
-void launch_long_step(const LongItem<T>* items, int n, int max_blk, int s, cudaStream_t st);
+constexpr int ritz_rb_long() { return sizeof(T) == 8 ? 64 : 128; }
+void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
 template <typename T>
-void launch_long_init(const LongItem<T>* items, int n, int max_blk, cudaStream_t st);
+void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
+template <typename T>
+void launch_long_init(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, cudaStream_t st);
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st);
 void launch_restart(const SvdItem* items, int n, cudaStream_t st);
 template <typename T>
-void launch_ritz(const RitzItem<T>* items, int n, int kmax, int64_t max_short, int64_t max_long, int final_pass,
-                 cudaStream_t st);
+void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s, int tiles_s, const int32_t* pre_l,
+                 int tiles_l, int final_pass, cudaStream_t st);
 template <typename T>
 void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st);
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "kernels.cuh"
+#include "fft_block.cuh"
 
 namespace ssa {
 
@@ -26,14 +27,28 @@ template <typename T> const Cx<T>* twiddles(int device);
 // matvec / spectrum
 template <typename T>
 void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st);
+// y-pass tile width: x-frequencies per block for a y-FFT of 2^log2My points,
+// from the block's two 64 KB buffers, at most 64.
 template <typename T>
-void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, int max_log2Mx, int max_log2My,
-                 int max_y_in, int max_y_out, int s, const Cx<T>* tw, cudaStream_t st);
+inline int ypass_tk(int log2My) {
+  const int buf = (64 * 1024) / (int)sizeof(Cx<T>);
+  int tk = buf / padded_len(1 << log2My);
+  return tk < 1 ? 1 : (tk > 64 ? 64 : tk);
+}
+// blocks of one y-pass item: ceil((H + 1) / tk)
+inline int ypass_blocks(int log2Mx, int tk) { return ((1 << (log2Mx - 1)) + 1 + tk - 1) / tk; }
+
+// 2D products: tiles of the x-pass forward (y_in_hi blocks per item), the
+// y-pass (ypass_blocks) and the x-pass inverse (y_out_hi blocks).
 template <typename T>
-void launch_ypass(const YItem<T>* items, int n, int mode, int max_log2Mx, int max_log2My, int s,
-                  const Cx<T>* tw, cudaStream_t st);
+void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, Tiles xf, Tiles yp, Tiles xi,
+                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st);
 template <typename T>
-void launch_spec(const SpecItem<T>* items, int n, const YItem<T>* yitems, int ny, int max_log2Mx, int max_log2My,
-                 int max_ny, const Cx<T>* tw, cudaStream_t st);
+void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int s, const Cx<T>* tw,
+                  cudaStream_t st);
+// spectra: sx gives ny blocks per item, sy ypass_blocks per 2D item
+template <typename T>
+void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Tiles sy, int max_log2Mx,
+                 int max_log2My, const Cx<T>* tw, cudaStream_t st);
 
 }  // namespace ssa
