@@ -170,7 +170,7 @@ template <> const Cx<double>* twiddles<double>(int dev) { return g_tables[dev].t
 // small helper kernels of the driver
 __global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int max_restarts, int full) {
   st->full = full; st->sweeps = 0;
-  st->j0 = 0; st->k = k; st->r = r; st->kk = kk; st->active = 1; st->converged = 0;
+  st->jc = 0; st->svd_done = 0; st->k = k; st->r = r; st->kk = kk; st->active = 1; st->converged = 0;
   st->nconv = 0; st->breakdown = 0; st->restarts = 0; st->max_restarts = max_restarts;
   st->beta_k = 0.0; st->anorm = 0.0; st->tol = tol; st->sigma1 = 0.0; st->maxres = 0.0;
 }
@@ -889,11 +889,13 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   return SSA_OK;
 }
 
-// Lanczos engine: a set of problems (contexts with a workspace) that advance in
-// lock-step, one launch per kernel kind for all of them.  Members may be in
-// different restart cycles (each has its own j0), and members can be added
-// and retired between cycles -- the batched decomposition and the server use
-// the same engine.
+// Lanczos engine: a set of problems (contexts with a workspace) that advance
+// together, one launch per kernel kind for all of them.  Each member keeps its
+// own position (LzState::jc) in its own restart cycle: a chunk of steps moves
+// every member that is inside a cycle, the small SVD runs for the members
+// whose cycle just ended, and the host then retires or restarts exactly those.
+// Members can be added and removed between chunks -- the batched
+// decomposition and the server use the same engine.
 template <typename T>
 struct LzEngine {
   cudaStream_t st = nullptr;
@@ -901,7 +903,8 @@ struct LzEngine {
   std::vector<ssa_ctx*> live;
   std::vector<uint64_t> seed;
   std::vector<bool> fresh;        // not started yet (no start vector)
-  std::vector<LzState> hst;       // host copy after the last cycle
+  std::vector<LzState> hst;       // host copy after the last chunk (kept current for restarts)
+  bool dirty = true;              // membership changed since the item arrays were built
   // device item arrays for the current membership
   ShortItem* d_sh = nullptr; LongItem<T>* d_lg = nullptr; SvdItem* d_sv = nullptr;
   RitzItem<T>* d_rz = nullptr; LzState** d_stp = nullptr; LzState* d_stg = nullptr;
@@ -918,7 +921,13 @@ struct LzEngine {
 
   ~LzEngine() { release_items(); if (h_st) cudaFreeHost(h_st); }
 
+  std::vector<void*> chunk_tmp;   // per-restart item arrays, freed by the next chunk
+  void release_chunk() {
+    for (void* p : chunk_tmp) cudaFreeAsync(p, st);
+    chunk_tmp.clear();
+  }
   void release_items() {
+    release_chunk();
     for (void* p : dev_tmp) cudaFreeAsync(p, st);
     dev_tmp.clear();
     mvA = MvSet<T>(); mvAT = MvSet<T>();
@@ -990,11 +999,15 @@ struct LzEngine {
   void add(ssa_ctx* c, uint64_t sd) {
     live.push_back(c); seed.push_back(sd); fresh.push_back(true);
     LzState z{};
+    z.k = c->ws.k; z.kk = c->ws.kk; z.r = c->ws.r; z.jc = 0; z.active = 1;
     hst.push_back(z);
+    dirty = true;
   }
 
-  // rebuild the device item arrays for the current members
+  // rebuild the device item arrays for the current members (when they changed)
   int build() {
+    if (!dirty) return SSA_OK;
+    dirty = false;
     release_items();
     std::vector<ShortItem> sh; std::vector<LongItem<T>> lg; std::vector<SvdItem> sv;
     std::vector<RitzItem<T>> rz; std::vector<LzState*> stp;
@@ -1086,22 +1099,28 @@ struct LzEngine {
     return SSA_OK;
   }
 
-  // one restart cycle for every member (members that are done skip it), then
-  // the small SVDs and a read-back of every member's state
-  int run_cycle() {
+  // One chunk: every member inside a cycle advances up to `steps` Lanczos
+  // steps (its own jc); members whose cycle is complete get their small SVD;
+  // the states are read back.  The chunk runs until the member closest to the
+  // end of its cycle gets there (at least 8 steps when others have that many
+  // left), so no member waits for a whole cycle of another.
+  int run_chunk() {
+    release_chunk();
     const int nl = (int)live.size();
     if (!nl) return SSA_OK;
-    int steps = 0;
+    int rmin = INT32_MAX, rmax = 0;
     for (int i = 0; i < nl; ++i) {
-      const Workspace& w = live[i]->ws;
-      const int j0 = (hst[i].restarts == 0) ? 0 : w.kk;
-      steps = std::max(steps, w.k - j0);
+      const LzState& h = hst[i];
+      if (!h.active || h.svd_done || h.jc >= h.k) continue;
+      rmin = std::min(rmin, h.k - h.jc);
+      rmax = std::max(rmax, h.k - h.jc);
     }
+    const int steps = rmax == 0 ? 0 : std::min(rmax, std::max(rmin, 8));
     for (int s = 0; s < steps; ++s) {
-      run_mv<T>(live[0], mvA, s);
-      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, t_sh, nl, n_sh, s, st); }
-      run_mv<T>(live[0], mvAT, s);
-      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, s, st); }
+      run_mv<T>(live[0], mvA, 0);
+      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st); }
+      run_mv<T>(live[0], mvAT, 0);
+      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, 0, st); }
     }
     { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
     CU(cudaGetLastError());
@@ -1109,15 +1128,52 @@ struct LzEngine {
     CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
+    if (!mvA.items1.empty() && mv_async_timeouts(st) != 0)
+      return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
     return SSA_OK;
   }
+  bool any_active() const {
+    for (auto& h : hst) if (h.active) return true;
+    return false;
+  }
+  bool any_restart() const {
+    for (auto& h : hst) if (h.active && h.svd_done) return true;
+    return false;
+  }
 
-  // restart every member still active
+  // restart the members whose cycle ended without convergence (the kernels
+  // skip every other member); the host copies follow
   int restart_active() {
+    std::vector<ssa_ctx*> cs;
+    std::vector<RitzItem<T>> rz;
+    std::vector<SvdItem> sv;
+    int mk = 1;
+    for (size_t i = 0; i < live.size(); ++i)
+      if (hst[i].active && hst[i].svd_done) {
+        cs.push_back(live[i]);
+        rz.push_back(ritz_item(live[i]));
+        sv.push_back(svd_item(live[i]));
+        mk = std::max(mk, live[i]->ws.k);
+      }
+    if (cs.empty()) return SSA_OK;
+    RitzItem<T>* d_r = nullptr; SvdItem* d_v = nullptr;
+    int32_t *ts = nullptr, *tl = nullptr;
+    int ns = 0, nlg = 0;
+    if (cs.size() == live.size()) {        // everyone: the member-wide arrays
+      d_r = d_rz; d_v = d_sv; ts = t_rs; tl = t_rl; ns = n_rs; nlg = n_rl;
+    } else {
+      const size_t keep = dev_tmp.size();
+      TRY(up(rz, &d_r)); TRY(up(sv, &d_v));
+      TRY(ritz_tiles(cs, &ts, &ns, &tl, &nlg));
+      chunk_tmp.insert(chunk_tmp.end(), dev_tmp.begin() + keep, dev_tmp.end());
+      dev_tmp.resize(keep);
+    }
     PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_rz, (int)live.size(), max_k, t_rs, n_rs, t_rl, n_rl, 0, st);
-    launch_restart(d_sv, (int)live.size(), st);
+    launch_ritz<T>(d_r, (int)cs.size(), mk, ts, ns, tl, nlg, 0, st);
+    launch_restart(d_v, (int)cs.size(), st);
     CU(cudaGetLastError());
+    for (auto& h : hst)
+      if (h.active && h.svd_done) { h.jc = h.kk; h.svd_done = 0; }
     return SSA_OK;
   }
 
@@ -1161,6 +1217,7 @@ struct LzEngine {
     for (size_t i = 0; i < live.size(); ++i)
       if (!drop[i]) { l2.push_back(live[i]); s2.push_back(seed[i]); f2.push_back(fresh[i]); h2.push_back(hst[i]); }
     live.swap(l2); seed.swap(s2); fresh.swap(f2); hst.swap(h2);
+    if (!idx.empty()) dirty = true;
   }
 };
 
@@ -1215,11 +1272,8 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
   if (!eng.live.empty()) {
     TRY(eng.build());
     TRY(eng.start_fresh());
-    for (;;) {
-      TRY(eng.run_cycle());
-      bool any = false;
-      for (auto& h : eng.hst) any |= h.active != 0;
-      if (!any) break;
+    while (eng.any_active()) {
+      TRY(eng.run_chunk());
       TRY(eng.restart_active());
     }
     std::vector<int> all(eng.live.size());
@@ -1515,6 +1569,8 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
   CU(cudaGetLastError());
   if (!on_device) CU(cudaMemcpyAsync(out, dres, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
+  if (!s.items1.empty() && mv_async_timeouts(c->stream) != 0)
+    return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
   c->release(din); c->release(dparts);
   if (!on_device) { c->release(dd); c->release(dres); }
   if (g1) { c->release(g1); c->release(g2); }
@@ -2108,7 +2164,7 @@ int server_round(ssa_server* s, LzEngine<T>& eng, std::vector<SrvReq*>& live, st
   if (live.empty()) return SSA_OK;
   TRY(eng.build());
   TRY(eng.start_fresh());
-  TRY(eng.run_cycle());
+  TRY(eng.run_chunk());
   // retire what is done; restart the rest
   std::vector<int> done;
   for (size_t i = 0; i < eng.live.size(); ++i)

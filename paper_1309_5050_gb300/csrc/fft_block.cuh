@@ -169,11 +169,15 @@ __device__ __forceinline__ void stockham_stage_s(const Cx<T>* __restrict__ src, 
       v[r] = s[PIN ? padi(i) : i];
     }
     if (log2Ns > 0) {
+      // W^{k r} for r = 1..R-1 from one table value by products (a few
+      // roundings more than separate lookups, far fewer instructions)
+      Cx<T> w1 = tw_oct(tab, log2N, (int64_t)k << tshift);
+      if (INV) w1 = conj(w1);
+      Cx<T> w = w1;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        Cx<T> w = tw_oct(tab, log2N, ((int64_t)k * r) << tshift);
-        if (INV) w = conj(w);
         v[r] = v[r] * w;
+        if (r + 1 < R) w = w * w1;
       }
     }
     if (LR == 3) dft8<T, INV>(v);

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(SHORT_RB) k_short1(const ShortItem* __restrict
                                                      int n, int s) {
   int blk;
   const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
-  const int j = it.st->j0 + s;
+  const int j = it.st->jc + s;
   if (j < 0 || lz_skip(it.st, j)) return;
   __shared__ double pv[SHORT_RB];
   const int64_t r0 = (int64_t)blk * SHORT_RB;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restric
                                                       int n, int s) {
   int blk;
   const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
-  const int j = it.st->j0 + s;
+  const int j = it.st->jc + s;
   if (j < 0 || lz_skip(it.st, j)) return;
   __shared__ double c[KMAX + 1];
   __shared__ double pv[SHORT_RB];
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict
   int blk;
   const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
   LzState* st = it.st;
-  const int j = st->j0 + s;
+  const int j = st->jc + s;
   if (j < 0 || lz_skip(st, j)) return;
   __shared__ double alpha_s;
   if (threadIdx.x == 0) {
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_long1(const LongItem<T>* __restrict__ i
                                                int n, int s) {
   int blk;
   const LongItem<T> it = items[tile_item(tpre, n, blockIdx.x, blk)];
-  const int j = it.st->j0 + s;
+  const int j = it.st->jc + s;
   if (j < 0 || lz_skip(it.st, j)) return;
   __shared__ double red[32];
   // alpha_j v_j with v_j = colscale[j] * V[:, j] (stored unnormalised)
@@ -222,7 +222,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict__ items, int s) {
   const LongItem<T> it = items[blockIdx.x];
   LzState* st = it.st;
-  const int j = st->j0 + s;
+  const int j = st->jc + s;
   if (lz_skip(st, j)) return;
   __shared__ double red[32];
   double a = 0.0;
@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
     st->beta_k = 0.0;
     st->breakdown = 1;
   }
+  st->jc = j + 1;   // last kernel of the step: the next step of this problem
 }
 
 // ------------------------------------------------------------ small SVD
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
 __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
-  if (!st->active) return;
+  if (!st->active || st->jc < st->k || st->svd_done) return;   // only at the end of a cycle, once
   const int k = st->k, ld = it.ldb;
   const bool aug = st->full != 0;
   const int nc = aug ? k + 1 : k;       // columns of W
@@ -439,15 +440,17 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     st->nconv = nconv;
     st->converged = conv ? 1 : 0;
     st->restarts += 1;
+    st->svd_done = 1;
     if (conv || st->breakdown || st->restarts > st->max_restarts) st->active = 0;
   }
 }
 
-// B <- [diag(sigma_1..kk) | rho] with rho_i = beta_k P[k-1, i]; j0 <- kk
+// B <- [diag(sigma_1..kk) | rho] with rho_i = beta_k P[k-1, i]; jc <- kk.
+// Only problems whose cycle ended with a small SVD and go on.
 __global__ void k_restart(const SvdItem* __restrict__ items) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
-  if (!st->active) return;
+  if (!st->active || !st->svd_done) return;
   const int k = st->k, kk = st->kk, ld = it.ldb;
   for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
     const int c = e / ld, i = e - c * ld;
@@ -462,7 +465,8 @@ __global__ void k_restart(const SvdItem* __restrict__ items) {
   __syncthreads();
   if (threadIdx.x == 0) {
     it.colscale[kk] = it.colscale[k];
-    st->j0 = kk;
+    st->jc = kk;
+    st->svd_done = 0;
   }
 }
 
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   int rblk;
   const RitzItem<T> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
   const LzState* st = it.st;
-  if (!final_pass && !st->active) return;
+  if (!final_pass && (!st->active || !st->svd_done)) return;
   const int k = st->k;
   const int kk = final_pass ? min(st->r, k) : st->kk;
   const bool move = !SHORT && !final_pass;

@@ -14,6 +14,7 @@
 #include "fft_block.cuh"
 #include "kernels.cuh"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace ssa {
 
@@ -50,7 +51,7 @@ __device__ void load_col(T* rb, int Mx, const TI* __restrict__ in, const MapDev&
 template <typename T>
 __device__ __forceinline__ T in_scale_of(const MvItem<T>& it, int s) {
   if (!it.in_scale || !it.in.st) return T(1);
-  return (T)it.in_scale[it.in.st->j0 + s + it.in.jdelta];
+  return (T)it.in_scale[it.in.st->jc + s + it.in.jdelta];
 }
 
 // Write the map's positions of grid column y from rb into a compact vector.
@@ -77,25 +78,30 @@ __device__ void store_col(const T* rb, TO* __restrict__ out, const MapDev& m, in
 
 template <typename T>
 __device__ __forceinline__ bool item_skip(const LzState* st, int s) {
-  return st && (!st->active || st->j0 + s >= st->k || st->j0 + s < 0);
+  return st && (!st->active || st->jc + s >= st->k || st->jc + s < 0);
 }
 
 // x-pass shared layout: two padded complex buffers (padded_len(H) >= H+1),
-// the octant twiddle table of W_H (the FFT's), then scan scratch.  The
-// untwist / twist factors W_{2H}^k are read once per element from the global
-// table, which keeps the footprint at three CTAs per SM for H = 4096.
+// the octant twiddle table of W_{2H} (it serves the length-H FFT, whose
+// twiddles are the even powers, and the untwist / twist factors W_{2H}^k),
+// optionally a 16-byte aligned staging buffer for the H+1 spectrum values,
+// then scan scratch.
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
 template <typename T>
 struct XSmem {
-  Cx<T>* A; Cx<T>* B; Cx<T>* tab; int32_t* pre; int32_t* wt;
+  Cx<T>* A; Cx<T>* B; Cx<T>* tab; Cx<T>* S; int32_t* pre; int32_t* wt;
   int log2H;
-  const Cx<T>* tw;
-  __device__ XSmem(unsigned char* p, int H, int log2M_, const Cx<T>* tw_) : log2H(log2M_ - 1), tw(tw_) {
+  __device__ XSmem(unsigned char* p, int H, int log2M_, const Cx<T>* tw, bool spec = false) : log2H(log2M_ - 1) {
     A = reinterpret_cast<Cx<T>*>(p);
     B = A + padded_len(H);
     tab = B + padded_len(H);
-    pre = reinterpret_cast<int32_t*>(tab + (H >> 3) + 1);
+    size_t off = align16((size_t)(2 * padded_len(H) + (H >> 2) + 1) * sizeof(Cx<T>));
+    S = reinterpret_cast<Cx<T>*>(p + off);
+    if (spec) off += align16((size_t)(H + 1) * sizeof(Cx<T>));
+    pre = reinterpret_cast<int32_t*>(p + off);
     wt = pre + ((2 * H) / 32 + 1);
-    load_octant(tab, log2H, tw);
+    load_octant(tab, log2H + 1, tw);
   }
 };
 
@@ -105,9 +111,9 @@ template <typename T>
 __device__ Cx<T>* xpass_forward(XSmem<T>& sm, int log2H) {
   const int H = 1 << log2H;
   __syncthreads();
-  Cx<T>* Z = block_fft_s<T, false>(sm.A, sm.B, log2H, 1, sm.tab, sm.log2H);
+  Cx<T>* Z = block_fft_s<T, false>(sm.A, sm.B, log2H, 1, sm.tab, log2H + 1);
   Cx<T>* G = (Z == sm.A) ? sm.B : sm.A;
-  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd(Z, k, log2H, sm.tw);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd_s(Z, k, log2H, sm.tab);
   __syncthreads();
   return G;
 }
@@ -118,29 +124,46 @@ template <typename T>
 __device__ T* xpass_inverse(XSmem<T>& sm, Cx<T>* P, int log2H) {
   const int H = 1 << log2H;
   Cx<T>* Q = (P == sm.A) ? sm.B : sm.A;
-  for (int k = threadIdx.x; k < H; k += blockDim.x) Q[k] = twist_inv(P, k, log2H, sm.tw);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) Q[k] = twist_inv_s(P, k, log2H, sm.tab);
   __syncthreads();
-  Cx<T>* R = block_fft_s<T, true>(Q, P, log2H, 1, sm.tab, sm.log2H);
+  Cx<T>* R = block_fft_s<T, true>(Q, P, log2H, 1, sm.tab, log2H + 1);
   return reinterpret_cast<T*>(R);
 }
 
+// Polls of a bulk-copy wait before the kernel gives up and flags it.
+constexpr int MBAR_POLL_LIMIT = 1 << 22;
+__device__ int g_mv_async_timeouts;
+
 // ---------------------------------------------------------------- kernels
+// Series product, one CTA per (problem, channel): the data spectrum (H+1
+// values, contiguous) is brought into shared memory by one bulk copy issued
+// at entry, which lands while the input is loaded and transformed.
 template <typename T>
 __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ items, int s,
                                               const Cx<T>* __restrict__ tw) {
   const MvItem<T> it = items[blockIdx.x];
   if (item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
-  XSmem<T> sm(smem, H, it.log2Mx, tw);
+  XSmem<T> sm(smem, H, it.log2Mx, tw, true);
+  // H complex values = a multiple of 16 bytes; the last value comes by a plain load
+  const uint32_t bulk = (uint32_t)(H * sizeof(Cx<T>));
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    bulk_load(sm.S, it.xh, bulk, &bar);
+  }
+  const Cx<T> last = it.xh[H];
   const int64_t ioff = vec_elem_off(it.in, s);
   const T isc = in_scale_of(it, s);
   if (it.in_type == 1)
     load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
   else
     load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
-  Cx<T>* G = xpass_forward(sm, log2H);
-  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = it.xh[k] * conj(G[k]);
+  Cx<T>* G = xpass_forward(sm, log2H);   // its barriers order the init before any wait
+  if (!mbar_wait_bounded(&bar, 0, MBAR_POLL_LIMIT) && threadIdx.x == 0) atomicAdd(&g_mv_async_timeouts, 1);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) G[k] = sm.S[k] * conj(G[k]);
+  if (threadIdx.x == 0) G[H] = last * conj(G[H]);
   __syncthreads();
   T* r = xpass_inverse(sm, G, log2H);
   __syncthreads();
@@ -277,18 +300,26 @@ __global__ void __launch_bounds__(512) k_spec_x(const SpecItem<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------- launchers
-static inline size_t xsmem_bytes(int log2Mx, size_t csz) {
+static inline size_t xsmem_bytes(int log2Mx, size_t csz, bool spec = false) {
   const size_t H = size_t(1) << (log2Mx - 1);
-  return (2 * (size_t)padded_len((int)H) + H / 8 + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
+  return align16((2 * (size_t)padded_len((int)H) + H / 4 + 1) * csz) + (spec ? align16((H + 1) * csz) : 0) +
+         ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
 }
 
-template <typename T>
-int ypass_buf_elems() { return (64 * 1024) / (int)sizeof(Cx<T>); }
+// Bulk-copy waits that gave up since the last call (read and reset).
+int mv_async_timeouts(cudaStream_t st) {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_mv_async_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbolAsync(g_mv_async_timeouts, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  return h;
+}
 
 template <typename T>
 void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st) {
   if (n <= 0) return;
-  size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
+  size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>), true);
   set_max_smem((const void*)k_mv1d<T>);
   k_mv1d<T><<<n, 512, sm, st>>>(items, s, tw); count_launch();
 }
@@ -309,7 +340,7 @@ template <typename T>
 void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int s, const Cx<T>* tw,
                   cudaStream_t st) {
   if (tl.total <= 0) return;
-  const int buf = ypass_buf_elems<T>();
+  const int buf = ypass_buf<T>(max_log2My);
   const int N = 1 << (max_log2My < 3 ? 3 : max_log2My);
   const size_t sm = (2 * (size_t)buf + N / 8 + 1) * sizeof(Cx<T>);
   set_max_smem((const void*)k_ypass<T>);

@@ -50,7 +50,7 @@ struct RSmem {
     B = A + padded_len(H);
     C = B + padded_len(H);
     tab = C + padded_len(H);
-    pre = reinterpret_cast<int32_t*>(tab + (H >> 3) + 1);
+    pre = reinterpret_cast<int32_t*>(tab + (H >> 2) + 1);   // octant table of W_{2H}
     wt = pre + ((2 * H) / 32 + 1);
   }
 };
@@ -59,9 +59,9 @@ template <typename T>
 __device__ Cx<T>* rec_forward(Cx<T>* A, Cx<T>* B, int log2H, const Cx<T>* tab, const Cx<T>* tw) {
   const int H = 1 << log2H;
   __syncthreads();
-  Cx<T>* Z = block_fft_s<T, false>(A, B, log2H, 1, tab, log2H);
+  Cx<T>* Z = block_fft_s<T, false>(A, B, log2H, 1, tab, log2H + 1);
   Cx<T>* G = (Z == A) ? B : A;
-  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd(Z, k, log2H, tw);
+  for (int k = threadIdx.x; k <= H; k += blockDim.x) G[k] = untwist_fwd_s(Z, k, log2H, tab);
   __syncthreads();
   return G;
 }
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(512) k_rec_col_fft(const RecColItem<T, TV>* __
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
   RSmem<T> sm(smem, H);
-  load_octant(sm.tab, it.log2Mx - 1, tw);
+  load_octant(sm.tab, it.log2Mx, tw);
   rec_load_col<T, TV>(reinterpret_cast<T*>(sm.A), 2 * H, it.vec, it.map, y, sm.pre, sm.wt);
   Cx<T>* G = rec_forward(sm.A, sm.B, log2H, sm.tab, tw);
   Cx<T>* dst = it.dst + (int64_t)y * (H + 1);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T, TV>* __restrict
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
   RSmem<T> sm(smem, H);
-  load_octant(sm.tab, it.log2Mx - 1, tw);
+  load_octant(sm.tab, it.log2Mx, tw);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = cx(T(0), T(0));
   __syncthreads();   // an empty group reads C right away below
   for (int c = 0; c < it.ncomp; ++c) {
@@ -104,9 +104,9 @@ __global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T, TV>* __restrict
     __syncthreads();
   }
   // inverse of the accumulated half spectrum (C), into A/C ping-pong
-  for (int k = threadIdx.x; k < H; k += blockDim.x) sm.A[k] = twist_inv(sm.C, k, log2H, tw);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) sm.A[k] = twist_inv_s(sm.C, k, log2H, sm.tab);
   __syncthreads();
-  Cx<T>* R = block_fft_s<T, true>(sm.A, sm.B, log2H, 1, sm.tab, log2H);
+  Cx<T>* R = block_fft_s<T, true>(sm.A, sm.B, log2H, 1, sm.tab, log2H + 1);
   const T* r = reinterpret_cast<const T*>(R);
   for (int n = threadIdx.x; n < it.n; n += blockDim.x) {
     const int w = it.w[n];
@@ -123,13 +123,13 @@ __global__ void __launch_bounds__(512) k_rec_xinv(const Rec2Item<T>* __restrict_
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2Mx - 1, H = 1 << log2H;
   RSmem<T> sm(smem, H);
-  load_octant(sm.tab, it.log2Mx - 1, tw);
+  load_octant(sm.tab, it.log2Mx, tw);
   const Cx<T>* src = it.g2 + (int64_t)y * (H + 1);
   for (int k = threadIdx.x; k <= H; k += blockDim.x) sm.C[k] = src[k];
   __syncthreads();
-  for (int k = threadIdx.x; k < H; k += blockDim.x) sm.A[k] = twist_inv(sm.C, k, log2H, tw);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) sm.A[k] = twist_inv_s(sm.C, k, log2H, sm.tab);
   __syncthreads();
-  Cx<T>* R = block_fft_s<T, true>(sm.A, sm.B, log2H, 1, sm.tab, log2H);
+  Cx<T>* R = block_fft_s<T, true>(sm.A, sm.B, log2H, 1, sm.tab, log2H + 1);
   const T* r = reinterpret_cast<const T*>(R);
   for (int x = threadIdx.x; x < it.nx; x += blockDim.x) {
     const int64_t g = x + (int64_t)it.nx * y;
@@ -193,7 +193,7 @@ void launch_residual_batch(const ResItem* items, int n, int64_t max_n, cudaStrea
 // ---------------------------------------------------------------- launchers
 static inline size_t rsmem_bytes(int log2Mx, size_t csz) {
   const size_t H = size_t(1) << (log2Mx - 1);
-  return (3 * (size_t)padded_len((int)H) + H / 8 + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
+  return (3 * (size_t)padded_len((int)H) + H / 4 + 1) * csz + ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
 }
 
 template <typename T, typename TV>

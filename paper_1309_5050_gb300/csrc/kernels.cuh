@@ -6,7 +6,8 @@ namespace ssa {
 
 // Per-problem Lanczos state kept in device memory.
 struct LzState {
-  int32_t j0;         // first step of the current cycle (0, or kk after a restart)
+  int32_t jc;         // next Lanczos step of the current cycle (from 0, or kk after a restart);
+                      // the cycle is complete when jc reaches k
   int32_t k;          // Krylov dimension
   int32_t r;          // wanted rank
   int32_t kk;         // vectors kept on restart
@@ -18,6 +19,7 @@ struct LzState {
   int32_t max_restarts;
   int32_t full;       // k equals min(L, K): one cycle spans the whole space
   int32_t sweeps;     // Jacobi sweeps of the last small SVD
+  int32_t svd_done;   // the small SVD of the completed cycle has run (cleared by a restart)
   double beta_k;      // coupling to the (k+1)-th long vector after k steps
   double anorm;       // largest Lanczos coefficient seen (scale for breakdown)
   double tol;         // residual tolerance relative to sigma_1
@@ -25,7 +27,7 @@ struct LzState {
   double maxres;      // largest relative residual among the r wanted
 };
 
-// A compact vector, possibly column (j0 + s + jdelta) of a basis.
+// A compact vector, possibly column (jc + s + jdelta) of a basis.
 struct VecRef {
   void* base;
   int64_t off;              // element offset (channel slice or partial row)
@@ -37,7 +39,7 @@ struct VecRef {
 
 __device__ __forceinline__ int64_t vec_elem_off(const VecRef& v, int s) {
   int64_t o = v.off;
-  if (v.st) o += (int64_t)(v.st->j0 + s + v.jdelta) * v.ld;
+  if (v.st) o += (int64_t)(v.st->jc + s + v.jdelta) * v.ld;
   return o;
 }
 

@@ -27,13 +27,26 @@ template <typename T> const Cx<T>* twiddles(int device);
 // matvec / spectrum
 template <typename T>
 void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st);
-// y-pass tile width: x-frequencies per block for a y-FFT of 2^log2My points,
-// from the block's two 64 KB buffers, at most 64.
+// Bulk-copy waits in the series product that gave up since the last call
+// (each sets a device counter instead of spinning on); read and reset, -1 on
+// a CUDA error.  Synchronises the stream.
+int mv_async_timeouts(cudaStream_t st);
+
+// y-pass blocks stage tk x-frequencies (all My rows) in two buffers of
+// YPASS_BUF_BYTES (grown to one padded column where a column is larger), so
+// three blocks fit an SM.  tk: x-frequencies per block, 1..64.
+constexpr int YPASS_BUF_BYTES = 36 * 1024;
 template <typename T>
 inline int ypass_tk(int log2My) {
-  const int buf = (64 * 1024) / (int)sizeof(Cx<T>);
+  const int buf = YPASS_BUF_BYTES / (int)sizeof(Cx<T>);
   int tk = buf / padded_len(1 << log2My);
   return tk < 1 ? 1 : (tk > 64 ? 64 : tk);
+}
+// buffer elements of a y-pass launch whose largest grid has 2^max_log2My rows
+template <typename T>
+inline int ypass_buf(int max_log2My) {
+  const int b = YPASS_BUF_BYTES / (int)sizeof(Cx<T>), c = padded_len(1 << max_log2My);
+  return b > c ? b : c;
 }
 // blocks of one y-pass item: ceil((H + 1) / tk)
 inline int ypass_blocks(int log2Mx, int tk) { return ((1 << (log2Mx - 1)) + 1 + tk - 1) / tk; }
