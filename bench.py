@@ -206,16 +206,27 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
             "phases_ms": {k: v[0] for k, v in prof.items()}}
 
 
+def _probe_info(pkg, probs, cfg, stream, args):
+    """Krylov dimension the library uses for one problem of the workload."""
+    lens, flat = probs[0]
+    p = pkg.SSA.multi_concat(flat, lens, cfg["L"], stream=stream)
+    p.decompose(cfg["rank"], args.prec, krylov_dim=args.krylov_dim)
+    info = p.info()
+    p.close()
+    return info
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=304)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--krylov-dim", type=int, default=0, help="0: the library default min(2r+16, 112, min(L,K))")
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=1000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
@@ -278,9 +289,12 @@ def main():
     host_outs = [torch.empty(int(l.sum()) * nout, dtype=torch.float64).pin_memory() for l, _ in probs]
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    restarts = []
+
     def step(inputs, outs, prec):
         ps = pkg.embed_multi_batch(inputs, [l for l, _ in probs], CFG["L"], stream=stream)
-        pkg.decompose_batch(ps, CFG["rank"], prec)
+        pkg.decompose_batch(ps, CFG["rank"], prec, krylov_dim=args.krylov_dim)
+        restarts.append(ps[0].info()["restarts"])
         if outs[0].is_cuda:
             pkg.reconstruct_batch(ps, GROUPS, residual=True, outs=outs)
         else:
@@ -323,6 +337,7 @@ def main():
     _lib.profile_enable(False)
     clocks = ck.summary()
 
+    ps_info = _probe_info(pkg, probs, CFG, stream, args)
     ms = sum(ts) / len(ts)
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -391,6 +406,7 @@ def main():
                 "e2e": {"value": world * B / (ms_e2e / 1000.0), "unit": "decomps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
                 "gpu_launches": int(launches),
+                "lanczos": {"krylov_dim": ps_info["krylov_dim"], "restarts_first_problem": restarts[-1]},
                 "phases_ms": {k: v[0] / args.steps for k, v in prof.items()},
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

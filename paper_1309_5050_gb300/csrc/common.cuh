@@ -77,5 +77,6 @@ __device__ __forceinline__ int tile_item(const int32_t* __restrict__ pre, int n,
 enum : int { DEV_OK = 0, DEV_BAD_INPUT = 1 };
 
 __device__ __forceinline__ int ilog2(int n) { return 31 - __clz(n); }
+__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 }  // namespace ssa

@@ -233,6 +233,72 @@ __device__ Cx<T>* block_fft_s(Cx<T>* a, Cx<T>* b, int log2n, int nb, const Cx<T>
   return a;
 }
 
+// One radix-2^LR Stockham stage of a single transform (nb = 1) whose input
+// element i comes from in(i) and whose output element i goes to out(i, v):
+// the first stage can read global memory and the last one write it directly.
+template <typename T, bool INV, int LR, class In, class Out>
+__device__ __forceinline__ void stage_io(In& in, Out& out, int log2n, int log2Ns, const Cx<T>* tab, int log2N) {
+  constexpr int R = 1 << LR;
+  const int nq = (1 << log2n) >> LR;
+  const int Ns = 1 << log2Ns;
+  const int tshift = log2N - (log2Ns + LR);
+  for (int j = threadIdx.x; j < nq; j += blockDim.x) {
+    const int k = j & (Ns - 1);
+    Cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in(j + r * nq);
+    if (log2Ns > 0) {
+      Cx<T> w1 = tw_oct(tab, log2N, (int64_t)k << tshift);
+      if (INV) w1 = conj(w1);
+      Cx<T> w = w1;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        v[r] = v[r] * w;
+        if (r + 1 < R) w = w * w1;
+      }
+    }
+    if (LR == 3) dft8<T, INV>(v);
+    else if (LR == 2) dft4<T, INV>(v[0], v[1], v[2], v[3]);
+    else dft2<T, INV>(v[0], v[1]);
+    const int base = ((j - k) << LR) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(base + r * Ns, v[r]);
+  }
+}
+
+// Stages of one transform of length 2^log2n: the first reads in(i), the last
+// writes out(i, v), the ones between ping-pong through the padded buffers
+// (the first stage writes b).  A barrier follows every stage.
+template <typename T, bool INV, class In, class Out>
+__device__ void block_fft_io(In in, Out out, Cx<T>* a, Cx<T>* b, int log2n, const Cx<T>* tab, int log2N) {
+  int done = 0;
+  bool first = true;
+  while (done < log2n) {
+    const int rem = log2n - done;
+    const int lr = rem >= 3 ? 3 : rem;
+    const bool last = (done + lr == log2n);
+    Cx<T>* src = a;
+    Cx<T>* dst = b;
+    auto rd = [src](int i) { return src[padi(i)]; };
+    auto wr = [dst](int i, Cx<T> v) { dst[padi(i)] = v; };
+#define SSA_IO(LRV)                                                           \
+  if (first && last) stage_io<T, INV, LRV>(in, out, log2n, done, tab, log2N); \
+  else if (first) stage_io<T, INV, LRV>(in, wr, log2n, done, tab, log2N);     \
+  else if (last) stage_io<T, INV, LRV>(rd, out, log2n, done, tab, log2N);     \
+  else stage_io<T, INV, LRV>(rd, wr, log2n, done, tab, log2N);
+    if (lr == 3) { SSA_IO(3) } else if (lr == 2) { SSA_IO(2) } else { SSA_IO(1) }
+#undef SSA_IO
+    done += lr;
+    first = false;
+    __syncthreads();
+    a = dst;
+    b = src;
+  }
+}
+
+// number of stages block_fft_io runs for length 2^log2n
+__host__ __device__ __forceinline__ int fft_io_stages(int log2n) { return (log2n + 2) / 3; }
+
 template <typename T>
 __device__ __forceinline__ Cx<T> untwist_fwd_s(const Cx<T>* Z, int k, int log2H, const Cx<T>* tab) {
   const int H = 1 << log2H;

@@ -11,7 +11,6 @@
 
 namespace ssa {
 
-__device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

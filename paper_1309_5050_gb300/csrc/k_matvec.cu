@@ -135,9 +135,15 @@ constexpr int MBAR_POLL_LIMIT = 1 << 22;
 __device__ int g_mv_async_timeouts;
 
 // ---------------------------------------------------------------- kernels
-// Series product, one CTA per (problem, channel): the data spectrum (H+1
-// values, contiguous) is brought into shared memory by one bulk copy issued
-// at entry, which lands while the input is loaded and transformed.
+// Series product, one CTA per (problem, channel):
+//  * the data spectrum (H+1 values, contiguous) is brought into shared memory
+//    by one bulk copy issued at entry, which lands during the forward FFT;
+//  * the first forward stage reads the input column straight from global
+//    memory (dense maps; a bit-mapped input is staged by load_col);
+//  * untwist, product with the spectrum and twist run as one pass over the
+//    pairs (k, H-k);
+//  * the last inverse stage writes the output column straight to global
+//    memory (dense maps; else through store_col).
 template <typename T>
 __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ items, int s,
                                               const Cx<T>* __restrict__ tw) {
@@ -156,18 +162,70 @@ __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ item
   const Cx<T> last = it.xh[H];
   const int64_t ioff = vec_elem_off(it.in, s);
   const T isc = in_scale_of(it, s);
-  if (it.in_type == 1)
-    load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
-  else
-    load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
-  Cx<T>* G = xpass_forward(sm, log2H);   // its barriers order the init before any wait
+  const int nst = fft_io_stages(log2H);
+  Cx<T>* Z = (nst & 1) ? sm.B : sm.A;   // forward result (written by the last stage)
+  Cx<T>* X = (nst & 1) ? sm.A : sm.B;   // the other buffer: twisted product
+  auto zout = [Z](int i, Cx<T> v) { Z[i] = v; };
+  if (it.min.dense) {
+    const int64_t xe = imin64((int64_t)it.min.bx, it.min.limit);
+    __syncthreads();                    // twiddle table
+    if (it.in_type == 1) {
+      const double* src = (const double*)it.in.base + ioff;
+      auto in = [src, xe, isc](int i) {
+        const int64_t x = 2 * (int64_t)i;
+        return cx(x < xe ? (T)src[x] * isc : T(0), x + 1 < xe ? (T)src[x + 1] * isc : T(0));
+      };
+      block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
+    } else {
+      const T* src = (const T*)it.in.base + ioff;
+      auto in = [src, xe, isc](int i) {
+        const int64_t x = 2 * (int64_t)i;
+        return cx(x < xe ? src[x] * isc : T(0), x + 1 < xe ? src[x + 1] * isc : T(0));
+      };
+      block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
+    }
+  } else {
+    if (it.in_type == 1)
+      load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
+    else
+      load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
+    __syncthreads();
+    const Cx<T>* A = sm.A;
+    auto in = [A](int i) { return A[i]; };
+    block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
+  }
   if (!mbar_wait_bounded(&bar, 0, MBAR_POLL_LIMIT) && threadIdx.x == 0) atomicAdd(&g_mv_async_timeouts, 1);
-  for (int k = threadIdx.x; k < H; k += blockDim.x) G[k] = sm.S[k] * conj(G[k]);
-  if (threadIdx.x == 0) G[H] = last * conj(G[H]);
+  // G = untwist(Z); P = S conj(G); Q = twist(P), over the pairs (k, H - k)
+  for (int k = threadIdx.x; k <= (H >> 1); k += blockDim.x) {
+    const int k2 = H - k;
+    const Cx<T> za = Z[k], zb = Z[k2 & (H - 1)];
+    const Cx<T> w = tw_oct(sm.tab, log2H + 1, k);      // W_2H^k
+    const Cx<T> w2 = cx(-w.re, w.im);                    // W_2H^(H-k) = -conj(W_2H^k)
+    const Cx<T> g1 = T(0.5) * (za + conj(zb)) + w * (T(0.5) * mul_mi(za - conj(zb)));
+    const Cx<T> g2 = T(0.5) * (zb + conj(za)) + w2 * (T(0.5) * mul_mi(zb - conj(za)));
+    const Cx<T> p1 = sm.S[k] * conj(g1);
+    const Cx<T> p2 = (k == 0 ? last : sm.S[k2]) * conj(g2);
+    X[k] = (p1 + conj(p2)) + mul_pi(conj(w) * (p1 - conj(p2)));
+    if (k != 0 && k2 != k) X[k2] = (p2 + conj(p1)) + mul_pi(conj(w2) * (p2 - conj(p1)));
+  }
   __syncthreads();
-  T* r = xpass_inverse(sm, G, log2H);
-  __syncthreads();
-  store_col<T, T>(r, (T*)it.out.base + vec_elem_off(it.out, s), it.mout, 0, sm.pre, sm.wt);
+  const Cx<T>* Xc = X;
+  auto qin = [Xc](int i) { return Xc[i]; };
+  T* o = (T*)it.out.base + vec_elem_off(it.out, s);
+  if (it.mout.dense) {
+    const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
+    auto st = [o, xe](int i, Cx<T> v) {
+      const int64_t x = 2 * (int64_t)i;
+      if (x < xe) o[x] = v.re;
+      if (x + 1 < xe) o[x + 1] = v.im;
+    };
+    block_fft_io<T, true>(qin, st, X, Z, log2H, sm.tab, log2H + 1);
+  } else {
+    Cx<T>* R = (nst & 1) ? Z : X;
+    auto rout = [R](int i, Cx<T> v) { R[i] = v; };
+    block_fft_io<T, true>(qin, rout, X, Z, log2H, sm.tab, log2H + 1);
+    store_col<T, T>(reinterpret_cast<const T*>(R), o, it.mout, 0, sm.pre, sm.wt);
+  }
 }
 
 template <typename T>

@@ -59,6 +59,21 @@ def case_1d(n, L, seed):
     return pkg.SSA.series(x, L), O.Problem.series(x, L), x
 
 
+def case_1d_gaps(n, L, seed, gaps):
+    """A series with missing stretches: the origin set has holes (bit-mapped)."""
+    x = noisy_series(n, seed)
+    for a, b in gaps:
+        x[a:b] = np.nan
+    return pkg.SSA.series(x, L), O.Problem.series(x, L), x
+
+
+def case_mssa_gaps(lengths, L, seed):
+    xs = [noisy_series(n, seed + i) for i, n in enumerate(lengths)]
+    xs[1][7:9] = np.nan
+    xs32 = [np.asarray(v, np.float32).astype(np.float64) for v in xs]
+    return pkg.SSA.multi(xs, L), O.Problem.multi(xs32, L), xs32
+
+
 def case_mssa(lengths, L, seed):
     xs = [noisy_series(n, seed + i) for i, n in enumerate(lengths)]
     xs32 = [np.asarray(v, np.float32).astype(np.float64) for v in xs]
@@ -85,6 +100,8 @@ SMALL = [
     ("1d_1000_500", lambda: case_1d(1000, 500, 2)),
     ("1d_1000_700_swapped", lambda: case_1d(1000, 700, 3)),
     ("1d_4097_1500", lambda: case_1d(4097, 1500, 4)),
+    ("1d_gaps_600_80", lambda: case_1d_gaps(600, 80, 11, [(130, 133), (400, 401)])),
+    ("mssa_3x_gaps", lambda: case_mssa_gaps([120, 173, 161], 30, 12)),
     ("mssa_3x_ragged", lambda: case_mssa([50, 73, 61], 20, 5)),
     ("mssa_5x_300_700", lambda: case_mssa([300, 701, 455, 512, 333], 100, 6)),
     ("2d_30x27_w7x5", lambda: case_2d(30, 27, 7, 5, 7)),
