@@ -302,6 +302,7 @@ struct Workspace {             // Lanczos + results, per precision
   int n_part_s = 1, n_part_l = 1;
   double* B = nullptr; double* P = nullptr; double* Q = nullptr; double* sig = nullptr;
   double* colscale = nullptr;
+  void* Cs = nullptr;          // scaled long-side Ritz coefficients, (k + 2) x ritz_ldcs(k) of T
   double* cpa = nullptr; double* cpb = nullptr; double* np_s = nullptr; double* np_l = nullptr;
   void* g1 = nullptr; void* g2 = nullptr;
   void* Uo = nullptr; void* Vo = nullptr;
@@ -844,7 +845,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
                   rnd256(cz * w.Kl) + rnd256(cz * w.Ls * w.n_part_s) + rnd256(cz * w.Kl * w.n_part_l) +
                   3 * rnd256(8 * k1 * k1) + 2 * rnd256(8 * (k1 + 1)) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
                   rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)w.nblk_l) + rnd256(cz * c->L * w.r) +
-                  rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r);
+                  rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r) + rnd256(cz * (k1 + 1) * ritz_ldcs(w.k));
     if (c->log2My > 0) {
       const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
       need += 2 * rnd256(2 * cz * hs * c->ch.size());
@@ -865,6 +866,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->allocT(&w.Q, (size_t)(w.k + 1) * w.k));
   TRY(c->allocT(&w.sig, (size_t)w.k));
   TRY(c->allocT(&w.colscale, (size_t)w.k + 2));
+  TRY(c->alloc(&w.Cs, sizeof(T) * (k1 + 1) * ritz_ldcs(w.k)));
   TRY(c->allocT(&w.cpa, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.cpb, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.np_s, (size_t)w.nblk_s));
@@ -984,7 +986,7 @@ struct LzEngine {
     Workspace& w = c->ws;
     RitzItem<T> z;
     z.st = w.st; z.U = w.U; z.ldu = w.Ls; z.Ls = w.Ls; z.V = (T*)w.V; z.ldv = w.Kl; z.Kl = w.Kl;
-    z.colscale = w.colscale; z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.pad_ = 0;
+    z.colscale = w.colscale; z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.ldcs = ritz_ldcs(w.k); z.Cs = (T*)w.Cs;
     return z;
   }
   FinalItem<T> final_item(ssa_ctx* c) {

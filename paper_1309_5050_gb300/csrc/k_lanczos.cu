@@ -470,19 +470,49 @@ __global__ void k_restart(const SvdItem* __restrict__ items) {
 }
 
 // ------------------------------------------------------------ Ritz vectors
+// Long-side coefficients for one restart (or the final pass): Cs[i, c] =
+// Q[i, c] * colscale[i] in T (the long basis is stored unnormalised), zero
+// for c >= kk; one block per problem.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ritz_coef(const RitzItem<T>* __restrict__ items, int final_pass) {
+  const RitzItem<T> it = items[blockIdx.x];
+  const LzState* st = it.st;
+  if (!final_pass && (!st->active || !st->svd_done)) return;
+  const int k = st->k;
+  const int kk = final_pass ? min(st->r, k) : st->kk;
+  const int kc = k + 1, cld = it.ldc + 1, ld = it.ldcs;
+  for (int e = threadIdx.x; e < kc * ld; e += blockDim.x) {
+    const int i = e / ld, c = e - i * ld;
+    it.Cs[e] = (c < kk) ? (T)(it.Q[i + (int64_t)cld * c] * it.colscale[i]) : T(0);
+  }
+}
+
+template <typename E>
+__device__ __forceinline__ void lds4(const E* p, E* v) {
+  if (sizeof(E) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = (E)q.x; v[1] = (E)q.y; v[2] = (E)q.z; v[3] = (E)q.w;
+  } else {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = (E)q0.x; v[1] = (E)q0.y; v[2] = (E)q1.x; v[3] = (E)q1.y;
+  }
+}
+
 // In place, by row blocks: basis[:, 0:kk] <- basis[:, 0:kc] C[0:kc, 0:kk]
 // (kc = k on the short side, k + 1 on the long side, whose coefficients carry
 // the extra row of the complete-basis case); on a restart the long basis also
-// moves column k to column kk.  A CTA stages its RB rows and the coefficients
-// in shared memory; thread (tx, ty) of 8 x 32 accumulates rows ty + 32a and
-// columns tx + 8m (a < RB/32, m < 8) in registers, so every shared load feeds
-// several FMAs and each warp writes 32 consecutive rows of a column.
+// moves column k to column kk.  A block stages its RB rows of every column and
+// the coefficients in shared memory; thread (rg, cg) accumulates a 4 x 4 tile
+// (rows 4 rg.., columns 4 cg..) from 16-byte shared loads, and a warp writes
+// 128 consecutive rows of a column.
 template <typename T, bool SHORT>
 __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, const int32_t* __restrict__ tpre,
                                               int n, int final_pass) {
   typedef typename std::conditional<SHORT, double, T>::type E;
-  constexpr int RB = (sizeof(E) == 8) ? 64 : 128;
-  constexpr int RA = RB / 32;
+  constexpr int RB = RITZ_RB<E>();
+  constexpr int RG = RB / 4;          // row groups
+  constexpr int CP = (256 / RG) * 4;  // columns per pass
   int rblk;
   const RitzItem<T> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
   const LzState* st = it.st;
@@ -493,56 +523,57 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   E* basis = SHORT ? (E*)it.U : (E*)it.V;
   const int64_t ldb = SHORT ? it.ldu : it.ldv;
   const int64_t nrow = SHORT ? it.Ls : it.Kl;
-  const double* C = SHORT ? it.P : it.Q;
   const int kc = SHORT ? k : k + 1;
-  const int cld = SHORT ? it.ldc : it.ldc + 1;
   const int64_t r0 = (int64_t)rblk * RB;
   if (r0 >= nrow) return;
   const int nr = (int)imin64(RB, nrow - r0);
   extern __shared__ __align__(16) unsigned char smraw[];
   E* blk = reinterpret_cast<E*>(smraw);               // RB x (k+1), column-major
-  const int kkp = ((kk + 7) / 8) * 8;
+  const int kkp = ((kk + CP - 1) / CP) * CP;
   E* cf = blk + (int64_t)RB * (k + 1);                 // kc x kkp, row-major in i
   const int ncol = SHORT ? k : k + 1;
   for (int e = threadIdx.x; e < ncol * RB; e += blockDim.x) {
     const int c = e / RB, t = e - c * RB;
     blk[e] = (t < nr) ? basis[r0 + t + ldb * c] : E(0);
   }
-  for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
-    const int i = e / kkp, c = e - i * kkp;
-    const double sc = SHORT ? 1.0 : it.colscale[i];
-    cf[e] = (c < kk) ? (E)(C[i + (int64_t)cld * c] * sc) : E(0);
+  if (SHORT) {
+    for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
+      const int i = e / kkp, c = e - i * kkp;
+      cf[e] = (c < kk) ? (E)it.P[i + (int64_t)it.ldc * c] : E(0);
+    }
+  } else {
+    for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
+      const int i = e / kkp, c = e - i * kkp;
+      cf[e] = (E)it.Cs[(int64_t)i * it.ldcs + c];
+    }
   }
   __syncthreads();
-  const int tx = threadIdx.x >> 5, ty = threadIdx.x & 31;
-  for (int c0 = 0; c0 < kk; c0 += 64) {
-    E acc[RA][8];
+  const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
+  for (int c0 = 0; c0 < kk; c0 += CP) {
+    const int cb = c0 + 4 * cg;
+    if (cb >= kk) continue;
+    E acc[4][4];
 #pragma unroll
-    for (int a = 0; a < RA; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int m = 0; m < 8; ++m) acc[a][m] = E(0);
+      for (int b = 0; b < 4; ++b) acc[a][b] = E(0);
     for (int i = 0; i < kc; ++i) {
-      E av[RA], bv[8];
+      E av[4], bv[4];
+      lds4(blk + i * RB + 4 * rg, av);
+      lds4(cf + i * kkp + cb, bv);
 #pragma unroll
-      for (int a = 0; a < RA; ++a) av[a] = blk[i * RB + ty + 32 * a];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int c = c0 + tx + 8 * m;
-        bv[m] = (c < kkp) ? cf[i * kkp + c] : E(0);
-      }
-#pragma unroll
-      for (int a = 0; a < RA; ++a)
-#pragma unroll
-        for (int m = 0; m < 8; ++m) acc[a][m] = fma(av[a], bv[m], acc[a][m]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int c = c0 + tx + 8 * m;
-      if (c >= kk) continue;
+    for (int b = 0; b < 4; ++b) {
+      const int c = cb + b;
+      if (c >= kk) break;
 #pragma unroll
-      for (int a = 0; a < RA; ++a) {
-        const int t = ty + 32 * a;
-        if (t < nr) basis[r0 + t + ldb * c] = acc[a][m];
+      for (int a = 0; a < 4; ++a) {
+        const int t = 4 * rg + a;
+        if (t < nr) basis[r0 + t + ldb * c] = acc[a][b];
       }
     }
   }
@@ -652,14 +683,18 @@ template <typename T>
 void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s, int tiles_s, const int32_t* pre_l,
                  int tiles_l, int final_pass, cudaStream_t st) {
   if (n <= 0) return;
-  const int rs = RITZ_RB_SHORT, rl = ritz_rb_long<T>();
-  const int kp = ((kmax + 7) / 8) * 8;
-  const size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)(kmax + 1) * kp * sizeof(double);
-  const size_t sml = (size_t)rl * (kmax + 2) * sizeof(T) + (size_t)(kmax + 1) * kp * sizeof(T);
+  const int rs = RITZ_RB<double>(), rl = RITZ_RB<T>();
+  const int cps = (256 / (rs / 4)) * 4, cpl = (256 / (rl / 4)) * 4;
+  const int kps = ((kmax + cps - 1) / cps) * cps, kpl = ((kmax + cpl - 1) / cpl) * cpl;
+  const size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)(kmax + 1) * kps * sizeof(double);
+  const size_t sml = (size_t)rl * (kmax + 2) * sizeof(T) + (size_t)(kmax + 1) * kpl * sizeof(T);
   set_max_smem((const void*)k_ritz<T, true>);
   set_max_smem((const void*)k_ritz<T, false>);
   if (tiles_s > 0) { k_ritz<T, true><<<tiles_s, 256, sms, st>>>(items, pre_s, n, final_pass); count_launch(); }
-  if (tiles_l > 0) { k_ritz<T, false><<<tiles_l, 256, sml, st>>>(items, pre_l, n, final_pass); count_launch(); }
+  if (tiles_l > 0) {
+    k_ritz_coef<T><<<n, 256, 0, st>>>(items, final_pass); count_launch();
+    k_ritz<T, false><<<tiles_l, 256, sml, st>>>(items, pre_l, n, final_pass); count_launch();
+  }
 }
 
 template <typename T>

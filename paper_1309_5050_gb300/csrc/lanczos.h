@@ -61,8 +61,11 @@ struct RitzItem {
   T* V; int64_t ldv; int64_t Kl;          // long basis (column scales below)
   double* colscale;
   const double* P; const double* Q;       // from the small SVD
-  int32_t ldc; int32_t pad_;              // their leading dimension (allocated k)
+  int32_t ldc; int32_t ldcs;              // their leading dimension (allocated k); row length of Cs
+  T* Cs;                                  // long-side coefficients Q[i, c] * colscale[i] as T, row-major
 };
+// row length of the scaled long-side coefficients for an allocated Krylov dimension k
+inline int ritz_ldcs(int k) { return ((k + 63) / 64) * 64; }
 
 template <typename T>
 struct FinalItem {
@@ -80,9 +83,11 @@ struct FinalItem {
 // Row-block launches are tile-mapped: item i owns blocks [tpre[i], tpre[i+1])
 // (short side ceil(Ls / SHORT_RB), long side ceil(Kl / LONG_RB), Ritz
 // ceil(rows / RITZ_RB_*)), tiles = tpre[n].
-constexpr int RITZ_RB_SHORT = 64;
+template <typename E>
+constexpr int RITZ_RB() { return sizeof(E) == 8 ? 64 : 128; }   // rows per Ritz block
+constexpr int RITZ_RB_SHORT = RITZ_RB<double>();
 template <typename T>
-constexpr int ritz_rb_long() { return sizeof(T) == 8 ? 64 : 128; }
+constexpr int ritz_rb_long() { return RITZ_RB<T>(); }
 void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
 template <typename T>
 void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
