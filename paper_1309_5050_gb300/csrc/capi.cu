@@ -754,6 +754,7 @@ static MvItem<T> make_mv(ssa_ctx* c, const Channel& h, bool XT, VecRef in, int i
   m.min = XT ? c->Lset.dev() : h.K.dev();
   m.mout = XT ? h.K.dev() : c->Lset.dev();
   m.g1 = g1; m.g2 = g2; m.st = st;
+  m.lV = nullptr; m.lld = 0; m.lB = nullptr; m.lcolscale = nullptr; m.lnpart = nullptr; m.lldb = 0; m.lslot = 0;
   m.log2Mx = h.log2M; m.log2My = c->log2My;
   m.in_type = in_type;
   m.y_in_hi = XT ? c->ey : h.cy;
@@ -844,7 +845,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
     size_t need = rnd256(sizeof(LzState)) + rnd256(8 * w.Ls * k1) + rnd256(cz * w.Kl * k1) + rnd256(8 * w.Ls) +
                   rnd256(cz * w.Kl) + rnd256(cz * w.Ls * w.n_part_s) + rnd256(cz * w.Kl * w.n_part_l) +
                   3 * rnd256(8 * k1 * k1) + 2 * rnd256(8 * (k1 + 1)) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
-                  rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)w.nblk_l) + rnd256(cz * c->L * w.r) +
+                  rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)std::max<int64_t>(w.nblk_l, (int64_t)c->ch.size())) + rnd256(cz * c->L * w.r) +
                   rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r) + rnd256(cz * (k1 + 1) * ritz_ldcs(w.k));
     if (c->log2My > 0) {
       const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
@@ -870,7 +871,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->allocT(&w.cpa, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.cpb, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.np_s, (size_t)w.nblk_s));
-  TRY(c->allocT(&w.np_l, (size_t)w.nblk_l));
+  TRY(c->allocT(&w.np_l, (size_t)std::max<int64_t>(w.nblk_l, (int64_t)c->ch.size())));
   if (c->log2My > 0) {
     const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
     TRY(c->alloc(&w.g1, sizeof(Cx<T>) * hs * nch));
@@ -960,6 +961,16 @@ struct LzEngine {
     return SSA_OK;
   }
 
+  // The long-side step runs inside the X^T u series products when the long
+  // side is the origin side (each channel's product is its own slice of the
+  // long vector) and every slice is a dense range.
+  static bool fuse_long(ssa_ctx* c) {
+    if (c->ws.swapped || c->log2My != 0) return false;
+    for (auto& h : c->ch)
+      if (!h.K.dense) return false;
+    return true;
+  }
+
   ShortItem short_item(ssa_ctx* c) {
     Workspace& w = c->ws;
     ShortItem s;
@@ -973,7 +984,8 @@ struct LzEngine {
     LongItem<T> l;
     l.st = w.st; l.V = (T*)w.V; l.ldv = w.Kl; l.colscale = w.colscale; l.parts = (const T*)w.parts_l;
     l.part_ld = w.Kl; l.n_part = w.n_part_l; l.nblk = w.nblk_l; l.q = (T*)w.q; l.npart = w.np_l; l.B = w.B;
-    l.ldb = w.k; l.pad_ = 0; l.Kl = w.Kl; l.seed = sd;
+    l.ldb = w.k; l.Kl = w.Kl; l.seed = sd;
+    l.nsum = fuse_long(c) ? (int)c->ch.size() : w.nblk_l;
     return l;
   }
   SvdItem svd_item(ssa_ctx* c) {
@@ -1037,7 +1049,12 @@ struct LzEngine {
           // A^T u = X^T u : L -> K slice
           vin.base = w.U; vin.off = 0; vin.ld = w.Ls; vin.st = w.st;
           vout.base = w.parts_l; vout.off = h.koff; vout.st = nullptr;
-          mvAT.add(make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st));
+          MvItem<T> mt = make_mv<T>(c, h, true, vin, 1, vout, g1, g2, w.st);
+          if (fuse_long(c)) {
+            mt.lV = (T*)w.V; mt.lld = w.Kl; mt.lB = w.B; mt.lcolscale = w.colscale; mt.lnpart = w.np_l;
+            mt.lldb = w.k; mt.lslot = (int32_t)q;
+          }
+          mvAT.add(mt);
         } else {
           // A v = X^T v : L -> K slice
           vin.base = w.V; vin.off = 0; vin.ld = w.Kl; vin.st = w.st;
@@ -1064,7 +1081,7 @@ struct LzEngine {
     if (live.empty()) return SSA_OK;
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
     TRY(tiles(live, [](ssa_ctx* c) { return c->ws.nblk_s; }, &t_sh, &n_sh));
-    TRY(tiles(live, [](ssa_ctx* c) { return c->ws.nblk_l; }, &t_lg, &n_lg));
+    TRY(tiles(live, [](ssa_ctx* c) { return fuse_long(c) ? 0 : c->ws.nblk_l; }, &t_lg, &n_lg));
     TRY(ritz_tiles(live, &t_rs, &n_rs, &t_rl, &n_rl));
     auto upl = [&](auto& v, auto** d) { return up(v, d); };
     TRY(finish_set(mvA, upl));

@@ -234,8 +234,10 @@ __device__ Cx<T>* block_fft_s(Cx<T>* a, Cx<T>* b, int log2n, int nb, const Cx<T>
 }
 
 // One radix-2^LR Stockham stage of a single transform (nb = 1) whose input
-// element i comes from in(i) and whose output element i goes to out(i, v):
-// the first stage can read global memory and the last one write it directly.
+// element i comes from in(i) and whose R outputs base + r * stride go to
+// out(base, stride, v[R]) together (so an output functor can issue all its
+// global loads before its stores): the first stage can read global memory and
+// the last one write it directly.
 template <typename T, bool INV, int LR, class In, class Out>
 __device__ __forceinline__ void stage_io(In& in, Out& out, int log2n, int log2Ns, const Cx<T>* tab, int log2N) {
   constexpr int R = 1 << LR;
@@ -261,8 +263,7 @@ __device__ __forceinline__ void stage_io(In& in, Out& out, int log2n, int log2Ns
     else if (LR == 2) dft4<T, INV>(v[0], v[1], v[2], v[3]);
     else dft2<T, INV>(v[0], v[1]);
     const int base = ((j - k) << LR) + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) out(base + r * Ns, v[r]);
+    out(base, Ns, v);
   }
 }
 
@@ -280,7 +281,11 @@ __device__ void block_fft_io(In in, Out out, Cx<T>* a, Cx<T>* b, int log2n, cons
     Cx<T>* src = a;
     Cx<T>* dst = b;
     auto rd = [src](int i) { return src[padi(i)]; };
-    auto wr = [dst](int i, Cx<T> v) { dst[padi(i)] = v; };
+    auto wr = [dst](int base, int stride, auto& v) {
+      constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[padi(base + r * stride)] = v[r];
+    };
 #define SSA_IO(LRV)                                                           \
   if (first && last) stage_io<T, INV, LRV>(in, out, log2n, done, tab, log2N); \
   else if (first) stage_io<T, INV, LRV>(in, wr, log2n, done, tab, log2N);     \

@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
   if (lz_skip(st, j)) return;
   __shared__ double red[32];
   double a = 0.0;
-  for (int b = threadIdx.x; b < it.nblk; b += blockDim.x) a += it.npart[b];
+  const int nb = (s < 0) ? it.nblk : it.nsum;    // start vector: its blocks; a step: nsum partials
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += it.npart[b];
   const double beta = sqrt(block_sum(a, red));
   if (threadIdx.x != 0) return;
   const bool ok = beta > 1e-200;
@@ -655,8 +656,9 @@ void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int 
 
 template <typename T>
 void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st) {
-  if (n <= 0 || tiles <= 0) return;
-  k_long1<T><<<tiles, 256, 0, st>>>(items, tpre, n, s); count_launch();
+  if (n <= 0) return;
+  // problems whose step ran inside their X^T u products own no blocks here
+  if (tiles > 0) { k_long1<T><<<tiles, 256, 0, st>>>(items, tpre, n, s); count_launch(); }
   k_long_norm<T><<<n, 256, 0, st>>>(items, s); count_launch();
 }
 

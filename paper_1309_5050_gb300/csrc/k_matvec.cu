@@ -145,7 +145,7 @@ __device__ int g_mv_async_timeouts;
 //  * the last inverse stage writes the output column straight to global
 //    memory (dense maps; else through store_col).
 template <typename T>
-__global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ items, int s,
+__global__ void __launch_bounds__(512, 2) k_mv1d(const MvItem<T>* __restrict__ items, int s,
                                               const Cx<T>* __restrict__ tw) {
   const MvItem<T> it = items[blockIdx.x];
   if (item_skip<T>(it.st, s)) return;
@@ -165,7 +165,11 @@ __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ item
   const int nst = fft_io_stages(log2H);
   Cx<T>* Z = (nst & 1) ? sm.B : sm.A;   // forward result (written by the last stage)
   Cx<T>* X = (nst & 1) ? sm.A : sm.B;   // the other buffer: twisted product
-  auto zout = [Z](int i, Cx<T> v) { Z[i] = v; };
+  auto zout = [Z](int base, int stride, auto& v) {
+    constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) Z[base + r * stride] = v[r];
+  };
   if (it.min.dense) {
     const int64_t xe = imin64((int64_t)it.min.bx, it.min.limit);
     __syncthreads();                    // twiddle table
@@ -212,17 +216,59 @@ __global__ void __launch_bounds__(512) k_mv1d(const MvItem<T>* __restrict__ item
   const Cx<T>* Xc = X;
   auto qin = [Xc](int i) { return Xc[i]; };
   T* o = (T*)it.out.base + vec_elem_off(it.out, s);
-  if (it.mout.dense) {
+  if (it.mout.dense && it.lV) {
+    // fused long-side step: q = (X^T u) - alpha_j v_j into column j+1, partial |q|^2
     const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
-    auto st = [o, xe](int i, Cx<T> v) {
-      const int64_t x = 2 * (int64_t)i;
-      if (x < xe) o[x] = v.re;
-      if (x + 1 < xe) o[x + 1] = v.im;
+    const int j = it.st->jc + s;
+    const T coef = (T)(it.lB[j + (int64_t)it.lldb * j] * it.lcolscale[j]);
+    const T* vj = it.lV + it.lld * j + it.out.off;
+    T* qn = it.lV + it.lld * (j + 1) + it.out.off;
+    double acc = 0.0;
+    auto st = [vj, qn, xe, coef, &acc](int base, int stride, auto& v) {
+      constexpr int R = sizeof(v) / sizeof(v[0]);
+      T a[2 * R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {      // every load first, then the stores
+        const int64_t x = 2 * (int64_t)(base + r * stride);
+        a[2 * r] = x < xe ? vj[x] : T(0);
+        a[2 * r + 1] = x + 1 < xe ? vj[x + 1] : T(0);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int64_t x = 2 * (int64_t)(base + r * stride);
+        if (x < xe) { const T q = v[r].re - coef * a[2 * r]; qn[x] = q; acc += (double)q * (double)q; }
+        if (x + 1 < xe) { const T q = v[r].im - coef * a[2 * r + 1]; qn[x + 1] = q; acc += (double)q * (double)q; }
+      }
+    };
+    block_fft_io<T, true>(qin, st, X, Z, log2H, sm.tab, log2H + 1);
+    __shared__ double red[16];
+    for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];   // fixed order
+      it.lnpart[it.lslot] = t;
+    }
+  } else if (it.mout.dense) {
+    const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
+    auto st = [o, xe](int base, int stride, auto& v) {
+      constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int64_t x = 2 * (int64_t)(base + r * stride);
+        if (x < xe) o[x] = v[r].re;
+        if (x + 1 < xe) o[x + 1] = v[r].im;
+      }
     };
     block_fft_io<T, true>(qin, st, X, Z, log2H, sm.tab, log2H + 1);
   } else {
     Cx<T>* R = (nst & 1) ? Z : X;
-    auto rout = [R](int i, Cx<T> v) { R[i] = v; };
+    auto rout = [R](int base, int stride, auto& v) {
+      constexpr int RR = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+      for (int r = 0; r < RR; ++r) R[base + r * stride] = v[r];
+    };
     block_fft_io<T, true>(qin, rout, X, Z, log2H, sm.tab, log2H + 1);
     store_col<T, T>(reinterpret_cast<const T*>(R), o, it.mout, 0, sm.pre, sm.wt);
   }

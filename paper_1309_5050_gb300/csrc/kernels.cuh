@@ -58,6 +58,14 @@ struct MvItem {
   int32_t y_in_hi;          // grid columns [0, y_in_hi) may hold input
   int32_t y_out_hi;         // grid columns [0, y_out_hi) hold output positions
   int32_t pad_;
+  // Long-side Lanczos step fused into the store of X^T u (series whose long
+  // side is the origin side): instead of the product slice, row o of the
+  // output writes q = (X^T u)_o - alpha_j v_j[o] into column j+1 of lV,
+  // alpha_j v_j = lB[j, j] lcolscale[j] lV[:, j] (j = jc + s), and the
+  // block's partial sum of q^2 goes to lnpart[lslot].  lV == null: off.
+  T* lV; int64_t lld;
+  const double* lB; const double* lcolscale; double* lnpart;
+  int32_t lldb, lslot;
 };
 
 // Raw data to half spectrum (step 1 of the matvec algorithms, precomputed).

@@ -39,8 +39,9 @@ struct LongItem {
   double* colscale;                       // k+1: column c of V times colscale[c] is v_c
   const T* parts; int64_t part_ld; int32_t n_part; int32_t nblk;
   T* q;                                   // work vector, Kl
-  double* npart;                          // nblk partial squared norms
-  double* B; int32_t ldb; int32_t pad_;
+  double* npart;                          // partial squared norms
+  double* B; int32_t ldb;
+  int32_t nsum;                           // partial norms of a step (nblk, or the fused products' count)
   int64_t Kl;
   uint64_t seed;
 };
