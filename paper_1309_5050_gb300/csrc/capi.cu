@@ -720,19 +720,21 @@ template <typename T>
 struct MvSet {
   // series on one FFT grid (fused single-CTA products) and grids with a y
   // extent (images, segment-form series: x-pass, y-pass, x-pass)
-  std::vector<MvItem<T>> items1, items2;
+  // items1[mode]: series products of one k_mv1d code path (mv1d_mode)
+  std::vector<MvItem<T>> items1[MV1_MODES], items2;
   std::vector<YItem<T>> yitems2;
-  MvItem<T>* d1 = nullptr;
+  MvItem<T>* d1[MV1_MODES] = {};
   MvItem<T>* d2 = nullptr;
   YItem<T>* dy2 = nullptr;
   int32_t *t_xf = nullptr, *t_yp = nullptr, *t_xi = nullptr;   // block ranges of the 2D launches
   int n_xf = 0, n_yp = 0, n_xi = 0;
   int max_y_in = 0, max_y_out = 0;
-  int lx1 = 1, lx2 = 1, ly2 = 0;   // largest log2 grid sizes of each list
+  int lx1[MV1_MODES] = {}, lx2 = 1, ly2 = 0;   // largest log2 grid sizes of each list
   void add(const MvItem<T>& m) {
     if (m.log2My == 0) {
-      items1.push_back(m);
-      lx1 = std::max(lx1, (int)m.log2Mx);
+      const int md = mv1d_mode(m);
+      items1[md].push_back(m);
+      lx1[md] = std::max(lx1[md], (int)m.log2Mx);
     } else {
       items2.push_back(m);
       lx2 = std::max(lx2, (int)m.log2Mx);
@@ -741,7 +743,12 @@ struct MvSet {
       max_y_out = std::max(max_y_out, (int)m.y_out_hi);
     }
   }
-  size_t size() const { return items1.size() + items2.size(); }
+  size_t n1() const {
+    size_t n = 0;
+    for (auto& v : items1) n += v.size();
+    return n;
+  }
+  size_t size() const { return n1() + items2.size(); }
 };
 
 template <typename T>
@@ -792,7 +799,8 @@ static int finish_set(MvSet<T>& s, Up&& up) {
     yp.push_back(yp.back() + ypass_blocks(m.log2Mx, s.yitems2.back().tk));
     xi.push_back(xi.back() + m.y_out_hi);
   }
-  if (!s.items1.empty()) TRY(up(s.items1, &s.d1));
+  for (int md = 0; md < MV1_MODES; ++md)
+    if (!s.items1[md].empty()) TRY(up(s.items1[md], &s.d1[md]));
   if (!s.items2.empty()) {
     TRY(up(s.items2, &s.d2));
     TRY(up(s.yitems2, &s.dy2));
@@ -805,8 +813,9 @@ static int finish_set(MvSet<T>& s, Up&& up) {
 template <typename T>
 static void run_mv(ssa_ctx* c, const MvSet<T>& s, int step) {
   PhaseScope ps_(PH_MATVEC, c->stream);
-  if (!s.items1.empty())
-    launch_mv1d<T>(s.d1, (int)s.items1.size(), s.lx1, step, twiddles<T>(c->device), c->stream);
+  for (int md = 0; md < MV1_MODES; ++md)
+    if (!s.items1[md].empty())
+      launch_mv1d<T>(s.d1[md], (int)s.items1[md].size(), s.lx1[md], step, twiddles<T>(c->device), c->stream, md);
   if (!s.items2.empty()) {
     const int n2 = (int)s.items2.size();
     launch_mv2d<T>(s.d2, s.dy2, n2, Tiles{s.t_xf, n2, s.n_xf}, Tiles{s.t_yp, n2, s.n_yp},
@@ -1147,7 +1156,7 @@ struct LzEngine {
     CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
-    if (!mvA.items1.empty() && mv_async_timeouts(st) != 0)
+    if ((mvA.n1() || mvAT.n1()) && mv_async_timeouts(st) != 0)
       return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
     return SSA_OK;
   }
@@ -1588,12 +1597,13 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
   CU(cudaGetLastError());
   if (!on_device) CU(cudaMemcpyAsync(out, dres, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  if (!s.items1.empty() && mv_async_timeouts(c->stream) != 0)
+  if (s.n1() && mv_async_timeouts(c->stream) != 0)
     return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
   c->release(din); c->release(dparts);
   if (!on_device) { c->release(dd); c->release(dres); }
   if (g1) { c->release(g1); c->release(g2); }
-  if (s.d1) c->release(s.d1);
+  for (auto* d : s.d1)
+    if (d) c->release(d);
   if (s.d2) {
     c->release(s.d2); c->release(s.dy2);
     c->release(s.t_xf); c->release(s.t_yp); c->release(s.t_xi);

@@ -268,36 +268,45 @@ __device__ __forceinline__ void stage_io(In& in, Out& out, int log2n, int log2Ns
 }
 
 // Stages of one transform of length 2^log2n: the first reads in(i), the last
-// writes out(i, v), the ones between ping-pong through the padded buffers
-// (the first stage writes b).  A barrier follows every stage.
+// hands its outputs to out(base, stride, v), the ones between ping-pong through
+// the padded buffers (the first stage writes b).  The first stage takes the
+// 1..3 leftover bits and every later stage is radix 8, which keeps the number
+// of stage bodies the compiler emits small.  A barrier follows every stage.
 template <typename T, bool INV, class In, class Out>
 __device__ void block_fft_io(In in, Out out, Cx<T>* a, Cx<T>* b, int log2n, const Cx<T>* tab, int log2N) {
-  int done = 0;
-  bool first = true;
-  while (done < log2n) {
-    const int rem = log2n - done;
-    const int lr = rem >= 3 ? 3 : rem;
-    const bool last = (done + lr == log2n);
-    Cx<T>* src = a;
-    Cx<T>* dst = b;
-    auto rd = [src](int i) { return src[padi(i)]; };
-    auto wr = [dst](int base, int stride, auto& v) {
-      constexpr int R = sizeof(v) / sizeof(v[0]);
+  auto wr = [b](int base, int stride, auto& v) {
+    constexpr int R = sizeof(v) / sizeof(v[0]);
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[padi(base + r * stride)] = v[r];
-    };
-#define SSA_IO(LRV)                                                           \
-  if (first && last) stage_io<T, INV, LRV>(in, out, log2n, done, tab, log2N); \
-  else if (first) stage_io<T, INV, LRV>(in, wr, log2n, done, tab, log2N);     \
-  else if (last) stage_io<T, INV, LRV>(rd, out, log2n, done, tab, log2N);     \
-  else stage_io<T, INV, LRV>(rd, wr, log2n, done, tab, log2N);
-    if (lr == 3) { SSA_IO(3) } else if (lr == 2) { SSA_IO(2) } else { SSA_IO(1) }
-#undef SSA_IO
-    done += lr;
-    first = false;
+    for (int r = 0; r < R; ++r) b[padi(base + r * stride)] = v[r];
+  };
+  const int lr0 = log2n - 3 * ((log2n - 1) / 3);   // 1..3
+  if (lr0 == log2n) {                                // a single stage
+    if (lr0 == 3) stage_io<T, INV, 3>(in, out, log2n, 0, tab, log2N);
+    else if (lr0 == 2) stage_io<T, INV, 2>(in, out, log2n, 0, tab, log2N);
+    else stage_io<T, INV, 1>(in, out, log2n, 0, tab, log2N);
     __syncthreads();
-    a = dst;
-    b = src;
+    return;
+  }
+  if (lr0 == 3) stage_io<T, INV, 3>(in, wr, log2n, 0, tab, log2N);
+  else if (lr0 == 2) stage_io<T, INV, 2>(in, wr, log2n, 0, tab, log2N);
+  else stage_io<T, INV, 1>(in, wr, log2n, 0, tab, log2N);
+  __syncthreads();
+  Cx<T>* src = b;
+  Cx<T>* dst = a;
+  for (int done = lr0; done < log2n; done += 3) {
+    auto rd = [src](int i) { return src[padi(i)]; };
+    if (done + 3 == log2n) {
+      stage_io<T, INV, 3>(rd, out, log2n, done, tab, log2N);
+    } else {
+      auto wd = [dst](int base, int stride, auto& v) {
+        constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[padi(base + r * stride)] = v[r];
+      };
+      stage_io<T, INV, 3>(rd, wd, log2n, done, tab, log2N);
+    }
+    __syncthreads();
+    Cx<T>* t = src; src = dst; dst = t;
   }
 }
 

@@ -144,9 +144,16 @@ __device__ int g_mv_async_timeouts;
 //    pairs (k, H-k);
 //  * the last inverse stage writes the output column straight to global
 //    memory (dense maps; else through store_col).
-template <typename T>
-__global__ void __launch_bounds__(512, 2) k_mv1d(const MvItem<T>* __restrict__ items, int s,
-                                              const Cx<T>* __restrict__ tw) {
+// MODE (see mv1d_mode) selects one code path per instantiation: input type,
+// input map, output form -- every item of a launch shares it.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvItem<T>* __restrict__ items, int s,
+                                                 const Cx<T>* __restrict__ tw) {
+  constexpr bool IN_DOUBLE = (MODE & MV1_IN_DOUBLE) != 0;
+  constexpr bool IN_MAPPED = (MODE & MV1_IN_MAPPED) != 0;
+  constexpr bool OUT_FUSED = (MODE & MV1_OUT_FUSED) != 0;
+  constexpr bool OUT_MAPPED = (MODE & MV1_OUT_MAPPED) != 0;
+  typedef typename std::conditional<IN_DOUBLE, double, T>::type TI;
   const MvItem<T> it = items[blockIdx.x];
   if (item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -170,29 +177,17 @@ __global__ void __launch_bounds__(512, 2) k_mv1d(const MvItem<T>* __restrict__ i
 #pragma unroll
     for (int r = 0; r < R; ++r) Z[base + r * stride] = v[r];
   };
-  if (it.min.dense) {
+  if constexpr (!IN_MAPPED) {
     const int64_t xe = imin64((int64_t)it.min.bx, it.min.limit);
     __syncthreads();                    // twiddle table
-    if (it.in_type == 1) {
-      const double* src = (const double*)it.in.base + ioff;
-      auto in = [src, xe, isc](int i) {
-        const int64_t x = 2 * (int64_t)i;
-        return cx(x < xe ? (T)src[x] * isc : T(0), x + 1 < xe ? (T)src[x + 1] * isc : T(0));
-      };
-      block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
-    } else {
-      const T* src = (const T*)it.in.base + ioff;
-      auto in = [src, xe, isc](int i) {
-        const int64_t x = 2 * (int64_t)i;
-        return cx(x < xe ? src[x] * isc : T(0), x + 1 < xe ? src[x + 1] * isc : T(0));
-      };
-      block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
-    }
+    const TI* src = (const TI*)it.in.base + ioff;
+    auto in = [src, xe, isc](int i) {
+      const int64_t x = 2 * (int64_t)i;
+      return cx(x < xe ? (T)src[x] * isc : T(0), x + 1 < xe ? (T)src[x + 1] * isc : T(0));
+    };
+    block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
   } else {
-    if (it.in_type == 1)
-      load_col<T, double>(reinterpret_cast<T*>(sm.A), 2 * H, (const double*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
-    else
-      load_col<T, T>(reinterpret_cast<T*>(sm.A), 2 * H, (const T*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
+    load_col<T, TI>(reinterpret_cast<T*>(sm.A), 2 * H, (const TI*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
     __syncthreads();
     const Cx<T>* A = sm.A;
     auto in = [A](int i) { return A[i]; };
@@ -216,41 +211,59 @@ __global__ void __launch_bounds__(512, 2) k_mv1d(const MvItem<T>* __restrict__ i
   const Cx<T>* Xc = X;
   auto qin = [Xc](int i) { return Xc[i]; };
   T* o = (T*)it.out.base + vec_elem_off(it.out, s);
-  if (it.mout.dense && it.lV) {
+  if constexpr (OUT_FUSED) {
     // fused long-side step: q = (X^T u) - alpha_j v_j into column j+1, partial |q|^2
     const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
     const int j = it.st->jc + s;
     const T coef = (T)(it.lB[j + (int64_t)it.lldb * j] * it.lcolscale[j]);
     const T* vj = it.lV + it.lld * j + it.out.off;
     T* qn = it.lV + it.lld * (j + 1) + it.out.off;
-    double acc = 0.0;
-    auto st = [vj, qn, xe, coef, &acc](int base, int stride, auto& v) {
+    // v_j lands in the (now free) spectrum buffer while the inverse FFT runs:
+    // each thread copies exactly the entries its last-stage butterflies use
+    // (complex outputs b + r*Ns, b = thread index + multiples of the block)
+    T* vs = reinterpret_cast<T*>(sm.S);
+    {
+      const int Ns = H >> 3;
+      for (int b = threadIdx.x; b < Ns; b += blockDim.x)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int64_t x = 2 * (int64_t)(b + r * Ns);
+          if (x < xe) cp_async_elem<sizeof(T)>(vs + x, vj + x);
+          if (x + 1 < xe) cp_async_elem<sizeof(T)>(vs + x + 1, vj + x + 1);
+        }
+    }
+    // per-thread partial of |q|^2 in T (a few dozen terms), the block sum in
+    // double: FP64 per element would cost more than the product on GB300
+    T acc = T(0);
+    auto st = [vs, qn, xe, coef, &acc](int base, int stride, auto& v) {
       constexpr int R = sizeof(v) / sizeof(v[0]);
+      cp_async_wait_all();
       T a[2 * R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {      // every load first, then the stores
+      for (int r = 0; r < R; ++r) {
         const int64_t x = 2 * (int64_t)(base + r * stride);
-        a[2 * r] = x < xe ? vj[x] : T(0);
-        a[2 * r + 1] = x + 1 < xe ? vj[x + 1] : T(0);
+        a[2 * r] = x < xe ? vs[x] : T(0);
+        a[2 * r + 1] = x + 1 < xe ? vs[x + 1] : T(0);
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int64_t x = 2 * (int64_t)(base + r * stride);
-        if (x < xe) { const T q = v[r].re - coef * a[2 * r]; qn[x] = q; acc += (double)q * (double)q; }
-        if (x + 1 < xe) { const T q = v[r].im - coef * a[2 * r + 1]; qn[x + 1] = q; acc += (double)q * (double)q; }
+        if (x < xe) { const T q = v[r].re - coef * a[2 * r]; qn[x] = q; acc = fma(q, q, acc); }
+        if (x + 1 < xe) { const T q = v[r].im - coef * a[2 * r + 1]; qn[x + 1] = q; acc = fma(q, q, acc); }
       }
     };
     block_fft_io<T, true>(qin, st, X, Z, log2H, sm.tab, log2H + 1);
     __shared__ double red[16];
-    for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double dacc = (double)acc;
+    for (int o2 = 16; o2 > 0; o2 >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dacc;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];   // fixed order
       it.lnpart[it.lslot] = t;
     }
-  } else if (it.mout.dense) {
+  } else if constexpr (!OUT_MAPPED) {
     const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
     auto st = [o, xe](int base, int stride, auto& v) {
       constexpr int R = sizeof(v) / sizeof(v[0]);
@@ -420,12 +433,24 @@ int mv_async_timeouts(cudaStream_t st) {
   return h;
 }
 
+template <typename T, int MODE>
+static void launch_mv1d_mode(const MvItem<T>* items, int n, size_t sm, int s, const Cx<T>* tw, cudaStream_t st) {
+  set_max_smem((const void*)k_mv1d<T, MODE>);
+  k_mv1d<T, MODE><<<n, 512, sm, st>>>(items, s, tw); count_launch();
+}
+
 template <typename T>
-void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st) {
+void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st, int mode) {
   if (n <= 0) return;
-  size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>), true);
-  set_max_smem((const void*)k_mv1d<T>);
-  k_mv1d<T><<<n, 512, sm, st>>>(items, s, tw); count_launch();
+  const size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>), true);
+  switch (mode) {
+#define SSA_MV1(M) case M: launch_mv1d_mode<T, M>(items, n, sm, s, tw, st); break;
+    SSA_MV1(0) SSA_MV1(1) SSA_MV1(2) SSA_MV1(3)
+    SSA_MV1(4) SSA_MV1(5) SSA_MV1(6) SSA_MV1(7)
+    SSA_MV1(8) SSA_MV1(9) SSA_MV1(10) SSA_MV1(11)
+#undef SSA_MV1
+    default: break;
+  }
 }
 
 template <typename T>
@@ -462,7 +487,7 @@ void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Til
 }
 
 #define INST(T)                                                                                       \
-  template void launch_mv1d<T>(const MvItem<T>*, int, int, int, const Cx<T>*, cudaStream_t);          \
+  template void launch_mv1d<T>(const MvItem<T>*, int, int, int, const Cx<T>*, cudaStream_t, int);     \
   template void launch_mv2d<T>(const MvItem<T>*, const YItem<T>*, int, Tiles, Tiles, Tiles, int, int,  \
                                int, const Cx<T>*, cudaStream_t);                                      \
   template void launch_ypass<T>(const YItem<T>*, Tiles, int, int, int, const Cx<T>*, cudaStream_t);    \

@@ -68,6 +68,16 @@ struct MvItem {
   int32_t lldb, lslot;
 };
 
+// Code path of a series product (one k_mv1d instantiation per value): the
+// input is double (else T), the input map is bit-mapped (else a dense range),
+// the output is the fused long-side step, or bit-mapped (else a dense range).
+enum : int { MV1_IN_DOUBLE = 1, MV1_IN_MAPPED = 2, MV1_OUT_FUSED = 4, MV1_OUT_MAPPED = 8, MV1_MODES = 12 };
+template <typename T>
+inline int mv1d_mode(const MvItem<T>& m) {
+  return (m.in_type == 1 ? MV1_IN_DOUBLE : 0) | (m.min.dense ? 0 : MV1_IN_MAPPED) |
+         (!m.mout.dense ? MV1_OUT_MAPPED : (m.lV ? MV1_OUT_FUSED : 0));
+}
+
 // Raw data to half spectrum (step 1 of the matvec algorithms, precomputed).
 template <typename T>
 struct SpecItem {

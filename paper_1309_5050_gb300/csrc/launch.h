@@ -25,8 +25,9 @@ int device_max_smem();
 template <typename T> const Cx<T>* twiddles(int device);
 
 // matvec / spectrum
+// Series products of one code path `mode` (mv1d_mode): every item shares it.
 template <typename T>
-void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st);
+void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st, int mode);
 // Bulk-copy waits in the series product that gave up since the last call
 // (each sets a device counter instead of spinning on); read and reset, -1 on
 // a CUDA error.  Synchronises the stream.
