@@ -206,6 +206,93 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
             "phases_ms": {k: v[0] for k, v in prof.items()}}
 
 
+def mv1d_algorithmic(probs):
+    """Algorithmic bytes of one k_mv1d launch over the batch, per direction,
+    and its FFT flops (average of the two).  Per problem and channel q with
+    grid M_q = next power of two >= N_q (>= 16), H_q = M_q / 2:
+      X v   : v slice (K_q fp32) + spectrum ((H_q+1) complex fp32) + partial u (L fp32)
+      X^T u : u (L fp64) + spectrum + v_j slice (K_q fp32) + q slice (K_q fp32)
+    (the X^T u launch carries the fused long-side step).  Flops: two packed
+    real FFTs of M_q points, 5 H log2 H each, per channel."""
+    L = CFG["L"]
+    ba = bt = fl = 0.0
+    for lens, _ in probs:
+        for n in lens:
+            M = 16
+            while M < n:
+                M *= 2
+            H = M // 2
+            K = int(n) - L + 1
+            spec = (H + 1) * 8
+            ba += K * 4 + spec + L * 4
+            bt += L * 8 + spec + 2 * K * 4
+            fl += 2 * 5 * H * np.log2(H)
+    return {"bytes_A": ba, "bytes_AT": bt, "flops": fl}
+
+
+def mv1d_traffic(batch):
+    """DRAM bytes per k_mv1d launch (average of the two directions) from the
+    committed ncu summary, when it was taken on this batch size and the
+    kernel's sources are unchanged since; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_mv1d_mssa_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None, "no committed capture"
+    h = hashlib.sha256()
+    for rel in d.get("sources", []):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != d.get("sources_sha256"):
+        return None, "kernel sources changed since the capture"
+    if int(d.get("batch", -1)) != int(batch):
+        return None, f"capture taken at batch {d.get('batch')}"
+    return float(d["dram_bytes_per_launch"]), "profiles/k_mv1d_mssa_traffic.json"
+
+
+MV1D_SOURCES = ["paper_1309_5050_gb300/csrc/k_matvec.cu", "paper_1309_5050_gb300/csrc/fft_block.cuh",
+                "paper_1309_5050_gb300/csrc/tma.cuh", "paper_1309_5050_gb300/csrc/kernels.cuh",
+                "paper_1309_5050_gb300/csrc/common.cuh"]
+
+
+def write_traffic(csv_path, batch, command):
+    """Summarise an ncu launch capture of k_mv1d (metrics dram__bytes_read.sum,
+    dram__bytes_write.sum) into profiles/k_mv1d_mssa_traffic.json, keyed by
+    the kernel's source hash so a later change voids it."""
+    import csv
+    import hashlib
+    rows = list(csv.reader(open(csv_path)))
+    hdr = [r for r in rows if r and r[0] == "ID"][0]
+    per = {}
+    for r in rows:
+        if not r or r[0] == "ID" or len(r) != len(hdr):
+            continue
+        d = dict(zip(hdr, r))
+        if "k_mv1d" not in d["Kernel Name"]:
+            continue
+        v = float(d["Metric Value"].replace(",", ""))
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1, "nsecond": 1,
+                 "usecond": 1e3, "us": 1e3, "msecond": 1e6, "ms": 1e6}.get(d["Metric Unit"], 1)
+        e = per.setdefault(d["ID"], {"kernel": d["Kernel Name"].split("(")[0]})
+        e[d["Metric Name"]] = v * scale
+    launches = [e for e in per.values() if "dram__bytes_read.sum" in e]
+    tot = [e["dram__bytes_read.sum"] + e.get("dram__bytes_write.sum", 0.0) for e in launches]
+    h = hashlib.sha256()
+    for rel in MV1D_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    out = {"kernel": "k_mv1d", "workload": WORKLOAD, "batch": batch, "command": command,
+           "launches": [{"kernel": e["kernel"], "dram_bytes": t, "ns": e.get("gpu__time_duration.sum")}
+                        for e, t in zip(launches, tot)],
+           "dram_bytes_per_launch": sum(tot) / max(len(tot), 1),
+           "sources": MV1D_SOURCES, "sources_sha256": h.hexdigest()}
+    with open(os.path.join(ROOT, "profiles", "k_mv1d_mssa_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+
+
 def _probe_info(pkg, probs, cfg, stream, args):
     """Krylov dimension the library uses for one problem of the workload."""
     lens, flat = probs[0]
@@ -230,7 +317,13 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=1000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--write-traffic", default=None,
+                    help="ncu CSV of k_mv1d dram bytes -> profiles/k_mv1d_mssa_traffic.json (no GPU use)")
+    ap.add_argument("--traffic-command", default="")
     args = ap.parse_args()
+    if args.write_traffic:
+        write_traffic(args.write_traffic, args.batch, args.traffic_command)
+        return 0
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -370,21 +463,24 @@ def main():
                                   n_max=SERVE_N_MAX)
         serving = run_serving(pkg, reqs, args.prec, int(args.serve_budget_gb * (1 << 30)), args.serve_rate)
 
-    # roofline of the dominant phase
+    # roofline of the series product (k_mv1d), the dominant kernel
     hbm, src = peaks()
     total_ms = sum(v[0] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][0])
     mv_ms, mv_launch, mv_calls = prof["matvec"]
-    # algorithmic bytes of one trajectory product of one problem: v (K fp32) +
-    # spectra (16 x (H+1) complex fp32) + u (L fp32); one call = B problems.
-    Ks = [int((l - CFG["L"] + 1).sum()) for l, _ in probs]
-    H = 4096
-    per_call = sum(K * 4 + 16 * (H + 1) * 8 + CFG["L"] * 4 for K in Ks)
-    mv_avg_ms = mv_ms / max(mv_calls, 1)
+    alg = mv1d_algorithmic(probs)
+    mv_avg_ms = mv_ms / max(mv_calls, 1)          # one phase instance = one k_mv1d launch
+    per_call = (alg["bytes_A"] + alg["bytes_AT"]) / 2.0
     achieved = per_call / (mv_avg_ms / 1000.0) / 1e9
-    roof = {"kernel": "k_mv1d (fused FFT trajectory product)", "bound": "hbm", "achieved": achieved,
-            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-            "peak_source": src, "launches_timed": mv_calls,
+    flops = alg["flops"] / (mv_avg_ms / 1000.0) / 1e12
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12      # FP32 FMA lanes x 2 flops x max SM clock
+    traffic, traffic_src = mv1d_traffic(B)
+    roof = {"kernel": "k_mv1d (fused FFT trajectory product, both directions)", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "traffic_source": traffic_src, "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)",
+            "algorithmic_bytes_per_launch": per_call, "launches_timed": mv_calls,
+            "alu": {"achieved": flops, "peak": alu_peak, "unit": "TFLOP/s", "frac": flops / alu_peak,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
             "phase_share": {k: (v[0] / total_ms if total_ms else 0.0) for k, v in prof.items()},
             "dominant_phase": dom}
 
