@@ -387,7 +387,8 @@ def main():
     def step(inputs, outs, prec):
         ps = pkg.embed_multi_batch(inputs, [l for l, _ in probs], CFG["L"], stream=stream)
         pkg.decompose_batch(ps, CFG["rank"], prec, krylov_dim=args.krylov_dim)
-        restarts.append(ps[0].info()["restarts"])
+        inf0 = ps[0].info()
+        restarts.append((inf0["restarts"], inf0["jacobi_sweeps"]))
         if outs[0].is_cuda:
             pkg.reconstruct_batch(ps, GROUPS, residual=True, outs=outs)
         else:
@@ -502,7 +503,8 @@ def main():
                 "e2e": {"value": world * B / (ms_e2e / 1000.0), "unit": "decomps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
                 "gpu_launches": int(launches),
-                "lanczos": {"krylov_dim": ps_info["krylov_dim"], "restarts_first_problem": restarts[-1]},
+                "lanczos": {"krylov_dim": ps_info["krylov_dim"], "restarts_first_problem": restarts[-1][0],
+                            "last_jacobi_sweeps_first_problem": restarts[-1][1]},
                 "phases_ms": {k: v[0] / args.steps for k, v in prof.items()},
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

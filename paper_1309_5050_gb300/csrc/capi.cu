@@ -1371,7 +1371,10 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
       tmp.push_back(dout[p]);
     }
   }
-  // ---- series on one grid: F(U_i) once per problem, then one CTA per (problem, group, channel)
+  // ---- series on one grid: F(U_i) once per problem and grid size (each
+  // channel keeps its own M_q >= N_q: the group's convolution of U with the
+  // channel's V slice has linear length N_q), then one CTA per (problem,
+  // group, channel)
   {
     std::vector<RecColItem<T, TV>> ui;
     std::vector<Rec1Item<T, TV>> ri;
@@ -1381,30 +1384,37 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
       if (c->log2My != 0) continue;
       Workspace& w = c->ws;
       const int r = w.r, ng = req[p].ng;
-      const int H = 1 << (c->log2Mx - 1);
-      Cx<T>* gu = nullptr;
-      TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * (size_t)(H + 1) * r));
-      tmp.push_back(gu);
       double* o = dout[p];
-      for (int i = 0; i < r; ++i) {
-        RecColItem<T, TV> u;
-        u.vec = (const TV*)w.Uo + (size_t)c->L * i; u.map = c->Lset.dev(); u.dst = gu + (size_t)(H + 1) * i;
-        u.log2Mx = c->log2Mx; u.ncols = 1;
-        ui.push_back(u);
+      Cx<T>* gu_of[32] = {};
+      for (const Channel& h : c->ch) {
+        if (gu_of[h.log2M]) continue;
+        const int H = 1 << (h.log2M - 1);
+        Cx<T>* gu = nullptr;
+        TRY(c0->alloc((void**)&gu, sizeof(Cx<T>) * (size_t)(H + 1) * r));
+        tmp.push_back(gu);
+        gu_of[h.log2M] = gu;
+        for (int i = 0; i < r; ++i) {
+          if (req[p].group_of[i] < 0) continue;      // component in no group
+          RecColItem<T, TV> u;
+          u.vec = (const TV*)w.Uo + (size_t)c->L * i; u.map = c->Lset.dev(); u.dst = gu + (size_t)(H + 1) * i;
+          u.log2Mx = h.log2M; u.ncols = 1;
+          ui.push_back(u);
+        }
+        max_log2Mx = std::max(max_log2Mx, h.log2M);
       }
       for (int g = 0; g < ng; ++g)
         for (size_t q = 0; q < c->ch.size(); ++q) {
           const Channel& h = c->ch[q];
+          const int H = 1 << (h.log2M - 1);
           Rec1Item<T, TV> it;
           it.V = (const TV*)w.Vo + h.koff; it.ldv = c->K; it.map = h.K.dev();
-          it.gu = gu; it.ldgu = H + 1; it.sigma = w.sigma;
+          it.gu = gu_of[h.log2M]; it.ldgu = H + 1; it.sigma = w.sigma;
           it.comps = d_flat + start[p][g]; it.ncomp = start[p][g + 1] - start[p][g];
-          it.log2Mx = c->log2Mx; it.w = h.w; it.n = (int32_t)h.nx;
+          it.log2Mx = h.log2M; it.w = h.w; it.n = (int32_t)h.nx;
           it.out = o + (size_t)g * c->total + h.data_off;
           it.inv_norm = 1.0 / (double)(2 * H);
           ri.push_back(it);
         }
-      max_log2Mx = std::max(max_log2Mx, c->log2Mx);
     }
     if (!ui.empty()) {
       RecColItem<T, TV>* d_ui = nullptr; Rec1Item<T, TV>* d_ri = nullptr;
@@ -1926,6 +1936,7 @@ int ssa_get_info(const ssa_ctx* c, ssa_info* info) {
     info->rank = c->ws.r; info->krylov_dim = c->ws.k; info->restarts = c->ws.host_st.restarts;
     info->converged = c->ws.host_st.converged || c->ws.host_st.breakdown; info->prec = c->ws.prec;
     info->max_residual = c->ws.host_st.maxres;
+    info->jacobi_sweeps = c->ws.host_st.sweeps;
   }
   return SSA_OK;
 }

@@ -332,11 +332,37 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
           be = nrm2[b];
           // a pair is done once its cosine is at the rounding level of a
           // k-term FP64 dot product (k * eps); tighter never settles.
-          rot = ga != 0.0 && fabs(ga) > jtol * sqrt(al * be);
+          rot = ga != 0.0 && ga * ga > jtol * jtol * (al * be);
         }
         if (rot) {
-          const double zeta = (be - al) / (2.0 * ga);
-          tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          // Tangent of the angle from zeta = (be - al) / (2 ga), formed in FP32
+          // after scaling both terms by one power of two: an FP32 angle leaves
+          // a ~1e-7 relative residual in the pair, which the next sweep
+          // removes, and saves most of the FP64 instructions of a round.
+          // Angles below FP32 resolution take the FP64 formula.  Cosine and
+          // sine follow in FP64 from that tangent, so the rotation is
+          // orthogonal to FP64 rounding whatever its angle.
+          const double dz = be - al, g2 = 2.0 * ga;
+          const double mx = fmax(fabs(dz), fabs(g2));
+          int ex = ((__double2hiint(mx) >> 20) & 0x7ff) - 1023;
+          ex = ex > 1022 ? 1022 : ex;
+          const double sc = __hiloint2double((1023 - ex) << 20, 0);     // 2^-ex
+          const float zn = (float)(dz * sc), zd = (float)(g2 * sc);
+          float tf = 0.0f;
+          if (zd != 0.0f) {
+            const float zf = zn / zd, az = fabsf(zf);
+            if (az < 1e18f) tf = copysignf(1.0f, zf) / (az + sqrtf(fmaf(zf, zf, 1.0f)));
+          }
+          if (tf != 0.0f) {
+            tt = (double)tf;
+          } else {
+            const double zeta = dz / g2;
+            const double az = fabs(zeta);
+            tt = az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + zeta * zeta));
+          }
+          if (tt == 0.0) rot = false;
+        }
+        if (rot) {
           const double cn = rsqrt(1.0 + tt * tt), sn = cn * tt;
           int m = q;
           for (; m + 4 < k; m += 8) {
