@@ -923,6 +923,9 @@ struct LzEngine {
   // block ranges of the members in the row-block launches
   int32_t *t_sh = nullptr, *t_lg = nullptr, *t_rs = nullptr, *t_rl = nullptr;
   int n_sh = 0, n_lg = 0, n_rs = 0, n_rl = 0;
+  ShortItem* d_shf = nullptr;      // members whose short step runs in one block
+  int n_shf = 0;
+  int64_t max_ls_f = 1;
   MvSet<T> mvA, mvAT;
   int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1;
   int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
@@ -1089,7 +1092,16 @@ struct LzEngine {
     }
     if (live.empty()) return SSA_OK;
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
-    TRY(tiles(live, [](ssa_ctx* c) { return c->ws.nblk_s; }, &t_sh, &n_sh));
+    TRY(tiles(live, [](ssa_ctx* c) { return c->ws.Ls <= SHORT_FUSED_MAX ? 0 : c->ws.nblk_s; }, &t_sh, &n_sh));
+    {
+      std::vector<ShortItem> shf;
+      max_ls_f = 1;
+      for (ssa_ctx* c : live)
+        if (c->ws.Ls <= SHORT_FUSED_MAX) { shf.push_back(short_item(c)); max_ls_f = std::max(max_ls_f, c->ws.Ls); }
+      n_shf = (int)shf.size();
+      d_shf = nullptr;
+      if (n_shf) TRY(up(shf, &d_shf));
+    }
     TRY(tiles(live, [](ssa_ctx* c) { return fuse_long(c) ? 0 : c->ws.nblk_l; }, &t_lg, &n_lg));
     TRY(ritz_tiles(live, &t_rs, &n_rs, &t_rl, &n_rl));
     auto upl = [&](auto& v, auto** d) { return up(v, d); };
@@ -1146,7 +1158,11 @@ struct LzEngine {
     const int steps = rmax == 0 ? 0 : std::min(rmax, std::max(rmin, 8));
     for (int s = 0; s < steps; ++s) {
       run_mv<T>(live[0], mvA, 0);
-      { PhaseScope ps_(PH_SHORT, st); launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st); }
+      {
+        PhaseScope ps_(PH_SHORT, st);
+        launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st);
+        launch_short_fused(d_shf, n_shf, max_ls_f, 0, st);
+      }
       run_mv<T>(live[0], mvAT, 0);
       { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, 0, st); }
     }

@@ -157,6 +157,111 @@ __global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict
   }
 }
 
+// Whole short-side step of one problem in one block (Ls <= SHORT_FUSED_MAX):
+// p = sum of the channel partial products; classical Gram-Schmidt against
+// U[:, 0:j]; a second pass only when the first left a component above a
+// rounding-level fraction of the remaining norm (the criterion of Daniel,
+// Gragg, Kaufman and Stewart); alpha_j = ||p||, u_j = p / alpha_j,
+// B[j, j] = alpha_j.  One launch per step instead of four, and each warp's
+// dot products run over all rows, so the FP64 reductions stay a small part of
+// the FP64 work.
+template <int NT>
+__device__ __forceinline__ void short_dots(const double* __restrict__ U, int64_t ldu, const double* p, int Ls, int j,
+                                           double* c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < j; i += NT / 32) {
+    const double* col = U + ldu * i;
+    // two accumulators: every extra one costs an FP64 add per lane
+    double a0 = 0.0, a1 = 0.0;
+    int t = lane;
+    for (; t + 32 < Ls; t += 64) { a0 = fma(col[t], p[t], a0); a1 = fma(col[t + 32], p[t + 32], a1); }
+    if (t < Ls) a0 = fma(col[t], p[t], a0);
+    const double tot = warp_sum(a0 + a1);
+    if (lane == 0) c[i] = tot;
+  }
+}
+
+// p -= U c over the block's rows; returns this thread's share of ||p||^2
+__device__ __forceinline__ double short_update(const double* __restrict__ U, int64_t ldu, double* p, int Ls, int j,
+                                               const double* c) {
+  double nn = 0.0;
+  for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < j; i += 2) { s0 = fma(U[row + ldu * i], c[i], s0); s1 = fma(U[row + ldu * (i + 1)], c[i + 1], s1); }
+    if (i < j) s0 = fma(U[row + ldu * i], c[i], s0);
+    const double v = p[row] - (s0 + s1);
+    p[row] = v;
+    nn = fma(v, v, nn);
+  }
+  return nn;
+}
+
+constexpr int SHORT_FUSED_NT = 512;
+__global__ void __launch_bounds__(SHORT_FUSED_NT) k_short_fused(const ShortItem* __restrict__ items, int s) {
+  const ShortItem it = items[blockIdx.x];
+  LzState* st = it.st;
+  const int j = st->jc + s;
+  if (j < 0 || lz_skip(st, j)) return;
+  extern __shared__ __align__(16) double sp[];      // p, Ls values
+  __shared__ double c[KMAX + 1];
+  __shared__ double red[32];
+  __shared__ int second;
+  const int Ls = (int)it.Ls;
+  double* p = sp;
+  for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
+    int q = 0;
+    if (it.parts_double) {
+      double a0 = 0.0, a1 = 0.0;
+      const double* pp = (const double*)it.parts + row;
+      for (; q + 1 < it.n_part; q += 2) { a0 += pp[q * it.part_ld]; a1 += pp[(q + 1) * it.part_ld]; }
+      if (q < it.n_part) a0 += pp[q * it.part_ld];
+      p[row] = a0 + a1;
+    } else {
+      // FP32 products: their channel sum in FP32 (the products carry FP32
+      // error already), one conversion; GB300's FP64 pipe is the bound here
+      float a0 = 0.0f, a1 = 0.0f;
+      const float* pp = (const float*)it.parts + row;
+      for (; q + 1 < it.n_part; q += 2) { a0 += pp[q * it.part_ld]; a1 += pp[(q + 1) * it.part_ld]; }
+      if (q < it.n_part) a0 += pp[q * it.part_ld];
+      p[row] = (double)(a0 + a1);
+    }
+  }
+  __syncthreads();
+  short_dots<SHORT_FUSED_NT>(it.U, it.ldu, p, Ls, j, c);
+  __syncthreads();
+  double nn = block_sum(short_update(it.U, it.ldu, p, Ls, j, c), red);
+  __syncthreads();
+  short_dots<SHORT_FUSED_NT>(it.U, it.ldu, p, Ls, j, c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // second pass unless the first left less than thr ||p|| along U: 1e-12
+    // when the products are FP32 (far below their own error), 1e-14 in the
+    // FP64 form
+    const double thr = it.parts_double ? 1e-14 : 1e-12;
+    double cc = 0.0;
+    for (int i = 0; i < j; ++i) cc = fma(c[i], c[i], cc);
+    second = cc > thr * thr * nn;
+  }
+  __syncthreads();
+  if (second) nn = block_sum(short_update(it.U, it.ldu, p, Ls, j, c), red);
+  const double alpha = sqrt(nn);
+  const bool ok = alpha > 1e-200;
+  const double inv = ok ? 1.0 / alpha : 0.0;
+  for (int row = threadIdx.x; row < Ls; row += blockDim.x) it.U[row + it.ldu * j] = p[row] * inv;
+  if (threadIdx.x == 0) {
+    it.B[j + (int64_t)it.ldb * j] = ok ? alpha : 0.0;
+    if (ok) { if (alpha > st->anorm) st->anorm = alpha; }
+    else { st->k = j + 1; st->beta_k = 0.0; st->breakdown = 1; }
+  }
+}
+
+void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st) {
+  if (n <= 0) return;
+  set_max_smem((const void*)k_short_fused);
+  k_short_fused<<<n, SHORT_FUSED_NT, sizeof(double) * (size_t)max_ls, st>>>(items, s); count_launch();
+}
+
 // ------------------------------------------------------------ long side
 __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i) {
   // SplitMix64 output function (Steele, Lea, Flood 2014) -> [-1, 1)

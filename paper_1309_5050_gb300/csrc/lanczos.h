@@ -90,6 +90,10 @@ constexpr int RITZ_RB_SHORT = RITZ_RB<double>();
 template <typename T>
 constexpr int ritz_rb_long() { return RITZ_RB<T>(); }
 void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
+// Problems whose short side has at most SHORT_FUSED_MAX rows: the whole
+// short-side step in one block per problem (items: only those problems).
+constexpr int SHORT_FUSED_MAX = 4096;
+void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st);
 template <typename T>
 void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
 template <typename T>
