@@ -317,6 +317,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--serve-rate", type=float, default=1000.0)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving stream")
     ap.add_argument("--write-traffic", default=None,
                     help="ncu CSV of k_mv1d dram bytes -> profiles/k_mv1d_mssa_traffic.json (no GPU use)")
     ap.add_argument("--traffic-command", default="")
@@ -366,6 +367,16 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     pkg.load()
+    if args.serve_only:
+        # only the serving stream (profiling and latency studies)
+        reqs = W.serving_requests(n=args.serve_requests, rate_hz=args.serve_rate, seed=5 + rank, n_max=SERVE_N_MAX)
+        with Clocks(local) as ck:
+            serving = run_serving(pkg, reqs, args.prec, int(args.serve_budget_gb * (1 << 30)), args.serve_rate)
+        if rank == 0:
+            print(json.dumps({"metric": "serving_requests_per_s", "value": serving["throughput_rps"], "unit": "req/s",
+                              "higher_is_better": True, "serving": serving, "clocks": ck.summary(),
+                              "data": "synthetic"}), flush=True)
+        return 0
     B = args.batch
 
     # inputs: B problems per rank, distinct seeds per rank
