@@ -1351,7 +1351,7 @@ struct RecReq {
 };
 
 template <typename TC, typename TV>
-static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_device) {
+static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_device, bool border = false) {
   typedef TC T;
   ssa_ctx* c0 = cs[0];
   cudaStream_t st = c0->stream;
@@ -1441,6 +1441,32 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         TRY(upload(c0, ri, &d_ri));
         tmp.push_back(d_ri);
         launch_rec1d<T, TV>(d_ri, (int)ri.size(), max_log2Mx, tw, st);
+      }
+      if constexpr (std::is_same<TC, float>::value && std::is_same<TV, float>::value) {
+        if (border) {
+          // low-weight elements by direct FP64 sums (complete series only)
+          std::vector<RecBorderItem> bi;
+          for (int p = 0; p < n; ++p) {
+            ssa_ctx* c = cs[p];
+            if (c->log2My != 0) continue;
+            Workspace& w = c->ws;
+            for (int g = 0; g < req[p].ng; ++g)
+              for (const Channel& h : c->ch) {
+                RecBorderItem b;
+                b.U = (const float*)w.Uo; b.V = (const float*)w.Vo + h.koff; b.ldv = c->K; b.sigma = w.sigma;
+                b.comps = d_flat + start[p][g]; b.ncomp = start[p][g + 1] - start[p][g];
+                b.L = (int32_t)c->L; b.K = (int32_t)h.K.count; b.pad_ = 0;
+                b.out = dout[p] + (size_t)g * c->total + h.data_off;
+                bi.push_back(b);
+              }
+          }
+          if (!bi.empty()) {
+            RecBorderItem* d_bi = nullptr;
+            TRY(upload(c0, bi, &d_bi));
+            tmp.push_back(d_bi);
+            launch_rec_border(d_bi, (int)bi.size(), st);
+          }
+        }
       }
       CU(cudaGetLastError());
     }
@@ -1753,11 +1779,27 @@ static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_
 // fit a CTA (x grids above 8192)
 static int reconstruct_dispatch(ssa_ctx* const* ctxs, int n, const RecReq* req, int on_device) {
   const int prec = ctxs[0]->ws.prec;
-  int max_log2Mx = 0;
-  for (int i = 0; i < n; ++i) max_log2Mx = std::max(max_log2Mx, ctxs[i]->log2Mx);
   if (prec == SSA_PREC_FP64) return reconstruct_T<double, double>(ctxs, n, req, on_device);
-  if (max_log2Mx <= 13) return reconstruct_T<double, float>(ctxs, n, req, on_device);
-  return reconstruct_T<float, float>(ctxs, n, req, on_device);
+  // FP32 form: complete series (dense origins, L and every K_q at least
+  // REC_BORDER_W) take FP32 FFT sums plus direct FP64 sums where the weight
+  // is small; the rest FP64 FFT sums where the grid allows it.
+  std::vector<ssa_ctx*> fc, sc;
+  std::vector<RecReq> fr, sr;
+  int max_log2Mx = 0;
+  for (int i = 0; i < n; ++i) {
+    ssa_ctx* c = ctxs[i];
+    bool fast = c->log2My == 0 && c->log2Mx <= 14 && c->L >= REC_BORDER_W;
+    for (const Channel& h : c->ch) fast = fast && h.K.dense && h.K.count >= REC_BORDER_W;
+    if (fast) { fc.push_back(c); fr.push_back(req[i]); }
+    else { sc.push_back(c); sr.push_back(req[i]); max_log2Mx = std::max(max_log2Mx, c->log2Mx); }
+  }
+  if (!fc.empty()) {
+    const int rc = reconstruct_T<float, float>(fc.data(), (int)fc.size(), fr.data(), on_device, true);
+    if (rc != SSA_OK) return rc;
+  }
+  if (sc.empty()) return SSA_OK;
+  if (max_log2Mx <= 13) return reconstruct_T<double, float>(sc.data(), (int)sc.size(), sr.data(), on_device);
+  return reconstruct_T<float, float>(sc.data(), (int)sc.size(), sr.data(), on_device);
 }
 
 // ============================================================== C ABI

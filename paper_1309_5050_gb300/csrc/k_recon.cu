@@ -157,6 +157,34 @@ __global__ void k_rec_fold(const RecFoldItem* __restrict__ items) {
   }
 }
 
+// One warp per border element p: x~[p] = (1/w_p) sum over the anti-diagonal
+// i + j = p of sum_{c in group} sigma_c U[i, c] V[j, c], in FP64.
+__global__ void __launch_bounds__(256) k_rec_border(const RecBorderItem* __restrict__ items) {
+  const RecBorderItem it = items[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);    // 0 .. 2W-1
+  const int64_t N = (int64_t)it.L + it.K - 1;
+  if (e >= 2 * REC_BORDER_W) return;
+  const int64_t p = e < REC_BORDER_W ? e : N - 1 - (e - REC_BORDER_W);
+  if (p < 0 || p >= N || (e >= REC_BORDER_W && p < REC_BORDER_W)) return;
+  const int64_t i0 = p - it.K + 1 > 0 ? p - it.K + 1 : 0;
+  const int64_t i1 = p < it.L - 1 ? p : it.L - 1;
+  double acc = 0.0;
+  for (int64_t i = i0 + lane; i <= i1; i += 32)
+    for (int q = 0; q < it.ncomp; ++q) {
+      const int c = it.comps[q];
+      acc = fma(it.sigma[c] * (double)it.U[i + (int64_t)it.L * c], (double)it.V[(p - i) + it.ldv * c], acc);
+    }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) it.out[p] = acc / (double)(i1 - i0 + 1);
+}
+
+void launch_rec_border(const RecBorderItem* items, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int warps = 8;
+  k_rec_border<<<dim3((2 * REC_BORDER_W + warps - 1) / warps, n), 32 * warps, 0, st>>>(items); count_launch();
+}
+
 void launch_rec_fold(const RecFoldItem* items, int n, int64_t max_n, cudaStream_t st) {
   if (n <= 0) return;
   const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((max_n + 255) / 256, 1024));

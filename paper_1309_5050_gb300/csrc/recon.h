@@ -46,6 +46,22 @@ void launch_rec1d(const Rec1Item<T, TV>* items, int n, int max_log2Mx, const Cx<
 template <typename T>
 void launch_rec_xinv(const Rec2Item<T>* items, int n, int max_log2Mx, int max_ny, const Cx<T>* tw,
                      cudaStream_t st);
+// Complete series reconstructed with FP32 FFTs: the elements whose weight is
+// below REC_BORDER_W (the first and last REC_BORDER_W of the series) are
+// recomputed by direct FP64 summation over their anti-diagonal -- the FFT's
+// absolute error, divided by a small weight, would dominate there.
+constexpr int REC_BORDER_W = 64;
+struct RecBorderItem {
+  const float* U;              // L x r, column c at U + L c
+  const float* V;              // the channel's slice of V: K x r, column c at V + ldv c
+  int64_t ldv;
+  const double* sigma;
+  const int32_t* comps; int32_t ncomp;
+  int32_t L, K;                // window length and the channel's K (N = L + K - 1)
+  int32_t pad_;
+  double* out;                 // the channel's N outputs of this group
+};
+void launch_rec_border(const RecBorderItem* items, int n, cudaStream_t st);
 struct RecFoldItem {            // long series: segment-image sums -> one group's output
   const double* S;              // 2B x (segments), column-major
   const int32_t* w;             // n weights
