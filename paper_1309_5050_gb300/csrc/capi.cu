@@ -245,7 +245,8 @@ struct ShapeSet {          // a set of grid points as per-column bit rows
 // aB + i, origin (j, b) <-> column bB + j, so X_{aB+i, bB+j} = x[(a+b)B + i + j]
 // = S[i + j, a + b].  Rows and columns past L and K are absent (zero input,
 // output dropped), which is what MapDev::limit expresses.
-constexpr int FOLD_B = 4096;           // segment length: grid 2B = 8192 along x
+constexpr int FOLD_B = 4096;
+constexpr int DECOMP_SPLIT_MIN = 64;   // batches at least this large run as two interleaved halves           // segment length: grid 2B = 8192 along x
 constexpr int FOLD_MIN_LOG2 = 15;      // series needing a 2^15 grid or longer are folded
 
 static MapDev fold_map(int B, int nb, int64_t count) {
@@ -810,16 +811,17 @@ static int finish_set(MvSet<T>& s, Up&& up) {
   return SSA_OK;
 }
 
+// the set's products, on stream st of device dev
 template <typename T>
-static void run_mv(ssa_ctx* c, const MvSet<T>& s, int step) {
-  PhaseScope ps_(PH_MATVEC, c->stream);
+static void run_mv(int dev, const MvSet<T>& s, int step, cudaStream_t st) {
+  PhaseScope ps_(PH_MATVEC, st);
   for (int md = 0; md < MV1_MODES; ++md)
     if (!s.items1[md].empty())
-      launch_mv1d<T>(s.d1[md], (int)s.items1[md].size(), s.lx1[md], step, twiddles<T>(c->device), c->stream, md);
+      launch_mv1d<T>(s.d1[md], (int)s.items1[md].size(), s.lx1[md], step, twiddles<T>(dev), st, md);
   if (!s.items2.empty()) {
     const int n2 = (int)s.items2.size();
     launch_mv2d<T>(s.d2, s.dy2, n2, Tiles{s.t_xf, n2, s.n_xf}, Tiles{s.t_yp, n2, s.n_yp},
-                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(c->device), c->stream);
+                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(dev), st);
   }
 }
 
@@ -1144,37 +1146,58 @@ struct LzEngine {
   // the states are read back.  The chunk runs until the member closest to the
   // end of its cycle gets there (at least 8 steps when others have that many
   // left), so no member waits for a whole cycle of another.
-  int run_chunk() {
+  // number of steps of the next chunk (0 when no member is inside a cycle)
+  int plan_steps() {
     release_chunk();
-    const int nl = (int)live.size();
-    if (!nl) return SSA_OK;
     int rmin = INT32_MAX, rmax = 0;
-    for (int i = 0; i < nl; ++i) {
+    for (size_t i = 0; i < live.size(); ++i) {
       const LzState& h = hst[i];
       if (!h.active || h.svd_done || h.jc >= h.k) continue;
       rmin = std::min(rmin, h.k - h.jc);
       rmax = std::max(rmax, h.k - h.jc);
     }
-    const int steps = rmax == 0 ? 0 : std::min(rmax, std::max(rmin, 8));
-    for (int s = 0; s < steps; ++s) {
-      run_mv<T>(live[0], mvA, 0);
-      {
-        PhaseScope ps_(PH_SHORT, st);
-        launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st);
-        launch_short_fused(d_shf, n_shf, max_ls_f, 0, st);
-      }
-      run_mv<T>(live[0], mvAT, 0);
-      { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, 0, st); }
+    return rmax == 0 ? 0 : std::min(rmax, std::max(rmin, 8));
+  }
+  // one Lanczos step for every member inside a cycle
+  void issue_step() {
+    const int nl = (int)live.size();
+    run_mv<T>(device, mvA, 0, st);
+    {
+      PhaseScope ps_(PH_SHORT, st);
+      launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st);
+      launch_short_fused(d_shf, n_shf, max_ls_f, 0, st);
     }
+    run_mv<T>(device, mvAT, 0, st);
+    { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, 0, st); }
+  }
+  // small SVDs of the members whose cycle ended, and the state read-back (async)
+  int finish_chunk_async() {
+    const int nl = (int)live.size();
     { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
     CU(cudaGetLastError());
     k_gather_states<<<1, 128, 0, st>>>(d_stp, nl, d_stg); count_launch();
     CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
+    return SSA_OK;
+  }
+  int finish_chunk_sync() {
+    const int nl = (int)live.size();
     CU(cudaStreamSynchronize(st));
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
     if ((mvA.n1() || mvAT.n1()) && mv_async_timeouts(st) != 0)
       return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
     return SSA_OK;
+  }
+  // One chunk: every member inside a cycle advances up to `steps` Lanczos
+  // steps (its own jc); members whose cycle is complete get their small SVD;
+  // the states are read back.  The chunk runs until the member closest to the
+  // end of its cycle gets there (at least 8 steps when others have that many
+  // left), so no member waits for a whole cycle of another.
+  int run_chunk() {
+    if (live.empty()) return SSA_OK;
+    const int steps = plan_steps();
+    for (int s = 0; s < steps; ++s) issue_step();
+    TRY(finish_chunk_async());
+    return finish_chunk_sync();
   }
   bool any_active() const {
     for (auto& h : hst) if (h.active) return true;
@@ -1304,35 +1327,93 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
     }
   std::vector<int> rc;
   TRY(prepare_members<T>(cs, n, ps, st, rc));
-  LzEngine<T> eng;
-  eng.st = st;
-  eng.device = c0->device;
+  // Large batches run as two engines on two streams whose launches are issued
+  // alternately: one half's FP64-bound kernels (Gram-Schmidt, small SVD) then
+  // share the SMs with the other half's FP32 products.  Each problem's
+  // arithmetic is the same either way.
+  int nok = 0;
+  for (int i = 0; i < n; ++i) nok += rc[i] == SSA_OK;
+  const int ng = nok >= DECOMP_SPLIT_MIN ? 2 : 1;
+  LzEngine<T> engs[2];
+  cudaStream_t gst[2] = {st, st};
+  cudaEvent_t ready = nullptr;
+  if (ng == 2) {
+    CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CU(cudaEventRecord(ready, st));
+    for (int g = 0; g < 2; ++g) {
+      CU(cudaStreamCreateWithFlags(&gst[g], cudaStreamNonBlocking));
+      CU(cudaStreamWaitEvent(gst[g], ready, 0));
+    }
+  }
+  int placed = 0;
   for (int i = 0; i < n; ++i) {
     if (status) status[i] = rc[i];
-    if (rc[i] == SSA_OK) eng.add(cs[i], ps[i].seed);
-    else cs[i]->ws.done = false;
+    if (rc[i] == SSA_OK) {
+      LzEngine<T>& e = engs[(ng == 2 && placed >= nok / 2) ? 1 : 0];
+      e.add(cs[i], ps[i].seed);
+      ++placed;
+    } else {
+      cs[i]->ws.done = false;
+    }
   }
   int rc_all = SSA_OK;
-  if (!eng.live.empty()) {
-    TRY(eng.build());
-    TRY(eng.start_fresh());
-    while (eng.any_active()) {
-      TRY(eng.run_chunk());
-      TRY(eng.restart_active());
+  int rc_run = SSA_OK;
+  auto run = [&]() -> int {
+    for (int g = 0; g < ng; ++g) {
+      engs[g].st = gst[g];
+      engs[g].device = c0->device;
+      if (engs[g].live.empty()) continue;
+      TRY(engs[g].build());
+      TRY(engs[g].start_fresh());
     }
-    std::vector<int> all(eng.live.size());
-    for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
-    TRY(eng.retire(all));
-    CU(cudaStreamSynchronize(st));
-    for (size_t i = 0; i < eng.live.size(); ++i) {
-      const LzState& h = eng.hst[i];
-      if (!h.converged && !h.breakdown) {
-        const int idx = (int)(std::find(cs, cs + n, eng.live[i]) - cs);
-        if (status) status[idx] = SSA_ENOTCONV;
-        if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
+    for (;;) {
+      bool any = false;
+      for (int g = 0; g < ng; ++g) any |= !engs[g].live.empty() && engs[g].any_active();
+      if (!any) break;
+      int steps[2] = {0, 0}, smax = 0;
+      for (int g = 0; g < ng; ++g)
+        if (!engs[g].live.empty()) { steps[g] = engs[g].plan_steps(); smax = std::max(smax, steps[g]); }
+      for (int s2 = 0; s2 < smax; ++s2)
+        for (int g = 0; g < ng; ++g)
+          if (s2 < steps[g]) engs[g].issue_step();
+      for (int g = 0; g < ng; ++g)
+        if (!engs[g].live.empty()) TRY(engs[g].finish_chunk_async());
+      for (int g = 0; g < ng; ++g)
+        if (!engs[g].live.empty()) TRY(engs[g].finish_chunk_sync());
+      for (int g = 0; g < ng; ++g)
+        if (!engs[g].live.empty()) TRY(engs[g].restart_active());
+    }
+    for (int g = 0; g < ng; ++g) {
+      LzEngine<T>& eng = engs[g];
+      if (eng.live.empty()) continue;
+      std::vector<int> all(eng.live.size());
+      for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
+      TRY(eng.retire(all));
+      CU(cudaStreamSynchronize(eng.st));
+      for (size_t i = 0; i < eng.live.size(); ++i) {
+        const LzState& h = eng.hst[i];
+        if (!h.converged && !h.breakdown) {
+          const int idx = (int)(std::find(cs, cs + n, eng.live[i]) - cs);
+          if (status) status[idx] = SSA_ENOTCONV;
+          if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
+        }
       }
     }
+    return SSA_OK;
+  };
+  rc_run = run();
+  if (ng == 2) {
+    // later work on the batch stream (reconstruction) follows both halves;
+    // the engines free their item arrays on their streams before those go
+    for (int g = 0; g < 2; ++g) {
+      engs[g].release_items();
+      cudaStreamSynchronize(gst[g]);
+      cudaStreamDestroy(gst[g]);
+      engs[g].st = st;
+    }
+    cudaEventDestroy(ready);
   }
+  if (rc_run != SSA_OK) return rc_run;
   for (auto e : evs) cudaEventDestroy(e);
   for (int i = 0; i < n; ++i)
     if (rc[i] != SSA_OK && rc_all == SSA_OK) rc_all = rc[i];
@@ -1644,7 +1725,7 @@ static int matvec_T(ssa_ctx* c, int transpose, const double* in, double* out, in
                      hs ? (Cx<T>*)g2 + q * hs : nullptr, nullptr));
   }
   TRY(finish_set(s, [&](auto& v, auto** d) { return upload(c, v, d); }));
-  run_mv<T>(c, s, 0);
+  run_mv<T>(c->device, s, 0, c->stream);
   k_sum_parts_to_double<T><<<grid1(nout), 256, 0, c->stream>>>(dparts, nparts, nout, nout, dres); count_launch();
   CU(cudaGetLastError());
   if (!on_device) CU(cudaMemcpyAsync(out, dres, sizeof(double) * nout, cudaMemcpyDeviceToHost, c->stream));

@@ -205,6 +205,22 @@ def test_batch_equals_single():
         np.testing.assert_allclose(s.sigma(), ref, rtol=1e-6)
 
 
+def test_large_batch_runs_in_two_halves_with_single_results():
+    """Batches of 64 problems or more run as two interleaved halves on two
+    streams; every problem still gets the result it gets alone."""
+    cases = [case_1d(300 + 7 * i, 90, 40 + i)[0] for i in range(70)]
+    singles = []
+    for s in cases[:6] + cases[-6:]:
+        s.decompose(5, "fp32", seed=3)
+        singles.append((s.sigma(), s.reconstruct([[0], [1, 2]])))
+    pkg.decompose_batch(cases, 5, "fp32", seed=3)
+    for s, (ref, rec) in zip(cases[:6] + cases[-6:], singles):
+        np.testing.assert_allclose(s.sigma(), ref, rtol=1e-12, atol=0)
+        got = s.reconstruct([[0], [1, 2]])
+        for a, b in zip(got, rec):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * float(np.max(np.abs(b))))
+
+
 # ------------------------------------------------------------------ errors
 def test_error_codes():
     lib = pkg.load()
