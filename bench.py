@@ -241,8 +241,10 @@ def mv1d_traffic(batch):
             d = json.load(f)
     except Exception:
         return None, "no committed capture"
+    if d.get("sources") != MV1D_SOURCES:
+        return None, "capture keyed to other sources"
     h = hashlib.sha256()
-    for rel in d.get("sources", []):
+    for rel in MV1D_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     if h.hexdigest() != d.get("sources_sha256"):
