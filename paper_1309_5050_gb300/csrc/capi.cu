@@ -303,6 +303,8 @@ struct Workspace {             // Lanczos + results, per precision
   int n_part_s = 1, n_part_l = 1;
   double* B = nullptr; double* P = nullptr; double* Q = nullptr; double* sig = nullptr;
   double* colscale = nullptr;
+  void* uz = nullptr;          // forward transforms of u_j per channel grid size (fused members)
+  int64_t uz_off[32] = {};     // element offset of the transform for grid 2^log2M (-1: none)
   void* Cs = nullptr;          // scaled long-side Ritz coefficients, (k + 2) x ritz_ldcs(k) of T
   double* cpa = nullptr; double* cpb = nullptr; double* np_s = nullptr; double* np_l = nullptr;
   void* g1 = nullptr; void* g2 = nullptr;
@@ -763,6 +765,7 @@ static MvItem<T> make_mv(ssa_ctx* c, const Channel& h, bool XT, VecRef in, int i
   m.mout = XT ? h.K.dev() : c->Lset.dev();
   m.g1 = g1; m.g2 = g2; m.st = st;
   m.lV = nullptr; m.lld = 0; m.lB = nullptr; m.lcolscale = nullptr; m.lnpart = nullptr; m.lldb = 0; m.lslot = 0;
+  m.zin = nullptr;
   m.log2Mx = h.log2M; m.log2My = c->log2My;
   m.in_type = in_type;
   m.y_in_hi = XT ? c->ey : h.cy;
@@ -835,6 +838,25 @@ static int default_k(int r, int64_t L, int64_t K, int req) {
   return (int)k;
 }
 
+// The long-side step runs inside the X^T u series products (and u's forward
+// transform is shared by the channels) when the long side is the origin side
+// (each channel's product is its own slice of the long vector) and every
+// slice is a dense range.
+static size_t uz_bound(const ssa_ctx* c) {     // complex values of all distinct grids
+  bool seen[32] = {};
+  size_t t = 0;
+  for (auto& h : c->ch)
+    if (!seen[h.log2M]) { seen[h.log2M] = true; t += size_t(1) << (h.log2M - 1); }
+  return t;
+}
+
+static bool member_fuses_long(const ssa_ctx* c, bool swapped) {
+  if (swapped || c->log2My != 0) return false;
+  for (auto& h : c->ch)
+    if (!h.K.dense) return false;
+  return true;
+}
+
 template <typename T>
 static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   w = Workspace();
@@ -857,7 +879,8 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
                   rnd256(cz * w.Kl) + rnd256(cz * w.Ls * w.n_part_s) + rnd256(cz * w.Kl * w.n_part_l) +
                   3 * rnd256(8 * k1 * k1) + 2 * rnd256(8 * (k1 + 1)) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
                   rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)std::max<int64_t>(w.nblk_l, (int64_t)c->ch.size())) + rnd256(cz * c->L * w.r) +
-                  rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r) + rnd256(cz * (k1 + 1) * ritz_ldcs(w.k));
+                  rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r) + rnd256(cz * (k1 + 1) * ritz_ldcs(w.k)) +
+                  rnd256(2 * cz * uz_bound(c));
     if (c->log2My > 0) {
       const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
       need += 2 * rnd256(2 * cz * hs * c->ch.size());
@@ -878,6 +901,13 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->allocT(&w.Q, (size_t)(w.k + 1) * w.k));
   TRY(c->allocT(&w.sig, (size_t)w.k));
   TRY(c->allocT(&w.colscale, (size_t)w.k + 2));
+  for (auto& o : w.uz_off) o = -1;
+  if (member_fuses_long(c, w.swapped)) {
+    int64_t tot = 0;
+    for (auto& h : c->ch)
+      if (w.uz_off[h.log2M] < 0) { w.uz_off[h.log2M] = tot; tot += int64_t(1) << (h.log2M - 1); }
+    TRY(c->alloc(&w.uz, sizeof(Cx<T>) * (size_t)tot));
+  }
   TRY(c->alloc(&w.Cs, sizeof(T) * (k1 + 1) * ritz_ldcs(w.k)));
   TRY(c->allocT(&w.cpa, (size_t)w.nblk_s * (KMAX + 1)));
   TRY(c->allocT(&w.cpb, (size_t)w.nblk_s * (KMAX + 1)));
@@ -928,6 +958,9 @@ struct LzEngine {
   ShortItem* d_shf = nullptr;      // members whose short step runs in one block
   int n_shf = 0;
   int64_t max_ls_f = 1;
+  UzItem<T>* d_uz = nullptr;       // shared forward transforms of u_j
+  int n_uz = 0, max_uz_log2 = 1;
+  bool share_u = false;            // X^T u products take u's transform from k_uspec
   MvSet<T> mvA, mvAT;
   int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1;
   int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
@@ -978,12 +1011,7 @@ struct LzEngine {
   // The long-side step runs inside the X^T u series products when the long
   // side is the origin side (each channel's product is its own slice of the
   // long vector) and every slice is a dense range.
-  static bool fuse_long(ssa_ctx* c) {
-    if (c->ws.swapped || c->log2My != 0) return false;
-    for (auto& h : c->ch)
-      if (!h.K.dense) return false;
-    return true;
-  }
+  static bool fuse_long(ssa_ctx* c) { return member_fuses_long(c, c->ws.swapped); }
 
   ShortItem short_item(ssa_ctx* c) {
     Workspace& w = c->ws;
@@ -1037,6 +1065,8 @@ struct LzEngine {
     if (!dirty) return SSA_OK;
     dirty = false;
     release_items();
+    // one extra launch per step pays off once enough products share it
+    share_u = live.size() >= 32;
     std::vector<ShortItem> sh; std::vector<LongItem<T>> lg; std::vector<SvdItem> sv;
     std::vector<RitzItem<T>> rz; std::vector<LzState*> stp;
     max_blk_s = max_blk_l = max_k = max_r = 1;
@@ -1067,6 +1097,7 @@ struct LzEngine {
           if (fuse_long(c)) {
             mt.lV = (T*)w.V; mt.lld = w.Kl; mt.lB = w.B; mt.lcolscale = w.colscale; mt.lnpart = w.np_l;
             mt.lldb = w.k; mt.lslot = (int32_t)q;
+            if (share_u) mt.zin = (const Cx<T>*)w.uz + w.uz_off[h.log2M];
           }
           mvAT.add(mt);
         } else {
@@ -1095,6 +1126,25 @@ struct LzEngine {
     if (live.empty()) return SSA_OK;
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
     TRY(tiles(live, [](ssa_ctx* c) { return c->ws.Ls <= SHORT_FUSED_MAX ? 0 : c->ws.nblk_s; }, &t_sh, &n_sh));
+    {
+      std::vector<UzItem<T>> uz;
+      max_uz_log2 = 1;
+      for (ssa_ctx* c : live) {
+        if (!share_u || !fuse_long(c)) continue;
+        Workspace& w = c->ws;
+        for (int lg = 0; lg < 32; ++lg)
+          if (w.uz_off[lg] >= 0) {
+            UzItem<T> z;
+            z.U = w.U; z.ldu = w.Ls; z.st = w.st; z.L = (int32_t)c->L; z.log2M = lg;
+            z.z = (Cx<T>*)w.uz + w.uz_off[lg];
+            uz.push_back(z);
+            max_uz_log2 = std::max(max_uz_log2, lg);
+          }
+      }
+      n_uz = (int)uz.size();
+      d_uz = nullptr;
+      if (n_uz) TRY(up(uz, &d_uz));
+    }
     {
       std::vector<ShortItem> shf;
       max_ls_f = 1;
@@ -1166,6 +1216,10 @@ struct LzEngine {
       PhaseScope ps_(PH_SHORT, st);
       launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st);
       launch_short_fused(d_shf, n_shf, max_ls_f, 0, st);
+    }
+    {
+      PhaseScope ps_(PH_MATVEC, st);
+      launch_uspec<T>(d_uz, n_uz, max_uz_log2, 0, twiddles<T>(device), st);
     }
     run_mv<T>(device, mvAT, 0, st);
     { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, 0, st); }

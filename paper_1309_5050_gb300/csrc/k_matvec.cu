@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
   constexpr bool IN_MAPPED = (MODE & MV1_IN_MAPPED) != 0;
   constexpr bool OUT_FUSED = (MODE & MV1_OUT_FUSED) != 0;
   constexpr bool OUT_MAPPED = (MODE & MV1_OUT_MAPPED) != 0;
+  constexpr bool IN_ZSPEC = (MODE & MV1_IN_ZSPEC) != 0;
   typedef typename std::conditional<IN_DOUBLE, double, T>::type TI;
   const MvItem<T> it = items[blockIdx.x];
   if (item_skip<T>(it.st, s)) return;
@@ -162,22 +163,33 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
   XSmem<T> sm(smem, H, it.log2Mx, tw, true);
   // H complex values = a multiple of 16 bytes; the last value comes by a plain load
   const uint32_t bulk = (uint32_t)(H * sizeof(Cx<T>));
+  const int nst = fft_io_stages(log2H);
+  // forward result Z (written by the last forward stage, or copied in) and
+  // the other buffer X (twisted product); a copied-in Z sits at the 16-byte
+  // aligned start of the shared block
+  Cx<T>* Z = (IN_ZSPEC || !(nst & 1)) ? sm.A : sm.B;
+  Cx<T>* X = (Z == sm.A) ? sm.B : sm.A;
   if (threadIdx.x == 0) {
     mbar_init(&bar);
-    bulk_load(sm.S, it.xh, bulk, &bar);
+    if constexpr (IN_ZSPEC) {
+      mbar_arrive_expect(&bar, 2 * bulk);
+      bulk_copy(sm.S, it.xh, bulk, &bar);
+      bulk_copy(Z, it.zin, bulk, &bar);
+    } else {
+      bulk_load(sm.S, it.xh, bulk, &bar);
+    }
   }
   const Cx<T> last = it.xh[H];
-  const int64_t ioff = vec_elem_off(it.in, s);
-  const T isc = in_scale_of(it, s);
-  const int nst = fft_io_stages(log2H);
-  Cx<T>* Z = (nst & 1) ? sm.B : sm.A;   // forward result (written by the last stage)
-  Cx<T>* X = (nst & 1) ? sm.A : sm.B;   // the other buffer: twisted product
   auto zout = [Z](int base, int stride, auto& v) {
     constexpr int R = sizeof(v) / sizeof(v[0]);
 #pragma unroll
     for (int r = 0; r < R; ++r) Z[base + r * stride] = v[r];
   };
-  if constexpr (!IN_MAPPED) {
+  if constexpr (IN_ZSPEC) {
+    __syncthreads();                    // twiddle table and barrier initialised
+  } else if constexpr (!IN_MAPPED) {
+    const int64_t ioff = vec_elem_off(it.in, s);
+    const T isc = in_scale_of(it, s);
     const int64_t xe = imin64((int64_t)it.min.bx, it.min.limit);
     __syncthreads();                    // twiddle table
     const TI* src = (const TI*)it.in.base + ioff;
@@ -187,6 +199,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
     };
     block_fft_io<T, false>(in, zout, sm.A, sm.B, log2H, sm.tab, log2H + 1);
   } else {
+    const int64_t ioff = vec_elem_off(it.in, s);
+    const T isc = in_scale_of(it, s);
     load_col<T, TI>(reinterpret_cast<T*>(sm.A), 2 * H, (const TI*)it.in.base + ioff, it.min, 0, sm.pre, sm.wt, isc);
     __syncthreads();
     const Cx<T>* A = sm.A;
@@ -433,6 +447,41 @@ int mv_async_timeouts(cudaStream_t st) {
   return h;
 }
 
+// Forward transform of u_j = U[:, jc + s] (window side, L FP64 values) on a
+// 2^log2M grid, the H packed values before the untwist, straight to global
+// memory from the last stage (one block per problem and grid size).
+template <typename T>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_uspec(const UzItem<T>* __restrict__ items, int s,
+                                                                        const Cx<T>* __restrict__ tw) {
+  const UzItem<T> it = items[blockIdx.x];
+  if (item_skip<T>(it.st, s)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int log2H = it.log2M - 1;
+  XSmem<T> sm(smem, 1 << log2H, it.log2M, tw, false);
+  __syncthreads();
+  const double* src = it.U + it.ldu * (int64_t)(it.st->jc + s);
+  const int64_t xe = it.L;
+  auto in = [src, xe](int i) {
+    const int64_t x = 2 * (int64_t)i;
+    return cx(x < xe ? (T)src[x] : T(0), x + 1 < xe ? (T)src[x + 1] : T(0));
+  };
+  Cx<T>* z = it.z;
+  auto out = [z](int base, int stride, auto& v) {
+    constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[base + r * stride] = v[r];
+  };
+  block_fft_io<T, false>(in, out, sm.A, sm.B, log2H, sm.tab, log2H + 1);
+}
+
+template <typename T>
+void launch_uspec(const UzItem<T>* items, int n, int max_log2M, int s, const Cx<T>* tw, cudaStream_t st) {
+  if (n <= 0) return;
+  const size_t sm = xsmem_bytes(max_log2M, sizeof(Cx<T>));
+  set_max_smem((const void*)k_uspec<T>);
+  k_uspec<T><<<n, 512, sm, st>>>(items, s, tw); count_launch();
+}
+
 template <typename T, int MODE>
 static void launch_mv1d_mode(const MvItem<T>* items, int n, size_t sm, int s, const Cx<T>* tw, cudaStream_t st) {
   set_max_smem((const void*)k_mv1d<T, MODE>);
@@ -448,6 +497,7 @@ void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<
     SSA_MV1(0) SSA_MV1(1) SSA_MV1(2) SSA_MV1(3)
     SSA_MV1(4) SSA_MV1(5) SSA_MV1(6) SSA_MV1(7)
     SSA_MV1(8) SSA_MV1(9) SSA_MV1(10) SSA_MV1(11)
+    SSA_MV1(16) SSA_MV1(20) SSA_MV1(24)
 #undef SSA_MV1
     default: break;
   }
@@ -488,6 +538,7 @@ void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Til
 
 #define INST(T)                                                                                       \
   template void launch_mv1d<T>(const MvItem<T>*, int, int, int, const Cx<T>*, cudaStream_t, int);     \
+  template void launch_uspec<T>(const UzItem<T>*, int, int, int, const Cx<T>*, cudaStream_t);          \
   template void launch_mv2d<T>(const MvItem<T>*, const YItem<T>*, int, Tiles, Tiles, Tiles, int, int,  \
                                int, const Cx<T>*, cudaStream_t);                                      \
   template void launch_ypass<T>(const YItem<T>*, Tiles, int, int, int, const Cx<T>*, cudaStream_t);    \

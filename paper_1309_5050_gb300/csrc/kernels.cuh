@@ -66,16 +66,33 @@ struct MvItem {
   T* lV; int64_t lld;
   const double* lB; const double* lcolscale; double* lnpart;
   int32_t lldb, lslot;
+  // Non-null: the input's forward transform (H values before the untwist),
+  // computed once per problem and grid size by k_uspec, replaces the forward
+  // FFT of this product.
+  const Cx<T>* zin;
+};
+
+// Forward transform of the window-side vector u_j (column jc + s of the FP64
+// short basis) on a grid of 2^log2M, shared by every channel of that size.
+template <typename T>
+struct UzItem {
+  const double* U; int64_t ldu;
+  const LzState* st;
+  int32_t L, log2M;
+  Cx<T>* z;                 // H values
 };
 
 // Code path of a series product (one k_mv1d instantiation per value): the
 // input is double (else T), the input map is bit-mapped (else a dense range),
 // the output is the fused long-side step, or bit-mapped (else a dense range).
-enum : int { MV1_IN_DOUBLE = 1, MV1_IN_MAPPED = 2, MV1_OUT_FUSED = 4, MV1_OUT_MAPPED = 8, MV1_MODES = 12 };
+// MV1_IN_ZSPEC: the input arrives as its precomputed forward transform.
+enum : int { MV1_IN_DOUBLE = 1, MV1_IN_MAPPED = 2, MV1_OUT_FUSED = 4, MV1_OUT_MAPPED = 8, MV1_IN_ZSPEC = 16,
+             MV1_MODES = 25 };
 template <typename T>
 inline int mv1d_mode(const MvItem<T>& m) {
-  return (m.in_type == 1 ? MV1_IN_DOUBLE : 0) | (m.min.dense ? 0 : MV1_IN_MAPPED) |
-         (!m.mout.dense ? MV1_OUT_MAPPED : (m.lV ? MV1_OUT_FUSED : 0));
+  const int out = !m.mout.dense ? MV1_OUT_MAPPED : (m.lV ? MV1_OUT_FUSED : 0);
+  if (m.zin) return MV1_IN_ZSPEC | out;
+  return (m.in_type == 1 ? MV1_IN_DOUBLE : 0) | (m.min.dense ? 0 : MV1_IN_MAPPED) | out;
 }
 
 // Raw data to half spectrum (step 1 of the matvec algorithms, precomputed).

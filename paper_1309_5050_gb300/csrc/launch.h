@@ -28,6 +28,10 @@ template <typename T> const Cx<T>* twiddles(int device);
 // Series products of one code path `mode` (mv1d_mode): every item shares it.
 template <typename T>
 void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<T>* tw, cudaStream_t st, int mode);
+// Forward transforms of the window-side vector shared by the X^T u products.
+template <typename T>
+void launch_uspec(const UzItem<T>* items, int n, int max_log2M, int s, const Cx<T>* tw, cudaStream_t st);
+
 // Bulk-copy waits in the series product that gave up since the last call
 // (each sets a device counter instead of spinning on); read and reset, -1 on
 // a CUDA error.  Synchronises the stream.
