@@ -402,7 +402,7 @@ def main():
         ps = pkg.embed_multi_batch(inputs, [l for l, _ in probs], CFG["L"], stream=stream)
         pkg.decompose_batch(ps, CFG["rank"], prec, krylov_dim=args.krylov_dim)
         inf0 = ps[0].info()
-        restarts.append((inf0["restarts"], inf0["jacobi_sweeps"]))
+        restarts.append((inf0["restarts"], inf0["jacobi_sweeps"], inf0["jacobi_sweeps_fp32"]))
         if outs[0].is_cuda:
             pkg.reconstruct_batch(ps, GROUPS, residual=True, outs=outs)
         else:
@@ -522,7 +522,7 @@ def main():
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
                 "gpu_launches": int(launches),
                 "lanczos": {"krylov_dim": ps_info["krylov_dim"], "restarts_first_problem": restarts[-1][0],
-                            "last_jacobi_sweeps_first_problem": restarts[-1][1]},
+                            "last_jacobi_sweeps_first_problem": {"fp64": restarts[-1][1], "fp32": restarts[-1][2]}},
                 "phases_ms": {k: v[0] / args.steps for k, v in prof.items()},
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -103,8 +103,8 @@ typedef struct {
   int64_t fft_mx, fft_my;  /* FFT grid */
   double max_residual;     /* max_i ||X^T u_i - sigma_i v_i|| / sigma_1 (Lanczos estimate) */
   int64_t device_bytes;    /* device memory held by the context */
-  int32_t jacobi_sweeps;   /* sweeps of the last small SVD (one-sided Jacobi) */
-  int32_t pad_;
+  int32_t jacobi_sweeps;   /* FP64 sweeps of the last small SVD (one-sided Jacobi) */
+  int32_t jacobi_sweeps_fp32;  /* FP32 sweeps that found its rotations first */
 } ssa_info;
 
 /*

@@ -169,7 +169,7 @@ template <> const Cx<double>* twiddles<double>(int dev) { return g_tables[dev].t
 
 // small helper kernels of the driver
 __global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int max_restarts, int full) {
-  st->full = full; st->sweeps = 0;
+  st->full = full; st->sweeps = 0; st->sweeps32 = 0;
   st->jc = 0; st->svd_done = 0; st->k = k; st->r = r; st->kk = kk; st->active = 1; st->converged = 0;
   st->nconv = 0; st->breakdown = 0; st->restarts = 0; st->max_restarts = max_restarts;
   st->beta_k = 0.0; st->anorm = 0.0; st->tol = tol; st->sigma1 = 0.0; st->maxres = 0.0;
@@ -2130,6 +2130,7 @@ int ssa_get_info(const ssa_ctx* c, ssa_info* info) {
     info->converged = c->ws.host_st.converged || c->ws.host_st.breakdown; info->prec = c->ws.prec;
     info->max_residual = c->ws.host_st.maxres;
     info->jacobi_sweeps = c->ws.host_st.sweeps;
+    info->jacobi_sweeps_fp32 = c->ws.host_st.sweeps32;
   }
   return SSA_OK;
 }

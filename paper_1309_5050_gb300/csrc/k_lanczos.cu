@@ -8,6 +8,7 @@
 #include <type_traits>
 #include "lanczos.h"
 #include "launch.h"
+#include "tma.cuh"
 
 namespace ssa {
 
@@ -164,7 +165,11 @@ __global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict
 // Gragg, Kaufman and Stewart); alpha_j = ||p||, u_j = p / alpha_j,
 // B[j, j] = alpha_j.  One launch per step instead of four, and each warp's
 // dot products run over all rows, so the FP64 reductions stay a small part of
-// the FP64 work.
+// the FP64 work.  The long side is not re-orthogonalised, so U must stay
+// orthogonal to FP64 rounding (the loss in V grows with U's times the
+// condition of B): the component left along U is measured, not bounded from
+// the norms -- a norm-ratio test let ghost singular values through on long
+// noisy series.
 template <int NT>
 __device__ __forceinline__ void short_dots(const double* __restrict__ U, int64_t ldu, const double* p, int Ls, int j,
                                            double* c) {
@@ -358,37 +363,220 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
 // A = U_k [B | beta_k e_k] V_{k+1}^T holds exactly, so W gets that extra
 // column and the singular values are exact (no restart needed).
 //
-// GB300 runs FP64 at two lanes per clock per SM, so the work is laid out to
-// spend FP64 only where it counts: one thread owns one column pair of a
-// round-robin round (dot product, rotation parameters, column update), the
-// squared column norms are carried by the exact Jacobi update
-// (a' = a - t g, b' = b + t g) and refreshed once per sweep, and no rotation
-// is accumulated (Q is formed once at the end).
+// GB300 runs FP64 at two lanes per clock per SM and FP32 at 128, so the
+// rotations are found in FP32 and FP64 only polishes them:
+//  1. FP32 Jacobi on a copy of W0 scaled by a power of two, accumulating the
+//     rotations in V (nc x nc), until every pair's cosine is at the rounding
+//     level of an FP32 dot product;
+//  2. one Newton-Schulz step makes V orthogonal in FP64: V' = V - V E / 2
+//     with E = V^T V - I summed in FP64 (products of FP32 entries are exact
+//     in FP64); V E is of the size of E and needs only FP32.  This leaves
+//     |V'^T V' - I| ~ 3|E|^2 / 4;
+//  3. W = W0 V' in FP64 (W0 is upper triangular with a few nonzeros per
+//     row: bidiagonal plus the restart column), and the FP64 Jacobi below
+//     runs on W.  Its columns start orthogonal to FP32 level, so it needs
+//     about two sweeps and a check sweep where it needs nine from W0.
+// W0 V' J = P Sigma with V' J orthogonal to FP64 rounding is an SVD of W0,
+// so sigma, P and Q are FP64-accurate whatever the FP32 steps did (they only
+// decide how many FP64 sweeps remain).
+//
+// In the FP64 sweeps one thread owns one column pair of a round-robin round
+// (dot product, rotation parameters, column update), the squared column norms
+// are carried by the exact Jacobi update (a' = a - t g, b' = b + t g) and
+// refreshed once per sweep, and no rotation is accumulated (Q is formed once
+// at the end).
 // Outputs: sig (k), P (k x k, ld ldb), Q ((k+1) x k, ld ldb+1; row k is zero
 // unless the extra column was used).
-__global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items) {
+__device__ __forceinline__ double block_max(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+  return t;
+}
+
+// column pair of team t in round rd of the round-robin order over n2 slots
+// (n2 even; slots >= nc are empty): -1 when the team has no pair
+__device__ __forceinline__ void jacobi_pair(int t, int rd, int n2, int nc, int& a, int& b) {
+  a = b = -1;
+  if (t >= n2 / 2) return;
+  const int sa = t, sb = n2 - 1 - t;
+  a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
+  b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
+  if (a >= nc || b >= nc) a = b = -1;
+}
+
+__global__ void __launch_bounds__(256, 2) k_bsvd(const SvdItem* __restrict__ items) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
   if (!st->active || st->jc < st->k || st->svd_done) return;   // only at the end of a cycle, once
   const int k = st->k, ld = it.ldb;
   const bool aug = st->full != 0;
   const int nc = aug ? k + 1 : k;       // columns of W
-  const int cs = k | 1;                 // odd column stride: lane-per-pair accesses spread over banks
+  const BsvdLayout lay = bsvd_layout(k, nc);
+  const int cs = lay.cs, lv = lay.lv, s0 = lay.s0;
   extern __shared__ __align__(16) double sm[];
-  double* W = sm;                        // column c at W + c*cs (k rows)
+  float* W32 = reinterpret_cast<float*>(sm);                    // step 1, column c at W32 + c*cs
+  double* V64 = sm;                                             // step 2, column c at V64 + c*s0
+  float* V32 = reinterpret_cast<float*>(sm + (size_t)nc * s0);  // column c at V32 + c*lv
+  float* E32 = V32 + (size_t)nc * lv;
+  double* W = sm + (size_t)nc * s0;                              // step 3 on, over V32 and E32; column c at W + c*cs
   __shared__ int rotated;
   __shared__ double nrm2[KMAX + 2];
   __shared__ double nrm[KMAX + 2];
+  __shared__ float nrm2f[KMAX + 2];
   __shared__ int order[KMAX + 2];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int team = lane >> 2, q = lane & 3;
+  const int nteams = (blockDim.x >> 5) * 8;
+  const int n2 = nc + (nc & 1);
+
+  // ---- step 1: FP32 Jacobi with accumulated rotations
+  double mx = 0.0;
   for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
     const int c = e / k, i = e - c * k;
-    double v;
-    if (c < k) v = it.B[i + (int64_t)ld * c];
-    else v = (i == k - 1) ? st->beta_k : 0.0;
-    W[c * cs + i] = v;
+    const double v = (c < k) ? it.B[i + (int64_t)ld * c] : ((i == k - 1) ? st->beta_k : 0.0);
+    mx = fmax(mx, fabs(v));
+  }
+  mx = block_max(mx, red);
+  double scale = 1.0;
+  if (mx > 0.0) {
+    int ex = ((__double2hiint(mx) >> 20) & 0x7ff) - 1023;
+    ex = ex > 1022 ? 1022 : ex;
+    scale = __hiloint2double((1023 - ex) << 20, 0);          // 2^-ex: entries below 2 in magnitude
+  }
+  for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    const double v = (c < k) ? it.B[i + (int64_t)ld * c] : ((i == k - 1) ? st->beta_k : 0.0);
+    W32[c * cs + i] = (float)(v * scale);
+  }
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+    const int c = e / nc, m = e - c * nc;
+    V32[c * lv + m] = (m == c) ? 1.0f : 0.0f;
   }
   __syncthreads();
-  const int n2 = nc + (nc & 1);
+  const float tol32 = 1.1920929e-7f * (float)(k > 8 ? k : 8);
+  int sweeps32 = 0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    sweeps32 = sweep + 1;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const float* w = W32 + c * cs;
+      float a0 = 0.0f, a1 = 0.0f;
+      int i = 0;
+      for (; i + 1 < k; i += 2) { a0 = fmaf(w[i], w[i], a0); a1 = fmaf(w[i + 1], w[i + 1], a1); }
+      if (i < k) a0 = fmaf(w[i], w[i], a0);
+      nrm2f[c] = a0 + a1;
+    }
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int rd = 0; rd < n2 - 1; ++rd) {
+      for (int t0 = warp * 8; t0 < n2 / 2; t0 += nteams) {
+        int a, b;
+        jacobi_pair(t0 + team, rd, n2, nc, a, b);
+        float* __restrict__ wa = W32 + (a < 0 ? 0 : a) * cs;
+        float* __restrict__ wb = W32 + (b < 0 ? 0 : b) * cs;
+        float g0 = 0.0f, g1 = 0.0f;
+        if (a >= 0) {
+          int i = q;
+          for (; i + 4 < k; i += 8) { g0 = fmaf(wa[i], wb[i], g0); g1 = fmaf(wa[i + 4], wb[i + 4], g1); }
+          for (; i < k; i += 4) g0 = fmaf(wa[i], wb[i], g0);
+        }
+        float ga = g0 + g1;
+        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+        bool rot = false;
+        float tt = 0.0f, al = 0.0f, be = 0.0f;
+        if (a >= 0) {
+          al = nrm2f[a];
+          be = nrm2f[b];
+          rot = ga != 0.0f && fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be);
+        }
+        if (rot) {
+          const float zeta = (be - al) / (2.0f * ga), az = fabsf(zeta);
+          tt = az > 1e18f ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+          if (tt == 0.0f) rot = false;
+        }
+        if (rot) {
+          const float cn = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cn * tt;
+          for (int m = q; m < k; m += 4) {
+            const float x = wa[m], y = wb[m];
+            wa[m] = cn * x - sn * y;
+            wb[m] = sn * x + cn * y;
+          }
+          float* __restrict__ va = V32 + a * lv;
+          float* __restrict__ vb = V32 + b * lv;
+          for (int m = q; m < nc; m += 4) {
+            const float x = va[m], y = vb[m];
+            va[m] = cn * x - sn * y;
+            vb[m] = sn * x + cn * y;
+          }
+        }
+        __syncwarp();   // every lane of the team has read the old norms
+        if (rot && q == 0) {
+          nrm2f[a] = al - tt * ga;
+          nrm2f[b] = be + tt * ga;
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+
+  // ---- step 2: V' = V - V E / 2, E = V^T V - I (W32 is dead: V64 takes its place)
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+    const int c = e / nc, m = e - c * nc;
+    V64[c * s0 + m] = (double)V32[c * lv + m];
+  }
+  __syncthreads();
+  {
+    // upper triangle a <= b, row by row; each thread walks its share in steps of blockDim.x
+    const int npair = nc * (nc + 1) / 2;
+    int a = 0, rem = threadIdx.x, len = nc;
+    while (a < nc && rem >= len) { rem -= len; ++a; --len; }
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+      const int b = a + rem;
+      const double* va = V64 + a * s0;
+      const double* vb = V64 + b * s0;
+      double e0 = 0.0, e1 = 0.0;
+      int m = 0;
+      for (; m + 1 < nc; m += 2) { e0 = fma(va[m], vb[m], e0); e1 = fma(va[m + 1], vb[m + 1], e1); }
+      if (m < nc) e0 = fma(va[m], vb[m], e0);
+      const float ev = (float)((e0 + e1) - (a == b ? 1.0 : 0.0));
+      E32[b * lv + a] = ev;
+      E32[a * lv + b] = ev;
+      rem += blockDim.x;
+      while (a < nc && rem >= len) { rem -= len; ++a; --len; }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+    const int c = e / nc, m = e - c * nc;
+    float acc = 0.0f;
+    for (int j = 0; j < nc; ++j) acc = fmaf(V32[j * lv + m], E32[c * lv + j], acc);
+    V64[c * s0 + m] -= 0.5 * (double)acc;
+  }
+  __syncthreads();
+
+  // ---- step 3: W = W0 V' (V32 and E32 are dead: W takes their place)
+  for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+    const int i = e / nc, c = e - i * nc;
+    const double* vc = V64 + c * s0;
+    double acc = 0.0;
+    for (int m = i; m < nc; ++m) {        // W0 is upper triangular
+      const double b = (m < k) ? it.B[i + (int64_t)ld * m] : ((i == k - 1) ? st->beta_k : 0.0);
+      if (b != 0.0) acc = fma(b, vc[m], acc);
+    }
+    W[c * cs + i] = acc;
+  }
+  __syncthreads();
   const double jtol = 2.220446049250313e-16 * (double)(k > 8 ? k : 8);
   int sweeps = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
@@ -406,19 +594,10 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     // A team of 4 lanes owns one column pair (rows interleaved over the team);
     // teams fill whole warps (pair t -> warp t / 8, team t % 8), so a round's
     // FP64 instructions run with full warps on every scheduler of the SM.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int team = lane >> 2, q = lane & 3;
-    const int nteams = (blockDim.x >> 5) * 8;
     for (int rd = 0; rd < n2 - 1; ++rd) {
       for (int t0 = warp * 8; t0 < n2 / 2; t0 += nteams) {
-        const int t = t0 + team;
-        int a = -1, b = -1;
-        if (t < n2 / 2) {
-          const int sa = t, sb = n2 - 1 - t;
-          a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
-          b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
-          if (a >= nc || b >= nc) a = b = -1;
-        }
+        int a, b;
+        jacobi_pair(t0 + team, rd, n2, nc, a, b);
         double* __restrict__ wa = W + (a < 0 ? 0 : a) * cs;
         double* __restrict__ wb = W + (b < 0 ? 0 : b) * cs;
         double g0 = 0.0, g1 = 0.0;
@@ -568,6 +747,7 @@ __global__ void __launch_bounds__(256) k_bsvd(const SvdItem* __restrict__ items)
     st->sigma1 = s1;
     st->maxres = mres;
     st->sweeps = sweeps;
+    st->sweeps32 = sweeps32;
     st->nconv = nconv;
     st->converged = conv ? 1 : 0;
     st->restarts += 1;
@@ -664,21 +844,28 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   const int kkp = ((kk + CP - 1) / CP) * CP;
   E* cf = blk + (int64_t)RB * (k + 1);                 // kc x kkp, row-major in i
   const int ncol = SHORT ? k : k + 1;
+  // The block's rows of every basis column and the coefficients arrive by
+  // element-wise asynchronous copies: a thread issues all of its copies before
+  // waiting, so the whole tile is in flight at once (a load loop through
+  // registers keeps one or two per thread).
   for (int e = threadIdx.x; e < ncol * RB; e += blockDim.x) {
     const int c = e / RB, t = e - c * RB;
-    blk[e] = (t < nr) ? basis[r0 + t + ldb * c] : E(0);
+    if (t < nr) cp_async_elem<sizeof(E)>(blk + e, basis + r0 + t + ldb * c);
+    else blk[e] = E(0);
   }
   if (SHORT) {
     for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
       const int i = e / kkp, c = e - i * kkp;
-      cf[e] = (c < kk) ? (E)it.P[i + (int64_t)it.ldc * c] : E(0);
+      if (c < kk) cp_async_elem<sizeof(E)>(cf + e, it.P + i + (int64_t)it.ldc * c);
+      else cf[e] = E(0);
     }
   } else {
     for (int e = threadIdx.x; e < kc * kkp; e += blockDim.x) {
       const int i = e / kkp, c = e - i * kkp;
-      cf[e] = (E)it.Cs[(int64_t)i * it.ldcs + c];
+      cp_async_elem<sizeof(E)>(cf + e, it.Cs + (int64_t)i * it.ldcs + c);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
   for (int c0 = 0; c0 < kk; c0 += CP) {
@@ -802,7 +989,7 @@ void launch_long_init(const LongItem<T>* items, const int32_t* tpre, int n, int 
 
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
   if (n <= 0) return;
-  const size_t sm = (size_t)(kmax + 1) * (kmax | 1) * sizeof(double);
+  const size_t sm = bsvd_layout(kmax, kmax + 1).bytes;
   set_max_smem((const void*)k_bsvd);
   k_bsvd<<<n, 256, sm, st>>>(items); count_launch();
 }

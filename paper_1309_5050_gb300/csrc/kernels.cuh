@@ -18,8 +18,9 @@ struct LzState {
   int32_t restarts;   // restart cycles done
   int32_t max_restarts;
   int32_t full;       // k equals min(L, K): one cycle spans the whole space
-  int32_t sweeps;     // Jacobi sweeps of the last small SVD
+  int32_t sweeps;     // FP64 Jacobi sweeps of the last small SVD
   int32_t svd_done;   // the small SVD of the completed cycle has run (cleared by a restart)
+  int32_t sweeps32;   // FP32 Jacobi sweeps that preceded them
   double beta_k;      // coupling to the (k+1)-th long vector after k steps
   double anorm;       // largest Lanczos coefficient seen (scale for breakdown)
   double tol;         // residual tolerance relative to sigma_1

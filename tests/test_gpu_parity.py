@@ -193,6 +193,21 @@ def test_vectors_satisfy_svd_relations():
         assert U[k, i] > 0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_small_svd_fp32_rotations_fp64_polish(prec):
+    """The small SVD finds its rotations in FP32 and polishes them in a few
+    FP64 sweeps; the triples keep the accuracy of the form."""
+    x = W.series_1d(3000, seed=17)
+    s = pkg.SSA.series(x, 1200)
+    s.decompose(12, prec, seed=4)
+    inf = s.info()
+    assert inf["jacobi_sweeps_fp32"] >= 1
+    assert 1 <= inf["jacobi_sweeps"] <= 4, inf["jacobi_sweeps"]
+    so, _, _ = O.decompose(O.Problem.series(x, 1200), 12)
+    np.testing.assert_allclose(s.sigma(), so, rtol=TOL_SIG[prec], atol=0)
+    s.close()
+
+
 def test_batch_equals_single():
     """ssa_decompose_batch gives each problem the result it gets alone."""
     cases = [case_mssa([300, 400, 350], 80, 20 + i)[0] for i in range(3)]
