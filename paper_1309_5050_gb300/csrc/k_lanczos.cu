@@ -387,6 +387,8 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
 // at the end).
 // Outputs: sig (k), P (k x k, ld ldb), Q ((k+1) x k, ld ldb+1; row k is zero
 // unless the extra column was used).
+constexpr int BSVD_NT = 512;
+
 __device__ __forceinline__ double block_max(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -410,7 +412,7 @@ __device__ __forceinline__ void jacobi_pair(int t, int rd, int n2, int nc, int& 
   if (a >= nc || b >= nc) a = b = -1;
 }
 
-__global__ void __launch_bounds__(256, 2) k_bsvd(const SvdItem* __restrict__ items) {
+__global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__ items) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
   if (!st->active || st->jc < st->k || st->svd_done) return;   // only at the end of a cycle, once
@@ -432,8 +434,10 @@ __global__ void __launch_bounds__(256, 2) k_bsvd(const SvdItem* __restrict__ ite
   __shared__ int order[KMAX + 2];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int team = lane >> 2, q = lane & 3;
+  const int team = lane >> 2, q = lane & 3;                    // FP64 sweeps: 4-lane teams
   const int nteams = (blockDim.x >> 5) * 8;
+  const int team16 = lane >> 4, q16 = lane & 15;               // FP32 sweeps: 16-lane teams
+  const int nteams16 = (blockDim.x >> 5) * 2;
   const int n2 = nc + (nc & 1);
 
   // ---- step 1: FP32 Jacobi with accumulated rotations
@@ -474,21 +478,25 @@ __global__ void __launch_bounds__(256, 2) k_bsvd(const SvdItem* __restrict__ ite
     }
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
+    // FP32 arithmetic is cheap and its rounds are latency-bound: a team of 16
+    // lanes owns a pair (two teams per warp), so each lane carries a few rows
     for (int rd = 0; rd < n2 - 1; ++rd) {
-      for (int t0 = warp * 8; t0 < n2 / 2; t0 += nteams) {
+      for (int t0 = warp * 2; t0 < n2 / 2; t0 += nteams16) {
         int a, b;
-        jacobi_pair(t0 + team, rd, n2, nc, a, b);
+        jacobi_pair(t0 + team16, rd, n2, nc, a, b);
         float* __restrict__ wa = W32 + (a < 0 ? 0 : a) * cs;
         float* __restrict__ wb = W32 + (b < 0 ? 0 : b) * cs;
         float g0 = 0.0f, g1 = 0.0f;
         if (a >= 0) {
-          int i = q;
-          for (; i + 4 < k; i += 8) { g0 = fmaf(wa[i], wb[i], g0); g1 = fmaf(wa[i + 4], wb[i + 4], g1); }
-          for (; i < k; i += 4) g0 = fmaf(wa[i], wb[i], g0);
+          int i = q16;
+          for (; i + 16 < k; i += 32) { g0 = fmaf(wa[i], wb[i], g0); g1 = fmaf(wa[i + 16], wb[i + 16], g1); }
+          if (i < k) g0 = fmaf(wa[i], wb[i], g0);
         }
         float ga = g0 + g1;
         ga += __shfl_xor_sync(0xffffffffu, ga, 1);
         ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 4);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 8);
         bool rot = false;
         float tt = 0.0f, al = 0.0f, be = 0.0f;
         if (a >= 0) {
@@ -497,27 +505,30 @@ __global__ void __launch_bounds__(256, 2) k_bsvd(const SvdItem* __restrict__ ite
           rot = ga != 0.0f && fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be);
         }
         if (rot) {
-          const float zeta = (be - al) / (2.0f * ga), az = fabsf(zeta);
-          tt = az > 1e18f ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+          // approximate division and reciprocal square root: the FP64
+          // steps make the result exact whatever these rotations are
+          const float zeta = __fdividef(be - al, 2.0f * ga), az = fabsf(zeta);
+          tt = az > 1e18f ? __fdividef(0.5f, zeta)
+                          : __fdividef(copysignf(1.0f, zeta), az + sqrtf(fmaf(zeta, zeta, 1.0f)));
           if (tt == 0.0f) rot = false;
         }
         if (rot) {
           const float cn = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cn * tt;
-          for (int m = q; m < k; m += 4) {
+          for (int m = q16; m < k; m += 16) {
             const float x = wa[m], y = wb[m];
             wa[m] = cn * x - sn * y;
             wb[m] = sn * x + cn * y;
           }
           float* __restrict__ va = V32 + a * lv;
           float* __restrict__ vb = V32 + b * lv;
-          for (int m = q; m < nc; m += 4) {
+          for (int m = q16; m < nc; m += 16) {
             const float x = va[m], y = vb[m];
             va[m] = cn * x - sn * y;
             vb[m] = sn * x + cn * y;
           }
         }
         __syncwarp();   // every lane of the team has read the old norms
-        if (rot && q == 0) {
+        if (rot && q16 == 0) {
           nrm2f[a] = al - tt * ga;
           nrm2f[b] = be + tt * ga;
           rotated = 1;
@@ -815,16 +826,19 @@ __device__ __forceinline__ void lds4(const E* p, E* v) {
 // (kc = k on the short side, k + 1 on the long side, whose coefficients carry
 // the extra row of the complete-basis case); on a restart the long basis also
 // moves column k to column kk.  A block stages its RB rows of every column and
-// the coefficients in shared memory; thread (rg, cg) accumulates a 4 x 4 tile
-// (rows 4 rg.., columns 4 cg..) from 16-byte shared loads, and a warp writes
-// 128 consecutive rows of a column.
+// the coefficients in shared memory; thread (rg, cg) accumulates a 4 x CW tile
+// (rows 4 rg.., columns CW cg..) from 16-byte shared loads (the basis rows
+// differ across a warp, the coefficients are one broadcast), and a warp
+// writes 128 consecutive rows of a column.  FP32 takes 4 x 8 tiles: two
+// shared loads of the basis per 32 FMA would otherwise bound the kernel.
 template <typename T, bool SHORT>
 __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ items, const int32_t* __restrict__ tpre,
                                               int n, int final_pass) {
   typedef typename std::conditional<SHORT, double, T>::type E;
   constexpr int RB = RITZ_RB<E>();
-  constexpr int RG = RB / 4;          // row groups
-  constexpr int CP = (256 / RG) * 4;  // columns per pass
+  constexpr int CW = RITZ_CW<E>();
+  constexpr int RG = RB / 4;           // row groups
+  constexpr int CP = (256 / RG) * CW;  // columns per pass
   int rblk;
   const RitzItem<T> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
   const LzState* st = it.st;
@@ -869,24 +883,25 @@ __global__ void __launch_bounds__(256) k_ritz(const RitzItem<T>* __restrict__ it
   __syncthreads();
   const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
   for (int c0 = 0; c0 < kk; c0 += CP) {
-    const int cb = c0 + 4 * cg;
+    const int cb = c0 + CW * cg;
     if (cb >= kk) continue;
-    E acc[4][4];
+    E acc[4][CW];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = E(0);
+      for (int b = 0; b < CW; ++b) acc[a][b] = E(0);
     for (int i = 0; i < kc; ++i) {
-      E av[4], bv[4];
+      E av[4], bv[CW];
       lds4(blk + i * RB + 4 * rg, av);
-      lds4(cf + i * kkp + cb, bv);
+#pragma unroll
+      for (int h = 0; h < CW; h += 4) lds4(cf + i * kkp + cb + h, bv + h);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < CW; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < CW; ++b) {
       const int c = cb + b;
       if (c >= kk) break;
 #pragma unroll
@@ -991,7 +1006,7 @@ void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
   if (n <= 0) return;
   const size_t sm = bsvd_layout(kmax, kmax + 1).bytes;
   set_max_smem((const void*)k_bsvd);
-  k_bsvd<<<n, 256, sm, st>>>(items); count_launch();
+  k_bsvd<<<n, BSVD_NT, sm, st>>>(items); count_launch();
 }
 
 void launch_restart(const SvdItem* items, int n, cudaStream_t st) {
@@ -1004,7 +1019,7 @@ void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s
                  int tiles_l, int final_pass, cudaStream_t st) {
   if (n <= 0) return;
   const int rs = RITZ_RB<double>(), rl = RITZ_RB<T>();
-  const int cps = (256 / (rs / 4)) * 4, cpl = (256 / (rl / 4)) * 4;
+  const int cps = (256 / (rs / 4)) * RITZ_CW<double>(), cpl = (256 / (rl / 4)) * RITZ_CW<T>();
   const int kps = ((kmax + cps - 1) / cps) * cps, kpl = ((kmax + cpl - 1) / cpl) * cpl;
   const size_t sms = (size_t)rs * (kmax + 1) * sizeof(double) + (size_t)(kmax + 1) * kps * sizeof(double);
   const size_t sml = (size_t)rl * (kmax + 2) * sizeof(T) + (size_t)(kmax + 1) * kpl * sizeof(T);
@@ -1021,7 +1036,9 @@ template <typename T>
 void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st) {
   if (n <= 0) return;
   k_sign<T><<<dim3(max_r, n), 256, 0, st>>>(items); count_launch();
-  unsigned gx = (unsigned)std::min<int64_t>((max_rows + 255) / 256, 1024);
+  // eight elements per thread: a block per 256 rows spent most of its time
+  // starting up (one element each)
+  unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((max_rows + 2047) / 2048, 1024));
   k_final_copy<T><<<dim3(gx, max_r, n), 256, 0, st>>>(items); count_launch();
 }
 

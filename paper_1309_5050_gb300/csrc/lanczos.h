@@ -99,7 +99,9 @@ struct FinalItem {
 // (short side ceil(Ls / SHORT_RB), long side ceil(Kl / LONG_RB), Ritz
 // ceil(rows / RITZ_RB_*)), tiles = tpre[n].
 template <typename E>
-constexpr int RITZ_RB() { return sizeof(E) == 8 ? 64 : 128; }   // rows per Ritz block
+constexpr int RITZ_RB() { return sizeof(E) == 8 ? 64 : 256; }   // rows per Ritz block
+template <typename E>
+constexpr int RITZ_CW() { return sizeof(E) == 8 ? 4 : 8; }      // columns per thread tile
 constexpr int RITZ_RB_SHORT = RITZ_RB<double>();
 template <typename T>
 constexpr int ritz_rb_long() { return RITZ_RB<T>(); }
