@@ -388,6 +388,12 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
 // Outputs: sig (k), P (k x k, ld ldb), Q ((k+1) x k, ld ldb+1; row k is zero
 // unless the extra column was used).
 constexpr int BSVD_NT = 512;
+constexpr int BSVD_T32 = 16;   // lanes per column pair in the FP32 sweeps (latency-bound: many lanes)
+constexpr int BSVD_T64 = 4;    // lanes per column pair in the FP64 sweeps (FP64 issue-bound: few lanes,
+                               // so the per-pair scalar work is repeated by few warps)
+
+// sqrt of a non-negative FP32 value from the hardware reciprocal square root
+__device__ __forceinline__ float sqrt_approx(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
 __device__ __forceinline__ double block_max(double v, double* red) {
 #pragma unroll
@@ -412,7 +418,7 @@ __device__ __forceinline__ void jacobi_pair(int t, int rd, int n2, int nc, int& 
   if (a >= nc || b >= nc) a = b = -1;
 }
 
-__global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__ items) {
+__global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__ items, int b_in_smem) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
   if (!st->active || st->jc < st->k || st->svd_done) return;   // only at the end of a cycle, once
@@ -427,19 +433,30 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
   float* V32 = reinterpret_cast<float*>(sm + (size_t)nc * s0);  // column c at V32 + c*lv
   float* E32 = V32 + (size_t)nc * lv;
   double* W = sm + (size_t)nc * s0;                              // step 3 on, over V32 and E32; column c at W + c*cs
+  // B for the products with W0: a shared copy (region 2) or global memory
+  double* Bs = b_in_smem ? W + (size_t)nc * lv : nullptr;       // region 2, column m at Bs + m*cs
+  const double* bp = b_in_smem ? Bs : it.B;
+  const int bld = b_in_smem ? cs : ld;
   __shared__ int rotated;
   __shared__ double nrm2[KMAX + 2];
   __shared__ double nrm[KMAX + 2];
   __shared__ float nrm2f[KMAX + 2];
   __shared__ int order[KMAX + 2];
+  __shared__ unsigned char keep[KMAX + 2];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int team = lane >> 2, q = lane & 3;                    // FP64 sweeps: 4-lane teams
-  const int nteams = (blockDim.x >> 5) * 8;
-  const int team16 = lane >> 4, q16 = lane & 15;               // FP32 sweeps: 16-lane teams
-  const int nteams16 = (blockDim.x >> 5) * 2;
+  const int team = lane / BSVD_T64, q = lane % BSVD_T64;        // FP64 sweeps
+  const int nteams = (blockDim.x >> 5) * (32 / BSVD_T64);
+  const int team16 = lane / BSVD_T32, q16 = lane % BSVD_T32;    // FP32 sweeps
+  const int nteams16 = (blockDim.x >> 5) * (32 / BSVD_T32);
   const int n2 = nc + (nc & 1);
 
+  if (b_in_smem) {
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+      const int m = e / k, i = e - m * k;
+      Bs[m * cs + i] = (i <= m) ? it.B[i + (int64_t)ld * m] : 0.0;
+    }
+  }
   // ---- step 1: FP32 Jacobi with accumulated rotations
   double mx = 0.0;
   for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
@@ -478,10 +495,10 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     }
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
-    // FP32 arithmetic is cheap and its rounds are latency-bound: a team of 16
-    // lanes owns a pair (two teams per warp), so each lane carries a few rows
+    // FP32 arithmetic is cheap and its rounds are latency-bound: a team of
+    // BSVD_T32 lanes owns a pair, so each lane carries a few rows
     for (int rd = 0; rd < n2 - 1; ++rd) {
-      for (int t0 = warp * 2; t0 < n2 / 2; t0 += nteams16) {
+      for (int t0 = warp * (32 / BSVD_T32); t0 < n2 / 2; t0 += nteams16) {
         int a, b;
         jacobi_pair(t0 + team16, rd, n2, nc, a, b);
         float* __restrict__ wa = W32 + (a < 0 ? 0 : a) * cs;
@@ -489,39 +506,40 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
         float g0 = 0.0f, g1 = 0.0f;
         if (a >= 0) {
           int i = q16;
-          for (; i + 16 < k; i += 32) { g0 = fmaf(wa[i], wb[i], g0); g1 = fmaf(wa[i + 16], wb[i + 16], g1); }
+          for (; i + BSVD_T32 < k; i += 2 * BSVD_T32) {
+            g0 = fmaf(wa[i], wb[i], g0);
+            g1 = fmaf(wa[i + BSVD_T32], wb[i + BSVD_T32], g1);
+          }
           if (i < k) g0 = fmaf(wa[i], wb[i], g0);
         }
         float ga = g0 + g1;
-        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
-        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
-        ga += __shfl_xor_sync(0xffffffffu, ga, 4);
-        ga += __shfl_xor_sync(0xffffffffu, ga, 8);
+#pragma unroll
+        for (int o = 1; o < BSVD_T32; o <<= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
         bool rot = false;
         float tt = 0.0f, al = 0.0f, be = 0.0f;
         if (a >= 0) {
           al = nrm2f[a];
           be = nrm2f[b];
-          rot = ga != 0.0f && fabsf(ga) > tol32 * sqrtf(al) * sqrtf(be);
+          rot = ga != 0.0f && fabsf(ga) > tol32 * sqrt_approx(al) * sqrt_approx(be);
         }
         if (rot) {
-          // approximate division and reciprocal square root: the FP64
-          // steps make the result exact whatever these rotations are
+          // approximate division and square roots: the FP64 steps make the
+          // result exact whatever these rotations are
           const float zeta = __fdividef(be - al, 2.0f * ga), az = fabsf(zeta);
           tt = az > 1e18f ? __fdividef(0.5f, zeta)
-                          : __fdividef(copysignf(1.0f, zeta), az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                          : __fdividef(copysignf(1.0f, zeta), az + sqrt_approx(fmaf(zeta, zeta, 1.0f)));
           if (tt == 0.0f) rot = false;
         }
         if (rot) {
           const float cn = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cn * tt;
-          for (int m = q16; m < k; m += 16) {
+          for (int m = q16; m < k; m += BSVD_T32) {
             const float x = wa[m], y = wb[m];
             wa[m] = cn * x - sn * y;
             wb[m] = sn * x + cn * y;
           }
           float* __restrict__ va = V32 + a * lv;
           float* __restrict__ vb = V32 + b * lv;
-          for (int m = q16; m < nc; m += 16) {
+          for (int m = q16; m < nc; m += BSVD_T32) {
             const float x = va[m], y = vb[m];
             va[m] = cn * x - sn * y;
             vb[m] = sn * x + cn * y;
@@ -581,14 +599,25 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     const int i = e / nc, c = e - i * nc;
     const double* vc = V64 + c * s0;
     double acc = 0.0;
-    for (int m = i; m < nc; ++m) {        // W0 is upper triangular
-      const double b = (m < k) ? it.B[i + (int64_t)ld * m] : ((i == k - 1) ? st->beta_k : 0.0);
-      if (b != 0.0) acc = fma(b, vc[m], acc);
+    for (int m = i; m < k; ++m) {         // B is upper triangular; zeros skipped by their bits
+      const double b = bp[i + (int64_t)bld * m];
+      if ((__double_as_longlong(b) << 1) != 0) acc = fma(b, vc[m], acc);
     }
+    if (aug && i == k - 1) acc = fma(st->beta_k, vc[k], acc);   // the extra column of W0
     W[c * cs + i] = acc;
   }
   __syncthreads();
-  const double jtol = 2.220446049250313e-16 * (double)(k > 8 ? k : 8);
+  // a pair is done once its cosine is at the rounding level of a k-term FP64
+  // dot product (k eps; tighter never settles) or at 1e-3 of the residual
+  // tolerance, whichever is larger: with cosines below c the singular values
+  // are within a relative k c and the vectors orthogonal to c, far inside
+  // what the residual test and the FP32 products resolve (FP32 form: tol
+  // 1e-7, so 1e-10, and the sweeps after the first one only test)
+  const double keps = 2.220446049250313e-16 * (double)(k > 8 ? k : 8);
+  const bool relaxed = 1e-3 * st->tol > keps;
+  const double jtol = relaxed ? 1e-3 * st->tol : keps;
+  // FP32 form: pairs of two trailing columns are not rotated (below)
+  const int nkeep = relaxed ? min(nc, max(st->kk, st->r) + 4) : nc;
   int sweeps = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
     sweeps = sweep + 1;
@@ -600,33 +629,52 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
       if (i < k) a0 = fma(w[i], w[i], a0);
       nrm2[c] = a0 + a1;
     }
+    __syncthreads();
+    // Only the leading kk triples are used (restart, Ritz vectors, residual
+    // test), so in the FP32 form a pair of two columns ranked below kk + 4 by
+    // norm is left alone: those columns need not be orthogonal to each other,
+    // only to the leading ones, and their own norms are off by no more than
+    // the FP32 sweeps left (~1e-6 relative), far from the leading ranks.
+    // This skips the slowly converging noise clusters.
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const long long v = __double_as_longlong(nrm2[c]);
+      int rk = 0;
+      for (int b = 0; b < nc; ++b) {
+        const long long u = __double_as_longlong(nrm2[b]);
+        rk += (u > v) || (u == v && b < c);
+      }
+      keep[c] = rk < nkeep;
+    }
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
-    // A team of 4 lanes owns one column pair (rows interleaved over the team);
-    // teams fill whole warps (pair t -> warp t / 8, team t % 8), so a round's
-    // FP64 instructions run with full warps on every scheduler of the SM.
+    // A team of BSVD_T64 lanes owns one column pair (rows interleaved over the
+    // team); teams fill whole warps, so a round's FP64 instructions run with
+    // full warps on every scheduler of the SM.
     for (int rd = 0; rd < n2 - 1; ++rd) {
-      for (int t0 = warp * 8; t0 < n2 / 2; t0 += nteams) {
+      for (int t0 = warp * (32 / BSVD_T64); t0 < n2 / 2; t0 += nteams) {
         int a, b;
         jacobi_pair(t0 + team, rd, n2, nc, a, b);
+        if (a >= 0 && !keep[a] && !keep[b]) a = b = -1;
         double* __restrict__ wa = W + (a < 0 ? 0 : a) * cs;
         double* __restrict__ wb = W + (b < 0 ? 0 : b) * cs;
         double g0 = 0.0, g1 = 0.0;
         if (a >= 0) {
           int i = q;
-          for (; i + 4 < k; i += 8) { g0 = fma(wa[i], wb[i], g0); g1 = fma(wa[i + 4], wb[i + 4], g1); }
-          for (; i < k; i += 4) g0 = fma(wa[i], wb[i], g0);
+          for (; i + BSVD_T64 < k; i += 2 * BSVD_T64) {
+            g0 = fma(wa[i], wb[i], g0);
+            g1 = fma(wa[i + BSVD_T64], wb[i + BSVD_T64], g1);
+          }
+          if (i < k) g0 = fma(wa[i], wb[i], g0);
         }
         double ga = g0 + g1;
-        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
-        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
-        bool rot = false;
+#pragma unroll
+        for (int o = 1; o < BSVD_T64; o <<= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        bool rot = false, small = false;
         double tt = 0.0, al = 0.0, be = 0.0;
         if (a >= 0) {
           al = nrm2[a];
           be = nrm2[b];
-          // a pair is done once its cosine is at the rounding level of a
-          // k-term FP64 dot product (k * eps); tighter never settles.
+          // a pair is done once its cosine is below jtol
           rot = ga != 0.0 && ga * ga > jtol * jtol * (al * be);
         }
         if (rot) {
@@ -648,6 +696,7 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
             const float zf = zn / zd, az = fabsf(zf);
             if (az < 1e18f) tf = copysignf(1.0f, zf) / (az + sqrtf(fmaf(zf, zf, 1.0f)));
           }
+          small = tf != 0.0f && fabsf(tf) < 1e-4f;
           if (tf != 0.0f) {
             tt = (double)tf;
           } else {
@@ -658,15 +707,18 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
           if (tt == 0.0) rot = false;
         }
         if (rot) {
-          const double cn = rsqrt(1.0 + tt * tt), sn = cn * tt;
+          // |t| < 1e-4 (the polish after the FP32 sweeps): 1 / sqrt(1 + t^2)
+          // = 1 - t^2 / 2 to FP64 rounding (the next term, 3 t^4 / 8, is below
+          // 4e-17), so the rotation stays orthogonal without the square root
+          const double cn = small ? fma(-0.5 * tt, tt, 1.0) : rsqrt(1.0 + tt * tt), sn = cn * tt;
           int m = q;
-          for (; m + 4 < k; m += 8) {
-            const double x0 = wa[m], x1 = wa[m + 4];
-            const double y0 = wb[m], y1 = wb[m + 4];
-            wa[m] = cn * x0 - sn * y0; wa[m + 4] = cn * x1 - sn * y1;
-            wb[m] = sn * x0 + cn * y0; wb[m + 4] = sn * x1 + cn * y1;
+          for (; m + BSVD_T64 < k; m += 2 * BSVD_T64) {
+            const double x0 = wa[m], x1 = wa[m + BSVD_T64];
+            const double y0 = wb[m], y1 = wb[m + BSVD_T64];
+            wa[m] = cn * x0 - sn * y0; wa[m + BSVD_T64] = cn * x1 - sn * y1;
+            wb[m] = sn * x0 + cn * y0; wb[m + BSVD_T64] = sn * x1 + cn * y1;
           }
-          for (; m < k; m += 4) {
+          for (; m < k; m += BSVD_T64) {
             const double x = wa[m], y = wb[m];
             wa[m] = cn * x - sn * y;
             wb[m] = sn * x + cn * y;
@@ -692,47 +744,97 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     nrm[c] = sqrt(a0);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < nc; ++c) order[c] = c;
-    for (int a = 0; a < nc; ++a) {          // selection sort, descending, stable
-      int best = a;
-      for (int b = a + 1; b < nc; ++b)
-        if (nrm[order[b]] > nrm[order[best]]) best = b;
-      const int t = order[a]; order[a] = order[best]; order[best] = t;
+  // descending order of the norms, ties by column: each column counts the
+  // columns ahead of it (non-negative doubles order like their bit patterns,
+  // so the comparisons stay off the FP64 pipe); 1 / sigma once per column
+  double* inv = nrm2;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const long long v = __double_as_longlong(nrm[c]);
+    int rk = 0;
+    for (int b = 0; b < nc; ++b) {
+      const long long u = __double_as_longlong(nrm[b]);
+      rk += (u > v) || (u == v && b < c);
     }
+    order[rk] = c;
+    inv[c] = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
   }
   __syncthreads();
+  // W <- W diag(1 / sigma): the left vectors, unsorted
+  for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    W[c * cs + i] *= inv[c];
+  }
+  __syncthreads();
+  if (relaxed) {
+    // The sweeps stopped at cosines below jtol > k eps: one Newton-Schulz step
+    // P <- P - P F / 2, F = P^T P - I (summed in FP64), brings the left vectors
+    // to orthogonality at FP64 rounding, which the restarted short basis U P
+    // needs (zero columns stay zero).  F is of the size of jtol, so P F needs
+    // only FP32.  Region 0 (V') is free: F and an FP32 copy of P go there.
+    float* F32 = reinterpret_cast<float*>(sm);                   // nc x lv
+    float* P32 = F32 + (size_t)nc * lv;                           // nc x cs
+    for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+      const int c = e / k, i = e - c * k;
+      P32[c * cs + i] = (float)W[c * cs + i];
+    }
+    const int npair = nc * (nc + 1) / 2;
+    int a = 0, rem = threadIdx.x, len = nc;
+    while (a < nc && rem >= len) { rem -= len; ++a; --len; }
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+      const int b = a + rem;
+      const double* pa = W + a * cs;
+      const double* pb = W + b * cs;
+      double f0 = 0.0, f1 = 0.0;
+      int i = 0;
+      for (; i + 1 < k; i += 2) { f0 = fma(pa[i], pb[i], f0); f1 = fma(pa[i + 1], pb[i + 1], f1); }
+      if (i < k) f0 = fma(pa[i], pb[i], f0);
+      const float fv = (float)((f0 + f1) - (a == b ? 1.0 : 0.0));
+      F32[b * lv + a] = fv;
+      F32[a * lv + b] = fv;
+      rem += blockDim.x;
+      while (a < nc && rem >= len) { rem -= len; ++a; --len; }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+      const int c = e / k, i = e - c * k;
+      float acc = 0.0f;
+      for (int j = 0; j < nc; ++j) acc = fmaf(P32[j * cs + i], F32[c * lv + j], acc);
+      W[c * cs + i] -= 0.5 * (double)acc;
+    }
+    __syncthreads();
+  }
   const int kd = ld, kq = ld + 1;
-  // P_i = W_{o(i)} / sigma_i
+  // P_i = W_{o(i)}
   for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
     const int c = e / kd, i = e - c * kd;
     double pv = 0.0;
-    if (c < k && i < k) {
-      const int o = order[c];
-      const double sg = nrm[o];
-      pv = sg > 0.0 ? W[o * cs + i] / sg : 0.0;
-    }
+    if (c < k && i < k) pv = W[order[c] * cs + i];
     it.P[i + (int64_t)kd * c] = pv;
   }
   for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
   __syncthreads();
-  // Q_i = W0^T P_i / sigma_i with W0 = [B | beta_k e_k] (re-read from global)
+  // Q_i = W0^T P_i / sigma_i with W0 = [B | beta_k e_k]
   for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
     const int c = e / kq, j = e - c * kq;
     double qv = 0.0;
     if (c < k && j < nc) {
       const int o = order[c];
-      const double sg = nrm[o];
-      if (sg > 0.0) {
-        const double* pc = W + o * cs;         // unnormalised P column
+      const double is = inv[o];
+      if (is > 0.0) {
+        const double* pc = W + o * cs;         // P column
         double acc = 0.0;
         if (j < k) {
-          const double* bc = it.B + (int64_t)ld * j;
-          for (int m = 0; m <= j && m < k; ++m) acc = fma(bc[m], pc[m], acc);   // B upper triangular
+          // B is upper triangular with a few nonzeros per column; zeros are
+          // skipped by their bit pattern (no FP64 compare)
+          const double* bc = bp + (int64_t)bld * j;
+          for (int m = 0; m <= j && m < k; ++m) {
+            const double bv = bc[m];
+            if ((__double_as_longlong(bv) << 1) != 0) acc = fma(bv, pc[m], acc);
+          }
         } else {
           acc = st->beta_k * pc[k - 1];
         }
-        qv = acc / (sg * sg);
+        qv = acc * is;
       }
     }
     it.Q[j + (int64_t)kq * c] = qv;
@@ -740,16 +842,15 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
   __syncthreads();
   if (threadIdx.x == 0) {
     const int r = min(st->r, k);
-    const double s1 = nrm[order[0]];
+    const double s1 = nrm[order[0]], is1 = inv[order[0]];
     double mres = 0.0;
     int nconv = 0;
     bool conv = true;
     for (int i = 0; i < r; ++i) {
       const int o = order[i];
-      const double sg = nrm[o];
-      const double pk = sg > 0.0 ? W[o * cs + (k - 1)] / sg : 0.0;
+      const double pk = W[o * cs + (k - 1)];
       const double res = aug ? 0.0 : fabs(st->beta_k * pk);
-      const double rel = s1 > 0.0 ? res / s1 : 0.0;
+      const double rel = res * is1;
       if (rel > mres) mres = rel;
       if (rel <= st->tol) { if (nconv == i) ++nconv; }
       else conv = false;
@@ -1004,9 +1105,12 @@ void launch_long_init(const LongItem<T>* items, const int32_t* tpre, int n, int 
 
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
   if (n <= 0) return;
-  const size_t sm = bsvd_layout(kmax, kmax + 1).bytes;
+  const BsvdLayout lay = bsvd_layout(kmax, kmax + 1);
+  // B in shared memory when two blocks still fit on an SM
+  const int b_in_smem = 2 * (lay.bytes_b + 4096) <= (size_t)device_max_smem() ? 1 : 0;
+  const size_t sm = b_in_smem ? lay.bytes_b : lay.bytes;
   set_max_smem((const void*)k_bsvd);
-  k_bsvd<<<n, BSVD_NT, sm, st>>>(items); count_launch();
+  k_bsvd<<<n, BSVD_NT, sm, st>>>(items, b_in_smem); count_launch();
 }
 
 void launch_restart(const SvdItem* items, int n, cudaStream_t st) {

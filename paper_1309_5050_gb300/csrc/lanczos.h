@@ -49,14 +49,18 @@ struct LongItem {
 // Shared memory of the small SVD for a k-row W of nc columns: the FP64 W
 // (column stride cs = k | 1), V and E (nc x nc FP32, stride lv = nc | 1), and
 // V' in FP64 (stride s0).  Region 0 (nc x s0 doubles) holds the FP32 copy of
-// W0, then V'; region 1 (nc x lv floats twice) holds V and E, then the FP64 W.
-struct BsvdLayout { int cs, lv, s0; size_t bytes; };
+// W0, then V'; region 1 (nc x lv floats twice) holds V and E, then the FP64 W;
+// region 2 (k x k doubles, stride cs), when the launch gives room for it, a
+// copy of B for the products with it (W0 V' and W0^T P), which otherwise read
+// B from global memory.
+struct BsvdLayout { int cs, lv, s0; size_t bytes, bytes_b; };
 __host__ __device__ inline BsvdLayout bsvd_layout(int k, int nc) {
   BsvdLayout l;
   l.cs = k | 1;
   l.lv = nc | 1;
   l.s0 = l.cs > l.lv ? l.cs : l.lv;
   l.bytes = sizeof(double) * (size_t)nc * l.s0 + 2 * sizeof(float) * (size_t)nc * l.lv;
+  l.bytes_b = l.bytes + sizeof(double) * (size_t)k * l.cs;
   return l;
 }
 
