@@ -37,7 +37,7 @@ __all__ = [
     "Problem", "window_set", "origin_set", "trajectory_matrix",
     "trajectory_columns", "weights", "svd_eigen", "svd_eigen_t", "svd_jacobi", "decompose",
     "reconstruct", "reconstruct_at", "matvec", "rmatvec",
-    "series_rows", "series_cols", "series_hankelize_at",
+    "series_rows", "series_cols", "series_hankelize_at", "w_inner", "wcor",
 ]
 
 
@@ -428,3 +428,40 @@ def series_hankelize_at(sigma, U, V, group, points) -> np.ndarray:
         vals = (U[i][:, g] * s[None, :] * V[p - i][:, g]).sum(axis=1)
         out.append(float(vals.mean()))
     return np.array(out)
+
+
+# ---------------------------------------------------------------- w-correlations
+def w_inner(P: Problem, ys, zs) -> float:
+    """Weighted inner product ``(Y, Z)_w = sum_k w_k y_k z_k`` (Sec. 2.2,
+    paragraph Separability), summed over every channel; ``w_k = |A_k|`` is zero outside
+    N', where the reconstructions hold NaN and are skipped."""
+    tot = 0.0
+    for c in range(len(P.channels)):
+        w = P.weights(c).astype(np.float64)
+        ok = w > 0
+        tot += float(np.sum(w[ok] * np.asarray(ys[c])[ok] * np.asarray(zs[c])[ok]))
+    return tot
+
+
+def wcor(P: Problem, sigma, U, V, groups):
+    """The w-correlation matrix of the reconstructed components of
+    ``groups`` (Sec. 2.2): ``rho_ij = (X~_i, X~_j)_w / (||X~_i||_w ||X~_j||_w)``
+    (means not subtracted; 0 when a norm is 0), and each component's
+    contribution ``||X~_i||_w^2 / ||X||_w^2``.  Elementary grouping
+    ``[[0], [1], ...]`` gives the w-correlation matrix of the paper."""
+    rec = reconstruct(P, sigma, U, V, groups)
+    n = len(groups)
+    G = np.zeros((n, n))
+    for i in range(n):
+        for j in range(i, n):
+            G[i, j] = G[j, i] = w_inner(P, rec[i], rec[j])
+    xx = w_inner(P, P.channels, P.channels)
+    d = np.sqrt(np.diag(G))
+    rho = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if d[i] > 0 and d[j] > 0:
+                rho[i, j] = G[i, j] / (d[i] * d[j])
+    contrib = np.diag(G) / xx if xx > 0 else np.zeros(n)
+    return rho, contrib
+

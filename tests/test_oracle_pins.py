@@ -463,3 +463,64 @@ def test_series_hankelize_at_full_sum_is_input_and_matches_groups():
     np.testing.assert_allclose(O.series_hankelize_at(s, U, V, range(len(s)), pts), x, atol=1e-10)
     full = O.reconstruct(P, s, U, V, [[0, 1]])[0][0][:, 0]
     np.testing.assert_allclose(O.series_hankelize_at(s, U, V, [0, 1], pts), full, atol=1e-12)
+
+
+# ---------------------------------------------------------------- w-correlations
+def test_w_inner_is_frobenius_product_of_trajectory_matrices():
+    """Sec. 2.2: each element y_k sits in w_k = |A_k| entries of T(Y), so
+    (Y, Z)_w = <T(Y), T(Z)>_F for any Y, Z -- checked on random objects for a
+    shaped image with holes and an MSSA system, the trajectory matrices built
+    entry by entry."""
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(15, 13))
+    mask = np.ones((15, 13), bool)
+    mask[4:7, 5:8] = False
+    wmask = np.array([[1, 1, 0], [1, 1, 1], [1, 1, 1], [0, 1, 1]], bool)
+    P2 = O.Problem.image(x, 4, 3, wmask=wmask, mask=mask)
+    Pm = O.Problem.multi([rng.normal(size=n) for n in (23, 31, 19)], 7)
+    for P in (P2, Pm):
+        ys = [rng.normal(size=c.shape) for c in P.channels]
+        zs = [rng.normal(size=c.shape) for c in P.channels]
+        frob = sum(float(np.sum(O.trajectory_columns(ys[c], P.Lset, P.Ksets[c])
+                                * O.trajectory_columns(zs[c], P.Lset, P.Ksets[c])))
+                   for c in range(len(P.channels)))
+        assert abs(O.w_inner(P, ys, zs) - frob) <= 1e-12 * abs(frob) + 1e-12
+
+
+def test_wcor_exactly_separable_harmonics():
+    """Two harmonics with periods 8 and 4 and L, K multiples of 8 have
+    orthogonal trajectory rows and columns (weak separability, Sec. 2.2): the
+    reconstructions of the two rank-2 groups are the harmonics themselves, so
+    their w-correlation is 0, each self-correlation 1, and the contributions
+    are the harmonics' weighted energies, summing to 1."""
+    L, K = 16, 32
+    n = np.arange(L + K - 1, dtype=float)
+    x1 = 2.0 * np.cos(2 * np.pi * n / 8 + 0.4)
+    x2 = np.cos(2 * np.pi * n / 4 + 0.3)
+    P = O.Problem.series(x1 + x2, L)
+    sig, U, V = O.decompose(P, 4)
+    rho, contrib = O.wcor(P, sig, U, V, [[0, 1], [2, 3]])
+    np.testing.assert_allclose(np.diag(rho), 1.0, atol=1e-12)
+    assert abs(rho[0, 1]) <= 1e-10 and rho[0, 1] == rho[1, 0]
+    w = np.minimum.reduce([n + 1, np.full_like(n, L), np.full_like(n, K), len(n) - n])   # 1D weights
+    xx = np.sum(w * (x1 + x2) ** 2)
+    np.testing.assert_allclose(contrib, [np.sum(w * x1 ** 2) / xx, np.sum(w * x2 ** 2) / xx], rtol=1e-10)
+    assert abs(contrib.sum() - 1.0) <= 1e-10
+
+
+def test_wcor_invariants_on_noisy_image():
+    """Elementary w-correlations of a shaped 2D decomposition: symmetric,
+    unit diagonal, |rho| <= 1 (Cauchy-Schwarz in the weighted inner product);
+    a component that mixes two others is correlated with both."""
+    rng = np.random.default_rng(8)
+    i, j = np.meshgrid(np.arange(20), np.arange(18), indexing="ij")
+    x = np.cos(2 * np.pi * i / 7) * np.cos(2 * np.pi * j / 5) + 0.3 * rng.normal(size=i.shape)
+    P = O.Problem.image(x, 6, 5)
+    sig, U, V = O.decompose(P, 6)
+    rho, contrib = O.wcor(P, sig, U, V, [[k] for k in range(6)])
+    np.testing.assert_allclose(rho, rho.T, atol=0)
+    np.testing.assert_allclose(np.diag(rho), 1.0, atol=1e-12)
+    assert np.all(np.abs(rho) <= 1 + 1e-12)
+    assert np.all(contrib > 0) and contrib.sum() < 1.0 + 1e-12
+    rho2, _ = O.wcor(P, sig, U, V, [[0], [1], [0, 1]])
+    assert rho2[0, 2] > 0.3 and rho2[1, 2] > 0.3
