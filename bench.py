@@ -302,6 +302,14 @@ def _probe_info(pkg, probs, cfg, stream, args):
     p = pkg.SSA.multi_concat(flat, lens, cfg["L"], stream=stream)
     p.decompose(cfg["rank"], args.prec, krylov_dim=args.krylov_dim)
     info = p.info()
+    # w-correlation matrix of the elementary components (Sec. 2.2): one call
+    # reconstructs the r components and sums their weighted Gram matrix
+    p.wcor()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        p.wcor()
+    info["wcor_ms"] = (time.perf_counter() - t0) * 1000.0 / reps
     p.close()
     return info
 
@@ -523,6 +531,8 @@ def main():
                 "e2e": {"value": world * B / (ms_e2e / 1000.0), "unit": "decomps/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
                 "gpu_launches": int(launches),
+                "wcor": {"ms_per_call": ps_info["wcor_ms"], "components": CFG["rank"],
+                         "what": "ssa_wcor, elementary w-correlations of one problem, host call"},
                 "lanczos": {"krylov_dim": ps_info["krylov_dim"], "restarts_first_problem": restarts[-1][0],
                             "last_jacobi_sweeps_first_problem": {"fp64": restarts[-1][1], "fp32": restarts[-1][2]}},
                 "phases_ms": {k: v[0] / args.steps for k, v in prof.items()},

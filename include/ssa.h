@@ -199,6 +199,23 @@ int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_
                           int32_t residual, double* const* out_ptrs, int32_t on_device);
 
 /*
+ * ssa_wcor -- w-correlations and contributions of reconstructed components
+ * (Sec. 2.2, paragraph Separability).  With the weighted inner product
+ * (Y, Z)_w = sum_k w_k y_k z_k (w_k = |A_k|, over every channel's elements):
+ * wcor[i * n + j] = (X~_i, X~_j)_w / (||X~_i||_w ||X~_j||_w) for the
+ * components X~_i of the n = n_groups groups of group_of (as for
+ * ssa_reconstruct; group_of[i] = i gives the paper's w-correlation matrix of
+ * the elementary components), means not subtracted, 0 where a norm is 0;
+ * contrib[i] = ||X~_i||_w^2 / ||X||_w^2 (may be NULL).  wcor, contrib: host
+ * buffers of n*n and n FP64 values.  The components are reconstructed on the
+ * device and the weighted Gram matrix is summed there in FP64, in a fixed
+ * order (repeatable results).
+ * Errors: SSA_EINVAL (n_groups outside [1, 120], null pointers), SSA_ESTATE
+ * (no decomposition), SSA_ENOMEM, SSA_ECUDA.
+ */
+int ssa_wcor(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, double* wcor, double* contrib);
+
+/*
  * ssa_get_shape -- the shape calculus results (host buffers, any may be NULL):
  * L, K; origin_mask (uint8, input layout: 1 where an element is a window origin
  * kappa of K); weights (int32, input layout: w_k = |A_k|, 0 outside N').

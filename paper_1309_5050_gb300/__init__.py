@@ -210,6 +210,20 @@ class SSA:
                                           1 if residual else 0, out.ctypes.data, 0), "ssa_reconstruct")
         return [self._split(out[g * total:(g + 1) * total]) for g in range(nout)]
 
+    def wcor(self, groups=None):
+        """w-correlation matrix (n x n) and contributions (n) of the
+        reconstructed components of ``groups`` (default: the elementary
+        components 0..r-1), Sec. 2.2; computed by ssa_wcor on the device."""
+        if groups is None:
+            groups = [[i] for i in range(self.rank)]
+        gof = _group_of(groups, self.rank)
+        n = len(groups)
+        rho = np.zeros(n * n)
+        contrib = np.zeros(n)
+        L.check(self._lib.ssa_wcor(self.ctx, gof.ctypes.data_as(C.POINTER(C.c_int32)), n, rho.ctypes.data,
+                                   contrib.ctypes.data), "ssa_wcor")
+        return rho.reshape(n, n), contrib
+
     def shape(self):
         """(L, K, origin_mask, weights) in the input's layout."""
         total = self._total()

@@ -2189,6 +2189,59 @@ int ssa_reconstruct(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, int
   return ssa_reconstruct_batch(&ctx, 1, group_of, n_groups, residual, &out, on_device);
 }
 
+int ssa_wcor(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, double* wcor, double* contrib) {
+  if (!ctx || !group_of || !wcor) return fail(SSA_EINVAL, "null argument");
+  if (!ctx->ws.done) return fail(SSA_ESTATE, "context has no decomposition");
+  if (n_groups < 1 || n_groups > WCOR_MAX) return fail(SSA_EINVAL, "n_groups %d outside [1, %d]", n_groups, WCOR_MAX);
+  ssa_ctx* c = ctx;
+  const int n = n_groups, m = n + 1;
+  const int64_t total = c->total;
+  double* Y = nullptr;
+  int32_t* w = nullptr;
+  int2* pairs = nullptr;
+  double* partials = nullptr;
+  double* G = nullptr;
+  double* res = nullptr;
+  auto cleanup = [&]() {
+    for (void* q : {(void*)Y, (void*)w, (void*)pairs, (void*)partials, (void*)G, (void*)res})
+      if (q) c->release(q);
+  };
+  int rc = c->allocT(&Y, (size_t)n * total);
+  if (rc == SSA_OK) rc = ssa_reconstruct_batch(&c, 1, group_of, n_groups, 0, &Y, 1);
+  if (rc == SSA_OK) rc = c->allocT(&w, (size_t)total);
+  if (rc == SSA_OK)
+    for (auto& h : c->ch)
+      if (cudaMemcpyAsync(w + h.data_off, h.w, sizeof(int32_t) * h.nx * h.ny, cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess) {
+        rc = fail(SSA_ECUDA, "weights copy failed");
+        break;
+      }
+  std::vector<int2> hp;
+  for (int i = 0; i < m; ++i)
+    for (int j = i; j < m; ++j) hp.push_back(make_int2(i, j));
+  const int npair = (int)hp.size();
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((total + WGRAM_CH - 1) / WGRAM_CH, std::max(sms, 1)));
+  if (rc == SSA_OK) rc = upload(c, hp, &pairs);
+  if (rc == SSA_OK) rc = c->allocT(&partials, (size_t)nblk * npair);
+  if (rc == SSA_OK) rc = c->allocT(&G, (size_t)m * m);
+  if (rc == SSA_OK) rc = c->allocT(&res, (size_t)n * n + n);
+  if (rc == SSA_OK) {
+    launch_wgram(Y, total, n, c->data, c->dtype == SSA_F64 ? 1 : 0, w, total, pairs, npair, partials, nblk, c->stream);
+    launch_wcor_final(partials, nblk, pairs, npair, n, G, res, res + (size_t)n * n, c->stream);
+    if (cudaGetLastError() != cudaSuccess) rc = fail(SSA_ECUDA, "w-correlation launch failed");
+  }
+  if (rc == SSA_OK && cudaMemcpyAsync(wcor, res, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of the w-correlations failed");
+  if (rc == SSA_OK && contrib &&
+      cudaMemcpyAsync(contrib, res + (size_t)n * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of the contributions failed");
+  if (rc == SSA_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = fail(SSA_ECUDA, "w-correlation failed");
+  cleanup();
+  return rc;
+}
+
 int ssa_get_shape(const ssa_ctx* cc, int64_t* L, int64_t* K, uint8_t* origin_mask, int32_t* weights) {
   ssa_ctx* c = const_cast<ssa_ctx*>(cc);
   if (!c) return fail(SSA_EINVAL, "null argument");

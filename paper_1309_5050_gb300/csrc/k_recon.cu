@@ -266,4 +266,97 @@ INST(double, double)
 template void launch_rec_xinv<float>(const Rec2Item<float>*, int, int, int, const Cx<float>*, cudaStream_t);
 template void launch_rec_xinv<double>(const Rec2Item<double>*, int, int, int, const Cx<double>*, cudaStream_t);
 
+// ------------------------------------------------------------ w-correlations
+// A block stages sqrt(w_k) y_i[k] for the m vectors over WGRAM_CH elements
+// (zero where w_k = 0, which also drops the NaN outside N'), then each thread
+// adds the chunk's products to its WGRAM_PT pairs; blocks stride over chunks.
+__global__ void __launch_bounds__(WGRAM_NT) k_wgram(const double* __restrict__ Y, int64_t ldy, int n,
+                                                    const void* __restrict__ x, int x_f64,
+                                                    const int32_t* __restrict__ w, int64_t total,
+                                                    const int2* __restrict__ pairs, int npair,
+                                                    double* __restrict__ partials) {
+  extern __shared__ __align__(16) double ys[];     // m x WGRAM_CH, then sqrt(w) (WGRAM_CH)
+  const int m = n + 1;
+  double* sw = ys + (size_t)m * WGRAM_CH;
+  double acc[WGRAM_PT];
+  int2 pr[WGRAM_PT];
+#pragma unroll
+  for (int q = 0; q < WGRAM_PT; ++q) {
+    acc[q] = 0.0;
+    const int p = threadIdx.x + q * WGRAM_NT;
+    pr[q] = p < npair ? pairs[p] : make_int2(0, 0);
+  }
+  for (int64_t c0 = (int64_t)blockIdx.x * WGRAM_CH; c0 < total; c0 += (int64_t)gridDim.x * WGRAM_CH) {
+    __syncthreads();                                  // the previous chunk has been used
+    if (threadIdx.x < WGRAM_CH) {
+      const int64_t k = c0 + threadIdx.x;
+      const int32_t wk = k < total ? w[k] : 0;
+      sw[threadIdx.x] = wk > 0 ? sqrt((double)wk) : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * WGRAM_CH; e += WGRAM_NT) {
+      const int i = e / WGRAM_CH, t = e - i * WGRAM_CH;
+      const int64_t k = c0 + t;
+      double v = 0.0;
+      const double s = sw[t];
+      if (s != 0.0) {
+        const double y = i < n ? Y[(int64_t)i * ldy + k]
+                               : (x_f64 ? ((const double*)x)[k] : (double)((const float*)x)[k]);
+        v = s * y;
+      }
+      ys[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < WGRAM_PT; ++q) {
+      if (threadIdx.x + q * WGRAM_NT < npair) {
+        const double* yi = ys + pr[q].x * WGRAM_CH;
+        const double* yj = ys + pr[q].y * WGRAM_CH;
+        double s0 = acc[q], s1 = 0.0;
+#pragma unroll 4
+        for (int t = 0; t < WGRAM_CH; t += 2) { s0 = fma(yi[t], yj[t], s0); s1 = fma(yi[t + 1], yj[t + 1], s1); }
+        acc[q] = s0 + s1;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < WGRAM_PT; ++q) {
+    const int p = threadIdx.x + q * WGRAM_NT;
+    if (p < npair) partials[(int64_t)blockIdx.x * npair + p] = acc[q];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_wcor_final(const double* __restrict__ partials, int nblk,
+                                                    const int2* __restrict__ pairs, int npair, int n,
+                                                    double* __restrict__ G, double* __restrict__ rho,
+                                                    double* __restrict__ contrib) {
+  const int m = n + 1;
+  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partials[(int64_t)b * npair + p];
+    const int2 ij = pairs[p];
+    G[ij.x * m + ij.y] = s;
+    G[ij.y * m + ij.x] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    const double gi = G[i * m + i], gj = G[j * m + j];
+    rho[e] = (gi > 0.0 && gj > 0.0) ? (i == j ? 1.0 : G[i * m + j] / (sqrt(gi) * sqrt(gj))) : 0.0;
+  }
+  const double xx = G[n * m + n];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) contrib[i] = xx > 0.0 ? G[i * m + i] / xx : 0.0;
+}
+
+void launch_wgram(const double* Y, int64_t ldy, int n, const void* x, int x_f64, const int32_t* w, int64_t total,
+                  const int2* pairs, int npair, double* partials, int nblk, cudaStream_t st) {
+  const size_t sm = sizeof(double) * (size_t)(n + 2) * WGRAM_CH;
+  k_wgram<<<nblk, WGRAM_NT, sm, st>>>(Y, ldy, n, x, x_f64, w, total, pairs, npair, partials); count_launch();
+}
+
+void launch_wcor_final(const double* partials, int nblk, const int2* pairs, int npair, int n, double* G, double* rho,
+                       double* contrib, cudaStream_t st) {
+  k_wcor_final<<<1, 256, 0, st>>>(partials, nblk, pairs, npair, n, G, rho, contrib); count_launch();
+}
+
 }  // namespace ssa

@@ -62,6 +62,23 @@ struct RecBorderItem {
   double* out;                 // the channel's N outputs of this group
 };
 void launch_rec_border(const RecBorderItem* items, int n, cudaStream_t st);
+
+// w-correlations (Sec. 2.2, paragraph Separability): the Gram matrix
+// G = Y^T diag(w) Y of m = n + 1 vectors over the data elements -- the n
+// reconstructed components (FP64, ld ldy, NaN outside N') and, last, the data
+// x (FP32 or FP64) -- with w_k = |A_k| (zero outside N').  k_wgram: each block
+// sums the pairs listed in `pairs` (i <= j) over its chunks of elements into
+// partials[block][pair]; k_wcor_final adds the blocks' partials in block order
+// (deterministic) and writes rho (n x n, row-major; 0 where a norm is 0) and
+// the contributions G_ii / G_mm.
+constexpr int WGRAM_NT = 512;
+constexpr int WGRAM_PT = 16;                 // pairs per thread
+constexpr int WGRAM_CH = 32;                 // elements per staged chunk
+constexpr int WCOR_MAX = 120;                // components: (n+1)(n+2)/2 <= WGRAM_NT * WGRAM_PT
+void launch_wgram(const double* Y, int64_t ldy, int n, const void* x, int x_f64, const int32_t* w, int64_t total,
+                  const int2* pairs, int npair, double* partials, int nblk, cudaStream_t st);
+void launch_wcor_final(const double* partials, int nblk, const int2* pairs, int npair, int n, double* G, double* rho,
+                       double* contrib, cudaStream_t st);
 struct RecFoldItem {            // long series: segment-image sums -> one group's output
   const double* S;              // 2B x (segments), column-major
   const int32_t* w;             // n weights
