@@ -38,6 +38,7 @@ __all__ = [
     "trajectory_columns", "weights", "svd_eigen", "svd_eigen_t", "svd_jacobi", "decompose",
     "reconstruct", "reconstruct_at", "matvec", "rmatvec",
     "series_rows", "series_cols", "series_hankelize_at", "w_inner", "wcor",
+    "lrr_column", "forecast_recurrent_column",
 ]
 
 
@@ -464,4 +465,37 @@ def wcor(P: Problem, sigma, U, V, groups):
                 rho[i, j] = G[i, j] / (d[i] * d[j])
     contrib = np.diag(G) / xx if xx > 0 else np.zeros(n)
     return rho, contrib
+
+
+# ---------------------------------------------------------------- forecasting
+def lrr_column(Ug: np.ndarray) -> np.ndarray:
+    """The linear recurrence of the column recurrent forecast (Sec. 3.3,
+    eq. Forec:ContMSSAL): with pi(U_j) the last coordinate of U_j and U_j
+    without it written U_j', ``R_L = sum_j pi(U_j) U_j' / (1 - nu^2)``,
+    ``nu^2 = sum_j pi(U_j)^2``; defined only when nu^2 < 1."""
+    Ug = np.asarray(Ug, dtype=np.float64)
+    pi = Ug[-1, :]
+    nu2 = float(np.sum(pi * pi))
+    if nu2 >= 1.0:
+        raise ValueError("nu^2 >= 1: the subspace contains the last unit vector, no recurrence")
+    return (Ug[:-1, :] @ pi) / (1.0 - nu2)
+
+
+def forecast_recurrent_column(P: Problem, sigma, U, V, group, M: int):
+    """M-step recurrent column forecast of every series of a 1D or MSSA
+    problem (Sec. 3.3): the reconstruction of ``group`` is continued by
+    ``x~_{N_p + 1} = R_L . (the last L - 1 values)`` applied M times, one
+    recurrence R_L for all series.  Returns a list of M-vectors, one per
+    series."""
+    assert all(c.shape[1] == 1 for c in P.channels) and P.Lset[:, 1].max() == 0, "series problems only"
+    L = P.L
+    R = lrr_column(np.asarray(U)[:, list(group)])
+    rec = reconstruct(P, sigma, U, V, [list(group)])[0]
+    out = []
+    for c in range(len(P.channels)):
+        y = list(rec[c][:, 0])
+        for _ in range(M):
+            y.append(float(np.dot(R, y[len(y) - (L - 1):])))
+        out.append(np.array(y[len(y) - M:]))
+    return out
 

@@ -524,3 +524,46 @@ def test_wcor_invariants_on_noisy_image():
     assert np.all(contrib > 0) and contrib.sum() < 1.0 + 1e-12
     rho2, _ = O.wcor(P, sig, U, V, [[0], [1], [0, 1]])
     assert rho2[0, 2] > 0.3 and rho2[1, 2] > 0.3
+
+
+# ---------------------------------------------------------------- forecasting
+def test_lrr_reproduces_last_coordinate_of_the_subspace():
+    """R_L of eq. Forec:ContMSSAL is the recurrence of the subspace: for every
+    vector of span(U_I), its last coordinate is R_L . (the others)."""
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.normal(size=(15, 3)))
+    R = O.lrr_column(Q)
+    for j in range(3):
+        assert abs(R @ Q[:-1, j] - Q[-1, j]) <= 1e-12
+    y = Q @ rng.normal(size=3)
+    assert abs(R @ y[:-1] - y[-1]) <= 1e-12
+    e = np.zeros((15, 1))
+    e[-1, 0] = 1.0
+    with pytest.raises(ValueError):
+        O.lrr_column(e)                      # nu^2 = 1: no recurrence
+
+
+def test_recurrent_forecast_continues_a_finite_rank_series_exactly():
+    """A sum of two damped / growing harmonics has rank 4 and satisfies an
+    LRR; its reconstruction by the 4 leading triples is the series itself and
+    the recurrent forecast is its exact continuation (Sec. 3.3)."""
+    n = np.arange(75, dtype=float)
+    f = 1.01 ** n * np.cos(2 * np.pi * n / 9 + 0.2) + 0.5 * 0.99 ** n * np.cos(2 * np.pi * n / 5)
+    P = O.Problem.series(f[:60], 20)
+    sig, U, V = O.decompose(P, 4)
+    (fc,) = O.forecast_recurrent_column(P, sig, U, V, [0, 1, 2, 3], 15)
+    np.testing.assert_allclose(fc, f[60:], rtol=1e-8, atol=1e-8)
+
+
+def test_recurrent_column_forecast_mssa_common_recurrence():
+    """Two series of one frequency (different phases, amplitudes and
+    lengths) span a common rank-2 column space; one recurrence continues both
+    exactly (column forecast: the same LRR, different initial data)."""
+    n = np.arange(70, dtype=float)
+    x1 = np.cos(2 * np.pi * n / 7)
+    x2 = 2.0 * np.sin(2 * np.pi * n / 7 + 0.5)
+    P = O.Problem.multi([x1[:40], x2[:50]], 12)
+    sig, U, V = O.decompose(P, 2)
+    f1, f2 = O.forecast_recurrent_column(P, sig, U, V, [0, 1], 10)
+    np.testing.assert_allclose(f1, x1[40:50], atol=1e-9)
+    np.testing.assert_allclose(f2, x2[50:60], atol=1e-9)
