@@ -216,6 +216,21 @@ int ssa_reconstruct_batch(ssa_ctx* const* ctxs, int32_t n, const int32_t* group_
 int ssa_wcor(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, double* wcor, double* contrib);
 
 /*
+ * ssa_forecast -- M-step recurrent column forecast of a series or of every
+ * series of an MSSA system (Sec. 3.3, eq. Forec:ContMSSAL).  The component of
+ * the n_idx components idx (0-based, below the decomposed rank) is
+ * reconstructed on the device; the recurrence R = sum_j pi(U_j) U'_j /
+ * (1 - nu^2), nu^2 = sum_j pi(U_j)^2 (pi: last coordinate, U': the others, of
+ * the window-side vectors) is applied M times to the last L - 1 values of
+ * each series' reconstruction -- one recurrence for all series, FP64 sums.
+ * out (host): M values per series, series after series (s x M).
+ * Errors: SSA_EINVAL (images, M < 1, an index out of range, nu^2 >= 1),
+ * SSA_ESTATE (no decomposition), SSA_ENOMEM, SSA_ECUDA.  A series whose last
+ * L - 1 values are missing gets NaN forecasts.
+ */
+int ssa_forecast(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, double* out);
+
+/*
  * ssa_get_shape -- the shape calculus results (host buffers, any may be NULL):
  * L, K; origin_mask (uint8, input layout: 1 where an element is a window origin
  * kappa of K); weights (int32, input layout: w_k = |A_k|, 0 outside N').

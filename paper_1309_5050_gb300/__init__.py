@@ -224,6 +224,19 @@ class SSA:
                                    contrib.ctypes.data), "ssa_wcor")
         return rho.reshape(n, n), contrib
 
+    def forecast(self, group, M: int):
+        """M-step recurrent column forecast of the component ``group``
+        (0-based indices), Sec. 3.3; one array of M values for a series, a
+        list of them for an MSSA system.  Computed by ssa_forecast."""
+        idx = np.ascontiguousarray(list(group), dtype=np.int32)
+        multi = self.layout[0] == "mssa"
+        ns = len(self.layout[1]) if multi else 1
+        out = np.zeros(ns * M)
+        L.check(self._lib.ssa_forecast(self.ctx, idx.ctypes.data_as(C.POINTER(C.c_int32)), len(idx), int(M),
+                                       out.ctypes.data), "ssa_forecast")
+        parts = [out[p * M:(p + 1) * M] for p in range(ns)]
+        return parts if multi else parts[0]
+
     def shape(self):
         """(L, K, origin_mask, weights) in the input's layout."""
         total = self._total()

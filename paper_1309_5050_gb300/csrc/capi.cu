@@ -2242,6 +2242,58 @@ int ssa_wcor(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, double* wc
   return rc;
 }
 
+int ssa_forecast(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, double* out) {
+  if (!ctx || !idx || !out) return fail(SSA_EINVAL, "null argument");
+  ssa_ctx* c = ctx;
+  if (c->kind != SSA_1D && c->kind != SSA_MSSA) return fail(SSA_EINVAL, "forecasting needs a series or a system of series");
+  if (!c->ws.done) return fail(SSA_ESTATE, "context has no decomposition");
+  if (M < 1 || n_idx < 1) return fail(SSA_EINVAL, "M and n_idx must be positive");
+  const int r = c->ws.r;
+  std::vector<int32_t> gof(std::max(r, 1), -1);
+  std::vector<int32_t> hidx(idx, idx + n_idx);
+  for (int32_t i : hidx) {
+    if (i < 0 || i >= r) return fail(SSA_EINVAL, "component %d outside [0, %d)", i, r);
+    gof[i] = 0;
+  }
+  const int64_t L = c->L, total = c->total;
+  const int s = (int)c->ch.size();
+  std::vector<int64_t> hoff, hlen;
+  for (auto& h : c->ch) { hoff.push_back(h.data_off); hlen.push_back(h.nx * h.ny); }
+  const int64_t ldw = L - 1 + M;
+  double *Y = nullptr, *R = nullptr, *nu2 = nullptr, *work = nullptr, *dout = nullptr;
+  int32_t* didx = nullptr;
+  int64_t *doff = nullptr, *dlen = nullptr;
+  auto cleanup = [&]() {
+    for (void* q : {(void*)Y, (void*)R, (void*)nu2, (void*)work, (void*)dout, (void*)didx, (void*)doff, (void*)dlen})
+      if (q) c->release(q);
+  };
+  int rc = c->allocT(&Y, (size_t)total);
+  if (rc == SSA_OK) rc = ssa_reconstruct_batch(&c, 1, gof.data(), 1, 0, &Y, 1);
+  if (rc == SSA_OK) rc = upload(c, hidx, &didx);
+  if (rc == SSA_OK) rc = upload(c, hoff, &doff);
+  if (rc == SSA_OK) rc = upload(c, hlen, &dlen);
+  if (rc == SSA_OK) rc = c->allocT(&R, (size_t)std::max<int64_t>(L - 1, 1));
+  if (rc == SSA_OK) rc = c->allocT(&nu2, 1);
+  if (rc == SSA_OK) rc = c->allocT(&work, (size_t)s * ldw);
+  if (rc == SSA_OK) rc = c->allocT(&dout, (size_t)s * M);
+  if (rc == SSA_OK) {
+    if (c->ws.prec == SSA_PREC_FP64) launch_lrr<double>((const double*)c->ws.Uo, L, didx, n_idx, R, nu2, c->stream);
+    else launch_lrr<float>((const float*)c->ws.Uo, L, didx, n_idx, R, nu2, c->stream);
+    launch_forecast_rec(Y, doff, dlen, s, L, R, M, work, ldw, dout, c->stream);
+    if (cudaGetLastError() != cudaSuccess) rc = fail(SSA_ECUDA, "forecast launch failed");
+  }
+  double hnu2 = 0.0;
+  if (rc == SSA_OK && cudaMemcpyAsync(out, dout, sizeof(double) * s * M, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of the forecast failed");
+  if (rc == SSA_OK && cudaMemcpyAsync(&hnu2, nu2, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of nu^2 failed");
+  if (rc == SSA_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = fail(SSA_ECUDA, "forecast failed");
+  cleanup();
+  if (rc == SSA_OK && !(hnu2 < 1.0))
+    rc = fail(SSA_EINVAL, "nu^2 = %g >= 1: the group's window space holds the last unit vector, no recurrence", hnu2);
+  return rc;
+}
+
 int ssa_get_shape(const ssa_ctx* cc, int64_t* L, int64_t* K, uint8_t* origin_mask, int32_t* weights) {
   ssa_ctx* c = const_cast<ssa_ctx*>(cc);
   if (!c) return fail(SSA_EINVAL, "null argument");

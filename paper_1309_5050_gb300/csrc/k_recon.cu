@@ -359,4 +359,66 @@ void launch_wcor_final(const double* partials, int nblk, const int2* pairs, int 
   k_wcor_final<<<1, 256, 0, st>>>(partials, nblk, pairs, npair, n, G, rho, contrib); count_launch();
 }
 
+// ------------------------------------------------------------ forecasting
+template <typename T>
+__global__ void __launch_bounds__(256) k_lrr(const T* __restrict__ U, int64_t L, const int32_t* __restrict__ idx,
+                                             int nidx, double* __restrict__ R, double* __restrict__ nu2) {
+  double n2 = 0.0;
+  for (int j = 0; j < nidx; ++j) {
+    const double pj = (double)U[(L - 1) + L * idx[j]];
+    n2 = fma(pj, pj, n2);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *nu2 = n2;
+  const double scale = n2 < 1.0 ? 1.0 / (1.0 - n2) : 0.0;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L - 1) return;
+  double acc = 0.0;
+  for (int j = 0; j < nidx; ++j) {
+    const int64_t col = L * idx[j];
+    acc = fma((double)U[(L - 1) + col], (double)U[i + col], acc);
+  }
+  R[i] = acc * scale;
+}
+
+__global__ void __launch_bounds__(256) k_forecast_rec(const double* __restrict__ rec, const int64_t* __restrict__ off,
+                                                      const int64_t* __restrict__ len, int64_t L,
+                                                      const double* __restrict__ R, int M, double* __restrict__ work,
+                                                      int64_t ldw, double* __restrict__ out) {
+  const int p = blockIdx.x;
+  double* y = work + ldw * p;
+  const int64_t n1 = L - 1;
+  const double* src = rec + off[p] + len[p] - n1;      // the last L - 1 values of the series
+  for (int64_t t = threadIdx.x; t < n1; t += blockDim.x) y[t] = src[t];
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int m = 0; m < M; ++m) {
+    __syncthreads();                                    // y[m + L - 2] is in place
+    double a = 0.0;
+    for (int64_t t = threadIdx.x; t < n1; t += blockDim.x) a = fma(R[t], y[m + t], a);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < nw; ++w) tot += red[w];     // fixed order
+      y[m + n1] = tot;
+      out[(int64_t)p * M + m] = tot;
+    }
+  }
+}
+
+template <typename T>
+void launch_lrr(const T* U, int64_t L, const int32_t* idx, int nidx, double* R, double* nu2, cudaStream_t st) {
+  const unsigned g = (unsigned)std::max<int64_t>(1, (L - 1 + 255) / 256);
+  k_lrr<T><<<g, 256, 0, st>>>(U, L, idx, nidx, R, nu2); count_launch();
+}
+template void launch_lrr<float>(const float*, int64_t, const int32_t*, int, double*, double*, cudaStream_t);
+template void launch_lrr<double>(const double*, int64_t, const int32_t*, int, double*, double*, cudaStream_t);
+
+void launch_forecast_rec(const double* rec, const int64_t* off, const int64_t* len, int s, int64_t L,
+                         const double* R, int M, double* work, int64_t ldw, double* out, cudaStream_t st) {
+  k_forecast_rec<<<s, 256, 0, st>>>(rec, off, len, L, R, M, work, ldw, out); count_launch();
+}
+
 }  // namespace ssa

@@ -79,6 +79,18 @@ void launch_wgram(const double* Y, int64_t ldy, int n, const void* x, int x_f64,
                   const int2* pairs, int npair, double* partials, int nblk, cudaStream_t st);
 void launch_wcor_final(const double* partials, int nblk, const int2* pairs, int npair, int n, double* G, double* rho,
                        double* contrib, cudaStream_t st);
+
+// Column recurrent forecast (Sec. 3.3, eq. Forec:ContMSSAL).  k_lrr: the
+// recurrence R (L - 1 values) from the group's window-side vectors U[:, idx]
+// (T, ld L), R = sum_j pi_j U'_j / (1 - nu^2), and nu^2 into *nu2 (the caller
+// refuses nu^2 >= 1).  k_forecast_rec: one block per series p continues the
+// reconstruction rec[off[p] .. off[p] + len[p]) by M values, each the dot
+// product of R with the last L - 1 values (block sum in a fixed order), into
+// out[p * M ..]; work holds the running series (ld ldw >= L - 1 + M).
+template <typename T>
+void launch_lrr(const T* U, int64_t L, const int32_t* idx, int nidx, double* R, double* nu2, cudaStream_t st);
+void launch_forecast_rec(const double* rec, const int64_t* off, const int64_t* len, int s, int64_t L,
+                         const double* R, int M, double* work, int64_t ldw, double* out, cudaStream_t st);
 struct RecFoldItem {            // long series: segment-image sums -> one group's output
   const double* S;              // 2B x (segments), column-major
   const int32_t* w;             // n weights

@@ -1,0 +1,94 @@
+"""GPU parity of the recurrent column forecast (Sec. 3.3, eq. Forec:ContMSSAL).
+
+ssa_forecast reconstructs the component on the device, forms the recurrence
+from the window-side vectors and continues every series.  Checked against the
+continuation of a finite-rank series and against the oracle on noisy series
+and an MSSA system (groups bounded by spectral gaps).
+
+Tolerances: FP64 form 1e-7 of max|x|; FP32 form 5e-3 of max|x| (the
+starting values carry the FP32 form's reconstruction error, up to 1e-4 of
+max|x|, and the forecast feeds on itself).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1309_5050_gb300 as pkg  # noqa: E402
+from oracle import ssa_oracle as O  # noqa: E402
+from paper_1309_5050_gb300 import _lib as LL  # noqa: E402
+
+TOL = {"fp32": 5e-3, "fp64": 1e-7}
+
+
+def noisy_series(n, seed):
+    rng = np.random.default_rng(seed)
+    t = np.arange(n, dtype=float)
+    return 0.02 * t + 3 * np.sin(2 * np.pi * t / 11.3) + 1.5 * np.cos(2 * np.pi * t / 4.7 + 0.3) + rng.normal(0, 0.3, n)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_forecast_continues_finite_rank_series(prec):
+    """A rank-4 series (two damped / growing harmonics) with 1e-6 noise: the
+    forecast of the four leading components continues the noiseless series
+    to the noise level."""
+    n = np.arange(80, dtype=float)
+    f = 1.01 ** n * np.cos(2 * np.pi * n / 9 + 0.2) + 0.5 * 0.99 ** n * np.cos(2 * np.pi * n / 5)
+    x = f[:60] + 1e-6 * np.random.default_rng(0).normal(size=60)
+    s = pkg.SSA.series(x, 20)
+    s.decompose(4, prec)
+    fc = s.forecast([0, 1, 2, 3], 20)
+    assert np.max(np.abs(fc - f[60:])) <= 1e-5 * np.max(np.abs(f))
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_forecast_matches_oracle(prec):
+    x = noisy_series(600, 5)
+    s = pkg.SSA.series(x, 200)
+    P = O.Problem.series(x, 200)
+    s.decompose(6, prec)
+    so, Uo, Vo = O.decompose(P, 6)
+    # the trend and the two harmonic pairs: ranks 1 + 2 + 2 lead the spectrum
+    grp = [0, 1, 2, 3, 4]
+    assert so[4] / so[5] > 1.5
+    (ref,) = O.forecast_recurrent_column(P, so, Uo, Vo, grp, 12)
+    got = s.forecast(grp, 12)
+    assert np.max(np.abs(got - ref)) <= TOL[prec] * np.max(np.abs(x))
+    s.close()
+    xs = [noisy_series(n, 20 + i) for i, n in enumerate((300, 350, 280))]
+    xs32 = [np.asarray(v, np.float32).astype(np.float64) for v in xs]
+    m = pkg.SSA.multi(xs, 100)
+    Pm = O.Problem.multi(xs32, 100)
+    m.decompose(6, prec)
+    so, Uo, Vo = O.decompose(Pm, 6)
+    assert so[4] / so[5] > 1.5
+    refs = O.forecast_recurrent_column(Pm, so, Uo, Vo, grp, 8)
+    gots = m.forecast(grp, 8)
+    for g, r_ in zip(gots, refs):
+        assert np.max(np.abs(g - r_)) <= TOL[prec] * max(np.max(np.abs(v)) for v in xs32)
+    m.close()
+
+
+def test_forecast_errors():
+    x = noisy_series(300, 1)
+    s = pkg.SSA.series(x, 100)
+    with pytest.raises(pkg.SSAError) as e:
+        s.forecast([0], 5)
+    assert e.value.code == LL.SSA_ESTATE
+    s.decompose(4, "fp32")
+    with pytest.raises(pkg.SSAError) as e:
+        s.forecast([7], 5)
+    assert e.value.code == LL.SSA_EINVAL
+    s.close()
+    img = np.random.default_rng(2).normal(size=(20, 20))
+    g = pkg.SSA.image(img, 5, 5)
+    g.decompose(3, "fp32")
+    with pytest.raises(pkg.SSAError) as e:
+        g.forecast([0], 5)
+    assert e.value.code == LL.SSA_EINVAL
+    g.close()
