@@ -38,7 +38,7 @@ __all__ = [
     "trajectory_columns", "weights", "svd_eigen", "svd_eigen_t", "svd_jacobi", "decompose",
     "reconstruct", "reconstruct_at", "matvec", "rmatvec",
     "series_rows", "series_cols", "series_hankelize_at", "w_inner", "wcor",
-    "lrr_column", "forecast_recurrent_column",
+    "lrr_column", "forecast_recurrent_column", "forecast_vector_column",
 ]
 
 
@@ -497,5 +497,46 @@ def forecast_recurrent_column(P: Problem, sigma, U, V, group, M: int):
         for _ in range(M):
             y.append(float(np.dot(R, y[len(y) - (L - 1):])))
         out.append(np.array(y[len(y) - M:]))
+    return out
+
+
+def forecast_vector_column(P: Problem, sigma, U, V, group, M: int):
+    """M-step vector column forecast of every series of a 1D or MSSA problem
+    (Sec. 3.3, vector forecasting, eqs. PGcolumn and V_FORcolumn).
+
+    For series p the columns of the reconstructed matrix X^ = U_I U_I^T X^(p)
+    (the lagged vectors projected on the group's column space) are continued
+    by Z_j = [Pi Z_{j-1}' ; R_L . Z_{j-1}'] for j = K_p + 1 .. K_p + M + L - 1,
+    where Z' drops the first coordinate, Pi projects R^{L-1} orthogonally on
+    the span of the vectors U_i without their last coordinate, and R_L is the
+    recurrence of ``lrr_column``.  The extended L x (K_p + M + L - 1) matrix
+    is diagonally averaged and its values N_p + 1 .. N_p + M are the
+    forecast.  Returns a list of M-vectors, one per series."""
+    assert all(c.shape[1] == 1 for c in P.channels) and P.Lset[:, 1].max() == 0, "series problems only"
+    L = P.L
+    Ug = np.asarray(U, dtype=np.float64)[:, list(group)]
+    R = lrr_column(Ug)
+    Ub = Ug[:-1, :]                                   # U_i without the last coordinate
+    Pi = Ub @ np.linalg.solve(Ub.T @ Ub, Ub.T)        # orthogonal projector on span(Ub)
+    out = []
+    for c in range(len(P.channels)):
+        X = P.block(c)                                # L x K_p trajectory matrix
+        Kp = X.shape[1]
+        Z = np.zeros((L, Kp + M + L - 1))
+        Z[:, :Kp] = Ug @ (Ug.T @ X)
+        for j in range(Kp, Kp + M + L - 1):
+            y = Z[1:, j - 1]
+            Z[:-1, j] = Pi @ y
+            Z[-1, j] = R @ y
+        # diagonal averaging of the L x Kz matrix: element n collects Z[i, j], i + j = n
+        Kz = Z.shape[1]
+        acc = np.zeros(L + Kz - 1)
+        cnt = np.zeros(L + Kz - 1)
+        for i in range(L):
+            acc[i:i + Kz] += Z[i]
+            cnt[i:i + Kz] += 1
+        z = acc / cnt
+        Np = len(P.channels[c])
+        out.append(z[Np:Np + M])
     return out
 

@@ -567,3 +567,24 @@ def test_recurrent_column_forecast_mssa_common_recurrence():
     f1, f2 = O.forecast_recurrent_column(P, sig, U, V, [0, 1], 10)
     np.testing.assert_allclose(f1, x1[40:50], atol=1e-9)
     np.testing.assert_allclose(f2, x2[50:60], atol=1e-9)
+
+
+def test_vector_forecast_continues_finite_rank_series_exactly():
+    """The vector column forecast (Sec. 3.3, eqs. PGcolumn, V_FORcolumn)
+    continues a finite-rank series exactly, for one series and for an MSSA
+    pair sharing its column space."""
+    n = np.arange(75, dtype=float)
+    f = 1.01 ** n * np.cos(2 * np.pi * n / 9 + 0.2) + 0.5 * 0.99 ** n * np.cos(2 * np.pi * n / 5)
+    P = O.Problem.series(f[:60], 20)
+    sig, U, V = O.decompose(P, 4)
+    (fc,) = O.forecast_vector_column(P, sig, U, V, [0, 1, 2, 3], 15)
+    np.testing.assert_allclose(fc, f[60:], rtol=1e-8, atol=1e-8)
+    n = np.arange(70, dtype=float)
+    x1 = np.cos(2 * np.pi * n / 7)
+    x2 = 2.0 * np.sin(2 * np.pi * n / 7 + 0.5)
+    P = O.Problem.multi([x1[:40], x2[:50]], 12)
+    sig, U, V = O.decompose(P, 2)
+    f1, f2 = O.forecast_vector_column(P, sig, U, V, [0, 1], 10)
+    np.testing.assert_allclose(f1, x1[40:50], atol=1e-9)
+    np.testing.assert_allclose(f2, x2[50:60], atol=1e-9)
+
