@@ -39,6 +39,7 @@ __all__ = [
     "reconstruct", "reconstruct_at", "matvec", "rmatvec",
     "series_rows", "series_cols", "series_hankelize_at", "w_inner", "wcor",
     "lrr_column", "forecast_recurrent_column", "forecast_vector_column",
+    "forecast_recurrent_row", "forecast_vector_row",
 ]
 
 
@@ -535,6 +536,81 @@ def forecast_vector_column(P: Problem, sigma, U, V, group, M: int):
         for i in range(L):
             acc[i:i + Kz] += Z[i]
             cnt[i:i + Kz] += 1
+        z = acc / cnt
+        Np = len(P.channels[c])
+        out.append(z[Np:Np + M])
+    return out
+
+
+def _row_parts(P: Problem, V, group):
+    """For the row forecasts: the blocks of V_I per series, S = [mu(V_j)] (the
+    last coordinate of every series' block, s x r), V_I with those rows
+    removed ((K - s) x r), and R_K = (I_s - S S^T)^-1 S Vbar^T (Sec. 3.3,
+    eq. Forec:ContMSSAK)."""
+    Vg = np.asarray(V, dtype=np.float64)[:, list(group)]
+    s_ = len(P.channels)
+    last = [P.offsets[c + 1] - 1 for c in range(s_)]
+    keep = np.ones(P.K, bool)
+    keep[last] = False
+    S = Vg[last, :]
+    Vbar = Vg[keep, :]
+    RK = np.linalg.solve(np.eye(s_) - S @ S.T, S @ Vbar.T)
+    return Vg, S, Vbar, RK, keep
+
+
+def forecast_recurrent_row(P: Problem, sigma, U, V, group, M: int):
+    """M-step recurrent row forecast of an MSSA system (Sec. 3.3, eq.
+    Forec:ContMSSAK): every step the next value of each series is R_K Z, Z the
+    stacked last K_p - 1 reconstructed values of all series -- a different
+    relation per series, the same data for all.  Returns one M-vector per
+    series."""
+    assert all(c.shape[1] == 1 for c in P.channels) and P.Lset[:, 1].max() == 0, "series problems only"
+    _, _, _, RK, _ = _row_parts(P, V, group)
+    rec = reconstruct(P, sigma, U, V, [list(group)])[0]
+    ys = [list(rec[c][:, 0]) for c in range(len(P.channels))]
+    for _ in range(M):
+        Z = np.concatenate([ys[c][len(ys[c]) - (P.Ks[c] - 1):] for c in range(len(P.channels))])
+        nxt = RK @ Z
+        for c in range(len(P.channels)):
+            ys[c].append(float(nxt[c]))
+    return [np.array(y[len(y) - M:]) for y in ys]
+
+
+def forecast_vector_row(P: Problem, sigma, U, V, group, M: int):
+    """M-step vector row forecast of an MSSA system (Sec. 3.3, eqs. PGrow and
+    V_FORrow).  The rows of the reconstructed matrix X^ = X V_I V_I^T are
+    continued by A = P(Z): with Z' the row without the first coordinate of
+    each series' block, A without the last coordinate of each block is the
+    orthogonal projection of Z' on span(Vbar_I), and the last coordinates are
+    R_K Z'.  The (L + M + K* - 1) x K matrix of rows is averaged along each
+    series' anti-diagonals (the MSSA reconstruction step) and the values
+    N_p + 1 .. N_p + M of series p are its forecast."""
+    assert all(c.shape[1] == 1 for c in P.channels) and P.Lset[:, 1].max() == 0, "series problems only"
+    Vg, S, Vbar, RK, keep = _row_parts(P, V, group)
+    Pi = Vbar @ np.linalg.solve(Vbar.T @ Vbar, Vbar.T)      # projector on span(Vbar) in R^(K - s)
+    X = P.matrix()
+    L = P.L
+    s_ = len(P.channels)
+    Kstar = max(P.Ks)
+    rows = L + M + Kstar - 1
+    Z = np.zeros((rows, P.K))
+    Z[:L] = (X @ Vg) @ Vg.T
+    first = np.ones(P.K, bool)                              # drop the first coordinate of each block
+    first[P.offsets[:-1]] = False
+    last_idx = [P.offsets[c + 1] - 1 for c in range(s_)]
+    for i in range(L, rows):
+        zp = Z[i - 1, first]
+        Z[i, keep] = Pi @ zp
+        Z[i, last_idx] = RK @ zp
+    out = []
+    for c in range(s_):
+        blk = Z[:, P.offsets[c]:P.offsets[c + 1]]           # rows x K_c; element (i, j) is series index i + j
+        Kc = blk.shape[1]
+        acc = np.zeros(rows + Kc - 1)
+        cnt = np.zeros(rows + Kc - 1)
+        for j in range(Kc):
+            acc[j:j + rows] += blk[:, j]
+            cnt[j:j + rows] += 1
         z = acc / cnt
         Np = len(P.channels[c])
         out.append(z[Np:Np + M])

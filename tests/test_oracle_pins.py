@@ -588,3 +588,19 @@ def test_vector_forecast_continues_finite_rank_series_exactly():
     np.testing.assert_allclose(f1, x1[40:50], atol=1e-9)
     np.testing.assert_allclose(f2, x2[50:60], atol=1e-9)
 
+
+@pytest.mark.parametrize("lens", [(40, 40), (40, 50)])
+def test_row_forecasts_continue_an_mssa_pair_exactly(lens):
+    """Recurrent and vector row forecasts (Sec. 3.3, eqs. Forec:ContMSSAK,
+    PGrow, V_FORrow) continue a finite-rank MSSA pair exactly, for equal and
+    unequal series lengths."""
+    n = np.arange(70, dtype=float)
+    x1 = np.cos(2 * np.pi * n / 7)
+    x2 = 2.0 * np.sin(2 * np.pi * n / 7 + 0.5)
+    P = O.Problem.multi([x1[:lens[0]], x2[:lens[1]]], 12)
+    sig, U, V = O.decompose(P, 2)
+    for fn in (O.forecast_recurrent_row, O.forecast_vector_row):
+        f1, f2 = fn(P, sig, U, V, [0, 1], 10)
+        np.testing.assert_allclose(f1, x1[lens[0]:lens[0] + 10], atol=1e-9)
+        np.testing.assert_allclose(f2, x2[lens[1]:lens[1] + 10], atol=1e-9)
+
