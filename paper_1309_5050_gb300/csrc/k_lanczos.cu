@@ -438,6 +438,7 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
   const double* bp = b_in_smem ? Bs : it.B;
   const int bld = b_in_smem ? cs : ld;
   __shared__ int rotated;
+  __shared__ int ns_bad;
   __shared__ double nrm2[KMAX + 2];
   __shared__ double nrm[KMAX + 2];
   __shared__ float nrm2f[KMAX + 2];
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     const int c = e / nc, m = e - c * nc;
     V32[c * lv + m] = (m == c) ? 1.0f : 0.0f;
   }
+  if (threadIdx.x == 0) ns_bad = 0;
   __syncthreads();
   const float tol32 = 1.1920929e-7f * (float)(k > 8 ? k : 8);
   int sweeps32 = 0;
@@ -520,7 +522,9 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
         if (a >= 0) {
           al = nrm2f[a];
           be = nrm2f[b];
-          rot = ga != 0.0f && fabsf(ga) > tol32 * sqrt_approx(al) * sqrt_approx(be);
+          // columns that vanished (or whose squared norms underflowed) are
+          // left alone: their dot products are below FP32 resolution
+          rot = ga != 0.0f && al > 0.0f && be > 0.0f && fabsf(ga) > tol32 * sqrt_approx(al) * sqrt_approx(be);
         }
         if (rot) {
           // approximate division and square roots: the FP64 steps make the
@@ -528,7 +532,9 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
           const float zeta = __fdividef(be - al, 2.0f * ga), az = fabsf(zeta);
           tt = az > 1e18f ? __fdividef(0.5f, zeta)
                           : __fdividef(copysignf(1.0f, zeta), az + sqrt_approx(fmaf(zeta, zeta, 1.0f)));
-          if (tt == 0.0f) rot = false;
+          // |t| <= 1 for the inner rotation; a denormal divisor in the
+          // approximate division can give 0, inf or NaN instead: no rotation
+          if (!(fabsf(tt) > 0.0f && fabsf(tt) <= 2.0f)) rot = false;
         }
         if (rot) {
           const float cn = rsqrtf(fmaf(tt, tt, 1.0f)), sn = cn * tt;
@@ -578,7 +584,11 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
       int m = 0;
       for (; m + 1 < nc; m += 2) { e0 = fma(va[m], vb[m], e0); e1 = fma(va[m + 1], vb[m + 1], e1); }
       if (m < nc) e0 = fma(va[m], vb[m], e0);
-      const float ev = (float)((e0 + e1) - (a == b ? 1.0 : 0.0));
+      const double ed = (e0 + e1) - (a == b ? 1.0 : 0.0);
+      // one step leaves |V'^T V' - I| ~ 3|E|^2/4: with |E| <= 3e-5 the
+      // singular values of W0 V' are those of W0 to 4e-10 (also catches NaN)
+      if (!(fabs(ed) <= 3e-5)) ns_bad = 1;
+      const float ev = (float)ed;
       E32[b * lv + a] = ev;
       E32[a * lv + b] = ev;
       rem += blockDim.x;
@@ -586,11 +596,20 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
-    const int c = e / nc, m = e - c * nc;
-    float acc = 0.0f;
-    for (int j = 0; j < nc; ++j) acc = fmaf(V32[j * lv + m], E32[c * lv + j], acc);
-    V64[c * s0 + m] -= 0.5 * (double)acc;
+  if (ns_bad) {
+    // V too far from orthogonal for one step (the FP32 sweeps went wrong or
+    // did not settle): V' = I, and the FP64 sweeps orthogonalise W0 itself
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+      const int c = e / nc, m = e - c * nc;
+      V64[c * s0 + m] = (m == c) ? 1.0 : 0.0;
+    }
+  } else {
+    for (int e = threadIdx.x; e < nc * nc; e += blockDim.x) {
+      const int c = e / nc, m = e - c * nc;
+      float acc = 0.0f;
+      for (int j = 0; j < nc; ++j) acc = fmaf(V32[j * lv + m], E32[c * lv + j], acc);
+      V64[c * s0 + m] -= 0.5 * (double)acc;
+    }
   }
   __syncthreads();
 
@@ -704,7 +723,7 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
             const double az = fabs(zeta);
             tt = az > 1e150 ? 0.5 / zeta : copysign(1.0, zeta) / (az + sqrt(1.0 + zeta * zeta));
           }
-          if (tt == 0.0) rot = false;
+          if (!(fabs(tt) > 0.0 && fabs(tt) <= 2.0)) rot = false;
         }
         if (rot) {
           // |t| < 1e-4 (the polish after the FP32 sweeps): 1 / sqrt(1 + t^2)
