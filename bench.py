@@ -53,6 +53,21 @@ def problem_series(seed):
     return W.mssa_series(CFG["s"], seed=seed)
 
 
+def problem_seed(rank, i):
+    """Seed of problem i on a rank: every replica draws its own problems."""
+    return 2 + rank * 100003 + i
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time -- the job ends with it; unchanged on one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ oracle arm
 def run_oracle(n_problems, base_seed):
     from oracle import ssa_oracle as O
@@ -393,7 +408,7 @@ def main():
     # inputs: B problems per rank, distinct seeds per rank
     probs = []
     for i in range(B):
-        xs = problem_series(2 + rank * 100003 + i)
+        xs = problem_series(problem_seed(rank, i))
         lens = np.array([len(x) for x in xs], dtype=np.int64)
         flat = np.concatenate(xs).astype(np.float32)
         probs.append((lens, flat))
@@ -454,22 +469,14 @@ def main():
     clocks = ck.summary()
 
     ps_info = _probe_info(pkg, probs, CFG, stream, args)
-    ms = sum(ts) / len(ts)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(ts) / len(ts), dist, dev)
     value = world * B / (ms / 1000.0)
 
     # end to end from pinned host memory (one untimed step first, as for the device path)
     step(host_inputs, host_outs, args.prec)
     torch.cuda.synchronize()
     ts_e2e = timed(max(2, args.steps // 2), host_inputs, host_outs, args.prec)
-    ms_e2e = sum(ts_e2e) / len(ts_e2e)
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(sum(ts_e2e) / len(ts_e2e), dist, dev)
     h2d = int(sum(f.nbytes for _, f in probs))
     d2h = int(sum(o.numel() * 8 for o in host_outs))
 
@@ -478,8 +485,8 @@ def main():
     if not args.no_fp64_form and args.prec == "fp32":
         step(dev_inputs, dev_outs, "fp64")
         t64 = timed(max(1, args.steps // 3), dev_inputs, dev_outs, "fp64")
-        fp64 = {"value": world * B / (sum(t64) / len(t64) / 1000.0), "unit": "decomps/s",
-                "ms_per_step": sum(t64) / len(t64)}
+        ms64 = max_over_ranks(sum(t64) / len(t64), dist, dev)
+        fp64 = {"value": world * B / (ms64 / 1000.0), "unit": "decomps/s", "ms_per_step": ms64}
 
     # serving: a Poisson stream of mixed requests through ssa_server_*
     serving = None
