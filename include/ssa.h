@@ -231,6 +231,20 @@ int ssa_wcor(ssa_ctx* ctx, const int32_t* group_of, int32_t n_groups, double* wc
 int ssa_forecast(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, double* out);
 
 /*
+ * ssa_forecast_vector -- M-step vector column forecast of a series or of every
+ * series of an MSSA system (Sec. 3.3, eqs. PGcolumn and V_FORcolumn).  The
+ * last lagged vector of each series is projected on the window space of the
+ * n_idx components idx, continued M + L - 1 times by the operator that drops
+ * its first coordinate, projects the rest on the span of the U_j without
+ * their last coordinate and appends the recurrence value, and the continued
+ * lagged vectors are diagonally averaged.  On the device this runs in the
+ * coefficients of the window space (c_t = D c_{t-1} with an n_idx x n_idx
+ * shift matrix D), FP64 sums in a fixed order.  out (host): M values per
+ * series, series after series.  M <= 65535.  Errors as for ssa_forecast.
+ */
+int ssa_forecast_vector(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, double* out);
+
+/*
  * ssa_get_shape -- the shape calculus results (host buffers, any may be NULL):
  * L, K; origin_mask (uint8, input layout: 1 where an element is a window origin
  * kappa of K); weights (int32, input layout: w_k = |A_k|, 0 outside N').

@@ -2294,6 +2294,58 @@ int ssa_forecast(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, dou
   return rc;
 }
 
+int ssa_forecast_vector(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, double* out) {
+  if (!ctx || !idx || !out) return fail(SSA_EINVAL, "null argument");
+  ssa_ctx* c = ctx;
+  if (c->kind != SSA_1D && c->kind != SSA_MSSA) return fail(SSA_EINVAL, "forecasting needs a series or a system of series");
+  if (!c->ws.done) return fail(SSA_ESTATE, "context has no decomposition");
+  if (M < 1 || n_idx < 1) return fail(SSA_EINVAL, "M and n_idx must be positive");
+  if (M > 65535) return fail(SSA_EINVAL, "M = %d above 65535", M);
+  const int r = c->ws.r;
+  std::vector<int32_t> hidx(idx, idx + n_idx);
+  for (int32_t i : hidx)
+    if (i < 0 || i >= r) return fail(SSA_EINVAL, "component %d outside [0, %d)", i, r);
+  const int64_t L = c->L;
+  const int s = (int)c->ch.size();
+  std::vector<int64_t> hoff, hlen;
+  for (auto& h : c->ch) { hoff.push_back(h.data_off); hlen.push_back(h.nx * h.ny); }
+  double *G = nullptr, *D = nullptr, *nu2 = nullptr, *cs = nullptr, *dout = nullptr;
+  int32_t* didx = nullptr;
+  int64_t *doff = nullptr, *dlen = nullptr;
+  auto cleanup = [&]() {
+    for (void* q : {(void*)G, (void*)D, (void*)nu2, (void*)cs, (void*)dout, (void*)didx, (void*)doff, (void*)dlen})
+      if (q) c->release(q);
+  };
+  int rc = upload(c, hidx, &didx);
+  if (rc == SSA_OK) rc = upload(c, hoff, &doff);
+  if (rc == SSA_OK) rc = upload(c, hlen, &dlen);
+  if (rc == SSA_OK) rc = c->allocT(&G, (size_t)n_idx * n_idx);
+  if (rc == SSA_OK) rc = c->allocT(&D, (size_t)n_idx * n_idx);
+  if (rc == SSA_OK) rc = c->allocT(&nu2, 1);
+  if (rc == SSA_OK) rc = c->allocT(&cs, (size_t)s * (M + L) * n_idx);
+  if (rc == SSA_OK) rc = c->allocT(&dout, (size_t)s * M);
+  if (rc == SSA_OK) {
+    const int x_f64 = c->dtype == SSA_F64 ? 1 : 0;
+    if (c->ws.prec == SSA_PREC_FP64)
+      launch_vector_forecast<double>((const double*)c->ws.Uo, L, didx, n_idx, c->data, x_f64, doff, dlen, s, M, G, D,
+                                     nu2, cs, dout, c->stream);
+    else
+      launch_vector_forecast<float>((const float*)c->ws.Uo, L, didx, n_idx, c->data, x_f64, doff, dlen, s, M, G, D,
+                                    nu2, cs, dout, c->stream);
+    if (cudaGetLastError() != cudaSuccess) rc = fail(SSA_ECUDA, "vector forecast launch failed");
+  }
+  double hnu2 = 0.0;
+  if (rc == SSA_OK && cudaMemcpyAsync(out, dout, sizeof(double) * s * M, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of the forecast failed");
+  if (rc == SSA_OK && cudaMemcpyAsync(&hnu2, nu2, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of nu^2 failed");
+  if (rc == SSA_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = fail(SSA_ECUDA, "vector forecast failed");
+  cleanup();
+  if (rc == SSA_OK && !(hnu2 < 1.0))
+    rc = fail(SSA_EINVAL, "nu^2 = %g >= 1: the group's window space holds the last unit vector, no recurrence", hnu2);
+  return rc;
+}
+
 int ssa_get_shape(const ssa_ctx* cc, int64_t* L, int64_t* K, uint8_t* origin_mask, int32_t* weights) {
   ssa_ctx* c = const_cast<ssa_ctx*>(cc);
   if (!c) return fail(SSA_EINVAL, "null argument");

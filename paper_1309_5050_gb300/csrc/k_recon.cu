@@ -421,4 +421,115 @@ void launch_forecast_rec(const double* rec, const int64_t* off, const int64_t* l
   k_forecast_rec<<<s, 256, 0, st>>>(rec, off, len, L, R, M, work, ldw, out); count_launch();
 }
 
+// ------------------------------------------------------------ vector forecast
+__device__ __forceinline__ double vf_block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nw; ++w) t += red[w];     // fixed order
+  return t;
+}
+
+// G[a * nidx + b] = sum_{i < L-1} U[i, idx_a] U[i+1, idx_b]
+template <typename T>
+__global__ void __launch_bounds__(256) k_vf_gram(const T* __restrict__ U, int64_t L, const int32_t* __restrict__ idx,
+                                                 int nidx, double* __restrict__ G) {
+  __shared__ double red[32];
+  const int a = blockIdx.x / nidx, b = blockIdx.x - a * nidx;
+  const T* ua = U + L * idx[a];
+  const T* ub = U + L * idx[b] + 1;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < L - 1; i += blockDim.x) acc = fma((double)ua[i], (double)ub[i], acc);
+  const double t = vf_block_sum(acc, red);
+  if (threadIdx.x == 0) G[blockIdx.x] = t;
+}
+
+// D = G + pi (pi^T G) / (1 - nu^2), nu^2 = |pi|^2 (written to *nu2)
+template <typename T>
+__global__ void __launch_bounds__(256) k_vf_shift(const T* __restrict__ U, int64_t L, const int32_t* __restrict__ idx,
+                                                  int nidx, const double* __restrict__ G, double* __restrict__ D,
+                                                  double* __restrict__ nu2) {
+  double n2 = 0.0;
+  for (int j = 0; j < nidx; ++j) {
+    const double pj = (double)U[(L - 1) + L * idx[j]];
+    n2 = fma(pj, pj, n2);
+  }
+  if (threadIdx.x == 0) *nu2 = n2;
+  const double scale = n2 < 1.0 ? 1.0 / (1.0 - n2) : 0.0;
+  for (int e = threadIdx.x; e < nidx * nidx; e += blockDim.x) {
+    const int a = e / nidx, b = e - a * nidx;
+    double pg = 0.0;                               // (pi^T G)_b
+    for (int c = 0; c < nidx; ++c) pg = fma((double)U[(L - 1) + L * idx[c]], G[c * nidx + b], pg);
+    D[e] = G[e] + (double)U[(L - 1) + L * idx[a]] * pg * scale;
+  }
+}
+
+// c_0 = U_I^T (last L values of series p), then c_t = D c_{t-1}, t < M + L
+template <typename T>
+__global__ void __launch_bounds__(256) k_vf_coef(const T* __restrict__ U, int64_t L, const int32_t* __restrict__ idx,
+                                                 int nidx, const void* __restrict__ x, int x_f64,
+                                                 const int64_t* __restrict__ off, const int64_t* __restrict__ len,
+                                                 int M, const double* __restrict__ D, double* __restrict__ cs) {
+  __shared__ double red[32];
+  const int p = blockIdx.x;
+  double* c = cs + (int64_t)p * (M + L) * nidx;
+  const int64_t x0 = off[p] + len[p] - L;
+  for (int a = 0; a < nidx; ++a) {
+    const T* ua = U + L * idx[a];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < L; i += blockDim.x) {
+      const double xv = x_f64 ? ((const double*)x)[x0 + i] : (double)((const float*)x)[x0 + i];
+      acc = fma((double)ua[i], xv, acc);
+    }
+    const double t = vf_block_sum(acc, red);
+    if (threadIdx.x == 0) c[a] = t;
+  }
+  for (int64_t t = 1; t < M + L; ++t) {
+    __syncthreads();                               // c_{t-1} is complete
+    const double* prev = c + (t - 1) * nidx;
+    double* cur = c + t * nidx;
+    for (int a = threadIdx.x; a < nidx; a += blockDim.x) {
+      double acc = 0.0;
+      for (int b = 0; b < nidx; ++b) acc = fma(D[a * nidx + b], prev[b], acc);
+      cur[a] = acc;
+    }
+  }
+}
+
+// out[p * M + m] = (1 / L) sum_{i < L} sum_a U[i, idx_a] c_{L + m - i}[a]; block (m, p)
+template <typename T>
+__global__ void __launch_bounds__(256) k_vf_out(const T* __restrict__ U, int64_t L, const int32_t* __restrict__ idx,
+                                                int nidx, int M, const double* __restrict__ cs, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int m = blockIdx.x, p = blockIdx.y;
+  const double* c = cs + (int64_t)p * (M + L) * nidx;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < L; i += blockDim.x) {
+    const double* ct = c + (L + m - i) * nidx;
+    for (int a = 0; a < nidx; ++a) acc = fma((double)U[i + L * idx[a]], ct[a], acc);
+  }
+  const double t = vf_block_sum(acc, red);
+  if (threadIdx.x == 0) out[(int64_t)p * M + m] = t / (double)L;
+}
+
+template <typename T>
+void launch_vector_forecast(const T* U, int64_t L, const int32_t* idx, int nidx, const void* x, int x_f64,
+                            const int64_t* off, const int64_t* len, int s, int M, double* G, double* D, double* nu2,
+                            double* cs, double* out, cudaStream_t st) {
+  k_vf_gram<T><<<nidx * nidx, 256, 0, st>>>(U, L, idx, nidx, G); count_launch();
+  k_vf_shift<T><<<1, 256, 0, st>>>(U, L, idx, nidx, G, D, nu2); count_launch();
+  k_vf_coef<T><<<s, 256, 0, st>>>(U, L, idx, nidx, x, x_f64, off, len, M, D, cs); count_launch();
+  k_vf_out<T><<<dim3(M, s), 256, 0, st>>>(U, L, idx, nidx, M, cs, out); count_launch();
+}
+template void launch_vector_forecast<float>(const float*, int64_t, const int32_t*, int, const void*, int,
+                                            const int64_t*, const int64_t*, int, int, double*, double*, double*,
+                                            double*, double*, cudaStream_t);
+template void launch_vector_forecast<double>(const double*, int64_t, const int32_t*, int, const void*, int,
+                                             const int64_t*, const int64_t*, int, int, double*, double*, double*,
+                                             double*, double*, cudaStream_t);
+
 }  // namespace ssa

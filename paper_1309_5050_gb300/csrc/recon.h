@@ -91,6 +91,21 @@ template <typename T>
 void launch_lrr(const T* U, int64_t L, const int32_t* idx, int nidx, double* R, double* nu2, cudaStream_t st);
 void launch_forecast_rec(const double* rec, const int64_t* off, const int64_t* len, int s, int64_t L,
                          const double* R, int M, double* work, int64_t ldw, double* out, cudaStream_t st);
+
+// Vector column forecast in the coefficients of the group's window space
+// (Sec. 3.3, eqs. PGcolumn and V_FORcolumn; the fast form with a shift
+// matrix).  Every continued lagged vector is U_I c_t with c_t = D c_{t-1},
+// D = (I + pi pi^T / (1 - nu^2)) Ubar^T Uup (Ubar, Uup: U_I without its last,
+// first row; pi its last row); c_0 = U_I^T (the last L values of the series);
+// forecast m = (1 / L) sum_{i < L} (U_I c_{L + m - i})_i (diagonal averaging of
+// the continued columns).  k_vf_gram: G = Ubar^T Uup, one block per entry;
+// k_vf_shift: D and nu^2 (one block); k_vf_coef: c_0 .. c_{M+L-1} per series
+// (one block each, stored in cs, ld nidx, per series (M + L) rows);
+// k_vf_out: the M values of every series.
+template <typename T>
+void launch_vector_forecast(const T* U, int64_t L, const int32_t* idx, int nidx, const void* x, int x_f64,
+                            const int64_t* off, const int64_t* len, int s, int M, double* G, double* D, double* nu2,
+                            double* cs, double* out, cudaStream_t st);
 struct RecFoldItem {            // long series: segment-image sums -> one group's output
   const double* S;              // 2B x (segments), column-major
   const int32_t* w;             // n weights

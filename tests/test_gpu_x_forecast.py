@@ -1,4 +1,5 @@
-"""GPU parity of the recurrent column forecast (Sec. 3.3, eq. Forec:ContMSSAL).
+"""GPU parity of the column forecasts (Sec. 3.3): recurrent (eq. Forec:ContMSSAL)
+and vector (eqs. PGcolumn, V_FORcolumn).
 
 ssa_forecast reconstructs the component on the device, forms the recurrence
 from the window-side vectors and continues every series.  Checked against the
@@ -92,3 +93,51 @@ def test_forecast_errors():
         g.forecast([0], 5)
     assert e.value.code == LL.SSA_EINVAL
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_vector_forecast_continues_finite_rank_series(prec):
+    """The vector column forecast (eqs. PGcolumn, V_FORcolumn) of a rank-4
+    series with 1e-6 noise continues the noiseless series to the noise level."""
+    n = np.arange(80, dtype=float)
+    f = 1.01 ** n * np.cos(2 * np.pi * n / 9 + 0.2) + 0.5 * 0.99 ** n * np.cos(2 * np.pi * n / 5)
+    x = f[:60] + 1e-6 * np.random.default_rng(0).normal(size=60)
+    s = pkg.SSA.series(x, 20)
+    s.decompose(4, prec)
+    fc = s.forecast([0, 1, 2, 3], 20, method="vector")
+    assert np.max(np.abs(fc - f[60:])) <= 1e-5 * np.max(np.abs(f))
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_vector_forecast_matches_oracle(prec):
+    """ssa_forecast_vector (shift-matrix recursion in the window space's
+    coefficients) against the oracle's explicit projector form."""
+    grp = [0, 1, 2, 3, 4]
+    x = noisy_series(600, 5)
+    s = pkg.SSA.series(x, 200)
+    P = O.Problem.series(x, 200)
+    s.decompose(6, prec)
+    so, Uo, Vo = O.decompose(P, 6)
+    (ref,) = O.forecast_vector_column(P, so, Uo, Vo, grp, 12)
+    got = s.forecast(grp, 12, method="vector")
+    assert np.max(np.abs(got - ref)) <= TOL[prec] * np.max(np.abs(x))
+    s.close()
+    xs = [noisy_series(n, 20 + i) for i, n in enumerate((300, 350, 280))]
+    xs32 = [np.asarray(v, np.float32).astype(np.float64) for v in xs]
+    m = pkg.SSA.multi(xs, 100)
+    Pm = O.Problem.multi(xs32, 100)
+    m.decompose(6, prec)
+    so, Uo, Vo = O.decompose(Pm, 6)
+    refs = O.forecast_vector_column(Pm, so, Uo, Vo, grp, 8)
+    gots = m.forecast(grp, 8, method="vector")
+    for g, r_ in zip(gots, refs):
+        assert np.max(np.abs(g - r_)) <= TOL[prec] * max(np.max(np.abs(v)) for v in xs32)
+    m.close()
+    img = np.random.default_rng(2).normal(size=(20, 20))
+    im = pkg.SSA.image(img, 5, 5)
+    im.decompose(3, "fp32")
+    with pytest.raises(pkg.SSAError) as e:
+        im.forecast([0], 5, method="vector")
+    assert e.value.code == LL.SSA_EINVAL
+    im.close()
