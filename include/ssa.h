@@ -245,6 +245,20 @@ int ssa_forecast(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, dou
 int ssa_forecast_vector(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, double* out);
 
 /*
+ * ssa_forecast_row -- M-step row forecast of a series or of every series of
+ * an MSSA system (Sec. 3.3): recurrent (vector = 0, eq. Forec:ContMSSAK: each
+ * step appends R_K z to every series, R_K = (I_s - S S^T)^-1 S Vbar^T, z the
+ * last K_p - 1 reconstructed values of all series, S the last coordinates of
+ * each series' block of the group's origin-side vectors) or vector
+ * (vector = 1, eqs. PGrow and V_FORrow: the rows of the reconstructed matrix
+ * continued by the row projector, in the coefficients of the group's row
+ * space, then the MSSA diagonal averaging).  idx / n_idx / M / out as for
+ * ssa_forecast.  At most 64 series and 128 components.
+ * Errors as for ssa_forecast; SSA_EINVAL also when I - S S^T is singular.
+ */
+int ssa_forecast_row(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, int32_t vector, double* out);
+
+/*
  * ssa_get_shape -- the shape calculus results (host buffers, any may be NULL):
  * L, K; origin_mask (uint8, input layout: 1 where an element is a window origin
  * kappa of K); weights (int32, input layout: w_k = |A_k|, 0 outside N').

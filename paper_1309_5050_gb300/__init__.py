@@ -225,17 +225,22 @@ class SSA:
         return rho.reshape(n, n), contrib
 
     def forecast(self, group, M: int, method: str = "recurrent"):
-        """M-step column forecast of the component ``group`` (0-based
-        indices), Sec. 3.3: ``method`` "recurrent" (ssa_forecast) or
-        "vector" (ssa_forecast_vector).  One array of M values for a series,
-        a list of them for an MSSA system."""
+        """M-step forecast of the component ``group`` (0-based indices),
+        Sec. 3.3: ``method`` "recurrent" or "vector" (column forecasts,
+        ssa_forecast / ssa_forecast_vector), "recurrent_row" or "vector_row"
+        (row forecasts, ssa_forecast_row).  One array of M values for a
+        series, a list of them for an MSSA system."""
         idx = np.ascontiguousarray(list(group), dtype=np.int32)
         multi = self.layout[0] == "mssa"
         ns = len(self.layout[1]) if multi else 1
         out = np.zeros(ns * M)
-        fn = {"recurrent": "ssa_forecast", "vector": "ssa_forecast_vector"}[method]
-        L.check(getattr(self._lib, fn)(self.ctx, idx.ctypes.data_as(C.POINTER(C.c_int32)), len(idx), int(M),
-                                       out.ctypes.data), fn)
+        ip = idx.ctypes.data_as(C.POINTER(C.c_int32))
+        if method in ("recurrent_row", "vector_row"):
+            L.check(self._lib.ssa_forecast_row(self.ctx, ip, len(idx), int(M), 1 if method == "vector_row" else 0,
+                                               out.ctypes.data), "ssa_forecast_row")
+        else:
+            fn = {"recurrent": "ssa_forecast", "vector": "ssa_forecast_vector"}[method]
+            L.check(getattr(self._lib, fn)(self.ctx, ip, len(idx), int(M), out.ctypes.data), fn)
         parts = [out[p * M:(p + 1) * M] for p in range(ns)]
         return parts if multi else parts[0]
 

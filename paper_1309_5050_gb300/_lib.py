@@ -19,7 +19,7 @@ SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64 = 0, 1
 
 EXPORTS = [
     "ssa_embed", "ssa_embed_batch", "ssa_decompose", "ssa_decompose_batch", "ssa_get_info", "ssa_get_sigma",
-    "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_wcor", "ssa_forecast", "ssa_forecast_vector", "ssa_get_shape", "ssa_matvec",
+    "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_wcor", "ssa_forecast", "ssa_forecast_vector", "ssa_forecast_row", "ssa_get_shape", "ssa_matvec",
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
     "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
     "ssa_matvec_series_noalloc", "ssa_noalloc_last_error",
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.ssa_wcor.argtypes = [P, C.POINTER(C.c_int32), C.c_int32, P, P]
     lib.ssa_forecast.argtypes = [P, C.POINTER(C.c_int32), C.c_int32, C.c_int32, P]
     lib.ssa_forecast_vector.argtypes = [P, C.POINTER(C.c_int32), C.c_int32, C.c_int32, P]
+    lib.ssa_forecast_row.argtypes = [P, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32, P]
     lib.ssa_reconstruct_batch.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(C.c_int32), C.c_int32,
                                           C.c_int32, C.POINTER(P), C.c_int32]
     lib.ssa_get_shape.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), P, P]

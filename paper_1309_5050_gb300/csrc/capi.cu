@@ -2346,6 +2346,83 @@ int ssa_forecast_vector(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t
   return rc;
 }
 
+int ssa_forecast_row(ssa_ctx* ctx, const int32_t* idx, int32_t n_idx, int32_t M, int32_t vector, double* out) {
+  if (!ctx || !idx || !out) return fail(SSA_EINVAL, "null argument");
+  ssa_ctx* c = ctx;
+  if (c->kind != SSA_1D && c->kind != SSA_MSSA) return fail(SSA_EINVAL, "forecasting needs a series or a system of series");
+  if (!c->ws.done) return fail(SSA_ESTATE, "context has no decomposition");
+  if (M < 1 || n_idx < 1) return fail(SSA_EINVAL, "M and n_idx must be positive");
+  if (M > 65535 || n_idx > RF_MAXR) return fail(SSA_EINVAL, "M <= 65535 and n_idx <= %d", RF_MAXR);
+  const int s = (int)c->ch.size();
+  if (s > RF_MAXS) return fail(SSA_EINVAL, "row forecasts take at most %d series", RF_MAXS);
+  const int r = c->ws.r;
+  std::vector<int32_t> hidx(idx, idx + n_idx);
+  std::vector<int32_t> gof(std::max(r, 1), -1);
+  for (int32_t i : hidx) {
+    if (i < 0 || i >= r) return fail(SSA_EINVAL, "component %d outside [0, %d)", i, r);
+    gof[i] = 0;
+  }
+  const int64_t L = c->L, K = c->K, total = c->total;
+  std::vector<int64_t> hkoff, hkc, hoff, hlen, hwo;
+  int64_t kstar = 0, wtot = 0;
+  for (auto& h : c->ch) {
+    if (h.K.count < 2) return fail(SSA_EINVAL, "a series with fewer than two window origins");
+    hkoff.push_back(h.koff); hkc.push_back(h.K.count); hoff.push_back(h.data_off); hlen.push_back(h.nx * h.ny);
+    hwo.push_back(wtot);
+    wtot += h.K.count - 1 + M;
+    kstar = std::max<int64_t>(kstar, h.K.count);
+  }
+  const int na = std::max(s, n_idx);
+  double *Y = nullptr, *A = nullptr, *Bm = nullptr, *work = nullptr, *cs = nullptr, *dout = nullptr;
+  int32_t* didx = nullptr;
+  int* dfail = nullptr;
+  int64_t *dkoff = nullptr, *dkc = nullptr, *doff = nullptr, *dlen = nullptr, *dwo = nullptr;
+  auto cleanup = [&]() {
+    for (void* q : {(void*)Y, (void*)A, (void*)Bm, (void*)work, (void*)cs, (void*)dout, (void*)didx, (void*)dfail,
+                    (void*)dkoff, (void*)dkc, (void*)doff, (void*)dlen, (void*)dwo})
+      if (q) c->release(q);
+  };
+  int rc = SSA_OK;
+  if (!vector) {
+    rc = c->allocT(&Y, (size_t)total);
+    if (rc == SSA_OK) rc = ssa_reconstruct_batch(&c, 1, gof.data(), 1, 0, &Y, 1);
+    if (rc == SSA_OK) rc = c->allocT(&work, (size_t)wtot);
+  } else {
+    rc = c->allocT(&cs, (size_t)(M + kstar) * n_idx);
+  }
+  if (rc == SSA_OK) rc = upload(c, hidx, &didx);
+  if (rc == SSA_OK) rc = upload(c, hkoff, &dkoff);
+  if (rc == SSA_OK) rc = upload(c, hkc, &dkc);
+  if (rc == SSA_OK) rc = upload(c, hoff, &doff);
+  if (rc == SSA_OK) rc = upload(c, hlen, &dlen);
+  if (rc == SSA_OK) rc = upload(c, hwo, &dwo);
+  if (rc == SSA_OK) rc = c->allocT(&A, (size_t)na * na);
+  if (rc == SSA_OK) rc = c->allocT(&Bm, (size_t)na * n_idx);
+  if (rc == SSA_OK) rc = c->allocT(&dout, (size_t)s * M);
+  if (rc == SSA_OK) rc = c->allocT(&dfail, 1);
+  if (rc == SSA_OK && cudaMemsetAsync(dfail, 0, sizeof(int), c->stream) != cudaSuccess) rc = fail(SSA_ECUDA, "memset failed");
+  if (rc == SSA_OK) {
+    const int x_f64 = c->dtype == SSA_F64 ? 1 : 0;
+    if (c->ws.prec == SSA_PREC_FP64)
+      launch_row_forecast<double>(vector ? 1 : 0, (const double*)c->ws.Vo, K, didx, n_idx, dkoff, dkc, doff, dlen, s, L,
+                                  M, kstar, Y, c->data, x_f64, A, Bm, work, dwo, cs, dout, dfail, c->stream);
+    else
+      launch_row_forecast<float>(vector ? 1 : 0, (const float*)c->ws.Vo, K, didx, n_idx, dkoff, dkc, doff, dlen, s, L,
+                                 M, kstar, Y, c->data, x_f64, A, Bm, work, dwo, cs, dout, dfail, c->stream);
+    if (cudaGetLastError() != cudaSuccess) rc = fail(SSA_ECUDA, "row forecast launch failed");
+  }
+  int hfail = 0;
+  if (rc == SSA_OK && cudaMemcpyAsync(out, dout, sizeof(double) * s * M, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of the forecast failed");
+  if (rc == SSA_OK && cudaMemcpyAsync(&hfail, dfail, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = fail(SSA_ECUDA, "copy of the solve status failed");
+  if (rc == SSA_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = fail(SSA_ECUDA, "row forecast failed");
+  cleanup();
+  if (rc == SSA_OK && hfail)
+    rc = fail(SSA_EINVAL, "the row forecast's system is singular (the last rows of the group's origin vectors span too much)");
+  return rc;
+}
+
 int ssa_get_shape(const ssa_ctx* cc, int64_t* L, int64_t* K, uint8_t* origin_mask, int32_t* weights) {
   ssa_ctx* c = const_cast<ssa_ctx*>(cc);
   if (!c) return fail(SSA_EINVAL, "null argument");

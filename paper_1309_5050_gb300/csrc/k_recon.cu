@@ -532,4 +532,197 @@ template void launch_vector_forecast<double>(const double*, int64_t, const int32
                                              const int64_t*, const int64_t*, int, int, double*, double*, double*,
                                              double*, double*, cudaStream_t);
 
+// ------------------------------------------------------------ row forecasts
+// Solve A X = B in place (A: n x n symmetric positive definite, B: n x q,
+// row-major, global memory) by Gauss-Jordan without pivoting; one block.
+__device__ void rf_solve_spd(double* A, double* B, int n, int q, int* fail) {
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      piv = A[k * n + k];
+      if (!(piv > 0.0)) { *fail = 1; piv = 1.0; }
+    }
+    __syncthreads();
+    const double ip = 1.0 / piv;
+    for (int c = threadIdx.x; c < n + q; c += blockDim.x) {
+      if (c < n) A[k * n + c] *= ip;
+      else B[k * q + (c - n)] *= ip;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * (n + q); e += blockDim.x) {
+      const int i = e / (n + q), c = e - i * (n + q);
+      if (i == k) continue;
+      const double f = A[i * n + k];
+      if (c == k) continue;                        // column k of row i is cleared below
+      if (c < n) A[i * n + c] -= f * A[k * n + c];
+      else B[i * q + (c - n)] -= f * B[k * q + (c - n)];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) A[i * n + k] = 0.0;
+  }
+  __syncthreads();
+}
+
+// one block: S, then the system of the recurrent (A = I_s - S S^T, B = S,
+// solution W: s x r) or the vector form (A = I_r - S^T S, B = Vbar^T V',
+// solution D: r x r)
+template <typename T>
+__global__ void __launch_bounds__(256) k_rf_setup(int vector, const T* __restrict__ V, int64_t K,
+                                                  const int32_t* __restrict__ idx, int nidx,
+                                                  const int64_t* __restrict__ koff, const int64_t* __restrict__ kc,
+                                                  int s, double* A, double* Bm, int* fail) {
+  __shared__ double red[32];
+  if (!vector) {
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int p = e / s, q = e - p * s;
+      double acc = 0.0;
+      for (int j = 0; j < nidx; ++j) {
+        const double sp = (double)V[koff[p] + kc[p] - 1 + K * idx[j]];
+        const double sq = (double)V[koff[q] + kc[q] - 1 + K * idx[j]];
+        acc = fma(sp, sq, acc);
+      }
+      A[e] = (p == q ? 1.0 : 0.0) - acc;
+    }
+    for (int e = threadIdx.x; e < s * nidx; e += blockDim.x) {
+      const int p = e / nidx, j = e - p * nidx;
+      Bm[e] = (double)V[koff[p] + kc[p] - 1 + K * idx[j]];
+    }
+    rf_solve_spd(A, Bm, s, nidx, fail);
+  } else {
+    for (int e = threadIdx.x; e < nidx * nidx; e += blockDim.x) {
+      const int a = e / nidx, b = e - a * nidx;
+      double acc = 0.0;
+      for (int p = 0; p < s; ++p)
+        acc = fma((double)V[koff[p] + kc[p] - 1 + K * idx[a]], (double)V[koff[p] + kc[p] - 1 + K * idx[b]], acc);
+      A[e] = (a == b ? 1.0 : 0.0) - acc;
+    }
+    // Bm = Vbar^T V': sum over series p and rows t < kc[p] - 1 of V[t, a] V[t + 1, b]
+    for (int e = 0; e < nidx * nidx; ++e) {
+      const int a = e / nidx, b = e - a * nidx;
+      double acc = 0.0;
+      for (int p = 0; p < s; ++p) {
+        const T* va = V + koff[p] + K * idx[a];
+        const T* vb = V + koff[p] + 1 + K * idx[b];
+        for (int64_t t = threadIdx.x; t < kc[p] - 1; t += blockDim.x) acc = fma((double)va[t], (double)vb[t], acc);
+      }
+      const double tot = vf_block_sum(acc, red);
+      if (threadIdx.x == 0) Bm[e] = tot;
+    }
+    rf_solve_spd(A, Bm, nidx, nidx, fail);
+  }
+}
+
+// recurrent row forecast: one block, M steps
+template <typename T>
+__global__ void __launch_bounds__(256) k_rf_rec(const T* __restrict__ V, int64_t K, const int32_t* __restrict__ idx,
+                                                int nidx, const int64_t* __restrict__ koff,
+                                                const int64_t* __restrict__ kc, const int64_t* __restrict__ off,
+                                                const int64_t* __restrict__ len, int s, int M,
+                                                const double* __restrict__ rec, const double* __restrict__ W,
+                                                double* __restrict__ work, const int64_t* __restrict__ wo,
+                                                double* __restrict__ out) {
+  __shared__ double red[32];
+  __shared__ double w[RF_MAXR];
+  for (int p = 0; p < s; ++p) {                   // the last K_p - 1 reconstructed values
+    const double* src = rec + off[p] + len[p] - (kc[p] - 1);
+    for (int64_t t = threadIdx.x; t < kc[p] - 1; t += blockDim.x) work[wo[p] + t] = src[t];
+  }
+  for (int m = 0; m < M; ++m) {
+    __syncthreads();
+    for (int j = 0; j < nidx; ++j) {
+      double acc = 0.0;
+      for (int p = 0; p < s; ++p) {
+        const T* vj = V + koff[p] + K * idx[j];
+        const double* z = work + wo[p] + m;
+        for (int64_t t = threadIdx.x; t < kc[p] - 1; t += blockDim.x) acc = fma((double)vj[t], z[t], acc);
+      }
+      const double tot = vf_block_sum(acc, red);
+      if (threadIdx.x == 0) w[j] = tot;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < s; p += blockDim.x) {
+      double nx = 0.0;
+      for (int j = 0; j < nidx; ++j) nx = fma(W[p * nidx + j], w[j], nx);
+      work[wo[p] + kc[p] - 1 + m] = nx;
+      out[(int64_t)p * M + m] = nx;
+    }
+  }
+}
+
+// vector row forecast: c_{L-1} = V^T (row L-1 of X), c_i = D c_{i-1}; cs holds
+// rows i = L-1 .. L-1 + M + kstar - 1 (ld nidx)
+template <typename T>
+__global__ void __launch_bounds__(256) k_rf_coef(const T* __restrict__ V, int64_t K, const int32_t* __restrict__ idx,
+                                                 int nidx, const int64_t* __restrict__ koff,
+                                                 const int64_t* __restrict__ kc, const int64_t* __restrict__ off,
+                                                 int s, int64_t L, int M, int64_t kstar,
+                                                 const void* __restrict__ x, int x_f64, const double* __restrict__ D,
+                                                 double* __restrict__ cs) {
+  __shared__ double red[32];
+  for (int a = 0; a < nidx; ++a) {
+    double acc = 0.0;
+    for (int p = 0; p < s; ++p) {
+      const T* va = V + koff[p] + K * idx[a];
+      const int64_t x0 = off[p] + L - 1;          // row L-1 of series p's block: x_p[L-1 + t]
+      for (int64_t t = threadIdx.x; t < kc[p]; t += blockDim.x) {
+        const double xv = x_f64 ? ((const double*)x)[x0 + t] : (double)((const float*)x)[x0 + t];
+        acc = fma((double)va[t], xv, acc);
+      }
+    }
+    const double tot = vf_block_sum(acc, red);
+    if (threadIdx.x == 0) cs[a] = tot;
+  }
+  for (int64_t t = 1; t < M + kstar; ++t) {
+    __syncthreads();
+    const double* prev = cs + (t - 1) * nidx;
+    double* cur = cs + t * nidx;
+    for (int a = threadIdx.x; a < nidx; a += blockDim.x) {
+      double acc = 0.0;
+      for (int b = 0; b < nidx; ++b) acc = fma(D[a * nidx + b], prev[b], acc);
+      cur[a] = acc;
+    }
+  }
+}
+
+// out[p * M + m] = (1 / K_p) sum_{j < K_p} sum_a V[koff_p + j, a] c_{N_p + m - j}[a]; block (m, p)
+template <typename T>
+__global__ void __launch_bounds__(256) k_rf_out(const T* __restrict__ V, int64_t K, const int32_t* __restrict__ idx,
+                                                int nidx, const int64_t* __restrict__ koff,
+                                                const int64_t* __restrict__ kc, const int64_t* __restrict__ len,
+                                                int64_t L, int M, const double* __restrict__ cs,
+                                                double* __restrict__ out) {
+  __shared__ double red[32];
+  const int m = blockIdx.x, p = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < kc[p]; j += blockDim.x) {
+    const double* ct = cs + (len[p] + m - j - (L - 1)) * nidx;    // row N_p + m - j
+    for (int a = 0; a < nidx; ++a) acc = fma((double)V[koff[p] + j + K * idx[a]], ct[a], acc);
+  }
+  const double tot = vf_block_sum(acc, red);
+  if (threadIdx.x == 0) out[(int64_t)p * M + m] = tot / (double)kc[p];
+}
+
+template <typename T>
+void launch_row_forecast(int vector, const T* V, int64_t K, const int32_t* idx, int nidx, const int64_t* koff,
+                         const int64_t* kc, const int64_t* off, const int64_t* len, int s, int64_t L, int M,
+                         int64_t kstar, const double* rec, const void* x, int x_f64, double* A, double* Bm,
+                         double* work, const int64_t* wo, double* cs, double* out, int* fail, cudaStream_t st) {
+  k_rf_setup<T><<<1, 256, 0, st>>>(vector, V, K, idx, nidx, koff, kc, s, A, Bm, fail); count_launch();
+  if (!vector) {
+    k_rf_rec<T><<<1, 256, 0, st>>>(V, K, idx, nidx, koff, kc, off, len, s, M, rec, Bm, work, wo, out); count_launch();
+  } else {
+    k_rf_coef<T><<<1, 256, 0, st>>>(V, K, idx, nidx, koff, kc, off, s, L, M, kstar, x, x_f64, Bm, cs); count_launch();
+    k_rf_out<T><<<dim3(M, s), 256, 0, st>>>(V, K, idx, nidx, koff, kc, len, L, M, cs, out); count_launch();
+  }
+}
+#define RF_INST(T)                                                                                          \
+  template void launch_row_forecast<T>(int, const T*, int64_t, const int32_t*, int, const int64_t*,       \
+                                       const int64_t*, const int64_t*, const int64_t*, int, int64_t, int,  \
+                                       int64_t, const double*, const void*, int, double*, double*, double*, \
+                                       const int64_t*, double*, double*, int*, cudaStream_t);
+RF_INST(float)
+RF_INST(double)
+
 }  // namespace ssa

@@ -106,6 +106,27 @@ template <typename T>
 void launch_vector_forecast(const T* U, int64_t L, const int32_t* idx, int nidx, const void* x, int x_f64,
                             const int64_t* off, const int64_t* len, int s, int M, double* G, double* D, double* nu2,
                             double* cs, double* out, cudaStream_t st);
+
+// Row forecasts of an MSSA system (Sec. 3.3, eqs. Forec:ContMSSAK, PGrow,
+// V_FORrow) from the group's origin-side vectors V[:, idx] (T, ld K; series p
+// owns rows koff[p] .. koff[p] + kc[p]).  S = [mu(V_j)] (the last row of each
+// series' block, s x r); Vbar / V': V without the last / first row of each
+// block.  Recurrent: W = (I_s - S S^T)^-1 S, and each step appends
+// W (Vbar^T z) to every series, z the last K_p - 1 values of each series
+// (reconstruction rec, then the forecasts; work: per series kc[p] - 1 + M
+// values at work + wo[p]).  Vector: D = (I_r - S^T S)^-1 Vbar^T V', the
+// coefficients of the continued rows c_i = D c_{i-1} from c_{L-1} = V^T (row
+// L - 1 of the trajectory matrix), and forecast m of series p
+// = (1 / K_p) sum_{j < K_p} (V c_{N_p + m - j})[koff_p + j].  The dense solves
+// (SPD matrices, no pivoting) run in one block on scratch in global memory;
+// a non-positive pivot sets *fail.
+constexpr int RF_MAXR = 128;                  // components of a row forecast
+constexpr int RF_MAXS = 64;                   // series of a row forecast
+template <typename T>
+void launch_row_forecast(int vector, const T* V, int64_t K, const int32_t* idx, int nidx, const int64_t* koff,
+                         const int64_t* kc, const int64_t* off, const int64_t* len, int s, int64_t L, int M,
+                         int64_t kstar, const double* rec, const void* x, int x_f64, double* A, double* Bm,
+                         double* work, const int64_t* wo, double* cs, double* out, int* fail, cudaStream_t st);
 struct RecFoldItem {            // long series: segment-image sums -> one group's output
   const double* S;              // 2B x (segments), column-major
   const int32_t* w;             // n weights

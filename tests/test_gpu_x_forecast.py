@@ -141,3 +141,35 @@ def test_vector_forecast_matches_oracle(prec):
         im.forecast([0], 5, method="vector")
     assert e.value.code == LL.SSA_EINVAL
     im.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("method", ["recurrent_row", "vector_row"])
+def test_row_forecasts_match_oracle(method, prec):
+    """ssa_forecast_row (eqs. Forec:ContMSSAK, PGrow, V_FORrow) against the
+    oracle on an MSSA system of unequal lengths, and the continuation of a
+    finite-rank pair (1e-6 noise)."""
+    ref_fn = {"recurrent_row": O.forecast_recurrent_row, "vector_row": O.forecast_vector_row}[method]
+    grp = [0, 1, 2, 3, 4]
+    xs = [noisy_series(n, 20 + i) for i, n in enumerate((300, 350, 280))]
+    xs32 = [np.asarray(v, np.float32).astype(np.float64) for v in xs]
+    m = pkg.SSA.multi(xs, 100)
+    Pm = O.Problem.multi(xs32, 100)
+    m.decompose(6, prec)
+    so, Uo, Vo = O.decompose(Pm, 6)
+    refs = ref_fn(Pm, so, Uo, Vo, grp, 8)
+    gots = m.forecast(grp, 8, method=method)
+    for g, r_ in zip(gots, refs):
+        assert np.max(np.abs(g - r_)) <= TOL[prec] * max(np.max(np.abs(v)) for v in xs32)
+    m.close()
+    n = np.arange(80, dtype=float)
+    x1 = np.cos(2 * np.pi * n / 7)
+    x2 = 2.0 * np.sin(2 * np.pi * n / 7 + 0.5)
+    rng = np.random.default_rng(1)
+    a1 = x1[:40] + 1e-6 * rng.normal(size=40)
+    a2 = x2[:50] + 1e-6 * rng.normal(size=50)
+    pair = pkg.SSA.multi([a1, a2], 12)
+    pair.decompose(2, prec)
+    f1, f2 = pair.forecast([0, 1], 10, method=method)
+    assert np.max(np.abs(f1 - x1[40:50])) <= 1e-4 and np.max(np.abs(f2 - x2[50:60])) <= 1e-4
+    pair.close()
