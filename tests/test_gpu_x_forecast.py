@@ -173,3 +173,15 @@ def test_row_forecasts_match_oracle(method, prec):
     f1, f2 = pair.forecast([0, 1], 10, method=method)
     assert np.max(np.abs(f1 - x1[40:50])) <= 1e-4 and np.max(np.abs(f2 - x2[50:60])) <= 1e-4
     pair.close()
+
+
+@pytest.mark.xfail(reason="FP64 form on a series of exact rank below the Krylov dimension: open issue, cause not "
+                          "found (the FP32 form and the same series with 1e-6 noise are correct)", strict=False)
+def test_fp64_exact_rank_series_decomposition():
+    n = np.arange(60, dtype=float)
+    f = 1.01 ** n * np.cos(2 * np.pi * n / 9 + 0.2) + 0.5 * 0.99 ** n * np.cos(2 * np.pi * n / 5)
+    s = pkg.SSA.series(f, 20)
+    s.decompose(4, "fp64")
+    so = np.linalg.svd(O.Problem.series(f, 20).matrix(), compute_uv=False)[:4]
+    np.testing.assert_allclose(s.sigma(), so, rtol=1e-9, atol=0)
+    s.close()
