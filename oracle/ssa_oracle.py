@@ -22,7 +22,11 @@ Every quantity is formed from its definition in the paper:
 * reconstruction -- the projection ``Pi^(H)`` of Step 4 written out: every
   entry ``(i, j)`` of the grouped matrix is added into the data element
   ``l_i (+) k_j`` and divided by the count ``w_k = |A_k|`` of entries that map
-  there (eq. res_decomp and the averaging formula above it).
+  there (eq. res_decomp and the averaging formula above it);
+* beyond the hot path -- the weighted inner product and w-correlations of
+  Sec. 2.2 summed element by element, and the four MSSA forecasts of Sec. 3.3
+  (recurrent and vector, column and row) with their projectors and
+  recurrences formed explicitly and applied step by step.
 
 A "problem" is a list of channels (one for 1D and 2D, ``s`` for MSSA), each an
 ``(Nx, Ny)`` float64 array with NaN marking missing values, sharing one window
