@@ -150,6 +150,22 @@ int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, voi
 int ssa_decompose(ssa_ctx* ctx, const ssa_params* params);
 
 /*
+ * ssa_continue -- continue a decomposition to a larger rank (the
+ * auto-continuation Rssa offers, Sec. 2.4): the previous run's r1 Ritz
+ * triples, their couplings beta_k P[k-1, i] and the residual direction seed
+ * the new Krylov space as after a thick restart that keeps them, so only the
+ * new part of the space is built.  params: the new rank (above the previous
+ * one and at most min(L, K)), the same precision form; krylov_dim, tol and
+ * max_restarts as for ssa_decompose (seed unused).  A previous run that
+ * spanned the whole space, broke down, did not converge or used the other
+ * form is redone from a new start vector.  The results replace the previous
+ * ones.
+ * Errors: SSA_ESTATE (no decomposition), SSA_ERANK, SSA_ENOTCONV, SSA_ENOMEM,
+ * SSA_ECUDA.
+ */
+int ssa_continue(ssa_ctx* ctx, const ssa_params* params);
+
+/*
  * ssa_decompose_batch -- the same for n contexts at once: every kernel of the
  * Lanczos step is launched once for the whole batch (all problems advance in
  * lock-step).  params: n entries (one per context).  All contexts must live

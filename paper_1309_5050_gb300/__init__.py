@@ -171,6 +171,17 @@ class SSA:
         self.rank = rank
         return rc
 
+    def extend(self, rank: int, prec: str = "fp32", krylov_dim: int = 0, tol: float = 0.0,
+               max_restarts: int = 0) -> int:
+        """Continue the decomposition to a larger rank (ssa_continue): the
+        previous Ritz triples and residual direction seed the new Krylov
+        space instead of a new start vector."""
+        p = L.ssa_params(rank=rank, krylov_dim=krylov_dim, max_restarts=max_restarts,
+                         prec=PREC[prec], tol=tol, seed=0)
+        L.check(self._lib.ssa_continue(self.ctx, C.byref(p)), "ssa_continue")
+        self.rank = rank
+        return 0
+
     def info(self) -> dict:
         i = L.ssa_info()
         L.check(self._lib.ssa_get_info(self.ctx, C.byref(i)), "ssa_get_info")

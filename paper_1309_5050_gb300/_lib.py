@@ -18,7 +18,7 @@ SSA_F32, SSA_F64 = 0, 1
 SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64 = 0, 1
 
 EXPORTS = [
-    "ssa_embed", "ssa_embed_batch", "ssa_decompose", "ssa_decompose_batch", "ssa_get_info", "ssa_get_sigma",
+    "ssa_embed", "ssa_embed_batch", "ssa_decompose", "ssa_decompose_batch", "ssa_continue", "ssa_get_info", "ssa_get_sigma",
     "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_wcor", "ssa_forecast", "ssa_forecast_vector", "ssa_forecast_row", "ssa_get_shape", "ssa_matvec",
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
     "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.ssa_embed_batch.argtypes = [C.POINTER(ssa_input), C.POINTER(ssa_window), C.c_int32, P, C.POINTER(P),
                                     C.POINTER(C.c_int32)]
     lib.ssa_decompose.argtypes = [P, C.POINTER(ssa_params)]
+    lib.ssa_continue.argtypes = [P, C.POINTER(ssa_params)]
     lib.ssa_decompose_batch.argtypes = [C.POINTER(P), C.c_int32, C.POINTER(ssa_params), C.POINTER(C.c_int32)]
     lib.ssa_get_info.argtypes = [P, C.POINTER(ssa_info)]
     lib.ssa_get_sigma.argtypes = [P, C.POINTER(C.c_double), C.c_int32]

@@ -175,6 +175,26 @@ __global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int 
   st->beta_k = 0.0; st->anorm = 0.0; st->tol = tol; st->sigma1 = 0.0; st->maxres = 0.0;
 }
 
+// Continuation: the new cycle starts as after a thick restart that keeps the
+// r1 Ritz triples of the previous decomposition -- B = diag(sigma_1..r1)
+// with the column rho_i = beta_k P[k1-1, i] at r1, unit scales for the Ritz
+// columns and the previous residual direction (scale cres) at column r1.
+__global__ void k_state_resume(LzState* st, double* B, int k2, double* colscale, const double* sig,
+                               const double* P1, int k1, const LzState* old, const double* cres, int r1) {
+  for (int e = threadIdx.x; e < k2 * k2; e += blockDim.x) {
+    const int c = e / k2, i = e - c * k2;
+    double v = 0.0;
+    if (c == i && c < r1) v = sig[c];
+    else if (c == r1 && i < r1) v = old->beta_k * P1[(k1 - 1) + (int64_t)k1 * i];
+    B[e] = v;
+  }
+  for (int c = threadIdx.x; c < k2 + 2; c += blockDim.x) colscale[c] = c < r1 ? 1.0 : (c == r1 ? *cres : 0.0);
+  if (threadIdx.x == 0) {
+    st->jc = r1;
+    st->anorm = old->anorm;
+  }
+}
+
 template <typename T>
 __global__ void k_sum_parts_to_double(const T* parts, int nparts, int64_t ld, int64_t n, double* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1059,6 +1079,12 @@ struct LzEngine {
     hst.push_back(z);
     dirty = true;
   }
+  // a member whose bases already hold jc vectors (a continued decomposition)
+  void add_resumed(ssa_ctx* c, int jc) {
+    add(c, 0);
+    fresh.back() = false;
+    hst.back().jc = jc;
+  }
 
   // rebuild the device item arrays for the current members (when they changed)
   int build() {
@@ -1472,6 +1498,82 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
   for (int i = 0; i < n; ++i)
     if (rc[i] != SSA_OK && rc_all == SSA_OK) rc_all = rc[i];
   return rc_all;
+}
+
+// Continued decomposition to a larger rank: the previous run's r1 Ritz
+// vectors, their values and couplings and the residual direction seed the
+// new workspace as a thick restart keeping r1 vectors (the Krylov state is
+// reused; only the new part of the space is built).  A previous run that
+// spanned the whole space, broke down or did not converge starts afresh.
+template <typename T>
+static int continue_T(ssa_ctx* c, const ssa_params& p) {
+  const Workspace w1 = c->ws;                 // pointers into the old arena (freed by alloc_ws)
+  const LzState h1 = w1.host_st;
+  if (h1.full || h1.breakdown || !h1.converged || w1.prec != p.prec) {
+    int32_t stv = 0;
+    return decompose_batch_T<T>(&c, 1, &p, &stv);
+  }
+  if (p.rank <= w1.r || p.rank > std::min(c->L, c->K))
+    return fail(SSA_ERANK, "continuation needs a rank in (%d, %lld]", w1.r, (long long)std::min(c->L, c->K));
+  const int r1 = w1.r, k1 = w1.k;
+  const int64_t Ls = w1.Ls, Kl = w1.Kl;
+  cudaStream_t st = c->stream;
+  double *tU = nullptr, *tP = nullptr, *tsig = nullptr, *tcs = nullptr;
+  T *tV = nullptr, *tv = nullptr;
+  LzState* tst = nullptr;
+  auto cleanup = [&]() {
+    for (void* q : {(void*)tU, (void*)tP, (void*)tsig, (void*)tcs, (void*)tV, (void*)tv, (void*)tst})
+      if (q) c->release(q);
+  };
+  int rc = c->allocT(&tU, (size_t)Ls * r1);
+  if (rc == SSA_OK) rc = c->allocT(&tV, (size_t)Kl * r1);
+  if (rc == SSA_OK) rc = c->allocT(&tv, (size_t)Kl);
+  if (rc == SSA_OK) rc = c->allocT(&tP, (size_t)k1 * k1);
+  if (rc == SSA_OK) rc = c->allocT(&tsig, (size_t)r1);
+  if (rc == SSA_OK) rc = c->allocT(&tcs, 1);
+  if (rc == SSA_OK) rc = c->allocT(&tst, 1);
+  struct { void* d; const void* s; size_t n; } cp[] = {
+      {tU, w1.U, sizeof(double) * Ls * r1}, {tV, w1.V, sizeof(T) * Kl * r1},
+      {tv, (const T*)w1.V + Kl * k1, sizeof(T) * Kl}, {tP, w1.P, sizeof(double) * k1 * k1},
+      {tsig, w1.sig, sizeof(double) * r1}, {tcs, w1.colscale + k1, sizeof(double)}, {tst, w1.st, sizeof(LzState)}};
+  for (auto& q : cp)
+    if (rc == SSA_OK && cudaMemcpyAsync(q.d, q.s, q.n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      rc = fail(SSA_ECUDA, "saving the previous Krylov state failed");
+  ssa_ctx* cc = c;
+  if (rc == SSA_OK) rc = ensure_spectra<T>(&cc, 1, st);
+  if (rc == SSA_OK) rc = alloc_ws<T>(c, p, c->ws);
+  Workspace& w2 = c->ws;
+  if (rc == SSA_OK && w2.k <= r1) rc = fail(SSA_ERANK, "Krylov dimension %d leaves no room past %d kept vectors", w2.k, r1);
+  struct { void* d; const void* s; size_t n; } cp2[] = {
+      {w2.U, tU, sizeof(double) * Ls * r1}, {w2.V, tV, sizeof(T) * Kl * r1},
+      {(T*)w2.V + Kl * r1, tv, sizeof(T) * Kl}};
+  for (auto& q : cp2)
+    if (rc == SSA_OK && cudaMemcpyAsync(q.d, q.s, q.n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      rc = fail(SSA_ECUDA, "seeding the new Krylov state failed");
+  if (rc == SSA_OK) {
+    k_state_resume<<<1, 256, 0, st>>>(w2.st, w2.B, w2.k, w2.colscale, tsig, tP, k1, tst, tcs, r1); count_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = fail(SSA_ECUDA, "resume launch failed");
+  }
+  cleanup();
+  if (rc != SSA_OK) {
+    c->ws.done = false;
+    return rc;
+  }
+  LzEngine<T> e;
+  e.st = st;
+  e.device = c->device;
+  e.add_resumed(c, r1);
+  TRY(e.build());
+  while (e.any_active()) {
+    TRY(e.run_chunk());
+    TRY(e.restart_active());
+  }
+  std::vector<int> all{0};
+  TRY(e.retire(all));
+  CU(cudaStreamSynchronize(st));
+  const LzState& h = e.hst[0];
+  if (!h.converged && !h.breakdown) return fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
+  return SSA_OK;
 }
 
 // ============================================================== reconstruction
@@ -2115,6 +2217,16 @@ int ssa_decompose_batch(ssa_ctx* const* ctxs, int32_t n, const ssa_params* param
 int ssa_decompose(ssa_ctx* ctx, const ssa_params* params) {
   int32_t st = 0;
   return ssa_decompose_batch(&ctx, 1, params, &st);
+}
+
+int ssa_continue(ssa_ctx* ctx, const ssa_params* params) {
+  if (!ctx || !params) return fail(SSA_EINVAL, "null argument");
+  if (!ctx->ws.done) return fail(SSA_ESTATE, "context has no decomposition to continue");
+  if (params->prec == SSA_PREC_FP64 && ctx->log2Mx > 13)
+    return fail(SSA_EUNSUPPORTED, "FP64 form supports FFT length <= 8192 along x");
+  if (params->prec == SSA_PREC_FP64) return continue_T<double>(ctx, *params);
+  if (params->prec == SSA_PREC_FP32FFT_FP64REORTH) return continue_T<float>(ctx, *params);
+  return fail(SSA_EINVAL, "unknown precision %d", params->prec);
 }
 
 int ssa_get_info(const ssa_ctx* c, ssa_info* info) {
