@@ -108,11 +108,23 @@ static int na_setup(int dev, cudaStream_t st, unsigned char** base, char* err, s
     return SSA_ECUDA;
   }
   int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    snprintf(err, errn, "shared-memory limit query failed: %s", cudaGetErrorString(e));
+    return SSA_ECUDA;
+  }
   const int need = (int)(2 * (NA_HMAX + 1) * sizeof(Cx<float>));
   if (optin < need) { snprintf(err, errn, "device allows %d bytes of shared memory, %d needed", optin, need); return SSA_EUNSUPPORTED; }
-  cudaFuncSetAttribute((const void*)k_na_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-  cudaFuncSetAttribute((const void*)k_na_product, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  // both kernels need the raised limit: a failure here is reported with its
+  // cause and the device stays unprepared (the next call tries again)
+  const void* fns[2] = {(const void*)k_na_spectrum, (const void*)k_na_product};
+  for (const void* fn : fns) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    if (e != cudaSuccess) {
+      snprintf(err, errn, "raising the shared-memory limit of a product kernel failed: %s", cudaGetErrorString(e));
+      return SSA_ECUDA;
+    }
+  }
   k_na_twiddles<<<64, 256, 0, st>>>(reinterpret_cast<Cx<float>*>(p)); count_launch();
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
