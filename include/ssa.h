@@ -105,6 +105,11 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int32_t jacobi_sweeps;   /* FP64 sweeps of the last small SVD (one-sided Jacobi) */
   int32_t jacobi_sweeps_fp32;  /* FP32 sweeps that found its rotations first */
+  int32_t breakdowns;      /* Lanczos coefficients found at the rounding level of the largest
+                              one (an invariant subspace: exact rank below k, or a multiple
+                              singular value): set to 0, the process went on from a random
+                              vector orthogonal to the basis.  Results are not affected. */
+  int32_t pad_;
 } ssa_info;
 
 /*

@@ -50,7 +50,8 @@ class ssa_info(C.Structure):
                 ("n_channels", C.c_int32), ("rank", C.c_int32), ("krylov_dim", C.c_int32),
                 ("restarts", C.c_int32), ("converged", C.c_int32), ("prec", C.c_int32),
                 ("fft_mx", C.c_int64), ("fft_my", C.c_int64), ("max_residual", C.c_double),
-                ("device_bytes", C.c_int64), ("jacobi_sweeps", C.c_int32), ("jacobi_sweeps_fp32", C.c_int32)]
+                ("device_bytes", C.c_int64), ("jacobi_sweeps", C.c_int32), ("jacobi_sweeps_fp32", C.c_int32),
+                ("breakdowns", C.c_int32), ("pad_", C.c_int32)]
 
 
 class ssa_server_config(C.Structure):

@@ -1033,9 +1033,10 @@ struct LzEngine {
   // long vector) and every slice is a dense range.
   static bool fuse_long(ssa_ctx* c) { return member_fuses_long(c, c->ws.swapped); }
 
-  ShortItem short_item(ssa_ctx* c) {
+  ShortItem short_item(ssa_ctx* c, uint64_t sd) {
     Workspace& w = c->ws;
     ShortItem s;
+    s.seed = sd;
     s.st = w.st; s.U = w.U; s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
     s.parts_double = std::is_same<T, double>::value; s.p = w.p; s.B = w.B; s.ldb = w.k; s.nblk = w.nblk_s;
     s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
@@ -1101,7 +1102,7 @@ struct LzEngine {
     for (size_t i = 0; i < live.size(); ++i) {
       ssa_ctx* c = live[i];
       Workspace& w = c->ws;
-      sh.push_back(short_item(c)); lg.push_back(long_item(c, seed[i])); sv.push_back(svd_item(c));
+      sh.push_back(short_item(c, seed[i])); lg.push_back(long_item(c, seed[i])); sv.push_back(svd_item(c));
       rz.push_back(ritz_item(c)); stp.push_back(w.st);
       const size_t hs = c->log2My > 0 ? ((size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My) : 0;
       for (size_t q = 0; q < c->ch.size(); ++q) {
@@ -1174,8 +1175,10 @@ struct LzEngine {
     {
       std::vector<ShortItem> shf;
       max_ls_f = 1;
-      for (ssa_ctx* c : live)
-        if (c->ws.Ls <= SHORT_FUSED_MAX) { shf.push_back(short_item(c)); max_ls_f = std::max(max_ls_f, c->ws.Ls); }
+      for (size_t i = 0; i < live.size(); ++i) {
+        ssa_ctx* c = live[i];
+        if (c->ws.Ls <= SHORT_FUSED_MAX) { shf.push_back(short_item(c, seed[i])); max_ls_f = std::max(max_ls_f, c->ws.Ls); }
+      }
       n_shf = (int)shf.size();
       d_shf = nullptr;
       if (n_shf) TRY(up(shf, &d_shf));
@@ -1472,7 +1475,7 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
       CU(cudaStreamSynchronize(eng.st));
       for (size_t i = 0; i < eng.live.size(); ++i) {
         const LzState& h = eng.hst[i];
-        if (!h.converged && !h.breakdown) {
+        if (!h.converged) {
           const int idx = (int)(std::find(cs, cs + n, eng.live[i]) - cs);
           if (status) status[idx] = SSA_ENOTCONV;
           if (rc_all == SSA_OK) rc_all = fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
@@ -1509,12 +1512,13 @@ template <typename T>
 static int continue_T(ssa_ctx* c, const ssa_params& p) {
   const Workspace w1 = c->ws;                 // pointers into the old arena (freed by alloc_ws)
   const LzState h1 = w1.host_st;
+  // the rank rule holds whichever way the continuation is carried out
+  if (p.rank <= w1.r || p.rank > std::min(c->L, c->K))
+    return fail(SSA_ERANK, "continuation needs a rank in (%d, %lld]", w1.r, (long long)std::min(c->L, c->K));
   if (h1.full || h1.breakdown || !h1.converged || w1.prec != p.prec) {
     int32_t stv = 0;
     return decompose_batch_T<T>(&c, 1, &p, &stv);
   }
-  if (p.rank <= w1.r || p.rank > std::min(c->L, c->K))
-    return fail(SSA_ERANK, "continuation needs a rank in (%d, %lld]", w1.r, (long long)std::min(c->L, c->K));
   const int r1 = w1.r, k1 = w1.k;
   const int64_t Ls = w1.Ls, Kl = w1.Kl;
   cudaStream_t st = c->stream;
@@ -1572,7 +1576,7 @@ static int continue_T(ssa_ctx* c, const ssa_params& p) {
   TRY(e.retire(all));
   CU(cudaStreamSynchronize(st));
   const LzState& h = e.hst[0];
-  if (!h.converged && !h.breakdown) return fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
+  if (!h.converged) return fail(SSA_ENOTCONV, "restarts exhausted (max residual %.3g)", h.maxres);
   return SSA_OK;
 }
 
@@ -2239,7 +2243,8 @@ int ssa_get_info(const ssa_ctx* c, ssa_info* info) {
   info->device_bytes = c->bytes;
   if (c->ws.done) {
     info->rank = c->ws.r; info->krylov_dim = c->ws.k; info->restarts = c->ws.host_st.restarts;
-    info->converged = c->ws.host_st.converged || c->ws.host_st.breakdown; info->prec = c->ws.prec;
+    info->converged = c->ws.host_st.converged; info->prec = c->ws.prec;
+    info->breakdowns = c->ws.host_st.breakdown;
     info->max_residual = c->ws.host_st.maxres;
     info->jacobi_sweeps = c->ws.host_st.sweeps;
     info->jacobi_sweeps_fp32 = c->ws.host_st.sweeps32;
@@ -2764,7 +2769,7 @@ int server_round(ssa_server* s, LzEngine<T>& eng, std::vector<SrvReq*>& live, st
       q->out.assign((size_t)q->total * std::max(nout, 0), 0.0);
       q->restarts = eng.hst[i].restarts;
       q->maxres = eng.hst[i].maxres;
-      if (!eng.hst[i].converged && !eng.hst[i].breakdown) q->status = SSA_ENOTCONV;
+      if (!eng.hst[i].converged) q->status = SSA_ENOTCONV;
       if (nout > 0) {
         cs.push_back(c);
         req.push_back({q->group_of.data(), q->ng, q->residual, q->out.data()});

@@ -31,6 +31,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+__device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i) {
+  // SplitMix64 output function (Steele, Lea, Flood 2014) -> [-1, 1)
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// Seed of the replacement vector after a breakdown at step j on one side
+// (0 short, 1 long): distinct from the start vector's stream and per step.
+__device__ __forceinline__ uint64_t breakdown_seed(uint64_t seed, int side, int j) {
+  uint64_t z = seed ^ 0xD1B54A32D192ED03ull;
+  z += 0x632BE59BD9B4E019ull * (uint64_t)(2 * (j + 1) + side);
+  z = (z ^ (z >> 29)) * 0xBF58476D1CE4E5B9ull;
+  return z ^ (z >> 32);
+}
+
 __device__ __forceinline__ bool lz_skip(const LzState* st, int j) {
   return !st->active || j >= st->k || j < -1;
 }
@@ -132,32 +150,6 @@ __global__ void __launch_bounds__(SHORT_RB) k_short23(const ShortItem* __restric
   }
 }
 
-// step 4: alpha_j = ||p||, u_j = p / alpha_j, B[j,j] = alpha_j
-__global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict__ items, const int32_t* __restrict__ tpre,
-                                                     int n, int s) {
-  int blk;
-  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
-  LzState* st = it.st;
-  const int j = st->jc + s;
-  if (j < 0 || lz_skip(st, j)) return;
-  __shared__ double alpha_s;
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int b = 0; b < it.nblk; ++b) a += it.npart[b];
-    alpha_s = sqrt(a);
-  }
-  __syncthreads();
-  const double alpha = alpha_s;
-  const bool ok = alpha > 1e-200;
-  const int64_t row = (int64_t)blk * SHORT_RB + threadIdx.x;
-  if (row < it.Ls) it.U[row + it.ldu * j] = ok ? it.p[row] / alpha : 0.0;
-  if (blk == 0 && threadIdx.x == 0) {
-    it.B[j + (int64_t)it.ldb * j] = ok ? alpha : 0.0;
-    if (ok) { if (alpha > st->anorm) st->anorm = alpha; }
-    else { st->k = j + 1; st->beta_k = 0.0; st->breakdown = 1; }
-  }
-}
-
 // Whole short-side step of one problem in one block (Ls <= SHORT_FUSED_MAX):
 // p = sum of the channel partial products; classical Gram-Schmidt against
 // U[:, 0:j]; a second pass only when the first left a component above a
@@ -171,14 +163,14 @@ __global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict
 // the norms -- a norm-ratio test let ghost singular values through on long
 // noisy series.
 template <int NT>
-__device__ __forceinline__ void short_dots(const double* __restrict__ U, int64_t ldu, const double* p, int Ls, int j,
-                                           double* c) {
+__device__ __forceinline__ void short_dots(const double* __restrict__ U, int64_t ldu, const double* p, int64_t Ls,
+                                           int j, double* c) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < j; i += NT / 32) {
     const double* col = U + ldu * i;
     // two accumulators: every extra one costs an FP64 add per lane
     double a0 = 0.0, a1 = 0.0;
-    int t = lane;
+    int64_t t = lane;
     for (; t + 32 < Ls; t += 64) { a0 = fma(col[t], p[t], a0); a1 = fma(col[t + 32], p[t + 32], a1); }
     if (t < Ls) a0 = fma(col[t], p[t], a0);
     const double tot = warp_sum(a0 + a1);
@@ -187,10 +179,10 @@ __device__ __forceinline__ void short_dots(const double* __restrict__ U, int64_t
 }
 
 // p -= U c over the block's rows; returns this thread's share of ||p||^2
-__device__ __forceinline__ double short_update(const double* __restrict__ U, int64_t ldu, double* p, int Ls, int j,
+__device__ __forceinline__ double short_update(const double* __restrict__ U, int64_t ldu, double* p, int64_t Ls, int j,
                                                const double* c) {
   double nn = 0.0;
-  for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
+  for (int64_t row = threadIdx.x; row < Ls; row += blockDim.x) {
     double s0 = 0.0, s1 = 0.0;
     int i = 0;
     for (; i + 1 < j; i += 2) { s0 = fma(U[row + ldu * i], c[i], s0); s1 = fma(U[row + ldu * (i + 1)], c[i + 1], s1); }
@@ -200,6 +192,73 @@ __device__ __forceinline__ double short_update(const double* __restrict__ U, int
     nn = fma(v, v, nn);
   }
   return nn;
+}
+
+// Breakdown level of the short side (BD_REL_* times the largest coefficient).
+__device__ __forceinline__ double short_bd_level(const ShortItem& it, double anorm) {
+  return (it.parts_double ? BD_REL_FP64 : BD_REL_FP32) * anorm;
+}
+
+// After a breakdown at step j: p (Ls values, shared or global memory of this
+// block) <- a seeded random vector, orthogonalised twice against U[:, 0:j].
+// NT = blockDim.x.  Returns ||p||^2; every thread gets it.
+template <int NT>
+__device__ double short_random(const ShortItem& it, double* p, int64_t Ls, int j, double* c, double* red) {
+  const uint64_t sd = breakdown_seed(it.seed, 0, j);
+  for (int64_t row = threadIdx.x; row < Ls; row += blockDim.x) p[row] = hash_uniform(sd, (uint64_t)row);
+  __syncthreads();
+  double nn = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    short_dots<NT>(it.U, it.ldu, p, Ls, j, c);
+    __syncthreads();
+    nn = block_sum(short_update(it.U, it.ldu, p, Ls, j, c), red);
+  }
+  return nn;
+}
+
+// B[j, j] = alpha_j (0 after a breakdown, which is counted); one thread.
+__device__ __forceinline__ void short_coef(const ShortItem& it, LzState* st, int j, bool ok, double alpha) {
+  it.B[j + (int64_t)it.ldb * j] = ok ? alpha : 0.0;
+  if (ok) { if (alpha > st->anorm) st->anorm = alpha; }
+  else st->breakdown += 1;
+}
+
+// step 4: alpha_j = ||p||, u_j = p / alpha_j, B[j,j] = alpha_j
+__global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict__ items, const int32_t* __restrict__ tpre,
+                                                     int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
+  LzState* st = it.st;
+  const int j = st->jc + s;
+  if (j < 0 || lz_skip(st, j)) return;
+  __shared__ double alpha_s;
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int b = 0; b < it.nblk; ++b) a += it.npart[b];
+    alpha_s = sqrt(a);
+    // every block of the problem takes this decision: anorm only grows, to
+    // alpha_j, when alpha_j passes, so a block reading it late agrees
+    ok_s = alpha_s > short_bd_level(it, st->anorm);
+  }
+  __syncthreads();
+  const double alpha = alpha_s;
+  const bool ok = ok_s != 0;
+  if (ok) {
+    const int64_t row = (int64_t)blk * SHORT_RB + threadIdx.x;
+    if (row < it.Ls) it.U[row + it.ldu * j] = it.p[row] / alpha;
+    if (blk == 0 && threadIdx.x == 0) short_coef(it, st, j, true, alpha);
+    return;
+  }
+  // breakdown (rare): block 0 alone builds the whole replacement vector; the
+  // other blocks of the problem write nothing (they took the same decision)
+  if (blk != 0) return;
+  __shared__ double c[KMAX + 1];
+  __shared__ double red[32];
+  const double nn = short_random<SHORT_RB>(it, it.p, it.Ls, j, c, red);
+  const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  for (int64_t row = threadIdx.x; row < it.Ls; row += blockDim.x) it.U[row + it.ldu * j] = it.p[row] * inv;
+  if (threadIdx.x == 0) short_coef(it, st, j, false, 0.0);
 }
 
 constexpr int SHORT_FUSED_NT = 512;
@@ -213,6 +272,7 @@ __global__ void __launch_bounds__(SHORT_FUSED_NT) k_short_fused(const ShortItem*
   __shared__ double red[32];
   __shared__ int second;
   const int Ls = (int)it.Ls;
+  const double level = short_bd_level(it, st->anorm);   // read before thread 0 may raise anorm
   double* p = sp;
   for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
     int q = 0;
@@ -250,15 +310,16 @@ __global__ void __launch_bounds__(SHORT_FUSED_NT) k_short_fused(const ShortItem*
   }
   __syncthreads();
   if (second) nn = block_sum(short_update(it.U, it.ldu, p, Ls, j, c), red);
-  const double alpha = sqrt(nn);
-  const bool ok = alpha > 1e-200;
-  const double inv = ok ? 1.0 / alpha : 0.0;
-  for (int row = threadIdx.x; row < Ls; row += blockDim.x) it.U[row + it.ldu * j] = p[row] * inv;
-  if (threadIdx.x == 0) {
-    it.B[j + (int64_t)it.ldb * j] = ok ? alpha : 0.0;
-    if (ok) { if (alpha > st->anorm) st->anorm = alpha; }
-    else { st->k = j + 1; st->beta_k = 0.0; st->breakdown = 1; }
+  double alpha = sqrt(nn);
+  const bool ok = alpha > level;
+  if (!ok) {
+    __syncthreads();
+    nn = short_random<SHORT_FUSED_NT>(it, p, Ls, j, c, red);
+    alpha = sqrt(nn);
   }
+  const double inv = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  for (int row = threadIdx.x; row < Ls; row += blockDim.x) it.U[row + it.ldu * j] = p[row] * inv;
+  if (threadIdx.x == 0) short_coef(it, st, j, ok, alpha);
 }
 
 void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st) {
@@ -268,14 +329,6 @@ void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cu
 }
 
 // ------------------------------------------------------------ long side
-__device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t i) {
-  // SplitMix64 output function (Steele, Lea, Flood 2014) -> [-1, 1)
-  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
-}
 
 // q = sum(partials) - alpha_j v_j ; partial squared norms
 template <typename T>
@@ -325,8 +378,46 @@ __global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict
   if (threadIdx.x == 0) it.npart[blk] = tot;
 }
 
+// After a breakdown at step j on the long side: column j+1 of V <- a seeded
+// random vector orthogonalised twice against v_0..v_j (v_c = colscale[c] V[:, c],
+// the long basis of the three-term recurrence), by this block alone -- the one
+// time the long side is re-orthogonalised.  Returns its norm (every thread).
+// d: KMAX + 2 shared doubles.
+template <typename T>
+__device__ double long_random(const LongItem<T>& it, int j, double* red, double* d) {
+  const uint64_t sd = breakdown_seed(it.seed, 1, j);
+  const int64_t Kl = it.Kl;
+  T* w = it.V + it.ldv * (j + 1);
+  for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) w[row] = (T)hash_uniform(sd, (uint64_t)row);
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int c = 0; c <= j; ++c) {
+      const T* vc = it.V + it.ldv * c;
+      double a = 0.0;
+      for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) a = fma((double)vc[row], (double)w[row], a);
+      a = block_sum(a, red);
+      if (threadIdx.x == 0) d[c] = a * it.colscale[c] * it.colscale[c];
+    }
+    __syncthreads();
+    for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) {
+      double acc = (double)w[row];
+      for (int c = 0; c <= j; ++c) acc = fma(-d[c], (double)it.V[row + it.ldv * c], acc);
+      w[row] = (T)acc;
+    }
+    __syncthreads();
+  }
+  double nn = 0.0;
+  for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) {
+    const double v = (double)w[row];
+    nn = fma(v, v, nn);
+  }
+  return sqrt(block_sum(nn, red));
+}
+
 // beta_j = ||q|| from the partial norms (fixed order); column j+1 of V keeps q
 // and its scale 1/beta_j is recorded; B[j, j+1] = beta_j (beta_k at the end).
+// A beta_j at the breakdown level (BD_REL_* anorm) is set to 0 and q replaced
+// (long_random).
 template <typename T>
 __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict__ items, int s) {
   const LongItem<T> it = items[blockIdx.x];
@@ -334,23 +425,22 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
   const int j = st->jc + s;
   if (lz_skip(st, j)) return;
   __shared__ double red[32];
+  __shared__ double d[KMAX + 2];
+  const double level = (sizeof(T) == 8 ? BD_REL_FP64 : BD_REL_FP32) * st->anorm;
   double a = 0.0;
   const int nb = (s < 0) ? it.nblk : it.nsum;    // start vector: its blocks; a step: nsum partials
   for (int b = threadIdx.x; b < nb; b += blockDim.x) a += it.npart[b];
-  const double beta = sqrt(block_sum(a, red));
+  double beta = sqrt(block_sum(a, red));
+  const bool ok = j < 0 || beta > level;         // (the start vector is random: never replaced)
+  if (!ok) beta = long_random<T>(it, j, red, d);
   if (threadIdx.x != 0) return;
-  const bool ok = beta > 1e-200;
-  it.colscale[j + 1] = ok ? 1.0 / beta : 0.0;
+  it.colscale[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
   if (j < 0) return;
-  if (ok) {
-    if (j + 1 < st->k) it.B[j + (int64_t)it.ldb * (j + 1)] = beta;
-    else st->beta_k = beta;
-    if (beta > st->anorm) st->anorm = beta;
-  } else {
-    st->k = j + 1;
-    st->beta_k = 0.0;
-    st->breakdown = 1;
-  }
+  const double coupling = ok ? beta : 0.0;
+  if (j + 1 < st->k) it.B[j + (int64_t)it.ldb * (j + 1)] = coupling;
+  else st->beta_k = coupling;
+  if (ok) { if (beta > st->anorm) st->anorm = beta; }
+  else st->breakdown += 1;
   st->jc = j + 1;   // last kernel of the step: the next step of this problem
 }
 
@@ -883,7 +973,7 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     st->converged = conv ? 1 : 0;
     st->restarts += 1;
     st->svd_done = 1;
-    if (conv || st->breakdown || st->restarts > st->max_restarts) st->active = 0;
+    if (conv || st->restarts > st->max_restarts) st->active = 0;
   }
 }
 

@@ -14,7 +14,8 @@ struct LzState {
   int32_t active;     // 1 while the problem still iterates
   int32_t converged;  // set by the small-SVD kernel
   int32_t nconv;      // leading triples that pass the residual test
-  int32_t breakdown;  // a Lanczos norm vanished
+  int32_t breakdown;  // breakdowns met: coefficients at rounding level set to 0 and their vectors
+                      // replaced by random ones orthogonal to the basis (k_lanczos.cu)
   int32_t restarts;   // restart cycles done
   int32_t max_restarts;
   int32_t full;       // k equals min(L, K): one cycle spans the whole space

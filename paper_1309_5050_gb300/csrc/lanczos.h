@@ -30,7 +30,22 @@ struct ShortItem {
   double* cpa; double* cpb;               // nblk x (KMAX+1) partial dots
   double* npart;                          // nblk partial squared norms
   int64_t Ls;
+  uint64_t seed;                          // seeds the replacement vectors after a breakdown
 };
+
+// Breakdown test.  A Lanczos coefficient at the rounding level of the largest
+// one seen so far (alpha_j or beta_j <= BD_REL * anorm) means the Krylov space
+// is invariant to working precision -- the data has exact rank below k, or a
+// multiple singular value whose other copies one start vector cannot reach.
+// Normalising that residual would feed rounding noise into the basis (the
+// long side is not re-orthogonalised, so the bases lose orthogonality and B
+// stops describing A).  Instead the coefficient is set to 0 and the new basis
+// vector is a seeded random vector orthogonalised twice against the basis of
+// its side; the bidiagonal then splits into blocks and the process goes on in
+// the rest of the space.  The levels sit above the noise of one product: FFT
+// convolution error ~ eps log2(M) ||x|| ||v|| (FP64 and FP32 products).
+constexpr double BD_REL_FP64 = 1e-12;
+constexpr double BD_REL_FP32 = 1e-6;
 
 template <typename T>
 struct LongItem {

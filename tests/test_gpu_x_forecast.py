@@ -175,9 +175,10 @@ def test_row_forecasts_match_oracle(method, prec):
     pair.close()
 
 
-@pytest.mark.xfail(reason="FP64 form on a series of exact rank below the Krylov dimension: open issue, cause not "
-                          "found (the FP32 form and the same series with 1e-6 noise are correct)", strict=False)
 def test_fp64_exact_rank_series_decomposition():
+    """A noiseless rank-4 series whose Krylov dimension spans the window
+    space: the FP64 form meets a breakdown after four steps and must go on
+    from a random vector instead of normalising rounding noise."""
     n = np.arange(60, dtype=float)
     f = 1.01 ** n * np.cos(2 * np.pi * n / 9 + 0.2) + 0.5 * 0.99 ** n * np.cos(2 * np.pi * n / 5)
     s = pkg.SSA.series(f, 20)

@@ -63,3 +63,20 @@ def test_continue_errors():
         s.extend(5)
     assert e.value.code == LL.SSA_ERANK
     s.close()
+
+
+def test_continue_rank_rule_holds_on_the_fresh_run_fallback():
+    """A previous run in the other precision form is redone from a new start
+    vector; the rank must still grow (equal or lower rank: SSA_ERANK), and a
+    valid larger rank gives the oracle's triples."""
+    x = noisy_series(500, 6)
+    s = pkg.SSA.series(x, 180)
+    s.decompose(5, "fp32")
+    for r in (5, 3):
+        with pytest.raises(pkg.SSAError) as e:
+            s.extend(r, "fp64")
+        assert e.value.code == LL.SSA_ERANK
+    s.extend(8, "fp64")
+    so, _, _ = O.decompose(O.Problem.series(x, 180), 8)
+    np.testing.assert_allclose(s.sigma(), so, rtol=TOL_SIG["fp64"], atol=0)
+    s.close()
