@@ -228,9 +228,21 @@ def serving_requests(n: int = 20000, rate_hz: float = 1000.0, seed: int = 5,
             mask, _ = disc_with_holes_mask(side, side, n_holes=holes, seed=sub + 1)
             img = img.copy()
             img[~mask] = np.nan
-            reqs.append(Request(i, float(t[i]), "2d", min(r, 30), img,
+            # the rank is capped at 30 and at min(L, K): a large hole can leave
+            # fewer admissible window positions than the drawn rank
+            r = min(r, 30, w * w, _full_boxes(mask, w))
+            reqs.append(Request(i, float(t[i]), "2d", r, img,
                                 window=(w, w), mask=mask))
     return reqs
+
+
+def _full_boxes(mask: np.ndarray, w: int) -> int:
+    """Number of w x w boxes lying wholly inside ``mask`` (a request
+    parameter of the generator: bounds the rank a masked image can take)."""
+    c = np.zeros((mask.shape[0] + 1, mask.shape[1] + 1), dtype=np.int64)
+    c[1:, 1:] = np.cumsum(np.cumsum(mask.astype(np.int64), axis=0), axis=1)
+    box = c[w:, w:] - c[:-w, w:] - c[w:, :-w] + c[:-w, :-w]
+    return int(np.count_nonzero(box == w * w))
 
 
 # Workload catalogue: sizes only (the data comes from the generators above).
