@@ -168,7 +168,12 @@ template <> const Cx<float>* twiddles<float>(int dev) { return g_tables[dev].t32
 template <> const Cx<double>* twiddles<double>(int dev) { return g_tables[dev].t64; }
 
 // small helper kernels of the driver
-__global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int max_restarts, int full) {
+// bd_scale = 4 eps_T log2(grid points): with ||x|| it is a few times the rounding
+// error of one product with a unit vector (FFT error ~ eps log2 M ||x|| ||v||); a
+// Lanczos coefficient below it is noise (the breakdown test of k_lanczos.cu).
+__global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int max_restarts, int full,
+                             const double* xnorm, double bd_scale) {
+  st->bd_floor = bd_scale * *xnorm;
   st->full = full; st->sweeps = 0; st->sweeps32 = 0;
   st->jc = 0; st->svd_done = 0; st->k = k; st->r = r; st->kk = kk; st->active = 1; st->converged = 0;
   st->nconv = 0; st->breakdown = 0; st->restarts = 0; st->max_restarts = max_restarts;
@@ -309,6 +314,8 @@ struct Channel {
   void* xh32 = nullptr;        // spectra
   void* xh64 = nullptr;
   int kb = 0, fy = 0;          // segment form: origin blocks ceil(K_p/B), segments lb + kb - 1
+  double* sq = nullptr;        // sums of squares of the observation kernel's blocks (nsq)
+  int64_t nsq = 0;
 };
 
 struct Workspace {             // Lanczos + results, per precision
@@ -342,6 +349,7 @@ struct ssa_ctx {
   std::vector<Channel> ch;
   int64_t total = 0;           // data elements
   void* data = nullptr;        // device copy of the input (dtype)
+  double* xnorm = nullptr;     // device: ||x||_2 over the observed values (scale of the products' rounding)
   int log2Mx = 0, log2My = 0;
   int fold_B = 0, lb = 0;      // segment form of long series (0: off), window blocks ceil(L/B)
   ShapeSet Lset;               // window set (bounding box ex x ey)
@@ -468,6 +476,7 @@ static int upload(ssa_ctx* c, const std::vector<X>& h, X** d) {
 // stage 3 checks the error flags -- two host waits for the whole batch.
 struct EmbedBatch {
   std::vector<ObsItem> obs;
+  std::vector<NormItem> norms;
   std::vector<PrefixItem> opre, kpre;
   int max_opre_cols = 1, max_kpre_cols = 1;
   std::vector<OriginItem> org;
@@ -538,12 +547,22 @@ static int embed_stage1(ssa_ctx* c, const ssa_window* win, EmbedBatch& eb, int c
   eb.max_cols = std::max(eb.max_cols, Ls.by);
   const size_t esz = c->dtype == SSA_F64 ? 8 : 4;
   eb.cnt_slot_K[ci].assign(c->ch.size(), -1);
+  // the observation kernel's block sums of squares, one array for all channels
+  int64_t nsq = 0;
+  for (auto& h : c->ch) nsq += ((h.nx + 255) >> 8) * h.ny;
+  double* sq = nullptr;
+  TRY(c->allocT(&sq, (size_t)nsq));
+  TRY(c->allocT(&c->xnorm, 1));
+  eb.norms.push_back({sq, nsq, c->xnorm});
   for (size_t q = 0; q < c->ch.size(); ++q) {
     Channel& h = c->ch[q];
     h.nwords = (int)((h.nx + 31) / 32);
     TRY(c->allocT(&h.obs, (size_t)h.ny * h.nwords));
+    h.sq = sq;
+    h.nsq = ((h.nx + 255) >> 8) * h.ny;
+    sq += h.nsq;
     const void* dptr = (const char*)c->data + h.data_off * esz;
-    eb.obs.push_back({dptr, c->dtype == SSA_F64, (int)h.nx, (int)h.ny, h.nwords, h.obs, d_err + ci});
+    eb.obs.push_back({dptr, c->dtype == SSA_F64, (int)h.nx, (int)h.ny, h.nwords, h.obs, d_err + ci, h.sq});
     int32_t* opre = nullptr;
     if (runs) {
       TRY(c->allocT(&opre, (size_t)h.ny * (h.nwords + 1)));
@@ -948,7 +967,12 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   double tol = p.tol > 0 ? p.tol : (std::is_same<T, float>::value ? 1e-7 : 1e-13);
   int maxr = p.max_restarts > 0 ? p.max_restarts : 40;
   c->cur = keep_cur;
-  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0); count_launch();
+  int lg = 0;
+  for (auto& h : c->ch) lg = std::max(lg, h.log2M);
+  const double eps_t = std::is_same<T, float>::value ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+  const double bd_scale = 4.0 * eps_t * (double)(lg + c->log2My);
+  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0,
+                                       c->xnorm, bd_scale); count_launch();
   CU(cudaGetLastError());
   return SSA_OK;
 }
@@ -1032,6 +1056,18 @@ struct LzEngine {
   // side is the origin side (each channel's product is its own slice of the
   // long vector) and every slice is a dense range.
   static bool fuse_long(ssa_ctx* c) { return member_fuses_long(c, c->ws.swapped); }
+
+  // The whole short-side step in one block per problem pays off when the
+  // problems fill the GPU; a few problems with a long short side (an image
+  // with a 64 x 64 window: 4096 rows) would leave most SMs idle for a step
+  // that is FP64-bound, so they take the row-block kernels instead.
+  int sm_count = 0;
+  bool fused_short(ssa_ctx* c) {
+    if (c->ws.Ls > SHORT_FUSED_MAX) return false;
+    if (!sm_count && cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+      sm_count = 1;
+    return c->ws.Ls <= 512 || (int)live.size() >= sm_count;
+  }
 
   ShortItem short_item(ssa_ctx* c, uint64_t sd) {
     Workspace& w = c->ws;
@@ -1152,7 +1188,7 @@ struct LzEngine {
     }
     if (live.empty()) return SSA_OK;
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
-    TRY(tiles(live, [](ssa_ctx* c) { return c->ws.Ls <= SHORT_FUSED_MAX ? 0 : c->ws.nblk_s; }, &t_sh, &n_sh));
+    TRY(tiles(live, [this](ssa_ctx* c) { return fused_short(c) ? 0 : c->ws.nblk_s; }, &t_sh, &n_sh));
     {
       std::vector<UzItem<T>> uz;
       max_uz_log2 = 1;
@@ -1177,7 +1213,7 @@ struct LzEngine {
       max_ls_f = 1;
       for (size_t i = 0; i < live.size(); ++i) {
         ssa_ctx* c = live[i];
-        if (c->ws.Ls <= SHORT_FUSED_MAX) { shf.push_back(short_item(c, seed[i])); max_ls_f = std::max(max_ls_f, c->ws.Ls); }
+        if (fused_short(c)) { shf.push_back(short_item(c, seed[i])); max_ls_f = std::max(max_ls_f, c->ws.Ls); }
       }
       n_shf = (int)shf.size();
       d_shf = nullptr;
@@ -1984,12 +2020,15 @@ static int embed_prepare(const ssa_input* in, const ssa_window* win, void* cuda_
     const size_t ww = (lx + 31) / 32;
     size_t need = rnd256(esz * c->total) + (in->mask ? rnd256(c->total) : 0) + 2 * rnd256(ly * ww * 4) +
                   2 * rnd256((ly + 1) * 4) + rnd256(4) + rnd256(2 * ly * 4);
+    size_t nsq = 0;
     for (auto& h : c->ch) {
       const size_t nw = (h.nx + 31) / 32;
       const size_t cy = h.ny, kw = nw;
       need += rnd256(h.ny * nw * 4) * 2 + rnd256(cy * kw * 4) + 2 * rnd256((cy + 1) * 4) + rnd256(h.nx * h.ny * 4) +
               rnd256(h.ny * (nw + 1) * 4) + rnd256(cy * (kw + 1) * 4);
+      nsq += (size_t)((h.nx + 255) >> 8) * h.ny;
     }
+    need += rnd256(8 * nsq) + rnd256(8);
     int rc0 = c->make_arena(c->embed_arena, need);
     if (rc0) return bail(rc0);
     c->cur = &c->embed_arena;
@@ -2142,6 +2181,7 @@ int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, voi
   for (int i = 0; i < n; ++i)
     if (rc[i] == SSA_OK) rc[i] = embed_stage1(outs[i], &wins[i], eb, i, d_tot, d_err);
   ObsItem* d_obs = nullptr; OriginItem* d_org = nullptr; CountItem* d_cnt = nullptr; WeightItem* d_wts = nullptr;
+  NormItem* d_nrm = nullptr;
   auto upload_raw = [&](auto& vec, auto** dptr) -> int {
     typedef typename std::remove_reference<decltype(vec[0])>::type X;
     if (cudaMallocAsync((void**)dptr, sizeof(X) * std::max<size_t>(vec.size(), 1), st) != cudaSuccess) return SSA_ENOMEM;
@@ -2167,8 +2207,10 @@ int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, voi
   if (urc == SSA_OK) urc = upload_raw(t_cnt, &p_cnt);
   if (urc == SSA_OK) urc = upload_raw(t_opre, &p_opre);
   if (urc == SSA_OK) urc = upload_raw(t_kpre, &p_kpre);
+  if (urc == SSA_OK) urc = upload_raw(eb.norms, &d_nrm);
   if (urc != SSA_OK) return fail(urc, "embed item upload");
   launch_obs_batch(d_obs, p_obs, (int)eb.obs.size(), t_obs.back(), st);
+  launch_norm_batch(d_nrm, (int)eb.norms.size(), st);
   launch_prefix_batch(d_opre, p_opre, (int)eb.opre.size(), t_opre.back(), st);
   launch_origins_batch(d_org, p_org, (int)eb.org.size(), t_org.back(), st);
   launch_prefix_batch(d_kpre, p_kpre, (int)eb.kpre.size(), t_kpre.back(), st);
@@ -2191,7 +2233,7 @@ int ssa_embed_batch(const ssa_input* ins, const ssa_window* wins, int32_t n, voi
     if (rc[i] == SSA_OK) rc[i] = embed_stage3(outs[i], pin[i]);
   cudaFreeAsync(d_tot, st); cudaFreeAsync(d_err, st);
   cudaFreeAsync(d_obs, st); cudaFreeAsync(d_org, st); cudaFreeAsync(d_cnt, st); cudaFreeAsync(d_wts, st);
-  cudaFreeAsync(d_opre, st); cudaFreeAsync(d_kpre, st);
+  cudaFreeAsync(d_opre, st); cudaFreeAsync(d_kpre, st); cudaFreeAsync(d_nrm, st);
   for (int32_t* q : {p_obs, p_org, p_cnt, p_opre, p_kpre, p_wts}) cudaFreeAsync(q, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(SSA_ECUDA, "embed: %s", cudaGetErrorString(e));

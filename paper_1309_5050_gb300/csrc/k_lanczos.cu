@@ -194,9 +194,10 @@ __device__ __forceinline__ double short_update(const double* __restrict__ U, int
   return nn;
 }
 
-// Breakdown level of the short side (BD_REL_* times the largest coefficient).
-__device__ __forceinline__ double short_bd_level(const ShortItem& it, double anorm) {
-  return (it.parts_double ? BD_REL_FP64 : BD_REL_FP32) * anorm;
+// Breakdown level of the short side (lanczos.h): the products' rounding level
+// or BD_REL_* times the largest coefficient, whichever is larger.
+__device__ __forceinline__ double short_bd_level(const ShortItem& it, const LzState* st) {
+  return fmax(st->bd_floor, (it.parts_double ? BD_REL_FP64 : BD_REL_FP32) * st->anorm);
 }
 
 // After a breakdown at step j: p (Ls values, shared or global memory of this
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(SHORT_RB) k_short4(const ShortItem* __restrict
     alpha_s = sqrt(a);
     // every block of the problem takes this decision: anorm only grows, to
     // alpha_j, when alpha_j passes, so a block reading it late agrees
-    ok_s = alpha_s > short_bd_level(it, st->anorm);
+    ok_s = alpha_s > short_bd_level(it, st);
   }
   __syncthreads();
   const double alpha = alpha_s;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(SHORT_FUSED_NT) k_short_fused(const ShortItem*
   __shared__ double red[32];
   __shared__ int second;
   const int Ls = (int)it.Ls;
-  const double level = short_bd_level(it, st->anorm);   // read before thread 0 may raise anorm
+  const double level = short_bd_level(it, st);   // read before thread 0 may raise anorm
   double* p = sp;
   for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
     int q = 0;
@@ -378,46 +379,16 @@ __global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict
   if (threadIdx.x == 0) it.npart[blk] = tot;
 }
 
-// After a breakdown at step j on the long side: column j+1 of V <- a seeded
-// random vector orthogonalised twice against v_0..v_j (v_c = colscale[c] V[:, c],
-// the long basis of the three-term recurrence), by this block alone -- the one
-// time the long side is re-orthogonalised.  Returns its norm (every thread).
-// d: KMAX + 2 shared doubles.
-template <typename T>
-__device__ double long_random(const LongItem<T>& it, int j, double* red, double* d) {
-  const uint64_t sd = breakdown_seed(it.seed, 1, j);
-  const int64_t Kl = it.Kl;
-  T* w = it.V + it.ldv * (j + 1);
-  for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) w[row] = (T)hash_uniform(sd, (uint64_t)row);
-  __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int c = 0; c <= j; ++c) {
-      const T* vc = it.V + it.ldv * c;
-      double a = 0.0;
-      for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) a = fma((double)vc[row], (double)w[row], a);
-      a = block_sum(a, red);
-      if (threadIdx.x == 0) d[c] = a * it.colscale[c] * it.colscale[c];
-    }
-    __syncthreads();
-    for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) {
-      double acc = (double)w[row];
-      for (int c = 0; c <= j; ++c) acc = fma(-d[c], (double)it.V[row + it.ldv * c], acc);
-      w[row] = (T)acc;
-    }
-    __syncthreads();
-  }
-  double nn = 0.0;
-  for (int64_t row = threadIdx.x; row < Kl; row += blockDim.x) {
-    const double v = (double)w[row];
-    nn = fma(v, v, nn);
-  }
-  return sqrt(block_sum(nn, red));
-}
-
 // beta_j = ||q|| from the partial norms (fixed order); column j+1 of V keeps q
 // and its scale 1/beta_j is recorded; B[j, j+1] = beta_j (beta_k at the end).
-// A beta_j at the breakdown level (BD_REL_* anorm) is set to 0 and q replaced
-// (long_random).
+// A beta_j at the breakdown level (lanczos.h) is set to 0 and v_{j+1} is the
+// zero vector (scale 0).  The next short step then sees A v_{j+1} = 0, a
+// breakdown there, and continues from a random u_{j+1} orthogonal to U; the
+// long step after it forms X^T u_{j+1}, which is orthogonal to v_0..v_j in
+// exact arithmetic (A v_i lies in span U_{j+1} for i <= j) -- so the long
+// side never needs its own re-orthogonalisation.  When the data's column
+// space is already inside span U, X^T u_{j+1} is rounding again and the step
+// repeats: the remaining singular values are zero and B holds zero blocks.
 template <typename T>
 __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict__ items, int s) {
   const LongItem<T> it = items[blockIdx.x];
@@ -425,16 +396,14 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
   const int j = st->jc + s;
   if (lz_skip(st, j)) return;
   __shared__ double red[32];
-  __shared__ double d[KMAX + 2];
-  const double level = (sizeof(T) == 8 ? BD_REL_FP64 : BD_REL_FP32) * st->anorm;
+  const double level = fmax(st->bd_floor, (sizeof(T) == 8 ? BD_REL_FP64 : BD_REL_FP32) * st->anorm);
   double a = 0.0;
   const int nb = (s < 0) ? it.nblk : it.nsum;    // start vector: its blocks; a step: nsum partials
   for (int b = threadIdx.x; b < nb; b += blockDim.x) a += it.npart[b];
-  double beta = sqrt(block_sum(a, red));
+  const double beta = sqrt(block_sum(a, red));
   const bool ok = j < 0 || beta > level;         // (the start vector is random: never replaced)
-  if (!ok) beta = long_random<T>(it, j, red, d);
   if (threadIdx.x != 0) return;
-  it.colscale[j + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+  it.colscale[j + 1] = (ok && beta > 0.0) ? 1.0 / beta : 0.0;
   if (j < 0) return;
   const double coupling = ok ? beta : 0.0;
   if (j + 1 < st->k) it.B[j + (int64_t)it.ldb * (j + 1)] = coupling;

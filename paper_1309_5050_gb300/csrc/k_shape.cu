@@ -153,15 +153,44 @@ __global__ void k_obs_batch(const ObsItem* __restrict__ items, const int32_t* __
   const int y = t / tx;
   const int x = (t - y * tx) * 256 + threadIdx.x;
   bool ok = false;
+  double sq = 0.0;
   if (x < it.nx) {
     const int64_t g = x + (int64_t)it.nx * y;
     const double v = it.data_double ? ((const double*)it.data)[g] : (double)((const float*)it.data)[g];
     ok = !isnan(v);
     if (ok && isinf(v)) { atomicExch(it.err, 1); ok = false; }
+    if (ok) sq = v * v;
   }
   const unsigned bal = __ballot_sync(0xffffffffu, ok);
   const int w = x >> 5;
   if ((threadIdx.x & 31) == 0 && w < it.words) it.bits[(int64_t)y * it.words + w] = bal;
+  // the block's sum of squares (warp sums, then warps in order: repeatable)
+  __shared__ double wsum[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += wsum[i];
+    it.sq[t] = tot;
+  }
+}
+
+// ||x||_2 of each problem: its observation blocks' sums of squares, added in
+// a fixed order (one block per problem).
+__global__ void k_norm_batch(const NormItem* __restrict__ items) {
+  const NormItem it = items[blockIdx.x];
+  __shared__ double part[256];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < it.n; i += blockDim.x) a += it.sq[i];
+  part[threadIdx.x] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) tot += part[i];
+    *it.out = sqrt(tot);
+  }
 }
 
 // Set bits of a column bit row at positions < x, from the word prefix counts
@@ -327,6 +356,10 @@ __global__ void k_weights_batch(const WeightItem* __restrict__ items, const int3
 void launch_obs_batch(const ObsItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
   if (n <= 0 || tiles <= 0) return;
   k_obs_batch<<<tiles, 256, 0, st>>>(it, pre, n); count_launch();
+}
+void launch_norm_batch(const NormItem* it, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_norm_batch<<<n, 256, 0, st>>>(it); count_launch();
 }
 void launch_origins_batch(const OriginItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st) {
   if (n <= 0 || tiles <= 0) return;

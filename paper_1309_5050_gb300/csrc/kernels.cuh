@@ -27,6 +27,7 @@ struct LzState {
   double tol;         // residual tolerance relative to sigma_1
   double sigma1;      // current leading Ritz value
   double maxres;      // largest relative residual among the r wanted
+  double bd_floor;    // rounding level of one product with a unit vector (breakdown test)
 };
 
 // A compact vector, possibly column (jc + s + jdelta) of a basis.

@@ -33,19 +33,24 @@ struct ShortItem {
   uint64_t seed;                          // seeds the replacement vectors after a breakdown
 };
 
-// Breakdown test.  A Lanczos coefficient at the rounding level of the largest
-// one seen so far (alpha_j or beta_j <= BD_REL * anorm) means the Krylov space
-// is invariant to working precision -- the data has exact rank below k, or a
-// multiple singular value whose other copies one start vector cannot reach.
-// Normalising that residual would feed rounding noise into the basis (the
-// long side is not re-orthogonalised, so the bases lose orthogonality and B
-// stops describing A).  Instead the coefficient is set to 0 and the new basis
-// vector is a seeded random vector orthogonalised twice against the basis of
-// its side; the bidiagonal then splits into blocks and the process goes on in
-// the rest of the space.  The levels sit above the noise of one product: FFT
-// convolution error ~ eps log2(M) ||x|| ||v|| (FP64 and FP32 products).
+// Breakdown test.  A Lanczos coefficient at the rounding level of the
+// products (alpha_j or beta_j <= the larger of LzState::bd_floor = 4 eps
+// log2(grid) ||x|| -- one FFT product with a unit vector is exact to about
+// eps log2 M ||x|| -- and BD_REL times the largest coefficient so far) means
+// the Krylov space is invariant to working precision: the data has exact rank
+// below k, or a multiple singular value whose other copies one start vector
+// cannot reach.  Normalising that residual would feed rounding noise into the
+// basis (the long side is not re-orthogonalised, so the bases lose
+// orthogonality and B stops describing A).  Instead the coefficient is set to
+// 0: on the short side u_j becomes a seeded random vector orthogonalised twice
+// against U; on the long side v_{j+1} becomes the zero vector, so the next
+// short step breaks down too and X^T of its random u starts the next block
+// (orthogonal to V in exact arithmetic, see k_long_norm).  The bidiagonal
+// splits into blocks and the process goes on in the rest of the space.  The floor follows the data's
+// scale, not sigma_1: a long series with a steep trend has legitimate noise
+// singular values near 1e-6 sigma_1, far above its products' rounding.
 constexpr double BD_REL_FP64 = 1e-12;
-constexpr double BD_REL_FP32 = 1e-6;
+constexpr double BD_REL_FP32 = 1e-9;
 
 template <typename T>
 struct LongItem {

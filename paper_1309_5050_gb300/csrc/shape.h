@@ -9,7 +9,10 @@ namespace ssa {
 struct ObsItem {
   const void* data; int32_t data_double, nx, ny, words;
   uint32_t* bits; int* err;
+  double* sq;               // per block of the item: sum of the squared observed values
 };
+// ||x||_2 of one problem from the observation kernel's block sums (fixed order)
+struct NormItem { const double* sq; int64_t n; double* out; };
 // Window columns that are one run of elements [a, b] (every rectangle, disc
 // or triangle) let the origin and weight tests count set bits in a range
 // from per-word prefix counts instead of matching every window word.
@@ -44,6 +47,7 @@ void launch_prefix_batch(const PrefixItem* it, const int32_t* pre, int n, int ti
 // weights ceil(nx/256) * ny, origins ceil(cx/256) * cy, counts and prefixes
 // one block per column.
 void launch_obs_batch(const ObsItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st);
+void launch_norm_batch(const NormItem* it, int n, cudaStream_t st);
 void launch_origins_batch(const OriginItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st);
 void launch_counts_batch(const CountItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st);
 void launch_weights_batch(const WeightItem* it, const int32_t* pre, int n, int tiles, cudaStream_t st);

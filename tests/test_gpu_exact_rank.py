@@ -157,3 +157,25 @@ def test_fp64_breakdown_path_is_taken():
     assert s.info()["breakdowns"] >= 1
     check_sigma(s.sigma(), expect, 4, "fp64")
     s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_wide_dynamic_range_is_not_a_breakdown(prec):
+    """A steep trend with small noise (x = t + N(0, 0.05^2), N = 4000, L =
+    2000): the noise part's Lanczos coefficients sit near 5e-7 sigma_1, far
+    below any fixed fraction of sigma_1 one would call rounding, but well above
+    the products' own rounding (4 eps log2 M ||x||).  No breakdown may be
+    declared there, and the leading values keep the form's accuracy."""
+    rng = np.random.default_rng(21)
+    t = np.arange(1, 4001, dtype=float)
+    x = t + rng.normal(0, 0.05, t.size)
+    s = pkg.SSA.series(x, 2000)
+    s.decompose(6, prec)
+    assert s.info()["breakdowns"] == 0
+    so, _, _ = O.decompose(O.Problem.series(x, 2000), 6)
+    sig = s.sigma()
+    # the two trend values only: at sigma_1 / sigma_3 ~ 1e6 the noise values
+    # are resolved to ~eps (sigma_1 / sigma_3)^2 relative by the oracle's
+    # S = X X^T route and by a one-sided bidiagonalisation alike
+    np.testing.assert_allclose(sig[:2], so[:2], rtol=RTOL[prec], atol=0)
+    s.close()

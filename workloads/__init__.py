@@ -216,7 +216,11 @@ def serving_requests(n: int = 20000, rate_hz: float = 1000.0, seed: int = 5,
                 reqs.append(Request(i, float(t[i]), "1d", r, x, L=L))
             else:
                 s = int(rng.integers(2, 17))
-                xs = mssa_series(s, max(N // 2, 64), max(N, 65), seed=sub)
+                # the 16-series recipe's exp(0.0002 t) reaches e^1.6 at its
+                # longest series (8000); longer series keep that end value
+                # instead of growing to e^40 at 200,000 samples
+                growth = 0.0002 * min(1.0, 8000.0 / max(N, 65))
+                xs = mssa_series(s, max(N // 2, 64), max(N, 65), seed=sub, growth=growth)
                 L = min(len(v) for v in xs) // 2
                 r = min(r, L - 1)
                 reqs.append(Request(i, float(t[i]), "mssa", r, xs, L=L))
