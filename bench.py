@@ -156,10 +156,32 @@ def serve_submit(srv, q, seed):
                             seed=seed)
 
 
+def serve_at_spec(pkg, n_sat, n_open, prec, budget, seed, load=0.8):
+    """Config 5 as specified: first the saturating throughput C, closed loop
+    (n_sat requests all queued at once, completions per second of wall time),
+    then an open-loop Poisson stream of n_open further requests at
+    load * C (arrival times of the generator's stream rescaled to that rate),
+    whose p50 / p99 are service latencies (arrival to result in host memory)."""
+    import dataclasses
+    reqs = W.serving_requests(n=n_sat + n_open, rate_hz=1000.0, seed=seed, n_max=SERVE_N_MAX)
+    sat = run_serving(pkg, reqs[:n_sat], prec, budget, None)
+    lam = load * sat["throughput_rps"]
+    rest = reqs[n_sat:]
+    t0 = rest[0].arrival_s
+    scaled = [dataclasses.replace(q, arrival_s=(q.arrival_s - t0) * 1000.0 / lam) for q in rest]
+    opn = run_serving(pkg, scaled, prec, budget, lam)
+    return {"saturation": sat, "poisson": opn, "load": load,
+            "what": "closed-loop capacity, then Poisson arrivals at load x capacity; latencies of the Poisson part"}
+
+
 def run_serving(pkg, reqs, prec, budget, rate_hz):
     """Open-loop serving: each request is submitted when its Poisson arrival
     time comes up on the server's clock; latency runs from that arrival time
-    to the request's completion (results in host memory)."""
+    to the request's completion (results in host memory).  rate_hz None:
+    closed loop, every request queued at the start (arrival = start)."""
+    if rate_hz is None:
+        import dataclasses
+        reqs = [dataclasses.replace(q, arrival_s=0.0) for q in reqs]
     from paper_1309_5050_gb300 import _lib
     srv = pkg.Server(memory_budget=budget, prec=prec)
     for q in reqs[:8]:                      # warm-up requests (not counted)
@@ -211,7 +233,8 @@ def run_serving(pkg, reqs, prec, budget, rate_hz):
     kinds = {}
     for q in reqs:
         kinds[q.kind] = kinds.get(q.kind, 0) + 1
-    return {"requests": n, "rate_hz": rate_hz, "kinds": kinds, "throughput_rps": n / wall, "wall_s": wall,
+    return {"requests": n, "rate_hz": rate_hz if rate_hz is not None else "closed loop", "kinds": kinds,
+            "throughput_rps": n / wall, "wall_s": wall,
             "p50_ms": 1000 * float(np.percentile(lat, 50)), "p99_ms": 1000 * float(np.percentile(lat, 99)),
             "mean_ms": 1000 * float(np.mean(lat)), "max_live": max_live, "max_queued": max_q,
             "server_steps": steps, "step_ms_mean": 1000 * float(np.mean(step_s)),
@@ -270,8 +293,7 @@ def mv1d_traffic(batch):
 
 
 MV1D_SOURCES = ["paper_1309_5050_gb300/csrc/k_matvec.cu", "paper_1309_5050_gb300/csrc/fft_block.cuh",
-                "paper_1309_5050_gb300/csrc/tma.cuh", "paper_1309_5050_gb300/csrc/kernels.cuh",
-                "paper_1309_5050_gb300/csrc/common.cuh", "paper_1309_5050_gb300/csrc/capi.cu"]
+                "paper_1309_5050_gb300/csrc/tma.cuh", "paper_1309_5050_gb300/csrc/common.cuh"]
 DECOMP_SPLIT_MIN = 64   # mirrors the library's split of large batches into two streams
 
 
@@ -311,6 +333,206 @@ def write_traffic(csv_path, batch, command):
     print(json.dumps(out))
 
 
+# ------------------------------------------------------------------ configs 1, 3, 4
+# The other workloads of the method, each timed as its own step (shapes and
+# weights, spectra, decomposition, reconstruction of the signal groups plus
+# the residual) in both precision forms.  The series workload is latency-bound
+# alone, so B distinct series (seeds seed, seed + 1, ...) run per step, as the
+# MSSA headline does; an image is one problem per step.
+CONFIG_RUNS = {
+    "series_1d_n1000": {"batch": 456, "groups": [[0, 1], [2, 3]]},
+    "image_1024x1024_w64": {"batch": 1, "groups": [list(range(8)), list(range(8, 12)), list(range(12, 16))]},
+    "shaped_2048x2048_disc40holes_w32": {"batch": 1,
+                                         "groups": [[0], list(range(1, 9)), list(range(9, 13)), list(range(13, 17))]},
+}
+
+
+def config_input(name, i):
+    """Host data of problem i of a workload (i = 0: the workload's own seed)."""
+    cfg = W.CONFIGS[name]
+    seed = cfg["seed"] + i
+    if cfg["kind"] == "1d":
+        return W.series_1d(cfg["n"], seed=seed)
+    if cfg["kind"] == "2d":
+        return W.harmonic_image(cfg["nx"], cfg["ny"], seed=seed)
+    x, _, _ = W.shaped_image(cfg["nx"], cfg["ny"], seed=seed)
+    return x
+
+
+def pow2_at_least(n, lo=16):
+    m = lo
+    while m < n:
+        m *= 2
+    return m
+
+
+def product_algorithmic_bytes(name, prec, K):
+    """Floor bytes of one trajectory product (average of X v and X^T u) of one
+    problem: the input vector, the data's half spectrum and the output vector,
+    each read or written once.  X v reads v (K) and writes u (L); X^T u reads
+    the FP64 window-side vector u (L) and writes v (K) -- for a series, whose
+    long-side Lanczos step is fused into that store, also reading v_j (K)."""
+    cfg = W.CONFIGS[name]
+    t = 4 if prec == "fp32" else 8
+    if cfg["kind"] == "1d":
+        H = pow2_at_least(cfg["n"]) // 2
+        spec, L = (H + 1) * 2 * t, cfg["L"]
+        a = K * t + spec + L * t
+        at = L * 8 + spec + 2 * K * t
+    else:
+        mx, my = pow2_at_least(cfg["nx"]), pow2_at_least(cfg["ny"], 1)
+        spec, L = (mx // 2 + 1) * my * 2 * t, cfg["lx"] * cfg["ly"]
+        a = K * t + spec + L * t
+        at = L * 8 + spec + K * t
+    return (a + at) / 2.0
+
+
+def run_config(pkg, torch, name, prec, stream, flush, steps, warmup):
+    """decompositions/s of one workload in one precision form, with the phase
+    profile and the roofline of the trajectory product."""
+    from paper_1309_5050_gb300 import _lib
+    cfg = W.CONFIGS[name]
+    run = CONFIG_RUNS[name]
+    B, groups = run["batch"], run["groups"]
+    hosts = [config_input(name, i) for i in range(B)]
+    if cfg["kind"] == "1d":
+        dev = [torch.from_numpy(np.ascontiguousarray(h, np.float64)).cuda() for h in hosts]
+    else:
+        # column-major bytes: a (ny, nx) row-major tensor viewed transposed
+        dev = [torch.from_numpy(np.ascontiguousarray(h.T, np.float32)).cuda() for h in hosts]
+    total = hosts[0].size
+    nout = len(groups) + 1
+    outs = [torch.empty(total * nout, dtype=torch.float64, device="cuda") for _ in range(B)]
+    info = {}
+
+    def step():
+        if cfg["kind"] == "1d":
+            ps = pkg.embed_series_batch(dev, cfg["L"], stream=stream)
+        else:
+            ps = [pkg.SSA.image(d.t(), cfg["lx"], cfg["ly"], stream=stream) for d in dev]
+        pkg.decompose_batch(ps, cfg["rank"], prec)
+        if not info:
+            info.update(ps[0].info())
+        pkg.reconstruct_batch(ps, groups, residual=True, outs=outs)
+        for p in ps:
+            p.close()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    l0 = _lib.kernel_launches()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    launches = _lib.kernel_launches() - l0
+    prof = _lib.profile_read()
+    _lib.profile_enable(False)
+    ms = sum(ts) / len(ts)
+    mv_ms, _, mv_calls = prof["matvec"]
+    engines = 2 if B >= DECOMP_SPLIT_MIN else 1
+    per_call = product_algorithmic_bytes(name, prec, int(info["K"])) * B / engines
+    mv_avg = mv_ms / max(mv_calls, 1)
+    hbm, src = peaks()
+    achieved = per_call / (mv_avg / 1000.0) / 1e9
+    kernel = "k_mv1d" if cfg["kind"] == "1d" else "k_mv_xfwd + k_ypass + k_mv_xinv"
+    return {"decomps_per_s": B / (ms / 1000.0), "ms_per_step": ms, "batch": B, "steps": steps,
+            "ms_p50": float(np.percentile(ts, 50)), "ms_max": float(np.max(ts)),
+            "krylov_dim": info.get("krylov_dim"), "restarts": info.get("restarts"),
+            "gpu_launches_per_step": launches / steps,
+            "phases_ms_per_step": {k: v[0] / steps for k, v in prof.items()},
+            "product": {"kernels": kernel, "bound": "hbm", "algorithmic_bytes_per_call": per_call,
+                        "ms_per_call": mv_avg, "achieved": achieved, "unit": "GB/s", "peak": hbm,
+                        "frac": achieved / hbm, "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)",
+                        "calls_timed": mv_calls,
+                        "what": "one call = every problem's product in one direction (one engine's launch set)"}}
+
+
+def oracle_sample(name, budget_s):
+    """The CPU oracle on a bounded sample of one workload, in this process
+    (the caller sets the BLAS thread count through the environment)."""
+    from oracle import ssa_oracle as O
+    cfg = W.CONFIGS[name]
+    if cfg["kind"] == "mssa":
+        n, total = 0, 0.0
+        while total < budget_s and n < 8:
+            total += run_oracle(1, 1000 + n)
+            n += 1
+        return {"value": n / total, "sample": f"{n} full problems (decomposition + reconstruction), {total:.1f} s"}
+    if cfg["kind"] == "1d":
+        groups = CONFIG_RUNS[name]["groups"]
+        n, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and n < 200:
+            x = config_input(name, n)
+            P = O.Problem.series(x, cfg["L"])
+            sg, U, V = O.decompose(P, cfg["rank"])
+            O.reconstruct(P, sg, U, V, groups, residual=True)
+            n += 1
+        total = time.perf_counter() - t0
+        return {"value": n / total, "sample": f"{n} full problems (decomposition + reconstruction), {total:.1f} s"}
+    # images: Step 2 as the oracle runs it (S = X X^T over column blocks, eigh,
+    # V = X^T U / sigma) on the first column blocks, scaled to all of them;
+    # the explicit reconstruction (an L x K matrix per group, 15-16 GB) is left out
+    x = config_input(name, 0)
+    P = O.Problem.image(x, cfg["lx"], cfg["ly"])
+    nblk = sum(1 for _ in range(0, P.K, 4096))
+    S = np.zeros((P.L, P.L))
+    t0 = time.perf_counter()
+    done = 0
+    blocks = []
+    for _, Xb in P.column_blocks():
+        S += Xb @ Xb.T
+        blocks.append(Xb)
+        done += 1
+        if time.perf_counter() - t0 > budget_s / 2:
+            break
+    t_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    lam, U = np.linalg.eigh(S)
+    U = U[:, ::-1][:, :cfg["rank"]]
+    t_e = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    for Xb in blocks:
+        Xb.T @ U
+    t_v = time.perf_counter() - t2
+    est = (t_s + t_v) * nblk / done + t_e
+    return {"value": 1.0 / est, "extrapolated_s": est,
+            "sample": f"decomposition only: S = X X^T and V = X^T U on {done} of {nblk} column blocks "
+                      f"({time.perf_counter() - t0:.1f} s), scaled to all blocks, plus eigh of S; the explicit "
+                      f"reconstruction (L x K per group) does not fit the host and is left out"}
+
+
+def oracle_baselines(names, budget_s):
+    """Each workload's oracle sample on all host cores and on one thread, each
+    in a fresh interpreter (the BLAS thread count is fixed at start-up)."""
+    out = {}
+    for name in names:
+        out[name] = {}
+        for label, threads in (("all_cores", None), ("one_thread", 1)):
+            env = dict(os.environ)
+            if threads:
+                for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                    env[v] = str(threads)
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", name,
+                                "--oracle-budget", str(budget_s)], env=env, capture_output=True, text=True)
+            try:
+                d = json.loads(r.stdout.strip().splitlines()[-1])
+            except Exception:
+                d = {"error": (r.stderr or r.stdout)[-300:]}
+            d.update({"unit": "decomps/s", "cores": threads or cpu_cores(), "kind": "oracle"})
+            out[name][label] = d
+    return out
+
+
 def _probe_info(pkg, probs, cfg, stream, args):
     """Krylov dimension the library uses for one problem of the workload."""
     lens, flat = probs[0]
@@ -340,17 +562,31 @@ def main():
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--krylov-dim", type=int, default=0, help="0: the library default min(2r+16, 112, min(L,K))")
-    ap.add_argument("--serve-requests", type=int, default=1500)
-    ap.add_argument("--serve-rate", type=float, default=1000.0)
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the Poisson part")
+    ap.add_argument("--serve-saturation", type=int, default=1000, help="requests of the closed-loop part")
+    ap.add_argument("--serve-load", type=float, default=0.8, help="Poisson rate as a fraction of capacity")
+    ap.add_argument("--serve-rate", type=float, default=1000.0, help="--serve-only: open-loop rate (0: closed)")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-only", action="store_true", help="run only the serving stream")
     ap.add_argument("--write-traffic", default=None,
                     help="ncu CSV of k_mv1d dram bytes -> profiles/k_mv1d_mssa_traffic.json (no GPU use)")
     ap.add_argument("--traffic-command", default="")
+    ap.add_argument("--configs", default=",".join(CONFIG_RUNS),
+                    help="other workloads timed after the headline (comma list; empty: none)")
+    ap.add_argument("--config-steps", type=int, default=5)
+    ap.add_argument("--oracle-budget", type=float, default=6.0, help="seconds of oracle work per sample")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--configs-only", action="store_true",
+                    help="time only the --configs workloads (profiling runs); no headline line")
+    ap.add_argument("--config-precs", default="fp32,fp64")
     args = ap.parse_args()
     if args.write_traffic:
         write_traffic(args.write_traffic, args.batch, args.traffic_command)
         return 0
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample, args.oracle_budget)), flush=True)
+        return 0
+    configs = [c for c in args.configs.split(",") if c]
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,10 +616,13 @@ def main():
     import paper_1309_5050_gb300 as pkg
     from paper_1309_5050_gb300 import _lib
 
-    # a process pool is never used; the oracle leg runs in-process before CUDA work
+    # a process pool is never used; the oracle legs run before CUDA work (in
+    # process, and in fresh interpreters for the per-workload samples)
     cpu = None
+    oracles = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        oracles = oracle_baselines(configs + [WORKLOAD], args.oracle_budget)
 
     torch.cuda.set_device(local)
     dist = None
@@ -393,13 +632,29 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     pkg.load()
+    if args.configs_only:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        out = {}
+        for name in configs:
+            out[name] = {pr: run_config(pkg, torch, name, pr, stream, flush, args.config_steps, args.warmup)
+                         for pr in args.config_precs.split(",")}
+        if rank == 0:
+            print(json.dumps({"configs": out}), flush=True)
+        return 0
     if args.serve_only:
         # only the serving stream (profiling and latency studies)
-        reqs = W.serving_requests(n=args.serve_requests, rate_hz=args.serve_rate, seed=5 + rank, n_max=SERVE_N_MAX)
         with Clocks(local) as ck:
-            serving = run_serving(pkg, reqs, args.prec, int(args.serve_budget_gb * (1 << 30)), args.serve_rate)
+            if args.serve_rate > 0:
+                reqs = W.serving_requests(n=args.serve_requests, rate_hz=args.serve_rate, seed=5 + rank,
+                                          n_max=SERVE_N_MAX)
+                serving = run_serving(pkg, reqs, args.prec, int(args.serve_budget_gb * (1 << 30)), args.serve_rate)
+                value = serving["throughput_rps"]
+            else:
+                serving = serve_at_spec(pkg, args.serve_saturation, args.serve_requests, args.prec,
+                                        int(args.serve_budget_gb * (1 << 30)), 5 + rank, args.serve_load)
+                value = serving["saturation"]["throughput_rps"]
         if rank == 0:
-            print(json.dumps({"metric": "serving_requests_per_s", "value": serving["throughput_rps"], "unit": "req/s",
+            print(json.dumps({"metric": "serving_requests_per_s", "value": value, "unit": "req/s",
                               "higher_is_better": True, "serving": serving, "clocks": ck.summary(),
                               "data": "synthetic"}), flush=True)
         return 0
@@ -491,9 +746,19 @@ def main():
     # serving: a Poisson stream of mixed requests through ssa_server_*
     serving = None
     if args.serve_requests > 0:
-        reqs = W.serving_requests(n=args.serve_requests, rate_hz=args.serve_rate, seed=5 + rank,
-                                  n_max=SERVE_N_MAX)
-        serving = run_serving(pkg, reqs, args.prec, int(args.serve_budget_gb * (1 << 30)), args.serve_rate)
+        serving = serve_at_spec(pkg, args.serve_saturation, args.serve_requests, args.prec,
+                                int(args.serve_budget_gb * (1 << 30)), 5 + rank, args.serve_load)
+
+    # the other workloads, both forms
+    per_config = {}
+    for name in configs:
+        per_config[name] = {}
+        for pr in args.config_precs.split(","):
+            per_config[name][pr] = run_config(pkg, torch, name, pr, stream, flush, args.config_steps, 3)
+        if oracles:
+            per_config[name]["oracle"] = oracles.get(name)
+    if oracles:
+        per_config.setdefault(WORKLOAD, {})["oracle"] = oracles.get(WORKLOAD)
 
     # roofline of the series product (k_mv1d), the dominant kernel
     hbm, src = peaks()
@@ -543,6 +808,7 @@ def main():
                 "lanczos": {"krylov_dim": ps_info["krylov_dim"], "restarts_first_problem": restarts[-1][0],
                             "last_jacobi_sweeps_first_problem": {"fp64": restarts[-1][1], "fp32": restarts[-1][2]}},
                 "phases_ms": {k: v[0] / args.steps for k, v in prof.items()},
+                "configs": per_config,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

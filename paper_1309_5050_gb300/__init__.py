@@ -14,7 +14,7 @@ from . import _lib as L
 from ._lib import (SSA_1D, SSA_2D, SSA_F32, SSA_F64, SSA_MSSA,  # noqa: F401
                    SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64, SSAError)
 
-__all__ = ["SSA", "Server", "embed_multi_batch", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
+__all__ = ["SSA", "Server", "embed_multi_batch", "embed_series_batch", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
            "load", "SSAError", "PREC"]
 
 PREC = {"fp32": SSA_PREC_FP32FFT_FP64REORTH, "fp64": SSA_PREC_FP64}
@@ -464,6 +464,25 @@ def embed_multi_batch(flats, lengths, L_: int, stream=None):
     L.check(lib.ssa_embed_batch(ins, wins, n, _stream_ptr(stream), outs, st), "ssa_embed_batch")
     return [SSA._wrap(C.c_void_p(outs[i]), ("mssa", np.asarray(lengths[i], dtype=np.int64).copy()))
             for i in range(n)]
+
+
+def embed_series_batch(xs, L_: int, stream=None):
+    """Batched 1D embed of n series (numpy arrays or torch tensors, host or
+    device) with one window length: ssa_embed_batch.  Returns n SSA objects."""
+    lib = L.load()
+    n = len(xs)
+    ins = (L.ssa_input * n)()
+    wins = (L.ssa_window * n)()
+    keep = []
+    for i, x in enumerate(xs):
+        ptr, dev, kp, code = _buf(x)
+        keep.append(kp)
+        ins[i] = L.ssa_input(kind=SSA_1D, dtype=code, on_device=dev, n_series=1, data=ptr, n=int(x.shape[0]))
+        wins[i] = L.ssa_window(L=L_)
+    outs = (C.c_void_p * n)()
+    st = (C.c_int32 * n)()
+    L.check(lib.ssa_embed_batch(ins, wins, n, _stream_ptr(stream), outs, st), "ssa_embed_batch")
+    return [SSA._wrap(C.c_void_p(outs[i]), ("1d", int(xs[i].shape[0]))) for i in range(n)]
 
 
 def decompose_batch(problems, rank, prec: str = "fp32", krylov_dim: int = 0, tol: float = 0.0, seed: int = 0,
