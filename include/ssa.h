@@ -295,6 +295,40 @@ int ssa_get_shape(const ssa_ctx* ctx, int64_t* L, int64_t* K, uint8_t* origin_ma
 int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, double* out, int32_t on_device);
 
 /*
+ * Tuned plans (process-wide; no paper counterpart -- implementation tuning).
+ * Two choices are otherwise derived from the sizes: the Krylov dimension k of
+ * a decomposition (default min(2r + 16, 112, min(L, K))) and the y-pass tile
+ * of 2D grids (x-frequencies transformed along y by one block; default from a
+ * fixed shared-memory budget).  ssa_autotune times one decomposition of ctx
+ * for each candidate -- k in {2/3, 1, 3/2, 2} x the default (clipped to
+ * [r, min(112, L, K)]), then for 2D grids the tile in {1/2, 2, 4} x the
+ * default that fit a block -- keeps the fastest converged one and records it
+ * as the plan of its size class: k keyed by (precision form, kind, L,
+ * ceil log2 K, r), the tile by (element size, grid).  Every later
+ * decomposition with krylov_dim = 0 and every product on such a grid uses
+ * the plans.  ctx ends decomposed with the chosen plan.  out (may be NULL):
+ * the choice, candidates timed, and the default and best times (ms,
+ * CUDA events on the context's stream).
+ * ssa_plans_export writes the plans as text lines "kdim <key> <k>" /
+ * "ytk <key> <tile>" into buf (cap bytes, NUL-terminated; *len = bytes
+ * needed) so a caller can keep them in a file; ssa_plans_import reads such
+ * text back.
+ * Errors: SSA_EINVAL, SSA_ERANK; those of ssa_decompose.
+ */
+typedef struct {
+  int32_t krylov_dim;      /* chosen k */
+  int32_t ytk;             /* chosen y-pass tile (0: not a 2D grid) */
+  int32_t n_tried;         /* candidates timed */
+  int32_t pad_;
+  double ms_default;       /* one decomposition with the default plan */
+  double ms_best;          /* one decomposition with the chosen plan */
+} ssa_tune_result;
+
+int ssa_autotune(ssa_ctx* ctx, const ssa_params* params, ssa_tune_result* out);
+int ssa_plans_export(char* buf, int64_t cap, int64_t* len);
+int ssa_plans_import(const char* text);
+
+/*
  * Profiling (process-wide; no paper counterpart -- measurement support).
  * Phases: 0 shapes and weights, 1 data spectrum, 2 trajectory products
  * (X v and X^T u), 3 short-side Lanczos (re-orthogonalisation), 4 long-side

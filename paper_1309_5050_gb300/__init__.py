@@ -15,7 +15,7 @@ from ._lib import (SSA_1D, SSA_2D, SSA_F32, SSA_F64, SSA_MSSA,  # noqa: F401
                    SSA_PREC_FP32FFT_FP64REORTH, SSA_PREC_FP64, SSAError)
 
 __all__ = ["SSA", "Server", "embed_multi_batch", "embed_series_batch", "decompose_batch", "reconstruct_batch", "window_circle", "window_triangle",
-           "load", "SSAError", "PREC"]
+           "load", "SSAError", "PREC", "save_plans", "load_plans"]
 
 PREC = {"fp32": SSA_PREC_FP32FFT_FP64REORTH, "fp64": SSA_PREC_FP64}
 
@@ -181,6 +181,15 @@ class SSA:
         L.check(self._lib.ssa_continue(self.ctx, C.byref(p)), "ssa_continue")
         self.rank = rank
         return 0
+
+    def autotune(self, rank: int, prec: str = "fp32", seed: int = 0) -> dict:
+        """Time the candidate plans on this problem (ssa_autotune), record
+        the fastest for its size class and leave the problem decomposed."""
+        p = L.ssa_params(rank=rank, krylov_dim=0, max_restarts=0, prec=PREC[prec], tol=0.0, seed=seed)
+        res = L.ssa_tune_result()
+        L.check(self._lib.ssa_autotune(self.ctx, C.byref(p), C.byref(res)), "ssa_autotune")
+        self.rank = rank
+        return {f: getattr(res, f) for f, _ in L.ssa_tune_result._fields_ if f != "pad_"}
 
     def info(self) -> dict:
         i = L.ssa_info()
@@ -532,3 +541,15 @@ def reconstruct_batch(problems, groups, residual: bool = False, outs=None):
         t = p._total()
         res.append([p._split(o[g * t:(g + 1) * t]) for g in range(nout)])
     return res
+
+
+def save_plans(path: str) -> None:
+    """Write the tuned plans to a text file (ssa_plans_export)."""
+    with open(path, "w") as f:
+        f.write(L.plans_export())
+
+
+def load_plans(path: str) -> None:
+    """Read tuned plans from a text file (ssa_plans_import)."""
+    with open(path) as f:
+        L.plans_import(f.read())

@@ -22,7 +22,7 @@ EXPORTS = [
     "ssa_get_vectors", "ssa_reconstruct", "ssa_reconstruct_batch", "ssa_wcor", "ssa_forecast", "ssa_forecast_vector", "ssa_forecast_row", "ssa_get_shape", "ssa_matvec",
     "ssa_synchronize", "ssa_destroy", "ssa_strerror", "ssa_last_error", "ssa_version",
     "ssa_profile_enable", "ssa_profile_reset", "ssa_profile_read", "ssa_kernel_launches",
-    "ssa_matvec_series_noalloc", "ssa_noalloc_last_error",
+    "ssa_matvec_series_noalloc", "ssa_noalloc_last_error", "ssa_autotune", "ssa_plans_export", "ssa_plans_import",
     "ssa_server_create", "ssa_server_submit", "ssa_server_step", "ssa_server_stats", "ssa_server_finished", "ssa_server_take",
     "ssa_server_clock", "ssa_server_destroy",
 ]
@@ -52,6 +52,11 @@ class ssa_info(C.Structure):
                 ("fft_mx", C.c_int64), ("fft_my", C.c_int64), ("max_residual", C.c_double),
                 ("device_bytes", C.c_int64), ("jacobi_sweeps", C.c_int32), ("jacobi_sweeps_fp32", C.c_int32),
                 ("breakdowns", C.c_int32), ("pad_", C.c_int32)]
+
+
+class ssa_tune_result(C.Structure):
+    _fields_ = [("krylov_dim", C.c_int32), ("ytk", C.c_int32), ("n_tried", C.c_int32), ("pad_", C.c_int32),
+                ("ms_default", C.c_double), ("ms_best", C.c_double)]
 
 
 class ssa_server_config(C.Structure):
@@ -118,6 +123,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.ssa_matvec_series_noalloc.argtypes = [P, C.c_int64, C.c_int64, C.c_int32, P, P, P]
     lib.ssa_noalloc_last_error.argtypes = []
     lib.ssa_noalloc_last_error.restype = C.c_char_p
+    lib.ssa_autotune.argtypes = [P, C.POINTER(ssa_params), C.POINTER(ssa_tune_result)]
+    lib.ssa_plans_export.argtypes = [C.c_char_p, C.c_int64, C.POINTER(C.c_int64)]
+    lib.ssa_plans_import.argtypes = [C.c_char_p]
     lib.ssa_server_create.argtypes = [C.POINTER(ssa_server_config), P, C.POINTER(P)]
     lib.ssa_server_submit.argtypes = [P, C.POINTER(ssa_input), C.POINTER(ssa_window), C.POINTER(ssa_params),
                                       P, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]
@@ -183,3 +191,17 @@ def matvec_series_noalloc(x, L: int, v, out, transpose: bool = False, stream=Non
     if rc != SSA_OK:
         raise RuntimeError(f"ssa_matvec_series_noalloc: {lib.ssa_strerror(rc).decode()} ({rc}): "
                            f"{lib.ssa_noalloc_last_error().decode()}")
+
+
+def plans_export() -> str:
+    """The tuned plans (ssa_plans_export) as text."""
+    lib = load()
+    n = C.c_int64()
+    check(lib.ssa_plans_export(None, 0, C.byref(n)), "ssa_plans_export")
+    buf = C.create_string_buffer(int(n.value) + 1)
+    check(lib.ssa_plans_export(buf, int(n.value) + 1, C.byref(n)), "ssa_plans_export")
+    return buf.value.decode()
+
+
+def plans_import(text: str) -> None:
+    check(load().ssa_plans_import(text.encode()), "ssa_plans_import")

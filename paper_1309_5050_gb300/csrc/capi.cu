@@ -167,6 +167,45 @@ static int ensure_tables(int dev) {
 template <> const Cx<float>* twiddles<float>(int dev) { return g_tables[dev].t32; }
 template <> const Cx<double>* twiddles<double>(int dev) { return g_tables[dev].t64; }
 
+// ---------------------------------------------------------------- tuned plans
+// A plan fixes two choices the library otherwise derives from the sizes: the
+// Krylov dimension of a decomposition (keyed by precision form, kind, L,
+// ceil log2 K and rank) and the y-pass tile -- the x-frequencies a block
+// transforms along y -- of 2D grids (keyed by element size and grid).
+// ssa_autotune times candidates on a real problem and records the fastest;
+// later decompositions and products of the same class use them.
+struct PlanTable {
+  std::mutex mu;
+  std::map<std::string, int> kdim;
+  std::map<std::string, int> ytk;
+};
+static PlanTable g_plans;
+
+static std::string kdim_key(int prec, int kind, int64_t L, int64_t K, int r) {
+  int lk = 0;
+  while ((int64_t(1) << lk) < K) ++lk;
+  char b[96];
+  snprintf(b, sizeof(b), "p%d.k%d.L%lld.K%d.r%d", prec, kind, (long long)L, lk, r);
+  return b;
+}
+static std::string ytk_key(int esz, int log2Mx, int log2My) {
+  char b[48];
+  snprintf(b, sizeof(b), "e%d.x%d.y%d", esz, log2Mx, log2My);
+  return b;
+}
+static int plan_kdim(int prec, int kind, int64_t L, int64_t K, int r) {
+  std::lock_guard<std::mutex> lk(g_plans.mu);
+  auto it = g_plans.kdim.find(kdim_key(prec, kind, L, K, r));
+  return it == g_plans.kdim.end() ? 0 : it->second;
+}
+// y-pass tile of a grid: the tuned one, else the default from the buffer budget
+template <typename T>
+static int tuned_ytk(int log2Mx, int log2My) {
+  std::lock_guard<std::mutex> lk(g_plans.mu);
+  auto it = g_plans.ytk.find(ytk_key((int)sizeof(T), log2Mx, log2My));
+  return it == g_plans.ytk.end() ? ypass_tk<T>(log2My) : it->second;
+}
+
 // small helper kernels of the driver
 // bd_scale = 4 eps_T log2(grid points): with ||x|| it is a few times the rounding
 // error of one product with a unit vector (FFT error ~ eps log2 M ||x|| ||v||); a
@@ -708,7 +747,7 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
         YItem<T> y;
         y.src = sp.g1; y.dst = sp.xh; y.mul = nullptr; y.st = nullptr;
         y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = sp.ny; y.out_hi = My; y.scale = T(0);
-        y.tk = ypass_tk<T>(c->log2My);
+        y.tk = tuned_ytk<T>(c->log2Mx, c->log2My);
         yitems.push_back(y);
         sy_pre.push_back(sy_pre.back() + ypass_blocks(c->log2Mx, y.tk));
       }
@@ -737,8 +776,11 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
       g_ring.copy(dpy, sy_pre.data(), sizeof(int32_t) * sy_pre.size(), st) != SSA_OK)
     return fail(SSA_ECUDA, "spectrum tile upload");
   (void)max_ny;
+  int max_tk = 1;
+  for (auto& y : yitems) max_tk = std::max(max_tk, (int)y.tk);
   launch_spec<T>(di, Tiles{dpx, (int)items.size(), sx_pre.back()}, dy,
-                 Tiles{dpy, (int)yitems.size(), sy_pre.back()}, max_log2Mx, max_log2My, twiddles<T>(cs[0]->device), st);
+                 Tiles{dpy, (int)yitems.size(), sy_pre.back()}, max_log2Mx, max_log2My, twiddles<T>(cs[0]->device), st,
+                 max_tk);
   CU(cudaGetLastError());
   cudaFreeAsync(di, st);
   cudaFreeAsync(dy, st);
@@ -770,7 +812,7 @@ struct MvSet {
   YItem<T>* dy2 = nullptr;
   int32_t *t_xf = nullptr, *t_yp = nullptr, *t_xi = nullptr;   // block ranges of the 2D launches
   int n_xf = 0, n_yp = 0, n_xi = 0;
-  int max_y_in = 0, max_y_out = 0;
+  int max_y_in = 0, max_y_out = 0, max_tk = 1;
   int lx1[MV1_MODES] = {}, lx2 = 1, ly2 = 0;   // largest log2 grid sizes of each list
   void add(const MvItem<T>& m) {
     if (m.log2My == 0) {
@@ -826,7 +868,7 @@ static YItem<T> ymv(const MvItem<T>& m) {
   y.src = m.g1; y.dst = m.g2; y.mul = m.xh; y.st = m.st;
   y.log2Mx = m.log2Mx; y.log2My = m.log2My;
   y.in_hi = m.y_in_hi; y.out_hi = m.y_out_hi; y.scale = T(0);
-  y.tk = ypass_tk<T>(m.log2My);
+  y.tk = tuned_ytk<T>(m.log2Mx, m.log2My);
   return y;
 }
 
@@ -838,6 +880,7 @@ static int finish_set(MvSet<T>& s, Up&& up) {
   std::vector<int32_t> xf{0}, yp{0}, xi{0};
   for (auto& m : s.items2) {
     s.yitems2.push_back(ymv(m));
+    s.max_tk = std::max(s.max_tk, (int)s.yitems2.back().tk);
     xf.push_back(xf.back() + m.y_in_hi);
     yp.push_back(yp.back() + ypass_blocks(m.log2Mx, s.yitems2.back().tk));
     xi.push_back(xi.back() + m.y_out_hi);
@@ -863,7 +906,7 @@ static void run_mv(int dev, const MvSet<T>& s, int step, cudaStream_t st) {
   if (!s.items2.empty()) {
     const int n2 = (int)s.items2.size();
     launch_mv2d<T>(s.d2, s.dy2, n2, Tiles{s.t_xf, n2, s.n_xf}, Tiles{s.t_yp, n2, s.n_yp},
-                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(dev), st);
+                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(dev), st, s.max_tk);
   }
 }
 
@@ -901,7 +944,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   w = Workspace();
   w.prec = p.prec;
   w.r = p.rank;
-  w.k = default_k(p.rank, c->L, c->K, p.krylov_dim);
+  w.k = default_k(p.rank, c->L, c->K, p.krylov_dim ? p.krylov_dim : plan_kdim(p.prec, c->kind, c->L, c->K, p.rank));
   w.kk = std::max(w.r, std::min(w.k - 2, w.r + std::max(8, w.r / 2)));
   w.swapped = c->L > c->K;
   w.Ls = w.swapped ? c->K : c->L;
@@ -1304,6 +1347,8 @@ struct LzEngine {
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
     if ((mvA.n1() || mvAT.n1()) && mv_async_timeouts(st) != 0)
       return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
+    if (std::is_same<T, float>::value && ritz_tc_timeouts(st) != 0)
+      return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
     return SSA_OK;
   }
   // One chunk: every member inside a cycle advances up to `steps` Lanczos
@@ -1333,13 +1378,14 @@ struct LzEngine {
     std::vector<ssa_ctx*> cs;
     std::vector<RitzItem<T>> rz;
     std::vector<SvdItem> sv;
-    int mk = 1;
+    int mk = 1, mkk = 1;
     for (size_t i = 0; i < live.size(); ++i)
       if (hst[i].active && hst[i].svd_done) {
         cs.push_back(live[i]);
         rz.push_back(ritz_item(live[i]));
         sv.push_back(svd_item(live[i]));
         mk = std::max(mk, live[i]->ws.k);
+        mkk = std::max(mkk, live[i]->ws.kk);
       }
     if (cs.empty()) return SSA_OK;
     RitzItem<T>* d_r = nullptr; SvdItem* d_v = nullptr;
@@ -1355,7 +1401,7 @@ struct LzEngine {
       dev_tmp.resize(keep);
     }
     PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_r, (int)cs.size(), mk, ts, ns, tl, nlg, 0, st);
+    launch_ritz<T>(d_r, (int)cs.size(), mk, mkk, ts, ns, tl, nlg, 0, st);
     launch_restart(d_v, (int)cs.size(), st);
     CU(cudaGetLastError());
     for (auto& h : hst)
@@ -1384,7 +1430,7 @@ struct LzEngine {
     TRY(up(rz, &d_r)); TRY(up(fi, &d_f));
     TRY(ritz_tiles(cs, &ts, &ns, &tl, &nl));
     PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_r, (int)idx.size(), mk, ts, ns, tl, nl, 1, st);
+    launch_ritz<T>(d_r, (int)idx.size(), mk, mr, ts, ns, tl, nl, 1, st);
     launch_finalize<T>(d_f, (int)idx.size(), mr, mrows, st);
     CU(cudaGetLastError());
     for (int i : idx) {
@@ -1509,6 +1555,8 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
       for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
       TRY(eng.retire(all));
       CU(cudaStreamSynchronize(eng.st));
+      if (std::is_same<T, float>::value && ritz_tc_timeouts(eng.st) != 0)
+        return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
       for (size_t i = 0; i < eng.live.size(); ++i) {
         const LzState& h = eng.hst[i];
         if (!h.converged) {
@@ -1800,7 +1848,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         YItem<T> ya;
         ya.src = gx; ya.dst = gu; ya.mul = nullptr; ya.st = nullptr; ya.log2Mx = c->log2Mx; ya.log2My = c->log2My;
         ya.in_hi = wcols; ya.out_hi = My; ya.scale = T(0);
-        ya.tk = ypass_tk<T>(c->log2My);
+        ya.tk = tuned_ytk<T>(c->log2Mx, c->log2My);
         YItem<T> yb = ya;
         yb.dst = acc + (size_t)std::max(g, 0) * hs; yb.mul = gu; yb.in_hi = kcols;
         yb.scale = (T)(sig[i] / ((double)(2 * H) * (double)My));
@@ -1812,7 +1860,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         YItem<T> y;
         y.src = acc + (size_t)g * hs; y.dst = g2; y.mul = nullptr; y.st = nullptr;
         y.log2Mx = c->log2Mx; y.log2My = c->log2My; y.in_hi = My; y.out_hi = oy; y.scale = T(0);
-        y.tk = ypass_tk<T>(c->log2My);
+        y.tk = tuned_ytk<T>(c->log2Mx, c->log2My);
         yi.push_back(y);
         Rec2Item<T> x;
         x.g2 = g2; x.log2Mx = c->log2Mx; x.pad_ = 0; x.inv_norm = 1.0;
@@ -1832,7 +1880,8 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
     TRY(upload(c0, yi, &d_yi)); tmp.push_back(d_yi);
     TRY(upload(c0, xi, &d_xi)); tmp.push_back(d_xi);
     if (fold) { TRY(upload(c0, fi, &d_fi)); tmp.push_back(d_fi); }
-    const Tiles y1{nullptr, 1, ypass_blocks(c->log2Mx, ypass_tk<T>(c->log2My))};
+    const int rtk = tuned_ytk<T>(c->log2Mx, c->log2My);
+    const Tiles y1{nullptr, 1, ypass_blocks(c->log2Mx, rtk)};
     for (size_t q = 0; q < c->ch.size(); ++q) {
       const Channel& h = c->ch[q];
       const int wcols = fold ? c->lb : c->ey, kcols = fold ? h.kb : h.cy;
@@ -1841,13 +1890,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         if (group_of[i] < 0) continue;
         const size_t e = 2 * ((size_t)q * r + i);
         launch_rec_col_fft<T, TV>(d_cu + e, 1, c->log2Mx, wcols, tw, st);
-        launch_ypass<T>(d_yu + e, y1, Y_FWD, c->log2My, -1, tw, st);
+        launch_ypass<T>(d_yu + e, y1, Y_FWD, c->log2My, -1, tw, st, rtk);
         launch_rec_col_fft<T, TV>(d_cu + e + 1, 1, c->log2Mx, kcols, tw, st);
-        launch_ypass<T>(d_yu + e + 1, y1, Y_CONVACC, c->log2My, -1, tw, st);
+        launch_ypass<T>(d_yu + e + 1, y1, Y_CONVACC, c->log2My, -1, tw, st, rtk);
       }
       for (int g = 0; g < ng; ++g) {
         const size_t e = (size_t)q * ng + g;
-        launch_ypass<T>(d_yi + e, y1, Y_INV, c->log2My, -1, tw, st);
+        launch_ypass<T>(d_yi + e, y1, Y_INV, c->log2My, -1, tw, st, rtk);
         launch_rec_xinv<T>(d_xi + e, 1, c->log2Mx, xi[e].ny, tw, st);
         if (fold) launch_rec_fold(d_fi + e, 1, h.nx, st);
       }
@@ -2618,6 +2667,133 @@ int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, 
     return matvec_T<double>(ctx, transpose, in, out, on_device);
   }
   return matvec_T<float>(ctx, transpose, in, out, on_device);
+}
+
+// ---------------------------------------------------------------- autotuner
+// Times one decomposition of ctx (with its own Krylov dimension kd) on the
+// context's stream: the span between two events, host round trips included.
+static int tune_run(ssa_ctx* ctx, const ssa_params& p0, int kd, double* ms) {
+  ssa_params p = p0;
+  p.krylov_dim = kd;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CU(cudaEventCreate(&a));
+  CU(cudaEventCreate(&b));
+  CU(cudaEventRecord(a, ctx->stream));
+  const int rc = ssa_decompose(ctx, &p);
+  cudaEventRecord(b, ctx->stream);
+  cudaEventSynchronize(b);
+  float f = 0.0f;
+  cudaEventElapsedTime(&f, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = f;
+  return rc;
+}
+
+int ssa_autotune(ssa_ctx* ctx, const ssa_params* params, ssa_tune_result* out) {
+  if (!ctx || !params) return fail(SSA_EINVAL, "null argument");
+  if (params->rank < 1 || params->rank > std::min(ctx->L, ctx->K))
+    return fail(SSA_ERANK, "rank %d outside [1, min(L, K)]", params->rank);
+  const bool f64 = params->prec == SSA_PREC_FP64;
+  const int esz = f64 ? 16 : 8;                     // complex element of the form
+  const int r = params->rank;
+  const std::string kkey = kdim_key(params->prec, ctx->kind, ctx->L, ctx->K, r);
+  const std::string tkey = ytk_key(esz, ctx->log2Mx, ctx->log2My);
+  {
+    std::lock_guard<std::mutex> lk(g_plans.mu);     // candidates are timed without earlier plans
+    g_plans.kdim.erase(kkey);
+    g_plans.ytk.erase(tkey);
+  }
+  // Krylov dimensions around the default 2r + 16
+  const int d = default_k(r, ctx->L, ctx->K, 0);
+  const int kmax = (int)std::min<int64_t>(KMAX, std::min(ctx->L, ctx->K));
+  std::vector<int> ks;
+  for (int c : {std::max(r + 2, (2 * d) / 3), d, (3 * d) / 2, 2 * d}) {
+    const int kc = std::max(r, std::min(c, kmax));
+    if (std::find(ks.begin(), ks.end(), kc) == ks.end()) ks.push_back(kc);
+  }
+  double ms = 0.0, ms_default = 0.0, best_ms = 1e300;
+  int best_k = d, tried = 0;
+  TRY(tune_run(ctx, *params, d, &ms));              // warm-up: spectra, workspaces
+  for (int kc : ks) {
+    const int rc = tune_run(ctx, *params, kc, &ms);
+    ++tried;
+    if (kc == d) ms_default = ms;
+    if (rc == SSA_OK && ms < best_ms) { best_ms = ms; best_k = kc; }
+  }
+  // y-pass tile of 2D grids: powers of two around the default that fit the
+  // shared memory of a block
+  const int dtk = f64 ? ypass_tk<double>(ctx->log2My) : ypass_tk<float>(ctx->log2My);
+  int best_tk = dtk;
+  if (ctx->log2My > 0) {
+    const int pl = padded_len(1 << ctx->log2My);
+    const int nb = YPASS_BUF_BYTES / esz;
+    for (int tk : {dtk / 2, dtk * 2, dtk * 4}) {
+      if (tk < 1 || tk > 64) continue;
+      const size_t bytes = (size_t)esz * (2 * (size_t)std::max(nb, tk * pl) + (1 << std::max(ctx->log2My, 3)) / 8 + 1);
+      if (bytes > (size_t)device_max_smem()) continue;
+      {
+        std::lock_guard<std::mutex> lk(g_plans.mu);
+        g_plans.ytk[tkey] = tk;
+      }
+      const int rc = tune_run(ctx, *params, best_k, &ms);
+      ++tried;
+      if (rc == SSA_OK && ms < best_ms) { best_ms = ms; best_tk = tk; }
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_plans.mu);
+    g_plans.kdim[kkey] = best_k;
+    if (ctx->log2My > 0) g_plans.ytk[tkey] = best_tk;
+  }
+  // leave the context decomposed with the chosen plan
+  TRY(tune_run(ctx, *params, 0, &ms));
+  if (out) {
+    out->krylov_dim = best_k;
+    out->ytk = ctx->log2My > 0 ? best_tk : 0;
+    out->n_tried = tried;
+    out->pad_ = 0;
+    out->ms_default = ms_default;
+    out->ms_best = best_ms;
+  }
+  return SSA_OK;
+}
+
+int ssa_plans_export(char* buf, int64_t cap, int64_t* len) {
+  std::string t;
+  {
+    std::lock_guard<std::mutex> lk(g_plans.mu);
+    for (auto& kv : g_plans.kdim) t += "kdim " + kv.first + " " + std::to_string(kv.second) + "\n";
+    for (auto& kv : g_plans.ytk) t += "ytk " + kv.first + " " + std::to_string(kv.second) + "\n";
+  }
+  if (len) *len = (int64_t)t.size();
+  if (buf && cap > 0) {
+    const size_t n = std::min<size_t>(t.size(), (size_t)cap - 1);
+    std::memcpy(buf, t.data(), n);
+    buf[n] = 0;
+    if (n < t.size()) return fail(SSA_EINVAL, "buffer of %lld bytes holds %zu of %zu", (long long)cap, n, t.size());
+  }
+  return SSA_OK;
+}
+
+int ssa_plans_import(const char* text) {
+  if (!text) return fail(SSA_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(g_plans.mu);
+  const char* p = text;
+  while (*p) {
+    const char* e = std::strchr(p, '\n');
+    const std::string line(p, e ? (size_t)(e - p) : std::strlen(p));
+    p = e ? e + 1 : p + line.size();
+    if (line.empty()) continue;
+    char kind[16] = {}, key[96] = {};
+    int v = 0;
+    if (std::sscanf(line.c_str(), "%15s %95s %d", kind, key, &v) != 3 || v < 1)
+      return fail(SSA_EINVAL, "bad plan line: %s", line.c_str());
+    if (!std::strcmp(kind, "kdim") && v <= KMAX) g_plans.kdim[key] = v;
+    else if (!std::strcmp(kind, "ytk") && v <= 64) g_plans.ytk[key] = v;
+    else return fail(SSA_EINVAL, "bad plan line: %s", line.c_str());
+  }
+  return SSA_OK;
 }
 
 int ssa_synchronize(ssa_ctx* c) {

@@ -310,6 +310,93 @@ __device__ void block_fft_io(In in, Out out, Cx<T>* a, Cx<T>* b, int log2n, cons
   }
 }
 
+// ---------------------------------------------------------------- compile-time sizes
+// The same Stockham transform with the length 2^LOG2N, the block size NT and
+// the twiddle table order LOG2TN (octant table of W_{2^LOG2TN}) known at
+// compile time: every index, stride, padding offset and loop count folds to
+// constants, which removes most of the integer work of the runtime form (the
+// series product is issue-bound).  Stage with LR = log2 radix after LOG2NS
+// bits; its NQ = 2^(LOG2N - LR) butterflies are spread over the NT threads.
+template <typename T, bool INV, int LR, int LOG2N, int LOG2NS, int NT, int LOG2TN, class In, class Out>
+__device__ __forceinline__ void stage_ct(In& in, Out& out, const Cx<T>* tab) {
+  constexpr int R = 1 << LR;
+  constexpr int NQ = (1 << LOG2N) >> LR;
+  constexpr int NS = 1 << LOG2NS;
+  constexpr int TSHIFT = LOG2TN - (LOG2NS + LR);     // W_{NS R}^a = W_{2^LOG2TN}^{a << TSHIFT}
+  constexpr int ITER = (NQ + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < ITER; ++it) {
+    const int j = (int)threadIdx.x + it * NT;
+    if (NQ % NT != 0 && j >= NQ) break;
+    const int k = j & (NS - 1);
+    Cx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in(j, r, NQ);      // element j + r NQ
+    if (LOG2NS > 0) {
+      Cx<T> w1 = tw_oct(tab, LOG2TN, (int64_t)k << TSHIFT);
+      if (INV) w1 = conj(w1);
+      Cx<T> w = w1;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        v[r] = v[r] * w;
+        if (r + 1 < R) w = w * w1;
+      }
+    }
+    if (LR == 3) dft8<T, INV>(v);
+    else if (LR == 2) dft4<T, INV>(v[0], v[1], v[2], v[3]);
+    else dft2<T, INV>(v[0], v[1]);
+    out(((j - k) << LR) + k, NS, v);
+  }
+}
+
+// radix-8 stages after the first DONE bits, ping-ponging between the padded
+// buffers src and dst; the last one hands its outputs to out
+// Padded element j + r nq with j < nq and 16 | nq: padi(j) + r (nq + nq / 16),
+// a constant offset per r once nq is a compile-time constant.
+template <typename T>
+__device__ __forceinline__ Cx<T> padded_at(const Cx<T>* src, int j, int r, int nq) {
+  return (nq & 15) ? src[padi(j + r * nq)] : src[padi(j) + r * (nq + (nq >> 4))];
+}
+// padded store of a butterfly's outputs base + r stride (16 | stride: constant offsets)
+template <typename T, int R>
+__device__ __forceinline__ void padded_put(Cx<T>* dst, int base, int stride, const Cx<T> (&v)[R]) {
+  if (stride & 15) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[padi(base + r * stride)] = v[r];
+  } else {
+    const int pb = padi(base);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[pb + r * (stride + (stride >> 4))] = v[r];
+  }
+}
+
+template <typename T, bool INV, int LOG2N, int DONE, int NT, int LOG2TN, class Out>
+__device__ __forceinline__ void stages8_ct(Cx<T>* src, Cx<T>* dst, Out& out, const Cx<T>* tab) {
+  auto rd = [src](int j, int r, int nq) { return padded_at(src, j, r, nq); };
+  if constexpr (DONE + 3 == LOG2N) {
+    stage_ct<T, INV, 3, LOG2N, DONE, NT, LOG2TN>(rd, out, tab);
+    __syncthreads();
+  } else {
+    auto wd = [dst](int base, int stride, auto& v) { padded_put(dst, base, stride, v); };
+    stage_ct<T, INV, 3, LOG2N, DONE, NT, LOG2TN>(rd, wd, tab);
+    __syncthreads();
+    stages8_ct<T, INV, LOG2N, DONE + 3, NT, LOG2TN>(dst, src, out, tab);
+  }
+}
+
+// block_fft_io with compile-time sizes (LOG2N >= 4): first stage of the 1..3
+// leftover bits from in(j, r, nq) (element j + r nq), radix-8 stages after
+// it, the last to out(base, stride, v).  A barrier follows every stage.
+template <typename T, bool INV, int LOG2N, int NT, int LOG2TN, class In, class Out>
+__device__ __forceinline__ void block_fft_io_ct(In in, Out out, Cx<T>* a, Cx<T>* b, const Cx<T>* tab) {
+  static_assert(LOG2N >= 4, "compile-time form needs at least two stages");
+  constexpr int LR0 = LOG2N - 3 * ((LOG2N - 1) / 3);   // 1..3
+  auto wr = [b](int base, int stride, auto& v) { padded_put(b, base, stride, v); };
+  stage_ct<T, INV, LR0, LOG2N, 0, NT, LOG2TN>(in, wr, tab);
+  __syncthreads();
+  stages8_ct<T, INV, LOG2N, LR0, NT, LOG2TN>(b, a, out, tab);
+}
+
 // number of stages block_fft_io runs for length 2^log2n
 __host__ __device__ __forceinline__ int fft_io_stages(int log2n) { return (log2n + 2) / 3; }
 

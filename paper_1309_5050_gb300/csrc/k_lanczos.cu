@@ -694,11 +694,17 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
   const double keps = 2.220446049250313e-16 * (double)(k > 8 ? k : 8);
   const bool relaxed = 1e-3 * st->tol > keps;
   const double jtol = relaxed ? 1e-3 * st->tol : keps;
-  // FP32 form: pairs of two trailing columns are not rotated (below)
-  const int nkeep = relaxed ? min(nc, max(st->kk, st->r) + 4) : nc;
+  // FP32 form: pairs of two trailing columns are not rotated (below) -- for
+  // the first sweeps only: when the trailing columns are nearly dependent
+  // (a long cycle leaves B with singular values far below eps ||B||) the
+  // leading ones never settle against them that way, and the FP64 sweeps
+  // started from B itself (after a failed Newton-Schulz step) ran to the
+  // sweep limit at k = 112; all pairs then converge in about ten sweeps
+  const int nkeep_fast = relaxed ? min(nc, max(st->kk, st->r) + 4) : nc;
   int sweeps = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
     sweeps = sweep + 1;
+    const int nkeep = sweep < 6 ? nkeep_fast : nc;
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       const double* w = W + c * cs;
       double a0 = 0.0, a1 = 0.0;
@@ -1197,8 +1203,8 @@ void launch_restart(const SvdItem* items, int n, cudaStream_t st) {
 }
 
 template <typename T>
-void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s, int tiles_s, const int32_t* pre_l,
-                 int tiles_l, int final_pass, cudaStream_t st) {
+void launch_ritz(const RitzItem<T>* items, int n, int kmax, int kkmax, const int32_t* pre_s, int tiles_s,
+                 const int32_t* pre_l, int tiles_l, int final_pass, cudaStream_t st) {
   if (n <= 0) return;
   const int rs = RITZ_RB<double>(), rl = RITZ_RB<T>();
   const int cps = (256 / (rs / 4)) * RITZ_CW<double>(), cpl = (256 / (rl / 4)) * RITZ_CW<T>();
@@ -1210,7 +1216,11 @@ void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s
   if (tiles_s > 0) { k_ritz<T, true><<<tiles_s, 256, sms, st>>>(items, pre_s, n, final_pass); count_launch(); }
   if (tiles_l > 0) {
     k_ritz_coef<T><<<n, 256, 0, st>>>(items, final_pass); count_launch();
-    k_ritz<T, false><<<tiles_l, 256, sml, st>>>(items, pre_l, n, final_pass); count_launch();
+    if constexpr (std::is_same<T, float>::value)
+      launch_ritz_tc(items, n, kmax, kkmax, pre_l, tiles_l, final_pass, st);
+    else {
+      k_ritz<T, false><<<tiles_l, 256, sml, st>>>(items, pre_l, n, final_pass); count_launch();
+    }
   }
 }
 
@@ -1227,8 +1237,8 @@ void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_ro
 #define INST(T)                                                                                        \
   template void launch_long_step<T>(const LongItem<T>*, const int32_t*, int, int, int, cudaStream_t);  \
   template void launch_long_init<T>(const LongItem<T>*, const int32_t*, int, int, cudaStream_t);       \
-  template void launch_ritz<T>(const RitzItem<T>*, int, int, const int32_t*, int, const int32_t*, int,  \
-                               int, cudaStream_t);                                                      \
+  template void launch_ritz<T>(const RitzItem<T>*, int, int, int, const int32_t*, int, const int32_t*,  \
+                               int, int, cudaStream_t);                                                 \
   template void launch_finalize<T>(const FinalItem<T>*, int, int, int64_t, cudaStream_t);
 INST(float)
 INST(double)

@@ -1,0 +1,237 @@
+// Long-side Ritz vectors of the FP32 form on the 5th-generation tensor cores.
+//
+// After the small SVD B = P Sigma Q^T (Sec. 2.4: the role of PROPACK /
+// nu-TRLan's Ritz extraction) the long basis is rotated in place:
+//   V[:, 0:kk] <- V[:, 0:kc] C,   C = Q[0:kc, 0:kk] * colscale (kc = k + 1),
+// a dense contraction of Kl x kc by kc x kk per problem -- the one place on the
+// path where the work is a GEMM.  Each CTA owns 128 rows of one problem's
+// basis (M = 128, N = kk rounded up to 16, K = kc in chunks of 32):
+//   1. a chunk of the rows of the basis columns and of the coefficients
+//      arrives by element-wise cp.async straight into the K-major
+//      core-matrix layout the MMA reads (8 rows x 16 bytes per core matrix,
+//      no swizzle);
+//   2. each FP32 value x is split into two TF32 parts, hi = rna(x) and
+//      lo = rna(x - hi), so x = hi + lo to about 2^-24 |x|;
+//   3. one thread issues tcgen05.mma kind::tf32 for hi*hi + hi*lo + lo*hi
+//      (the lo*lo term is below FP32 rounding) per K step of 8, accumulating
+//      in FP32 in tensor memory (TMEM), and commits to an mbarrier;
+//   4. the warps read their 32 TMEM lanes (one row each) with tcgen05.ld and
+//      write the kk new columns, coalesced along the rows.
+// The in-place update is safe: a tile's rows are all read before any is
+// written, and only by the CTA that writes them.  On a restart column k (the
+// residual direction) moves to column kk.
+#include "lanczos.h"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace ssa {
+
+namespace {
+
+constexpr int RTC_M = 128;          // rows per CTA = TMEM lanes
+constexpr int RTC_NT = 256;         // eight warps: two per quarter of the 128 TMEM lanes
+constexpr int RTC_POLL = 1 << 22;   // bounded wait on the MMA barrier
+
+__device__ int g_ritz_tc_timeouts;
+
+// byte offset of element (r, c) of an operand with kp K-columns, K-major
+// core matrices: core (r / 8, c / 4) at ((r / 8) (kp / 4) + c / 4) * 128,
+// row r % 8 at 16 (r % 8), element c % 4 at 4 (c % 4)
+__device__ __forceinline__ uint32_t kmaj(int r, int c, int kp) {
+  return (uint32_t)((((r >> 3) * (kp >> 2) + (c >> 2)) << 7) + ((r & 7) << 4) + ((c & 3) << 2));
+}
+
+// shared-memory matrix descriptor (no swizzle): start address, leading byte
+// offset (next core matrix along K), stride byte offset (next 8-row group),
+// fixed 0b001 at bits 46-48
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+}  // namespace
+
+// One CTA per 128-row tile.  K is taken in chunks of KC = 32 (four MMA K
+// steps), so a CTA holds one chunk of the rows (hi in place of the raw
+// values, lo beside it) and of the coefficients: about 40 KB of shared
+// memory, and several CTAs per SM keep enough rows in flight -- the
+// contraction is memory-bound (kk of 20-60 columns per row read).
+constexpr int RTC_KC = 32;
+
+__global__ void __launch_bounds__(RTC_NT) k_ritz_tc(const RitzItem<float>* __restrict__ items,
+                                                  const int32_t* __restrict__ tpre, int n, int final_pass, int np_max) {
+  int rblk;
+  const RitzItem<float> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
+  const LzState* st = it.st;
+  if (!final_pass && (!st->active || !st->svd_done)) return;
+  const int k = st->k;
+  const int kk = final_pass ? min(st->r, k) : st->kk;
+  const int64_t r0 = (int64_t)rblk * RTC_M;
+  if (r0 >= it.Kl || kk <= 0) return;
+  const int nr = (int)imin64(RTC_M, it.Kl - r0);
+  const int kc = k + 1;
+  const int nchunk = (kc + RTC_KC - 1) / RTC_KC;
+  const int np = (kk + 15) & ~15;
+  const int ncol = np_max <= 32 ? 32 : (np_max <= 64 ? 64 : 128);   // TMEM columns (power of two >= 32)
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* ahi = reinterpret_cast<float*>(smraw);            // RTC_M x RTC_KC, core-matrix layout
+  float* alo = ahi + RTC_M * RTC_KC;
+  float* bhi = alo + RTC_M * RTC_KC;                        // np_max x RTC_KC
+  float* blo = bhi + np_max * RTC_KC;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t taddr_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* basis = it.V;
+  const int64_t ldb = it.ldv;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(ncol)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init(&bar);
+  const int rin = lane & 7, cin = lane >> 3;
+  // kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+  // both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(np >> 3) << 17) |
+                         ((uint32_t)(RTC_M >> 4) << 24);
+  bool ok = true;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int c0 = ch * RTC_KC;
+    // 1. this chunk's basis rows and coefficients into the core-matrix
+    //    layout (a warp fills one core matrix per pass: lane = row + 8 column)
+    for (int q = warp; q < (RTC_M / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
+      const int rg = q % (RTC_M / 8), cg = q / (RTC_M / 8);
+      const int r = rg * 8 + rin, c = cg * 4 + cin;
+      float* dst = reinterpret_cast<float*>(smraw + kmaj(r, c, RTC_KC));
+      if (r < nr && c0 + c < kc) cp_async_elem<4>(dst, basis + r0 + r + ldb * (c0 + c));
+      else *dst = 0.0f;
+    }
+    for (int q = warp; q < (np / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
+      const int ng = q % (np / 8), cg = q / (np / 8);
+      const int nn = ng * 8 + rin, c = cg * 4 + cin;
+      float* dst = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bhi) + kmaj(nn, c, RTC_KC));
+      if (c0 + c < kc) cp_async_elem<4>(dst, it.Cs + (int64_t)(c0 + c) * it.ldcs + nn);   // zero past kk
+      else *dst = 0.0f;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // 2. x -> hi = rna(x) in place, lo = rna(x - hi)
+    {
+      float4* h4 = reinterpret_cast<float4*>(ahi);
+      float4* l4 = reinterpret_cast<float4*>(alo);
+      for (int e = tid; e < RTC_M * RTC_KC / 4; e += RTC_NT) {
+        const float4 x = h4[e];
+        float4 h, l;
+        h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
+        l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
+        h4[e] = h;
+        l4[e] = l;
+      }
+      float4* b4 = reinterpret_cast<float4*>(bhi);
+      float4* m4 = reinterpret_cast<float4*>(blo);
+      for (int e = tid; e < np * RTC_KC / 4; e += RTC_NT) {
+        const float4 x = b4[e];
+        float4 h, l;
+        h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
+        l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
+        b4[e] = h;
+        m4[e] = l;
+      }
+    }
+    // generic-proxy stores become visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // 3. one thread: D (128 x np, FP32 in TMEM) += Ahi Bhi + Ahi Blo + Alo Bhi
+    if (tid == 0) {
+      const uint32_t tmem = taddr_s;
+      const uint32_t kstep = 2 * 128;                   // 8 K-elements = two core matrices
+      const uint32_t lbo = 128, sbo = (uint32_t)(RTC_KC / 4) * 128;
+      const uint32_t sa = smem_u32(ahi), sl = smem_u32(alo), sb = smem_u32(bhi), sm = smem_u32(blo);
+      for (int ks = 0; ks < RTC_KC / 8; ++ks) {
+        const uint32_t o = ks * kstep;
+        mma_tf32(tmem, smem_desc(sa + o, lbo, sbo), smem_desc(sb + o, lbo, sbo), idesc, (ch | ks) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(sa + o, lbo, sbo), smem_desc(sm + o, lbo, sbo), idesc, 1u);
+        mma_tf32(tmem, smem_desc(sl + o, lbo, sbo), smem_desc(sb + o, lbo, sbo), idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&bar))
+                   : "memory");
+    }
+    // the next chunk overwrites the operands: wait for these MMAs
+    ok = mbar_wait_bounded(&bar, (uint32_t)(ch & 1), RTC_POLL);
+    if (!ok && tid == 0) atomicAdd(&g_ritz_tc_timeouts, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!__syncthreads_and(ok)) { ok = false; break; }
+  }
+  const uint32_t tmem = taddr_s;
+  // 4. TMEM -> rows: warp w reads lanes 32 (w % 4).. (its rows), warps 0-3
+  //    the even groups of eight columns, warps 4-7 the odd ones
+  if (ok) {
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    float* out = basis + r0 + row;
+    for (int cb = half * 8; cb < np; cb += 16) {
+      uint32_t v[8];
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                   : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < nr) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (cb + j < kk) out[ldb * (cb + j)] = __uint_as_float(v[j]);
+      }
+    }
+    // restart: the residual direction (column k, not written above) moves to kk
+    if (!final_pass)
+      for (int t = tid; t < nr; t += RTC_NT) basis[r0 + t + ldb * kk] = basis[r0 + t + ldb * k];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol) : "memory");
+}
+
+size_t ritz_tc_smem(int kkmax) {
+  const int np = (kkmax + 15) & ~15;
+  return sizeof(float) * (size_t)(2 * RTC_M * RTC_KC + 2 * np * RTC_KC);
+}
+
+void launch_ritz_tc(const RitzItem<float>* items, int n, int kmax, int kkmax, const int32_t* pre, int tiles,
+                    int final_pass, cudaStream_t st) {
+  (void)kmax;
+  if (n <= 0 || tiles <= 0) return;
+  set_max_smem((const void*)k_ritz_tc);
+  const int np = (kkmax + 15) & ~15;
+  k_ritz_tc<<<tiles, RTC_NT, ritz_tc_smem(kkmax), st>>>(items, pre, n, final_pass, np); count_launch();
+}
+
+int ritz_tc_timeouts(cudaStream_t st) {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_ritz_tc_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbolAsync(g_ritz_tc_timeouts, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  return h;
+}
+
+}  // namespace ssa

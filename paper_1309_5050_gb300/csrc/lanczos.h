@@ -127,8 +127,10 @@ constexpr int RITZ_RB() { return sizeof(E) == 8 ? 64 : 256; }   // rows per Ritz
 template <typename E>
 constexpr int RITZ_CW() { return sizeof(E) == 8 ? 4 : 8; }      // columns per thread tile
 constexpr int RITZ_RB_SHORT = RITZ_RB<double>();
+// FP32 long side: the tensor-core kernel (k_ritz_tc.cu) takes 128-row tiles
+constexpr int RITZ_TC_M = 128;
 template <typename T>
-constexpr int ritz_rb_long() { return RITZ_RB<T>(); }
+constexpr int ritz_rb_long() { return sizeof(T) == 4 ? RITZ_TC_M : RITZ_RB<T>(); }
 void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
 // Problems whose short side has at most SHORT_FUSED_MAX rows: the whole
 // short-side step in one block per problem (items: only those problems).
@@ -140,9 +142,18 @@ template <typename T>
 void launch_long_init(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, cudaStream_t st);
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st);
 void launch_restart(const SvdItem* items, int n, cudaStream_t st);
+// kmax / kkmax: largest Krylov dimension and largest number of kept columns
+// (restart: kk; final pass: r) among the items
 template <typename T>
-void launch_ritz(const RitzItem<T>* items, int n, int kmax, const int32_t* pre_s, int tiles_s, const int32_t* pre_l,
-                 int tiles_l, int final_pass, cudaStream_t st);
+void launch_ritz(const RitzItem<T>* items, int n, int kmax, int kkmax, const int32_t* pre_s, int tiles_s,
+                 const int32_t* pre_l, int tiles_l, int final_pass, cudaStream_t st);
+// FP32 long side on the tensor cores (k_ritz_tc.cu): 128-row tiles, tcgen05.mma
+// kind::tf32 with each operand split into two TF32 parts
+void launch_ritz_tc(const RitzItem<float>* items, int n, int kmax, int kkmax, const int32_t* pre, int tiles,
+                    int final_pass, cudaStream_t st);
+// bounded MMA-barrier waits of k_ritz_tc that gave up since the last call
+// (read and reset; synchronises the stream; -1 on a CUDA error)
+int ritz_tc_timeouts(cudaStream_t st);
 template <typename T>
 void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st);
 

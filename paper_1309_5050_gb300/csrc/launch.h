@@ -58,15 +58,17 @@ inline int ypass_blocks(int log2Mx, int tk) { return ((1 << (log2Mx - 1)) + 1 + 
 
 // 2D products: tiles of the x-pass forward (y_in_hi blocks per item), the
 // y-pass (ypass_blocks) and the x-pass inverse (y_out_hi blocks).
+// max_tk: the largest tile width (x-frequencies per block) among the y-pass
+// items, which sizes the launch's staging buffers
 template <typename T>
 void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, Tiles xf, Tiles yp, Tiles xi,
-                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st);
+                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st, int max_tk);
 template <typename T>
 void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int s, const Cx<T>* tw,
-                  cudaStream_t st);
+                  cudaStream_t st, int max_tk);
 // spectra: sx gives ny blocks per item, sy ypass_blocks per 2D item
 template <typename T>
 void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Tiles sy, int max_log2Mx,
-                 int max_log2My, const Cx<T>* tw, cudaStream_t st);
+                 int max_log2My, const Cx<T>* tw, cudaStream_t st, int max_tk);
 
 }  // namespace ssa

@@ -193,6 +193,24 @@ def test_vectors_satisfy_svd_relations():
         assert U[k, i] > 0
 
 
+def test_fp32_vectors_satisfy_svd_relations():
+    """FP32 form: the long-side Ritz vectors come from the tensor-core
+    contraction (3xTF32 split, FP32 accumulation in TMEM) at every restart and
+    at the end; they stay orthonormal to FP32 level and satisfy
+    X V_i = sigma_i U_i to the form's accuracy on an MSSA problem that
+    restarts several times."""
+    s, P, _ = case_mssa([300, 701, 455, 512, 333], 100, 6)
+    s.decompose(12, "fp32", krylov_dim=30)
+    assert s.info()["restarts"] >= 2
+    sig = s.sigma()
+    U, V = s.vectors()
+    np.testing.assert_allclose(V.T @ V, np.eye(12), atol=2e-5)
+    for i in range(12):
+        np.testing.assert_allclose(O.matvec(P, V[:, i]), sig[i] * U[:, i], atol=2e-5 * sig[0])
+    so = O.decompose(P, 12)[0]
+    np.testing.assert_allclose(sig, so, rtol=TOL_SIG["fp32"], atol=0)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_small_svd_fp32_rotations_fp64_polish(prec):
     """The small SVD finds its rotations in FP32 and polishes them in a few
