@@ -364,6 +364,7 @@ struct Workspace {             // Lanczos + results, per precision
   int nblk_s = 0, nblk_l = 0;
   LzState* st = nullptr;
   double* U = nullptr; void* V = nullptr;
+  float2* Uf = nullptr;        // FP32 form: float-float copy of U for the short side
   double* p = nullptr; void* q = nullptr;
   void* parts_s = nullptr; void* parts_l = nullptr;
   int n_part_s = 1, n_part_l = 1;
@@ -962,7 +963,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
                   3 * rnd256(8 * k1 * k1) + 2 * rnd256(8 * (k1 + 1)) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
                   rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)std::max<int64_t>(w.nblk_l, (int64_t)c->ch.size())) + rnd256(cz * c->L * w.r) +
                   rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r) + rnd256(cz * (k1 + 1) * ritz_ldcs(w.k)) +
-                  rnd256(2 * cz * uz_bound(c));
+                  rnd256(2 * cz * uz_bound(c)) + (std::is_same<T, float>::value ? rnd256(8 * (size_t)((w.Ls + 1) & ~int64_t(1)) * k1) : 0);
     if (c->log2My > 0) {
       const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
       need += 2 * rnd256(2 * cz * hs * c->ch.size());
@@ -973,6 +974,8 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   c->cur = &c->ws_arena;
   TRY(c->allocT(&w.st, 1));
   TRY(c->allocT(&w.U, (size_t)w.Ls * k1));
+  w.Uf = nullptr;
+  if (std::is_same<T, float>::value) TRY(c->allocT(&w.Uf, (size_t)((w.Ls + 1) & ~int64_t(1)) * k1));
   TRY(c->alloc(&w.V, sizeof(T) * (size_t)w.Kl * k1));
   TRY(c->allocT(&w.p, (size_t)w.Ls));
   TRY(c->alloc(&w.q, sizeof(T) * (size_t)w.Kl));
@@ -1116,7 +1119,7 @@ struct LzEngine {
     Workspace& w = c->ws;
     ShortItem s;
     s.seed = sd;
-    s.st = w.st; s.U = w.U; s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
+    s.st = w.st; s.U = w.U; s.Uf = w.Uf; s.ldf = (w.Ls + 1) & ~int64_t(1); s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
     s.parts_double = std::is_same<T, double>::value; s.p = w.p; s.B = w.B; s.ldb = w.k; s.nblk = w.nblk_s;
     s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
     return s;
@@ -1164,6 +1167,26 @@ struct LzEngine {
     add(c, 0);
     fresh.back() = false;
     hst.back().jc = jc;
+    if (std::is_same<T, float>::value) uf_pending.push_back({c, jc});
+  }
+  // Uf[:, 0:n] <- U[:, 0:n] of the given members (their float-float copy
+  // after U was written in FP64)
+  std::vector<std::pair<ssa_ctx*, int>> uf_pending;
+  int sync_uf(const std::vector<std::pair<ssa_ctx*, int>>& ms) {
+    std::vector<ShortItem> it;
+    std::vector<int32_t> nc;
+    for (auto& m : ms)
+      if (m.second > 0) { it.push_back(short_item(m.first, 0)); nc.push_back(m.second); }
+    if (it.empty()) return SSA_OK;
+    ShortItem* d_i = nullptr;
+    int32_t* d_n = nullptr;
+    const size_t keep = dev_tmp.size();
+    TRY(up(it, &d_i));
+    TRY(up(nc, &d_n));
+    chunk_tmp.insert(chunk_tmp.end(), dev_tmp.begin() + keep, dev_tmp.end());
+    dev_tmp.resize(keep);
+    launch_uf_sync(d_i, d_n, (int)it.size(), st);
+    return SSA_OK;
   }
 
   // rebuild the device item arrays for the current members (when they changed)
@@ -1230,6 +1253,10 @@ struct LzEngine {
       max_log2My = std::max(max_log2My, c->log2My);
     }
     if (live.empty()) return SSA_OK;
+    if (!uf_pending.empty()) {
+      TRY(sync_uf(uf_pending));
+      uf_pending.clear();
+    }
     TRY(up(sh, &d_sh)); TRY(up(lg, &d_lg)); TRY(up(sv, &d_sv)); TRY(up(rz, &d_rz)); TRY(up(stp, &d_stp));
     TRY(tiles(live, [this](ssa_ctx* c) { return fused_short(c) ? 0 : c->ws.nblk_s; }, &t_sh, &n_sh));
     {
@@ -1322,8 +1349,13 @@ struct LzEngine {
     run_mv<T>(device, mvA, 0, st);
     {
       PhaseScope ps_(PH_SHORT, st);
-      launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st);
-      launch_short_fused(d_shf, n_shf, max_ls_f, 0, st);
+      if (std::is_same<T, float>::value) {
+        launch_short_steps_ff(d_sh, t_sh, nl, n_sh, 0, st);
+        launch_short_fused_ff(d_shf, n_shf, max_ls_f, 0, st);
+      } else {
+        launch_short_steps(d_sh, t_sh, nl, n_sh, 0, st);
+        launch_short_fused(d_shf, n_shf, max_ls_f, 0, st);
+      }
     }
     {
       PhaseScope ps_(PH_MATVEC, st);
@@ -1349,6 +1381,8 @@ struct LzEngine {
       return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
     if (std::is_same<T, float>::value && ritz_tc_timeouts(st) != 0)
       return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
+    if (std::is_same<T, float>::value && n_shf && short_tma_timeouts(st) != 0)
+      return fail(SSA_ETIMEOUT, "a bulk copy of the short-side basis did not complete");
     return SSA_OK;
   }
   // One chunk: every member inside a cycle advances up to `steps` Lanczos
@@ -1403,6 +1437,12 @@ struct LzEngine {
     PhaseScope ps_(PH_RITZ, st);
     launch_ritz<T>(d_r, (int)cs.size(), mk, mkk, ts, ns, tl, nlg, 0, st);
     launch_restart(d_v, (int)cs.size(), st);
+    if (std::is_same<T, float>::value) {
+      // the kept columns U[:, 0:kk] were rewritten in FP64: refresh their float-float copy
+      std::vector<std::pair<ssa_ctx*, int>> sy;
+      for (ssa_ctx* c : cs) sy.push_back({c, c->ws.kk});
+      TRY(sync_uf(sy));
+    }
     CU(cudaGetLastError());
     for (auto& h : hst)
       if (h.active && h.svd_done) { h.jc = h.kk; h.svd_done = 0; }
@@ -2670,23 +2710,29 @@ int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, 
 }
 
 // ---------------------------------------------------------------- autotuner
-// Times one decomposition of ctx (with its own Krylov dimension kd) on the
-// context's stream: the span between two events, host round trips included.
-static int tune_run(ssa_ctx* ctx, const ssa_params& p0, int kd, double* ms) {
+// Times decompositions of ctx (with its own Krylov dimension kd) on the
+// context's stream: the span between two events, host round trips included;
+// the faster of `reps` runs.
+static int tune_run(ssa_ctx* ctx, const ssa_params& p0, int kd, double* ms, int reps = 2) {
   ssa_params p = p0;
   p.krylov_dim = kd;
   cudaEvent_t a = nullptr, b = nullptr;
   CU(cudaEventCreate(&a));
   CU(cudaEventCreate(&b));
-  CU(cudaEventRecord(a, ctx->stream));
-  const int rc = ssa_decompose(ctx, &p);
-  cudaEventRecord(b, ctx->stream);
-  cudaEventSynchronize(b);
-  float f = 0.0f;
-  cudaEventElapsedTime(&f, a, b);
+  int rc = SSA_OK;
+  double best = 1e300;
+  for (int i = 0; i < reps && rc == SSA_OK; ++i) {
+    cudaEventRecord(a, ctx->stream);
+    rc = ssa_decompose(ctx, &p);
+    cudaEventRecord(b, ctx->stream);
+    cudaEventSynchronize(b);
+    float f = 0.0f;
+    cudaEventElapsedTime(&f, a, b);
+    best = std::min(best, (double)f);
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  *ms = f;
+  *ms = best;
   return rc;
 }
 
@@ -2714,7 +2760,7 @@ int ssa_autotune(ssa_ctx* ctx, const ssa_params* params, ssa_tune_result* out) {
   }
   double ms = 0.0, ms_default = 0.0, best_ms = 1e300;
   int best_k = d, tried = 0;
-  TRY(tune_run(ctx, *params, d, &ms));              // warm-up: spectra, workspaces
+  TRY(tune_run(ctx, *params, d, &ms, 1));           // warm-up: spectra, workspaces
   for (int kc : ks) {
     const int rc = tune_run(ctx, *params, kc, &ms);
     ++tried;
@@ -2747,7 +2793,7 @@ int ssa_autotune(ssa_ctx* ctx, const ssa_params* params, ssa_tune_result* out) {
     if (ctx->log2My > 0) g_plans.ytk[tkey] = best_tk;
   }
   // leave the context decomposed with the chosen plan
-  TRY(tune_run(ctx, *params, 0, &ms));
+  TRY(tune_run(ctx, *params, 0, &ms, 1));
   if (out) {
     out->krylov_dim = best_k;
     out->ytk = ctx->log2My > 0 ? best_tk : 0;

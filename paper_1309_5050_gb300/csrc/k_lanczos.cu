@@ -9,6 +9,7 @@
 #include "lanczos.h"
 #include "launch.h"
 #include "tma.cuh"
+#include "ff.cuh"
 
 namespace ssa {
 
@@ -327,6 +328,533 @@ void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cu
   if (n <= 0) return;
   set_max_smem((const void*)k_short_fused);
   k_short_fused<<<n, SHORT_FUSED_NT, sizeof(double) * (size_t)max_ls, st>>>(items, s); count_launch();
+}
+
+// ------------------------------------------------------------ short side, float-float
+// The FP32 form's short side: the steps above in float-float arithmetic
+// (ff.cuh) on Uf, U's (hi, lo) copy.  GB300's FP64 pipe issues about 1.7
+// FMAs per clock per SM against about 118 FP32 FMAs, and the FP64 short side
+// ran its FP64 pipe at 77% of peak; a float-float product-sum is about a
+// dozen FP32 instructions.  The coefficients of the Gram-Schmidt passes carry
+// about 48 bits, so U stays orthogonal to about n 2^-48 (n = Ls) -- far below
+// the FP32 products' own error, which bounds what the FP32 form resolves.
+
+template <int NT>
+__device__ __forceinline__ ff block_sum_ffv(ffacc v, float2* red) {
+  v = warp_sum_ff(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = make_float2(v.s, v.c);
+  __syncthreads();
+  ffacc t;
+  for (int i = 0; i < NT / 32; ++i) { ffacc o; o.s = red[i].x; o.c = red[i].y; t.add(o); }   // fixed order
+  return t.value();
+}
+
+// c[i] = U[:, i]^T p over rows [0, nrows) of U (from row r0) and p, i < j; a warp per column
+template <int NT>
+__device__ __forceinline__ void dots_ff(const float2* __restrict__ U, int64_t ldu, int64_t r0, const float2* p,
+                                        int nrows, int j, float2* c) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < j; i += NT / 32) {
+    const float2* __restrict__ col = U + ldu * i + r0;
+    ffacc a0, a1;                   // two chains: the TwoSum of one is a dependent sequence
+    int t = lane;
+    // eight loads issued before their arithmetic: U streams from L2 / HBM,
+    // and one block per problem has few warps to hide that latency with
+    for (; t + 7 * 32 < nrows; t += 8 * 32) {
+      float2 u[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) u[m] = col[t + 32 * m];
+#pragma unroll
+      for (int m = 0; m < 8; m += 2) { a0.fma(u[m], p[t + 32 * m]); a1.fma(u[m + 1], p[t + 32 * (m + 1)]); }
+    }
+    for (; t < nrows; t += 32) a0.fma(col[t], p[t]);
+    a0.add(a1);
+    const ff v = warp_sum_ff(a0).value();
+    if (lane == 0) c[i] = make_float2(v.hi, v.lo);
+  }
+}
+
+// p[row] -= (U c)[row] for this thread's rows of [0, Ls); returns the
+// thread's share of ||p||^2
+__device__ __forceinline__ ff update_row_ff(const float2* __restrict__ Ur, int64_t ldu, int j, const float2* c) {
+  ffacc s0, s1;
+  int i = 0;
+  for (; i + 7 < j; i += 8) {         // eight loads in flight (see dots_ff)
+    float2 u[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) u[m] = Ur[ldu * (i + m)];
+#pragma unroll
+    for (int m = 0; m < 8; m += 2) { s0.fma(u[m], c[i + m]); s1.fma(u[m + 1], c[i + m + 1]); }
+  }
+  for (; i < j; ++i) s0.fma(Ur[ldu * i], c[i]);
+  s0.add(s1);
+  return s0.value();
+}
+
+__device__ __forceinline__ ffacc update_ff(const float2* __restrict__ U, int64_t ldu, float2* p, int Ls, int j,
+                                           const float2* c) {
+  ffacc nn;
+  for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
+    const ff sv = update_row_ff(U + row, ldu, j, c);
+    const float2 pr = p[row];
+    const ff v = ff_add(ff{pr.x, pr.y}, ff_neg(sv));
+    p[row] = make_float2(v.hi, v.lo);
+    nn.fma(v.hi, v.lo, v.hi, v.lo);
+  }
+  return nn;
+}
+
+// After a breakdown at step j: p <- a seeded random vector (FP32 values of the
+// FP64 form's sequence), orthogonalised twice against U[:, 0:j]; returns ||p||^2.
+template <int NT>
+__device__ ff short_random_ff(const ShortItem& it, float2* p, int Ls, int j, float2* c, float2* red) {
+  const uint64_t sd = breakdown_seed(it.seed, 0, j);
+  for (int row = threadIdx.x; row < Ls; row += blockDim.x)
+    p[row] = make_float2((float)hash_uniform(sd, (uint64_t)row), 0.0f);
+  __syncthreads();
+  ff nn{0.0f, 0.0f};
+  for (int pass = 0; pass < 2; ++pass) {
+    dots_ff<NT>(it.Uf, it.ldf, 0, p, Ls, j, c);
+    __syncthreads();
+    nn = block_sum_ffv<NT>(update_ff(it.Uf, it.ldf, p, Ls, j, c), red);
+  }
+  return nn;
+}
+
+// u_j = p / alpha into Uf and U (thread's rows of [r0, r0 + nrows))
+// (and the zero pad row of Uf past Ls, from the block that owns row Ls - 1)
+__device__ __forceinline__ void write_u_ff(const ShortItem& it, const float2* p, int64_t r0, int nrows, int j,
+                                           float2 inv) {
+  for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
+    const float2 pr = p[t];
+    const ff u = ff_mul(ff{pr.x, pr.y}, ff{inv.x, inv.y});
+    it.Uf[r0 + t + it.ldf * j] = make_float2(u.hi, u.lo);
+    it.U[r0 + t + it.ldu * j] = ff_to_double(make_float2(u.hi, u.lo));
+  }
+  if (threadIdx.x == 0 && r0 + nrows == it.Ls && it.ldf > it.Ls) it.Uf[it.Ls + it.ldf * j] = make_float2(0.0f, 0.0f);
+}
+
+// sum of the FP32 channel partial products at one row (FP32 form: they carry
+// FP32 error already)
+__device__ __forceinline__ float parts_row(const ShortItem& it, int64_t row) {
+  const float* pp = (const float*)it.parts + row;
+  float a0 = 0.0f, a1 = 0.0f;
+  int q = 0;
+  for (; q + 1 < it.n_part; q += 2) { a0 += pp[q * it.part_ld]; a1 += pp[(q + 1) * it.part_ld]; }
+  if (q < it.n_part) a0 += pp[q * it.part_ld];
+  return a0 + a1;
+}
+
+// alpha = sqrt(nn), the breakdown decision and 1 / alpha as float-float;
+// one thread
+__device__ __forceinline__ void alpha_ff(ff nn, double level, double& alpha, int& ok, float2& inv) {
+  alpha = sqrt(fmax(ff_to_double(make_float2(nn.hi, nn.lo)), 0.0));
+  ok = alpha > level;
+  inv = ff_from_double(alpha > 0.0 ? 1.0 / alpha : 0.0);
+}
+
+// Whole step of one problem in one block, U streamed through shared memory:
+// each Gram-Schmidt pass (U^T p, or p -= U c) reads the columns of Uf in
+// chunks of CW columns that bulk copies (cp.async.bulk, the TMA engine)
+// bring into SHORT_TMA_S rotating stage buffers, completing on one mbarrier
+// per stage, while the warps work on the previous chunk.  A dot product pass
+// gives each column 16 / CW warps (partial sums, reduced in fixed order at the
+// end of the pass); an update pass keeps each thread's rows' running sums in
+// registers across the chunks.
+constexpr int SHORT_TMA_NT = 512;
+constexpr int MBAR_POLL_LIMIT_SHORT = 1 << 22;
+constexpr int SHORT_TMA_S = 3;
+constexpr int SHORT_TMA_RPP = SHORT_FUSED_MAX / (2 * SHORT_TMA_NT);   // row pairs per thread, at most
+__device__ int g_short_tma_timeouts;
+
+struct ShortStream {
+  float2* stage;      // stage s, column ci of its chunk at stage + (s * cw + ci) * sld
+  int64_t sld;        // column stride of the stage buffers (the launch's largest ldf)
+  uint64_t* bar;      // one mbarrier per stage
+  int cw;             // columns per chunk
+  uint32_t g;         // chunks consumed so far, over all passes: chunk g used stage
+                      // g % S in its (g / S)-th phase
+};
+
+// chunk q of a pass (columns [q cw, min(j, q cw + cw)) of Uf) into stage
+// (g0 + q) % S; one thread
+__device__ __forceinline__ void short_issue(const ShortItem& it, const ShortStream& ss, uint32_t g0, int q, int j) {
+  const int s = (int)((g0 + q) % SHORT_TMA_S);
+  const int c0 = q * ss.cw, cn = min(ss.cw, j - c0);
+  const uint32_t bytes = (uint32_t)(sizeof(float2) * it.ldf);
+  // the stage was last read by generic loads: order them before the async writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect(&ss.bar[s], bytes * (uint32_t)cn);
+  for (int ci = 0; ci < cn; ++ci)
+    bulk_copy(ss.stage + ((int64_t)s * ss.cw + ci) * ss.sld, it.Uf + it.ldf * (c0 + ci), bytes, &ss.bar[s]);
+}
+
+// One pass over columns [0, j) in one of four forms:
+//   SP_DOT_FF / SP_DOT_32: part[i * wpc + slot] = partial sums of U[:, i]^T p
+//     (float-float, or FP32 from the hi parts);
+//   SP_UPD_FF / SP_UPD_32: acc += (U c) for the thread's row pairs
+//     (2 (threadIdx.x + m NT), + 1), m < RPP.
+// Rows go in pairs (one 16-byte load of two float-float values); an odd Ls
+// has a zero pad row in p and in every column of Uf.  Ends with the block
+// synchronised.
+enum ShortPass { SP_DOT_FF, SP_DOT_32, SP_UPD_FF, SP_UPD_32 };
+
+template <int MODE, int RPP>
+__device__ __forceinline__ void short_pass(const ShortItem& it, ShortStream& ss, int j, int Ls, const float2* p,
+                                           const float2* c, float2* part, ffacc (&acc)[2 * RPP],
+                                           float (&acc32)[2 * RPP]) {
+  constexpr bool DOTS = MODE == SP_DOT_FF || MODE == SP_DOT_32;
+  const int nch = (j + ss.cw - 1) / ss.cw;
+  if (nch == 0) return;
+  const uint32_t g0 = ss.g;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < min(SHORT_TMA_S, nch); ++q) short_issue(it, ss, g0, q, j);
+  const int wpc = (SHORT_TMA_NT / 32) / ss.cw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int np2 = (Ls + 1) >> 1;
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  for (int q = 0; q < nch; ++q) {
+    const uint32_t gq = g0 + q;
+    const int s = (int)(gq % SHORT_TMA_S);
+    if (!mbar_wait_bounded(&ss.bar[s], (gq / SHORT_TMA_S) & 1u, MBAR_POLL_LIMIT_SHORT) && threadIdx.x == 0)
+      atomicAdd(&g_short_tma_timeouts, 1);
+    const float2* buf = ss.stage + (int64_t)s * ss.cw * ss.sld;
+    const int c0 = q * ss.cw, cn = min(ss.cw, j - c0);
+    if (DOTS) {
+      const int ci = warp / wpc, slot = warp - ci * wpc;
+      if (ci < cn) {
+        const float4* col = reinterpret_cast<const float4*>(buf + ci * ss.sld);
+        float2 v;
+        if (MODE == SP_DOT_FF) {
+          ffacc a0, a1;
+          for (int t = slot * 32 + lane; t < np2; t += 32 * wpc) {
+            const float4 u = col[t], w = p4[t];
+            a0.fma(u.x, u.y, w.x, w.y);
+            a1.fma(u.z, u.w, w.z, w.w);
+          }
+          a0.add(a1);
+          a0 = warp_sum_ff(a0);
+          v = make_float2(a0.s, a0.c);
+        } else {
+          float a0 = 0.0f, a1 = 0.0f;
+          for (int t = slot * 32 + lane; t < np2; t += 32 * wpc) {
+            const float4 u = col[t], w = p4[t];
+            a0 = fmaf(u.x, w.x, a0);
+            a1 = fmaf(u.z, w.z, a1);
+          }
+          a0 += a1;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+          v = make_float2(a0, 0.0f);
+        }
+        if (lane == 0) part[(c0 + ci) * wpc + slot] = v;
+      }
+    } else {
+      for (int ci = 0; ci < cn; ++ci) {
+        const float2 cc = c[c0 + ci];
+        const float4* col = reinterpret_cast<const float4*>(buf + ci * ss.sld);
+#pragma unroll
+        for (int m = 0; m < RPP; ++m) {
+          const int t = threadIdx.x + m * SHORT_TMA_NT;
+          if (t < np2) {
+            const float4 u = col[t];
+            if (MODE == SP_UPD_FF) {
+              acc[2 * m].fma(u.x, u.y, cc.x, cc.y);
+              acc[2 * m + 1].fma(u.z, u.w, cc.x, cc.y);
+            } else {
+              acc32[2 * m] = fmaf(u.x, cc.x, acc32[2 * m]);
+              acc32[2 * m + 1] = fmaf(u.z, cc.x, acc32[2 * m + 1]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();                      // every warp is done with stage s
+    if (threadIdx.x == 0 && q + SHORT_TMA_S < nch) short_issue(it, ss, g0, q + SHORT_TMA_S, j);
+  }
+  ss.g = g0 + (uint32_t)nch;
+}
+
+// c[i] = U[:, i]^T p, i < j (FP32: from the hi parts of U and p, as float-float with lo = 0)
+template <int MODE>
+__device__ __forceinline__ void short_dots_tma(const ShortItem& it, ShortStream& ss, int j, int Ls, const float2* p,
+                                               float2* c, float2* part) {
+  ffacc none[2];
+  float none32[2];
+  short_pass<MODE, 1>(it, ss, j, Ls, p, c, part, none, none32);
+  const int wpc = (SHORT_TMA_NT / 32) / ss.cw;
+  for (int i = threadIdx.x; i < j; i += SHORT_TMA_NT) {
+    ffacc a;
+    for (int sl = 0; sl < wpc; ++sl) {    // fixed order
+      const float2 v = part[i * wpc + sl];
+      ffacc o; o.s = v.x; o.c = v.y; a.add(o);
+    }
+    const ff v = a.value();
+    c[i] = MODE == SP_DOT_FF ? make_float2(v.hi, v.lo) : make_float2(v.hi, 0.0f);
+  }
+  __syncthreads();
+}
+
+// p -= U c (float-float, or FP32 from the hi parts: then p stays FP32, lo = 0);
+// returns ||p||^2 (every thread)
+template <int MODE, int RPP>
+__device__ __forceinline__ ff short_update_tma(const ShortItem& it, ShortStream& ss, int j, int Ls, float2* p,
+                                               const float2* c, float2* part, float2* red) {
+  ffacc acc[2 * RPP];
+  float acc32[2 * RPP];
+#pragma unroll
+  for (int m = 0; m < 2 * RPP; ++m) acc32[m] = 0.0f;
+  short_pass<MODE, RPP>(it, ss, j, Ls, p, c, part, acc, acc32);
+  const int np2 = (Ls + 1) >> 1;
+  float4* p4 = reinterpret_cast<float4*>(p);
+  ffacc nn;
+#pragma unroll
+  for (int m = 0; m < RPP; ++m) {
+    const int t = threadIdx.x + m * SHORT_TMA_NT;
+    if (t < np2) {
+      float4 w = p4[t];
+      if (MODE == SP_UPD_FF) {
+        const ff v0 = ff_add(ff{w.x, w.y}, ff_neg(acc[2 * m].value()));
+        const ff v1 = ff_add(ff{w.z, w.w}, ff_neg(acc[2 * m + 1].value()));
+        w = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+      } else {
+        w = make_float4(w.x - acc32[2 * m], 0.0f, w.z - acc32[2 * m + 1], 0.0f);
+      }
+      p4[t] = w;
+      nn.fma(w.x, w.y, w.x, w.y);
+      nn.fma(w.z, w.w, w.z, w.w);
+    }
+  }
+  return block_sum_ffv<SHORT_TMA_NT>(nn, red);   // synchronises the block
+}
+
+// Gram-Schmidt of the step: a first pass in FP32 (U's hi parts; the FP32
+// products carry FP32 error already, so its rounding costs nothing the data
+// resolves), then a float-float pass, whose dot products measure what the
+// first left along U; its update runs unless that is below 1e-12 ||p|| (the
+// criterion of Daniel, Gragg, Kaufman and Stewart).  RPP: row pairs per
+// thread, 2 RPP NT >= every item's Ls.
+template <int RPP>
+__global__ void __launch_bounds__(SHORT_TMA_NT) k_short_fused_ff(const ShortItem* __restrict__ items, int s,
+                                                                 int64_t sld, int cw) {
+  const ShortItem it = items[blockIdx.x];
+  LzState* st = it.st;
+  const int j = st->jc + s;
+  if (j < 0 || lz_skip(st, j)) return;
+  extern __shared__ __align__(16) float2 smf[];
+  __shared__ float2 c[KMAX + 1];
+  __shared__ float2 red[32];
+  __shared__ __align__(8) uint64_t bar[SHORT_TMA_S];
+  __shared__ int second, ok_s;
+  __shared__ double alpha_s;
+  __shared__ float2 inv_s;
+  const int Ls = (int)it.Ls;
+  float2* p = smf;                                            // sld values (a zero pad row when Ls is odd)
+  ShortStream ss;
+  ss.stage = smf + sld;                                       // S cw sld values
+  ss.sld = sld;
+  ss.bar = bar;
+  ss.cw = cw;
+  ss.g = 0;
+  float2* part = smf + sld * (1 + (int64_t)SHORT_TMA_S * cw); // (KMAX + 1) 16 / cw values
+  const double level = short_bd_level(it, st);   // read before thread 0 may raise anorm
+  if (threadIdx.x == 0)
+    for (int q = 0; q < SHORT_TMA_S; ++q) mbar_init(&bar[q]);
+  for (int row = threadIdx.x; row < it.ldf; row += SHORT_TMA_NT)
+    p[row] = make_float2(row < Ls ? parts_row(it, row) : 0.0f, 0.0f);
+  __syncthreads();
+  short_dots_tma<SP_DOT_32>(it, ss, j, Ls, p, c, part);
+  ff nn = short_update_tma<SP_UPD_32, RPP>(it, ss, j, Ls, p, c, part, red);
+  short_dots_tma<SP_DOT_FF>(it, ss, j, Ls, p, c, part);
+  if (threadIdx.x == 0) {
+    float cc = 0.0f;
+    for (int i = 0; i < j; ++i) cc = fmaf(c[i].x, c[i].x, cc);
+    second = cc > 1e-24f * nn.hi;
+  }
+  __syncthreads();
+  if (second) nn = short_update_tma<SP_UPD_FF, RPP>(it, ss, j, Ls, p, c, part, red);
+  if (threadIdx.x == 0) { double a; int o; float2 iv; alpha_ff(nn, level, a, o, iv); alpha_s = a; ok_s = o; inv_s = iv; }
+  __syncthreads();
+  if (!ok_s) {
+    // breakdown: a seeded random vector, orthogonalised twice in float-float
+    const uint64_t sd = breakdown_seed(it.seed, 0, j);
+    for (int row = threadIdx.x; row < Ls; row += SHORT_TMA_NT)
+      p[row] = make_float2((float)hash_uniform(sd, (uint64_t)row), 0.0f);
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      short_dots_tma<SP_DOT_FF>(it, ss, j, Ls, p, c, part);
+      nn = short_update_tma<SP_UPD_FF, RPP>(it, ss, j, Ls, p, c, part, red);
+    }
+    if (threadIdx.x == 0) { double a; int o; float2 iv; alpha_ff(nn, 0.0, a, o, iv); inv_s = iv; }
+    __syncthreads();
+  }
+  write_u_ff(it, p, 0, Ls, j, inv_s);
+  if (threadIdx.x == 0) short_coef(it, st, j, ok_s != 0, alpha_s);
+}
+
+// shared memory of k_short_fused_ff for stage column stride sld and cw columns per chunk
+static size_t short_tma_smem(int64_t sld, int cw) {
+  return sizeof(float2) * ((size_t)sld * (1 + SHORT_TMA_S * (size_t)cw) + (size_t)(KMAX + 1) * (16 / cw));
+}
+
+int short_tma_timeouts(cudaStream_t st) {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_short_tma_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbolAsync(g_short_tma_timeouts, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  return h;
+}
+
+// Row-block form (problems with more rows than one block should carry, or
+// too few problems to fill the SMs).  p: the item's work vector as Ls
+// float-float values; cpa / cpb: nblk x (KMAX+1) float-float partial dots;
+// npart: nblk float-float partial squared norms.
+__global__ void __launch_bounds__(SHORT_RB) k_short1_ff(const ShortItem* __restrict__ items,
+                                                        const int32_t* __restrict__ tpre, int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
+  const int j = it.st->jc + s;
+  if (j < 0 || lz_skip(it.st, j)) return;
+  __shared__ float2 pv[SHORT_RB];
+  const int64_t r0 = (int64_t)blk * SHORT_RB;
+  const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
+  float2 v = make_float2(0.0f, 0.0f);
+  if ((int)threadIdx.x < nrows) {
+    v.x = parts_row(it, r0 + threadIdx.x);
+    reinterpret_cast<float2*>(it.p)[r0 + threadIdx.x] = v;
+  }
+  pv[threadIdx.x] = v;
+  __syncthreads();
+  dots_ff<SHORT_RB>(it.Uf, it.ldf, r0, pv, nrows, j, reinterpret_cast<float2*>(it.cpa) + (int64_t)blk * (KMAX + 1));
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(SHORT_RB) k_short23_ff(const ShortItem* __restrict__ items,
+                                                         const int32_t* __restrict__ tpre, int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
+  const int j = it.st->jc + s;
+  if (j < 0 || lz_skip(it.st, j)) return;
+  __shared__ float2 c[KMAX + 1];
+  __shared__ float2 pv[SHORT_RB];
+  __shared__ float2 red[32];
+  const float2* src = reinterpret_cast<const float2*>(PASS == 2 ? it.cpa : it.cpb);
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    ffacc a;
+    for (int b = 0; b < it.nblk; ++b) {       // fixed order
+      const float2 q = src[(int64_t)b * (KMAX + 1) + i];
+      ffacc o; o.s = q.x; o.c = q.y; a.add(o);
+    }
+    const ff v = a.value();
+    c[i] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
+  const int64_t r0 = (int64_t)blk * SHORT_RB;
+  const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
+  float2* p = reinterpret_cast<float2*>(it.p) + r0;
+  ffacc nn;
+  float2 val = make_float2(0.0f, 0.0f);
+  if ((int)threadIdx.x < nrows) {
+    const int row = threadIdx.x;
+    const ff sv = update_row_ff(it.Uf + r0 + row, it.ldf, j, c);
+    const ff v = ff_add(ff{p[row].x, p[row].y}, ff_neg(sv));
+    val = make_float2(v.hi, v.lo);
+    p[row] = val;
+    nn.fma(v.hi, v.lo, v.hi, v.lo);
+  }
+  if (PASS == 2) {
+    pv[threadIdx.x] = val;
+    __syncthreads();
+    dots_ff<SHORT_RB>(it.Uf, it.ldf, r0, pv, nrows, j, reinterpret_cast<float2*>(it.cpb) + (int64_t)blk * (KMAX + 1));
+  } else {
+    const ff tot = block_sum_ffv<SHORT_RB>(nn, red);
+    if (threadIdx.x == 0) reinterpret_cast<float2*>(it.npart)[blk] = make_float2(tot.hi, tot.lo);
+  }
+}
+
+__global__ void __launch_bounds__(SHORT_RB) k_short4_ff(const ShortItem* __restrict__ items,
+                                                        const int32_t* __restrict__ tpre, int n, int s) {
+  int blk;
+  const ShortItem it = items[tile_item(tpre, n, blockIdx.x, blk)];
+  LzState* st = it.st;
+  const int j = st->jc + s;
+  if (j < 0 || lz_skip(st, j)) return;
+  __shared__ double alpha_s;
+  __shared__ int ok_s;
+  __shared__ float2 inv_s;
+  if (threadIdx.x == 0) {
+    ffacc a;
+    for (int b = 0; b < it.nblk; ++b) {
+      const float2 q = reinterpret_cast<const float2*>(it.npart)[b];
+      ffacc o; o.s = q.x; o.c = q.y; a.add(o);
+    }
+    // every block of the problem takes this decision: anorm only grows, to
+    // alpha_j, when alpha_j passes, so a block reading it late agrees
+    double al; int ok; float2 iv;
+    alpha_ff(a.value(), short_bd_level(it, st), al, ok, iv);
+    alpha_s = al; ok_s = ok; inv_s = iv;
+  }
+  __syncthreads();
+  float2* p = reinterpret_cast<float2*>(it.p);
+  if (ok_s) {
+    const int64_t r0 = (int64_t)blk * SHORT_RB;
+    const int nrows = (int)imin64(SHORT_RB, it.Ls - r0);
+    write_u_ff(it, p + r0, r0, nrows, j, inv_s);
+    if (blk == 0 && threadIdx.x == 0) short_coef(it, st, j, true, alpha_s);
+    return;
+  }
+  // breakdown (rare): block 0 alone builds the whole replacement vector
+  if (blk != 0) return;
+  __shared__ float2 c[KMAX + 1];
+  __shared__ float2 red[32];
+  const ff nn = short_random_ff<SHORT_RB>(it, p, (int)it.Ls, j, c, red);
+  __syncthreads();
+  if (threadIdx.x == 0) { double a; int o; float2 iv; alpha_ff(nn, 0.0, a, o, iv); inv_s = iv; }
+  __syncthreads();
+  write_u_ff(it, p, 0, (int)it.Ls, j, inv_s);
+  if (threadIdx.x == 0) short_coef(it, st, j, false, 0.0);
+}
+
+__global__ void __launch_bounds__(256) k_uf_sync(const ShortItem* __restrict__ items, const int32_t* __restrict__ ncols) {
+  const ShortItem it = items[blockIdx.y];
+  const int64_t n = it.ldf * (int64_t)ncols[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / it.ldf, row = e - c * it.ldf;
+    it.Uf[row + it.ldf * c] = row < it.Ls ? ff_from_double(it.U[row + it.ldu * c]) : make_float2(0.0f, 0.0f);
+  }
+}
+
+void launch_short_fused_ff(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t sld = (max_ls + 1) & ~int64_t(1);
+  // chunks of about 32 KB: cw = the largest power of two <= 32 KB / column, in [1, 16]
+  int cw = 1;
+  while (cw < 16 && (int64_t)sizeof(float2) * sld * (2 * cw) <= 32768) cw *= 2;
+  const size_t sm = short_tma_smem(sld, cw);
+  auto go = [&](auto kern) {
+    set_max_smem((const void*)kern);
+    kern<<<n, SHORT_TMA_NT, sm, st>>>(items, s, sld, cw);
+    count_launch();
+  };
+  if (max_ls <= 2 * SHORT_TMA_NT) go(k_short_fused_ff<1>);
+  else if (max_ls <= 4 * SHORT_TMA_NT) go(k_short_fused_ff<2>);
+  else go(k_short_fused_ff<SHORT_TMA_RPP>);
+}
+
+void launch_short_steps_ff(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st) {
+  if (n <= 0 || tiles <= 0) return;
+  k_short1_ff<<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+  k_short23_ff<2><<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+  k_short23_ff<3><<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+  k_short4_ff<<<tiles, SHORT_RB, 0, st>>>(items, tpre, n, s); count_launch();
+}
+
+void launch_uf_sync(const ShortItem* items, const int32_t* ncols, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_uf_sync<<<dim3(16, n), 256, 0, st>>>(items, ncols); count_launch();
 }
 
 // ------------------------------------------------------------ long side

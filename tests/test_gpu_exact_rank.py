@@ -107,10 +107,11 @@ def test_exact_rank_triples(name, make, r, prec):
     assert s.info()["converged"] == 1
     U, V = s.vectors()
     Ur, Vr = U[:, :rank], V[:, :rank]
-    # U is an FP64 basis in both forms, but the FP32 form's small SVD stops
-    # at cosines of 1e-10 (its products carry 1e-7 error); V is stored in
-    # FP32 in that form
-    tol_u = 1e-8 if prec == "fp32" else 1e-10
+    # The FP32 form returns its vectors in FP32: rounding each entry of unit
+    # vectors moves an entry of U^T U by at most 2 * 2^-24 (Cauchy-Schwarz),
+    # on top of the 1e-10 cosines its small SVD stops at.  V (the long side,
+    # not re-orthogonalised) is stored in FP32 in that form.
+    tol_u = 2.0 ** -23 + 1e-9 if prec == "fp32" else 1e-10
     tol_o = 1e-4 if prec == "fp32" else 1e-10
     np.testing.assert_allclose(Ur.T @ Ur, np.eye(rank), atol=tol_u)
     np.testing.assert_allclose(Vr.T @ Vr, np.eye(rank), atol=tol_o)
