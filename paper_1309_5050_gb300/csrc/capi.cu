@@ -198,11 +198,13 @@ static int plan_kdim(int prec, int kind, int64_t L, int64_t K, int r) {
   auto it = g_plans.kdim.find(kdim_key(prec, kind, L, K, r));
   return it == g_plans.kdim.end() ? 0 : it->second;
 }
-// y-pass tile of a grid: the tuned one, else the default from the buffer budget
+// y-pass tile of a grid: the tuned one, else the default from the buffer
+// budget.  Keyed by the size of the complex element (8 for the FP32 form's
+// transforms, 16 for FP64), as ssa_autotune records it.
 template <typename T>
 static int tuned_ytk(int log2Mx, int log2My) {
   std::lock_guard<std::mutex> lk(g_plans.mu);
-  auto it = g_plans.ytk.find(ytk_key((int)sizeof(T), log2Mx, log2My));
+  auto it = g_plans.ytk.find(ytk_key((int)sizeof(Cx<T>), log2Mx, log2My));
   return it == g_plans.ytk.end() ? ypass_tk<T>(log2My) : it->second;
 }
 
@@ -777,11 +779,11 @@ static int ensure_spectra(ssa_ctx* const* cs, int n, cudaStream_t st) {
       g_ring.copy(dpy, sy_pre.data(), sizeof(int32_t) * sy_pre.size(), st) != SSA_OK)
     return fail(SSA_ECUDA, "spectrum tile upload");
   (void)max_ny;
-  int max_tk = 1;
-  for (auto& y : yitems) max_tk = std::max(max_tk, (int)y.tk);
+  int max_buf = 0;                  // every item's own tk x padded column must fit
+  for (auto& y : yitems) max_buf = std::max(max_buf, (int)y.tk * padded_len(1 << y.log2My));
   launch_spec<T>(di, Tiles{dpx, (int)items.size(), sx_pre.back()}, dy,
                  Tiles{dpy, (int)yitems.size(), sy_pre.back()}, max_log2Mx, max_log2My, twiddles<T>(cs[0]->device), st,
-                 max_tk);
+                 max_buf);
   CU(cudaGetLastError());
   cudaFreeAsync(di, st);
   cudaFreeAsync(dy, st);
@@ -813,7 +815,7 @@ struct MvSet {
   YItem<T>* dy2 = nullptr;
   int32_t *t_xf = nullptr, *t_yp = nullptr, *t_xi = nullptr;   // block ranges of the 2D launches
   int n_xf = 0, n_yp = 0, n_xi = 0;
-  int max_y_in = 0, max_y_out = 0, max_tk = 1;
+  int max_y_in = 0, max_y_out = 0, max_buf = 0;
   int lx1[MV1_MODES] = {}, lx2 = 1, ly2 = 0;   // largest log2 grid sizes of each list
   void add(const MvItem<T>& m) {
     if (m.log2My == 0) {
@@ -881,7 +883,7 @@ static int finish_set(MvSet<T>& s, Up&& up) {
   std::vector<int32_t> xf{0}, yp{0}, xi{0};
   for (auto& m : s.items2) {
     s.yitems2.push_back(ymv(m));
-    s.max_tk = std::max(s.max_tk, (int)s.yitems2.back().tk);
+    s.max_buf = std::max(s.max_buf, (int)s.yitems2.back().tk * padded_len(1 << s.yitems2.back().log2My));
     xf.push_back(xf.back() + m.y_in_hi);
     yp.push_back(yp.back() + ypass_blocks(m.log2Mx, s.yitems2.back().tk));
     xi.push_back(xi.back() + m.y_out_hi);
@@ -907,7 +909,7 @@ static void run_mv(int dev, const MvSet<T>& s, int step, cudaStream_t st) {
   if (!s.items2.empty()) {
     const int n2 = (int)s.items2.size();
     launch_mv2d<T>(s.d2, s.dy2, n2, Tiles{s.t_xf, n2, s.n_xf}, Tiles{s.t_yp, n2, s.n_yp},
-                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(dev), st, s.max_tk);
+                   Tiles{s.t_xi, n2, s.n_xi}, s.lx2, s.ly2, step, twiddles<T>(dev), st, s.max_buf);
   }
 }
 
@@ -1379,6 +1381,8 @@ struct LzEngine {
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
     if ((mvA.n1() || mvAT.n1()) && mv_async_timeouts(st) != 0)
       return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
+    if (max_log2My > 0 && ypass_bad_tiles(st) != 0)
+      return fail(SSA_ECUDA, "a y-pass tile did not fit its launch's buffers");
     if (std::is_same<T, float>::value && ritz_tc_timeouts(st) != 0)
       return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
     if (std::is_same<T, float>::value && n_shf && short_tma_timeouts(st) != 0)
@@ -1921,6 +1925,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
     TRY(upload(c0, xi, &d_xi)); tmp.push_back(d_xi);
     if (fold) { TRY(upload(c0, fi, &d_fi)); tmp.push_back(d_fi); }
     const int rtk = tuned_ytk<T>(c->log2Mx, c->log2My);
+    const int rbuf = rtk * padded_len(1 << c->log2My);   // staging elements of that tile width
     const Tiles y1{nullptr, 1, ypass_blocks(c->log2Mx, rtk)};
     for (size_t q = 0; q < c->ch.size(); ++q) {
       const Channel& h = c->ch[q];
@@ -1930,13 +1935,13 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
         if (group_of[i] < 0) continue;
         const size_t e = 2 * ((size_t)q * r + i);
         launch_rec_col_fft<T, TV>(d_cu + e, 1, c->log2Mx, wcols, tw, st);
-        launch_ypass<T>(d_yu + e, y1, Y_FWD, c->log2My, -1, tw, st, rtk);
+        launch_ypass<T>(d_yu + e, y1, Y_FWD, c->log2My, -1, tw, st, rbuf);
         launch_rec_col_fft<T, TV>(d_cu + e + 1, 1, c->log2Mx, kcols, tw, st);
-        launch_ypass<T>(d_yu + e + 1, y1, Y_CONVACC, c->log2My, -1, tw, st, rtk);
+        launch_ypass<T>(d_yu + e + 1, y1, Y_CONVACC, c->log2My, -1, tw, st, rbuf);
       }
       for (int g = 0; g < ng; ++g) {
         const size_t e = (size_t)q * ng + g;
-        launch_ypass<T>(d_yi + e, y1, Y_INV, c->log2My, -1, tw, st, rtk);
+        launch_ypass<T>(d_yi + e, y1, Y_INV, c->log2My, -1, tw, st, rbuf);
         launch_rec_xinv<T>(d_xi + e, 1, c->log2Mx, xi[e].ny, tw, st);
         if (fold) launch_rec_fold(d_fi + e, 1, h.nx, st);
       }
@@ -1976,6 +1981,7 @@ static int reconstruct_T(ssa_ctx* const* cs, int n, const RecReq* req, int on_de
   CU(cudaStreamSynchronize(st));
   for (void* t : tmp) c0->release(t);
   c0->release(d_flat);
+  if (ypass_bad_tiles(st) != 0) return fail(SSA_ECUDA, "a y-pass tile did not fit its launch's buffers");
   return SSA_OK;
 }
 
@@ -2776,7 +2782,9 @@ int ssa_autotune(ssa_ctx* ctx, const ssa_params* params, ssa_tune_result* out) {
     const int nb = YPASS_BUF_BYTES / esz;
     for (int tk : {dtk / 2, dtk * 2, dtk * 4}) {
       if (tk < 1 || tk > 64) continue;
-      const size_t bytes = (size_t)esz * (2 * (size_t)std::max(nb, tk * pl) + (1 << std::max(ctx->log2My, 3)) / 8 + 1);
+      // (a launch shared with taller grids carries their twiddle table: the
+      // largest y-grid, 2^12, is assumed)
+      const size_t bytes = (size_t)esz * (2 * (size_t)std::max(nb, tk * pl) + (1 << 12) / 8 + 1);
       if (bytes > (size_t)device_max_smem()) continue;
       {
         std::lock_guard<std::mutex> lk(g_plans.mu);

@@ -55,6 +55,22 @@ __device__ __forceinline__ T in_scale_of(const MvItem<T>& it, int s) {
   return (T)it.in_scale[it.in.st->jc + s + it.in.jdelta];
 }
 
+// The series product's two scalars that come from FP64 state -- the input
+// column's scale and, for the fused long step, alpha_j times v_j's column
+// scale -- formed once per block by thread 0 into shared memory: GB300 runs
+// FP64 arithmetic and FP64 -> FP32 conversions at about 1/70 of the FP32
+// rate, and 512 threads forming each of them cost a measurable share of the
+// product.
+template <typename T, bool FUSED>
+__device__ __forceinline__ void series_scalars(const MvItem<T>& it, int s, T* scal) {
+  scal[0] = in_scale_of(it, s);
+  scal[1] = T(0);
+  if constexpr (FUSED) {
+    const int j = it.st->jc + s;
+    scal[1] = (T)(it.lB[j + (int64_t)it.lldb * j] * it.lcolscale[j]);
+  }
+}
+
 // Write the map's positions of grid column y from rb into a compact vector.
 template <typename T, typename TO>
 __device__ void store_col(const T* rb, TO* __restrict__ out, const MapDev& m, int y,
@@ -134,6 +150,7 @@ __device__ T* xpass_inverse(XSmem<T>& sm, Cx<T>* P, int log2H) {
 // Polls of a bulk-copy wait before the kernel gives up and flags it.
 constexpr int MBAR_POLL_LIMIT = 1 << 22;
 __device__ int g_mv_async_timeouts;
+__device__ int g_ypass_bad_tiles;      // y-pass blocks whose tile did not fit the launch's buffers
 
 // The series product with the transform size a compile-time constant
 // (H = 2^LOG2H complex points, NT threads) for dense maps -- the FP32 form's
@@ -160,6 +177,7 @@ __device__ __forceinline__ void mv1d_ct_body(const MvItem<T>& it, int s, const C
   constexpr int NST = (LOG2H + 2) / 3;            // stages of block_fft_io_ct
   Cx<T>* Z = (IN_ZSPEC || !(NST & 1)) ? A : B;
   Cx<T>* X = (Z == A) ? B : A;
+  __shared__ T scal[2];                 // input scale, fused-step coefficient (see series_scalars)
   if (threadIdx.x == 0) {
     mbar_init(&bar);
     if constexpr (IN_ZSPEC) {
@@ -169,15 +187,16 @@ __device__ __forceinline__ void mv1d_ct_body(const MvItem<T>& it, int s, const C
     } else {
       bulk_load(S, it.xh, bulk, &bar);
     }
+    series_scalars<T, OUT_FUSED>(it, s, scal);
   }
   const Cx<T> last = it.xh[H];
   if constexpr (IN_ZSPEC) {
     __syncthreads();                    // twiddle table and barrier initialised
   } else {
     const int64_t ioff = vec_elem_off(it.in, s);
-    const T isc = in_scale_of(it, s);
     const int64_t xe = imin64((int64_t)it.min.bx, it.min.limit);
-    __syncthreads();                    // twiddle table
+    __syncthreads();                    // twiddle table, scalars
+    const T isc = scal[0];
     const TI* src = (const TI*)it.in.base + ioff;
     auto in = [src, xe, isc](int j, int r, int nq) {
       const int64_t x = 2 * (int64_t)(j + r * nq);
@@ -213,7 +232,7 @@ __device__ __forceinline__ void mv1d_ct_body(const MvItem<T>& it, int s, const C
     // fused long-side step: q = (X^T u) - alpha_j v_j into column j+1, partial |q|^2
     const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
     const int j = it.st->jc + s;
-    const T coef = (T)(it.lB[j + (int64_t)it.lldb * j] * it.lcolscale[j]);
+    const T coef = scal[1];
     const T* vj = it.lV + it.lld * j + it.out.off;
     T* qn = it.lV + it.lld * (j + 1) + it.out.off;
     // v_j lands in the (now free) spectrum buffer while the inverse FFT runs:
@@ -249,9 +268,9 @@ __device__ __forceinline__ void mv1d_ct_body(const MvItem<T>& it, int s, const C
     };
     block_fft_io_ct<T, true, LOG2H, NT, LOG2TN>(qin, st, X, Z, tab);
     __shared__ double red[NT / 32];
-    double dacc = (double)acc;      // threads without a butterfly add 0
-    for (int o2 = 16; o2 > 0; o2 >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o2);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dacc;
+    T wacc = acc;                   // threads without a butterfly add 0
+    for (int o2 = 16; o2 > 0; o2 >>= 1) wacc += __shfl_down_sync(0xffffffffu, wacc, o2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)wacc;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -315,6 +334,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
   // aligned start of the shared block
   Cx<T>* Z = (IN_ZSPEC || !(nst & 1)) ? sm.A : sm.B;
   Cx<T>* X = (Z == sm.A) ? sm.B : sm.A;
+  __shared__ T scal[2];                 // input scale, fused-step coefficient (see series_scalars)
   if (threadIdx.x == 0) {
     mbar_init(&bar);
     if constexpr (IN_ZSPEC) {
@@ -324,6 +344,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
     } else {
       bulk_load(sm.S, it.xh, bulk, &bar);
     }
+    series_scalars<T, OUT_FUSED>(it, s, scal);
   }
   const Cx<T> last = it.xh[H];
   auto zout = [Z](int base, int stride, auto& v) {
@@ -335,9 +356,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
     __syncthreads();                    // twiddle table and barrier initialised
   } else if constexpr (!IN_MAPPED) {
     const int64_t ioff = vec_elem_off(it.in, s);
-    const T isc = in_scale_of(it, s);
     const int64_t xe = imin64((int64_t)it.min.bx, it.min.limit);
-    __syncthreads();                    // twiddle table
+    __syncthreads();                    // twiddle table, scalars
+    const T isc = scal[0];
     const TI* src = (const TI*)it.in.base + ioff;
     auto in = [src, xe, isc](int i) {
       const int64_t x = 2 * (int64_t)i;
@@ -375,7 +396,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
     // fused long-side step: q = (X^T u) - alpha_j v_j into column j+1, partial |q|^2
     const int64_t xe = imin64((int64_t)it.mout.bx, it.mout.limit);
     const int j = it.st->jc + s;
-    const T coef = (T)(it.lB[j + (int64_t)it.lldb * j] * it.lcolscale[j]);
+    const T coef = scal[1];
     const T* vj = it.lV + it.lld * j + it.out.off;
     T* qn = it.lV + it.lld * (j + 1) + it.out.off;
     // v_j lands in the (now free) spectrum buffer while the inverse FFT runs:
@@ -392,8 +413,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
           if (x + 1 < xe) cp_async_elem<sizeof(T)>(vs + x + 1, vj + x + 1);
         }
     }
-    // per-thread partial of |q|^2 in T (a few dozen terms), the block sum in
-    // double: FP64 per element would cost more than the product on GB300
+    // per-thread and per-warp partials of |q|^2 in T (a few dozen terms, then
+    // 32), the sum of the warps' partials in double: FP64 per element or per
+    // thread would cost more than the product on GB300
     T acc = T(0);
     auto st = [vs, qn, xe, coef, &acc](int base, int stride, auto& v) {
       constexpr int R = sizeof(v) / sizeof(v[0]);
@@ -414,9 +436,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_mv1d(const MvIt
     };
     block_fft_io<T, true>(qin, st, X, Z, log2H, sm.tab, log2H + 1);
     __shared__ double red[16];
-    double dacc = (double)acc;
-    for (int o2 = 16; o2 > 0; o2 >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o2);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dacc;
+    T wacc = acc;
+    for (int o2 = 16; o2 > 0; o2 >>= 1) wacc += __shfl_down_sync(0xffffffffu, wacc, o2);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)wacc;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -496,6 +518,11 @@ __global__ void __launch_bounds__(512) k_ypass(const YItem<T>* __restrict__ item
   const int TK = it.tk;             // TK * padded_len(My) <= buf_elems (ypass_tk)
   const int k0 = b0 * TK;
   if (k0 > H) return;
+  if (TK < 1 || (int64_t)TK * padded_len(1 << log2My) > buf_elems) {
+    // a launch sized for a smaller tile: touch nothing, report it
+    if (threadIdx.x == 0) atomicAdd(&g_ypass_bad_tiles, 1);
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
   Cx<T>* B = A + buf_elems;
@@ -583,6 +610,17 @@ static inline size_t xsmem_bytes(int log2Mx, size_t csz, bool spec = false) {
          ((2 * H) / 32 + 1 + 32) * sizeof(int32_t);
 }
 
+// y-pass blocks refused for a tile larger than their launch's buffers since
+// the last call (read and reset; -1 on a CUDA error)
+int ypass_bad_tiles(cudaStream_t st) {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbolAsync(&h, g_ypass_bad_tiles, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -1;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbolAsync(g_ypass_bad_tiles, &z, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  return h;
+}
+
 // Bulk-copy waits that gave up since the last call (read and reset).
 int mv_async_timeouts(cudaStream_t st) {
   int h = 0, z = 0;
@@ -651,21 +689,21 @@ void launch_mv1d(const MvItem<T>* items, int n, int max_log2Mx, int s, const Cx<
 
 template <typename T>
 void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, Tiles xf, Tiles yp, Tiles xi,
-                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st, int max_tk) {
+                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st, int max_buf) {
   if (n <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_mv_xfwd<T>);
   set_max_smem((const void*)k_mv_xinv<T>);
   if (xf.total > 0) { k_mv_xfwd<T><<<xf.total, 512, sm, st>>>(items, xf, s, tw); count_launch(); }
-  launch_ypass<T>(yitems, yp, Y_MULCONJ_INV, max_log2My, s, tw, st, max_tk);
+  launch_ypass<T>(yitems, yp, Y_MULCONJ_INV, max_log2My, s, tw, st, max_buf);
   if (xi.total > 0) { k_mv_xinv<T><<<xi.total, 512, sm, st>>>(items, xi, s, tw); count_launch(); }
 }
 
 template <typename T>
 void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int s, const Cx<T>* tw,
-                  cudaStream_t st, int max_tk) {
+                  cudaStream_t st, int max_buf) {
   if (tl.total <= 0) return;
-  const int buf = std::max(ypass_buf<T>(max_log2My), max_tk * padded_len(1 << max_log2My));
+  const int buf = std::max(ypass_buf<T>(max_log2My), max_buf);
   const int N = 1 << (max_log2My < 3 ? 3 : max_log2My);
   const size_t sm = (2 * (size_t)buf + N / 8 + 1) * sizeof(Cx<T>);
   set_max_smem((const void*)k_ypass<T>);
@@ -674,12 +712,12 @@ void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int
 
 template <typename T>
 void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Tiles sy, int max_log2Mx,
-                 int max_log2My, const Cx<T>* tw, cudaStream_t st, int max_tk) {
+                 int max_log2My, const Cx<T>* tw, cudaStream_t st, int max_buf) {
   if (sx.total <= 0) return;
   size_t sm = xsmem_bytes(max_log2Mx, sizeof(Cx<T>));
   set_max_smem((const void*)k_spec_x<T>);
   k_spec_x<T><<<sx.total, 512, sm, st>>>(items, sx, tw); count_launch();
-  if (max_log2My > 0) launch_ypass<T>(yitems, sy, Y_FWD, max_log2My, -1, tw, st, max_tk);
+  if (max_log2My > 0) launch_ypass<T>(yitems, sy, Y_FWD, max_log2My, -1, tw, st, max_buf);
 }
 
 #define INST(T)                                                                                       \

@@ -10,8 +10,9 @@
 //      arrives by element-wise cp.async straight into the K-major
 //      core-matrix layout the MMA reads (8 rows x 16 bytes per core matrix,
 //      no swizzle);
-//   2. each FP32 value x is split into two TF32 parts, hi = rna(x) and
-//      lo = rna(x - hi), so x = hi + lo to about 2^-24 |x|;
+//   2. each FP32 value x is split into hi = x rounded to TF32 and
+//      lo = x - hi (exact); the tensor core reads lo's leading 11 bits, so
+//      hi + lo carries x to about 2^-22 |x|;
 //   3. one thread issues tcgen05.mma kind::tf32 for hi*hi + hi*lo + lo*hi
 //      (the lo*lo term is below FP32 rounding) per K step of 8, accumulating
 //      in FP32 in tensor memory (TMEM), and commits to an mbarrier;
@@ -49,10 +50,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// x rounded to the 10 explicit mantissa bits of TF32, to nearest with ties
+// away from zero, by integer arithmetic on the bit pattern (adding half a TF32
+// unit to the magnitude bits carries into the exponent where it should; finite
+// inputs only)
+__device__ __forceinline__ float tf32_hi(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// x = hi + lo with hi the TF32 rounding of x; lo = x - hi is exact in FP32,
+// |lo| <= 2^-11 |x|, and the tensor core reads only its leading 11 bits,
+// which leaves an error below 2^-22 |x|
+__device__ __forceinline__ void tf32_split(float4 x, float4& h, float4& l) {
+  h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+  l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -72,7 +83,7 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, u
 // contraction is memory-bound (kk of 20-60 columns per row read).
 constexpr int RTC_KC = 32;
 
-__global__ void __launch_bounds__(RTC_NT) k_ritz_tc(const RitzItem<float>* __restrict__ items,
+__global__ void __launch_bounds__(RTC_NT, 4) k_ritz_tc(const RitzItem<float>* __restrict__ items,
                                                   const int32_t* __restrict__ tpre, int n, int final_pass, int np_max) {
   int rblk;
   const RitzItem<float> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
@@ -115,12 +126,32 @@ __global__ void __launch_bounds__(RTC_NT) k_ritz_tc(const RitzItem<float>* __res
     const int c0 = ch * RTC_KC;
     // 1. this chunk's basis rows and coefficients into the core-matrix
     //    layout (a warp fills one core matrix per pass: lane = row + 8 column)
-    for (int q = warp; q < (RTC_M / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
-      const int rg = q % (RTC_M / 8), cg = q / (RTC_M / 8);
-      const int r = rg * 8 + rin, c = cg * 4 + cin;
-      float* dst = reinterpret_cast<float*>(smraw + kmaj(r, c, RTC_KC));
-      if (r < nr && c0 + c < kc) cp_async_elem<4>(dst, basis + r0 + r + ldb * (c0 + c));
-      else *dst = 0.0f;
+    if (nr == RTC_M) {
+      // a full tile: warp w fills the core matrices of row groups w and w + 8
+      // in every column group, with offsets known at compile time
+      static_assert(RTC_M / 8 == 2 * (RTC_NT / 32), "two row groups per warp");
+      const float* src = basis + r0 + rin + ldb * (c0 + cin);
+      unsigned char* dst = smraw + (rin << 4) + (cin << 2);
+#pragma unroll
+      for (int cg = 0; cg < RTC_KC / 4; ++cg) {
+        const bool in = c0 + cg * 4 + cin < kc;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rg = warp + (RTC_NT / 32) * h;
+          unsigned char* d = dst + ((rg * (RTC_KC / 4) + cg) << 7);
+          if (in) cp_async_elem<4>(d, src + rg * 8);
+          else *reinterpret_cast<float*>(d) = 0.0f;
+        }
+        src += 4 * ldb;
+      }
+    } else {
+      for (int q = warp; q < (RTC_M / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
+        const int rg = q % (RTC_M / 8), cg = q / (RTC_M / 8);
+        const int r = rg * 8 + rin, c = cg * 4 + cin;
+        float* dst = reinterpret_cast<float*>(smraw + kmaj(r, c, RTC_KC));
+        if (r < nr && c0 + c < kc) cp_async_elem<4>(dst, basis + r0 + r + ldb * (c0 + c));
+        else *dst = 0.0f;
+      }
     }
     for (int q = warp; q < (np / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
       const int ng = q % (np / 8), cg = q / (np / 8);
@@ -131,28 +162,15 @@ __global__ void __launch_bounds__(RTC_NT) k_ritz_tc(const RitzItem<float>* __res
     }
     cp_async_wait_all();
     __syncthreads();
-    // 2. x -> hi = rna(x) in place, lo = rna(x - hi)
+    // 2. x -> hi (TF32 rounding) in place, lo = x - hi beside it
     {
       float4* h4 = reinterpret_cast<float4*>(ahi);
       float4* l4 = reinterpret_cast<float4*>(alo);
-      for (int e = tid; e < RTC_M * RTC_KC / 4; e += RTC_NT) {
-        const float4 x = h4[e];
-        float4 h, l;
-        h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
-        l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
-        h4[e] = h;
-        l4[e] = l;
-      }
+#pragma unroll
+      for (int e = tid; e < RTC_M * RTC_KC / 4; e += RTC_NT) tf32_split(h4[e], h4[e], l4[e]);
       float4* b4 = reinterpret_cast<float4*>(bhi);
       float4* m4 = reinterpret_cast<float4*>(blo);
-      for (int e = tid; e < np * RTC_KC / 4; e += RTC_NT) {
-        const float4 x = b4[e];
-        float4 h, l;
-        h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
-        l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
-        b4[e] = h;
-        m4[e] = l;
-      }
+      for (int e = tid; e < np * RTC_KC / 4; e += RTC_NT) tf32_split(b4[e], b4[e], m4[e]);
     }
     // generic-proxy stores become visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -36,6 +36,10 @@ void launch_uspec(const UzItem<T>* items, int n, int max_log2M, int s, const Cx<
 // (each sets a device counter instead of spinning on); read and reset, -1 on
 // a CUDA error.  Synchronises the stream.
 int mv_async_timeouts(cudaStream_t st);
+// y-pass blocks that refused a tile larger than their launch's staging
+// buffers (a sizing fault of the host, reported rather than run) since the
+// last call; read and reset, -1 on a CUDA error.
+int ypass_bad_tiles(cudaStream_t st);
 
 // y-pass blocks stage tk x-frequencies (all My rows) in two buffers of
 // YPASS_BUF_BYTES (grown to one padded column where a column is larger), so
@@ -58,17 +62,17 @@ inline int ypass_blocks(int log2Mx, int tk) { return ((1 << (log2Mx - 1)) + 1 + 
 
 // 2D products: tiles of the x-pass forward (y_in_hi blocks per item), the
 // y-pass (ypass_blocks) and the x-pass inverse (y_out_hi blocks).
-// max_tk: the largest tile width (x-frequencies per block) among the y-pass
-// items, which sizes the launch's staging buffers
+// max_buf: the largest tk * padded_len(My) among the y-pass items (complex
+// elements), which sizes the launch's staging buffers with ypass_buf
 template <typename T>
 void launch_mv2d(const MvItem<T>* items, const YItem<T>* yitems, int n, Tiles xf, Tiles yp, Tiles xi,
-                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st, int max_tk);
+                 int max_log2Mx, int max_log2My, int s, const Cx<T>* tw, cudaStream_t st, int max_buf);
 template <typename T>
 void launch_ypass(const YItem<T>* items, Tiles tl, int mode, int max_log2My, int s, const Cx<T>* tw,
-                  cudaStream_t st, int max_tk);
+                  cudaStream_t st, int max_buf);
 // spectra: sx gives ny blocks per item, sy ypass_blocks per 2D item
 template <typename T>
 void launch_spec(const SpecItem<T>* items, Tiles sx, const YItem<T>* yitems, Tiles sy, int max_log2Mx,
-                 int max_log2My, const Cx<T>* tw, cudaStream_t st, int max_tk);
+                 int max_log2My, const Cx<T>* tw, cudaStream_t st, int max_buf);
 
 }  // namespace ssa

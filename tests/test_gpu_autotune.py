@@ -55,3 +55,32 @@ def test_plans_round_trip_and_reject_garbage(tmp_path):
     with pytest.raises(pkg.SSAError):
         LL.plans_import("color x.y 3\n")
     s.close()
+
+
+def test_every_tile_width_gives_the_same_results():
+    """Whatever y-pass tile width a plan names (tuned or imported), every launch
+    that uses it -- products, spectra, the reconstruction's passes -- must size
+    its staging buffers for it, and the results must not depend on it (each
+    x-frequency's column transform is computed alone)."""
+    x = W.harmonic_image(45, 100, n_harm=2, seed=41, noise=0.1, dtype=np.float64)
+    before = set(LL.plans_export().splitlines())
+    s = pkg.SSA.image(x, 9, 12)
+    s.autotune(4, "fp32")
+    s.close()
+    new = [ln for ln in LL.plans_export().splitlines() if ln.startswith("ytk ") and ln not in before]
+    assert len(new) == 1, new
+    key = new[0].split()[1]
+    ref = None
+    for tk in (1, 2, 4, 8, 16, 32, 64):
+        LL.plans_import(f"ytk {key} {tk}\n")
+        t = pkg.SSA.image(x, 9, 12)
+        t.decompose(4, "fp32", seed=7)
+        got = (t.sigma(), t.reconstruct([[0, 1], [2, 3]], residual=True))
+        t.close()
+        if ref is None:
+            ref = got
+            continue
+        np.testing.assert_allclose(got[0], ref[0], rtol=1e-6, atol=0)
+        scale = float(np.nanmax(np.abs(x)))
+        for a, b in zip(got[1], ref[1]):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * scale)

@@ -238,6 +238,30 @@ def test_batch_equals_single():
         np.testing.assert_allclose(s.sigma(), ref, rtol=1e-6)
 
 
+def test_batch_images_of_different_heights():
+    """One y-pass launch serves images whose y-grids differ: each item keeps
+    the tile width that fits its own column length, and the launch's staging
+    buffer is sized for the largest tile x column among them (a wide tile of
+    a short image times the column of a tall one overflowed shared memory)."""
+    def image(nx, ny, seed):
+        rng = np.random.default_rng(seed)
+        m, n = np.arange(nx)[:, None], np.arange(ny)[None, :]
+        return (np.cos(2 * np.pi * m / 9 + 0.3) * np.cos(2 * np.pi * n / 13 + 0.7)
+                + 0.5 * np.cos(2 * np.pi * m / 5) * np.sin(2 * np.pi * n / 31) + 0.05 * rng.standard_normal((nx, ny)))
+    specs = [(40, 10, 6, 4, 1), (48, 700, 8, 40, 2), (36, 24, 5, 6, 3)]
+    singles = []
+    for nx, ny, lx, ly, sd in specs:
+        s = pkg.SSA.image(image(nx, ny, sd), lx, ly)
+        s.decompose(4, "fp32")
+        singles.append(s.sigma())
+        s.close()
+    batch = [pkg.SSA.image(image(nx, ny, sd), lx, ly) for nx, ny, lx, ly, sd in specs]
+    pkg.decompose_batch(batch, 4, "fp32")
+    for s, ref in zip(batch, singles):
+        np.testing.assert_allclose(s.sigma(), ref, rtol=1e-6)
+        s.close()
+
+
 def test_large_batch_runs_in_two_halves_with_single_results():
     """Batches of 64 problems or more run as two interleaved halves on two
     streams; every problem still gets the result it gets alone."""
