@@ -7,9 +7,9 @@
 // path where the work is a GEMM.  Each CTA owns 128 rows of one problem's
 // basis (M = 128, N = kk rounded up to 16, K = kc in chunks of 32):
 //   1. a chunk of the rows of the basis columns and of the coefficients
-//      arrives by element-wise cp.async straight into the K-major
-//      core-matrix layout the MMA reads (8 rows x 16 bytes per core matrix,
-//      no swizzle);
+//      is loaded (lane = row, coalesced along the rows) and stored into the
+//      K-major core-matrix layout the MMA reads (8 rows x 16 bytes per core
+//      matrix, no swizzle), one 16-byte store per core-matrix row;
 //   2. each FP32 value x is split into hi = x rounded to TF32 and
 //      lo = x - hi (exact); the tensor core reads lo's leading 11 bits, so
 //      hi + lo carries x to about 2^-22 |x|;
@@ -35,12 +35,9 @@ constexpr int RTC_POLL = 1 << 22;   // bounded wait on the MMA barrier
 
 __device__ int g_ritz_tc_timeouts;
 
-// byte offset of element (r, c) of an operand with kp K-columns, K-major
-// core matrices: core (r / 8, c / 4) at ((r / 8) (kp / 4) + c / 4) * 128,
-// row r % 8 at 16 (r % 8), element c % 4 at 4 (c % 4)
-__device__ __forceinline__ uint32_t kmaj(int r, int c, int kp) {
-  return (uint32_t)((((r >> 3) * (kp >> 2) + (c >> 2)) << 7) + ((r & 7) << 4) + ((c & 3) << 2));
-}
+// Operand layout: element (r, c) of an operand with kp K-columns, K-major
+// core matrices, sits at byte ((r / 8) (kp / 4) + c / 4) * 128 + 16 (r % 8)
+// + 4 (c % 4): core (r / 8, c / 4), row r % 8, element c % 4.
 
 // shared-memory matrix descriptor (no swizzle): start address, leading byte
 // offset (next core matrix along K), stride byte offset (next 8-row group),
@@ -82,6 +79,9 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, u
 // memory, and several CTAs per SM keep enough rows in flight -- the
 // contraction is memory-bound (kk of 20-60 columns per row read).
 constexpr int RTC_KC = 32;
+// (row group of 32, column group of 4) tasks of one chunk per thread
+constexpr int RTC_TASKS = (RTC_M / 32) * (RTC_KC / 4) / (RTC_NT / 32);
+static_assert((RTC_M / 32) * (RTC_KC / 4) % (RTC_NT / 32) == 0, "whole tasks per warp");
 
 __global__ void __launch_bounds__(RTC_NT, 4) k_ritz_tc(const RitzItem<float>* __restrict__ items,
                                                   const int32_t* __restrict__ tpre, int n, int final_pass, int np_max) {
@@ -116,61 +116,72 @@ __global__ void __launch_bounds__(RTC_NT, 4) k_ritz_tc(const RitzItem<float>* __
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) mbar_init(&bar);
-  const int rin = lane & 7, cin = lane >> 3;
   // kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
   // both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(np >> 3) << 17) |
                          ((uint32_t)(RTC_M >> 4) << 24);
   bool ok = true;
+  // the thread's RTC_TASKS (row, four-column group) values of chunk ch
+  auto load_chunk = [&](int ch, float4 (&x)[RTC_TASKS]) {
+#pragma unroll
+    for (int t = 0; t < RTC_TASKS; ++t) {
+      const int q = warp + t * (RTC_NT / 32);
+      const int c = ch * RTC_KC + 4 * (q / (RTC_M / 32));
+      const int r = (q % (RTC_M / 32)) * 32 + lane;
+      x[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (r < nr) {
+        const float* src = basis + r0 + r + ldb * c;
+        if (c < kc) x[t].x = src[0];
+        if (c + 1 < kc) x[t].y = src[ldb];
+        if (c + 2 < kc) x[t].z = src[2 * ldb];
+        if (c + 3 < kc) x[t].w = src[3 * ldb];
+      }
+    }
+  };
+  float4 xa[RTC_TASKS];
+  load_chunk(0, xa);
   for (int ch = 0; ch < nchunk; ++ch) {
     const int c0 = ch * RTC_KC;
-    // 1. this chunk's basis rows and coefficients into the core-matrix
-    //    layout (a warp fills one core matrix per pass: lane = row + 8 column)
-    if (nr == RTC_M) {
-      // a full tile: warp w fills the core matrices of row groups w and w + 8
-      // in every column group, with offsets known at compile time
-      static_assert(RTC_M / 8 == 2 * (RTC_NT / 32), "two row groups per warp");
-      const float* src = basis + r0 + rin + ldb * (c0 + cin);
-      unsigned char* dst = smraw + (rin << 4) + (cin << 2);
+    // 1. this chunk's basis rows and coefficients, split into TF32 hi / lo,
+    //    into the K-major core-matrix layout the MMA reads.  Lane = row:
+    //    four 4-byte loads (one per column of a group of four; 32 consecutive
+    //    rows of a column are 128 contiguous bytes) give each thread the 16
+    //    bytes of one core-matrix row, stored with one 16-byte store per
+    //    part, so each group of eight lanes fills one contiguous 128-byte
+    //    core matrix (no bank conflicts, no separate split pass).  The next
+    //    chunk's loads are issued first, so they are in flight during this
+    //    chunk's stores and MMAs.
+    float4 xn[RTC_TASKS];
+    if (ch + 1 < nchunk) load_chunk(ch + 1, xn);
 #pragma unroll
-      for (int cg = 0; cg < RTC_KC / 4; ++cg) {
-        const bool in = c0 + cg * 4 + cin < kc;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int rg = warp + (RTC_NT / 32) * h;
-          unsigned char* d = dst + ((rg * (RTC_KC / 4) + cg) << 7);
-          if (in) cp_async_elem<4>(d, src + rg * 8);
-          else *reinterpret_cast<float*>(d) = 0.0f;
-        }
-        src += 4 * ldb;
-      }
-    } else {
-      for (int q = warp; q < (RTC_M / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
-        const int rg = q % (RTC_M / 8), cg = q / (RTC_M / 8);
-        const int r = rg * 8 + rin, c = cg * 4 + cin;
-        float* dst = reinterpret_cast<float*>(smraw + kmaj(r, c, RTC_KC));
-        if (r < nr && c0 + c < kc) cp_async_elem<4>(dst, basis + r0 + r + ldb * (c0 + c));
-        else *dst = 0.0f;
-      }
+    for (int t = 0; t < RTC_TASKS; ++t) {
+      const int q = warp + t * (RTC_NT / 32);
+      const int g = q / (RTC_M / 32);
+      const int r = (q % (RTC_M / 32)) * 32 + lane;
+      float4 h, l;
+      tf32_split(xa[t], h, l);
+      const uint32_t off = (uint32_t)((((r >> 3) * (RTC_KC / 4) + g) << 7) + ((r & 7) << 4));
+      *reinterpret_cast<float4*>(smraw + off) = h;
+      *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(alo) + off) = l;
     }
-    for (int q = warp; q < (np / 8) * (RTC_KC / 4); q += RTC_NT / 32) {
-      const int ng = q % (np / 8), cg = q / (np / 8);
-      const int nn = ng * 8 + rin, c = cg * 4 + cin;
-      float* dst = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(bhi) + kmaj(nn, c, RTC_KC));
-      if (c0 + c < kc) cp_async_elem<4>(dst, it.Cs + (int64_t)(c0 + c) * it.ldcs + nn);   // zero past kk
-      else *dst = 0.0f;
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // 2. x -> hi (TF32 rounding) in place, lo = x - hi beside it
-    {
-      float4* h4 = reinterpret_cast<float4*>(ahi);
-      float4* l4 = reinterpret_cast<float4*>(alo);
 #pragma unroll
-      for (int e = tid; e < RTC_M * RTC_KC / 4; e += RTC_NT) tf32_split(h4[e], h4[e], l4[e]);
-      float4* b4 = reinterpret_cast<float4*>(bhi);
-      float4* m4 = reinterpret_cast<float4*>(blo);
-      for (int e = tid; e < np * RTC_KC / 4; e += RTC_NT) tf32_split(b4[e], b4[e], m4[e]);
+    for (int t = 0; t < RTC_TASKS; ++t) xa[t] = xn[t];
+    for (int q = warp; q < ((np + 31) / 32) * (RTC_KC / 4); q += RTC_NT / 32) {
+      const int ngs = (np + 31) / 32, g = q / ngs;
+      const int nn = (q % ngs) * 32 + lane, c = c0 + 4 * g;
+      if (nn < np) {
+        float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float* src = it.Cs + (int64_t)c * it.ldcs + nn;   // zero past kk
+        if (c < kc) x.x = src[0];
+        if (c + 1 < kc) x.y = src[it.ldcs];
+        if (c + 2 < kc) x.z = src[2 * it.ldcs];
+        if (c + 3 < kc) x.w = src[3 * it.ldcs];
+        float4 h, l;
+        tf32_split(x, h, l);
+        const uint32_t off = (uint32_t)((((nn >> 3) * (RTC_KC / 4) + g) << 7) + ((nn & 7) << 4));
+        *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(bhi) + off) = h;
+        *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(blo) + off) = l;
+      }
     }
     // generic-proxy stores become visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
