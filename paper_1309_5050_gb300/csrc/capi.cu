@@ -359,6 +359,10 @@ struct Channel {
   int64_t nsq = 0;
 };
 
+// leading dimension of the FP32 form's float-float short basis: rows rounded
+// up to a multiple of four (16-byte aligned FP32 columns for the bulk copies)
+static inline int64_t ldf_ff(int64_t Ls) { return (Ls + 3) & ~int64_t(3); }
+
 struct Workspace {             // Lanczos + results, per precision
   int prec = -1, r = 0, k = 0, kk = 0;
   bool swapped = false;
@@ -366,7 +370,8 @@ struct Workspace {             // Lanczos + results, per precision
   int nblk_s = 0, nblk_l = 0;
   LzState* st = nullptr;
   double* U = nullptr; void* V = nullptr;
-  float2* Uf = nullptr;        // FP32 form: float-float copy of U for the short side
+  float* Uf = nullptr;         // FP32 form: float-float copy of U for the short side, hi
+                               // parts then lo parts (ldf_ff(Ls) x (k+1) each)
   double* p = nullptr; void* q = nullptr;
   void* parts_s = nullptr; void* parts_l = nullptr;
   int n_part_s = 1, n_part_l = 1;
@@ -965,7 +970,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
                   3 * rnd256(8 * k1 * k1) + 2 * rnd256(8 * (k1 + 1)) + 2 * rnd256(8 * (size_t)w.nblk_s * (KMAX + 1)) +
                   rnd256(8 * (size_t)w.nblk_s) + rnd256(8 * (size_t)std::max<int64_t>(w.nblk_l, (int64_t)c->ch.size())) + rnd256(cz * c->L * w.r) +
                   rnd256(cz * c->K * w.r) + 2 * rnd256(8 * (size_t)w.r) + rnd256(cz * (k1 + 1) * ritz_ldcs(w.k)) +
-                  rnd256(2 * cz * uz_bound(c)) + (std::is_same<T, float>::value ? rnd256(8 * (size_t)((w.Ls + 1) & ~int64_t(1)) * k1) : 0);
+                  rnd256(2 * cz * uz_bound(c)) + (std::is_same<T, float>::value ? rnd256(8 * (size_t)ldf_ff(w.Ls) * k1) : 0);
     if (c->log2My > 0) {
       const size_t hs = (size_t)((1 << (c->log2Mx - 1)) + 1) << c->log2My;
       need += 2 * rnd256(2 * cz * hs * c->ch.size());
@@ -977,7 +982,7 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->allocT(&w.st, 1));
   TRY(c->allocT(&w.U, (size_t)w.Ls * k1));
   w.Uf = nullptr;
-  if (std::is_same<T, float>::value) TRY(c->allocT(&w.Uf, (size_t)((w.Ls + 1) & ~int64_t(1)) * k1));
+  if (std::is_same<T, float>::value) TRY(c->allocT(&w.Uf, 2 * (size_t)ldf_ff(w.Ls) * k1));
   TRY(c->alloc(&w.V, sizeof(T) * (size_t)w.Kl * k1));
   TRY(c->allocT(&w.p, (size_t)w.Ls));
   TRY(c->alloc(&w.q, sizeof(T) * (size_t)w.Kl));
@@ -1121,7 +1126,8 @@ struct LzEngine {
     Workspace& w = c->ws;
     ShortItem s;
     s.seed = sd;
-    s.st = w.st; s.U = w.U; s.Uf = w.Uf; s.ldf = (w.Ls + 1) & ~int64_t(1); s.ldu = w.Ls; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
+    s.st = w.st; s.U = w.U; s.ldf = ldf_ff(w.Ls); s.ldu = w.Ls;
+    s.Uh = w.Uf; s.Ul = w.Uf ? w.Uf + (size_t)s.ldf * (w.k + 1) : nullptr; s.parts = w.parts_s; s.part_ld = w.Ls; s.n_part = w.n_part_s;
     s.parts_double = std::is_same<T, double>::value; s.p = w.p; s.B = w.B; s.ldb = w.k; s.nblk = w.nblk_s;
     s.cpa = w.cpa; s.cpb = w.cpb; s.npart = w.np_s; s.Ls = w.Ls;
     return s;

@@ -332,12 +332,14 @@ void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cu
 
 // ------------------------------------------------------------ short side, float-float
 // The FP32 form's short side: the steps above in float-float arithmetic
-// (ff.cuh) on Uf, U's (hi, lo) copy.  GB300's FP64 pipe issues about 1.7
-// FMAs per clock per SM against about 118 FP32 FMAs, and the FP64 short side
-// ran its FP64 pipe at 77% of peak; a float-float product-sum is about a
-// dozen FP32 instructions.  The coefficients of the Gram-Schmidt passes carry
-// about 48 bits, so U stays orthogonal to about n 2^-48 (n = Ls) -- far below
-// the FP32 products' own error, which bounds what the FP32 form resolves.
+// (ff.cuh) on U's (hi, lo) copy, held as two FP32 arrays Uh and Ul (leading
+// dimension ldf = Ls rounded up to a multiple of four, zero pad rows).
+// GB300's FP64 pipe issues about 1.7 FMAs per clock per SM against about
+// 118 FP32 FMAs, and the FP64 short side ran its FP64 pipe at 77% of peak; a
+// float-float product-sum is about a dozen FP32 instructions.  The
+// coefficients of the Gram-Schmidt passes carry about 48 bits, so U stays
+// orthogonal to about n 2^-48 (n = Ls) -- far below the FP32 products' own
+// error, which bounds what the FP32 form resolves.
 
 template <int NT>
 __device__ __forceinline__ ff block_sum_ffv(ffacc v, float2* red) {
@@ -353,51 +355,62 @@ __device__ __forceinline__ ff block_sum_ffv(ffacc v, float2* red) {
 
 // c[i] = U[:, i]^T p over rows [0, nrows) of U (from row r0) and p, i < j; a warp per column
 template <int NT>
-__device__ __forceinline__ void dots_ff(const float2* __restrict__ U, int64_t ldu, int64_t r0, const float2* p,
-                                        int nrows, int j, float2* c) {
+__device__ __forceinline__ void dots_ff(const float* __restrict__ Uh, const float* __restrict__ Ul, int64_t ldf,
+                                        int64_t r0, const float2* p, int nrows, int j, float2* c) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < j; i += NT / 32) {
-    const float2* __restrict__ col = U + ldu * i + r0;
+    const float* __restrict__ ch = Uh + ldf * i + r0;
+    const float* __restrict__ cl = Ul + ldf * i + r0;
     ffacc a0, a1;                   // two chains: the TwoSum of one is a dependent sequence
     int t = lane;
-    // eight loads issued before their arithmetic: U streams from L2 / HBM,
-    // and one block per problem has few warps to hide that latency with
+    // eight loads of each part issued before their arithmetic: U streams
+    // from L2 / HBM, and one block per problem has few warps to hide that
+    // latency with
     for (; t + 7 * 32 < nrows; t += 8 * 32) {
-      float2 u[8];
+      float uh[8], ul[8];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) u[m] = col[t + 32 * m];
+      for (int m = 0; m < 8; ++m) { uh[m] = ch[t + 32 * m]; ul[m] = cl[t + 32 * m]; }
 #pragma unroll
-      for (int m = 0; m < 8; m += 2) { a0.fma(u[m], p[t + 32 * m]); a1.fma(u[m + 1], p[t + 32 * (m + 1)]); }
+      for (int m = 0; m < 8; m += 2) {
+        const float2 p0 = p[t + 32 * m], p1 = p[t + 32 * (m + 1)];
+        a0.fma(uh[m], ul[m], p0.x, p0.y);
+        a1.fma(uh[m + 1], ul[m + 1], p1.x, p1.y);
+      }
     }
-    for (; t < nrows; t += 32) a0.fma(col[t], p[t]);
+    for (; t < nrows; t += 32) { const float2 pv = p[t]; a0.fma(ch[t], cl[t], pv.x, pv.y); }
     a0.add(a1);
     const ff v = warp_sum_ff(a0).value();
     if (lane == 0) c[i] = make_float2(v.hi, v.lo);
   }
 }
 
-// p[row] -= (U c)[row] for this thread's rows of [0, Ls); returns the
-// thread's share of ||p||^2
-__device__ __forceinline__ ff update_row_ff(const float2* __restrict__ Ur, int64_t ldu, int j, const float2* c) {
+// (U c)[row] for one row (Uh, Ul point at the row in column 0)
+__device__ __forceinline__ ff update_row_ff(const float* __restrict__ Uh, const float* __restrict__ Ul, int64_t ldf,
+                                           int j, const float2* c) {
   ffacc s0, s1;
   int i = 0;
-  for (; i + 7 < j; i += 8) {         // eight loads in flight (see dots_ff)
-    float2 u[8];
+  for (; i + 7 < j; i += 8) {         // eight loads of each part in flight (see dots_ff)
+    float uh[8], ul[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) u[m] = Ur[ldu * (i + m)];
+    for (int m = 0; m < 8; ++m) { uh[m] = Uh[ldf * (i + m)]; ul[m] = Ul[ldf * (i + m)]; }
 #pragma unroll
-    for (int m = 0; m < 8; m += 2) { s0.fma(u[m], c[i + m]); s1.fma(u[m + 1], c[i + m + 1]); }
+    for (int m = 0; m < 8; m += 2) {
+      s0.fma(uh[m], ul[m], c[i + m].x, c[i + m].y);
+      s1.fma(uh[m + 1], ul[m + 1], c[i + m + 1].x, c[i + m + 1].y);
+    }
   }
-  for (; i < j; ++i) s0.fma(Ur[ldu * i], c[i]);
+  for (; i < j; ++i) s0.fma(Uh[ldf * i], Ul[ldf * i], c[i].x, c[i].y);
   s0.add(s1);
   return s0.value();
 }
 
-__device__ __forceinline__ ffacc update_ff(const float2* __restrict__ U, int64_t ldu, float2* p, int Ls, int j,
-                                           const float2* c) {
+// p[row] -= (U c)[row] for this thread's rows of [0, Ls); returns the
+// thread's share of ||p||^2
+__device__ __forceinline__ ffacc update_ff(const float* __restrict__ Uh, const float* __restrict__ Ul, int64_t ldf,
+                                           float2* p, int Ls, int j, const float2* c) {
   ffacc nn;
   for (int row = threadIdx.x; row < Ls; row += blockDim.x) {
-    const ff sv = update_row_ff(U + row, ldu, j, c);
+    const ff sv = update_row_ff(Uh + row, Ul + row, ldf, j, c);
     const float2 pr = p[row];
     const ff v = ff_add(ff{pr.x, pr.y}, ff_neg(sv));
     p[row] = make_float2(v.hi, v.lo);
@@ -416,24 +429,29 @@ __device__ ff short_random_ff(const ShortItem& it, float2* p, int Ls, int j, flo
   __syncthreads();
   ff nn{0.0f, 0.0f};
   for (int pass = 0; pass < 2; ++pass) {
-    dots_ff<NT>(it.Uf, it.ldf, 0, p, Ls, j, c);
+    dots_ff<NT>(it.Uh, it.Ul, it.ldf, 0, p, Ls, j, c);
     __syncthreads();
-    nn = block_sum_ffv<NT>(update_ff(it.Uf, it.ldf, p, Ls, j, c), red);
+    nn = block_sum_ffv<NT>(update_ff(it.Uh, it.Ul, it.ldf, p, Ls, j, c), red);
   }
   return nn;
 }
 
-// u_j = p / alpha into Uf and U (thread's rows of [r0, r0 + nrows))
-// (and the zero pad row of Uf past Ls, from the block that owns row Ls - 1)
+// u_j = p / alpha into Uh, Ul and U (thread's rows of [r0, r0 + nrows)), and
+// the zero pad rows past Ls from the block that owns row Ls - 1
 __device__ __forceinline__ void write_u_ff(const ShortItem& it, const float2* p, int64_t r0, int nrows, int j,
                                            float2 inv) {
   for (int t = threadIdx.x; t < nrows; t += blockDim.x) {
     const float2 pr = p[t];
     const ff u = ff_mul(ff{pr.x, pr.y}, ff{inv.x, inv.y});
-    it.Uf[r0 + t + it.ldf * j] = make_float2(u.hi, u.lo);
+    it.Uh[r0 + t + it.ldf * j] = u.hi;
+    it.Ul[r0 + t + it.ldf * j] = u.lo;
     it.U[r0 + t + it.ldu * j] = ff_to_double(make_float2(u.hi, u.lo));
   }
-  if (threadIdx.x == 0 && r0 + nrows == it.Ls && it.ldf > it.Ls) it.Uf[it.Ls + it.ldf * j] = make_float2(0.0f, 0.0f);
+  if (r0 + nrows == it.Ls)
+    for (int64_t t = it.Ls + threadIdx.x; t < it.ldf; t += blockDim.x) {
+      it.Uh[t + it.ldf * j] = 0.0f;
+      it.Ul[t + it.ldf * j] = 0.0f;
+    }
 }
 
 // sum of the FP32 channel partial products at one row (FP32 form: they carry
@@ -456,12 +474,14 @@ __device__ __forceinline__ void alpha_ff(ff nn, double level, double& alpha, int
 }
 
 // Whole step of one problem in one block, U streamed through shared memory:
-// each Gram-Schmidt pass (U^T p, or p -= U c) reads the columns of Uf in
-// chunks of CW columns that bulk copies (cp.async.bulk, the TMA engine)
-// bring into SHORT_TMA_S rotating stage buffers, completing on one mbarrier
-// per stage, while the warps work on the previous chunk.  A dot product pass
-// gives each column 16 / CW warps (partial sums, reduced in fixed order at the
-// end of the pass); an update pass keeps each thread's rows' running sums in
+// each Gram-Schmidt pass (U^T p, or p -= U c) reads the columns in chunks
+// that bulk copies (cp.async.bulk, the TMA engine) bring into SHORT_TMA_S
+// rotating stage buffers, completing on one mbarrier per stage, while the
+// warps work on the previous chunk.  A float-float pass brings cw columns of
+// both parts per chunk, an FP32 pass 2 cw columns of the hi part (the same
+// bytes: half the chunks).  A dot product pass gives each column 16 /
+// (columns per chunk) warps (partial sums, reduced in fixed order at the end
+// of the pass); an update pass keeps each thread's rows' running sums in
 // registers across the chunks.
 constexpr int SHORT_TMA_NT = 512;
 constexpr int MBAR_POLL_LIMIT_SHORT = 1 << 22;
@@ -470,79 +490,99 @@ constexpr int SHORT_TMA_RPP = SHORT_FUSED_MAX / (2 * SHORT_TMA_NT);   // row pai
 __device__ int g_short_tma_timeouts;
 
 struct ShortStream {
-  float2* stage;      // stage s, column ci of its chunk at stage + (s * cw + ci) * sld
+  float* stage;       // stage s: 2 cw columns of sld floats at stage + s * 2 cw sld
   int64_t sld;        // column stride of the stage buffers (the launch's largest ldf)
   uint64_t* bar;      // one mbarrier per stage
-  int cw;             // columns per chunk
+  int cw;             // float-float columns per chunk
   uint32_t g;         // chunks consumed so far, over all passes: chunk g used stage
                       // g % S in its (g / S)-th phase
 };
 
-// chunk q of a pass (columns [q cw, min(j, q cw + cw)) of Uf) into stage
-// (g0 + q) % S; one thread
-__device__ __forceinline__ void short_issue(const ShortItem& it, const ShortStream& ss, uint32_t g0, int q, int j) {
+// chunk q of a pass (columns [q w, min(j, q w + w)) of the pass's chunk
+// width w) into stage (g0 + q) % S; FF: the hi parts, then the lo parts.
+// One thread.
+template <bool FF>
+__device__ __forceinline__ void short_issue(const ShortItem& it, const ShortStream& ss, uint32_t g0, int q, int j,
+                                            int w) {
   const int s = (int)((g0 + q) % SHORT_TMA_S);
-  const int c0 = q * ss.cw, cn = min(ss.cw, j - c0);
-  const uint32_t bytes = (uint32_t)(sizeof(float2) * it.ldf);
+  const int c0 = q * w, cn = min(w, j - c0);
+  const uint32_t bytes = (uint32_t)(sizeof(float) * it.ldf);
+  float* dst = ss.stage + (int64_t)s * 2 * ss.cw * ss.sld;
   // the stage was last read by generic loads: order them before the async writes
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_arrive_expect(&ss.bar[s], bytes * (uint32_t)cn);
-  for (int ci = 0; ci < cn; ++ci)
-    bulk_copy(ss.stage + ((int64_t)s * ss.cw + ci) * ss.sld, it.Uf + it.ldf * (c0 + ci), bytes, &ss.bar[s]);
+  mbar_arrive_expect(&ss.bar[s], bytes * (uint32_t)cn * (FF ? 2u : 1u));
+  for (int ci = 0; ci < cn; ++ci) {
+    bulk_copy(dst + (int64_t)ci * ss.sld, it.Uh + it.ldf * (c0 + ci), bytes, &ss.bar[s]);
+    if (FF) bulk_copy(dst + (int64_t)(w + ci) * ss.sld, it.Ul + it.ldf * (c0 + ci), bytes, &ss.bar[s]);
+  }
 }
 
 // One pass over columns [0, j) in one of four forms:
 //   SP_DOT_FF / SP_DOT_32: part[i * wpc + slot] = partial sums of U[:, i]^T p
-//     (float-float, or FP32 from the hi parts);
+//     (float-float, or FP32 from the hi parts of U and p);
 //   SP_UPD_FF / SP_UPD_32: acc += (U c) for the thread's row pairs
 //     (2 (threadIdx.x + m NT), + 1), m < RPP.
-// Rows go in pairs (one 16-byte load of two float-float values); an odd Ls
-// has a zero pad row in p and in every column of Uf.  Ends with the block
-// synchronised.
+// The FP32 dot pass takes rows in fours (16-byte loads of the hi part), the
+// others in pairs; p and every column of U have zero pad rows up to ldf.
+// Ends with the block synchronised.
 enum ShortPass { SP_DOT_FF, SP_DOT_32, SP_UPD_FF, SP_UPD_32 };
+
+// columns per chunk of a pass: cw float-float, else 2 cw hi parts (at most 16:
+// a dot pass gives each column at least one warp)
+template <int MODE>
+__device__ __forceinline__ int pass_width(const ShortStream& ss) {
+  return (MODE == SP_DOT_FF || MODE == SP_UPD_FF) ? ss.cw : min(2 * ss.cw, SHORT_TMA_NT / 32);
+}
 
 template <int MODE, int RPP>
 __device__ __forceinline__ void short_pass(const ShortItem& it, ShortStream& ss, int j, int Ls, const float2* p,
                                            const float2* c, float2* part, ffacc (&acc)[2 * RPP],
                                            float (&acc32)[2 * RPP]) {
   constexpr bool DOTS = MODE == SP_DOT_FF || MODE == SP_DOT_32;
-  const int nch = (j + ss.cw - 1) / ss.cw;
+  constexpr bool FF = MODE == SP_DOT_FF || MODE == SP_UPD_FF;
+  const int w = pass_width<MODE>(ss);
+  const int nch = (j + w - 1) / w;
   if (nch == 0) return;
   const uint32_t g0 = ss.g;
   if (threadIdx.x == 0)
-    for (int q = 0; q < min(SHORT_TMA_S, nch); ++q) short_issue(it, ss, g0, q, j);
-  const int wpc = (SHORT_TMA_NT / 32) / ss.cw;
+    for (int q = 0; q < min(SHORT_TMA_S, nch); ++q) short_issue<FF>(it, ss, g0, q, j, w);
+  const int wpc = (SHORT_TMA_NT / 32) / w;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int np2 = (Ls + 1) >> 1;
+  const int np2 = (Ls + 1) >> 1, np4 = (Ls + 3) >> 2;
   const float4* p4 = reinterpret_cast<const float4*>(p);
   for (int q = 0; q < nch; ++q) {
     const uint32_t gq = g0 + q;
     const int s = (int)(gq % SHORT_TMA_S);
     if (!mbar_wait_bounded(&ss.bar[s], (gq / SHORT_TMA_S) & 1u, MBAR_POLL_LIMIT_SHORT) && threadIdx.x == 0)
       atomicAdd(&g_short_tma_timeouts, 1);
-    const float2* buf = ss.stage + (int64_t)s * ss.cw * ss.sld;
-    const int c0 = q * ss.cw, cn = min(ss.cw, j - c0);
+    const float* buf = ss.stage + (int64_t)s * 2 * ss.cw * ss.sld;
+    const int c0 = q * w, cn = min(w, j - c0);
     if (DOTS) {
       const int ci = warp / wpc, slot = warp - ci * wpc;
       if (ci < cn) {
-        const float4* col = reinterpret_cast<const float4*>(buf + ci * ss.sld);
         float2 v;
         if (MODE == SP_DOT_FF) {
+          const float2* ch = reinterpret_cast<const float2*>(buf + (int64_t)ci * ss.sld);
+          const float2* cl = reinterpret_cast<const float2*>(buf + (int64_t)(w + ci) * ss.sld);
           ffacc a0, a1;
           for (int t = slot * 32 + lane; t < np2; t += 32 * wpc) {
-            const float4 u = col[t], w = p4[t];
-            a0.fma(u.x, u.y, w.x, w.y);
-            a1.fma(u.z, u.w, w.z, w.w);
+            const float2 uh = ch[t], ul = cl[t];
+            const float4 pv = p4[t];
+            a0.fma(uh.x, ul.x, pv.x, pv.y);
+            a1.fma(uh.y, ul.y, pv.z, pv.w);
           }
           a0.add(a1);
           a0 = warp_sum_ff(a0);
           v = make_float2(a0.s, a0.c);
         } else {
+          const float4* ch = reinterpret_cast<const float4*>(buf + (int64_t)ci * ss.sld);
           float a0 = 0.0f, a1 = 0.0f;
-          for (int t = slot * 32 + lane; t < np2; t += 32 * wpc) {
-            const float4 u = col[t], w = p4[t];
-            a0 = fmaf(u.x, w.x, a0);
-            a1 = fmaf(u.z, w.z, a1);
+          for (int t = slot * 32 + lane; t < np4; t += 32 * wpc) {
+            const float4 uh = ch[t], p0 = p4[2 * t], p1 = p4[2 * t + 1];
+            a0 = fmaf(uh.x, p0.x, a0);
+            a1 = fmaf(uh.y, p0.z, a1);
+            a0 = fmaf(uh.z, p1.x, a0);
+            a1 = fmaf(uh.w, p1.z, a1);
           }
           a0 += a1;
 #pragma unroll
@@ -554,25 +594,27 @@ __device__ __forceinline__ void short_pass(const ShortItem& it, ShortStream& ss,
     } else {
       for (int ci = 0; ci < cn; ++ci) {
         const float2 cc = c[c0 + ci];
-        const float4* col = reinterpret_cast<const float4*>(buf + ci * ss.sld);
+        const float2* ch = reinterpret_cast<const float2*>(buf + (int64_t)ci * ss.sld);
+        const float2* cl = reinterpret_cast<const float2*>(buf + (int64_t)(w + ci) * ss.sld);
 #pragma unroll
         for (int m = 0; m < RPP; ++m) {
           const int t = threadIdx.x + m * SHORT_TMA_NT;
           if (t < np2) {
-            const float4 u = col[t];
+            const float2 uh = ch[t];
             if (MODE == SP_UPD_FF) {
-              acc[2 * m].fma(u.x, u.y, cc.x, cc.y);
-              acc[2 * m + 1].fma(u.z, u.w, cc.x, cc.y);
+              const float2 ul = cl[t];
+              acc[2 * m].fma(uh.x, ul.x, cc.x, cc.y);
+              acc[2 * m + 1].fma(uh.y, ul.y, cc.x, cc.y);
             } else {
-              acc32[2 * m] = fmaf(u.x, cc.x, acc32[2 * m]);
-              acc32[2 * m + 1] = fmaf(u.z, cc.x, acc32[2 * m + 1]);
+              acc32[2 * m] = fmaf(uh.x, cc.x, acc32[2 * m]);
+              acc32[2 * m + 1] = fmaf(uh.y, cc.x, acc32[2 * m + 1]);
             }
           }
         }
       }
     }
     __syncthreads();                      // every warp is done with stage s
-    if (threadIdx.x == 0 && q + SHORT_TMA_S < nch) short_issue(it, ss, g0, q + SHORT_TMA_S, j);
+    if (threadIdx.x == 0 && q + SHORT_TMA_S < nch) short_issue<FF>(it, ss, g0, q + SHORT_TMA_S, j, w);
   }
   ss.g = g0 + (uint32_t)nch;
 }
@@ -584,7 +626,7 @@ __device__ __forceinline__ void short_dots_tma(const ShortItem& it, ShortStream&
   ffacc none[2];
   float none32[2];
   short_pass<MODE, 1>(it, ss, j, Ls, p, c, part, none, none32);
-  const int wpc = (SHORT_TMA_NT / 32) / ss.cw;
+  const int wpc = (SHORT_TMA_NT / 32) / pass_width<MODE>(ss);
   for (int i = threadIdx.x; i < j; i += SHORT_TMA_NT) {
     ffacc a;
     for (int sl = 0; sl < wpc; ++sl) {    // fixed order
@@ -651,9 +693,9 @@ __global__ void __launch_bounds__(SHORT_TMA_NT) k_short_fused_ff(const ShortItem
   __shared__ double alpha_s;
   __shared__ float2 inv_s;
   const int Ls = (int)it.Ls;
-  float2* p = smf;                                            // sld values (a zero pad row when Ls is odd)
+  float2* p = smf;                                            // sld values (zero pad rows up to ldf)
   ShortStream ss;
-  ss.stage = smf + sld;                                       // S cw sld values
+  ss.stage = reinterpret_cast<float*>(smf + sld);            // S 2 cw sld floats
   ss.sld = sld;
   ss.bar = bar;
   ss.cw = cw;
@@ -694,7 +736,9 @@ __global__ void __launch_bounds__(SHORT_TMA_NT) k_short_fused_ff(const ShortItem
   if (threadIdx.x == 0) short_coef(it, st, j, ok_s != 0, alpha_s);
 }
 
-// shared memory of k_short_fused_ff for stage column stride sld and cw columns per chunk
+// shared memory of k_short_fused_ff for stage column stride sld and cw
+// float-float columns per chunk: p (sld float-float values), the stages
+// (S x 2 cw x sld floats) and the dot partials
 static size_t short_tma_smem(int64_t sld, int cw) {
   return sizeof(float2) * ((size_t)sld * (1 + SHORT_TMA_S * (size_t)cw) + (size_t)(KMAX + 1) * (16 / cw));
 }
@@ -728,7 +772,8 @@ __global__ void __launch_bounds__(SHORT_RB) k_short1_ff(const ShortItem* __restr
   }
   pv[threadIdx.x] = v;
   __syncthreads();
-  dots_ff<SHORT_RB>(it.Uf, it.ldf, r0, pv, nrows, j, reinterpret_cast<float2*>(it.cpa) + (int64_t)blk * (KMAX + 1));
+  dots_ff<SHORT_RB>(it.Uh, it.Ul, it.ldf, r0, pv, nrows, j,
+                    reinterpret_cast<float2*>(it.cpa) + (int64_t)blk * (KMAX + 1));
 }
 
 template <int PASS>
@@ -759,7 +804,7 @@ __global__ void __launch_bounds__(SHORT_RB) k_short23_ff(const ShortItem* __rest
   float2 val = make_float2(0.0f, 0.0f);
   if ((int)threadIdx.x < nrows) {
     const int row = threadIdx.x;
-    const ff sv = update_row_ff(it.Uf + r0 + row, it.ldf, j, c);
+    const ff sv = update_row_ff(it.Uh + r0 + row, it.Ul + r0 + row, it.ldf, j, c);
     const ff v = ff_add(ff{p[row].x, p[row].y}, ff_neg(sv));
     val = make_float2(v.hi, v.lo);
     p[row] = val;
@@ -768,7 +813,8 @@ __global__ void __launch_bounds__(SHORT_RB) k_short23_ff(const ShortItem* __rest
   if (PASS == 2) {
     pv[threadIdx.x] = val;
     __syncthreads();
-    dots_ff<SHORT_RB>(it.Uf, it.ldf, r0, pv, nrows, j, reinterpret_cast<float2*>(it.cpb) + (int64_t)blk * (KMAX + 1));
+    dots_ff<SHORT_RB>(it.Uh, it.Ul, it.ldf, r0, pv, nrows, j,
+                      reinterpret_cast<float2*>(it.cpb) + (int64_t)blk * (KMAX + 1));
   } else {
     const ff tot = block_sum_ffv<SHORT_RB>(nn, red);
     if (threadIdx.x == 0) reinterpret_cast<float2*>(it.npart)[blk] = make_float2(tot.hi, tot.lo);
@@ -823,14 +869,16 @@ __global__ void __launch_bounds__(256) k_uf_sync(const ShortItem* __restrict__ i
   const int64_t n = it.ldf * (int64_t)ncols[blockIdx.y];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / it.ldf, row = e - c * it.ldf;
-    it.Uf[row + it.ldf * c] = row < it.Ls ? ff_from_double(it.U[row + it.ldu * c]) : make_float2(0.0f, 0.0f);
+    const float2 v = row < it.Ls ? ff_from_double(it.U[row + it.ldu * c]) : make_float2(0.0f, 0.0f);
+    it.Uh[row + it.ldf * c] = v.x;
+    it.Ul[row + it.ldf * c] = v.y;
   }
 }
 
 void launch_short_fused_ff(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st) {
   if (n <= 0) return;
-  const int64_t sld = (max_ls + 1) & ~int64_t(1);
-  // chunks of about 32 KB: cw = the largest power of two <= 32 KB / column, in [1, 16]
+  const int64_t sld = (max_ls + 3) & ~int64_t(3);
+  // chunks of about 32 KB: cw = the largest power of two <= 32 KB / (8 bytes x column), in [1, 16]
   int cw = 1;
   while (cw < 16 && (int64_t)sizeof(float2) * sld * (2 * cw) <= 32768) cw *= 2;
   const size_t sm = short_tma_smem(sld, cw);

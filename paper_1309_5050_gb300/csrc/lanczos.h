@@ -23,8 +23,9 @@ constexpr int KMAX = 112;       // largest Krylov dimension (small SVD in shared
 struct ShortItem {
   LzState* st;
   double* U; int64_t ldu;                 // Ls x (k+1), FP64
-  float2* Uf; int64_t ldf;                // FP32 form: float-float copy of U (ldf = Ls rounded up to
-                                          // even: 16-byte aligned columns), else null
+  float* Uh; float* Ul; int64_t ldf;      // FP32 form: float-float copy of U as hi and lo parts
+                                          // (ldf = Ls rounded up to a multiple of four, zero pad
+                                          // rows: 16-byte aligned columns), else null
   const void* parts; int64_t part_ld;     // n_part partial products (type of the matvec)
   int32_t n_part; int32_t parts_double;
   double* p;                              // work vector, Ls
@@ -138,12 +139,12 @@ void launch_short_steps(const ShortItem* items, const int32_t* tpre, int n, int 
 // short-side step in one block per problem (items: only those problems).
 constexpr int SHORT_FUSED_MAX = 4096;
 void launch_short_fused(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st);
-// The same steps in float-float arithmetic on U's copy Uf (the FP32 form; see
-// ff.cuh): p, the Gram-Schmidt coefficients and the partial sums are
-// float-float, u_j is written to U and Uf.
+// The same steps in float-float arithmetic on U's copy (Uh, Ul) (the FP32
+// form; see ff.cuh): p, the Gram-Schmidt coefficients and the partial sums
+// are float-float, u_j is written to U, Uh and Ul.
 void launch_short_steps_ff(const ShortItem* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
 void launch_short_fused_ff(const ShortItem* items, int n, int64_t max_ls, int s, cudaStream_t st);
-// Uf[:, 0:ncols[i]] <- U[:, 0:ncols[i]] of item i (after a restart or a
+// (Uh, Ul)[:, 0:ncols[i]] <- U[:, 0:ncols[i]] of item i (after a restart or a
 // resumed decomposition rewrote U in FP64)
 void launch_uf_sync(const ShortItem* items, const int32_t* ncols, int n, cudaStream_t st);
 // Bulk-copy waits of the float-float short side that gave up since the last call
