@@ -520,12 +520,14 @@ __device__ __forceinline__ void short_issue(const ShortItem& it, const ShortStre
 // One pass over columns [0, j) in one of four forms:
 //   SP_DOT_FF / SP_DOT_32: part[i * wpc + slot] = partial sums of U[:, i]^T p
 //     (float-float, or FP32 from the hi parts of U and p);
-//   SP_UPD_FF / SP_UPD_32: acc += (U c) for the thread's row pairs
-//     (2 (threadIdx.x + m NT), + 1), m < RPP.
+//   SP_UPD_FF / SP_UPD_32 / SP_UPD_FC: acc += (U c) for the thread's row
+//     pairs (2 (threadIdx.x + m NT), + 1), m < RPP: float-float, or FP32
+//     from the hi parts (SP_UPD_FC subtracts that FP32 sum from the
+//     float-float p exactly, see k_short_fused_ff).
 // The FP32 dot pass takes rows in fours (16-byte loads of the hi part), the
 // others in pairs; p and every column of U have zero pad rows up to ldf.
 // Ends with the block synchronised.
-enum ShortPass { SP_DOT_FF, SP_DOT_32, SP_UPD_FF, SP_UPD_32 };
+enum ShortPass { SP_DOT_FF, SP_DOT_32, SP_UPD_FF, SP_UPD_32, SP_UPD_FC };
 
 // columns per chunk of a pass: cw float-float, else 2 cw hi parts (at most 16:
 // a dot pass gives each column at least one warp)
@@ -605,7 +607,7 @@ __device__ __forceinline__ void short_pass(const ShortItem& it, ShortStream& ss,
               const float2 ul = cl[t];
               acc[2 * m].fma(uh.x, ul.x, cc.x, cc.y);
               acc[2 * m + 1].fma(uh.y, ul.y, cc.x, cc.y);
-            } else {
+            } else {                      // SP_UPD_32, SP_UPD_FC
               acc32[2 * m] = fmaf(uh.x, cc.x, acc32[2 * m]);
               acc32[2 * m + 1] = fmaf(uh.y, cc.x, acc32[2 * m + 1]);
             }
@@ -661,6 +663,10 @@ __device__ __forceinline__ ff short_update_tma(const ShortItem& it, ShortStream&
         const ff v0 = ff_add(ff{w.x, w.y}, ff_neg(acc[2 * m].value()));
         const ff v1 = ff_add(ff{w.z, w.w}, ff_neg(acc[2 * m + 1].value()));
         w = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+      } else if (MODE == SP_UPD_FC) {
+        const ff v0 = ff_add(ff{w.x, w.y}, ff{-acc32[2 * m], 0.0f});
+        const ff v1 = ff_add(ff{w.z, w.w}, ff{-acc32[2 * m + 1], 0.0f});
+        w = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
       } else {
         w = make_float4(w.x - acc32[2 * m], 0.0f, w.z - acc32[2 * m + 1], 0.0f);
       }
@@ -676,8 +682,10 @@ __device__ __forceinline__ ff short_update_tma(const ShortItem& it, ShortStream&
 // products carry FP32 error already, so its rounding costs nothing the data
 // resolves), then a float-float pass, whose dot products measure what the
 // first left along U; its update runs unless that is below 1e-12 ||p|| (the
-// criterion of Daniel, Gragg, Kaufman and Stewart).  RPP: row pairs per
-// thread, 2 RPP NT >= every item's Ls.
+// criterion of Daniel, Gragg, Kaufman and Stewart), and in FP32 products of
+// the hi parts subtracted exactly from the float-float p when the remainder
+// is at most 1e-6 ||p|| (the usual case: the first pass leaves about 6e-8).
+// RPP: row pairs per thread, 2 RPP NT >= every item's Ls.
 template <int RPP>
 __global__ void __launch_bounds__(SHORT_TMA_NT) k_short_fused_ff(const ShortItem* __restrict__ items, int s,
                                                                  int64_t sld, int cw) {
@@ -713,10 +721,15 @@ __global__ void __launch_bounds__(SHORT_TMA_NT) k_short_fused_ff(const ShortItem
   if (threadIdx.x == 0) {
     float cc = 0.0f;
     for (int i = 0; i < j; ++i) cc = fmaf(c[i].x, c[i].x, cc);
-    second = cc > 1e-24f * nn.hi;
+    // 0: nothing left along U; 1: ||c|| <= 1e-6 ||p||, so FP32 products of
+    // the hi parts carry U c to within sqrt(j) eps32 ||c||: below 1e-12 ||p||
+    // at worst, about 3e-14 ||p|| in the usual case (||c|| near 6e-8 ||p||);
+    // U's lo parts and c's low bits contribute less; 2: float-float
+    second = cc > 1e-24f * nn.hi ? (cc > 1e-12f * nn.hi ? 2 : 1) : 0;
   }
   __syncthreads();
-  if (second) nn = short_update_tma<SP_UPD_FF, RPP>(it, ss, j, Ls, p, c, part, red);
+  if (second == 1) nn = short_update_tma<SP_UPD_FC, RPP>(it, ss, j, Ls, p, c, part, red);
+  else if (second == 2) nn = short_update_tma<SP_UPD_FF, RPP>(it, ss, j, Ls, p, c, part, red);
   if (threadIdx.x == 0) { double a; int o; float2 iv; alpha_ff(nn, level, a, o, iv); alpha_s = a; ok_s = o; inv_s = iv; }
   __syncthreads();
   if (!ok_s) {
