@@ -1144,7 +1144,7 @@ struct LzEngine {
   SvdItem svd_item(ssa_ctx* c) {
     Workspace& w = c->ws;
     SvdItem v;
-    v.st = w.st; v.B = w.B; v.ldb = w.k; v.pad_ = 0; v.colscale = w.colscale; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
+    v.st = w.st; v.B = w.B; v.ldb = w.k; v.ffpolish = std::is_same<T, float>::value; v.colscale = w.colscale; v.sig = w.sig; v.P = w.P; v.Q = w.Q;
     return v;
   }
   RitzItem<T> ritz_item(ssa_ctx* c) {

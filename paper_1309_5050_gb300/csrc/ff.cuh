@@ -109,6 +109,31 @@ __device__ __forceinline__ float2 ff_from_double(double d) {
   }
   return make_float2(hi, lo);
 }
+// d 2^-shift as hi + lo (the same split, with the exponent lowered by shift
+// first; integer instructions only)
+__device__ __forceinline__ float2 ff_from_double_scaled(double d, int shift) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FFull);
+  if (e == 0) return make_float2(0.0f, 0.0f);                    // zero (denormals flushed)
+  const int es = e - shift;
+  if (es < 1) return make_float2(0.0f, 0.0f);
+  const unsigned long long bs = (b & ~(0x7FFull << 52)) | ((unsigned long long)es << 52);
+  return ff_from_double(__longlong_as_double((long long)bs));
+}
+
+// sum over the lanes of a team of W consecutive lanes (W a power of two <= 32)
+template <int W>
+__device__ __forceinline__ ffacc team_sum_ff(ffacc a) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    ffacc b;
+    b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+    b.c = __shfl_xor_sync(0xffffffffu, a.c, o);
+    a.add(b);
+  }
+  return a;
+}
+
 // the double nearest hi + lo (two conversions and an FP64 add: off the hot loops)
 __device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
 

@@ -1066,6 +1066,277 @@ __device__ __forceinline__ void jacobi_pair(int t, int rd, int n2, int nc, int& 
   if (a >= nc || b >= nc) a = b = -1;
 }
 
+// FP32 form: the polish of k_bsvd (from W = W0 V' on) in float-float
+// arithmetic on the FP32 pipes instead of FP64 -- the one-sided Jacobi
+// sweeps, the column norms, the Newton-Schulz step on the left vectors and
+// the products for Q.  A phase-stamped build of k_bsvd put the FP64 sweeps
+// at half its time (1.5 M of 3.1 M cycles at batch 456), paced by GB300's
+// FP64 pipe whether a round rotated or only tested.  Float-float carries
+// about 48 bits, far inside the sweeps' stopping cosine (jtol = 1e-10 in
+// this form) and the left vectors' orthogonality after the Newton-Schulz
+// step.  W is scaled by a power of two (largest entry in [1, 2)) before the
+// split, so that FP32 exponents hold it, and the norms are scaled back.
+// Rotations: the tangent t in FP32 from the float-float norms and dot
+// product (as in the FP64 form, the next sweep removes what an FP32 angle
+// leaves), the cosine and sine in float-float from t -- 1 - t^2 / 2 below
+// |t| = 1e-4 (the next term is below 4e-17), else 1 / sqrt(1 + t^2) by one
+// Newton step on rsqrtf -- so each rotation is orthogonal to float-float
+// rounding.  Teams of 16 lanes per column pair, as in the FP32 sweeps.
+__device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool aug, int cs, int lv, double* W,
+                             const double* bp, int bld, float jtol, int nkeep_fast, int sweeps32, double* sm,
+                             double* nrm2d, double* nrm, int* order, unsigned char* keep, int* rotated) {
+  float2* W2 = reinterpret_cast<float2*>(W);   // column c at W2 + c * cs (the FP64 layout)
+  float2* nrm2 = reinterpret_cast<float2*>(nrm2d);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int team = lane / BSVD_T32, q = lane % BSVD_T32;
+  const int nteams = nw * (32 / BSVD_T32);
+  const int n2 = nc + (nc & 1);
+  __shared__ int ex_s;
+
+  // 1. scale: the largest |W| as a bit pattern (non-negative doubles order like
+  //    their patterns), its binary exponent, then W 2^-ex split in place
+  {
+    long long mb = 0;
+    for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+      const int c = e / k, i = e - c * k;
+      const long long b = __double_as_longlong(W[c * cs + i]) & 0x7FFFFFFFFFFFFFFFll;
+      mb = b > mb ? b : mb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long v = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = v > mb ? v : mb;
+    }
+    if (threadIdx.x == 0) ex_s = 0;
+    __syncthreads();
+    if (lane == 0) atomicMax(&ex_s, (int)((mb >> 52) & 0x7FF));   // exponent field of the largest entry
+    __syncthreads();
+  }
+  const int ex = ex_s > 0 ? ex_s - 1023 : 0;   // W 2^-ex has its largest entry in [1, 2)
+  for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    W2[c * cs + i] = ff_from_double_scaled(W[c * cs + i], ex);
+  }
+  __syncthreads();
+
+  // 2. sweeps
+  int sweeps = 0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    sweeps = sweep + 1;
+    const int nkeep = sweep < 6 ? nkeep_fast : nc;
+    for (int c = warp; c < nc; c += nw) {
+      const float2* w = W2 + c * cs;
+      ffacc a;
+      for (int i = lane; i < k; i += 32) a.fma(w[i], w[i]);
+      const ff v = warp_sum_ff(a).value();
+      if (lane == 0) nrm2[c] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    // ranks by the hi parts (non-negative floats order like their patterns)
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const int v = __float_as_int(nrm2[c].x);
+      int rk = 0;
+      for (int b = 0; b < nc; ++b) {
+        const int u = __float_as_int(nrm2[b].x);
+        rk += (u > v) || (u == v && b < c);
+      }
+      keep[c] = rk < nkeep;
+    }
+    if (threadIdx.x == 0) *rotated = 0;
+    __syncthreads();
+    for (int rd = 0; rd < n2 - 1; ++rd) {
+      for (int t0 = warp * (32 / BSVD_T32); t0 < n2 / 2; t0 += nteams) {
+        int a, b;
+        jacobi_pair(t0 + team, rd, n2, nc, a, b);
+        if (a >= 0 && !keep[a] && !keep[b]) a = b = -1;
+        float2* __restrict__ wa = W2 + (a < 0 ? 0 : a) * cs;
+        float2* __restrict__ wb = W2 + (b < 0 ? 0 : b) * cs;
+        ffacc g;
+        if (a >= 0)
+          for (int i = q; i < k; i += BSVD_T32) g.fma(wa[i], wb[i]);
+        const ff ga = team_sum_ff<BSVD_T32>(g).value();
+        bool rot = false;
+        float tt = 0.0f;
+        ff al{0.0f, 0.0f}, be{0.0f, 0.0f};
+        if (a >= 0) {
+          al = ff{nrm2[a].x, nrm2[a].y};
+          be = ff{nrm2[b].x, nrm2[b].y};
+          rot = ga.hi != 0.0f && al.hi > 0.0f && be.hi > 0.0f && fabsf(ga.hi) > jtol * sqrtf(al.hi) * sqrtf(be.hi);
+        }
+        if (rot) {
+          const float dz = ff_add(be, ff_neg(al)).hi, g2 = 2.0f * ga.hi;
+          const float zeta = dz / g2, az = fabsf(zeta);
+          tt = az > 1e18f ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+          if (!(fabsf(tt) > 0.0f && fabsf(tt) <= 2.0f)) rot = false;
+        }
+        if (rot) {
+          ff cn;
+          float p2, e2;                   // t^2 = p2 + e2 exactly
+          p2 = tt * tt;
+          e2 = __fmaf_rn(tt, tt, -p2);
+          if (fabsf(tt) < 1e-4f) {
+            cn = ff_add(ff{1.0f, 0.0f}, ff{-0.5f * p2, -0.5f * e2});
+          } else {
+            const ff x = ff_add(ff{1.0f, 0.0f}, ff{p2, e2});      // 1 + t^2
+            const float y0 = rsqrtf(x.hi);
+            const ff r = ff_mul(x, ff_mul(ff{y0, 0.0f}, ff{y0, 0.0f}));
+            const float er = ff_add(ff{1.0f, 0.0f}, ff_neg(r)).hi;   // 1 - x y0^2, near FP32 rounding
+            cn = ff_add(ff{y0, 0.0f}, ff{0.5f * y0 * er, 0.0f});
+          }
+          const ff sn = ff_mul(cn, ff{tt, 0.0f});
+          for (int m = q; m < k; m += BSVD_T32) {
+            const ff x{wa[m].x, wa[m].y}, y{wb[m].x, wb[m].y};
+            const ff xa = ff_add(ff_mul(cn, x), ff_neg(ff_mul(sn, y)));
+            const ff yb = ff_add(ff_mul(sn, x), ff_mul(cn, y));
+            wa[m] = make_float2(xa.hi, xa.lo);
+            wb[m] = make_float2(yb.hi, yb.lo);
+          }
+        }
+        __syncwarp();   // every lane of the team has read the old norms
+        if (rot && q == 0) {
+          const ff tg = ff_mul(ff{tt, 0.0f}, ga);
+          const ff na = ff_add(al, ff_neg(tg)), nb = ff_add(be, tg);
+          nrm2[a] = make_float2(na.hi, na.lo);
+          nrm2[b] = make_float2(nb.hi, nb.lo);
+          *rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = *rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+
+  // 3. norms (scaled back), order, 1 / sigma; columns normalised in place
+  double* inv = nrm2d;                 // reused: the squared norms are dead
+  __shared__ float2 invs[KMAX + 2];    // 1 / (scaled norm) as float-float
+  for (int c = warp; c < nc; c += nw) {
+    const float2* w = W2 + c * cs;
+    ffacc a;
+    for (int i = lane; i < k; i += 32) a.fma(w[i], w[i]);
+    const ff v = warp_sum_ff(a).value();
+    if (lane == 0) {
+      const double ns = sqrt(fmax(ff_to_double(make_float2(v.hi, v.lo)), 0.0));   // scaled norm
+      nrm[c] = ldexp(ns, ex);
+      invs[c] = ns > 0.0 ? ff_from_double(1.0 / ns) : make_float2(0.0f, 0.0f);
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const long long v = __double_as_longlong(nrm[c]);
+    int rk = 0;
+    for (int b = 0; b < nc; ++b) {
+      const long long u = __double_as_longlong(nrm[b]);
+      rk += (u > v) || (u == v && b < c);
+    }
+    order[rk] = c;
+    inv[c] = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
+  }
+  for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+    const int c = e / k, i = e - c * k;
+    const ff p = ff_mul(ff{W2[c * cs + i].x, W2[c * cs + i].y}, ff{invs[c].x, invs[c].y});
+    W2[c * cs + i] = make_float2(p.hi, p.lo);
+  }
+  __syncthreads();
+
+  // 4. one Newton-Schulz step on the left vectors P: P - P F / 2 with
+  //    F = P^T P - I summed in float-float (F is of the size of jtol, so P F in FP32)
+  {
+    float* F32 = reinterpret_cast<float*>(sm);                   // nc x lv
+    float* P32 = F32 + (size_t)nc * lv;                           // nc x cs
+    for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+      const int c = e / k, i = e - c * k;
+      P32[c * cs + i] = W2[c * cs + i].x;
+    }
+    for (int pr = warp; pr < nc * nc; pr += nw) {
+      const int a = pr / nc, b = pr - a * nc;
+      if (b < a) continue;
+      const float2* pa = W2 + a * cs;
+      const float2* pb = W2 + b * cs;
+      ffacc f;
+      for (int i = lane; i < k; i += 32) f.fma(pa[i], pb[i]);
+      const ff v = warp_sum_ff(f).value();
+      if (lane == 0) {
+        const float fv = ff_add(v, ff{a == b ? -1.0f : 0.0f, 0.0f}).hi;
+        F32[b * lv + a] = fv;
+        F32[a * lv + b] = fv;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+      const int c = e / k, i = e - c * k;
+      float acc = 0.0f;
+      for (int jj = 0; jj < nc; ++jj) acc = fmaf(P32[jj * cs + i], F32[c * lv + jj], acc);
+      const ff p = ff_add(ff{W2[c * cs + i].x, W2[c * cs + i].y}, ff{-0.5f * acc, 0.0f});
+      W2[c * cs + i] = make_float2(p.hi, p.lo);
+    }
+    __syncthreads();
+  }
+
+  // 5. outputs: P_i = W_{o(i)}, sigma, Q_i = W0^T P_i / sigma_i
+  const int kd = it.ldb, kq = it.ldb + 1;
+  for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
+    const int c = e / kd, i = e - c * kd;
+    double pv = 0.0;
+    if (c < k && i < k) pv = ff_to_double(W2[order[c] * cs + i]);
+    it.P[i + (int64_t)kd * c] = pv;
+  }
+  for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
+  for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
+    const int c = e / kq, j = e - c * kq;
+    double qv = 0.0;
+    if (c < k && j < nc) {
+      const int o = order[c];
+      const double is = inv[o];
+      if (is > 0.0) {
+        const float2* pc = W2 + o * cs;        // P column
+        ffacc acc;
+        if (j < k) {
+          const double* bc = bp + (int64_t)bld * j;
+          for (int m = 0; m <= j && m < k; ++m) {
+            const double bv = bc[m];
+            if ((__double_as_longlong(bv) << 1) != 0) acc.fma(ff_from_double_scaled(bv, ex), pc[m]);
+          }
+        } else {
+          acc.fma(ff_from_double_scaled(st->beta_k, ex), pc[k - 1]);
+        }
+        // (B 2^-ex) P_i / (sigma_i 2^-ex)
+        const ff av = acc.value();
+        qv = ff_to_double(make_float2(av.hi, av.lo)) * (is * ldexp(1.0, ex));
+      }
+    }
+    it.Q[j + (int64_t)kq * c] = qv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int r = min(st->r, k);
+    const double s1 = nrm[order[0]], is1 = inv[order[0]];
+    double mres = 0.0;
+    int nconv = 0;
+    bool conv = true;
+    for (int i = 0; i < r; ++i) {
+      const int o = order[i];
+      const double pk = ff_to_double(W2[o * cs + (k - 1)]);
+      const double res = aug ? 0.0 : fabs(st->beta_k * pk);
+      const double rel = res * is1;
+      if (rel > mres) mres = rel;
+      if (rel <= st->tol) { if (nconv == i) ++nconv; }
+      else conv = false;
+    }
+    if (st->full) { conv = true; nconv = r; }
+    st->sigma1 = s1;
+    st->maxres = mres;
+    st->sweeps = sweeps;
+    st->sweeps32 = sweeps32;
+    st->nconv = nconv;
+    st->converged = conv ? 1 : 0;
+    st->restarts += 1;
+    st->svd_done = 1;
+    if (conv || st->restarts > st->max_restarts) st->active = 0;
+  }
+}
+
 __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__ items, int b_in_smem) {
   const SvdItem it = items[blockIdx.x];
   LzState* st = it.st;
@@ -1290,6 +1561,11 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
   // started from B itself (after a failed Newton-Schulz step) ran to the
   // sweep limit at k = 112; all pairs then converge in about ten sweeps
   const int nkeep_fast = relaxed ? min(nc, max(st->kk, st->r) + 4) : nc;
+  if (it.ffpolish && relaxed) {
+    bsvd_tail_ff(it, st, k, nc, aug, cs, lv, W, bp, bld, (float)jtol, nkeep_fast, sweeps32, sm, nrm2, nrm, order, keep,
+                 &rotated);
+    return;
+  }
   int sweeps = 0;
   for (int sweep = 0; sweep < 60; ++sweep) {
     sweeps = sweep + 1;

@@ -89,7 +89,8 @@ __host__ __device__ inline BsvdLayout bsvd_layout(int k, int nc) {
 
 struct SvdItem {
   LzState* st;
-  double* B; int32_t ldb; int32_t pad_;
+  double* B; int32_t ldb;
+  int32_t ffpolish;                       // FP32 form: the polish in float-float (bsvd_tail_ff)
   double* colscale;                       // long-basis column scales (reset on restart)
   double* sig;                            // k singular values (descending)
   double* P;                              // k x k left vectors of B (ld k)
