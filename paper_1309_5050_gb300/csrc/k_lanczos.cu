@@ -1231,7 +1231,7 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
       rk += (u > v) || (u == v && b < c);
     }
     order[rk] = c;
-    inv[c] = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
+    inv[c] = nrm[c] > 0.0 ? 1.0 : 0.0;      // a nonzero flag (Q uses invs)
   }
   for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
     const int c = e / k, i = e - c * k;
@@ -1249,18 +1249,26 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
       const int c = e / k, i = e - c * k;
       P32[c * cs + i] = W2[c * cs + i].x;
     }
-    for (int pr = warp; pr < nc * nc; pr += nw) {
-      const int a = pr / nc, b = pr - a * nc;
-      if (b < a) continue;
-      const float2* pa = W2 + a * cs;
-      const float2* pb = W2 + b * cs;
-      ffacc f;
-      for (int i = lane; i < k; i += 32) f.fma(pa[i], pb[i]);
-      const ff v = warp_sum_ff(f).value();
-      if (lane == 0) {
-        const float fv = ff_add(v, ff{a == b ? -1.0f : 0.0f, 0.0f}).hi;
+    // upper triangle a <= b, one pair per thread (a whole float-float dot
+    // product each: no reductions across lanes)
+    {
+      const int npair = nc * (nc + 1) / 2;
+      int a = 0, rem = threadIdx.x, len = nc;
+      while (a < nc && rem >= len) { rem -= len; ++a; --len; }
+      for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+        const int b = a + rem;
+        const float2* pa = W2 + a * cs;
+        const float2* pb = W2 + b * cs;
+        ffacc f0, f1;
+        int i = 0;
+        for (; i + 1 < k; i += 2) { f0.fma(pa[i], pb[i]); f1.fma(pa[i + 1], pb[i + 1]); }
+        if (i < k) f0.fma(pa[i], pb[i]);
+        f0.add(f1);
+        const float fv = ff_add(f0.value(), ff{a == b ? -1.0f : 0.0f, 0.0f}).hi;
         F32[b * lv + a] = fv;
         F32[a * lv + b] = fv;
+        rem += blockDim.x;
+        while (a < nc && rem >= len) { rem -= len; ++a; --len; }
       }
     }
     __syncthreads();
@@ -1288,8 +1296,7 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
     double qv = 0.0;
     if (c < k && j < nc) {
       const int o = order[c];
-      const double is = inv[o];
-      if (is > 0.0) {
+      if (inv[o] > 0.0) {
         const float2* pc = W2 + o * cs;        // P column
         ffacc acc;
         if (j < k) {
@@ -1301,9 +1308,9 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
         } else {
           acc.fma(ff_from_double_scaled(st->beta_k, ex), pc[k - 1]);
         }
-        // (B 2^-ex) P_i / (sigma_i 2^-ex)
-        const ff av = acc.value();
-        qv = ff_to_double(make_float2(av.hi, av.lo)) * (is * ldexp(1.0, ex));
+        // (B 2^-ex) P_i / (sigma_i 2^-ex): the scaled norm's inverse invs
+        const ff av = ff_mul(acc.value(), ff{invs[o].x, invs[o].y});
+        qv = ff_to_double(make_float2(av.hi, av.lo));
       }
     }
     it.Q[j + (int64_t)kq * c] = qv;
@@ -1311,7 +1318,7 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
   __syncthreads();
   if (threadIdx.x == 0) {
     const int r = min(st->r, k);
-    const double s1 = nrm[order[0]], is1 = inv[order[0]];
+    const double s1 = nrm[order[0]], is1 = s1 > 0.0 ? 1.0 / s1 : 0.0;
     double mres = 0.0;
     int nconv = 0;
     bool conv = true;
