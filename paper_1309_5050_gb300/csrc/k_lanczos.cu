@@ -1057,12 +1057,17 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // column pair of team t in round rd of the round-robin order over n2 slots
 // (n2 even; slots >= nc are empty): -1 when the team has no pair
+// (rd < n2 - 1 and slot <= n2 - 1, so slot - 1 + rd < 2 (n2 - 1): the
+// remainder is one conditional subtraction, not an integer division)
 __device__ __forceinline__ void jacobi_pair(int t, int rd, int n2, int nc, int& a, int& b) {
   a = b = -1;
   if (t >= n2 / 2) return;
-  const int sa = t, sb = n2 - 1 - t;
-  a = (sa == 0) ? 0 : 1 + (sa - 1 + rd) % (n2 - 1);
-  b = (sb == 0) ? 0 : 1 + (sb - 1 + rd) % (n2 - 1);
+  const int m = n2 - 1, sa = t, sb = n2 - 1 - t;
+  int xa = sa - 1 + rd, xb = sb - 1 + rd;
+  xa -= xa >= m ? m : 0;
+  xb -= xb >= m ? m : 0;
+  a = (sa == 0) ? 0 : 1 + xa;
+  b = (sb == 0) ? 0 : 1 + xb;
   if (a >= nc || b >= nc) a = b = -1;
 }
 
@@ -1291,6 +1296,16 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
     it.P[i + (int64_t)kd * c] = pv;
   }
   for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
+  // first nonzero row of each column of B (upper triangular, a few nonzeros
+  // per column; the restart's arrow column reaches row 0)
+  __shared__ int bfirst[KMAX + 1];
+  for (int jj = threadIdx.x; jj < k; jj += blockDim.x) {
+    const double* bc = bp + (int64_t)bld * jj;
+    int m = 0;
+    while (m < jj && (__double_as_longlong(bc[m]) << 1) == 0) ++m;
+    bfirst[jj] = m;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
     const int c = e / kq, j = e - c * kq;
     double qv = 0.0;
@@ -1301,7 +1316,7 @@ __device__ void bsvd_tail_ff(const SvdItem& it, LzState* st, int k, int nc, bool
         ffacc acc;
         if (j < k) {
           const double* bc = bp + (int64_t)bld * j;
-          for (int m = 0; m <= j && m < k; ++m) {
+          for (int m = bfirst[j]; m <= j && m < k; ++m) {
             const double bv = bc[m];
             if ((__double_as_longlong(bv) << 1) != 0) acc.fma(ff_from_double_scaled(bv, ex), pc[m]);
           }
@@ -1768,6 +1783,15 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
     it.P[i + (int64_t)kd * c] = pv;
   }
   for (int c = threadIdx.x; c < kd; c += blockDim.x) it.sig[c] = (c < k) ? nrm[order[c]] : 0.0;
+  // first nonzero row of each column of B (upper triangular, a few nonzeros
+  // per column; the restart's arrow column reaches row 0)
+  __shared__ int bfirst[KMAX + 1];
+  for (int jj = threadIdx.x; jj < k; jj += blockDim.x) {
+    const double* bc = bp + (int64_t)bld * jj;
+    int m = 0;
+    while (m < jj && (__double_as_longlong(bc[m]) << 1) == 0) ++m;
+    bfirst[jj] = m;
+  }
   __syncthreads();
   // Q_i = W0^T P_i / sigma_i with W0 = [B | beta_k e_k]
   for (int e = threadIdx.x; e < kq * kd; e += blockDim.x) {
@@ -1783,7 +1807,7 @@ __global__ void __launch_bounds__(BSVD_NT, 2) k_bsvd(const SvdItem* __restrict__
           // B is upper triangular with a few nonzeros per column; zeros are
           // skipped by their bit pattern (no FP64 compare)
           const double* bc = bp + (int64_t)bld * j;
-          for (int m = 0; m <= j && m < k; ++m) {
+          for (int m = bfirst[j]; m <= j && m < k; ++m) {
             const double bv = bc[m];
             if ((__double_as_longlong(bv) << 1) != 0) acc = fma(bv, pc[m], acc);
           }
@@ -2063,7 +2087,7 @@ void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
   if (n <= 0) return;
   const BsvdLayout lay = bsvd_layout(kmax, kmax + 1);
   // B in shared memory when two blocks still fit on an SM
-  const int b_in_smem = 2 * (lay.bytes_b + 4096) <= (size_t)device_max_smem() ? 1 : 0;
+  const int b_in_smem = 2 * (lay.bytes_b + 8192) <= (size_t)device_max_smem() ? 1 : 0;   // (+ static shared memory)
   const size_t sm = b_in_smem ? lay.bytes_b : lay.bytes;
   set_max_smem((const void*)k_bsvd);
   k_bsvd<<<n, BSVD_NT, sm, st>>>(items, b_in_smem); count_launch();
