@@ -2043,20 +2043,19 @@ __global__ void __launch_bounds__(256) k_final_copy(const FinalItem<T>* __restri
   const int i = blockIdx.y;
   if (i >= it.r) return;
   const bool zero = i >= it.st->k;
+  // the sign is +-1: applied in T to the T-typed long basis (no FP64 per
+  // element there), in FP64 to the FP64 short basis before its conversion
   const double sg = it.sgn[i];
+  const T sgt = (T)sg;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // window side (L) and origin side (K)
   const int64_t L = it.swapped ? it.Kl : it.Ls;
   const int64_t K = it.swapped ? it.Ls : it.Kl;
-  for (int64_t t = t0; t < L; t += stride) {
-    double v = it.swapped ? (double)it.V[t + it.ldv * i] : it.U[t + it.ldu * i];
-    it.Uo[t + L * i] = zero ? T(0) : (T)(sg * v);
-  }
-  for (int64_t t = t0; t < K; t += stride) {
-    double v = it.swapped ? it.U[t + it.ldu * i] : (double)it.V[t + it.ldv * i];
-    it.Vo[t + K * i] = zero ? T(0) : (T)(sg * v);
-  }
+  for (int64_t t = t0; t < L; t += stride)
+    it.Uo[t + L * i] = zero ? T(0) : (it.swapped ? sgt * it.V[t + it.ldv * i] : (T)(sg * it.U[t + it.ldu * i]));
+  for (int64_t t = t0; t < K; t += stride)
+    it.Vo[t + K * i] = zero ? T(0) : (it.swapped ? (T)(sg * it.U[t + it.ldu * i]) : sgt * it.V[t + it.ldv * i]);
 }
 
 // ------------------------------------------------------------ launchers

@@ -110,7 +110,12 @@ __global__ void __launch_bounds__(512) k_rec1d(const Rec1Item<T, TV>* __restrict
   const T* r = reinterpret_cast<const T*>(R);
   for (int n = threadIdx.x; n < it.n; n += blockDim.x) {
     const int w = it.w[n];
-    it.out[n] = (w > 0) ? (double)r[n] / (double)w : __longlong_as_double(0x7ff8000000000000ll);
+    // FP32 sums: the division in FP32 (the sums carry FP32 error already),
+    // one conversion -- an FP64 division per element ran on GB300's FP64 pipe
+    if constexpr (std::is_same<T, float>::value)
+      it.out[n] = (w > 0) ? (double)(r[n] / (float)w) : __longlong_as_double(0x7ff8000000000000ll);
+    else
+      it.out[n] = (w > 0) ? (double)r[n] / (double)w : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -135,7 +140,10 @@ __global__ void __launch_bounds__(512) k_rec_xinv(const Rec2Item<T>* __restrict_
     const int64_t g = x + (int64_t)it.nx * y;
     if (!it.w) { it.out[g] = (double)r[x] * it.inv_norm; continue; }   // raw sums (long series)
     const int w = it.w[g];
-    it.out[g] = (w > 0) ? (double)r[x] * it.inv_norm / (double)w : __longlong_as_double(0x7ff8000000000000ll);
+    if constexpr (std::is_same<T, float>::value)   // FP32 sums: FP32 division, one conversion
+      it.out[g] = (w > 0) ? (double)(r[x] * (float)it.inv_norm / (float)w) : __longlong_as_double(0x7ff8000000000000ll);
+    else
+      it.out[g] = (w > 0) ? (double)r[x] * it.inv_norm / (double)w : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -169,14 +177,20 @@ __global__ void __launch_bounds__(256) k_rec_border(const RecBorderItem* __restr
   if (p < 0 || p >= N || (e >= REC_BORDER_W && p < REC_BORDER_W)) return;
   const int64_t i0 = p - it.K + 1 > 0 ? p - it.K + 1 : 0;
   const int64_t i1 = p < it.L - 1 ? p : it.L - 1;
-  double acc = 0.0;
-  for (int64_t i = i0 + lane; i <= i1; i += 32)
-    for (int q = 0; q < it.ncomp; ++q) {
-      const int c = it.comps[q];
-      acc = fma(it.sigma[c] * (double)it.U[i + (int64_t)it.L * c], (double)it.V[(p - i) + it.ldv * c], acc);
-    }
+  // FP32 products and sums of the FP32 vectors (at most 64 terms a
+  // component: a relative error near 64 eps32 of the terms' magnitude, far
+  // inside the form's tolerance); sigma converted once per component --
+  // GB300 runs FP64 at about 1/70 of the FP32 rate
+  float acc = 0.0f;
+  for (int q = 0; q < it.ncomp; ++q) {
+    const int c = it.comps[q];
+    const float sg = (float)it.sigma[c];
+    const float* uc = it.U + (int64_t)it.L * c;
+    const float* vc = it.V + it.ldv * c;
+    for (int64_t i = i0 + lane; i <= i1; i += 32) acc = fmaf(sg * uc[i], vc[p - i], acc);
+  }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) it.out[p] = acc / (double)(i1 - i0 + 1);
+  if (lane == 0) it.out[p] = (double)(acc / (float)(i1 - i0 + 1));
 }
 
 void launch_rec_border(const RecBorderItem* items, int n, cudaStream_t st) {
