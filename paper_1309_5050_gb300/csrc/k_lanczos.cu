@@ -1026,7 +1026,8 @@ __global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict
 //     about two sweeps and a check sweep where it needs nine from W0.
 // W0 V' J = P Sigma with V' J orthogonal to FP64 rounding is an SVD of W0,
 // so sigma, P and Q are FP64-accurate whatever the FP32 steps did (they only
-// decide how many FP64 sweeps remain).
+// decide how many FP64 sweeps remain).  The FP32 form runs step 3's sweeps
+// and what follows in float-float instead (bsvd_tail_ff), to its tolerance.
 //
 // In the FP64 sweeps one thread owns one column pair of a round-robin round
 // (dot product, rotation parameters, column update), the squared column norms
