@@ -634,6 +634,31 @@ int mv_async_timeouts(cudaStream_t st) {
 // Forward transform of u_j = U[:, jc + s] (window side, L FP64 values) on a
 // 2^log2M grid, the H packed values before the untwist, straight to global
 // memory from the last stage (one block per problem and grid size).
+// k_uspec's transform with H = 2^LOG2H fixed at compile time (512 threads)
+template <typename T, int LOG2H>
+__device__ __forceinline__ void uspec_ct(const UzItem<T>& it, int s, const Cx<T>* __restrict__ tw,
+                                         unsigned char* smem) {
+  constexpr int H = 1 << LOG2H, LOG2TN = LOG2H + 1;
+  Cx<T>* A = reinterpret_cast<Cx<T>*>(smem);
+  Cx<T>* B = A + padded_len(H);
+  Cx<T>* tab = B + padded_len(H);
+  load_octant(tab, LOG2TN, tw);
+  __syncthreads();
+  const double* src = it.U + it.ldu * (int64_t)(it.st->jc + s);
+  const int64_t xe = it.L;
+  auto in = [src, xe](int j, int r, int nq) {
+    const int64_t x = 2 * (int64_t)(j + r * nq);
+    return cx(x < xe ? (T)src[x] : T(0), x + 1 < xe ? (T)src[x + 1] : T(0));
+  };
+  Cx<T>* z = it.z;
+  auto out = [z](int base, int stride, auto& v) {
+    constexpr int R = sizeof(v) / sizeof(v[0]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[base + r * stride] = v[r];
+  };
+  block_fft_io_ct<T, false, LOG2H, 512, LOG2TN>(in, out, A, B, tab);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_uspec(const UzItem<T>* __restrict__ items, int s,
                                                                         const Cx<T>* __restrict__ tw) {
@@ -641,6 +666,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_uspec(const UzI
   if (item_skip<T>(it.st, s)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int log2H = it.log2M - 1;
+  if constexpr (std::is_same<T, float>::value) {
+    // the series workloads' sizes: the transform with its size fixed at
+    // compile time (the shared layout is the generic one's)
+    if (log2H == 12) { uspec_ct<T, 12>(it, s, tw, smem); return; }
+    if (log2H == 11) { uspec_ct<T, 11>(it, s, tw, smem); return; }
+    if (log2H == 10) { uspec_ct<T, 10>(it, s, tw, smem); return; }
+  }
   XSmem<T> sm(smem, 1 << log2H, it.log2M, tw, false);
   __syncthreads();
   const double* src = it.U + it.ldu * (int64_t)(it.st->jc + s);

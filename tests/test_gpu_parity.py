@@ -262,6 +262,27 @@ def test_batch_images_of_different_heights():
         s.close()
 
 
+def test_shared_u_transform_batch_equals_single():
+    """Engines of 32 problems or more transform u_j once per problem and grid
+    size (k_uspec, compile-time sizes for grids of 2^11..2^13 points) and the
+    X^T u products read it; alone, a problem transforms u_j inside each
+    product.  Both give the same triples and components."""
+    cases = [pkg.SSA.multi(W.mssa_series(3, seed=60 + i), 1000) for i in range(34)]
+    ref = []
+    for s in cases[:3] + cases[-2:]:
+        s.decompose(6, "fp32", seed=4)
+        ref.append((s.sigma(), s.reconstruct([[0], [1, 2]])))
+    pkg.decompose_batch(cases, 6, "fp32", seed=4)
+    for s, (sig, rec) in zip(cases[:3] + cases[-2:], ref):
+        np.testing.assert_allclose(s.sigma(), sig, rtol=1e-5, atol=0)
+        got = s.reconstruct([[0], [1, 2]])
+        for ga, gb in zip(got, rec):          # groups, then the system's series
+            for a, b in zip(ga, gb):
+                np.testing.assert_allclose(a, b, rtol=0, atol=1e-4 * float(np.nanmax(np.abs(b))))
+    for s in cases:
+        s.close()
+
+
 def test_large_batch_runs_in_two_halves_with_single_results():
     """Batches of 64 problems or more run as two interleaved halves on two
     streams; every problem still gets the result it gets alone."""
