@@ -1152,6 +1152,8 @@ struct LzEngine {
     RitzItem<T> z;
     z.st = w.st; z.U = w.U; z.ldu = w.Ls; z.Ls = w.Ls; z.V = (T*)w.V; z.ldv = w.Kl; z.Kl = w.Kl;
     z.colscale = w.colscale; z.P = w.P; z.Q = w.Q; z.ldc = w.k; z.ldcs = ritz_ldcs(w.k); z.Cs = (T*)w.Cs;
+    z.ldf = ldf_ff(w.Ls);
+    z.Uh = w.Uf; z.Ul = w.Uf ? w.Uf + (size_t)z.ldf * (w.k + 1) : nullptr;
     return z;
   }
   FinalItem<T> final_item(ssa_ctx* c) {
@@ -1447,12 +1449,7 @@ struct LzEngine {
     PhaseScope ps_(PH_RITZ, st);
     launch_ritz<T>(d_r, (int)cs.size(), mk, mkk, ts, ns, tl, nlg, 0, st);
     launch_restart(d_v, (int)cs.size(), st);
-    if (std::is_same<T, float>::value) {
-      // the kept columns U[:, 0:kk] were rewritten in FP64: refresh their float-float copy
-      std::vector<std::pair<ssa_ctx*, int>> sy;
-      for (ssa_ctx* c : cs) sy.push_back({c, c->ws.kk});
-      TRY(sync_uf(sy));
-    }
+
     CU(cudaGetLastError());
     for (auto& h : hst)
       if (h.active && h.svd_done) { h.jc = h.kk; h.svd_done = 0; }

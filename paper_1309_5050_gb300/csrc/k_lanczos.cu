@@ -2098,6 +2098,74 @@ void launch_restart(const SvdItem* items, int n, cudaStream_t st) {
   k_restart<<<n, 256, 0, st>>>(items); count_launch();
 }
 
+// Short-side Ritz vectors of the FP32 form: U[:, 0:kk] <- U[:, 0:k] P in
+// float-float from the basis's (hi, lo) copy, written to the copy and to the
+// FP64 basis.  The FP64 product (k_ritz<T, true>) ran on GB300's FP64 pipe;
+// a float-float product-sum is about a dozen FP32 instructions.  Tiling as
+// k_ritz: 64-row blocks, 4 x 4 register tiles of 16 row groups, 64 columns
+// per pass; the block's rows of every column and the coefficients (split
+// with integer instructions) are staged in shared memory first, so the
+// in-place update is safe.
+constexpr int RITZ_FF_RB = 64;
+__global__ void __launch_bounds__(256) k_ritz_short_ff(const RitzItem<float>* __restrict__ items,
+                                                       const int32_t* __restrict__ tpre, int n, int final_pass) {
+  constexpr int RB = RITZ_FF_RB, RG = RB / 4, CP = (256 / RG) * 4;
+  int rblk;
+  const RitzItem<float> it = items[tile_item(tpre, n, blockIdx.x, rblk)];
+  const LzState* st = it.st;
+  if (!final_pass && (!st->active || !st->svd_done)) return;
+  const int k = st->k;
+  const int kk = final_pass ? min(st->r, k) : st->kk;
+  const int64_t r0 = (int64_t)rblk * RB;
+  if (r0 >= it.Ls) return;
+  const int nr = (int)imin64(RB, it.Ls - r0);
+  extern __shared__ __align__(16) float2 smr[];
+  float2* blk = smr;                                   // RB x k, column-major
+  const int kkp = ((kk + CP - 1) / CP) * CP;
+  float2* cf = blk + (int64_t)RB * k;                  // k x kkp, row-major in i
+  for (int e = threadIdx.x; e < k * RB; e += blockDim.x) {
+    const int c = e / RB, t = e - c * RB;
+    blk[e] = t < nr ? make_float2(it.Uh[r0 + t + it.ldf * c], it.Ul[r0 + t + it.ldf * c]) : make_float2(0.0f, 0.0f);
+  }
+  for (int e = threadIdx.x; e < k * kkp; e += blockDim.x) {
+    const int i = e / kkp, c = e - i * kkp;
+    cf[e] = c < kk ? ff_from_double(it.P[i + (int64_t)it.ldc * c]) : make_float2(0.0f, 0.0f);
+  }
+  __syncthreads();
+  const int rg = threadIdx.x % RG, cg = threadIdx.x / RG;
+  for (int c0 = 0; c0 < kk; c0 += CP) {
+    const int cb = c0 + 4 * cg;
+    if (cb >= kk) continue;
+    ffacc acc[4][4];
+    for (int i = 0; i < k; ++i) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = blk[i * RB + 4 * rg + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = cf[i * kkp + cb + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b].fma(av[a], bv[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int c = cb + b;
+      if (c >= kk) break;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int t = 4 * rg + a;
+        if (t < nr) {
+          const ff v = acc[a][b].value();
+          it.Uh[r0 + t + it.ldf * c] = v.hi;
+          it.Ul[r0 + t + it.ldf * c] = v.lo;
+          it.U[r0 + t + it.ldu * c] = ff_to_double(make_float2(v.hi, v.lo));
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 void launch_ritz(const RitzItem<T>* items, int n, int kmax, int kkmax, const int32_t* pre_s, int tiles_s,
                  const int32_t* pre_l, int tiles_l, int final_pass, cudaStream_t st) {
@@ -2109,7 +2177,17 @@ void launch_ritz(const RitzItem<T>* items, int n, int kmax, int kkmax, const int
   const size_t sml = (size_t)rl * (kmax + 2) * sizeof(T) + (size_t)(kmax + 1) * kpl * sizeof(T);
   set_max_smem((const void*)k_ritz<T, true>);
   set_max_smem((const void*)k_ritz<T, false>);
-  if (tiles_s > 0) { k_ritz<T, true><<<tiles_s, 256, sms, st>>>(items, pre_s, n, final_pass); count_launch(); }
+  if (tiles_s > 0) {
+    if constexpr (std::is_same<T, float>::value) {
+      // the FP32 form's workspaces always carry the float-float copy
+      const int kkp = ((kkmax + 63) / 64) * 64;
+      const size_t smf = sizeof(float2) * ((size_t)RITZ_FF_RB * kmax + (size_t)kmax * kkp);
+      set_max_smem((const void*)k_ritz_short_ff);
+      k_ritz_short_ff<<<tiles_s, 256, smf, st>>>(items, pre_s, n, final_pass); count_launch();
+    } else {
+      k_ritz<T, true><<<tiles_s, 256, sms, st>>>(items, pre_s, n, final_pass); count_launch();
+    }
+  }
   if (tiles_l > 0) {
     k_ritz_coef<T><<<n, 256, 0, st>>>(items, final_pass); count_launch();
     if constexpr (std::is_same<T, float>::value)

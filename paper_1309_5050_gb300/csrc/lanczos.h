@@ -106,6 +106,7 @@ struct RitzItem {
   const double* P; const double* Q;       // from the small SVD
   int32_t ldc; int32_t ldcs;              // their leading dimension (allocated k); row length of Cs
   T* Cs;                                  // long-side coefficients Q[i, c] * colscale[i] as T, row-major
+  float* Uh; float* Ul; int64_t ldf;      // FP32 form: the short basis's float-float copy, else null
 };
 // row length of the scaled long-side coefficients for an allocated Krylov dimension k
 inline int ritz_ldcs(int k) { return ((k + 63) / 64) * 64; }
