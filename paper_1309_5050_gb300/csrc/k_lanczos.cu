@@ -979,19 +979,22 @@ __global__ void __launch_bounds__(256) k_long_init(const LongItem<T>* __restrict
 // space is already inside span U, X^T u_{j+1} is rounding again and the step
 // repeats: the remaining singular values are zero and B holds zero blocks.
 template <typename T>
-__global__ void __launch_bounds__(256) k_long_norm(const LongItem<T>* __restrict__ items, int s) {
+__global__ void __launch_bounds__(32) k_long_norm(const LongItem<T>* __restrict__ items, int s) {
+  // one warp per problem: the partials (one per channel, or per block for
+  // the start vector) summed in a fixed order; FP64 work on GB300's FP64
+  // pipe is charged per warp instruction, so more warps would only cost
   const LongItem<T> it = items[blockIdx.x];
   LzState* st = it.st;
   const int j = st->jc + s;
   if (lz_skip(st, j)) return;
-  __shared__ double red[32];
-  const double level = fmax(st->bd_floor, (sizeof(T) == 8 ? BD_REL_FP64 : BD_REL_FP32) * st->anorm);
   double a = 0.0;
   const int nb = (s < 0) ? it.nblk : it.nsum;    // start vector: its blocks; a step: nsum partials
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += it.npart[b];
-  const double beta = sqrt(block_sum(a, red));
-  const bool ok = j < 0 || beta > level;         // (the start vector is random: never replaced)
+  for (int b = threadIdx.x; b < nb; b += 32) a += it.npart[b];
+  a = warp_sum(a);
   if (threadIdx.x != 0) return;
+  const double level = fmax(st->bd_floor, (sizeof(T) == 8 ? BD_REL_FP64 : BD_REL_FP32) * st->anorm);
+  const double beta = sqrt(a);
+  const bool ok = j < 0 || beta > level;         // (the start vector is random: never replaced)
   it.colscale[j + 1] = (ok && beta > 0.0) ? 1.0 / beta : 0.0;
   if (j < 0) return;
   const double coupling = ok ? beta : 0.0;
@@ -2073,14 +2076,14 @@ void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int 
   if (n <= 0) return;
   // problems whose step ran inside their X^T u products own no blocks here
   if (tiles > 0) { k_long1<T><<<tiles, 256, 0, st>>>(items, tpre, n, s); count_launch(); }
-  k_long_norm<T><<<n, 256, 0, st>>>(items, s); count_launch();
+  k_long_norm<T><<<n, 32, 0, st>>>(items, s); count_launch();
 }
 
 template <typename T>
 void launch_long_init(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, cudaStream_t st) {
   if (n <= 0 || tiles <= 0) return;
   k_long_init<T><<<tiles, 256, 0, st>>>(items, tpre, n); count_launch();
-  k_long_norm<T><<<n, 256, 0, st>>>(items, -1); count_launch();
+  k_long_norm<T><<<n, 32, 0, st>>>(items, -1); count_launch();
 }
 
 void launch_bsvd(const SvdItem* items, int n, int kmax, cudaStream_t st) {
