@@ -221,6 +221,40 @@ __global__ void k_state_init(LzState* st, int k, int r, int kk, double tol, int 
   st->beta_k = 0.0; st->anorm = 0.0; st->tol = tol; st->sigma1 = 0.0; st->maxres = 0.0;
 }
 
+// A batch's workspace initialisation in one launch (one block per problem):
+// B and the channel partial-product buffers zeroed, the state as
+// k_state_init -- instead of three memsets and a launch per problem.
+struct WsInit {
+  LzState* st; double* B; int64_t bn;
+  void* parts_s; int64_t bytes_s; void* parts_l; int64_t bytes_l;
+  int32_t k, r, kk, maxr, full, pad_;
+  double tol; const double* xnorm; double bd_scale;
+};
+
+__device__ __forceinline__ void zero_bytes(void* p, int64_t bytes) {
+  // p is 256-byte aligned (arena), bytes a multiple of 4
+  uint4* q = reinterpret_cast<uint4*>(p);
+  const int64_t n16 = bytes >> 4;
+  for (int64_t e = threadIdx.x; e < n16; e += blockDim.x) q[e] = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t* t = reinterpret_cast<uint32_t*>(p);
+  for (int64_t e = (n16 << 2) + threadIdx.x; e < (bytes >> 2); e += blockDim.x) t[e] = 0u;
+}
+
+__global__ void __launch_bounds__(256) k_ws_init_batch(const WsInit* __restrict__ items) {
+  const WsInit it = items[blockIdx.x];
+  zero_bytes(it.B, it.bn * (int64_t)sizeof(double));
+  zero_bytes(it.parts_s, it.bytes_s);
+  zero_bytes(it.parts_l, it.bytes_l);
+  if (threadIdx.x == 0) {
+    LzState* st = it.st;
+    st->bd_floor = it.bd_scale * *it.xnorm;
+    st->full = it.full; st->sweeps = 0; st->sweeps32 = 0;
+    st->jc = 0; st->svd_done = 0; st->k = it.k; st->r = it.r; st->kk = it.kk; st->active = 1; st->converged = 0;
+    st->nconv = 0; st->breakdown = 0; st->restarts = 0; st->max_restarts = it.maxr;
+    st->beta_k = 0.0; st->anorm = 0.0; st->tol = it.tol; st->sigma1 = 0.0; st->maxres = 0.0;
+  }
+}
+
 // Continuation: the new cycle starts as after a thick restart that keeps the
 // r1 Ritz triples of the previous decomposition -- B = diag(sigma_1..r1)
 // with the column rho_i = beta_k P[k1-1, i] at r1, unit scales for the Ritz
@@ -948,7 +982,7 @@ static bool member_fuses_long(const ssa_ctx* c, bool swapped) {
 }
 
 template <typename T>
-static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
+static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w, std::vector<WsInit>* batch = nullptr) {
   w = Workspace();
   w.prec = p.prec;
   w.r = p.rank;
@@ -1014,9 +1048,11 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   TRY(c->alloc(&w.Vo, sizeof(T) * (size_t)c->K * w.r));
   TRY(c->allocT(&w.sigma, (size_t)w.r));
   TRY(c->allocT(&w.sgn, (size_t)w.r));
-  CU(cudaMemsetAsync(w.B, 0, sizeof(double) * w.k * w.k, c->stream));
-  CU(cudaMemsetAsync(w.parts_s, 0, sizeof(T) * (size_t)w.Ls * w.n_part_s, c->stream));
-  CU(cudaMemsetAsync(w.parts_l, 0, sizeof(T) * (size_t)w.Kl * w.n_part_l, c->stream));
+  if (!batch) {
+    CU(cudaMemsetAsync(w.B, 0, sizeof(double) * w.k * w.k, c->stream));
+    CU(cudaMemsetAsync(w.parts_s, 0, sizeof(T) * (size_t)w.Ls * w.n_part_s, c->stream));
+    CU(cudaMemsetAsync(w.parts_l, 0, sizeof(T) * (size_t)w.Kl * w.n_part_l, c->stream));
+  }
   double tol = p.tol > 0 ? p.tol : (std::is_same<T, float>::value ? 1e-7 : 1e-13);
   int maxr = p.max_restarts > 0 ? p.max_restarts : 40;
   c->cur = keep_cur;
@@ -1024,8 +1060,18 @@ static int alloc_ws(ssa_ctx* c, const ssa_params& p, Workspace& w) {
   for (auto& h : c->ch) lg = std::max(lg, h.log2M);
   const double eps_t = std::is_same<T, float>::value ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
   const double bd_scale = 4.0 * eps_t * (double)(lg + c->log2My);
-  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, w.k == std::min(c->L, c->K) ? 1 : 0,
-                                       c->xnorm, bd_scale); count_launch();
+  const int full = w.k == std::min(c->L, c->K) ? 1 : 0;
+  if (batch) {
+    WsInit wi;
+    wi.st = w.st; wi.B = w.B; wi.bn = (int64_t)w.k * w.k;
+    wi.parts_s = w.parts_s; wi.bytes_s = (int64_t)sizeof(T) * w.Ls * w.n_part_s;
+    wi.parts_l = w.parts_l; wi.bytes_l = (int64_t)sizeof(T) * w.Kl * w.n_part_l;
+    wi.k = w.k; wi.r = w.r; wi.kk = w.kk; wi.maxr = maxr; wi.full = full; wi.pad_ = 0;
+    wi.tol = tol; wi.xnorm = c->xnorm; wi.bd_scale = bd_scale;
+    batch->push_back(wi);
+    return SSA_OK;
+  }
+  k_state_init<<<1, 1, 0, c->stream>>>(w.st, w.k, w.r, w.kk, tol, maxr, full, c->xnorm, bd_scale); count_launch();
   CU(cudaGetLastError());
   return SSA_OK;
 }
@@ -1512,13 +1558,24 @@ static int prepare_members(ssa_ctx* const* cs, int n, const ssa_params* ps, cuda
     else need.push_back(cs[i]);
   }
   if (!need.empty()) TRY(ensure_spectra<T>(need.data(), (int)need.size(), st));
+  std::vector<WsInit> init;
   for (int i = 0; i < n; ++i) {
     if (rc[i] != SSA_OK) continue;
     ssa_ctx* c = cs[i];
     cudaStream_t keep = c->stream;
     c->stream = st;
-    rc[i] = alloc_ws<T>(c, ps[i], c->ws);
+    rc[i] = alloc_ws<T>(c, ps[i], c->ws, &init);
     c->stream = keep;
+  }
+  if (!init.empty()) {
+    WsInit* d = nullptr;
+    if (cudaMallocAsync((void**)&d, sizeof(WsInit) * init.size(), st) != cudaSuccess)
+      return fail(SSA_ENOMEM, "workspace init items");
+    if (g_ring.copy(d, init.data(), sizeof(WsInit) * init.size(), st) != SSA_OK)
+      return fail(SSA_ECUDA, "workspace init item upload");
+    k_ws_init_batch<<<(unsigned)init.size(), 256, 0, st>>>(d); count_launch();
+    CU(cudaGetLastError());
+    cudaFreeAsync(d, st);
   }
   return SSA_OK;
 }
