@@ -6,9 +6,13 @@ groups whose boundaries sit in spectral gaps (a group that splits a cluster
 of near-equal singular values has no unique answer), and with the closed
 form of two exactly separable harmonics.
 
-Tolerances: FP64 form 1e-8 on rho and relative on the contributions; FP32
-form 1e-3 (the components carry the FP32 form's 1e-4 max|x| error, divided
-by their own weighted norms).
+Tolerances: FP64 form 1e-11 on rho and relative on the contributions; FP32
+form 1e-5.  rho and the contributions are ratios of weighted inner products
+of the components, so the components' relative error (FP32 form: a few
+FP32 roundings per product and per diagonal average, about 1e-6 of their
+norms at these sizes) enters once, not amplified.  Measured on a GB300: FP32
+rho 2.9e-8, contributions 7.9e-7; FP64 rho 1.4e-14, contributions 1.8e-14
+-- the bounds sit more than ten times above them.
 """
 import numpy as np
 import pytest
@@ -24,7 +28,7 @@ import workloads as W  # noqa: E402
 from oracle import ssa_oracle as O  # noqa: E402
 from paper_1309_5050_gb300 import _lib as LL  # noqa: E402
 
-TOL = {"fp32": 1e-3, "fp64": 1e-8}
+TOL = {"fp32": 1e-5, "fp64": 1e-11}
 
 
 def gap_groups(sig, min_gap=1.1):
@@ -66,6 +70,8 @@ def test_wcor_matches_oracle(prec):
         assert len(groups) >= 2, name
         rho, contrib = s.wcor(groups)
         rho_o, contrib_o = O.wcor(P, so, Uo, Vo, groups)
+        print(f"wcor {name} {prec}: rho {np.max(np.abs(rho - rho_o)):.3e}, "
+              f"contributions {np.max(np.abs(contrib - contrib_o) / np.abs(contrib_o)):.3e}")
         assert np.max(np.abs(rho - rho_o)) <= TOL[prec], (name, rho, rho_o)
         np.testing.assert_allclose(contrib, contrib_o, rtol=TOL[prec], atol=0, err_msg=name)
         np.testing.assert_array_equal(rho, rho.T)

@@ -6,9 +6,11 @@ from the window-side vectors and continues every series.  Checked against the
 continuation of a finite-rank series and against the oracle on noisy series
 and an MSSA system (groups bounded by spectral gaps).
 
-Tolerances: FP64 form 1e-7 of max|x|; FP32 form 5e-3 of max|x| (the
-starting values carry the FP32 form's reconstruction error, up to 1e-4 of
-max|x|, and the forecast feeds on itself).
+Tolerances: FP64 form 1e-8 of max|x|; FP32 form 2e-4 of max|x|.  The
+starting values carry the reconstruction error (FP32 form: bounded by 1e-4
+of max|x|, about 1e-6 at these sizes) and the recurrence feeds on itself
+over 8-12 steps, so the error grows with the steps.  Measured on a GB300: FP32 2.6e-5, FP64 3.7e-10 of max|x|
+at most -- the bounds sit more than seven and twenty times above them.
 """
 import numpy as np
 import pytest
@@ -23,7 +25,7 @@ import paper_1309_5050_gb300 as pkg  # noqa: E402
 from oracle import ssa_oracle as O  # noqa: E402
 from paper_1309_5050_gb300 import _lib as LL  # noqa: E402
 
-TOL = {"fp32": 5e-3, "fp64": 1e-7}
+TOL = {"fp32": 2e-4, "fp64": 1e-8}
 
 
 def noisy_series(n, seed):
@@ -59,6 +61,7 @@ def test_forecast_matches_oracle(prec):
     assert so[4] / so[5] > 1.5
     (ref,) = O.forecast_recurrent_column(P, so, Uo, Vo, grp, 12)
     got = s.forecast(grp, 12)
+    print(f"forecast {prec}: {np.max(np.abs(got - ref)) / np.max(np.abs(x)):.3e} of max|x|")
     assert np.max(np.abs(got - ref)) <= TOL[prec] * np.max(np.abs(x))
     s.close()
     xs = [noisy_series(n, 20 + i) for i, n in enumerate((300, 350, 280))]
@@ -71,6 +74,7 @@ def test_forecast_matches_oracle(prec):
     refs = O.forecast_recurrent_column(Pm, so, Uo, Vo, grp, 8)
     gots = m.forecast(grp, 8)
     for g, r_ in zip(gots, refs):
+        print(f"forecast {prec}: {np.max(np.abs(g - r_)) / max(np.max(np.abs(v)) for v in xs32):.3e} of max|x|")
         assert np.max(np.abs(g - r_)) <= TOL[prec] * max(np.max(np.abs(v)) for v in xs32)
     m.close()
 
@@ -121,6 +125,7 @@ def test_vector_forecast_matches_oracle(prec):
     so, Uo, Vo = O.decompose(P, 6)
     (ref,) = O.forecast_vector_column(P, so, Uo, Vo, grp, 12)
     got = s.forecast(grp, 12, method="vector")
+    print(f"forecast {prec}: {np.max(np.abs(got - ref)) / np.max(np.abs(x)):.3e} of max|x|")
     assert np.max(np.abs(got - ref)) <= TOL[prec] * np.max(np.abs(x))
     s.close()
     xs = [noisy_series(n, 20 + i) for i, n in enumerate((300, 350, 280))]
@@ -132,6 +137,7 @@ def test_vector_forecast_matches_oracle(prec):
     refs = O.forecast_vector_column(Pm, so, Uo, Vo, grp, 8)
     gots = m.forecast(grp, 8, method="vector")
     for g, r_ in zip(gots, refs):
+        print(f"forecast {prec}: {np.max(np.abs(g - r_)) / max(np.max(np.abs(v)) for v in xs32):.3e} of max|x|")
         assert np.max(np.abs(g - r_)) <= TOL[prec] * max(np.max(np.abs(v)) for v in xs32)
     m.close()
     img = np.random.default_rng(2).normal(size=(20, 20))
@@ -160,6 +166,7 @@ def test_row_forecasts_match_oracle(method, prec):
     refs = ref_fn(Pm, so, Uo, Vo, grp, 8)
     gots = m.forecast(grp, 8, method=method)
     for g, r_ in zip(gots, refs):
+        print(f"forecast {prec}: {np.max(np.abs(g - r_)) / max(np.max(np.abs(v)) for v in xs32):.3e} of max|x|")
         assert np.max(np.abs(g - r_)) <= TOL[prec] * max(np.max(np.abs(v)) for v in xs32)
     m.close()
     n = np.arange(80, dtype=float)
