@@ -290,8 +290,18 @@ __global__ void k_convert(const TI* in, TO* out, int64_t n) {
     out[i] = (TO)in[i];
 }
 
-__global__ void k_gather_states(LzState* const* src, int n, LzState* dst) {
+// The device error counters an engine checks at the end of a chunk; their
+// values ride along with the states' read-back (no extra synchronisation).
+constexpr int N_ERR_WORDS = 4;
+enum { EW_MV_ASYNC = 0, EW_YPASS = 1, EW_RITZ_TC = 2, EW_SHORT_TMA = 3 };
+struct ErrWords { int* w[N_ERR_WORDS]; };
+
+__global__ void k_gather_states(LzState* const* src, int n, LzState* dst, ErrWords ew) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = *src[i];
+  if (blockIdx.x == 0 && threadIdx.x < N_ERR_WORDS) {
+    const int* w = ew.w[threadIdx.x];
+    reinterpret_cast<int*>(dst + n)[threadIdx.x] = w ? *w : 0;
+  }
 }
 
 __global__ void k_kmask(const uint32_t* kbits, int kwords, int cx, int cy, int nx, int ny, uint8_t* out) {
@@ -1105,7 +1115,7 @@ struct LzEngine {
   int n_uz = 0, max_uz_log2 = 1;
   bool share_u = false;            // X^T u products take u's transform from k_uspec
   MvSet<T> mvA, mvAT;
-  int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_r = 1;
+  int max_blk_s = 1, max_blk_l = 1, max_k = 1, max_kk = 1, max_r = 1;
   int64_t max_Ls = 1, max_Kl = 1, max_rows = 1;
   int max_log2Mx = 1, max_log2My = 0;
   std::vector<void*> dev_tmp;
@@ -1114,7 +1124,7 @@ struct LzEngine {
 
   ~LzEngine() { release_items(); if (h_st) cudaFreeHost(h_st); }
 
-  std::vector<void*> chunk_tmp;   // per-restart item arrays, freed by the next chunk
+  std::vector<void*> chunk_tmp;   // per-chunk item arrays, freed by the next chunk
   void release_chunk() {
     for (void* p : chunk_tmp) cudaFreeAsync(p, st);
     chunk_tmp.clear();
@@ -1254,7 +1264,7 @@ struct LzEngine {
     share_u = live.size() >= 32;
     std::vector<ShortItem> sh; std::vector<LongItem<T>> lg; std::vector<SvdItem> sv;
     std::vector<RitzItem<T>> rz; std::vector<LzState*> stp;
-    max_blk_s = max_blk_l = max_k = max_r = 1;
+    max_blk_s = max_blk_l = max_k = max_kk = max_r = 1;
     max_Ls = max_Kl = max_rows = 1;
     max_log2Mx = 1; max_log2My = 0;
     for (size_t i = 0; i < live.size(); ++i) {
@@ -1301,6 +1311,7 @@ struct LzEngine {
       max_blk_s = std::max(max_blk_s, w.nblk_s);
       max_blk_l = std::max(max_blk_l, w.nblk_l);
       max_k = std::max(max_k, w.k);
+      max_kk = std::max(max_kk, w.kk);
       max_r = std::max(max_r, w.r);
       max_Ls = std::max(max_Ls, w.Ls);
       max_Kl = std::max(max_Kl, w.Kl);
@@ -1350,13 +1361,15 @@ struct LzEngine {
     auto upl = [&](auto& v, auto** d) { return up(v, d); };
     TRY(finish_set(mvA, upl));
     TRY(finish_set(mvAT, upl));
-    if (cudaMallocAsync((void**)&d_stg, sizeof(LzState) * live.size(), st) != cudaSuccess)
+    if (cudaMallocAsync((void**)&d_stg, sizeof(LzState) * live.size() + sizeof(int) * N_ERR_WORDS, st) !=
+        cudaSuccess)
       return fail(SSA_ENOMEM, "engine state buffer");
     dev_tmp.push_back(d_stg);
     if ((int)live.size() > h_cap) {
       if (h_st) cudaFreeHost(h_st);
       h_cap = std::max((int)live.size(), 256);
-      if (cudaHostAlloc((void**)&h_st, sizeof(LzState) * h_cap, cudaHostAllocDefault) != cudaSuccess) {
+      if (cudaHostAlloc((void**)&h_st, sizeof(LzState) * h_cap + sizeof(int) * N_ERR_WORDS, cudaHostAllocDefault) !=
+          cudaSuccess) {
         h_st = nullptr; h_cap = 0;
         return fail(SSA_ENOMEM, "pinned state buffer");
       }
@@ -1420,27 +1433,54 @@ struct LzEngine {
     run_mv<T>(device, mvAT, 0, st);
     { PhaseScope ps_(PH_LONG, st); launch_long_step<T>(d_lg, t_lg, nl, n_lg, 0, st); }
   }
-  // small SVDs of the members whose cycle ended, and the state read-back (async)
+  // Small SVDs of the members whose cycle ended, then their thick restarts
+  // (Ritz vectors, new B) -- launched over every member: the kernels pick the
+  // members on the device (active, small SVD done), so the restart needs no
+  // read-back first -- and the state read-back (async).
   int finish_chunk_async() {
     const int nl = (int)live.size();
-    { PhaseScope ps_(PH_RITZ, st); launch_bsvd(d_sv, nl, max_k, st); }
+    {
+      PhaseScope ps_(PH_RITZ, st);
+      launch_bsvd(d_sv, nl, max_k, st);
+      launch_ritz<T>(d_rz, nl, max_k, max_kk, t_rs, n_rs, t_rl, n_rl, 0, st);
+      launch_restart(d_sv, nl, st);
+    }
     CU(cudaGetLastError());
-    k_gather_states<<<1, 128, 0, st>>>(d_stp, nl, d_stg); count_launch();
-    CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl, cudaMemcpyDeviceToHost, st));
+    ErrWords ew;
+    ew.w[EW_MV_ASYNC] = mv_async_timeout_word();
+    ew.w[EW_YPASS] = ypass_bad_tile_word();
+    ew.w[EW_RITZ_TC] = ritz_tc_timeout_word();
+    ew.w[EW_SHORT_TMA] = short_tma_timeout_word();
+    for (int q = 0; q < N_ERR_WORDS; ++q)
+      if (!ew.w[q]) return fail(SSA_ECUDA, "device error counters unavailable");
+    k_gather_states<<<1, 128, 0, st>>>(d_stp, nl, d_stg, ew); count_launch();
+    CU(cudaMemcpyAsync(h_st, d_stg, sizeof(LzState) * nl + sizeof(int) * N_ERR_WORDS, cudaMemcpyDeviceToHost, st));
     return SSA_OK;
   }
+  // after the states' read-back: the chunk's error counters (nonzero ones are
+  // reset on the device and reported)
   int finish_chunk_sync() {
     const int nl = (int)live.size();
     CU(cudaStreamSynchronize(st));
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
-    if ((mvA.n1() || mvAT.n1()) && mv_async_timeouts(st) != 0)
-      return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
-    if (max_log2My > 0 && ypass_bad_tiles(st) != 0)
-      return fail(SSA_ECUDA, "a y-pass tile did not fit its launch's buffers");
-    if (std::is_same<T, float>::value && ritz_tc_timeouts(st) != 0)
-      return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
-    if (std::is_same<T, float>::value && n_shf && short_tma_timeouts(st) != 0)
-      return fail(SSA_ETIMEOUT, "a bulk copy of the short-side basis did not complete");
+    const int* err = reinterpret_cast<const int*>(h_st + nl);
+    bool any = false;
+    for (int q = 0; q < N_ERR_WORDS; ++q) any |= err[q] != 0;
+    if (any) {
+      const int e_mv = err[EW_MV_ASYNC], e_y = err[EW_YPASS], e_rt = err[EW_RITZ_TC], e_sh = err[EW_SHORT_TMA];
+      const int z = 0;
+      int* words[N_ERR_WORDS] = {mv_async_timeout_word(), ypass_bad_tile_word(), ritz_tc_timeout_word(),
+                                 short_tma_timeout_word()};
+      for (int q = 0; q < N_ERR_WORDS; ++q)
+        if (err[q] && words[q]) cudaMemcpyAsync(words[q], &z, sizeof(int), cudaMemcpyHostToDevice, st);
+      cudaStreamSynchronize(st);
+      if (e_mv) return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
+      if (e_y) return fail(SSA_ECUDA, "a y-pass tile did not fit its launch's buffers");
+      if (e_rt) return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
+      if (e_sh) return fail(SSA_ETIMEOUT, "a bulk copy of the short-side basis did not complete");
+    }
+    if (std::is_same<T, float>::value && ritz_tc_plan_failures() != 0)
+      return fail(SSA_ENOMEM, "no scratch for a tensor-core Ritz update's tile plan");
     return SSA_OK;
   }
   // One chunk: every member inside a cycle advances up to `steps` Lanczos
@@ -1458,48 +1498,6 @@ struct LzEngine {
   bool any_active() const {
     for (auto& h : hst) if (h.active) return true;
     return false;
-  }
-  bool any_restart() const {
-    for (auto& h : hst) if (h.active && h.svd_done) return true;
-    return false;
-  }
-
-  // restart the members whose cycle ended without convergence (the kernels
-  // skip every other member); the host copies follow
-  int restart_active() {
-    std::vector<ssa_ctx*> cs;
-    std::vector<RitzItem<T>> rz;
-    std::vector<SvdItem> sv;
-    int mk = 1, mkk = 1;
-    for (size_t i = 0; i < live.size(); ++i)
-      if (hst[i].active && hst[i].svd_done) {
-        cs.push_back(live[i]);
-        rz.push_back(ritz_item(live[i]));
-        sv.push_back(svd_item(live[i]));
-        mk = std::max(mk, live[i]->ws.k);
-        mkk = std::max(mkk, live[i]->ws.kk);
-      }
-    if (cs.empty()) return SSA_OK;
-    RitzItem<T>* d_r = nullptr; SvdItem* d_v = nullptr;
-    int32_t *ts = nullptr, *tl = nullptr;
-    int ns = 0, nlg = 0;
-    if (cs.size() == live.size()) {        // everyone: the member-wide arrays
-      d_r = d_rz; d_v = d_sv; ts = t_rs; tl = t_rl; ns = n_rs; nlg = n_rl;
-    } else {
-      const size_t keep = dev_tmp.size();
-      TRY(up(rz, &d_r)); TRY(up(sv, &d_v));
-      TRY(ritz_tiles(cs, &ts, &ns, &tl, &nlg));
-      chunk_tmp.insert(chunk_tmp.end(), dev_tmp.begin() + keep, dev_tmp.end());
-      dev_tmp.resize(keep);
-    }
-    PhaseScope ps_(PH_RITZ, st);
-    launch_ritz<T>(d_r, (int)cs.size(), mk, mkk, ts, ns, tl, nlg, 0, st);
-    launch_restart(d_v, (int)cs.size(), st);
-
-    CU(cudaGetLastError());
-    for (auto& h : hst)
-      if (h.active && h.svd_done) { h.jc = h.kk; h.svd_done = 0; }
-    return SSA_OK;
   }
 
   // final Ritz vectors and outputs of the given members
@@ -1649,8 +1647,6 @@ static int decompose_batch_T(ssa_ctx* const* cs, int n, const ssa_params* ps, in
         if (!engs[g].live.empty()) TRY(engs[g].finish_chunk_async());
       for (int g = 0; g < ng; ++g)
         if (!engs[g].live.empty()) TRY(engs[g].finish_chunk_sync());
-      for (int g = 0; g < ng; ++g)
-        if (!engs[g].live.empty()) TRY(engs[g].restart_active());
     }
     for (int g = 0; g < ng; ++g) {
       LzEngine<T>& eng = engs[g];
@@ -1758,7 +1754,6 @@ static int continue_T(ssa_ctx* c, const ssa_params& p) {
   TRY(e.build());
   while (e.any_active()) {
     TRY(e.run_chunk());
-    TRY(e.restart_active());
   }
   std::vector<int> all{0};
   TRY(e.retire(all));
@@ -3087,7 +3082,6 @@ int server_round(ssa_server* s, LzEngine<T>& eng, std::vector<SrvReq*>& live, st
   for (size_t i = 0; i < eng.live.size(); ++i)
     if (!eng.hst[i].active) done.push_back((int)i);
   TRY(eng.retire(done));
-  TRY(eng.restart_active());
   if (!done.empty()) {
     std::vector<ssa_ctx*> cs;
     std::vector<RecReq> req;

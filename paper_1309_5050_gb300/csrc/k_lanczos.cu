@@ -756,6 +756,24 @@ static size_t short_tma_smem(int64_t sld, int cw) {
   return sizeof(float2) * ((size_t)sld * (1 + SHORT_TMA_S * (size_t)cw) + (size_t)(KMAX + 1) * (16 / cw));
 }
 
+
+// device address of a counter on the current device (looked up once per device)
+static int* counter_word(const void* sym, int* (&cache)[64]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cache[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, sym) != cudaSuccess) return nullptr;
+    cache[dev] = static_cast<int*>(p);
+  }
+  return cache[dev];
+}
+
+int* short_tma_timeout_word() {
+  static int* cache[64] = {};
+  return counter_word((const void*)&g_short_tma_timeouts, cache);
+}
+
 int short_tma_timeouts(cudaStream_t st) {
   int h = 0, z = 0;
   if (cudaMemcpyFromSymbolAsync(&h, g_short_tma_timeouts, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)

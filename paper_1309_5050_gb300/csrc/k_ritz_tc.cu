@@ -387,6 +387,25 @@ void launch_ritz_tc(const RitzItem<float>* items, int n, int kmax, int kkmax, co
   cudaFreeAsync(d, st);
 }
 
+
+// device address of a counter on the current device (looked up once per device)
+static int* counter_word(const void* sym, int* (&cache)[64]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cache[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, sym) != cudaSuccess) return nullptr;
+    cache[dev] = static_cast<int*>(p);
+  }
+  return cache[dev];
+}
+
+int* ritz_tc_timeout_word() {
+  static int* cache[64] = {};
+  return counter_word((const void*)&g_ritz_tc_timeouts, cache);
+}
+int ritz_tc_plan_failures() { return g_rtc_plan_fail.exchange(0); }
+
 int ritz_tc_timeouts(cudaStream_t st) {
   if (g_rtc_plan_fail.exchange(0) != 0) return 1;
   int h = 0, z = 0;

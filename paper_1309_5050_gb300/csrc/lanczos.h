@@ -152,6 +152,9 @@ void launch_uf_sync(const ShortItem* items, const int32_t* ncols, int n, cudaStr
 // Bulk-copy waits of the float-float short side that gave up since the last call
 // (read and reset; -1 on a CUDA error).
 int short_tma_timeouts(cudaStream_t st);
+// device address of that counter (current device), for a read-back that
+// rides along with other copies; null on a CUDA error
+int* short_tma_timeout_word();
 template <typename T>
 void launch_long_step(const LongItem<T>* items, const int32_t* tpre, int n, int tiles, int s, cudaStream_t st);
 template <typename T>
@@ -170,6 +173,11 @@ void launch_ritz_tc(const RitzItem<float>* items, int n, int kmax, int kkmax, co
 // bounded MMA-barrier waits of k_ritz_tc that gave up since the last call
 // (read and reset; synchronises the stream; -1 on a CUDA error)
 int ritz_tc_timeouts(cudaStream_t st);
+// device address of k_ritz_tc's counter (current device), null on a CUDA
+// error; and launches skipped for want of plan scratch since the last call
+// (read and reset, host side)
+int* ritz_tc_timeout_word();
+int ritz_tc_plan_failures();
 template <typename T>
 void launch_finalize(const FinalItem<T>* items, int n, int max_r, int64_t max_rows, cudaStream_t st);
 
