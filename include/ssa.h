@@ -302,7 +302,9 @@ int ssa_matvec(ssa_ctx* ctx, int32_t transpose, int32_t prec, const double* in, 
  * fixed shared-memory budget).  ssa_autotune times one decomposition of ctx
  * for each candidate -- k in {2/3, 1, 3/2, 2} x the default (clipped to
  * [r, min(112, L, K)]), then for 2D grids the tile in {1/2, 2, 4} x the
- * default that fit a block -- keeps the fastest converged one and records it
+ * default that fit a block -- keeps the fastest converged one (a candidate
+ * replaces the default, or the tile chosen so far, only when it is more than
+ * 2% faster: smaller differences are within run-to-run noise) and records it
  * as the plan of its size class: k keyed by (precision form, kind, L,
  * ceil log2 K, r), the tile by (element size, grid).  Every later
  * decomposition with krylov_dim = 0 and every product on such a grid uses
