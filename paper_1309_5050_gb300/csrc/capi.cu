@@ -290,10 +290,11 @@ __global__ void k_convert(const TI* in, TO* out, int64_t n) {
     out[i] = (TO)in[i];
 }
 
-// The device error counters an engine checks at the end of a chunk; their
-// values ride along with the states' read-back (no extra synchronisation).
-constexpr int N_ERR_WORDS = 4;
-enum { EW_MV_ASYNC = 0, EW_YPASS = 1, EW_RITZ_TC = 2, EW_SHORT_TMA = 3 };
+// Device error counters of the Lanczos kernels that an engine checks at the
+// end of a chunk; their values ride along with the states' read-back (no
+// extra synchronisation).
+constexpr int N_ERR_WORDS = 2;
+enum { EW_RITZ_TC = 0, EW_SHORT_TMA = 1 };
 struct ErrWords { int* w[N_ERR_WORDS]; };
 
 __global__ void k_gather_states(LzState* const* src, int n, LzState* dst, ErrWords ew) {
@@ -1447,8 +1448,6 @@ struct LzEngine {
     }
     CU(cudaGetLastError());
     ErrWords ew;
-    ew.w[EW_MV_ASYNC] = mv_async_timeout_word();
-    ew.w[EW_YPASS] = ypass_bad_tile_word();
     ew.w[EW_RITZ_TC] = ritz_tc_timeout_word();
     ew.w[EW_SHORT_TMA] = short_tma_timeout_word();
     for (int q = 0; q < N_ERR_WORDS; ++q)
@@ -1458,27 +1457,27 @@ struct LzEngine {
     return SSA_OK;
   }
   // after the states' read-back: the chunk's error counters (nonzero ones are
-  // reset on the device and reported)
+  // reset on the device and reported); the series products' counters are
+  // read (and reset) by their own calls
   int finish_chunk_sync() {
     const int nl = (int)live.size();
     CU(cudaStreamSynchronize(st));
     for (int i = 0; i < nl; ++i) hst[i] = h_st[i];
     const int* err = reinterpret_cast<const int*>(h_st + nl);
-    bool any = false;
-    for (int q = 0; q < N_ERR_WORDS; ++q) any |= err[q] != 0;
-    if (any) {
-      const int e_mv = err[EW_MV_ASYNC], e_y = err[EW_YPASS], e_rt = err[EW_RITZ_TC], e_sh = err[EW_SHORT_TMA];
+    if (err[EW_RITZ_TC] || err[EW_SHORT_TMA]) {
+      const int e_rt = err[EW_RITZ_TC], e_sh = err[EW_SHORT_TMA];
       const int z = 0;
-      int* words[N_ERR_WORDS] = {mv_async_timeout_word(), ypass_bad_tile_word(), ritz_tc_timeout_word(),
-                                 short_tma_timeout_word()};
+      int* words[N_ERR_WORDS] = {ritz_tc_timeout_word(), short_tma_timeout_word()};
       for (int q = 0; q < N_ERR_WORDS; ++q)
         if (err[q] && words[q]) cudaMemcpyAsync(words[q], &z, sizeof(int), cudaMemcpyHostToDevice, st);
       cudaStreamSynchronize(st);
-      if (e_mv) return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
-      if (e_y) return fail(SSA_ECUDA, "a y-pass tile did not fit its launch's buffers");
       if (e_rt) return fail(SSA_ETIMEOUT, "a tensor-core Ritz update did not complete");
       if (e_sh) return fail(SSA_ETIMEOUT, "a bulk copy of the short-side basis did not complete");
     }
+    if ((mvA.n1() || mvAT.n1()) && mv_async_timeouts(st) != 0)
+      return fail(SSA_ETIMEOUT, "a bulk copy of a data spectrum did not complete");
+    if (max_log2My > 0 && ypass_bad_tiles(st) != 0)
+      return fail(SSA_ECUDA, "a y-pass tile did not fit its launch's buffers");
     if (std::is_same<T, float>::value && ritz_tc_plan_failures() != 0)
       return fail(SSA_ENOMEM, "no scratch for a tensor-core Ritz update's tile plan");
     return SSA_OK;

@@ -621,28 +621,6 @@ int ypass_bad_tiles(cudaStream_t st) {
   return h;
 }
 
-
-// device address of a counter on the current device (looked up once per device)
-static int* counter_word(const void* sym, int* (&cache)[64]) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!cache[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, sym) != cudaSuccess) return nullptr;
-    cache[dev] = static_cast<int*>(p);
-  }
-  return cache[dev];
-}
-
-int* mv_async_timeout_word() {
-  static int* cache[64] = {};
-  return counter_word((const void*)&g_mv_async_timeouts, cache);
-}
-int* ypass_bad_tile_word() {
-  static int* cache[64] = {};
-  return counter_word((const void*)&g_ypass_bad_tiles, cache);
-}
-
 // Bulk-copy waits that gave up since the last call (read and reset).
 int mv_async_timeouts(cudaStream_t st) {
   int h = 0, z = 0;

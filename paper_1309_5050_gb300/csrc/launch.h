@@ -40,10 +40,6 @@ int mv_async_timeouts(cudaStream_t st);
 // buffers (a sizing fault of the host, reported rather than run) since the
 // last call; read and reset, -1 on a CUDA error.
 int ypass_bad_tiles(cudaStream_t st);
-// device addresses of those two counters (current device), for a read-back
-// that rides along with other copies; null on a CUDA error
-int* mv_async_timeout_word();
-int* ypass_bad_tile_word();
 
 // y-pass blocks stage tk x-frequencies (all My rows) in two buffers of
 // YPASS_BUF_BYTES (grown to one padded column where a column is larger), so
