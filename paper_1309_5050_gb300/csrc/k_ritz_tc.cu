@@ -102,7 +102,7 @@ __host__ __device__ inline size_t rtc_off_rec(int n) {
 __global__ void __launch_bounds__(1024) k_ritz_tc_plan(const RitzItem<float>* __restrict__ items, int n,
                                                        int final_pass, unsigned char* scratch) {
   __shared__ int32_t wt[32], wf[32];    // per-warp tile and problem counts
-  __shared__ int32_t carry[2];          // tiles, problems before this round
+  __shared__ int32_t carry[2];          // tiles, problems of the earlier 1024-item slices
   RtcPlan* pl = reinterpret_cast<RtcPlan*>(scratch);
   int32_t* const pre = reinterpret_cast<int32_t*>(scratch + RTC_OFF_PRE);
   RtcRec* const rec = reinterpret_cast<RtcRec*>(scratch + rtc_off_rec(n));
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(1024) k_ritz_tc_plan(const RitzItem<float>* __
       const int a = __shfl_up_sync(0xffffffffu, tinc, o), b = __shfl_up_sync(0xffffffffu, finc, o);
       if (lane >= o) { tinc += a; finc += b; }
     }
-    __syncthreads();                    // carry of the previous round read by all
+    __syncthreads();                    // carry of the earlier slices read by all
     const int c0 = carry[0], c1 = carry[1];
     if (lane == 31) { wt[warp] = tinc; wf[warp] = finc; }
     __syncthreads();
