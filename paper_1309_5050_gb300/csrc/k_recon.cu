@@ -166,7 +166,8 @@ __global__ void k_rec_fold(const RecFoldItem* __restrict__ items) {
 }
 
 // One warp per border element p: x~[p] = (1/w_p) sum over the anti-diagonal
-// i + j = p of sum_{c in group} sigma_c U[i, c] V[j, c], in FP64.
+// i + j = p of sum_{c in group} sigma_c U[i, c] V[j, c], summed directly
+// (not through the FFT, whose absolute error the small w_p would magnify).
 __global__ void __launch_bounds__(256) k_rec_border(const RecBorderItem* __restrict__ items) {
   const RecBorderItem it = items[blockIdx.y];
   const int lane = threadIdx.x & 31;
