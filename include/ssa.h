@@ -53,8 +53,12 @@ enum {
 
 typedef enum { SSA_1D = 0, SSA_MSSA = 1, SSA_2D = 2 } ssa_kind;  /* SSA_2D covers shaped */
 typedef enum { SSA_F32 = 0, SSA_F64 = 1 } ssa_dtype;
-/* Precision forms: FFTs, matvecs and the long-side Lanczos basis in FP32 with
- * FP64 re-orthogonalisation, small SVD and reconstruction sums; or all FP64. */
+/* Precision forms: FFTs, matvecs and the long-side Lanczos basis in FP32; the
+ * short basis stored in FP64 and re-orthogonalised in FP32 plus float-float
+ * (about 48 significant bits); the small SVD's rotations found in FP32 and
+ * polished in float-float; reconstruction sums in FP32 (complete series, the
+ * low-weight ends summed directly) or FP64 -- the name keeps the form's
+ * first definition, FP64 re-orthogonalisation; or all FP64. */
 typedef enum { SSA_PREC_FP32FFT_FP64REORTH = 0, SSA_PREC_FP64 = 1 } ssa_prec;
 
 typedef struct ssa_ctx ssa_ctx;
